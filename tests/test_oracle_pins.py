@@ -1,0 +1,442 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these re-types the oracle's formula: each compares it with a closed
+form, a brute-force enumeration, an invariant, a value the paper prints
+(fixtures in tests/golden/) or the exact result of a special case.
+"""
+
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import acom_oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+AU = _golden("fig1_fcc_au.json")
+A_AU = AU["lattice_constant_A"]
+LAM = 0.01969
+
+
+def au_reflections(q_max=1.5, **kw):
+    L = np.eye(3) * A_AU
+    return O.reflections(L, AU["frac_pos"], [79.0] * 4, [0.25] * 4, q_max, **kw)
+
+
+def mg_lattice():
+    a, c = 3.21, 5.21
+    return np.array([[a, 0, 0], [-a / 2, a * math.sqrt(3) / 2, 0], [0, 0, c]])
+
+
+MG_POS = [[1 / 3, 2 / 3, 1 / 4], [2 / 3, 1 / 3, 3 / 4]]
+
+
+@pytest.fixture(scope="module")
+def c1_plan():
+    v0, v1, v2, om = O.cubic_triangle()
+    za = O.zone_axis_grid(v0, v1, v2, 2.0, om)
+    prm = O.PlanParams(n_shells=75, dq=0.02, n_phi=180, delta=0.08, lam=LAM)
+    return O.orientation_plan(au_reflections(), za, prm)
+
+
+# ---------------------------------------------------------------- Eq. 1 ----
+
+@pytest.mark.parametrize("lattice", [
+    np.eye(3) * 4.08,
+    mg_lattice(),
+    np.array([[3.1, 0.2, -0.1], [0.4, 4.3, 0.3], [-0.2, 0.5, 5.7]]),
+])
+def test_reciprocal_basis_duality(lattice):
+    """a_i* . a_j = delta_ij is the defining property of the reciprocal basis
+    without 2 pi."""
+    rb = O.reciprocal_basis(lattice)
+    np.testing.assert_allclose(rb @ np.asarray(lattice).T, np.eye(3), atol=1e-14)
+
+
+# ------------------------------------------------------------- Eqs. 2-3 ----
+
+def test_fcc_reflection_set_and_structure_factor_closed_form():
+    """fcc: F = 4 f(|g|) when h, k, l are all even or all odd, 0 otherwise.
+    Brute force over a box twice as large as needed finds the same set."""
+    refl = au_reflections(drop_extinct=False)
+    q = np.linalg.norm(refl.g, axis=1)
+    f = 79.0 * np.exp(-0.25 * q * q)
+    h, k, l = refl.hkl.T
+    unmixed = ((h % 2) == (k % 2)) & ((k % 2) == (l % 2))
+    np.testing.assert_allclose(refl.F[unmixed].real, 4 * f[unmixed], rtol=1e-12)
+    np.testing.assert_allclose(refl.F[unmixed].imag, 0, atol=1e-10)
+    np.testing.assert_allclose(np.abs(refl.F[~unmixed]), 0, atol=1e-10)
+    # independent enumeration: cubic lattice, |g| = |hkl| / a
+    n = 2 * int(1.5 * A_AU) + 2
+    brute = set()
+    for hh, kk, ll in itertools.product(range(-n, n + 1), repeat=3):
+        qq = math.sqrt(hh * hh + kk * kk + ll * ll) / A_AU
+        if 0 < qq < 1.5:
+            brute.add((hh, kk, ll))
+    assert brute == set(map(tuple, refl.hkl.tolist()))
+    live = au_reflections()
+    assert len(live.F) == int(unmixed.sum()) == 258
+    radii = np.unique(np.round(np.linalg.norm(live.g, axis=1), 9))
+    assert len(radii) == 13
+    assert abs(radii[0] - math.sqrt(3) / A_AU) < 1e-9       # {111}
+    assert abs(radii[1] - 2 / A_AU) < 1e-9                  # {200}
+
+
+def test_hcp_structure_factor_closed_form():
+    """hcp basis (1/3,2/3,1/4), (2/3,1/3,3/4): |F|^2 = 0 for h+2k = 0 mod 3
+    and l odd; 4 f^2 for h+2k = 0 mod 3, l even; 3 f^2 for h+2k != 0 mod 3,
+    l odd; f^2 for h+2k != 0 mod 3, l even."""
+    refl = O.reflections(mg_lattice(), MG_POS, [12.0] * 2, [0.3] * 2, 1.5,
+                         drop_extinct=False)
+    q = np.linalg.norm(refl.g, axis=1)
+    f2 = (12.0 * np.exp(-0.3 * q * q)) ** 2
+    h, k, l = refl.hkl.T
+    m3 = ((h + 2 * k) % 3) == 0
+    lodd = (l % 2) != 0
+    expect = np.where(m3 & lodd, 0.0, np.where(m3, 4.0, np.where(lodd, 3.0, 1.0)))
+    np.testing.assert_allclose(np.abs(refl.F) ** 2, expect * f2, rtol=1e-9,
+                               atol=1e-9 * f2.max())
+    # with a hexagonal basis the search box must also catch (h, -h, l) rows
+    cart = refl.hkl.astype(float) @ O.reciprocal_basis(mg_lattice())
+    assert np.all(np.linalg.norm(cart, axis=1) < 1.5)
+
+
+# ------------------------------------------------- wavelength and Eq. 6 ----
+
+def test_wavelength_textbook_value():
+    """Textbook relativistic wavelength lambda = 12.2643 / sqrt(V (1 +
+    0.97845e-6 V)) Angstrom; 300 kV gives 0.01969 Angstrom."""
+    V = 300e3
+    textbook = 12.2643 / math.sqrt(V * (1 + 0.97845e-6 * V))
+    assert abs(O.electron_wavelength(300.0) - textbook) < 2e-6
+    assert abs(O.electron_wavelength(300.0) - 0.01969) < 5e-6
+
+
+def test_excitation_error_geometry():
+    """s_g = 0 on the Ewald sphere |k + g| = |k|; for a zero-order-Laue-zone
+    g (g . k = 0) s_g = -|g|^2 / (2 |k + g|) ~ -lambda |g|^2 / 2."""
+    k = O.beam_vector(LAM)
+    K = np.linalg.norm(k)
+    rng = np.random.default_rng(3)
+    for _ in range(10):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        g = -k + K * d                      # on the sphere centred at -k
+        assert abs(O.excitation_error(g, k)) < 1e-9
+    g = np.array([1.2, -0.3, 0.0])
+    s = O.excitation_error(g, k)
+    assert abs(s - (-(g @ g) / (2 * math.sqrt(K * K + g @ g)))) < 1e-15
+    assert abs(s + LAM * (g @ g) / 2) < 1e-5
+
+
+# -------------------------------------------------------------- Eq. 10 ----
+
+def test_za_frame_maps_z_to_zone_axis():
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        w = rng.normal(size=3)
+        w /= np.linalg.norm(w)
+        R = O.za_frame(w)
+        np.testing.assert_allclose(R @ np.array([0, 0, 1.0]), w, atol=1e-14)
+        np.testing.assert_allclose(R.T @ R, np.eye(3), atol=1e-14)
+        assert abs(np.linalg.det(R) - 1) < 1e-14
+    phi1, theta2 = O.za_angles([0, 0, 1.0])
+    assert theta2 == 0.0
+    np.testing.assert_allclose(O.za_frame([0, 0, 1.0]), np.eye(3), atol=1e-15)
+
+
+# --------------------------------------------------------- zone-axis grid --
+
+@pytest.mark.parametrize("step,count", [(3.0, 105), (2.0, 231), (1.0, 903), (0.5, 3486)])
+def test_cubic_grid_counts_and_triangle(step, count):
+    v0, v1, v2, om = O.cubic_triangle()
+    za = O.zone_axis_grid(v0, v1, v2, step, om)
+    assert len(za) == count
+    np.testing.assert_allclose(np.linalg.norm(za, axis=1), 1, atol=1e-14)
+    # standard triangle of m-3m: 0 <= x <= y <= z
+    assert np.all(za[:, 0] >= -1e-12)
+    assert np.all(za[:, 0] <= za[:, 1] + 1e-12)
+    assert np.all(za[:, 1] <= za[:, 2] + 1e-12)
+    for v in (v0, v1, v2):
+        assert np.min(np.linalg.norm(za - v, axis=1)) < 1e-12
+
+
+def test_hexagonal_grid_count():
+    v0, v1, v2, om = O.hexagonal_triangle()
+    za = O.zone_axis_grid(v0, v1, v2, 1.0, om)
+    assert len(za) == 1770
+    az = np.degrees(np.arctan2(za[:, 1], za[:, 0]))
+    ok = np.hypot(za[:, 0], za[:, 1]) < 1e-12
+    assert np.all(ok | ((az > -1e-9) & (az < 30 + 1e-9)))
+    assert np.all(za[:, 2] >= -1e-12)
+
+
+# -------------------------------------------------------------------- plan --
+
+def test_plan_normalised(c1_plan):
+    """A = 1/||P0||_2 makes every non-empty slice unit-norm."""
+    nrm = np.sqrt(np.sum(c1_plan.P ** 2, axis=(1, 2)))
+    np.testing.assert_allclose(nrm, 1.0, rtol=1e-12)
+
+
+def test_plan_fft_is_along_phi3(c1_plan):
+    """The plan spectrum's DC term is the sum over phi3 and its N/2 term the
+    alternating sum (definition of the DFT along phi3)."""
+    P = c1_plan.P
+    N = P.shape[2]
+    np.testing.assert_allclose(c1_plan.P_hat[..., 0].real, P.sum(axis=2), atol=1e-12)
+    alt = (P * ((-1.0) ** np.arange(N))).sum(axis=2)
+    np.testing.assert_allclose(c1_plan.P_hat[..., N // 2].real, alt, atol=1e-12)
+
+
+def test_plan_001_first_row_four_200_spots(c1_plan):
+    """Fig. 1f: at [001] the first populated row holds the four {200} spots
+    (the {111} points lie far off the Ewald sphere), 4-fold symmetric."""
+    gold = _golden("fig1_plan_001_first_row.json")
+    prm = c1_plan.params
+    z0 = int(np.argmin(np.linalg.norm(c1_plan.za - np.array(gold["zone_axis"]), axis=1)))
+    assert np.allclose(c1_plan.za[z0], gold["zone_axis"])
+    P = c1_plan.P[z0]
+    N = prm.n_phi
+    q_s = prm.shells()
+    q200 = 2.0 / A_AU
+    populated = np.nonzero(P.max(axis=1) > 0)[0]
+    assert q_s[populated[0]] > q200 - prm.delta - 1e-12
+    s0 = int(np.argmin(np.abs(q_s - q200)))
+    row = P[s0]
+    peaks = [j for j in range(N) if row[j] > row[(j - 1) % N] and row[j] >= row[(j + 1) % N]]
+    assert len(peaks) == gold["n_spots"]
+    expect = sorted(int(round(math.degrees(math.atan2(h[1], h[0])) % 360 / 360 * N)) % N
+                    for h in gold["first_row_hkl"])
+    assert sorted(peaks) == expect
+    np.testing.assert_allclose(P, np.roll(P, N // 4, axis=1), atol=1e-12)
+
+
+# ------------------------------------------------------------ polar image --
+
+def test_polar_image_single_peak_values():
+    """One peak on a bin angle: X(s, j0) = q_m^gamma I^(omega/2)
+    (1 - |q_m - q_s| / delta) for shells within delta, 0 elsewhere, and the
+    angular support at shell s is |dphi| q_s < delta."""
+    prm = O.PlanParams(n_shells=40, dq=0.025, n_phi=72, delta=0.08,
+                       gamma_pow=1.0, omega=1.0)
+    q_s = prm.shells()
+    j0 = 9
+    ang = 2 * math.pi * j0 / prm.n_phi
+    qm, I = 0.53, 4.0
+    X = O.polar_image([qm * math.cos(ang)], [qm * math.sin(ang)], [I], prm)
+    expect = qm * math.sqrt(I) * np.maximum(1 - np.abs(qm - q_s) / prm.delta, 0)
+    np.testing.assert_allclose(X[:, j0], expect, rtol=1e-12, atol=1e-12)
+    dphi = np.abs(O.wrap_angle(prm.phis() - ang))
+    for s in range(prm.n_shells):
+        outside = (dphi * q_s[s] >= prm.delta) | (abs(qm - q_s[s]) >= prm.delta)
+        assert np.all(X[s, outside] == 0)
+    # omega = 0: intensities are ignored; gamma = 0: radius is ignored
+    prm0 = O.PlanParams(n_shells=40, dq=0.025, n_phi=72, delta=0.08,
+                        gamma_pow=0.0, omega=0.0)
+    X0 = O.polar_image([qm * math.cos(ang)], [qm * math.sin(ang)], [I], prm0)
+    np.testing.assert_allclose(X0[:, j0], np.maximum(1 - np.abs(qm - q_s) / 0.08, 0),
+                               rtol=1e-12, atol=1e-12)
+
+
+def test_polar_image_wraps_and_ignores_order():
+    prm = O.PlanParams(n_shells=30, dq=0.05, n_phi=36, delta=0.1)
+    rng = np.random.default_rng(11)
+    q = rng.uniform(0.1, 1.4, 12)
+    g = rng.uniform(-math.pi, math.pi, 12)
+    I = rng.uniform(0.5, 2, 12)
+    qx, qy = q * np.cos(g), q * np.sin(g)
+    X = O.polar_image(qx, qy, I, prm)
+    p = rng.permutation(12)
+    np.testing.assert_allclose(O.polar_image(qx[p], qy[p], I[p], prm), X, atol=1e-12)
+    # rotating the peaks by whole bins rolls the image along phi3
+    r = 2 * math.pi * 5 / prm.n_phi
+    Xr = O.polar_image(q * np.cos(g + r), q * np.sin(g + r), I, prm)
+    np.testing.assert_allclose(Xr, np.roll(X, 5, axis=1), atol=1e-9)
+
+
+# ------------------------------------------------------------ correlation --
+
+@pytest.mark.parametrize("N", [12, 10, 9])
+def test_fft_correlation_equals_direct_circular_sum(N):
+    rng = np.random.default_rng(N)
+    Z, S = 3, 4
+    P = rng.normal(size=(Z, S, N))
+    X = rng.normal(size=(S, N))
+    C, Cm = O.correlogram(np.fft.rfft(P, axis=2), X)
+    # brute force written as explicit loops
+    Cb = np.zeros((Z, N))
+    Cmb = np.zeros((Z, N))
+    for z in range(Z):
+        for k in range(N):
+            for s in range(S):
+                for j in range(N):
+                    Cb[z, k] += P[z, s, j] * X[s, (j + k) % N]
+                    Cmb[z, k] += P[z, s, j] * X[s, (-j - k) % N]
+    np.testing.assert_allclose(C, Cb, atol=1e-12)
+    np.testing.assert_allclose(Cm, Cmb, atol=1e-12)
+    Cd, Cmd = O.direct_correlation(P, X)
+    np.testing.assert_allclose(Cd, Cb, atol=1e-12)
+    np.testing.assert_allclose(Cmd, Cmb, atol=1e-12)
+
+
+def test_mirror_correlation_is_correlation_of_mirrored_pattern(c1_plan):
+    """Conjugating FFT{X} mirrors the pattern: C_mirror of a pattern equals
+    C of its y -> -y mirror image."""
+    prm = c1_plan.params
+    rng = np.random.default_rng(2)
+    q = rng.uniform(0.3, 1.45, 15)
+    g = rng.uniform(-math.pi, math.pi, 15)
+    I = rng.uniform(1, 5, 15)
+    X = O.polar_image(q * np.cos(g), q * np.sin(g), I, prm)
+    Xm = O.polar_image(q * np.cos(g), -q * np.sin(g), I, prm)
+    C, Cm = O.correlogram(c1_plan.P_hat[:20], X)
+    C2, Cm2 = O.correlogram(c1_plan.P_hat[:20], Xm)
+    np.testing.assert_allclose(Cm, C2, atol=1e-9 * np.abs(C).max())
+    np.testing.assert_allclose(C, Cm2, atol=1e-9 * np.abs(C).max())
+
+
+def test_self_indexing_is_exact(c1_plan):
+    """X := P_z gives C(z, 0) = ||P_z||^2 = 1, the global maximum by
+    Cauchy-Schwarz since every ||P_z'|| = 1 (kinematical self-indexing)."""
+    rng = np.random.default_rng(7)
+    for z in rng.choice(len(c1_plan.za), 6, replace=False):
+        X = c1_plan.P[z]
+        C, Cm = O.correlogram(c1_plan.P_hat, X)
+        assert abs(C[z, 0] - 1.0) < 1e-12
+        assert C.max() <= 1.0 + 1e-12 and Cm.max() <= 1.0 + 1e-12
+        mt = O.best_match(C, Cm, X)
+        assert mt.score == pytest.approx(1.0, abs=1e-12)
+        assert abs(mt.score_cos - 1.0) < 1e-12
+        # a different winner is allowed only as an exact tie (symmetric slice)
+        assert (mt.za, mt.k, mt.mirror) == (z, 0, 0) or abs(mt.score - 1) < 1e-12
+
+
+def test_noiseless_grid_patterns_recovered(c1_plan):
+    """A noiseless pattern generated exactly at a grid zone axis and grid
+    phi3 (direct or mirror) scores its maximum there, up to exact ties with
+    zero symmetry-reduced misorientation.  The image weights (sqrt of the
+    shaped intensity) and the plan weights (|F|, excitation error inside the
+    tent) differ, so a grid neighbour may win by a small margin: that is
+    allowed only within 1.5 grid steps and 1 % of the score, and the exact
+    recoveries must be the large majority."""
+    refl = au_reflections()
+    ops = O.proper_point_group("cubic")
+    rng = np.random.default_rng(1)
+    N = c1_plan.params.n_phi
+    za = c1_plan.za
+    exact = 0
+    for z in rng.choice(len(za), 12, replace=False):
+        k = int(rng.integers(N))
+        mir = int(rng.integers(2))
+        m = O.orientation_matrix(za[z], -2 * math.pi * k / N, mir)
+        qx, qy, I = O.kinematical_pattern(refl, m, LAM, AU["sigma"], 1e-3)
+        mt = O.match_pattern(c1_plan, qx, qy, I)
+        at_truth = (mt.Cm if mir else mt.C)[z, k]
+        me = O.orientation_matrix(za[mt.za], -2 * math.pi * mt.k / N, mt.mirror)
+        mis = O.misorientation_deg(me, m, ops)
+        if at_truth >= mt.score * (1 - 1e-12):
+            exact += 1
+            assert mis < 1e-4
+        else:
+            assert at_truth >= 0.99 * mt.score
+            assert mis < 1.5 * 2.0
+    assert exact >= 10
+
+
+def test_symmetry_equivalent_orientations_score_equally(c1_plan):
+    refl = au_reflections()
+    ops = O.proper_point_group("cubic")
+    rng = np.random.default_rng(4)
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    m = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
+                  [2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)],
+                  [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)]])
+    base = O.match_pattern(c1_plan, *O.kinematical_pattern(refl, m, LAM, 0.02, 1e-3))
+    for S in ops[:8]:
+        other = O.match_pattern(c1_plan, *O.kinematical_pattern(refl, S @ m, LAM, 0.02, 1e-3))
+        assert other.score == pytest.approx(base.score, rel=1e-10)
+
+
+def test_fig1_zone_axes_inplane_symmetry_and_recovery():
+    """Fig. 1g/h: patterns along [001], [011], [111], [113], [135] are
+    indexed to their own zone axis, with 4-, 2-, 6-fold and single in-plane
+    correlation maxima."""
+    gold = _golden("fig1_inplane_symmetry.json")["folds"]
+    names = ["001", "011", "111", "113", "135"]
+    za = np.array([[int(c) for c in n] for n in names], dtype=float)
+    za /= np.linalg.norm(za, axis=1)[:, None]
+    prm = O.PlanParams(n_shells=75, dq=0.02, n_phi=360, delta=0.08, lam=LAM)
+    refl = au_reflections()
+    plan = O.orientation_plan(refl, za, prm)
+    N = prm.n_phi
+    for i, name in enumerate(names):
+        m = O.orientation_matrix(za[i], 0.3, 0)
+        qx, qy, I = O.kinematical_pattern(refl, m, LAM, 0.02, 1e-3)
+        mt = O.match_pattern(plan, qx, qy, I)
+        assert mt.za == i
+        C = mt.C[i]
+        fold = gold[name]
+        if fold > 1:
+            np.testing.assert_allclose(C, np.roll(C, N // fold), atol=1e-9 * C.max())
+        top = np.sort(C)[::-1]
+        n_max = int(np.sum(C >= C.max() * (1 - 1e-9)))
+        assert n_max == fold, (name, n_max)
+
+
+# ------------------------------------------------------------- refinement --
+
+def test_parabolic_offset_exact_on_parabola():
+    for x0 in (-0.5, -0.31, 0.0, 0.2, 0.49):
+        c = [5.0 - 2.0 * (t - x0) ** 2 for t in (-1, 0, 1)]
+        assert O.parabolic_offset(*c) == pytest.approx(x0, abs=1e-14)
+    assert O.parabolic_offset(1.0, 1.0, 1.0) == 0.0          # flat: no shift
+    assert O.parabolic_offset(0.0, 1.0, 1.5) == 0.5          # clamped
+
+
+def test_rotation_between_and_refined_axis():
+    rng = np.random.default_rng(9)
+    for _ in range(10):
+        u, v = rng.normal(size=3), rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        v /= np.linalg.norm(v)
+        R = O.rotation_between(u, v)
+        np.testing.assert_allclose(R @ u, v, atol=1e-12)
+        np.testing.assert_allclose(R.T @ R, np.eye(3), atol=1e-12)
+        axis = np.cross(u, v)
+        np.testing.assert_allclose(R @ axis, axis, atol=1e-12)
+
+
+def test_refinement_reduces_offgrid_error(c1_plan):
+    """A pattern between grid points is refined closer to the truth than
+    the grid result, on average."""
+    refl = au_reflections()
+    ops = O.proper_point_group("cubic")
+    rng = np.random.default_rng(12)
+    za = c1_plan.za
+    nb = O.za_neighbours(za, 2.0)
+    grid_err, ref_err = [], []
+    N = c1_plan.params.n_phi
+    for z in rng.choice(np.arange(30, len(za)), 10, replace=False):
+        w = za[z] + 0.012 * rng.normal(size=3)
+        w /= np.linalg.norm(w)
+        phi3 = -2 * math.pi * (rng.integers(N) + rng.uniform(-0.5, 0.5)) / N
+        m = O.orientation_matrix(w, phi3, 0)
+        mt = O.match_pattern(c1_plan, *O.kinematical_pattern(refl, m, LAM, 0.02, 1e-3))
+        mg = O.orientation_matrix(za[mt.za], -2 * math.pi * mt.k / N, mt.mirror)
+        rf = O.refine(mt, za, 2.0, nb)
+        grid_err.append(O.misorientation_deg(mg, m, ops, True))
+        ref_err.append(O.misorientation_deg(rf.m, m, ops, True))
+    assert np.mean(ref_err) < np.mean(grid_err)
