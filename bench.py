@@ -1,0 +1,419 @@
+#!/usr/bin/env python
+"""Benchmark of the sparse correlation match on one or more GB300s.
+
+Workload: the 256 x 256 fcc-Au scan (65,536 patterns with 10-60 Bragg peaks
+each in CSR, 200 Voronoi grains at random orientations) matched against the
+1-degree plan (903 zone axes, 150 shells of 0.01 1/A, 360 phi3 bins).  One
+step is the whole path: plan build (reflections, plan raster + transform,
+normalisation) and the match of every pattern (sparse polar raster +
+transform, shell contraction, inverse transform + argmax, refinement).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16]
+  python bench.py --impl reference ...   # the FP64 CPU oracle as the reference arm
+
+Under torchrun (N > 1) every rank matches its own scan (weak scaling); there is
+no collective on the data path; rank 0 prints one JSON line.
+"""
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "patterns indexed/s on 1 GB300, % of roofline, mean misorientation (deg)"
+W = dict(name="au_scan_256x256_1deg", step=1.0, S=150, dq=0.01, N=360, seed=1002, H=256,
+         Wd=256, grains=200, delta=0.08, lam=0.01969, q_max=1.5)
+WORKLOAD_TEXT = ("fcc Au 256x256 scan (65,536 patterns, 10-60 peaks each, CSR, 200 Voronoi "
+                 "grains) vs 1-degree plan (903 zone axes, 150 shells x 0.01 1/A, 360 phi3 bins)")
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=16)
+    return ap.parse_args()
+
+
+def peaks_file():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the
+    timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.rows = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "samples": len(self.rows),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- accuracy
+
+def cubic_ops():
+    import itertools
+    ops = []
+    for perm in itertools.permutations(range(3)):
+        for signs in itertools.product((1.0, -1.0), repeat=3):
+            M = np.zeros((3, 3))
+            for r in range(3):
+                M[r, perm[r]] = signs[r]
+            if np.linalg.det(M) > 0:
+                ops.append(M)
+    return np.array(ops)
+
+
+def misorientation(m_est, m_true):
+    """Mean symmetry-reduced misorientation (deg), also reduced over the
+    in-plane Friedel twin m Rz(pi), and the zone-axis tilt error."""
+    ops = cubic_ops()
+    me = m_est.astype(np.float64)
+    SM = np.einsum("sij,bjk->sbik", ops, me)
+    tr = np.einsum("bji,sbji->sb", m_true, SM)
+    ang = np.degrees(np.arccos(np.clip((tr.max(axis=0) - 1) / 2, -1, 1)))
+    Rz = np.diag([-1.0, -1.0, 1.0])
+    SM2 = np.einsum("sbik,kl->sbil", SM, Rz)
+    tr2 = np.einsum("bji,sbji->sb", m_true, SM2)
+    ang2 = np.degrees(np.arccos(np.clip((np.maximum(tr, tr2).max(axis=0) - 1) / 2, -1, 1)))
+    we = np.einsum("sij,bj->sbi", ops, me[:, :, 2])
+    c = np.abs(np.einsum("sbi,bi->sb", we, m_true[:, :, 2])).max(axis=0)
+    tilt = np.degrees(np.arccos(np.clip(c, -1, 1)))
+    return float(ang.mean()), float(ang2.mean()), float(tilt.mean())
+
+
+# ------------------------------------------------------------- oracle leg
+
+def oracle_plan(za_subset=None):
+    from oracle import acom_oracle as O
+    refl = O.reflections(np.eye(3) * 4.08, [[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0]],
+                         [79.0] * 4, [0.25] * 4, W["q_max"])
+    v0, v1, v2, om = O.cubic_triangle()
+    za = O.zone_axis_grid(v0, v1, v2, W["step"], om)
+    if za_subset is not None:
+        za = za[za_subset]
+    return O.orientation_plan(refl, za, O.PlanParams(W["S"], W["dq"], W["N"], W["delta"],
+                                                     lam=W["lam"]))
+
+
+def cpu_baseline(scan, gpu_res, n_sample):
+    """The oracle as it stands on this host: full plan build timed once, then
+    n_sample patterns matched; extrapolated to the whole scan."""
+    from oracle import acom_oracle as O
+    t0 = time.perf_counter()
+    plan = oracle_plan()
+    t_plan = time.perf_counter() - t0
+    rng = np.random.default_rng(0)
+    idx = rng.choice(scan.n_patterns, n_sample, replace=False)
+    agree = 0
+    t0 = time.perf_counter()
+    for b in idx:
+        mt = O.match_pattern(plan, *scan.pattern(b))
+        z, k, m = (int(gpu_res["za_idx"][b]), int(gpu_res["phi3_bin"][b]),
+                   int(gpu_res["mirror"][b]))
+        val = (mt.Cm if m else mt.C)[z, k]
+        agree += int((z, k, m) == (mt.za, mt.k, mt.mirror) or val >= mt.score * (1 - 1e-5))
+    t_match = (time.perf_counter() - t0) / n_sample
+    B = scan.n_patterns
+    value = B / (t_plan + B * t_match)
+    return {"value": value, "unit": "patterns/s", "cores": 1, "kind": "oracle",
+            "sample": (f"FP64 NumPy oracle, single thread: full 903-axis plan build timed "
+                       f"once ({t_plan:.1f} s) + {n_sample} sampled patterns matched "
+                       f"({t_match * 1e3:.0f} ms each), extrapolated to {B} patterns")}, \
+        f"{agree}/{n_sample}"
+
+
+def reference_arm(args):
+    """--impl reference: the oracle timed on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import synth
+    from oracle import acom_oracle as O
+    scan = synth.grain_scan(W["seed"])
+    full = oracle_plan()                    # set-up: the plan the sampled patterns match against
+    Z = len(full.za)
+    sub = np.arange(0, Z, 16)
+    rng = np.random.default_rng(1)
+    vals = []
+    tot = 0.0
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle_plan(sub)
+        t_plan = (time.perf_counter() - t0) * Z / len(sub)
+        bs = rng.choice(scan.n_patterns, 2, replace=False)
+        t0 = time.perf_counter()
+        for b in bs:
+            O.match_pattern(full, *scan.pattern(b))
+        t_p = (time.perf_counter() - t0) / len(bs)
+        if it >= args.warmup:
+            B = scan.n_patterns
+            vals.append(B / (t_plan + B * t_p))
+            tot += t_plan + B * t_p
+    v = float(np.mean(vals))
+    sample = (f"each step: plan build on {len(sub)} of {Z} zone axes (scaled by {Z / len(sub):.1f}) "
+              f"+ 2 sampled patterns; extrapolated to {scan.n_patterns} patterns")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "patterns/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_TEXT, "patterns": scan.n_patterns},
+            "cpu_baseline": {"value": v, "unit": "patterns/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "patterns/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# --------------------------------------------------------------- GPU arm
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_2111_00171_gb300 import acom
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    lib = acom.load_library()
+    prec = acom.ACOM_PREC_BF16 if args.precision == "bf16" else acom.ACOM_PREC_FP32
+
+    scan = synth.grain_scan(W["seed"] + rank)
+    B = scan.n_patterns
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    d_in = (dev(scan.row_ptr), dev(scan.qx), dev(scan.qy), dev(scan.I))
+    h_in = tuple(torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+                 for a in (scan.row_ptr, scan.qx, scan.qy, scan.I))
+    h2d = sum(t.numel() * t.element_size() for t in h_in)
+    v, om = acom.cubic_triangle()
+    cr = acom.au_crystal()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def make_plan():
+        return acom.Plan(cr, v, om, W["step"], W["S"], W["dq"], W["N"], delta=W["delta"],
+                         lam=W["lam"], q_max=W["q_max"], precision=prec)
+
+    out_keys = ("za_idx", "phi3_bin", "mirror", "score", "score_cos", "phi3", "orient")
+
+    def step(inputs, out):
+        p = make_plan()
+        p.match(*inputs, chunk=args.chunk, out=out)
+        p.close()
+        return out
+
+    probe = make_plan()
+    out = probe.alloc_result(B)
+    probe.close()
+    for _ in range(args.warmup):
+        step(d_in, out)
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident inputs
+    lib.acom_profile_reset()
+    lib.acom_profile_enable(1)
+    launches0 = lib.acom_kernel_launches()
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = []
+    w0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()                                      # L2 flush, outside the events
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(d_in, out)
+        e1.record(stream)
+        ev.append((e0, e1))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - w0
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop() if clocks else None
+    launches = lib.acom_kernel_launches() - launches0
+    lib.acom_profile_enable(0)
+    prof = read_profile(lib, acom)
+    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
+    t_max = torch.tensor([dev_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    dev_ms = float(t_max.item())
+
+    # ---- e2e: host buffers through the public API, copies inside the region
+    d_buf = tuple(torch.empty_like(t, device="cuda") for t in h_in)
+    h_out = {k: torch.empty(out[k].shape, dtype=out[k].dtype).pin_memory() for k in out_keys}
+    d2h = sum(t.numel() * t.element_size() for t in h_out.values())
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for d, h in zip(d_buf, h_in):
+            d.copy_(h, non_blocking=True)
+        step(d_buf, out)
+        for k in out_keys:
+            h_out[k].copy_(out[k], non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+    t_e = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t_e, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    e2e_ms = float(t_e.item())
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    res = {k: out[k].cpu().numpy() for k in out_keys}
+    mis, mis_twin, tilt = misorientation(res["orient"], scan.truth)
+    peaks, src = peaks_file()
+    K = args.steps
+    value = world * B * K / (dev_ms / 1e3)
+    roof = roofline(prof, peaks, src, B, K, args.precision)
+    line = {"metric": METRIC, "value": value, "unit": "patterns/s", "n_gpus": world,
+            "steps": K, "warmup": args.warmup, "ms_per_step": dev_ms / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "bf16", "data": "synthetic",
+            "config": {"workload": WORKLOAD_TEXT, "patterns_per_gpu": B,
+                       "peaks_nnz": int(scan.row_ptr[-1]), "zone_axes": 903, "shells": W["S"],
+                       "n_phi": W["N"], "precision": args.precision,
+                       "chunk": args.chunk or 1024,
+                       "l2": "flushed between steps (256 MiB write outside the timed events)",
+                       "step": "plan build + match of every pattern",
+                       "wall_ms_per_step": wall * 1e3 / K},
+            "roofline": roof,
+            "e2e": {"value": world * B * K / (e2e_ms / 1e3), "unit": "patterns/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches),
+            "clocks": ck,
+            "kernels_ms_per_step": {n: round(ms / K, 3) for n, (c, ms) in prof.items() if c},
+            "accuracy": {"mean_misorientation_deg": mis, "mean_misorientation_friedel_deg": mis_twin,
+                         "mean_za_tilt_deg": tilt}}
+    if not args.no_cpu_baseline and world == 1:
+        cb, agree = cpu_baseline(scan, res, args.cpu_sample)
+        line["cpu_baseline"] = cb
+        line["accuracy"]["oracle_argmax_agreement"] = agree
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def read_profile(lib, acom):
+    import ctypes as C
+
+    class Entry(C.Structure):
+        _fields_ = [("name", C.c_char_p), ("launches", C.c_int64), ("total_ms", C.c_double)]
+    lib.acom_profile_read.restype = C.c_int32
+    lib.acom_profile_read.argtypes = [C.POINTER(Entry), C.c_int32]
+    n = lib.acom_profile_read(None, 0)
+    arr = (Entry * n)()
+    lib.acom_profile_read(arr, n)
+    return {e.name.decode(): (e.launches, e.total_ms) for e in arr}
+
+
+def roofline(prof, peaks, src, B, K, precision):
+    """Dominant kernel's achieved rate from its algorithmic work per launch
+    over its event-timed average launch duration."""
+    Z, S, N = 903, W["S"], W["N"]
+    F = N // 2 + 1
+    name, (cnt, ms) = max(prof.items(), key=lambda kv: kv[1][1])
+    avg_s = ms / cnt / 1e3 if cnt else float("nan")
+    per_launch_patterns = B * K / cnt if cnt else 0
+    if name.startswith("contract"):
+        flops = 8.0 * Z * S * F * per_launch_patterns
+    elif name.startswith("idft"):
+        flops = 2.0 * Z * 2.5 * N * math.log2(N) * per_launch_patterns
+    else:
+        flops = float("nan")
+    if precision == "fp32":
+        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        bound = "alu"
+        note = f"FP32 FMA peak 152 SMs x 128 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz"
+    else:
+        peak = peaks["bf16_tflops_sustained"]
+        bound = "tensor"
+        note = f"bf16 sustained, {src}"
+    ach = flops / avg_s / 1e12
+    return {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak, "traffic": None, "avg_launch_ms": avg_s * 1e3,
+            "launches": cnt, "peak_source": note}
+
+
+if __name__ == "__main__":
+    main()

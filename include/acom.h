@@ -1,0 +1,250 @@
+/*
+ * acom.h - C ABI of the GB300 sparse correlation match (automated crystal
+ * orientation mapping by sparse correlation matching, arXiv 2111.00171).
+ *
+ * The library builds an orientation plan for a crystal and matches Bragg-peak
+ * lists against it on one CUDA device (sm_103a).  Every entry point takes
+ * plain pointers and sizes; no C++ or PyTorch type crosses this boundary and
+ * no exception escapes it.  All device work is ordered on the caller's CUDA
+ * stream (``cuda_stream`` is a cudaStream_t; NULL means the legacy default
+ * stream).
+ *
+ * Error behaviour: every entry point returns an acom_status.  Arguments are
+ * validated before any launch; on error nothing is launched and outputs are
+ * untouched, except where noted for device-side validation.  A human-readable
+ * message for the most recent error of the calling thread is returned by
+ * acom_last_error().
+ */
+#ifndef ACOM_H
+#define ACOM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ACOM_OK = 0,
+    ACOM_ERR_INVALID_ARG = 1,  /* bad pointer, size or option; nothing launched    */
+    ACOM_ERR_OOM = 2,          /* device allocation failed                          */
+    ACOM_ERR_CUDA = 3,         /* a CUDA runtime call or launch failed              */
+    ACOM_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up                */
+    ACOM_ERR_UNSUPPORTED = 5,  /* size or mode outside the compiled limits          */
+    ACOM_ERR_BAD_INPUT = 6     /* device-side check of the peak data failed         */
+} acom_status;
+
+/* Arithmetic used by the shell contraction and the inverse transform. */
+typedef enum {
+    ACOM_PREC_FP32 = 0,   /* FP32 CUDA-core path (reference GPU path)               */
+    ACOM_PREC_BF16 = 1    /* BF16 operands on tcgen05 tensor cores, FP32 accumulate,
+                             top candidates re-scored in FP32                       */
+} acom_precision;
+
+typedef struct acom_plan_s* acom_plan;
+
+/*
+ * Crystal (section "Structure Factor Calculations"): lattice vectors a, b, c
+ * as the rows of ``lattice`` (Angstrom, Cartesian), and the atomic basis:
+ * fractional positions p_n in [0, 1) and the form factor of each atom,
+ * f_n(q) = ff_A[n] exp(-ff_B[n] q^2) with q = |g| in 1/Angstrom (no 2 pi).
+ * All pointers are HOST memory, read during the call only.
+ */
+typedef struct {
+    double lattice[3][3];
+    int32_t n_atoms;          /* 1 .. 64                                         */
+    const double* frac_pos;   /* [n_atoms][3]                                   */
+    const double* ff_A;       /* [n_atoms]                                      */
+    const double* ff_B;       /* [n_atoms]                                      */
+} acom_crystal;
+
+/*
+ * Zone-axis grid (section "Generation of an Orientation Plan"): three
+ * boundary directions of the symmetry-reduced region (crystal Cartesian, any
+ * length, rows of ``v``) sampled by spherical linear interpolation.  With
+ * n = floor(sqrt(2 solid_angle) / step) the points are, for i = 0..n and
+ * j = 0..i, slerp(slerp(v0,v1,i/n), slerp(v0,v2,i/n), j/i), in (i, j) order.
+ */
+typedef struct {
+    double v[3][3];
+    double step_deg;          /* > 0                                            */
+    double solid_angle;       /* steradians of the region (4 pi / 48 for m-3m)  */
+} acom_za_grid;
+
+/* Radial shells q_s = (s + 1) * dq, s = 0 .. n_shells - 1 (1/Angstrom). */
+typedef struct {
+    int32_t n_shells;         /* 1 .. 512                                       */
+    double dq;                /* > 0                                            */
+} acom_shells;
+
+/*
+ * Plan options.  ``delta`` is the correlation kernel size, ``gamma_pow`` and
+ * ``omega`` the radial and amplitude power laws of the plan and image
+ * expressions, ``lambda`` the electron wavelength (Angstrom), ``q_max`` the
+ * reflection cut-off 0 < |g| < q_max, ``precision`` an acom_precision.
+ */
+typedef struct {
+    double delta;
+    double gamma_pow;
+    double omega;
+    double lambda;
+    double q_max;
+    int32_t precision;
+} acom_plan_opts;
+
+/*
+ * acom_plan_create - build the orientation plan (section "Generation of an
+ * Orientation Plan"): structure factors F_hkl of every reflection with
+ * 0 < |g| < q_max (Eqs. 2-3, FP64 phase sums on the device), the zone-axis
+ * grid and the rotation of each axis onto +z (the first two factors of
+ * Eq. 10), excitation errors (Eq. 6, beam along -z), the plan P0 over
+ * (zone axis, phi3, q_s), its normalisation A = 1/||P0||_2, and the Fourier
+ * transform of P = A P0 along phi3 (n_phi bins phi_j = 2 pi j / n_phi).
+ *
+ *   crystal, grid, shells, opts : host structs, read during the call.
+ *   n_phi      : in-plane bins, even, 8 .. 720.
+ *   sigma_exc  : excitation-error tolerance sigma of the Gaussian shape factor
+ *                (Eq. 8); the plan itself does not use it (the tent of size
+ *                delta carries the excitation error), it is kept on the plan
+ *                for forward models.
+ *   cuda_stream: stream on which the build runs; the call returns after the
+ *                plan is complete (it synchronises that stream once).
+ *   out        : receives the plan handle.  The plan owns its device memory
+ *                until acom_plan_destroy; it is bound to the device current at
+ *                creation.
+ */
+acom_status acom_plan_create(const acom_crystal* crystal, const acom_za_grid* grid,
+                             const acom_shells* shells, int32_t n_phi, double sigma_exc,
+                             const acom_plan_opts* opts, void* cuda_stream,
+                             acom_plan* out);
+
+/* Release a plan and all its device memory (after work on it has finished). */
+acom_status acom_plan_destroy(acom_plan plan);
+
+typedef struct {
+    int32_t n_za;             /* Z zone axes                                    */
+    int32_t n_shells;         /* S                                              */
+    int32_t n_phi;            /* N                                              */
+    int32_t n_freq;           /* F = N/2 + 1                                    */
+    int32_t n_reflections;    /* reflections kept (0 < |g| < q_max, F != 0)     */
+    int32_t precision;
+    int64_t device_bytes;     /* device memory owned by the plan                */
+} acom_plan_info;
+
+acom_status acom_plan_get_info(acom_plan plan, acom_plan_info* info);
+
+/* Copy the zone axes (unit vectors, crystal Cartesian) to HOST memory
+ * ``dst`` [Z][3].  Synchronous. */
+acom_status acom_plan_get_zone_axes(acom_plan plan, double* dst);
+
+/* Copy the plan spectrum FFT_phi3{P} to DEVICE memory ``dst`` laid out
+ * [Z][S][F][2] (real, imaginary), FP32.  Stream-ordered. */
+acom_status acom_plan_get_spectra(acom_plan plan, float* dst, void* cuda_stream);
+
+/*
+ * Bragg peaks of n_patterns diffraction patterns in CSR form (section
+ * "Correlation Pattern Matching"): the peaks of pattern b are the entries
+ * row_ptr[b] .. row_ptr[b+1]-1 of qx, qy (1/Angstrom, detector frame) and I
+ * (intensity).  All pointers are DEVICE memory owned by the caller.
+ * row_ptr[0] must be 0 and row_ptr non-decreasing; each pattern holds at most
+ * 1024 peaks; values must be finite.  These properties are checked on the
+ * device: a violation makes acom_match return ACOM_ERR_BAD_INPUT (outputs
+ * are then undefined).
+ */
+typedef struct {
+    int64_t n_patterns;
+    const int64_t* row_ptr;   /* [n_patterns + 1]                               */
+    const float* qx;          /* [row_ptr[n_patterns]]                          */
+    const float* qy;
+    const float* I;
+} acom_peaks_csr;
+
+/*
+ * Per-pattern results, DEVICE memory owned by the caller, [n_patterns] unless
+ * stated.  Pointers marked optional may be NULL.
+ *   za_idx    best zone axis (maximum over zone axes of max(C, C_mirror))
+ *   phi3_bin  its phi3 bin k (C is maximal at phi_k = 2 pi k / N)
+ *   mirror    1 when C_mirror gave the maximum
+ *   score     the maximum correlation value (raw C)
+ *   score_cos optional: score / ||X||_2, in [0, 1] since ||P_z||_2 = 1
+ *   phi3      optional: refined in-plane angle of the orientation (radians)
+ *   orient    optional: [n_patterns][9] refined orientation matrix m, row
+ *             major, mapping sample to crystal coordinates (Eq. 9)
+ *   za_scores optional: [n_patterns][Z] max over phi3 and mirror per axis
+ * Ties: the lowest zone-axis index wins, then C before C_mirror, then the
+ * lowest phi3 bin.
+ */
+typedef struct {
+    int32_t* za_idx;
+    int32_t* phi3_bin;
+    uint8_t* mirror;
+    float* score;
+    float* score_cos;
+    float* phi3;
+    float* orient;
+    float* za_scores;
+} acom_result;
+
+typedef struct {
+    int32_t refine;           /* 1: sub-grid refinement of phi3 / orient        */
+    int32_t chunk;            /* patterns per internal chunk, 0 = default       */
+} acom_match_opts;
+
+/*
+ * acom_match - sparse correlation match (section "Correlation Pattern
+ * Matching"): for every pattern, the sparse polar image X(phi3, q_s) of its
+ * peaks, its Fourier transform along phi3, the contraction over shells with
+ * the plan's conjugate spectra for every zone axis, the inverse transform to
+ * C and C_mirror over phi3, the maximum over (zone axis, phi3, mirror), and
+ * the refinement of the winner into an orientation matrix.
+ *
+ * Work is queued on ``cuda_stream``; the call synchronises that stream once at
+ * the end to read the device error word.  The first call on a plan allocates
+ * its scratch workspace (sized for ``chunk`` patterns).  ``opts`` may be NULL.
+ */
+acom_status acom_match(acom_plan plan, const acom_peaks_csr* peaks,
+                       const acom_match_opts* opts, acom_result* out,
+                       void* cuda_stream);
+
+/*
+ * acom_polar_spectra - the first half of acom_match alone: the sparse polar
+ * image of every pattern and its Fourier transform along phi3, written to
+ * DEVICE memory ``dst`` laid out [n_patterns][S][F][2] FP32, and optionally
+ * ||X||_2 per pattern to ``xnorm`` [n_patterns] (may be NULL).  Stream-ordered;
+ * synchronises once to read the error word.
+ */
+acom_status acom_polar_spectra(acom_plan plan, const acom_peaks_csr* peaks,
+                               float* dst, float* xnorm, void* cuda_stream);
+
+/*
+ * Tracing: per-kernel-class device time.  When enabled, each kernel the
+ * library launches is bracketed by CUDA events on its stream; the pairs are
+ * resolved at the library's next stream synchronisation (end of acom_match,
+ * acom_polar_spectra, acom_plan_create).  acom_profile_read fills up to
+ * ``max`` entries (name, launches timed, total milliseconds) and returns the
+ * number written (with out == NULL: the number of classes).
+ * acom_kernel_launches counts every kernel the library has launched in this
+ * process (timed or not).  Process-global state; not thread-safe.
+ */
+typedef struct {
+    const char* name;
+    int64_t launches;
+    double total_ms;
+} acom_profile_entry;
+
+void acom_profile_enable(int32_t on);
+void acom_profile_reset(void);
+int32_t acom_profile_read(acom_profile_entry* out, int32_t max);
+int64_t acom_kernel_launches(void);
+
+const char* acom_status_str(acom_status status);
+const char* acom_last_error(void);
+
+/* Library version, for the Python binding's compatibility check. */
+int32_t acom_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ACOM_H */

@@ -1,0 +1,289 @@
+"""Thin ctypes binding of libacom (include/acom.h).
+
+Argument marshalling only: every step of the match runs in the library's CUDA
+kernels.  PyTorch tensors supply device memory and the current CUDA stream.
+The binding refuses to run when the compiled library is missing.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+ACOM_OK = 0
+ACOM_PREC_FP32 = 0
+ACOM_PREC_BF16 = 1
+STATUS = {0: "ACOM_OK", 1: "ACOM_ERR_INVALID_ARG", 2: "ACOM_ERR_OOM", 3: "ACOM_ERR_CUDA",
+          4: "ACOM_ERR_TIMEOUT", 5: "ACOM_ERR_UNSUPPORTED", 6: "ACOM_ERR_BAD_INPUT"}
+
+EXPORTED = ("acom_plan_create", "acom_plan_destroy", "acom_plan_get_info",
+            "acom_plan_get_zone_axes", "acom_plan_get_spectra", "acom_match",
+            "acom_polar_spectra", "acom_status_str", "acom_last_error", "acom_version")
+
+
+class AcomError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Crystal(C.Structure):
+    _fields_ = [("lattice", (C.c_double * 3) * 3), ("n_atoms", C.c_int32),
+                ("frac_pos", C.POINTER(C.c_double)), ("ff_A", C.POINTER(C.c_double)),
+                ("ff_B", C.POINTER(C.c_double))]
+
+
+class ZaGrid(C.Structure):
+    _fields_ = [("v", (C.c_double * 3) * 3), ("step_deg", C.c_double),
+                ("solid_angle", C.c_double)]
+
+
+class Shells(C.Structure):
+    _fields_ = [("n_shells", C.c_int32), ("dq", C.c_double)]
+
+
+class PlanOpts(C.Structure):
+    _fields_ = [("delta", C.c_double), ("gamma_pow", C.c_double), ("omega", C.c_double),
+                ("lambda_", C.c_double), ("q_max", C.c_double), ("precision", C.c_int32)]
+
+
+class PlanInfo(C.Structure):
+    _fields_ = [("n_za", C.c_int32), ("n_shells", C.c_int32), ("n_phi", C.c_int32),
+                ("n_freq", C.c_int32), ("n_reflections", C.c_int32), ("precision", C.c_int32),
+                ("device_bytes", C.c_int64)]
+
+
+class PeaksCSR(C.Structure):
+    _fields_ = [("n_patterns", C.c_int64), ("row_ptr", C.c_void_p), ("qx", C.c_void_p),
+                ("qy", C.c_void_p), ("I", C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [("za_idx", C.c_void_p), ("phi3_bin", C.c_void_p), ("mirror", C.c_void_p),
+                ("score", C.c_void_p), ("score_cos", C.c_void_p), ("phi3", C.c_void_p),
+                ("orient", C.c_void_p), ("za_scores", C.c_void_p)]
+
+
+class MatchOpts(C.Structure):
+    _fields_ = [("refine", C.c_int32), ("chunk", C.c_int32)]
+
+
+_LIB = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load_library():
+    """Load the in-tree libacom.so; raise if it has not been built."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libacom is not built ({path} missing): run "
+                           "python -c 'import __graft_entry__ as g; g.build()'")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    lib.acom_plan_create.argtypes = [C.POINTER(Crystal), C.POINTER(ZaGrid), C.POINTER(Shells),
+                                     C.c_int32, C.c_double, C.POINTER(PlanOpts), P,
+                                     C.POINTER(P)]
+    lib.acom_plan_destroy.argtypes = [P]
+    lib.acom_plan_get_info.argtypes = [P, C.POINTER(PlanInfo)]
+    lib.acom_plan_get_zone_axes.argtypes = [P, P]
+    lib.acom_plan_get_spectra.argtypes = [P, P, P]
+    lib.acom_match.argtypes = [P, C.POINTER(PeaksCSR), C.POINTER(MatchOpts), C.POINTER(Result), P]
+    lib.acom_polar_spectra.argtypes = [P, C.POINTER(PeaksCSR), P, P, P]
+    lib.acom_status_str.restype = C.c_char_p
+    lib.acom_status_str.argtypes = [C.c_int]
+    lib.acom_last_error.restype = C.c_char_p
+    lib.acom_version.restype = C.c_int32
+    for name in ("acom_plan_create", "acom_plan_destroy", "acom_plan_get_info",
+                 "acom_plan_get_zone_axes", "acom_plan_get_spectra", "acom_match",
+                 "acom_polar_spectra"):
+        getattr(lib, name).restype = C.c_int
+    _LIB = lib
+    return lib
+
+
+def _check(status):
+    if status != ACOM_OK:
+        msg = load_library().acom_last_error().decode()
+        raise AcomError(status, msg)
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+@dataclass
+class CrystalSpec:
+    """Lattice rows (Angstrom), fractional basis and single-Gaussian form
+    factors f_n(q) = A_n exp(-B_n q^2)."""
+    lattice: np.ndarray
+    frac_pos: np.ndarray
+    ff_A: np.ndarray
+    ff_B: np.ndarray
+
+
+def cubic_triangle():
+    """[001], [011], [111]; the m-3m standard triangle covers 4 pi / 48."""
+    return [[0, 0, 1], [0, 1, 1], [1, 1, 1]], 4 * math.pi / 48
+
+
+def hexagonal_triangle():
+    """[0001], a axis, 30 degrees in the basal plane; 1/24 of the sphere."""
+    return [[0, 0, 1], [1, 0, 0], [math.cos(math.pi / 6), math.sin(math.pi / 6), 0]], \
+        4 * math.pi / 24
+
+
+class Plan:
+    """Orientation plan on the current CUDA device (acom_plan_create)."""
+
+    def __init__(self, crystal: CrystalSpec, za_vectors, solid_angle, step_deg, n_shells, dq,
+                 n_phi, delta=0.08, gamma_pow=1.0, omega=1.0, lam=0.01969, q_max=1.5,
+                 sigma_exc=0.02, precision=ACOM_PREC_FP32, stream=None):
+        import torch  # noqa: F401  (device context)
+        lib = load_library()
+        self._lib = lib
+        lat = np.ascontiguousarray(crystal.lattice, dtype=np.float64)
+        self._pos = np.ascontiguousarray(crystal.frac_pos, dtype=np.float64).reshape(-1, 3)
+        self._A = np.ascontiguousarray(crystal.ff_A, dtype=np.float64).reshape(-1)
+        self._B = np.ascontiguousarray(crystal.ff_B, dtype=np.float64).reshape(-1)
+        cr = Crystal()
+        for i in range(3):
+            for j in range(3):
+                cr.lattice[i][j] = float(lat[i, j])
+        cr.n_atoms = len(self._pos)
+        dp = C.POINTER(C.c_double)
+        cr.frac_pos = self._pos.ctypes.data_as(dp)
+        cr.ff_A = self._A.ctypes.data_as(dp)
+        cr.ff_B = self._B.ctypes.data_as(dp)
+        g = ZaGrid()
+        for i in range(3):
+            for j in range(3):
+                g.v[i][j] = float(za_vectors[i][j])
+        g.step_deg = float(step_deg)
+        g.solid_angle = float(solid_angle)
+        sh = Shells(int(n_shells), float(dq))
+        op = PlanOpts(float(delta), float(gamma_pow), float(omega), float(lam), float(q_max),
+                      int(precision))
+        h = C.c_void_p()
+        _check(lib.acom_plan_create(C.byref(cr), C.byref(g), C.byref(sh), int(n_phi),
+                                    float(sigma_exc), C.byref(op), _stream_ptr(stream),
+                                    C.byref(h)))
+        self.handle = h
+        self.step_deg = float(step_deg)
+        self.info = self.get_info()
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            _check(self._lib.acom_plan_destroy(self.handle))
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def get_info(self):
+        inf = PlanInfo()
+        _check(self._lib.acom_plan_get_info(self.handle, C.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in PlanInfo._fields_}
+
+    def zone_axes(self):
+        out = np.empty((self.info["n_za"], 3), dtype=np.float64)
+        _check(self._lib.acom_plan_get_zone_axes(self.handle, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def spectra(self, stream=None):
+        import torch
+        i = self.info
+        out = torch.empty((i["n_za"], i["n_shells"], i["n_freq"], 2), dtype=torch.float32,
+                          device="cuda")
+        _check(self._lib.acom_plan_get_spectra(self.handle, _ptr(out), _stream_ptr(stream)))
+        return out
+
+    @staticmethod
+    def _csr(row_ptr, qx, qy, I):
+        import torch
+        for t, dt in ((row_ptr, torch.int64), (qx, torch.float32), (qy, torch.float32),
+                      (I, torch.float32)):
+            if t.dtype != dt or not t.is_cuda or not t.is_contiguous():
+                raise ValueError("peaks must be contiguous CUDA tensors: row_ptr int64, "
+                                 "qx/qy/I float32")
+        return PeaksCSR(row_ptr.numel() - 1, row_ptr.data_ptr(), qx.data_ptr(), qy.data_ptr(),
+                        I.data_ptr())
+
+    def polar_spectra(self, row_ptr, qx, qy, I, stream=None):
+        """[B][S][F][2] spectra of the sparse polar images and ||X||_2."""
+        import torch
+        pk = self._csr(row_ptr, qx, qy, I)
+        i = self.info
+        out = torch.empty((pk.n_patterns, i["n_shells"], i["n_freq"], 2), dtype=torch.float32,
+                          device="cuda")
+        xn = torch.empty((pk.n_patterns,), dtype=torch.float32, device="cuda")
+        _check(self._lib.acom_polar_spectra(self.handle, C.byref(pk), _ptr(out), _ptr(xn),
+                                            _stream_ptr(stream)))
+        return out, xn.sqrt()
+
+    def alloc_result(self, n, za_scores=False, orient=True):
+        import torch
+        dev = "cuda"
+        r = {"za_idx": torch.empty(n, dtype=torch.int32, device=dev),
+             "phi3_bin": torch.empty(n, dtype=torch.int32, device=dev),
+             "mirror": torch.empty(n, dtype=torch.uint8, device=dev),
+             "score": torch.empty(n, dtype=torch.float32, device=dev),
+             "score_cos": torch.empty(n, dtype=torch.float32, device=dev)}
+        if orient:
+            r["phi3"] = torch.empty(n, dtype=torch.float32, device=dev)
+            r["orient"] = torch.empty((n, 3, 3), dtype=torch.float32, device=dev)
+        if za_scores:
+            r["za_scores"] = torch.empty((n, self.info["n_za"]), dtype=torch.float32, device=dev)
+        return r
+
+    def match(self, row_ptr, qx, qy, I, refine=True, chunk=0, za_scores=False, out=None,
+              stream=None):
+        """acom_match on device CSR tensors; returns a dict of device tensors."""
+        pk = self._csr(row_ptr, qx, qy, I)
+        r = out if out is not None else self.alloc_result(pk.n_patterns, za_scores=za_scores)
+        res = Result(*(_ptr(r.get(k)) for k, _ in Result._fields_))
+        opts = MatchOpts(1 if refine else 0, int(chunk))
+        _check(self._lib.acom_match(self.handle, C.byref(pk), C.byref(opts), C.byref(res),
+                                    _stream_ptr(stream)))
+        return r
+
+
+def au_crystal(a=4.08):
+    """fcc Au, f(q) = 79 exp(-0.25 q^2)."""
+    return CrystalSpec(np.eye(3) * a,
+                       np.array([[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0]], float),
+                       np.full(4, 79.0), np.full(4, 0.25))
+
+
+def mg_crystal(a=3.21, c=5.21):
+    """hcp Mg-like P6_3/mmc, f(q) = 12 exp(-0.3 q^2)."""
+    L = np.array([[a, 0, 0], [-a / 2, a * math.sqrt(3) / 2, 0], [0, 0, c]])
+    return CrystalSpec(L, np.array([[1 / 3, 2 / 3, .25], [2 / 3, 1 / 3, .75]]),
+                       np.full(2, 12.0), np.full(2, 0.3))

@@ -1,0 +1,154 @@
+// Internal declarations shared by the translation units of libacom.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/acom.h"
+
+namespace acom {
+
+constexpr int kMaxPeaks = 1024;     // peaks per pattern held on chip
+constexpr int kMaxPhi = 720;        // in-plane bins (F <= 361)
+constexpr int kMaxShells = 512;
+constexpr int kRasterThreads = 256;  // 8 warps: one shell per warp per group
+constexpr int kShellGroup = 8;
+
+// device error word bits
+constexpr int kErrRowPtr = 1;       // row_ptr[0] != 0 or decreasing
+constexpr int kErrNonFinite = 2;    // qx, qy or I not finite
+constexpr int kErrTooManyPeaks = 4; // more than kMaxPeaks peaks in a pattern
+constexpr int kErrTimeout = 8;      // a bounded device wait gave up
+
+// Parameters of the sparse polar raster shared by plan and pattern sources.
+struct RasterGeom {
+    int S, Spad, N, F;
+    float dq;          // shells q_s = (s + 1) dq
+    float delta;
+    float gamma_pow;   // radial power
+    int shell_power;   // 1: multiply rows by q_s^gamma_pow (plan); 0: peaks carry q_m^gamma
+};
+
+struct PlanSource {            // reflections rotated into each zone-axis frame
+    const double* g;           // [G][3] crystal Cartesian
+    const double* amp;         // [G] |F|^omega
+    const double* frames;      // [Z][9] row-major R = Rz(phi1) Rx(theta2)
+    int G;
+    double lambda;
+};
+
+struct PatternSource {         // one chunk of CSR patterns
+    const int64_t* row_ptr;    // global row_ptr, already offset to the chunk start
+    const float* qx;
+    const float* qy;
+    const float* I;
+    int64_t n_items;
+    float gamma_pow, omega;
+};
+
+// Workspace for one chunk of patterns.
+struct Workspace {
+    int chunk = 0;                 // capacity in patterns
+    float* Xr = nullptr;           // [chunk][F][Spad]
+    float* Xi = nullptr;
+    float* xnorm2 = nullptr;       // [chunk]
+    float* Chat = nullptr;         // [4][F][chunk][Zp]
+    unsigned long long* best = nullptr;  // [chunk] packed (score, index)
+    float* za_scores = nullptr;    // [chunk][Z]
+    size_t bytes = 0;
+};
+
+}  // namespace acom
+
+struct acom_plan_s {
+    int device = 0;
+    int Z = 0, S = 0, N = 0, F = 0, Spad = 0, Zp = 0, G = 0;
+    double delta = 0, gamma_pow = 1, omega = 1, lambda = 0, q_max = 0, sigma_exc = 0;
+    double step_deg = 0, dq = 0;
+    int precision = ACOM_PREC_FP32;
+    std::vector<double> za_host;      // [Z][3]
+    // device memory
+    float* Pr = nullptr;              // [Zp][F][Spad], zero rows beyond Z
+    float* Pi = nullptr;
+    double* za = nullptr;             // [Z][3]
+    double* frames = nullptr;         // [Z][9]
+    int* nbr_ptr = nullptr;           // [Z + 1]
+    int* nbr_idx = nullptr;
+    double* refl_g = nullptr;         // [G][3]
+    double* refl_amp = nullptr;       // [G]
+    int* err = nullptr;               // device error word
+    size_t bytes = 0;
+    acom::Workspace ws;
+};
+
+namespace acom {
+
+// ---- per-kernel timing and launch count (profile.cu) ----
+enum KernelClass {
+    kKReflections, kKRasterPlan, kKScale, kKRasterPatterns, kKContract, kKIdft, kKRefine,
+    kKMisc, kKContractBf16, kKIdftBf16, kKRescore, kKCount
+};
+void prof_begin(int cls, cudaStream_t st);
+void prof_end(int cls, cudaStream_t st);
+void prof_resolve();
+
+// ---- error reporting (api.cu) ----
+acom_status set_error(acom_status s, const std::string& msg);
+acom_status cuda_error(cudaError_t e, const char* what);
+
+// ---- launchers (defined in the .cu files) ----
+// plan.cu
+acom_status build_plan_device(acom_plan_s* p, const acom_crystal* crystal, cudaStream_t st);
+// raster.cu
+void launch_raster_plan(const RasterGeom& geo, const PlanSource& src, int Z,
+                        float* out_re, float* out_im, float* sumsq, int* err, cudaStream_t st);
+void launch_raster_patterns(const RasterGeom& geo, const PatternSource& src,
+                            float* out_re, float* out_im, float* sumsq, int* err,
+                            cudaStream_t st);
+void launch_scale_rows(float* re, float* im, const float* sumsq, int items, int row_elems,
+                       cudaStream_t st);
+void launch_spectra_export(const float* re, const float* im, int items, int F, int Spad, int S,
+                           float* dst, cudaStream_t st);
+size_t raster_smem_bytes(int N, int F);
+// match_fp32.cu
+void launch_contract_fp32(const acom_plan_s* p, const float* Xr, const float* Xi, int nb,
+                          float* Chat, int chunk, cudaStream_t st);
+void launch_idft_argmax_fp32(const acom_plan_s* p, const float* Chat, int nb, int chunk,
+                             float* za_scores, unsigned long long* best, cudaStream_t st);
+void launch_refine(const acom_plan_s* p, const float* Chat, int nb, int chunk,
+                   const float* za_scores, const unsigned long long* best, const float* xnorm2,
+                   int refine, acom_result out, int64_t out_offset, cudaStream_t st);
+
+// Order-preserving map of a float to an unsigned key: larger float -> larger key.
+__host__ __device__ inline unsigned int float_order_key(float v) {
+    unsigned int u;
+#ifdef __CUDA_ARCH__
+    u = __float_as_uint(v);
+#else
+    memcpy(&u, &v, 4);
+#endif
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__host__ __device__ inline float float_from_order_key(unsigned int k) {
+    unsigned int u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+    float v;
+#ifdef __CUDA_ARCH__
+    v = __uint_as_float(u);
+#else
+    memcpy(&v, &u, 4);
+#endif
+    return v;
+}
+
+// Packed (score, index) key: max over keys = max score, then lowest index.
+__host__ __device__ inline unsigned long long pack_best(float score, unsigned int index) {
+    return ((unsigned long long)float_order_key(score) << 32) |
+           (unsigned long long)(0xffffffffu - index);
+}
+
+}  // namespace acom

@@ -1,0 +1,413 @@
+// C ABI of libacom: argument validation, the zone-axis grid and its frames
+// (host FP64), plan ownership, and the chunked match loop.
+#include <cmath>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "acom_internal.cuh"
+
+namespace acom {
+
+static thread_local std::string g_last_error;
+
+acom_status set_error(acom_status s, const std::string& msg) {
+    g_last_error = msg;
+    return s;
+}
+
+acom_status cuda_error(cudaError_t e, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return e == cudaErrorMemoryAllocation ? ACOM_ERR_OOM : ACOM_ERR_CUDA;
+}
+
+static void normalize3(double* v) {
+    double n = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    v[0] /= n;
+    v[1] /= n;
+    v[2] /= n;
+}
+
+// Spherical linear interpolation between unit vectors (Shoemake).
+static void slerp3(const double* p0, const double* p1, double t, double* out) {
+    double d = p0[0] * p1[0] + p0[1] * p1[1] + p0[2] * p1[2];
+    d = d > 1.0 ? 1.0 : (d < -1.0 ? -1.0 : d);
+    double om = std::acos(d);
+    if (om < 1e-15) {
+        out[0] = p0[0];
+        out[1] = p0[1];
+        out[2] = p0[2];
+        return;
+    }
+    double a = std::sin((1.0 - t) * om) / std::sin(om), b = std::sin(t * om) / std::sin(om);
+    for (int i = 0; i < 3; ++i) out[i] = a * p0[i] + b * p1[i];
+}
+
+// Grid of zone axes spanning v0, v1, v2: n = floor(sqrt(2 Omega)/step)
+// subdivisions; row i interpolates between slerp(v0,v1,i/n) and
+// slerp(v0,v2,i/n) at j/i, j = 0..i.
+static std::vector<double> zone_axes(const acom_za_grid* g) {
+    double v[3][3];
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) v[r][c] = g->v[r][c];
+        normalize3(v[r]);
+    }
+    int n = (int)std::floor(std::sqrt(2.0 * g->solid_angle) / (g->step_deg * M_PI / 180.0));
+    if (n < 1) n = 1;
+    std::vector<double> out;
+    out.reserve(3 * (size_t)(n + 1) * (n + 2) / 2);
+    for (int i = 0; i <= n; ++i) {
+        if (i == 0) {
+            out.insert(out.end(), v[0], v[0] + 3);
+            continue;
+        }
+        double a[3], b[3], w[3];
+        slerp3(v[0], v[1], (double)i / n, a);
+        slerp3(v[0], v[2], (double)i / n, b);
+        for (int j = 0; j <= i; ++j) {
+            slerp3(a, b, (double)j / i, w);
+            normalize3(w);
+            out.insert(out.end(), w, w + 3);
+        }
+    }
+    return out;
+}
+
+// R = Rz(phi1) Rx(theta2) with R z_hat = w (Eq. 10 sign convention):
+// columns ... third column (-S1 S2, C1 S2, C2).
+static void za_frame(const double* w, double* R) {
+    double th = std::acos(w[2] > 1.0 ? 1.0 : (w[2] < -1.0 ? -1.0 : w[2]));
+    double ph = std::atan2(-w[0], w[1]);
+    double c1 = std::cos(ph), s1 = std::sin(ph), c2 = std::cos(th), s2 = std::sin(th);
+    R[0] = c1; R[1] = -s1 * c2; R[2] = -s1 * s2;
+    R[3] = s1; R[4] = c1 * c2;  R[5] = c1 * s2;
+    R[6] = 0;  R[7] = -s2;      R[8] = c2;
+}
+
+template <class T>
+static cudaError_t dalloc(T** p, size_t n, size_t* acc) {
+    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (n ? n : 1));
+    if (e == cudaSuccess) *acc += sizeof(T) * (n ? n : 1);
+    return e;
+}
+
+static void free_workspace(Workspace& ws) {
+    cudaFree(ws.Xr);
+    cudaFree(ws.Xi);
+    cudaFree(ws.xnorm2);
+    cudaFree(ws.Chat);
+    cudaFree(ws.best);
+    cudaFree(ws.za_scores);
+    ws = Workspace{};
+}
+
+static acom_status ensure_workspace(acom_plan_s* p, int chunk) {
+    if (p->ws.chunk >= chunk) return ACOM_OK;
+    free_workspace(p->ws);
+    Workspace& ws = p->ws;
+    size_t acc = 0;
+    const size_t spec = (size_t)chunk * p->F * p->Spad;
+    cudaError_t e = cudaSuccess;
+    if ((e = dalloc(&ws.Xr, spec, &acc)) != cudaSuccess) goto fail;
+    if ((e = dalloc(&ws.Xi, spec, &acc)) != cudaSuccess) goto fail;
+    if ((e = dalloc(&ws.xnorm2, (size_t)chunk, &acc)) != cudaSuccess) goto fail;
+    if ((e = dalloc(&ws.Chat, (size_t)4 * p->F * chunk * p->Zp, &acc)) != cudaSuccess) goto fail;
+    if ((e = dalloc(&ws.best, (size_t)chunk, &acc)) != cudaSuccess) goto fail;
+    if ((e = dalloc(&ws.za_scores, (size_t)chunk * p->Z, &acc)) != cudaSuccess) goto fail;
+    ws.chunk = chunk;
+    ws.bytes = acc;
+    return ACOM_OK;
+fail:
+    free_workspace(p->ws);
+    return cuda_error(e, "match workspace allocation");
+}
+
+static void destroy_plan(acom_plan_s* p) {
+    if (!p) return;
+    free_workspace(p->ws);
+    cudaFree(p->Pr);
+    cudaFree(p->Pi);
+    cudaFree(p->za);
+    cudaFree(p->frames);
+    cudaFree(p->nbr_ptr);
+    cudaFree(p->nbr_idx);
+    cudaFree(p->refl_g);
+    cudaFree(p->refl_amp);
+    cudaFree(p->err);
+    delete p;
+}
+
+static bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+}  // namespace acom
+
+using namespace acom;
+
+extern "C" {
+
+int32_t acom_version(void) { return 1; }
+
+const char* acom_status_str(acom_status s) {
+    switch (s) {
+        case ACOM_OK: return "ACOM_OK";
+        case ACOM_ERR_INVALID_ARG: return "ACOM_ERR_INVALID_ARG";
+        case ACOM_ERR_OOM: return "ACOM_ERR_OOM";
+        case ACOM_ERR_CUDA: return "ACOM_ERR_CUDA";
+        case ACOM_ERR_TIMEOUT: return "ACOM_ERR_TIMEOUT";
+        case ACOM_ERR_UNSUPPORTED: return "ACOM_ERR_UNSUPPORTED";
+        case ACOM_ERR_BAD_INPUT: return "ACOM_ERR_BAD_INPUT";
+    }
+    return "ACOM_ERR_UNKNOWN";
+}
+
+const char* acom_last_error(void) { return g_last_error.c_str(); }
+
+acom_status acom_plan_create(const acom_crystal* crystal, const acom_za_grid* grid,
+                             const acom_shells* shells, int32_t n_phi, double sigma_exc,
+                             const acom_plan_opts* opts, void* cuda_stream, acom_plan* out) {
+    g_last_error.clear();
+    if (!crystal || !grid || !shells || !opts || !out)
+        return set_error(ACOM_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (crystal->n_atoms < 1 || crystal->n_atoms > 64 || !crystal->frac_pos || !crystal->ff_A ||
+        !crystal->ff_B)
+        return set_error(ACOM_ERR_INVALID_ARG, "crystal: n_atoms in 1..64 and basis arrays required");
+    for (int i = 0; i < 3 * crystal->n_atoms; ++i)
+        if (!std::isfinite(crystal->frac_pos[i]))
+            return set_error(ACOM_ERR_INVALID_ARG, "crystal: non-finite fractional position");
+    for (int i = 0; i < crystal->n_atoms; ++i)
+        if (!std::isfinite(crystal->ff_A[i]) || !std::isfinite(crystal->ff_B[i]))
+            return set_error(ACOM_ERR_INVALID_ARG, "crystal: non-finite form factor");
+    if (!finite_pos(grid->step_deg) || !finite_pos(grid->solid_angle) || grid->solid_angle > 4 * M_PI)
+        return set_error(ACOM_ERR_INVALID_ARG, "grid: step_deg and solid_angle must be positive");
+    for (int r = 0; r < 3; ++r) {
+        double n2 = 0;
+        for (int c = 0; c < 3; ++c) n2 += grid->v[r][c] * grid->v[r][c];
+        if (!(n2 > 0) || !std::isfinite(n2))
+            return set_error(ACOM_ERR_INVALID_ARG, "grid: zero or non-finite boundary vector");
+    }
+    if (shells->n_shells < 1 || shells->n_shells > kMaxShells || !finite_pos(shells->dq))
+        return set_error(ACOM_ERR_INVALID_ARG, "shells: n_shells in 1..512, dq > 0");
+    if (n_phi < 8 || n_phi > kMaxPhi || (n_phi & 1))
+        return set_error(ACOM_ERR_INVALID_ARG, "n_phi must be even, 8..720");
+    if (!finite_pos(opts->delta) || !finite_pos(opts->lambda) || !finite_pos(opts->q_max) ||
+        !std::isfinite(opts->gamma_pow) || !std::isfinite(opts->omega) || opts->omega < 0)
+        return set_error(ACOM_ERR_INVALID_ARG, "opts: delta, lambda, q_max > 0; finite powers");
+    if (opts->precision != ACOM_PREC_FP32 && opts->precision != ACOM_PREC_BF16)
+        return set_error(ACOM_ERR_INVALID_ARG, "opts: unknown precision");
+    if (opts->precision == ACOM_PREC_BF16)
+        return set_error(ACOM_ERR_UNSUPPORTED, "BF16 tensor-core path not built in this library");
+
+    std::vector<double> za = zone_axes(grid);
+    const int Z = (int)(za.size() / 3);
+    if (Z > 65535) return set_error(ACOM_ERR_UNSUPPORTED, "more than 65535 zone axes");
+
+    acom_plan_s* p = new acom_plan_s();
+    cudaGetDevice(&p->device);
+    p->Z = Z;
+    p->S = shells->n_shells;
+    p->N = n_phi;
+    p->F = n_phi / 2 + 1;
+    p->Spad = (p->S + 15) / 16 * 16;
+    p->Zp = (Z + 63) / 64 * 64;
+    p->delta = opts->delta;
+    p->gamma_pow = opts->gamma_pow;
+    p->omega = opts->omega;
+    p->lambda = opts->lambda;
+    p->q_max = opts->q_max;
+    p->sigma_exc = sigma_exc;
+    p->step_deg = grid->step_deg;
+    p->dq = shells->dq;
+    p->precision = opts->precision;
+    p->za_host = za;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+
+    std::vector<double> frames(9 * (size_t)Z);
+    for (int z = 0; z < Z; ++z) za_frame(&za[3 * z], &frames[9 * z]);
+    // grid neighbours: axes within 1.5 steps
+    std::vector<int> nptr(Z + 1, 0), nidx;
+    const double lim = std::cos(1.5 * grid->step_deg * M_PI / 180.0);
+    for (int z = 0; z < Z; ++z) {
+        for (int z2 = 0; z2 < Z; ++z2) {
+            double c = za[3 * z] * za[3 * z2] + za[3 * z + 1] * za[3 * z2 + 1] +
+                       za[3 * z + 2] * za[3 * z2 + 2];
+            if (c >= lim) nidx.push_back(z2);
+        }
+        nptr[z + 1] = (int)nidx.size();
+    }
+
+    cudaError_t e = cudaSuccess;
+    acom_status s;
+    const size_t pelems = (size_t)p->Zp * p->F * p->Spad;
+#define ACOM_CK(x)                                     \
+    do {                                               \
+        e = (x);                                       \
+        if (e != cudaSuccess) goto cuda_fail;          \
+    } while (0)
+    ACOM_CK(dalloc(&p->Pr, pelems, &p->bytes));
+    ACOM_CK(dalloc(&p->Pi, pelems, &p->bytes));
+    ACOM_CK(dalloc(&p->za, za.size(), &p->bytes));
+    ACOM_CK(dalloc(&p->frames, frames.size(), &p->bytes));
+    ACOM_CK(dalloc(&p->nbr_ptr, nptr.size(), &p->bytes));
+    ACOM_CK(dalloc(&p->nbr_idx, nidx.size(), &p->bytes));
+    ACOM_CK(dalloc(&p->err, 1, &p->bytes));
+    ACOM_CK(cudaMemsetAsync(p->Pr, 0, sizeof(float) * pelems, st));
+    ACOM_CK(cudaMemsetAsync(p->Pi, 0, sizeof(float) * pelems, st));
+    ACOM_CK(cudaMemsetAsync(p->err, 0, sizeof(int), st));
+    ACOM_CK(cudaMemcpyAsync(p->za, za.data(), sizeof(double) * za.size(), cudaMemcpyHostToDevice, st));
+    ACOM_CK(cudaMemcpyAsync(p->frames, frames.data(), sizeof(double) * frames.size(),
+                            cudaMemcpyHostToDevice, st));
+    ACOM_CK(cudaMemcpyAsync(p->nbr_ptr, nptr.data(), sizeof(int) * nptr.size(),
+                            cudaMemcpyHostToDevice, st));
+    ACOM_CK(cudaMemcpyAsync(p->nbr_idx, nidx.data(), sizeof(int) * nidx.size(),
+                            cudaMemcpyHostToDevice, st));
+    s = build_plan_device(p, crystal, st);
+    if (s != ACOM_OK) {
+        destroy_plan(p);
+        return s;
+    }
+    *out = p;
+    return ACOM_OK;
+cuda_fail:
+    destroy_plan(p);
+    return cuda_error(e, "plan_create");
+#undef ACOM_CK
+}
+
+acom_status acom_plan_destroy(acom_plan plan) {
+    if (!plan) return set_error(ACOM_ERR_INVALID_ARG, "null plan");
+    destroy_plan(plan);
+    return ACOM_OK;
+}
+
+acom_status acom_plan_get_info(acom_plan p, acom_plan_info* info) {
+    if (!p || !info) return set_error(ACOM_ERR_INVALID_ARG, "null argument");
+    info->n_za = p->Z;
+    info->n_shells = p->S;
+    info->n_phi = p->N;
+    info->n_freq = p->F;
+    info->n_reflections = p->G;
+    info->precision = p->precision;
+    info->device_bytes = (int64_t)(p->bytes + p->ws.bytes);
+    return ACOM_OK;
+}
+
+acom_status acom_plan_get_zone_axes(acom_plan p, double* dst) {
+    if (!p || !dst) return set_error(ACOM_ERR_INVALID_ARG, "null argument");
+    std::memcpy(dst, p->za_host.data(), sizeof(double) * p->za_host.size());
+    return ACOM_OK;
+}
+
+acom_status acom_plan_get_spectra(acom_plan p, float* dst, void* cuda_stream) {
+    if (!p || !dst) return set_error(ACOM_ERR_INVALID_ARG, "null argument");
+    launch_spectra_export(p->Pr, p->Pi, p->Z, p->F, p->Spad, p->S, dst, (cudaStream_t)cuda_stream);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? ACOM_OK : cuda_error(e, "get_spectra");
+}
+
+static acom_status check_peaks(const acom_peaks_csr* pk) {
+    if (!pk) return set_error(ACOM_ERR_INVALID_ARG, "null peaks");
+    if (pk->n_patterns < 0) return set_error(ACOM_ERR_INVALID_ARG, "n_patterns < 0");
+    if (pk->n_patterns > 0 && (!pk->row_ptr || !pk->qx || !pk->qy || !pk->I))
+        return set_error(ACOM_ERR_INVALID_ARG, "null peak array");
+    return ACOM_OK;
+}
+
+static acom_status read_error_word(acom_plan_s* p, cudaStream_t st) {
+    int herr = 0;
+    cudaError_t e = cudaMemcpyAsync(&herr, p->err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_error(e, "match");
+    prof_resolve();
+    if (herr & kErrTimeout) return set_error(ACOM_ERR_TIMEOUT, "device wait timed out");
+    if (herr & (kErrRowPtr | kErrNonFinite | kErrTooManyPeaks)) {
+        std::string m = "bad peak data:";
+        if (herr & kErrRowPtr) m += " row_ptr not starting at 0 or decreasing;";
+        if (herr & kErrNonFinite) m += " non-finite qx/qy/I;";
+        if (herr & kErrTooManyPeaks) m += " more than 1024 peaks in a pattern;";
+        return set_error(ACOM_ERR_BAD_INPUT, m);
+    }
+    return ACOM_OK;
+}
+
+__global__ void k_check_row0(const int64_t* row_ptr, int* err) {
+    if (row_ptr[0] != 0) atomicOr(err, kErrRowPtr);
+}
+
+acom_status acom_polar_spectra(acom_plan p, const acom_peaks_csr* peaks, float* dst, float* xnorm,
+                               void* cuda_stream) {
+    g_last_error.clear();
+    if (!p || !dst) return set_error(ACOM_ERR_INVALID_ARG, "null argument");
+    acom_status s = check_peaks(peaks);
+    if (s != ACOM_OK) return s;
+    const int64_t B = peaks->n_patterns;
+    if (B == 0) return ACOM_OK;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int chunk = (int)std::min<int64_t>(B, 1024);
+    s = ensure_workspace(p, chunk);
+    if (s != ACOM_OK) return s;
+    cudaMemsetAsync(p->err, 0, sizeof(int), st);
+    prof_begin(kKMisc, st);
+    k_check_row0<<<1, 1, 0, st>>>(peaks->row_ptr, p->err);
+    prof_end(kKMisc, st);
+    RasterGeom geo{p->S, p->Spad, p->N, p->F, (float)p->dq, (float)p->delta, (float)p->gamma_pow, 0};
+    for (int64_t c0 = 0; c0 < B; c0 += chunk) {
+        const int nb = (int)std::min<int64_t>(chunk, B - c0);
+        PatternSource src{peaks->row_ptr + c0, peaks->qx, peaks->qy, peaks->I, nb,
+                          (float)p->gamma_pow, (float)p->omega};
+        launch_raster_patterns(geo, src, p->ws.Xr, p->ws.Xi, p->ws.xnorm2, p->err, st);
+        launch_spectra_export(p->ws.Xr, p->ws.Xi, nb, p->F, p->Spad, p->S,
+                              dst + 2 * c0 * (int64_t)p->S * p->F, st);
+        if (xnorm) {
+            cudaMemcpyAsync(xnorm + c0, p->ws.xnorm2, sizeof(float) * nb, cudaMemcpyDeviceToDevice, st);
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "polar_spectra launch");
+    s = read_error_word(p, st);
+    return s;
+}
+
+acom_status acom_match(acom_plan p, const acom_peaks_csr* peaks, const acom_match_opts* opts,
+                       acom_result* out, void* cuda_stream) {
+    g_last_error.clear();
+    if (!p || !out) return set_error(ACOM_ERR_INVALID_ARG, "null argument");
+    acom_status s = check_peaks(peaks);
+    if (s != ACOM_OK) return s;
+    const int64_t B = peaks->n_patterns;
+    if (B > 0 && (!out->za_idx || !out->phi3_bin || !out->mirror || !out->score))
+        return set_error(ACOM_ERR_INVALID_ARG, "result: za_idx, phi3_bin, mirror, score required");
+    if (B == 0) return ACOM_OK;
+    int refine = opts ? opts->refine : 1;
+    int chunk = opts && opts->chunk > 0 ? opts->chunk : 1024;
+    if (chunk > 65536) return set_error(ACOM_ERR_INVALID_ARG, "chunk must be <= 65536");
+    chunk = (int)std::min<int64_t>(chunk, B);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    s = ensure_workspace(p, chunk);
+    if (s != ACOM_OK) return s;
+    cudaMemsetAsync(p->err, 0, sizeof(int), st);
+    prof_begin(kKMisc, st);
+    k_check_row0<<<1, 1, 0, st>>>(peaks->row_ptr, p->err);
+    prof_end(kKMisc, st);
+    RasterGeom geo{p->S, p->Spad, p->N, p->F, (float)p->dq, (float)p->delta, (float)p->gamma_pow, 0};
+    const int wchunk = p->ws.chunk;
+    for (int64_t c0 = 0; c0 < B; c0 += chunk) {
+        const int nb = (int)std::min<int64_t>(chunk, B - c0);
+        PatternSource src{peaks->row_ptr + c0, peaks->qx, peaks->qy, peaks->I, nb,
+                          (float)p->gamma_pow, (float)p->omega};
+        launch_raster_patterns(geo, src, p->ws.Xr, p->ws.Xi, p->ws.xnorm2, p->err, st);
+        cudaMemsetAsync(p->ws.best, 0, sizeof(unsigned long long) * nb, st);
+        launch_contract_fp32(p, p->ws.Xr, p->ws.Xi, nb, p->ws.Chat, wchunk, st);
+        launch_idft_argmax_fp32(p, p->ws.Chat, nb, wchunk, p->ws.za_scores, p->ws.best, st);
+        launch_refine(p, p->ws.Chat, nb, wchunk, p->ws.za_scores, p->ws.best, p->ws.xnorm2, refine,
+                      *out, c0, st);
+        if (out->za_scores)
+            cudaMemcpyAsync(out->za_scores + c0 * (int64_t)p->Z, p->ws.za_scores,
+                            sizeof(float) * (size_t)nb * p->Z, cudaMemcpyDeviceToDevice, st);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "match launch");
+    return read_error_word(p, st);
+}
+
+}  // extern "C"

@@ -1,0 +1,361 @@
+// Sparse polar raster + Fourier transform along phi3.
+//
+// One CTA handles one item at a time: a diffraction pattern (its CSR peak
+// list) or a zone axis of the orientation plan (the reflections rotated into
+// that axis' frame).  Both are rasterised with the same tent
+//
+//   T(s, j) = max{1 - (1/delta) sqrt((r - q_s)^2 + e + wrap(phi_j - gam)^2 q_s^2), 0}
+//
+// which is the sparse polar image X of section "Correlation Pattern Matching"
+// for a pattern peak (r = q_m, gam = gamma_m, e = 0, weight q_m^gamma
+// I_m^(omega/2)) and the plan P0 of section "Generation of an Orientation
+// Plan" for a reflection (r = |g'_xy|, gam = gamma_g, e = s_g^2, weight
+// |V_g|^omega, rows scaled by q_s^gamma) under uniform shells.
+//
+// Each warp owns one shell row of N bins in shared memory; peaks whose tent
+// reaches the shell add into the bins inside their angular window (lanes own
+// distinct bins, peaks are visited in order, so the sums are deterministic).
+// The row's non-zero bins are compacted and transformed directly,
+// X^(s, f) = sum_j X(s, j) exp(-2 pi i f j / N), f = 0..N/2, with a shared
+// twiddle table; eight shells are staged and written as 32-byte runs of the
+// [item][f][Spad] output.
+#include <math_constants.h>
+
+#include "acom_internal.cuh"
+
+namespace acom {
+
+struct Peak {
+    float r, gam, w, e;
+};
+
+// Block-ordered compaction: returns this thread's slot among the threads with
+// keep == true (in thread order) and the block total in *total.
+__device__ inline int block_compact(bool keep, int* s_warp, int* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) s_warp[warp] = __popc(m);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int w = 0; w < nwarps; ++w) {
+            int c = s_warp[w];
+            s_warp[w] = acc;
+            acc += c;
+        }
+        s_warp[nwarps] = acc;
+    }
+    __syncthreads();
+    int pos = s_warp[warp] + __popc(m & ((1u << lane) - 1u));
+    *total = s_warp[nwarps];
+    __syncthreads();
+    return pos;
+}
+
+struct PatternLoader {
+    PatternSource src;
+    __device__ int load(int64_t item, Peak* sp, int* s_warp, int* err) const {
+        const int64_t b0 = src.row_ptr[item];
+        const int64_t b1 = src.row_ptr[item + 1];
+        int64_t cnt = b1 - b0;
+        if (cnt < 0) {
+            if (threadIdx.x == 0) atomicOr(err, kErrRowPtr);
+            return 0;
+        }
+        if (cnt > kMaxPeaks) {
+            if (threadIdx.x == 0) atomicOr(err, kErrTooManyPeaks);
+            return 0;
+        }
+        const float half_omega = 0.5f * src.omega;
+        for (int i = threadIdx.x; i < (int)cnt; i += blockDim.x) {
+            float x = src.qx[b0 + i], y = src.qy[b0 + i], I = src.I[b0 + i];
+            Peak pk;
+            if (!(isfinite(x) && isfinite(y) && isfinite(I))) {
+                atomicOr(err, kErrNonFinite);
+                pk.r = 0.f; pk.gam = 0.f; pk.w = 0.f; pk.e = 0.f;
+            } else {
+                pk.r = sqrtf(x * x + y * y);
+                pk.gam = atan2f(y, x);
+                pk.w = powf(pk.r, src.gamma_pow) * powf(fmaxf(I, 0.f), half_omega);
+                pk.e = 0.f;
+            }
+            sp[i] = pk;
+        }
+        __syncthreads();
+        return (int)cnt;
+    }
+};
+
+struct PlanLoader {
+    PlanSource src;
+    float delta;
+    __device__ int load(int64_t item, Peak* sp, int* s_warp, int* err) const {
+        const double* R = src.frames + 9 * item;
+        double R00 = R[0], R01 = R[1], R02 = R[2], R10 = R[3], R11 = R[4], R12 = R[5],
+               R20 = R[6], R21 = R[7], R22 = R[8];
+        const double kz = -1.0 / src.lambda;   // beam along -z
+        int count = 0;
+        for (int base = 0; base < src.G; base += blockDim.x) {
+            int i = base + threadIdx.x;
+            bool keep = false;
+            Peak pk;
+            if (i < src.G) {
+                double gx = src.g[3 * i], gy = src.g[3 * i + 1], gz = src.g[3 * i + 2];
+                // g' = R^T g: the inverse of the zone-axis rotation
+                double px = R00 * gx + R10 * gy + R20 * gz;
+                double py = R01 * gx + R11 * gy + R21 * gz;
+                double pz = R02 * gx + R12 * gy + R22 * gz;
+                // Eq. 6 with alpha = 0: s = -g'.(2k + g') / (2 |k + g'|)
+                double dot = px * px + py * py + pz * (2.0 * kz + pz);
+                double nk = sqrt(px * px + py * py + (kz + pz) * (kz + pz));
+                double s = -dot / (2.0 * nk);
+                keep = fabs(s) < (double)delta;
+                pk.r = (float)sqrt(px * px + py * py);
+                pk.gam = (float)atan2(py, px);
+                pk.w = (float)src.amp[i];
+                pk.e = (float)(s * s);
+            }
+            int total;
+            int pos = block_compact(keep, s_warp, &total);
+            if (keep && count + pos < kMaxPeaks) sp[count + pos] = pk;
+            count += total;
+        }
+        if (count > kMaxPeaks) {
+            if (threadIdx.x == 0) atomicOr(err, kErrTooManyPeaks);
+            count = kMaxPeaks;
+        }
+        __syncthreads();
+        return count;
+    }
+};
+
+size_t raster_smem_bytes(int N, int F) {
+    const int W = kRasterThreads / 32;
+    size_t b = 0;
+    b += sizeof(Peak) * kMaxPeaks;     // peaks
+    b += sizeof(float) * 2 * N;        // twiddles
+    b += sizeof(float) * W * N;        // rows
+    b += sizeof(int) * W * N;          // tap bins
+    b += sizeof(float) * W * N;        // tap values
+    b += sizeof(float) * 2 * W * F;    // staged spectra
+    b += sizeof(int) * 64;             // scratch
+    return b;
+}
+
+template <class Loader>
+__global__ void __launch_bounds__(kRasterThreads)
+k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, float* __restrict__ out_re,
+             float* __restrict__ out_im, float* __restrict__ sumsq, int* err) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int N = geo.N, F = geo.F, S = geo.S, Spad = geo.Spad;
+    constexpr int W = kRasterThreads / 32;
+    Peak* sp = reinterpret_cast<Peak*>(smem);
+    float* twc = reinterpret_cast<float*>(sp + kMaxPeaks);
+    float* tws = twc + N;
+    float* rows = tws + N;
+    int* tapj = reinterpret_cast<int*>(rows + W * N);
+    float* tapv = reinterpret_cast<float*>(tapj + W * N);
+    float* st_re = tapv + W * N;
+    float* st_im = st_re + W * F;
+    int* s_int = reinterpret_cast<int*>(st_im + W * F);
+    float* s_sum = reinterpret_cast<float*>(s_int + 32);
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        double c, s;
+        sincospi(2.0 * (double)i / (double)N, &s, &c);
+        twc[i] = (float)c;
+        tws[i] = (float)s;
+    }
+    __syncthreads();
+
+    const float delta = geo.delta, d2 = delta * delta, inv_delta = 1.0f / delta;
+    const float two_pi = 2.0f * CUDART_PI_F;
+    const float dphi = two_pi / (float)N;
+    const float inv_dphi = (float)N / two_pi;
+    const float invN = 1.0f / (float)N;
+    float* row = rows + warp * N;
+    int* my_tj = tapj + warp * N;
+    float* my_tv = tapv + warp * N;
+
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int np = ld.load(item, sp, s_int, err);
+        float warp_sq = 0.f;                 // lane 0's running sum of squares
+        for (int s0 = 0; s0 < Spad; s0 += W) {
+            const int s = s0 + warp;
+            for (int j = lane; j < N; j += 32) row[j] = 0.f;
+            __syncwarp();
+            int ntap = 0;
+            if (s < S) {
+                const float qs = (float)(s + 1) * geo.dq;
+                const float qs2 = qs * qs;
+                for (int m = 0; m < np; ++m) {
+                    const Peak pk = sp[m];
+                    const float dr = pk.r - qs;
+                    const float a2 = dr * dr + pk.e;
+                    if (!(a2 < d2) || pk.w == 0.f) continue;       // tent is zero on this shell
+                    const float hw = sqrtf(d2 - a2) / qs;            // angular half width
+                    int jlo, cnt;
+                    if (hw >= CUDART_PI_F) {
+                        jlo = 0;
+                        cnt = N;
+                    } else {
+                        jlo = (int)floorf((pk.gam - hw) * inv_dphi) - 1;
+                        int jhi = (int)ceilf((pk.gam + hw) * inv_dphi) + 1;
+                        cnt = min(jhi - jlo + 1, N);
+                    }
+                    for (int t = lane; t < cnt; t += 32) {
+                        int j = jlo + t;
+                        j %= N;
+                        if (j < 0) j += N;
+                        float d = (float)j * dphi - pk.gam;
+                        d -= two_pi * floorf((d + CUDART_PI_F) / two_pi);   // wrap to [-pi, pi)
+                        float tv = 1.0f - sqrtf(a2 + d * d * qs2) * inv_delta;
+                        if (tv > 0.f) row[j] += pk.w * tv;
+                    }
+                    __syncwarp();
+                }
+                const float rscale = geo.shell_power ? powf(qs, geo.gamma_pow) : 1.0f;
+                float sq = 0.f;
+                for (int base = 0; base < N; base += 32) {
+                    int j = base + lane;
+                    float v = (j < N) ? row[j] * rscale : 0.f;
+                    sq += v * v;
+                    unsigned msk = __ballot_sync(0xffffffffu, v != 0.f);
+                    if (v != 0.f) {
+                        int pos = ntap + __popc(msk & ((1u << lane) - 1u));
+                        my_tj[pos] = j;
+                        my_tv[pos] = v;
+                    }
+                    ntap += __popc(msk);
+                }
+                for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+                warp_sq += sq;
+            }
+            __syncwarp();
+            // direct transform of the compacted taps
+            for (int f = lane; f < F; f += 32) {
+                float re = 0.f, im = 0.f;
+                for (int t = 0; t < ntap; ++t) {
+                    const int j = my_tj[t];
+                    const float v = my_tv[t];
+                    int prod = f * j;
+                    int q = __float2int_rz((float)prod * invN);
+                    int idx = prod - q * N;
+                    if (idx >= N) idx -= N;
+                    if (idx < 0) idx += N;
+                    re = fmaf(v, twc[idx], re);
+                    im = fmaf(-v, tws[idx], im);
+                }
+                st_re[warp * F + f] = re;
+                st_im[warp * F + f] = im;
+            }
+            __syncthreads();
+            const int64_t obase = item * (int64_t)F * Spad + s0;
+            for (int e = threadIdx.x; e < F * W; e += blockDim.x) {
+                const int f = e / W, w = e - f * W;
+                out_re[obase + (int64_t)f * Spad + w] = st_re[w * F + f];
+                out_im[obase + (int64_t)f * Spad + w] = st_im[w * F + f];
+            }
+            __syncthreads();
+        }
+        if (lane == 0) s_sum[warp] = warp_sq;
+        __syncthreads();
+        if (threadIdx.x == 0 && sumsq) {
+            float tot = 0.f;
+            for (int w = 0; w < W; ++w) tot += s_sum[w];
+            sumsq[item] = tot;
+        }
+        __syncthreads();
+    }
+}
+
+template <class Loader>
+static void launch_raster(const RasterGeom& geo, const Loader& ld, int64_t n_items,
+                          float* out_re, float* out_im, float* sumsq, int* err,
+                          cudaStream_t st, int cls) {
+    if (n_items <= 0) return;
+    size_t smem = raster_smem_bytes(geo.N, geo.F);
+    cudaFuncSetAttribute(k_raster_dft<Loader>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_dft<Loader>, kRasterThreads,
+                                                  smem);
+    int64_t grid = (int64_t)nsm * (per_sm > 0 ? per_sm : 1);
+    if (grid > n_items) grid = n_items;
+    prof_begin(cls, st);
+    k_raster_dft<Loader><<<(unsigned)grid, kRasterThreads, smem, st>>>(geo, ld, n_items, out_re,
+                                                                        out_im, sumsq, err);
+    prof_end(cls, st);
+}
+
+void launch_raster_plan(const RasterGeom& geo, const PlanSource& src, int Z, float* out_re,
+                        float* out_im, float* sumsq, int* err, cudaStream_t st) {
+    PlanLoader ld{src, geo.delta};
+    launch_raster(geo, ld, Z, out_re, out_im, sumsq, err, st, kKRasterPlan);
+}
+
+void launch_raster_patterns(const RasterGeom& geo, const PatternSource& src, float* out_re,
+                            float* out_im, float* sumsq, int* err, cudaStream_t st) {
+    PatternLoader ld{src};
+    launch_raster(geo, ld, src.n_items, out_re, out_im, sumsq, err, st, kKRasterPatterns);
+}
+
+// P = A P0 with A = 1/||P0||_2 (0 for an empty slice): the transform is
+// linear, so the spectrum rows are scaled after the fact.
+__global__ void k_scale_rows(float* re, float* im, const float* sumsq, int items,
+                             int64_t row_elems) {
+    int64_t total = (int64_t)items * row_elems;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int item = (int)(i / row_elems);
+        float ss = sumsq[item];
+        float a = ss > 0.f ? rsqrtf(ss) : 0.f;
+        re[i] *= a;
+        im[i] *= a;
+    }
+}
+
+void launch_scale_rows(float* re, float* im, const float* sumsq, int items, int row_elems,
+                       cudaStream_t st) {
+    int64_t total = (int64_t)items * row_elems;
+    int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    if (blocks > 0) {
+        prof_begin(kKScale, st);
+        k_scale_rows<<<blocks, 256, 0, st>>>(re, im, sumsq, items, row_elems);
+        prof_end(kKScale, st);
+    }
+}
+
+// [items][F][Spad] planar -> [items][S][F][2] interleaved
+__global__ void k_spectra_export(const float* re, const float* im, int items, int F, int Spad,
+                                 int S, float* dst) {
+    int64_t total = (int64_t)items * S * F;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int f = (int)(i % F);
+        int64_t t = i / F;
+        int s = (int)(t % S);
+        int64_t item = t / S;
+        int64_t src = (item * F + f) * Spad + s;
+        dst[2 * i] = re[src];
+        dst[2 * i + 1] = im[src];
+    }
+}
+
+void launch_spectra_export(const float* re, const float* im, int items, int F, int Spad, int S,
+                           float* dst, cudaStream_t st) {
+    int64_t total = (int64_t)items * S * F;
+    int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    if (blocks > 0) {
+        prof_begin(kKMisc, st);
+        k_spectra_export<<<blocks, 256, 0, st>>>(re, im, items, F, Spad, S, dst);
+        prof_end(kKMisc, st);
+    }
+}
+
+}  // namespace acom

@@ -1,0 +1,92 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds, loads,
+exports every entry point that include/acom.h declares, and rejects invalid
+arguments before touching the device."""
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "acom.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2111_00171_gb300 import acom
+    return acom.load_library()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(acom_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("acom_plan_create", "acom_match", "acom_plan_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2111_00171_gb300 import acom
+    names = declared_functions()
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(acom.EXPORTED) <= set(names)
+    assert lib.acom_version() >= 1
+
+
+def test_status_strings(lib):
+    for code, name in [(0, b"ACOM_OK"), (1, b"ACOM_ERR_INVALID_ARG"), (6, b"ACOM_ERR_BAD_INPUT")]:
+        assert lib.acom_status_str(code) == name
+
+
+def _args(n_phi=180, step=2.0, n_atoms=4, delta=0.08):
+    from paper_2111_00171_gb300 import acom
+    cr = acom.Crystal()
+    for i in range(3):
+        cr.lattice[i][i] = 4.08
+    pos = np.array([[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0]], dtype=np.float64)
+    ff = np.full(4, 79.0)
+    fb = np.full(4, 0.25)
+    dp = C.POINTER(C.c_double)
+    cr.n_atoms = n_atoms
+    cr.frac_pos = pos.ctypes.data_as(dp)
+    cr.ff_A = ff.ctypes.data_as(dp)
+    cr.ff_B = fb.ctypes.data_as(dp)
+    g = acom.ZaGrid()
+    for i, v in enumerate([[0, 0, 1], [0, 1, 1], [1, 1, 1]]):
+        for j in range(3):
+            g.v[i][j] = v[j]
+    g.step_deg = step
+    g.solid_angle = 4 * np.pi / 48
+    sh = acom.Shells(75, 0.02)
+    op = acom.PlanOpts(delta, 1.0, 1.0, 0.01969, 1.5, 0)
+    keep = (pos, ff, fb)
+    return cr, g, sh, n_phi, op, keep
+
+
+@pytest.mark.parametrize("bad", ["odd_nphi", "big_nphi", "step0", "atoms0", "delta0"])
+def test_plan_create_rejects_invalid_arguments(lib, bad):
+    kw = {"odd_nphi": dict(n_phi=181), "big_nphi": dict(n_phi=2048), "step0": dict(step=0.0),
+          "atoms0": dict(n_atoms=0), "delta0": dict(delta=0.0)}[bad]
+    cr, g, sh, n_phi, op, keep = _args(**kw)
+    h = C.c_void_p()
+    st = lib.acom_plan_create(C.byref(cr), C.byref(g), C.byref(sh), n_phi, 0.02, C.byref(op),
+                              None, C.byref(h))
+    assert st == 1, lib.acom_last_error()
+    assert not h.value
+    assert lib.acom_last_error()
+
+
+def test_match_rejects_null_plan(lib):
+    from paper_2111_00171_gb300 import acom
+    pk = acom.PeaksCSR(0, None, None, None, None)
+    res = acom.Result()
+    assert lib.acom_match(None, C.byref(pk), None, C.byref(res), None) == 1
