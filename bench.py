@@ -130,13 +130,22 @@ def misorientation(m_est, m_true):
     in-plane Friedel twin m Rz(pi), and the zone-axis tilt error."""
     ops = cubic_ops()
     me = m_est.astype(np.float64)
+    # re-orthonormalise the FP32-stored matrices before taking angles
+    u, _, vt = np.linalg.svd(me)
+    me = u @ vt
     SM = np.einsum("sij,bjk->sbik", ops, me)
-    tr = np.einsum("bji,sbji->sb", m_true, SM)
-    ang = np.degrees(np.arccos(np.clip((tr.max(axis=0) - 1) / 2, -1, 1)))
+
+    def angles(M):                      # rotation angle of m_true^T M, robust near 0
+        D = np.einsum("bji,sbjk->sbik", m_true, M)
+        tr = np.trace(D, axis1=2, axis2=3)
+        v = np.stack([D[..., 2, 1] - D[..., 1, 2], D[..., 0, 2] - D[..., 2, 0],
+                      D[..., 1, 0] - D[..., 0, 1]], -1)
+        return np.degrees(2 * np.arctan2(np.linalg.norm(v, axis=-1) / 2, (1 + tr) / 2))
+
+    a1 = angles(SM)
+    ang = a1.min(axis=0)
     Rz = np.diag([-1.0, -1.0, 1.0])
-    SM2 = np.einsum("sbik,kl->sbil", SM, Rz)
-    tr2 = np.einsum("bji,sbji->sb", m_true, SM2)
-    ang2 = np.degrees(np.arccos(np.clip((np.maximum(tr, tr2).max(axis=0) - 1) / 2, -1, 1)))
+    ang2 = np.minimum(a1, angles(np.einsum("sbik,kl->sbil", SM, Rz))).min(axis=0)
     we = np.einsum("sij,bj->sbi", ops, me[:, :, 2])
     c = np.abs(np.einsum("sbi,bi->sb", we, m_true[:, :, 2])).max(axis=0)
     tilt = np.degrees(np.arccos(np.clip(c, -1, 1)))
