@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--exhaustive", action="store_true",
+                    help="inverse-transform every zone axis (no certified pruning)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=16)
     return ap.parse_args()
@@ -275,9 +277,12 @@ def main():
 
     out_keys = ("za_idx", "phi3_bin", "mirror", "score", "score_cos", "phi3", "orient")
 
+    stats = {}
+
     def step(inputs, out):
         p = make_plan()
-        p.match(*inputs, chunk=args.chunk, out=out)
+        p.match(*inputs, chunk=args.chunk, out=out, exhaustive=args.exhaustive)
+        stats["evaluated"] = p.get_info()["last_evaluated"]
         p.close()
         return out
 
@@ -362,7 +367,9 @@ def main():
             "config": {"workload": WORKLOAD_TEXT, "patterns_per_gpu": B,
                        "peaks_nnz": int(scan.row_ptr[-1]), "zone_axes": 903, "shells": W["S"],
                        "n_phi": W["N"], "precision": args.precision,
-                       "chunk": args.chunk or 1024,
+                       "chunk": args.chunk or (1024 if args.exhaustive else 8192),
+                       "mode": "exhaustive" if args.exhaustive else "certified pruning",
+                       "axes_evaluated_per_pattern": stats.get("evaluated", 0) / B,
                        "l2": "flushed between steps (256 MiB write outside the timed events)",
                        "step": "plan build + match of every pattern",
                        "wall_ms_per_step": wall * 1e3 / K},

@@ -129,6 +129,7 @@ typedef struct {
     int32_t n_reflections;    /* reflections kept (0 < |g| < q_max, F != 0)     */
     int32_t precision;
     int64_t device_bytes;     /* device memory owned by the plan                */
+    int64_t last_evaluated;   /* zone axes evaluated in full by the last match  */
 } acom_plan_info;
 
 acom_status acom_plan_get_info(acom_plan plan, acom_plan_info* info);
@@ -170,7 +171,11 @@ typedef struct {
  *   phi3      optional: refined in-plane angle of the orientation (radians)
  *   orient    optional: [n_patterns][9] refined orientation matrix m, row
  *             major, mapping sample to crystal coordinates (Eq. 9)
- *   za_scores optional: [n_patterns][Z] max over phi3 and mirror per axis
+ *   za_scores optional: [n_patterns][Z] max over phi3 and mirror per axis.
+ *             With certified pruning (the default) the value is exact for
+ *             every axis that was evaluated (the winner and every axis whose
+ *             bound could reach it) and is otherwise an upper bound of the
+ *             axis' maximum, (1/N) sum_f w_f |c_f| plus a rounding margin.
  * Ties: the lowest zone-axis index wins, then C before C_mirror, then the
  * lowest phi3 bin.
  */
@@ -188,6 +193,8 @@ typedef struct {
 typedef struct {
     int32_t refine;           /* 1: sub-grid refinement of phi3 / orient        */
     int32_t chunk;            /* patterns per internal chunk, 0 = default       */
+    int32_t exhaustive;       /* 1: inverse-transform every zone axis (test and
+                                 reference mode); 0: certified pruning         */
 } acom_match_opts;
 
 /*
@@ -197,6 +204,13 @@ typedef struct {
  * the plan's conjugate spectra for every zone axis, the inverse transform to
  * C and C_mirror over phi3, the maximum over (zone axis, phi3, mirror), and
  * the refinement of the winner into an orientation matrix.
+ *
+ * Certified pruning (default): the contraction reduces each (zone axis,
+ * pattern) pair to the bound U = (1/N) sum_f w_f |c_f| >= max_k C[k] of its
+ * correlation spectrum c_f (w_0 = w_{N/2} = 1, else 2) plus a rounding margin;
+ * axes are then evaluated in full, in decreasing U, until no remaining bound
+ * can reach the best score.  The winner equals that of the exhaustive
+ * evaluation.  Zone-axis counts above 16384 require exhaustive mode.
  *
  * Work is queued on ``cuda_stream``; the call synchronises that stream once at
  * the end to read the device error word.  The first call on a plan allocates

@@ -56,7 +56,7 @@ class PlanOpts(C.Structure):
 class PlanInfo(C.Structure):
     _fields_ = [("n_za", C.c_int32), ("n_shells", C.c_int32), ("n_phi", C.c_int32),
                 ("n_freq", C.c_int32), ("n_reflections", C.c_int32), ("precision", C.c_int32),
-                ("device_bytes", C.c_int64)]
+                ("device_bytes", C.c_int64), ("last_evaluated", C.c_int64)]
 
 
 class PeaksCSR(C.Structure):
@@ -71,7 +71,7 @@ class Result(C.Structure):
 
 
 class MatchOpts(C.Structure):
-    _fields_ = [("refine", C.c_int32), ("chunk", C.c_int32)]
+    _fields_ = [("refine", C.c_int32), ("chunk", C.c_int32), ("exhaustive", C.c_int32)]
 
 
 _LIB = None
@@ -264,12 +264,12 @@ class Plan:
         return r
 
     def match(self, row_ptr, qx, qy, I, refine=True, chunk=0, za_scores=False, out=None,
-              stream=None):
+              exhaustive=False, stream=None):
         """acom_match on device CSR tensors; returns a dict of device tensors."""
         pk = self._csr(row_ptr, qx, qy, I)
         r = out if out is not None else self.alloc_result(pk.n_patterns, za_scores=za_scores)
         res = Result(*(_ptr(r.get(k)) for k, _ in Result._fields_))
-        opts = MatchOpts(1 if refine else 0, int(chunk))
+        opts = MatchOpts(1 if refine else 0, int(chunk), 1 if exhaustive else 0)
         _check(self._lib.acom_match(self.handle, C.byref(pk), C.byref(opts), C.byref(res),
                                     _stream_ptr(stream)))
         return r

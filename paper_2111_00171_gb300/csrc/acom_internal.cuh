@@ -56,7 +56,10 @@ struct Workspace {
     float* Xr = nullptr;           // [chunk][F][Spad]
     float* Xi = nullptr;
     float* xnorm2 = nullptr;       // [chunk]
-    float* Chat = nullptr;         // [4][F][chunk][Zp]
+    float* Chat = nullptr;         // [4][F][chunk][Zp] (exhaustive mode only)
+    float* U = nullptr;            // [chunk][Z] spectral bounds
+    float* xfn = nullptr;          // [chunk][F] ||X^_bf|| over shells
+    int* n_eval = nullptr;         // axes evaluated exactly in the last match
     unsigned long long* best = nullptr;  // [chunk] packed (score, index)
     float* za_scores = nullptr;    // [chunk][Z]
     size_t bytes = 0;
@@ -81,6 +84,8 @@ struct acom_plan_s {
     double* refl_g = nullptr;         // [G][3]
     double* refl_amp = nullptr;       // [G]
     int* err = nullptr;               // device error word
+    float* pfmax = nullptr;           // [F] max over axes of ||P^_zf|| over shells
+    int64_t last_evaluated = 0;       // axes evaluated exactly in the last match
     size_t bytes = 0;
     acom::Workspace ws;
 };
@@ -90,7 +95,7 @@ namespace acom {
 // ---- per-kernel timing and launch count (profile.cu) ----
 enum KernelClass {
     kKReflections, kKRasterPlan, kKScale, kKRasterPatterns, kKContract, kKIdft, kKRefine,
-    kKMisc, kKContractBf16, kKIdftBf16, kKRescore, kKCount
+    kKMisc, kKContractBf16, kKIdftBf16, kKRescore, kKSelect, kKCount
 };
 void prof_begin(int cls, cudaStream_t st);
 void prof_end(int cls, cudaStream_t st);
@@ -107,7 +112,7 @@ acom_status build_plan_device(acom_plan_s* p, const acom_crystal* crystal, cudaS
 void launch_raster_plan(const RasterGeom& geo, const PlanSource& src, int Z,
                         float* out_re, float* out_im, float* sumsq, int* err, cudaStream_t st);
 void launch_raster_patterns(const RasterGeom& geo, const PatternSource& src,
-                            float* out_re, float* out_im, float* sumsq, int* err,
+                            float* out_re, float* out_im, float* sumsq, float* fnorm, int* err,
                             cudaStream_t st);
 void launch_scale_rows(float* re, float* im, const float* sumsq, int items, int row_elems,
                        cudaStream_t st);
@@ -119,6 +124,14 @@ void launch_contract_fp32(const acom_plan_s* p, const float* Xr, const float* Xi
                           float* Chat, int chunk, cudaStream_t st);
 void launch_idft_argmax_fp32(const acom_plan_s* p, const float* Chat, int nb, int chunk,
                              float* za_scores, unsigned long long* best, cudaStream_t st);
+// match_prune.cu
+void launch_contract_bound_fp32(const acom_plan_s* p, const float* Xr, const float* Xi, int nb,
+                                float* U, cudaStream_t st);
+void launch_plan_fnorm_max(const acom_plan_s* p, float* out, cudaStream_t st);
+void launch_select_exact(const acom_plan_s* p, const float* Xr, const float* Xi, const float* U,
+                         const float* xfn, const float* pfmax, const float* xnorm2, int nb,
+                         float kappa, int refine, acom_result out, int64_t off, int* n_eval,
+                         cudaStream_t st);
 void launch_refine(const acom_plan_s* p, const float* Chat, int nb, int chunk,
                    const float* za_scores, const unsigned long long* best, const float* xnorm2,
                    int refine, acom_result out, int64_t out_offset, cudaStream_t st);

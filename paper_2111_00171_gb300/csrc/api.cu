@@ -96,13 +96,17 @@ static void free_workspace(Workspace& ws) {
     cudaFree(ws.Xi);
     cudaFree(ws.xnorm2);
     cudaFree(ws.Chat);
+    cudaFree(ws.U);
+    cudaFree(ws.xfn);
+    cudaFree(ws.n_eval);
     cudaFree(ws.best);
     cudaFree(ws.za_scores);
     ws = Workspace{};
 }
 
-static acom_status ensure_workspace(acom_plan_s* p, int chunk) {
-    if (p->ws.chunk >= chunk) return ACOM_OK;
+static acom_status ensure_workspace(acom_plan_s* p, int chunk, bool need_chat) {
+    if (p->ws.chunk >= chunk && (!need_chat || p->ws.Chat)) return ACOM_OK;
+    if (p->ws.chunk > chunk) chunk = p->ws.chunk;
     free_workspace(p->ws);
     Workspace& ws = p->ws;
     size_t acc = 0;
@@ -111,7 +115,12 @@ static acom_status ensure_workspace(acom_plan_s* p, int chunk) {
     if ((e = dalloc(&ws.Xr, spec, &acc)) != cudaSuccess) goto fail;
     if ((e = dalloc(&ws.Xi, spec, &acc)) != cudaSuccess) goto fail;
     if ((e = dalloc(&ws.xnorm2, (size_t)chunk, &acc)) != cudaSuccess) goto fail;
-    if ((e = dalloc(&ws.Chat, (size_t)4 * p->F * chunk * p->Zp, &acc)) != cudaSuccess) goto fail;
+    if (need_chat &&
+        (e = dalloc(&ws.Chat, (size_t)4 * p->F * chunk * p->Zp, &acc)) != cudaSuccess)
+        goto fail;
+    if ((e = dalloc(&ws.U, (size_t)chunk * p->Z, &acc)) != cudaSuccess) goto fail;
+    if ((e = dalloc(&ws.xfn, (size_t)chunk * p->F, &acc)) != cudaSuccess) goto fail;
+    if ((e = dalloc(&ws.n_eval, (size_t)1, &acc)) != cudaSuccess) goto fail;
     if ((e = dalloc(&ws.best, (size_t)chunk, &acc)) != cudaSuccess) goto fail;
     if ((e = dalloc(&ws.za_scores, (size_t)chunk * p->Z, &acc)) != cudaSuccess) goto fail;
     ws.chunk = chunk;
@@ -134,6 +143,7 @@ static void destroy_plan(acom_plan_s* p) {
     cudaFree(p->refl_g);
     cudaFree(p->refl_amp);
     cudaFree(p->err);
+    cudaFree(p->pfmax);
     delete p;
 }
 
@@ -251,6 +261,7 @@ acom_status acom_plan_create(const acom_crystal* crystal, const acom_za_grid* gr
     ACOM_CK(dalloc(&p->nbr_ptr, nptr.size(), &p->bytes));
     ACOM_CK(dalloc(&p->nbr_idx, nidx.size(), &p->bytes));
     ACOM_CK(dalloc(&p->err, 1, &p->bytes));
+    ACOM_CK(dalloc(&p->pfmax, (size_t)p->F, &p->bytes));
     ACOM_CK(cudaMemsetAsync(p->Pr, 0, sizeof(float) * pelems, st));
     ACOM_CK(cudaMemsetAsync(p->Pi, 0, sizeof(float) * pelems, st));
     ACOM_CK(cudaMemsetAsync(p->err, 0, sizeof(int), st));
@@ -266,6 +277,10 @@ acom_status acom_plan_create(const acom_crystal* crystal, const acom_za_grid* gr
         destroy_plan(p);
         return s;
     }
+    launch_plan_fnorm_max(p, p->pfmax, st);
+    ACOM_CK(cudaGetLastError());
+    ACOM_CK(cudaStreamSynchronize(st));
+    prof_resolve();
     *out = p;
     return ACOM_OK;
 cuda_fail:
@@ -289,6 +304,7 @@ acom_status acom_plan_get_info(acom_plan p, acom_plan_info* info) {
     info->n_reflections = p->G;
     info->precision = p->precision;
     info->device_bytes = (int64_t)(p->bytes + p->ws.bytes);
+    info->last_evaluated = p->last_evaluated;
     return ACOM_OK;
 }
 
@@ -344,7 +360,7 @@ acom_status acom_polar_spectra(acom_plan p, const acom_peaks_csr* peaks, float* 
     if (B == 0) return ACOM_OK;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const int chunk = (int)std::min<int64_t>(B, 1024);
-    s = ensure_workspace(p, chunk);
+    s = ensure_workspace(p, chunk, false);
     if (s != ACOM_OK) return s;
     cudaMemsetAsync(p->err, 0, sizeof(int), st);
     prof_begin(kKMisc, st);
@@ -355,7 +371,7 @@ acom_status acom_polar_spectra(acom_plan p, const acom_peaks_csr* peaks, float* 
         const int nb = (int)std::min<int64_t>(chunk, B - c0);
         PatternSource src{peaks->row_ptr + c0, peaks->qx, peaks->qy, peaks->I, nb,
                           (float)p->gamma_pow, (float)p->omega};
-        launch_raster_patterns(geo, src, p->ws.Xr, p->ws.Xi, p->ws.xnorm2, p->err, st);
+        launch_raster_patterns(geo, src, p->ws.Xr, p->ws.Xi, p->ws.xnorm2, nullptr, p->err, st);
         launch_spectra_export(p->ws.Xr, p->ws.Xi, nb, p->F, p->Spad, p->S,
                               dst + 2 * c0 * (int64_t)p->S * p->F, st);
         if (xnorm) {
@@ -368,6 +384,12 @@ acom_status acom_polar_spectra(acom_plan p, const acom_peaks_csr* peaks, float* 
     return s;
 }
 
+// Rounding constant of the FP32 contraction: |c_f(computed) - c_f| <= kappa
+// ||P^_f|| ||X^_f|| (dot products of 2S terms, complex combination, sqrt).
+static float kappa_fp32(const acom_plan_s* p) {
+    return (float)((3.0 * (p->Spad + 2) + 2.0 * p->F) * std::ldexp(1.0, -24));
+}
+
 acom_status acom_match(acom_plan p, const acom_peaks_csr* peaks, const acom_match_opts* opts,
                        acom_result* out, void* cuda_stream) {
     g_last_error.clear();
@@ -378,14 +400,18 @@ acom_status acom_match(acom_plan p, const acom_peaks_csr* peaks, const acom_matc
     if (B > 0 && (!out->za_idx || !out->phi3_bin || !out->mirror || !out->score))
         return set_error(ACOM_ERR_INVALID_ARG, "result: za_idx, phi3_bin, mirror, score required");
     if (B == 0) return ACOM_OK;
-    int refine = opts ? opts->refine : 1;
-    int chunk = opts && opts->chunk > 0 ? opts->chunk : 1024;
+    const int refine = opts ? opts->refine : 1;
+    const bool exhaustive = opts && opts->exhaustive;
+    if (!exhaustive && p->Z > 16384)
+        return set_error(ACOM_ERR_UNSUPPORTED, "pruned mode supports at most 16384 zone axes");
+    int chunk = opts && opts->chunk > 0 ? opts->chunk : (exhaustive ? 1024 : 8192);
     if (chunk > 65536) return set_error(ACOM_ERR_INVALID_ARG, "chunk must be <= 65536");
     chunk = (int)std::min<int64_t>(chunk, B);
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    s = ensure_workspace(p, chunk);
+    s = ensure_workspace(p, chunk, exhaustive);
     if (s != ACOM_OK) return s;
     cudaMemsetAsync(p->err, 0, sizeof(int), st);
+    cudaMemsetAsync(p->ws.n_eval, 0, sizeof(int), st);
     prof_begin(kKMisc, st);
     k_check_row0<<<1, 1, 0, st>>>(peaks->row_ptr, p->err);
     prof_end(kKMisc, st);
@@ -395,19 +421,30 @@ acom_status acom_match(acom_plan p, const acom_peaks_csr* peaks, const acom_matc
         const int nb = (int)std::min<int64_t>(chunk, B - c0);
         PatternSource src{peaks->row_ptr + c0, peaks->qx, peaks->qy, peaks->I, nb,
                           (float)p->gamma_pow, (float)p->omega};
-        launch_raster_patterns(geo, src, p->ws.Xr, p->ws.Xi, p->ws.xnorm2, p->err, st);
-        cudaMemsetAsync(p->ws.best, 0, sizeof(unsigned long long) * nb, st);
-        launch_contract_fp32(p, p->ws.Xr, p->ws.Xi, nb, p->ws.Chat, wchunk, st);
-        launch_idft_argmax_fp32(p, p->ws.Chat, nb, wchunk, p->ws.za_scores, p->ws.best, st);
-        launch_refine(p, p->ws.Chat, nb, wchunk, p->ws.za_scores, p->ws.best, p->ws.xnorm2, refine,
-                      *out, c0, st);
-        if (out->za_scores)
-            cudaMemcpyAsync(out->za_scores + c0 * (int64_t)p->Z, p->ws.za_scores,
-                            sizeof(float) * (size_t)nb * p->Z, cudaMemcpyDeviceToDevice, st);
+        launch_raster_patterns(geo, src, p->ws.Xr, p->ws.Xi, p->ws.xnorm2, p->ws.xfn, p->err, st);
+        if (exhaustive) {
+            cudaMemsetAsync(p->ws.best, 0, sizeof(unsigned long long) * nb, st);
+            launch_contract_fp32(p, p->ws.Xr, p->ws.Xi, nb, p->ws.Chat, wchunk, st);
+            launch_idft_argmax_fp32(p, p->ws.Chat, nb, wchunk, p->ws.za_scores, p->ws.best, st);
+            launch_refine(p, p->ws.Chat, nb, wchunk, p->ws.za_scores, p->ws.best, p->ws.xnorm2,
+                          refine, *out, c0, st);
+            if (out->za_scores)
+                cudaMemcpyAsync(out->za_scores + c0 * (int64_t)p->Z, p->ws.za_scores,
+                                sizeof(float) * (size_t)nb * p->Z, cudaMemcpyDeviceToDevice, st);
+        } else {
+            launch_contract_bound_fp32(p, p->ws.Xr, p->ws.Xi, nb, p->ws.U, st);
+            launch_select_exact(p, p->ws.Xr, p->ws.Xi, p->ws.U, p->ws.xfn, p->pfmax,
+                                p->ws.xnorm2, nb, kappa_fp32(p), refine, *out, c0, p->ws.n_eval,
+                                st);
+        }
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "match launch");
-    return read_error_word(p, st);
+    int nev = 0;
+    cudaMemcpyAsync(&nev, p->ws.n_eval, sizeof(int), cudaMemcpyDeviceToHost, st);
+    s = read_error_word(p, st);
+    p->last_evaluated = exhaustive ? (int64_t)B * p->Z : nev;
+    return s;
 }
 
 }  // extern "C"

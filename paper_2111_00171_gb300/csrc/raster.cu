@@ -139,6 +139,7 @@ size_t raster_smem_bytes(int N, int F) {
     b += sizeof(int) * W * N;          // tap bins
     b += sizeof(float) * W * N;        // tap values
     b += sizeof(float) * 2 * W * F;    // staged spectra
+    b += sizeof(float) * F;            // per-frequency norms
     b += sizeof(int) * 64;             // scratch
     return b;
 }
@@ -146,7 +147,8 @@ size_t raster_smem_bytes(int N, int F) {
 template <class Loader>
 __global__ void __launch_bounds__(kRasterThreads)
 k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, float* __restrict__ out_re,
-             float* __restrict__ out_im, float* __restrict__ sumsq, int* err) {
+             float* __restrict__ out_im, float* __restrict__ sumsq, float* __restrict__ fnorm,
+             int* err) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int N = geo.N, F = geo.F, S = geo.S, Spad = geo.Spad;
     constexpr int W = kRasterThreads / 32;
@@ -158,7 +160,8 @@ k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, float* __restrict__ out
     float* tapv = reinterpret_cast<float*>(tapj + W * N);
     float* st_re = tapv + W * N;
     float* st_im = st_re + W * F;
-    int* s_int = reinterpret_cast<int*>(st_im + W * F);
+    float* fn2 = st_im + W * F;                         // [F] sum over shells of |X^|^2
+    int* s_int = reinterpret_cast<int*>(fn2 + F);
     float* s_sum = reinterpret_cast<float*>(s_int + 32);
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -182,6 +185,7 @@ k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, float* __restrict__ out
     for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int np = ld.load(item, sp, s_int, err);
         float warp_sq = 0.f;                 // lane 0's running sum of squares
+        for (int f = threadIdx.x; f < F; f += blockDim.x) fn2[f] = 0.f;
         for (int s0 = 0; s0 < Spad; s0 += W) {
             const int s = s0 + warp;
             for (int j = lane; j < N; j += 32) row[j] = 0.f;
@@ -252,6 +256,15 @@ k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, float* __restrict__ out
                 st_im[warp * F + f] = im;
             }
             __syncthreads();
+            if (fnorm) {
+                for (int f = threadIdx.x; f < F; f += blockDim.x) {
+                    float acc = fn2[f];
+                    for (int w = 0; w < W; ++w)
+                        acc = fmaf(st_re[w * F + f], st_re[w * F + f],
+                                   fmaf(st_im[w * F + f], st_im[w * F + f], acc));
+                    fn2[f] = acc;
+                }
+            }
             const int64_t obase = item * (int64_t)F * Spad + s0;
             for (int e = threadIdx.x; e < F * W; e += blockDim.x) {
                 const int f = e / W, w = e - f * W;
@@ -262,6 +275,9 @@ k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, float* __restrict__ out
         }
         if (lane == 0) s_sum[warp] = warp_sq;
         __syncthreads();
+        if (fnorm)
+            for (int f = threadIdx.x; f < F; f += blockDim.x)
+                fnorm[item * (int64_t)F + f] = sqrtf(fn2[f]);
         if (threadIdx.x == 0 && sumsq) {
             float tot = 0.f;
             for (int w = 0; w < W; ++w) tot += s_sum[w];
@@ -273,7 +289,7 @@ k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, float* __restrict__ out
 
 template <class Loader>
 static void launch_raster(const RasterGeom& geo, const Loader& ld, int64_t n_items,
-                          float* out_re, float* out_im, float* sumsq, int* err,
+                          float* out_re, float* out_im, float* sumsq, float* fnorm, int* err,
                           cudaStream_t st, int cls) {
     if (n_items <= 0) return;
     size_t smem = raster_smem_bytes(geo.N, geo.F);
@@ -289,20 +305,20 @@ static void launch_raster(const RasterGeom& geo, const Loader& ld, int64_t n_ite
     if (grid > n_items) grid = n_items;
     prof_begin(cls, st);
     k_raster_dft<Loader><<<(unsigned)grid, kRasterThreads, smem, st>>>(geo, ld, n_items, out_re,
-                                                                        out_im, sumsq, err);
+                                                                        out_im, sumsq, fnorm, err);
     prof_end(cls, st);
 }
 
 void launch_raster_plan(const RasterGeom& geo, const PlanSource& src, int Z, float* out_re,
                         float* out_im, float* sumsq, int* err, cudaStream_t st) {
     PlanLoader ld{src, geo.delta};
-    launch_raster(geo, ld, Z, out_re, out_im, sumsq, err, st, kKRasterPlan);
+    launch_raster(geo, ld, Z, out_re, out_im, sumsq, nullptr, err, st, kKRasterPlan);
 }
 
 void launch_raster_patterns(const RasterGeom& geo, const PatternSource& src, float* out_re,
-                            float* out_im, float* sumsq, int* err, cudaStream_t st) {
+                            float* out_im, float* sumsq, float* fnorm, int* err, cudaStream_t st) {
     PatternLoader ld{src};
-    launch_raster(geo, ld, src.n_items, out_re, out_im, sumsq, err, st, kKRasterPatterns);
+    launch_raster(geo, ld, src.n_items, out_re, out_im, sumsq, fnorm, err, st, kKRasterPatterns);
 }
 
 // P = A P0 with A = 1/||P0||_2 (0 for an empty slice): the transform is
