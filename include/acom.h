@@ -251,6 +251,18 @@ void acom_profile_reset(void);
 int32_t acom_profile_read(acom_profile_entry* out, int32_t max);
 int64_t acom_kernel_launches(void);
 
+/*
+ * acom_bounds - the shell contraction alone: for every pattern and zone axis
+ * the spectral bound U = max over {direct, mirror} of (1/N) sum_f w_f |c_f|,
+ * which is >= max over phi3 of C (section "Correlation Pattern Matching";
+ * w_0 = w_{N/2} = 1, else 2).  Computed at the plan's precision (FP32 CUDA
+ * cores, or BF16 tensor cores with FP32 accumulation) without any rounding
+ * margin.  ``dst``: DEVICE [n_patterns][Z] FP32.  Stream-ordered; synchronises
+ * once to read the error word.
+ */
+acom_status acom_bounds(acom_plan plan, const acom_peaks_csr* peaks, float* dst,
+                        void* cuda_stream);
+
 const char* acom_status_str(acom_status status);
 const char* acom_last_error(void);
 

@@ -42,6 +42,8 @@ struct PlanSource {            // reflections rotated into each zone-axis frame
 };
 
 struct PatternSource {         // one chunk of CSR patterns
+    void* xb;                  // optional BF16 [F][PTs][128][Spad] output
+    int PTs;
     const int64_t* row_ptr;    // global row_ptr, already offset to the chunk start
     const float* qx;
     const float* qy;
@@ -58,6 +60,9 @@ struct Workspace {
     float* xnorm2 = nullptr;       // [chunk]
     float* Chat = nullptr;         // [4][F][chunk][Zp] (exhaustive mode only)
     float* U = nullptr;            // [chunk][Z] spectral bounds
+    void* XB = nullptr;            // BF16 [F][PTs][128][Spad] (tensor-core operand)
+    int PTs = 0;                   // pattern tiles of 64 in XB
+    alignas(64) unsigned char map_x[128];   // TMA map of XB
     float* xfn = nullptr;          // [chunk][F] ||X^_bf|| over shells
     int* n_eval = nullptr;         // axes evaluated exactly in the last match
     unsigned long long* best = nullptr;  // [chunk] packed (score, index)
@@ -85,6 +90,10 @@ struct acom_plan_s {
     double* refl_amp = nullptr;       // [G]
     int* err = nullptr;               // device error word
     float* pfmax = nullptr;           // [F] max over axes of ||P^_zf|| over shells
+    void* Pb_r = nullptr;             // BF16 [F][Zp][Spad] (tensor-core operand)
+    void* Pb_i = nullptr;
+    alignas(64) unsigned char map_pr[128];  // TMA maps of Pb_r, Pb_i
+    alignas(64) unsigned char map_pi[128];
     int64_t last_evaluated = 0;       // axes evaluated exactly in the last match
     size_t bytes = 0;
     acom::Workspace ws;
@@ -128,6 +137,11 @@ void launch_idft_argmax_fp32(const acom_plan_s* p, const float* Chat, int nb, in
 void launch_contract_bound_fp32(const acom_plan_s* p, const float* Xr, const float* Xi, int nb,
                                 float* U, cudaStream_t st);
 void launch_plan_fnorm_max(const acom_plan_s* p, float* out, cudaStream_t st);
+// match_tc.cu
+acom_status make_bf16_map(void* map_storage, const void* base, uint64_t rows, uint64_t cols);
+void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_stride, int nb,
+                              float* U, cudaStream_t st);
+void launch_plan_to_bf16(const float* src, int Zp, int F, int Spad, void* dst, cudaStream_t st);
 void launch_select_exact(const acom_plan_s* p, const float* Xr, const float* Xi, const float* U,
                          const float* xfn, const float* pfmax, const float* xnorm2, int nb,
                          float kappa, int refine, acom_result out, int64_t off, int* n_eval,

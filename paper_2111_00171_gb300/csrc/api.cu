@@ -101,6 +101,7 @@ static void free_workspace(Workspace& ws) {
     cudaFree(ws.n_eval);
     cudaFree(ws.best);
     cudaFree(ws.za_scores);
+    cudaFree(ws.XB);
     ws = Workspace{};
 }
 
@@ -123,6 +124,18 @@ static acom_status ensure_workspace(acom_plan_s* p, int chunk, bool need_chat) {
     if ((e = dalloc(&ws.n_eval, (size_t)1, &acc)) != cudaSuccess) goto fail;
     if ((e = dalloc(&ws.best, (size_t)chunk, &acc)) != cudaSuccess) goto fail;
     if ((e = dalloc(&ws.za_scores, (size_t)chunk * p->Z, &acc)) != cudaSuccess) goto fail;
+    if (p->precision == ACOM_PREC_BF16) {
+        ws.PTs = (chunk + 63) / 64;
+        const size_t rows = (size_t)p->F * ws.PTs * 128;
+        if ((e = cudaMalloc(&ws.XB, rows * p->Spad * 2)) != cudaSuccess) goto fail;
+        acc += rows * p->Spad * 2;
+        if ((e = cudaMemset(ws.XB, 0, rows * p->Spad * 2)) != cudaSuccess) goto fail;
+        acom_status ms = make_bf16_map(ws.map_x, ws.XB, rows, (uint64_t)p->Spad);
+        if (ms != ACOM_OK) {
+            free_workspace(p->ws);
+            return ms;
+        }
+    }
     ws.chunk = chunk;
     ws.bytes = acc;
     return ACOM_OK;
@@ -144,6 +157,8 @@ static void destroy_plan(acom_plan_s* p) {
     cudaFree(p->refl_amp);
     cudaFree(p->err);
     cudaFree(p->pfmax);
+    cudaFree(p->Pb_r);
+    cudaFree(p->Pb_i);
     delete p;
 }
 
@@ -205,8 +220,6 @@ acom_status acom_plan_create(const acom_crystal* crystal, const acom_za_grid* gr
         return set_error(ACOM_ERR_INVALID_ARG, "opts: delta, lambda, q_max > 0; finite powers");
     if (opts->precision != ACOM_PREC_FP32 && opts->precision != ACOM_PREC_BF16)
         return set_error(ACOM_ERR_INVALID_ARG, "opts: unknown precision");
-    if (opts->precision == ACOM_PREC_BF16)
-        return set_error(ACOM_ERR_UNSUPPORTED, "BF16 tensor-core path not built in this library");
 
     std::vector<double> za = zone_axes(grid);
     const int Z = (int)(za.size() / 3);
@@ -218,8 +231,8 @@ acom_status acom_plan_create(const acom_crystal* crystal, const acom_za_grid* gr
     p->S = shells->n_shells;
     p->N = n_phi;
     p->F = n_phi / 2 + 1;
-    p->Spad = (p->S + 15) / 16 * 16;
-    p->Zp = (Z + 63) / 64 * 64;
+    p->Spad = (p->S + 31) / 32 * 32;     // K tiles of 32 for the tensor-core operands
+    p->Zp = (Z + 127) / 128 * 128;       // M tiles of 128
     p->delta = opts->delta;
     p->gamma_pow = opts->gamma_pow;
     p->omega = opts->omega;
@@ -279,6 +292,22 @@ acom_status acom_plan_create(const acom_crystal* crystal, const acom_za_grid* gr
     }
     launch_plan_fnorm_max(p, p->pfmax, st);
     ACOM_CK(cudaGetLastError());
+    if (p->precision == ACOM_PREC_BF16) {
+        const size_t n = (size_t)p->F * p->Zp * p->Spad;
+        ACOM_CK(cudaMalloc(&p->Pb_r, n * 2));
+        ACOM_CK(cudaMalloc(&p->Pb_i, n * 2));
+        p->bytes += 4 * n;
+        launch_plan_to_bf16(p->Pr, p->Zp, p->F, p->Spad, p->Pb_r, st);
+        launch_plan_to_bf16(p->Pi, p->Zp, p->F, p->Spad, p->Pb_i, st);
+        ACOM_CK(cudaGetLastError());
+        s = make_bf16_map(p->map_pr, p->Pb_r, (uint64_t)p->F * p->Zp, (uint64_t)p->Spad);
+        if (s == ACOM_OK)
+            s = make_bf16_map(p->map_pi, p->Pb_i, (uint64_t)p->F * p->Zp, (uint64_t)p->Spad);
+        if (s != ACOM_OK) {
+            destroy_plan(p);
+            return s;
+        }
+    }
     ACOM_CK(cudaStreamSynchronize(st));
     prof_resolve();
     *out = p;
@@ -369,7 +398,7 @@ acom_status acom_polar_spectra(acom_plan p, const acom_peaks_csr* peaks, float* 
     RasterGeom geo{p->S, p->Spad, p->N, p->F, (float)p->dq, (float)p->delta, (float)p->gamma_pow, 0};
     for (int64_t c0 = 0; c0 < B; c0 += chunk) {
         const int nb = (int)std::min<int64_t>(chunk, B - c0);
-        PatternSource src{peaks->row_ptr + c0, peaks->qx, peaks->qy, peaks->I, nb,
+        PatternSource src{nullptr, 0, peaks->row_ptr + c0, peaks->qx, peaks->qy, peaks->I, nb,
                           (float)p->gamma_pow, (float)p->omega};
         launch_raster_patterns(geo, src, p->ws.Xr, p->ws.Xi, p->ws.xnorm2, nullptr, p->err, st);
         launch_spectra_export(p->ws.Xr, p->ws.Xi, nb, p->F, p->Spad, p->S,
@@ -388,6 +417,15 @@ acom_status acom_polar_spectra(acom_plan p, const acom_peaks_csr* peaks, float* 
 // ||P^_f|| ||X^_f|| (dot products of 2S terms, complex combination, sqrt).
 static float kappa_fp32(const acom_plan_s* p) {
     return (float)((3.0 * (p->Spad + 2) + 2.0 * p->F) * std::ldexp(1.0, -24));
+}
+
+// BF16 operands: each product carries at most 2^-7 relative rounding, and
+// |Pr|+|Pi| <= sqrt(2)|P^| (same for X^) gives 2^-6 ||P^_f|| ||X^_f|| for the
+// complex spectrum; the tensor-core FP32 accumulation is charged 8x the FP32
+// dot-product term.
+static float kappa_bf16(const acom_plan_s* p) {
+    return (float)(std::ldexp(1.0, -6) +
+                   (3.0 * (p->Spad + 2) + 2.0 * p->F) * std::ldexp(1.0, -21));
 }
 
 acom_status acom_match(acom_plan p, const acom_peaks_csr* peaks, const acom_match_opts* opts,
@@ -419,8 +457,9 @@ acom_status acom_match(acom_plan p, const acom_peaks_csr* peaks, const acom_matc
     const int wchunk = p->ws.chunk;
     for (int64_t c0 = 0; c0 < B; c0 += chunk) {
         const int nb = (int)std::min<int64_t>(chunk, B - c0);
-        PatternSource src{peaks->row_ptr + c0, peaks->qx, peaks->qy, peaks->I, nb,
-                          (float)p->gamma_pow, (float)p->omega};
+        const bool tc = !exhaustive && p->precision == ACOM_PREC_BF16;
+        PatternSource src{tc ? p->ws.XB : nullptr, p->ws.PTs, peaks->row_ptr + c0, peaks->qx,
+                          peaks->qy, peaks->I, nb, (float)p->gamma_pow, (float)p->omega};
         launch_raster_patterns(geo, src, p->ws.Xr, p->ws.Xi, p->ws.xnorm2, p->ws.xfn, p->err, st);
         if (exhaustive) {
             cudaMemsetAsync(p->ws.best, 0, sizeof(unsigned long long) * nb, st);
@@ -432,10 +471,13 @@ acom_status acom_match(acom_plan p, const acom_peaks_csr* peaks, const acom_matc
                 cudaMemcpyAsync(out->za_scores + c0 * (int64_t)p->Z, p->ws.za_scores,
                                 sizeof(float) * (size_t)nb * p->Z, cudaMemcpyDeviceToDevice, st);
         } else {
-            launch_contract_bound_fp32(p, p->ws.Xr, p->ws.Xi, nb, p->ws.U, st);
+            if (tc)
+                launch_contract_bound_tc(p, p->ws.map_x, p->ws.PTs, nb, p->ws.U, st);
+            else
+                launch_contract_bound_fp32(p, p->ws.Xr, p->ws.Xi, nb, p->ws.U, st);
             launch_select_exact(p, p->ws.Xr, p->ws.Xi, p->ws.U, p->ws.xfn, p->pfmax,
-                                p->ws.xnorm2, nb, kappa_fp32(p), refine, *out, c0, p->ws.n_eval,
-                                st);
+                                p->ws.xnorm2, nb, tc ? kappa_bf16(p) : kappa_fp32(p), refine,
+                                *out, c0, p->ws.n_eval, st);
         }
     }
     cudaError_t e = cudaGetLastError();
@@ -445,6 +487,39 @@ acom_status acom_match(acom_plan p, const acom_peaks_csr* peaks, const acom_matc
     s = read_error_word(p, st);
     p->last_evaluated = exhaustive ? (int64_t)B * p->Z : nev;
     return s;
+}
+
+acom_status acom_bounds(acom_plan p, const acom_peaks_csr* peaks, float* dst, void* cuda_stream) {
+    g_last_error.clear();
+    if (!p || !dst) return set_error(ACOM_ERR_INVALID_ARG, "null argument");
+    acom_status s = check_peaks(peaks);
+    if (s != ACOM_OK) return s;
+    const int64_t B = peaks->n_patterns;
+    if (B == 0) return ACOM_OK;
+    const int chunk = (int)std::min<int64_t>(B, 8192);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    s = ensure_workspace(p, chunk, false);
+    if (s != ACOM_OK) return s;
+    cudaMemsetAsync(p->err, 0, sizeof(int), st);
+    prof_begin(kKMisc, st);
+    k_check_row0<<<1, 1, 0, st>>>(peaks->row_ptr, p->err);
+    prof_end(kKMisc, st);
+    RasterGeom geo{p->S, p->Spad, p->N, p->F, (float)p->dq, (float)p->delta, (float)p->gamma_pow, 0};
+    const bool tc = p->precision == ACOM_PREC_BF16;
+    for (int64_t c0 = 0; c0 < B; c0 += chunk) {
+        const int nb = (int)std::min<int64_t>(chunk, B - c0);
+        PatternSource src{tc ? p->ws.XB : nullptr, p->ws.PTs, peaks->row_ptr + c0, peaks->qx,
+                          peaks->qy, peaks->I, nb, (float)p->gamma_pow, (float)p->omega};
+        launch_raster_patterns(geo, src, p->ws.Xr, p->ws.Xi, p->ws.xnorm2, p->ws.xfn, p->err, st);
+        float* U = dst + c0 * (int64_t)p->Z;
+        if (tc)
+            launch_contract_bound_tc(p, p->ws.map_x, p->ws.PTs, nb, U, st);
+        else
+            launch_contract_bound_fp32(p, p->ws.Xr, p->ws.Xi, nb, U, st);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "bounds launch");
+    return read_error_word(p, st);
 }
 
 }  // extern "C"

@@ -1,0 +1,479 @@
+// Tensor-core (tcgen05) contraction over shells with the spectral-bound
+// epilogue (section "Correlation Pattern Matching"; see match_prune.cu for the
+// bound).
+//
+// Per frequency f the plan spectrum (zone axes x shells, BF16) meets the
+// pattern spectra (shells x patterns, BF16) on the 5th-generation tensor cores:
+//   D1 = Pr_f [Xr_f ; Xi_f]^T   -> columns (A = Pr.Xr | C = Pr.Xi)
+//   D2 = Pi_f [Xr_f ; Xi_f]^T   -> columns (D = Pi.Xr | B = Pi.Xi)
+// with FP32 accumulation in tensor memory.  Both MMAs put a zone axis in the
+// same TMEM lane, so one epilogue thread owns all four products of its pairs
+// and accumulates w_f |(A+B) + i(C-D)| and w_f |(A-B) - i(C+D)| over f.  The
+// spectra never leave the chip; only U = max(U_dir, U_mir)/N is written.
+//
+// CTA: one TMA producer warp, one MMA-issuing warp, eight epilogue warps;
+// persistent over (128-axis x 64-pattern) tiles; operands stream through a
+// 6-stage shared-memory ring (K tiles of 32 BF16 = 64-byte rows, 64-byte
+// swizzle); accumulators are double-buffered over f in 512 TMEM columns.
+// Every mbarrier wait is bounded: a timeout sets the device error word, stops
+// all roles, drains copies and MMAs in flight, frees TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+#include <math_constants.h>
+
+#include "acom_internal.cuh"
+
+namespace acom {
+namespace tc {
+
+constexpr int kM = 128;               // zone axes per tile (MMA M)
+constexpr int kNP = 64;               // patterns per tile (MMA N = 128 rows: re, im)
+constexpr int kKT = 32;               // BF16 per K tile row (64 bytes)
+constexpr int kStages = 6;
+constexpr int kTileBytes = 128 * kKT * 2;      // 8 KB
+constexpr int kStageBytes = 3 * kTileBytes;    // Pr, Pi, X
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = (2 + kEpiWarps) * 32;
+constexpr uint32_t kTmemCols = 512;
+constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
+
+// instruction descriptor: D f32, A bf16, B bf16, both K-major, N = 128, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) |
+                            ((128u >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait; false on timeout (recorded) or when another role aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          int* err) {
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (;;) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (clock64() - t0 > kWaitCycles) {
+            atomicOr(err, kErrTimeout);
+            *abort_flag = 1;
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups 512 B apart
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;               // leading byte offset (unused with swizzle)
+    d |= (uint64_t)(512 >> 4) << 32;      // stride byte offset
+    d |= (uint64_t)1 << 46;               // descriptor version
+    d |= (uint64_t)4 << 61;               // 64-byte swizzle
+    return d;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+        "}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+#define ACOM_TMEM_LD8(taddr, r)                                                             \
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"   \
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),  \
+                   "=r"(r[6]), "=r"(r[7])                                                   \
+                 : "r"(taddr))
+
+// wait for this thread's TMEM loads; the registers are tied to the wait so no
+// use can be scheduled before it
+#define ACOM_TMEM_WAIT32(a, c, d, b)                                                       \
+    asm volatile("tcgen05.wait::ld.sync.aligned;"                                          \
+                 : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), \
+                   "+r"(a[6]), "+r"(a[7]), "+r"(c[0]), "+r"(c[1]), "+r"(c[2]), "+r"(c[3]), \
+                   "+r"(c[4]), "+r"(c[5]), "+r"(c[6]), "+r"(c[7]), "+r"(d[0]), "+r"(d[1]), \
+                   "+r"(d[2]), "+r"(d[3]), "+r"(d[4]), "+r"(d[5]), "+r"(d[6]), "+r"(d[7]), \
+                   "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]), "+r"(b[4]), "+r"(b[5]), \
+                   "+r"(b[6]), "+r"(b[7])                                                  \
+                 :                                                                         \
+                 : "memory")
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+struct TcArgs {
+    int F, N, Z, nb, ZT, PT, KT;   // frequencies, bins, axes, patterns, axis tiles, pattern tiles, K tiles
+    int PTs;                       // pattern tiles per frequency in the pattern map (row stride)
+    int Zrows;                     // rows per frequency in the plan map (ZT * 128)
+    float* U;                      // [nb][Z]
+    int* err;
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
+                    const __grid_constant__ CUtensorMap map_pi,
+                    const __grid_constant__ CUtensorMap map_x, TcArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte alignment of the operand ring
+    unsigned char* base = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char* ring = base;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(ring + kStages * kStageBytes);
+    uint64_t* full = bars;                      // [kStages]
+    uint64_t* empty = bars + kStages;           // [kStages]
+    uint64_t* tfull = bars + 2 * kStages;       // [2]
+    uint64_t* tempty = tfull + 2;               // [2]
+    uint64_t* drain = tempty + 2;               // [1]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(smem_u32(full + s), 1);
+            mbar_init(smem_u32(empty + s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(tfull + b), 1);
+            mbar_init(smem_u32(tempty + b), kEpiWarps);
+        }
+        mbar_init(smem_u32(drain), 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_pr)));
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_pi)));
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_x)));
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int n_tiles = a.ZT * a.PT;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t issued_mask = 0, last_par = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+                const int zt = t % a.ZT, pt = t / a.ZT;
+                for (int f = 0; f < a.F && ok; ++f) {
+                    const int prow = f * a.Zrows + zt * kM;
+                    const int xrow = (f * a.PTs + pt) * 128;
+                    for (int kt = 0; kt < a.KT; ++kt) {
+                        if (!mbar_wait(smem_u32(empty + stage), phase ^ 1u, abort_flag, a.err)) {
+                            ok = false;
+                            break;
+                        }
+                        const uint32_t fb = smem_u32(full + stage);
+                        mbar_expect_tx(fb, kStageBytes);
+                        unsigned char* sbuf = ring + stage * kStageBytes;
+                        tma_load_2d(smem_u32(sbuf), &map_pr, kt * kKT, prow, fb);
+                        tma_load_2d(smem_u32(sbuf + kTileBytes), &map_pi, kt * kKT, prow, fb);
+                        tma_load_2d(smem_u32(sbuf + 2 * kTileBytes), &map_x, kt * kKT, xrow, fb);
+                        issued_mask |= 1u << stage;
+                        last_par = (last_par & ~(1u << stage)) | (phase << stage);
+                        if (++stage == kStages) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                    }
+                }
+            }
+            if (!ok) {
+                // let copies in flight land before the CTA's shared memory goes away
+                for (int s = 0; s < kStages; ++s)
+                    if (issued_mask & (1u << s)) {
+                        const uint32_t par = (last_par >> s) & 1u;
+                        const long long t0 = clock64();
+                        while (!mbar_try(smem_u32(full + s), par) && clock64() - t0 < kWaitCycles) {
+                        }
+                    }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t tph[2] = {0, 0};
+            int fcount = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+                for (int f = 0; f < a.F && ok; ++f, ++fcount) {
+                    const int buf = fcount & 1;
+                    if (!mbar_wait(smem_u32(tempty + buf), tph[buf] ^ 1u, abort_flag, a.err)) {
+                        ok = false;
+                        break;
+                    }
+                    tph[buf] ^= 1u;
+                    fence_after();
+                    const uint32_t d1 = tmem + buf * 256, d2 = d1 + 128;
+                    for (int kt = 0; kt < a.KT; ++kt) {
+                        if (!mbar_wait(smem_u32(full + stage), phase, abort_flag, a.err)) {
+                            ok = false;
+                            break;
+                        }
+                        fence_after();
+                        const uint32_t sb = smem_u32(ring + stage * kStageBytes);
+#pragma unroll
+                        for (int k16 = 0; k16 < 2; ++k16) {
+                            const uint64_t ar = sdesc(sb + k16 * 32);
+                            const uint64_t ai = sdesc(sb + kTileBytes + k16 * 32);
+                            const uint64_t bx = sdesc(sb + 2 * kTileBytes + k16 * 32);
+                            const uint32_t acc = (kt | k16) ? 1u : 0u;
+                            mma_bf16(d1, ar, bx, acc);
+                            mma_bf16(d2, ai, bx, acc);
+                        }
+                        mma_commit(smem_u32(empty + stage));       // frees the stage
+                        if (++stage == kStages) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                    }
+                    if (ok) mma_commit(smem_u32(tfull + buf));     // accumulators ready
+                }
+            }
+            // all MMAs issued by this thread complete before TMEM is released
+            mma_commit(smem_u32(drain));
+            const long long t0 = clock64();
+            while (!mbar_try(smem_u32(drain), 0) && clock64() - t0 < kWaitCycles) {
+            }
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------ epilogue
+        const int sp = warp & 3;                 // TMEM lane quarter this warp may access
+        const int half = (warp - 2) >> 2;        // patterns [32 half, 32 half + 32)
+        const float invN = 1.0f / (float)a.N;
+        float ud[32], um[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) ud[j] = um[j] = 0.f;
+        uint32_t tph[2] = {0, 0};
+        int fcount = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+            const int zt = t % a.ZT, pt = t / a.ZT;
+            for (int f = 0; f < a.F; ++f, ++fcount) {
+                const int buf = fcount & 1;
+                if (!mbar_wait(smem_u32(tfull + buf), tph[buf], abort_flag, a.err)) {
+                    ok = false;
+                    break;
+                }
+                tph[buf] ^= 1u;
+                fence_after();
+                const float w = (f == 0 || 2 * f == a.N) ? 1.f : 2.f;
+                const uint32_t tb = tmem + ((uint32_t)(sp * 32) << 16) + buf * 256 + half * 32;
+#pragma unroll
+                for (int piece = 0; piece < 4; ++piece) {
+                    uint32_t A[8], Cc[8], D[8], B[8];
+                    ACOM_TMEM_LD8(tb + piece * 8, A);
+                    ACOM_TMEM_LD8(tb + 64 + piece * 8, Cc);
+                    ACOM_TMEM_LD8(tb + 128 + piece * 8, D);
+                    ACOM_TMEM_LD8(tb + 192 + piece * 8, B);
+                    ACOM_TMEM_WAIT32(A, Cc, D, B);
+                    if (piece == 3) {
+                        fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(smem_u32(tempty + buf));
+                    }
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float fa = __uint_as_float(A[j]), fc = __uint_as_float(Cc[j]);
+                        const float fd = __uint_as_float(D[j]), fb = __uint_as_float(B[j]);
+                        const float dre = fa + fb, dim = fc - fd;
+                        const float mre = fa - fb, mim = fc + fd;
+                        ud[piece * 8 + j] =
+                            fmaf(w, sqrt_approx(fmaf(dre, dre, dim * dim)), ud[piece * 8 + j]);
+                        um[piece * 8 + j] =
+                            fmaf(w, sqrt_approx(fmaf(mre, mre, mim * mim)), um[piece * 8 + j]);
+                    }
+                }
+            }
+            if (!ok) break;
+            const int z = zt * kM + sp * 32 + lane;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int b = pt * kNP + half * 32 + j;
+                if (b < a.nb && z < a.Z) a.U[(int64_t)b * a.Z + z] = fmaxf(ud[j], um[j]) * invN;
+                ud[j] = um[j] = 0.f;
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols)
+                     : "memory");
+    }
+}
+
+size_t tc_smem_bytes() {
+    return 1024 + (size_t)kStages * kStageBytes + 8 * (2 * kStages + 5) + 16;
+}
+
+}  // namespace tc
+
+// ---------------------------------------------------------------------------
+// host side: tensor maps and launch
+// ---------------------------------------------------------------------------
+
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+static bool get_encoder() {
+    if (g_encode) return true;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+        return false;
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    return true;
+}
+
+// 2-D BF16 map: rows x cols (cols contiguous), boxes of 32 cols x 128 rows,
+// 64-byte swizzle.
+acom_status make_bf16_map(void* map_storage, const void* base, uint64_t rows, uint64_t cols) {
+    if (!get_encoder()) return set_error(ACOM_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    if ((cols * 2) % 16 != 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0)
+        return set_error(ACOM_ERR_INVALID_ARG, "tensor map: stride or base not 16-byte aligned");
+    CUtensorMap* m = reinterpret_cast<CUtensorMap*>(map_storage);
+    const cuuint64_t dims[2] = {cols, rows};
+    const cuuint64_t strides[1] = {cols * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)tc::kKT, 128};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
+                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(ACOM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    return ACOM_OK;
+}
+
+size_t tensor_map_bytes() { return sizeof(CUtensorMap); }
+
+void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_stride, int nb,
+                              float* U, cudaStream_t st) {
+    tc::TcArgs a;
+    a.F = p->F;
+    a.N = p->N;
+    a.Z = p->Z;
+    a.nb = nb;
+    a.ZT = p->Zp / tc::kM;
+    a.PT = (nb + tc::kNP - 1) / tc::kNP;
+    a.PTs = pt_stride;
+    a.KT = p->Spad / tc::kKT;
+    a.Zrows = p->Zp;
+    a.U = U;
+    a.err = p->err;
+    const size_t smem = tc::tc_smem_bytes();
+    cudaFuncSetAttribute(tc::k_contract_bound_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int n_tiles = a.ZT * a.PT;
+    const int grid = n_tiles < nsm ? n_tiles : nsm;
+    if (grid <= 0) return;
+    prof_begin(kKContractBf16, st);
+    tc::k_contract_bound_tc<<<grid, tc::kThreads, smem, st>>>(
+        *reinterpret_cast<const CUtensorMap*>(p->map_pr),
+        *reinterpret_cast<const CUtensorMap*>(p->map_pi),
+        *reinterpret_cast<const CUtensorMap*>(map_x), a);
+    prof_end(kKContractBf16, st);
+}
+
+// FP32 [Zp][F][Spad] planar -> BF16 [F][Zp][Spad] (frequency-major tiles)
+__global__ void k_plan_to_bf16(const float* __restrict__ src, int Zp, int F, int Spad,
+                               __nv_bfloat16* __restrict__ dst) {
+    const int64_t total = (int64_t)Zp * F * Spad;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int s = (int)(i % Spad);
+        const int64_t t = i / Spad;
+        const int z = (int)(t % Zp);
+        const int f = (int)(t / Zp);
+        dst[i] = __float2bfloat16_rn(src[((int64_t)z * F + f) * Spad + s]);
+    }
+}
+
+void launch_plan_to_bf16(const float* src, int Zp, int F, int Spad, void* dst, cudaStream_t st) {
+    const int64_t total = (int64_t)Zp * F * Spad;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
+    prof_begin(kKMisc, st);
+    k_plan_to_bf16<<<blocks, 256, 0, st>>>(src, Zp, F, Spad,
+                                           reinterpret_cast<__nv_bfloat16*>(dst));
+    prof_end(kKMisc, st);
+}
+
+}  // namespace acom

@@ -19,6 +19,7 @@
 // X^(s, f) = sum_j X(s, j) exp(-2 pi i f j / N), f = 0..N/2, with a shared
 // twiddle table; eight shells are staged and written as 32-byte runs of the
 // [item][f][Spad] output.
+#include <cuda_bf16.h>
 #include <math_constants.h>
 
 #include "acom_internal.cuh"
@@ -55,6 +56,8 @@ __device__ inline int block_compact(bool keep, int* s_warp, int* total) {
 
 struct PatternLoader {
     PatternSource src;
+    __device__ void* xb_out() const { return src.xb; }
+    __device__ int xb_tiles() const { return src.PTs; }
     __device__ int load(int64_t item, Peak* sp, int* s_warp, int* err) const {
         const int64_t b0 = src.row_ptr[item];
         const int64_t b1 = src.row_ptr[item + 1];
@@ -90,6 +93,8 @@ struct PatternLoader {
 struct PlanLoader {
     PlanSource src;
     float delta;
+    __device__ void* xb_out() const { return nullptr; }
+    __device__ int xb_tiles() const { return 0; }
     __device__ int load(int64_t item, Peak* sp, int* s_warp, int* err) const {
         const double* R = src.frames + 9 * item;
         double R00 = R[0], R01 = R[1], R02 = R[2], R10 = R[3], R11 = R[4], R12 = R[5],
@@ -263,6 +268,20 @@ k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, float* __restrict__ out
                         acc = fmaf(st_re[w * F + f], st_re[w * F + f],
                                    fmaf(st_im[w * F + f], st_im[w * F + f], acc));
                     fn2[f] = acc;
+                }
+            }
+            if (ld.xb_out()) {
+                // BF16 copy in the tensor-core tile layout: rows (re, im) of 64-pattern tiles
+                const int64_t tile = item / 64, r = item % 64;
+                for (int e = threadIdx.x; e < 2 * F; e += blockDim.x) {
+                    const int f = e >> 1, c = e & 1;
+                    const float* srcv = c ? st_im : st_re;
+                    __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+                    for (int w = 0; w < 8; ++w) v[w] = __float2bfloat16_rn(srcv[w * F + f]);
+                    const int64_t row = ((int64_t)f * ld.xb_tiles() + tile) * 128 + c * 64 + r;
+                    *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(ld.xb_out()) +
+                                              row * Spad + s0) = *reinterpret_cast<uint4*>(v);
                 }
             }
             const int64_t obase = item * (int64_t)F * Spad + s0;

@@ -265,3 +265,73 @@ def test_full_size_scan_sampled(full_scan):
         assert check_argmax(mt, za[b], kk[b], mi[b]), b
         assert math.isclose(sc[b], mt.score, rel_tol=1e-4), b
     plan.close()
+
+
+# ----------------------------------------------------------------- BF16 path
+
+@pytest.mark.parametrize("name", ["au_6deg_40x72", "au_2deg_75x180"])
+def test_bf16_bounds_track_fp32(name):
+    """The tcgen05 contraction's spectral bounds agree with the FP32 CUDA-core
+    bounds to BF16 operand rounding (relative error well under 2^-6)."""
+    p32 = gpu_plan(name)
+    p16 = gpu_plan(name, precision=1)
+    scan = synth.random_patterns(1001, n_patterns=100)
+    u32 = p32.bounds(*to_dev(scan)).cpu().numpy()
+    u16 = p16.bounds(*to_dev(scan)).cpu().numpy()
+    rel = np.abs(u16 - u32) / np.maximum(np.abs(u32), 1e-30)
+    print(f"bf16 bound rel err {name}: max {rel.max():.3e} mean {rel.mean():.3e}")
+    assert np.all(np.isfinite(u16))
+    assert rel.max() < 2.0 ** -6 and rel.mean() < 2.0 ** -9
+    p32.close()
+    p16.close()
+
+
+def test_fp32_bounds_dominate_oracle_maxima(c1):
+    """U >= max over phi3 and mirror of C for every axis (the pruning bound)."""
+    scan = synth.random_patterns(1002, n_patterns=30)
+    u = c1.bounds(*to_dev(scan)).cpu().numpy()
+    oplan = oracle_plan("au_2deg_75x180")
+    for b in range(scan.n_patterns):
+        mt = O.match_pattern(oplan, *scan.pattern(b))
+        assert np.all(u[b] >= mt.za_scores - 1e-5 * abs(mt.score)), b
+
+
+@pytest.fixture(scope="module")
+def c1_bf16():
+    plan = gpu_plan("au_2deg_75x180", precision=1)
+    yield plan
+    plan.close()
+
+
+@pytest.mark.parametrize("chunk", [0, 48])
+def test_match_bf16_matches_oracle(c1_bf16, chunk):
+    """BF16 tensor-core bounds + FP32 evaluation of the survivors: the oracle's
+    winner (up to ties) and FP32-level scores."""
+    scan = synth.random_patterns(1001, n_patterns=100)
+    _match_and_compare(c1_bf16, oracle_plan("au_2deg_75x180"), scan, chunk=chunk,
+                       exhaustive=False)
+
+
+def test_full_size_bf16_equals_fp32(full_scan):
+    """The 256x256 scan, 1-degree plan: BF16 certified pruning returns the FP32
+    winners (differences only at FP32 ties, checked against the oracle)."""
+    import torch
+    p32 = gpu_plan("au_1deg_150x360")
+    p16 = gpu_plan("au_1deg_150x360", precision=1)
+    a = p32.match(*to_dev(full_scan))
+    b = p16.match(*to_dev(full_scan))
+    torch.cuda.synchronize()
+    ka = np.stack([a[k].cpu().numpy().astype(np.int64) for k in ("za_idx", "phi3_bin", "mirror")], 1)
+    kb = np.stack([b[k].cpu().numpy().astype(np.int64) for k in ("za_idx", "phi3_bin", "mirror")], 1)
+    diff = np.nonzero(np.any(ka != kb, axis=1))[0]
+    assert len(diff) <= 0.001 * len(ka), len(diff)
+    np.testing.assert_allclose(a["score"].cpu().numpy(), b["score"].cpu().numpy(), rtol=1e-5)
+    op = oracle_plan("au_1deg_150x360")
+    for i in diff[:8]:
+        mt = O.match_pattern(op, *full_scan.pattern(i))
+        assert check_argmax(mt, *ka[i]) and check_argmax(mt, *kb[i]), i
+    ev = p16.get_info()["last_evaluated"] / full_scan.n_patterns
+    print(f"bf16 axes evaluated per pattern: {ev:.2f}")
+    assert ev < 40
+    p32.close()
+    p16.close()
