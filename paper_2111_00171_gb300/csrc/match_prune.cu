@@ -159,12 +159,18 @@ constexpr int kSelThreads = 256;
 struct SelSmem {
     float* U;        // [Z] bound, replaced by the exact score once evaluated
     uint8_t* ev;     // [Z] evaluated flag
-    float* twc;      // [N]
-    float* tws;      // [N]
-    float* cd;       // [4][F] weighted spectra of the axis being evaluated
-    float* Cv;       // [2][N] its direct and mirror correlations
+    float2* tw;      // [N] (cos, sin) of 2 pi i / N
+    float2* y0;      // [N] spectrum c_dir + i c_mir, then transform ping-pong
+    float2* y1;      // [N]
+    float2* res;     // points at the buffer holding C_dir[k] + i C_mir[k]
     float* red_v;    // [32]
     int* red_i;      // [32]
+};
+
+constexpr int kMaxRadix = 12;
+struct Radix {
+    int n;                 // number of stages (0: no factorisation, direct transform)
+    int r[kMaxRadix];      // radices 4, 2, 3, 5
 };
 
 __device__ inline bool better(float v, unsigned i, float bv, unsigned bi) {
@@ -211,60 +217,112 @@ __device__ void block_argmax(float& v, unsigned& i, float* red_v, int* red_i) {
     __syncthreads();
 }
 
-// Full FP32 correlation of axis z with pattern b (direct and mirror, all N
-// bins) into sm.Cv; returns the best (value, mir * N + k).
+// Full FP32 correlation of axis z with pattern b: its spectra (direct and
+// mirror) over shells, then both inverse transforms at once as one complex
+// transform of y = c_dir + i c_mir (both correlations are real), by a
+// Stockham mixed-radix FFT (radices 4, 2, 3, 5) when N factors so, otherwise
+// directly.  sm.res receives C_dir[k] + i C_mir[k]; returns the best value
+// and mir * N + k (lowest index on ties).
 __device__ void evaluate_axis(const float* __restrict__ Pr, const float* __restrict__ Pi,
                               const float* __restrict__ Xr, const float* __restrict__ Xi,
-                              int z, int64_t b, int F, int N, int Spad, SelSmem& sm, float& best_v,
-                              unsigned& best_i) {
+                              int z, int64_t b, int F, int N, int Spad, const Radix& rad,
+                              SelSmem& sm, float& best_v, unsigned& best_i) {
     const float invN = 1.0f / (float)N;
-    for (int f = threadIdx.x; f < F; f += blockDim.x) {
-        const float4* pr = reinterpret_cast<const float4*>(Pr + ((int64_t)z * F + f) * Spad);
-        const float4* pi = reinterpret_cast<const float4*>(Pi + ((int64_t)z * F + f) * Spad);
-        const float4* xr = reinterpret_cast<const float4*>(Xr + (b * F + f) * Spad);
-        const float4* xi = reinterpret_cast<const float4*>(Xi + (b * F + f) * Spad);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nw = blockDim.x >> 5;
+    for (int f = warp; f < F; f += nw) {
+        const float* pr = Pr + ((int64_t)z * F + f) * Spad;
+        const float* pi = Pi + ((int64_t)z * F + f) * Spad;
+        const float* xr = Xr + (b * F + f) * Spad;
+        const float* xi = Xi + (b * F + f) * Spad;
         float a = 0.f, bb = 0.f, c = 0.f, d = 0.f;
-        for (int q = 0; q < Spad / 4; ++q) {
-            const float4 p1 = pr[q], p2 = pi[q], x1 = xr[q], x2 = xi[q];
-            a = fmaf(p1.x, x1.x, fmaf(p1.y, x1.y, fmaf(p1.z, x1.z, fmaf(p1.w, x1.w, a))));
-            bb = fmaf(p2.x, x2.x, fmaf(p2.y, x2.y, fmaf(p2.z, x2.z, fmaf(p2.w, x2.w, bb))));
-            c = fmaf(p1.x, x2.x, fmaf(p1.y, x2.y, fmaf(p1.z, x2.z, fmaf(p1.w, x2.w, c))));
-            d = fmaf(p2.x, x1.x, fmaf(p2.y, x1.y, fmaf(p2.z, x1.z, fmaf(p2.w, x1.w, d))));
+        for (int s = lane; s < Spad; s += 32) {
+            const float p1 = pr[s], p2 = pi[s], x1 = xr[s], x2 = xi[s];
+            a = fmaf(p1, x1, a);
+            bb = fmaf(p2, x2, bb);
+            c = fmaf(p1, x2, c);
+            d = fmaf(p2, x1, d);
         }
-        const float w = ((f == 0 || 2 * f == N) ? 1.f : 2.f) * invN;
-        sm.cd[f] = w * (a + bb);
-        sm.cd[F + f] = w * (c - d);
-        sm.cd[2 * F + f] = w * (a - bb);
-        sm.cd[3 * F + f] = -w * (c + d);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            bb += __shfl_xor_sync(0xffffffffu, bb, o);
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+            d += __shfl_xor_sync(0xffffffffu, d, o);
+        }
+        if (lane == 0) {
+            const float dre = (a + bb) * invN, dim = (c - d) * invN;      // c_dir / N
+            const float mre = (a - bb) * invN, mim = -(c + d) * invN;     // c_mir / N
+            sm.y0[f] = make_float2(dre - mim, dim + mre);
+            if (f > 0 && 2 * f < N) sm.y0[N - f] = make_float2(dre + mim, mre - dim);
+        }
     }
     __syncthreads();
-    const int K2 = N / 2 + 1;
+    float2* src = sm.y0;
+    float2* dst = sm.y1;
+    if (rad.n > 0) {
+        int Ns = 1;
+        for (int stg = 0; stg < rad.n; ++stg) {
+            const int R = rad.r[stg];
+            const int NR = N / R;
+            const int tstep = N / (Ns * R);
+            for (int j = threadIdx.x; j < NR; j += blockDim.x) {
+                const int jm = j % Ns;
+                float2 v[5];
+#pragma unroll
+                for (int r = 0; r < 5; ++r) {
+                    if (r < R) {
+                        const float2 x = src[j + r * NR];
+                        const float2 t = sm.tw[r * jm * tstep];
+                        v[r] = make_float2(x.x * t.x - x.y * t.y, x.x * t.y + x.y * t.x);
+                    }
+                }
+                const int idxD = (j / Ns) * Ns * R + jm;
+#pragma unroll
+                for (int mo = 0; mo < 5; ++mo) {
+                    if (mo < R) {
+                        float2 o = v[0];
+#pragma unroll
+                        for (int r = 1; r < 5; ++r) {
+                            if (r < R) {
+                                const float2 t = sm.tw[((r * mo) % R) * NR];
+                                o.x = fmaf(v[r].x, t.x, fmaf(-v[r].y, t.y, o.x));
+                                o.y = fmaf(v[r].x, t.y, fmaf(v[r].y, t.x, o.y));
+                            }
+                        }
+                        dst[idxD + mo * Ns] = o;
+                    }
+                }
+            }
+            __syncthreads();
+            float2* tmp = src;
+            src = dst;
+            dst = tmp;
+            Ns *= R;
+        }
+    } else {
+        for (int k = threadIdx.x; k < N; k += blockDim.x) {
+            float2 acc = make_float2(0.f, 0.f);
+            int idx = 0;
+            for (int f = 0; f < N; ++f) {
+                const float2 x = src[f], t = sm.tw[idx];
+                acc.x = fmaf(x.x, t.x, fmaf(-x.y, t.y, acc.x));
+                acc.y = fmaf(x.x, t.y, fmaf(x.y, t.x, acc.y));
+                idx += k;
+                if (idx >= N) idx -= N;
+            }
+            dst[k] = acc;
+        }
+        __syncthreads();
+        src = dst;
+    }
+    sm.res = src;
     float bv = -CUDART_INF_F;
     unsigned bi = 0xffffffffu;
-    for (int k = threadIdx.x; k < K2; k += blockDim.x) {
-        float ud = 0.f, vd = 0.f, um = 0.f, vm = 0.f;
-        int idx = 0;
-        for (int f = 0; f < F; ++f) {
-            const float cs = sm.twc[idx], sn = sm.tws[idx];
-            ud = fmaf(sm.cd[f], cs, ud);
-            vd = fmaf(sm.cd[F + f], sn, vd);
-            um = fmaf(sm.cd[2 * F + f], cs, um);
-            vm = fmaf(sm.cd[3 * F + f], sn, vm);
-            idx += k;
-            if (idx >= N) idx -= N;
-        }
-        const float c0 = ud - vd, m0 = um - vm;
-        sm.Cv[k] = c0;
-        sm.Cv[N + k] = m0;
-        if (better(c0, (unsigned)k, bv, bi)) { bv = c0; bi = (unsigned)k; }
-        if (better(m0, (unsigned)(N + k), bv, bi)) { bv = m0; bi = (unsigned)(N + k); }
-        if (k > 0 && 2 * k < N) {
-            const float c1 = ud + vd, m1 = um + vm;
-            sm.Cv[N - k] = c1;
-            sm.Cv[2 * N - k] = m1;
-            if (better(c1, (unsigned)(N - k), bv, bi)) { bv = c1; bi = (unsigned)(N - k); }
-            if (better(m1, (unsigned)(2 * N - k), bv, bi)) { bv = m1; bi = (unsigned)(2 * N - k); }
-        }
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const float2 y = src[k];
+        if (better(y.x, (unsigned)k, bv, bi)) { bv = y.x; bi = (unsigned)k; }
+        if (better(y.y, (unsigned)(N + k), bv, bi)) { bv = y.y; bi = (unsigned)(N + k); }
     }
     block_argmax(bv, bi, sm.red_v, sm.red_i);
     best_v = bv;
@@ -289,6 +347,7 @@ struct SelectArgs {
     const int* nbr_idx;
     int Z, F, N, Spad, nb, refine;
     float kappa;                      // contraction rounding constant
+    Radix rad;                        // inverse-transform factorisation
     acom_result out;
     int64_t off;
     int* n_eval;                      // optional: total axes evaluated
@@ -298,12 +357,12 @@ __global__ void __launch_bounds__(kSelThreads) k_select_exact(SelectArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Z = a.Z, F = a.F, N = a.N;
     SelSmem sm;
-    sm.U = reinterpret_cast<float*>(smem_raw);
-    sm.twc = sm.U + Z;
-    sm.tws = sm.twc + N;
-    sm.cd = sm.tws + N;
-    sm.Cv = sm.cd + 4 * F;
-    sm.red_v = sm.Cv + 2 * N;
+    sm.tw = reinterpret_cast<float2*>(smem_raw);
+    sm.y0 = sm.tw + N;
+    sm.y1 = sm.y0 + N;
+    sm.res = sm.y0;
+    sm.U = reinterpret_cast<float*>(sm.y1 + N);
+    sm.red_v = sm.U + Z;
     sm.red_i = reinterpret_cast<int*>(sm.red_v + 32);
     sm.ev = reinterpret_cast<uint8_t*>(sm.red_i + 32);
     __shared__ float s_best3[3];
@@ -318,8 +377,7 @@ __global__ void __launch_bounds__(kSelThreads) k_select_exact(SelectArgs a) {
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         double s, c;
         sincospi(2.0 * (double)i / (double)N, &s, &c);
-        sm.twc[i] = (float)c;
-        sm.tws[i] = (float)s;
+        sm.tw[i] = make_float2((float)c, (float)s);
     }
     // E_b: rounding margin valid for every axis
     float e = 0.f;
@@ -358,7 +416,7 @@ __global__ void __launch_bounds__(kSelThreads) k_select_exact(SelectArgs a) {
         const int z = (int)zi;
         float sv;
         unsigned si;
-        evaluate_axis(a.Pr, a.Pi, a.Xr, a.Xi, z, b, F, N, a.Spad, sm, sv, si);
+        evaluate_axis(a.Pr, a.Pi, a.Xr, a.Xi, z, b, F, N, a.Spad, a.rad, sm, sv, si);
         ++evals;
         const unsigned gidx = (unsigned)z * 2u * (unsigned)N + si;
         if (better(sv, gidx, T, Tkey_idx)) {
@@ -368,10 +426,11 @@ __global__ void __launch_bounds__(kSelThreads) k_select_exact(SelectArgs a) {
             bm = (int)(si / (unsigned)N);
             bk = (int)(si - (unsigned)bm * N);
             if (threadIdx.x == 0) {
-                const float* Cz = sm.Cv + bm * N;
-                s_best3[0] = Cz[(bk + N - 1) % N];
-                s_best3[1] = Cz[bk];
-                s_best3[2] = Cz[(bk + 1) % N];
+                const float2* y = sm.res;
+                const float2 ym = y[(bk + N - 1) % N], y0 = y[bk], yp = y[(bk + 1) % N];
+                s_best3[0] = bm ? ym.y : ym.x;
+                s_best3[1] = bm ? y0.y : y0.x;
+                s_best3[2] = bm ? yp.y : yp.x;
             }
         }
         if (threadIdx.x == 0) {
@@ -388,7 +447,7 @@ __global__ void __launch_bounds__(kSelThreads) k_select_exact(SelectArgs a) {
             if (sm.ev[z2] || sm.U[z2] * rel + Emax < 0.9f * T) continue;
             float sv;
             unsigned si;
-            evaluate_axis(a.Pr, a.Pi, a.Xr, a.Xi, z2, b, F, N, a.Spad, sm, sv, si);
+            evaluate_axis(a.Pr, a.Pi, a.Xr, a.Xi, z2, b, F, N, a.Spad, a.rad, sm, sv, si);
             ++evals;
             if (threadIdx.x == 0) {
                 sm.U[z2] = sv;
@@ -477,7 +536,21 @@ __global__ void __launch_bounds__(kSelThreads) k_select_exact(SelectArgs a) {
 }
 
 size_t select_smem_bytes(int Z, int N, int F) {
-    return sizeof(float) * ((size_t)Z + 2 * N + 4 * F + 2 * N + 32) + sizeof(int) * 32 + Z + 16;
+    return sizeof(float2) * 3 * (size_t)N + sizeof(float) * ((size_t)Z + 32) + sizeof(int) * 32 +
+           Z + 16;
+}
+
+static Radix factor_radices(int N) {
+    Radix r{};
+    int n = N;
+    const int cand[4] = {4, 2, 3, 5};
+    for (int c = 0; c < 4; ++c)
+        while (n % cand[c] == 0 && r.n < kMaxRadix) {
+            r.r[r.n++] = cand[c];
+            n /= cand[c];
+        }
+    if (n != 1) r.n = 0;
+    return r;
 }
 
 void launch_select_exact(const acom_plan_s* p, const float* Xr, const float* Xi, const float* U,
@@ -485,7 +558,8 @@ void launch_select_exact(const acom_plan_s* p, const float* Xr, const float* Xi,
                          float kappa, int refine, acom_result out, int64_t off, int* n_eval,
                          cudaStream_t st) {
     SelectArgs a{p->Pr, p->Pi, Xr, Xi, U, xfn, pfmax, xnorm2, p->za, p->frames, p->nbr_ptr,
-                 p->nbr_idx, p->Z, p->F, p->N, p->Spad, nb, refine, kappa, out, off, n_eval};
+                 p->nbr_idx, p->Z, p->F, p->N, p->Spad, nb, refine, kappa, factor_radices(p->N),
+                 out, off, n_eval};
     const size_t smem = select_smem_bytes(p->Z, p->N, p->F);
     cudaFuncSetAttribute(k_select_exact, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     prof_begin(kKSelect, st);

@@ -11,7 +11,7 @@
 // and accumulates w_f |(A+B) + i(C-D)| and w_f |(A-B) - i(C+D)| over f.  The
 // spectra never leave the chip; only U = max(U_dir, U_mir)/N is written.
 //
-// CTA: one TMA producer warp, one MMA-issuing warp, eight epilogue warps;
+// CTA: one TMA producer warp, one MMA-issuing warp, sixteen epilogue warps;
 // persistent over (128-axis x 64-pattern) tiles; operands stream through a
 // 6-stage shared-memory ring (K tiles of 32 BF16 = 64-byte rows, 64-byte
 // swizzle); accumulators are double-buffered over f in 512 TMEM columns.
@@ -33,7 +33,7 @@ constexpr int kKT = 32;               // BF16 per K tile row (64 bytes)
 constexpr int kStages = 6;
 constexpr int kTileBytes = 128 * kKT * 2;      // 8 KB
 constexpr int kStageBytes = 3 * kTileBytes;    // Pr, Pi, X
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 16;
 constexpr int kThreads = (2 + kEpiWarps) * 32;
 constexpr uint32_t kTmemCols = 512;
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
@@ -152,10 +152,13 @@ __device__ __forceinline__ void fence_after() {
                  :                                                                         \
                  : "memory")
 
-__device__ __forceinline__ float sqrt_approx(float x) {
-    float y;
-    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
+// |c| from |c|^2 with one MUFU operation: q rsqrt(q), q = |c|^2 + 1e-30 (the
+// offset keeps q > 0 and only raises the bound by < 1e-15)
+__device__ __forceinline__ float mag_from_sq(float x) {
+    const float q = x + 1e-30f;
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(q));
+    return q * r;
 }
 
 struct TcArgs {
@@ -311,11 +314,11 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
     } else {
         // ------------------------------------------------ epilogue
         const int sp = warp & 3;                 // TMEM lane quarter this warp may access
-        const int half = (warp - 2) >> 2;        // patterns [32 half, 32 half + 32)
+        const int qtr = (warp - 2) >> 2;         // patterns [16 qtr, 16 qtr + 16)
         const float invN = 1.0f / (float)a.N;
-        float ud[32], um[32];
+        float ud[16], um[16];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) ud[j] = um[j] = 0.f;
+        for (int j = 0; j < 16; ++j) ud[j] = um[j] = 0.f;
         uint32_t tph[2] = {0, 0};
         int fcount = 0;
         bool ok = true;
@@ -330,16 +333,16 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
                 tph[buf] ^= 1u;
                 fence_after();
                 const float w = (f == 0 || 2 * f == a.N) ? 1.f : 2.f;
-                const uint32_t tb = tmem + ((uint32_t)(sp * 32) << 16) + buf * 256 + half * 32;
+                const uint32_t tb = tmem + ((uint32_t)(sp * 32) << 16) + buf * 256 + qtr * 16;
 #pragma unroll
-                for (int piece = 0; piece < 4; ++piece) {
+                for (int piece = 0; piece < 2; ++piece) {
                     uint32_t A[8], Cc[8], D[8], B[8];
                     ACOM_TMEM_LD8(tb + piece * 8, A);
                     ACOM_TMEM_LD8(tb + 64 + piece * 8, Cc);
                     ACOM_TMEM_LD8(tb + 128 + piece * 8, D);
                     ACOM_TMEM_LD8(tb + 192 + piece * 8, B);
                     ACOM_TMEM_WAIT32(A, Cc, D, B);
-                    if (piece == 3) {
+                    if (piece == 1) {
                         fence_before();
                         __syncwarp();
                         if (lane == 0) mbar_arrive(smem_u32(tempty + buf));
@@ -351,17 +354,17 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
                         const float dre = fa + fb, dim = fc - fd;
                         const float mre = fa - fb, mim = fc + fd;
                         ud[piece * 8 + j] =
-                            fmaf(w, sqrt_approx(fmaf(dre, dre, dim * dim)), ud[piece * 8 + j]);
+                            fmaf(w, mag_from_sq(fmaf(dre, dre, dim * dim)), ud[piece * 8 + j]);
                         um[piece * 8 + j] =
-                            fmaf(w, sqrt_approx(fmaf(mre, mre, mim * mim)), um[piece * 8 + j]);
+                            fmaf(w, mag_from_sq(fmaf(mre, mre, mim * mim)), um[piece * 8 + j]);
                     }
                 }
             }
             if (!ok) break;
             const int z = zt * kM + sp * 32 + lane;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int b = pt * kNP + half * 32 + j;
+            for (int j = 0; j < 16; ++j) {
+                const int b = pt * kNP + qtr * 16 + j;
                 if (b < a.nb && z < a.Z) a.U[(int64_t)b * a.Z + z] = fmaxf(ud[j], um[j]) * invN;
                 ud[j] = um[j] = 0.f;
             }

@@ -149,7 +149,7 @@ size_t raster_smem_bytes(int N, int F) {
     return b;
 }
 
-template <class Loader>
+template <class Loader, int NF2>
 __global__ void __launch_bounds__(kRasterThreads)
 k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, float* __restrict__ out_re,
              float* __restrict__ out_im, float* __restrict__ sumsq, float* __restrict__ fnorm,
@@ -158,9 +158,8 @@ k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, float* __restrict__ out
     const int N = geo.N, F = geo.F, S = geo.S, Spad = geo.Spad;
     constexpr int W = kRasterThreads / 32;
     Peak* sp = reinterpret_cast<Peak*>(smem);
-    float* twc = reinterpret_cast<float*>(sp + kMaxPeaks);
-    float* tws = twc + N;
-    float* rows = tws + N;
+    float2* tw = reinterpret_cast<float2*>(sp + kMaxPeaks);    // (cos, sin) of 2 pi i / N
+    float* rows = reinterpret_cast<float*>(tw + N);
     int* tapj = reinterpret_cast<int*>(rows + W * N);
     float* tapv = reinterpret_cast<float*>(tapj + W * N);
     float* st_re = tapv + W * N;
@@ -173,11 +172,18 @@ k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, float* __restrict__ out
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         double c, s;
         sincospi(2.0 * (double)i / (double)N, &s, &c);
-        twc[i] = (float)c;
-        tws[i] = (float)s;
+        tw[i] = make_float2((float)c, (float)s);
     }
     __syncthreads();
 
+    // z_f = exp(-2 pi i f / N) for this lane's frequencies f = lane + 32 g
+    float zr[NF2], zi[NF2];
+#pragma unroll
+    for (int g = 0; g < NF2; ++g) {
+        const int f = (lane + 32 * g) % N;
+        zr[g] = tw[f].x;
+        zi[g] = -tw[f].y;
+    }
     const float delta = geo.delta, d2 = delta * delta, inv_delta = 1.0f / delta;
     const float two_pi = 2.0f * CUDART_PI_F;
     const float dphi = two_pi / (float)N;
@@ -195,7 +201,7 @@ k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, float* __restrict__ out
             const int s = s0 + warp;
             for (int j = lane; j < N; j += 32) row[j] = 0.f;
             __syncwarp();
-            int ntap = 0;
+            int ntap = 0, nrun = 0;
             if (s < S) {
                 const float qs = (float)(s + 1) * geo.dq;
                 const float qs2 = qs * qs;
@@ -227,38 +233,73 @@ k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, float* __restrict__ out
                 }
                 const float rscale = geo.shell_power ? powf(qs, geo.gamma_pow) : 1.0f;
                 float sq = 0.f;
+                // non-zero bins in bin order; runs of consecutive bins are
+                // recorded as (first tap << 16 | first bin)
                 for (int base = 0; base < N; base += 32) {
                     int j = base + lane;
                     float v = (j < N) ? row[j] * rscale : 0.f;
                     sq += v * v;
+                    const bool start = v != 0.f && (j == 0 || row[j - 1] == 0.f);
                     unsigned msk = __ballot_sync(0xffffffffu, v != 0.f);
-                    if (v != 0.f) {
-                        int pos = ntap + __popc(msk & ((1u << lane) - 1u));
-                        my_tj[pos] = j;
-                        my_tv[pos] = v;
-                    }
+                    unsigned smk = __ballot_sync(0xffffffffu, start);
+                    const unsigned lt = (1u << lane) - 1u;
+                    const int pos = ntap + __popc(msk & lt);
+                    if (v != 0.f) my_tv[pos] = v;
+                    if (start) my_tj[nrun + __popc(smk & lt)] = (pos << 16) | j;
                     ntap += __popc(msk);
+                    nrun += __popc(smk);
                 }
+                if (lane == 0) my_tj[nrun] = ntap << 16;       // sentinel
                 for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
                 warp_sq += sq;
             }
             __syncwarp();
-            // direct transform of the compacted taps
-            for (int f = lane; f < F; f += 32) {
-                float re = 0.f, im = 0.f;
-                for (int t = 0; t < ntap; ++t) {
-                    const int j = my_tj[t];
-                    const float v = my_tv[t];
-                    int prod = f * j;
-                    int q = __float2int_rz((float)prod * invN);
-                    int idx = prod - q * N;
-                    if (idx >= N) idx -= N;
-                    if (idx < 0) idx += N;
-                    re = fmaf(v, twc[idx], re);
-                    im = fmaf(-v, tws[idx], im);
+            // transform of the non-zero bins.  Lane l owns the frequencies
+            // f = l + 32 g.  A run of consecutive bins j0 .. j0+L-1 contributes
+            // exp(-2 pi i f j0 / N) P(z_f), P(z) = sum_m v_m z^m, z_f =
+            // exp(-2 pi i f / N), evaluated by Horner's rule (4 FMA per bin and
+            // frequency, no table access); one table read per run and frequency.
+            __syncwarp();
+            {
+                float ar[NF2], ai[NF2];
+#pragma unroll
+                for (int g = 0; g < NF2; ++g) ar[g] = ai[g] = 0.f;
+                for (int rn = 0; rn < nrun; ++rn) {
+                    const int info = my_tj[rn];
+                    const int p0 = info >> 16, j0 = info & 0xffff;
+                    const int p1 = my_tj[rn + 1] >> 16;
+                    float hr[NF2], hi[NF2];
+#pragma unroll
+                    for (int g = 0; g < NF2; ++g) hr[g] = hi[g] = 0.f;
+                    for (int p = p1 - 1; p >= p0; --p) {
+                        const float v = my_tv[p];
+#pragma unroll
+                        for (int g = 0; g < NF2; ++g) {
+                            const float t = fmaf(hr[g], zr[g], fmaf(-hi[g], zi[g], v));
+                            hi[g] = fmaf(hr[g], zi[g], hi[g] * zr[g]);
+                            hr[g] = t;
+                        }
+                    }
+#pragma unroll
+                    for (int g = 0; g < NF2; ++g) {
+                        const int prod = (lane + 32 * g) * j0;
+                        const int q = __float2int_rz((float)prod * invN);
+                        int idx = prod - q * N;
+                        if (idx >= N) idx -= N;
+                        if (idx < 0) idx += N;
+                        const float2 w = tw[idx];                // exp(+i theta): conjugate it
+                        ar[g] = fmaf(hr[g], w.x, fmaf(hi[g], w.y, ar[g]));
+                        ai[g] = fmaf(hi[g], w.x, fmaf(-hr[g], w.y, ai[g]));
+                    }
                 }
-                st_re[warp * F + f] = re;
-                st_im[warp * F + f] = im;
+#pragma unroll
+                for (int g = 0; g < NF2; ++g) {
+                    const int f = lane + 32 * g;
+                    if (f < F) {
+                        st_re[warp * F + f] = ar[g];
+                        st_im[warp * F + f] = ai[g];
+                    }
+                }
             }
             __syncthreads();
             if (fnorm) {
@@ -306,26 +347,42 @@ k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, float* __restrict__ out
     }
 }
 
-template <class Loader>
-static void launch_raster(const RasterGeom& geo, const Loader& ld, int64_t n_items,
-                          float* out_re, float* out_im, float* sumsq, float* fnorm, int* err,
-                          cudaStream_t st, int cls) {
-    if (n_items <= 0) return;
+template <class Loader, int NF2>
+static void launch_raster_nf(const RasterGeom& geo, const Loader& ld, int64_t n_items,
+                             float* out_re, float* out_im, float* sumsq, float* fnorm, int* err,
+                             cudaStream_t st, int cls) {
     size_t smem = raster_smem_bytes(geo.N, geo.F);
-    cudaFuncSetAttribute(k_raster_dft<Loader>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_raster_dft<Loader, NF2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_dft<Loader>, kRasterThreads,
-                                                  smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_dft<Loader, NF2>,
+                                                  kRasterThreads, smem);
     int64_t grid = (int64_t)nsm * (per_sm > 0 ? per_sm : 1);
     if (grid > n_items) grid = n_items;
     prof_begin(cls, st);
-    k_raster_dft<Loader><<<(unsigned)grid, kRasterThreads, smem, st>>>(geo, ld, n_items, out_re,
-                                                                        out_im, sumsq, fnorm, err);
+    k_raster_dft<Loader, NF2><<<(unsigned)grid, kRasterThreads, smem, st>>>(
+        geo, ld, n_items, out_re, out_im, sumsq, fnorm, err);
     prof_end(cls, st);
+}
+
+// frequencies per lane: the smallest compiled count covering F = N/2 + 1
+template <class Loader>
+static void launch_raster(const RasterGeom& geo, const Loader& ld, int64_t n_items,
+                          float* out_re, float* out_im, float* sumsq, float* fnorm, int* err,
+                          cudaStream_t st, int cls) {
+    if (n_items <= 0) return;
+    const int nf2 = (geo.F + 31) / 32;
+    if (nf2 <= 2)
+        launch_raster_nf<Loader, 2>(geo, ld, n_items, out_re, out_im, sumsq, fnorm, err, st, cls);
+    else if (nf2 <= 3)
+        launch_raster_nf<Loader, 3>(geo, ld, n_items, out_re, out_im, sumsq, fnorm, err, st, cls);
+    else if (nf2 <= 6)
+        launch_raster_nf<Loader, 6>(geo, ld, n_items, out_re, out_im, sumsq, fnorm, err, st, cls);
+    else
+        launch_raster_nf<Loader, 12>(geo, ld, n_items, out_re, out_im, sumsq, fnorm, err, st, cls);
 }
 
 void launch_raster_plan(const RasterGeom& geo, const PlanSource& src, int Z, float* out_re,
