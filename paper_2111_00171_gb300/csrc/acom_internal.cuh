@@ -33,6 +33,17 @@ struct RasterGeom {
     int shell_power;   // 1: multiply rows by q_s^gamma_pow (plan); 0: peaks carry q_m^gamma
 };
 
+// Outputs of the raster + transform kernel (every pointer optional but one).
+struct RasterOut {
+    float* re = nullptr;       // [item][F][Spad] (frequency-major rows of shells)
+    float* im = nullptr;
+    float* sre = nullptr;      // [item][Spad][F] (shell-major rows of frequencies)
+    float* sim = nullptr;
+    float* sumsq = nullptr;    // [item] sum of squares of the polar image
+    float* fnorm = nullptr;    // [item][F] ||X^_f|| over shells
+    int2* srange = nullptr;    // [item] first and one-past-last shell with a non-zero row
+};
+
 struct PlanSource {            // reflections rotated into each zone-axis frame
     const double* g;           // [G][3] crystal Cartesian
     const double* amp;         // [G] |F|^omega
@@ -55,8 +66,10 @@ struct PatternSource {         // one chunk of CSR patterns
 // Workspace for one chunk of patterns.
 struct Workspace {
     int chunk = 0;                 // capacity in patterns
-    float* Xr = nullptr;           // [chunk][F][Spad]
+    float* Xr = nullptr;           // [chunk][F][Spad] (FP32 contraction only)
     float* Xi = nullptr;
+    float* Xsr = nullptr;          // [chunk][Spad][F] (exact evaluation)
+    float* Xsi = nullptr;
     float* xnorm2 = nullptr;       // [chunk]
     float* Chat = nullptr;         // [4][F][chunk][Zp] (exhaustive mode only)
     float* U = nullptr;            // [chunk][Z] spectral bounds
@@ -65,6 +78,7 @@ struct Workspace {
     alignas(64) unsigned char map_x[128];   // TMA map of XB
     float* xfn = nullptr;          // [chunk][F] ||X^_bf|| over shells
     int* n_eval = nullptr;         // axes evaluated exactly in the last match
+    int2* srange = nullptr;        // [chunk] non-zero shell range of each pattern
     unsigned long long* best = nullptr;  // [chunk] packed (score, index)
     float* za_scores = nullptr;    // [chunk][Z]
     size_t bytes = 0;
@@ -82,6 +96,8 @@ struct acom_plan_s {
     // device memory
     float* Pr = nullptr;              // [Zp][F][Spad], zero rows beyond Z
     float* Pi = nullptr;
+    float* Psr = nullptr;             // [Zp][Spad][F] (exact evaluation)
+    float* Psi = nullptr;
     double* za = nullptr;             // [Z][3]
     double* frames = nullptr;         // [Z][9]
     int* nbr_ptr = nullptr;           // [Z + 1]
@@ -119,10 +135,9 @@ acom_status cuda_error(cudaError_t e, const char* what);
 acom_status build_plan_device(acom_plan_s* p, const acom_crystal* crystal, cudaStream_t st);
 // raster.cu
 void launch_raster_plan(const RasterGeom& geo, const PlanSource& src, int Z,
-                        float* out_re, float* out_im, float* sumsq, int* err, cudaStream_t st);
+                        const RasterOut& out, int* err, cudaStream_t st);
 void launch_raster_patterns(const RasterGeom& geo, const PatternSource& src,
-                            float* out_re, float* out_im, float* sumsq, float* fnorm, int* err,
-                            cudaStream_t st);
+                            const RasterOut& out, int* err, cudaStream_t st);
 void launch_scale_rows(float* re, float* im, const float* sumsq, int items, int row_elems,
                        cudaStream_t st);
 void launch_spectra_export(const float* re, const float* im, int items, int F, int Spad, int S,
@@ -142,8 +157,9 @@ acom_status make_bf16_map(void* map_storage, const void* base, uint64_t rows, ui
 void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_stride, int nb,
                               float* U, cudaStream_t st);
 void launch_plan_to_bf16(const float* src, int Zp, int F, int Spad, void* dst, cudaStream_t st);
-void launch_select_exact(const acom_plan_s* p, const float* Xr, const float* Xi, const float* U,
-                         const float* xfn, const float* pfmax, const float* xnorm2, int nb,
+void launch_select_exact(const acom_plan_s* p, const float* Xsr, const float* Xsi, const float* U,
+                         const float* xfn, const int2* srange, const float* pfmax,
+                         const float* xnorm2, int nb,
                          float kappa, int refine, acom_result out, int64_t off, int* n_eval,
                          cudaStream_t st);
 void launch_refine(const acom_plan_s* p, const float* Chat, int nb, int chunk,

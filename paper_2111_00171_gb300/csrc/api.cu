@@ -94,27 +94,36 @@ static cudaError_t dalloc(T** p, size_t n, size_t* acc) {
 static void free_workspace(Workspace& ws) {
     cudaFree(ws.Xr);
     cudaFree(ws.Xi);
+    cudaFree(ws.Xsr);
+    cudaFree(ws.Xsi);
     cudaFree(ws.xnorm2);
     cudaFree(ws.Chat);
     cudaFree(ws.U);
     cudaFree(ws.xfn);
     cudaFree(ws.n_eval);
+    cudaFree(ws.srange);
     cudaFree(ws.best);
     cudaFree(ws.za_scores);
     cudaFree(ws.XB);
     ws = Workspace{};
 }
 
-static acom_status ensure_workspace(acom_plan_s* p, int chunk, bool need_chat) {
-    if (p->ws.chunk >= chunk && (!need_chat || p->ws.Chat)) return ACOM_OK;
+// need_fmajor: the frequency-major pattern spectra (FP32 contraction, export)
+static acom_status ensure_workspace(acom_plan_s* p, int chunk, bool need_chat, bool need_fmajor) {
+    if (p->ws.chunk >= chunk && (!need_chat || p->ws.Chat) && (!need_fmajor || p->ws.Xr))
+        return ACOM_OK;
+    need_chat = need_chat || p->ws.Chat;
+    need_fmajor = need_fmajor || need_chat || p->ws.Xr;
     if (p->ws.chunk > chunk) chunk = p->ws.chunk;
     free_workspace(p->ws);
     Workspace& ws = p->ws;
     size_t acc = 0;
     const size_t spec = (size_t)chunk * p->F * p->Spad;
     cudaError_t e = cudaSuccess;
-    if ((e = dalloc(&ws.Xr, spec, &acc)) != cudaSuccess) goto fail;
-    if ((e = dalloc(&ws.Xi, spec, &acc)) != cudaSuccess) goto fail;
+    if (need_fmajor && (e = dalloc(&ws.Xr, spec, &acc)) != cudaSuccess) goto fail;
+    if (need_fmajor && (e = dalloc(&ws.Xi, spec, &acc)) != cudaSuccess) goto fail;
+    if ((e = dalloc(&ws.Xsr, spec, &acc)) != cudaSuccess) goto fail;
+    if ((e = dalloc(&ws.Xsi, spec, &acc)) != cudaSuccess) goto fail;
     if ((e = dalloc(&ws.xnorm2, (size_t)chunk, &acc)) != cudaSuccess) goto fail;
     if (need_chat &&
         (e = dalloc(&ws.Chat, (size_t)4 * p->F * chunk * p->Zp, &acc)) != cudaSuccess)
@@ -122,6 +131,7 @@ static acom_status ensure_workspace(acom_plan_s* p, int chunk, bool need_chat) {
     if ((e = dalloc(&ws.U, (size_t)chunk * p->Z, &acc)) != cudaSuccess) goto fail;
     if ((e = dalloc(&ws.xfn, (size_t)chunk * p->F, &acc)) != cudaSuccess) goto fail;
     if ((e = dalloc(&ws.n_eval, (size_t)1, &acc)) != cudaSuccess) goto fail;
+    if ((e = dalloc(&ws.srange, (size_t)chunk, &acc)) != cudaSuccess) goto fail;
     if ((e = dalloc(&ws.best, (size_t)chunk, &acc)) != cudaSuccess) goto fail;
     if ((e = dalloc(&ws.za_scores, (size_t)chunk * p->Z, &acc)) != cudaSuccess) goto fail;
     if (p->precision == ACOM_PREC_BF16) {
@@ -149,6 +159,8 @@ static void destroy_plan(acom_plan_s* p) {
     free_workspace(p->ws);
     cudaFree(p->Pr);
     cudaFree(p->Pi);
+    cudaFree(p->Psr);
+    cudaFree(p->Psi);
     cudaFree(p->za);
     cudaFree(p->frames);
     cudaFree(p->nbr_ptr);
@@ -269,6 +281,8 @@ acom_status acom_plan_create(const acom_crystal* crystal, const acom_za_grid* gr
     } while (0)
     ACOM_CK(dalloc(&p->Pr, pelems, &p->bytes));
     ACOM_CK(dalloc(&p->Pi, pelems, &p->bytes));
+    ACOM_CK(dalloc(&p->Psr, pelems, &p->bytes));
+    ACOM_CK(dalloc(&p->Psi, pelems, &p->bytes));
     ACOM_CK(dalloc(&p->za, za.size(), &p->bytes));
     ACOM_CK(dalloc(&p->frames, frames.size(), &p->bytes));
     ACOM_CK(dalloc(&p->nbr_ptr, nptr.size(), &p->bytes));
@@ -277,6 +291,8 @@ acom_status acom_plan_create(const acom_crystal* crystal, const acom_za_grid* gr
     ACOM_CK(dalloc(&p->pfmax, (size_t)p->F, &p->bytes));
     ACOM_CK(cudaMemsetAsync(p->Pr, 0, sizeof(float) * pelems, st));
     ACOM_CK(cudaMemsetAsync(p->Pi, 0, sizeof(float) * pelems, st));
+    ACOM_CK(cudaMemsetAsync(p->Psr, 0, sizeof(float) * pelems, st));
+    ACOM_CK(cudaMemsetAsync(p->Psi, 0, sizeof(float) * pelems, st));
     ACOM_CK(cudaMemsetAsync(p->err, 0, sizeof(int), st));
     ACOM_CK(cudaMemcpyAsync(p->za, za.data(), sizeof(double) * za.size(), cudaMemcpyHostToDevice, st));
     ACOM_CK(cudaMemcpyAsync(p->frames, frames.data(), sizeof(double) * frames.size(),
@@ -389,7 +405,7 @@ acom_status acom_polar_spectra(acom_plan p, const acom_peaks_csr* peaks, float* 
     if (B == 0) return ACOM_OK;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const int chunk = (int)std::min<int64_t>(B, 1024);
-    s = ensure_workspace(p, chunk, false);
+    s = ensure_workspace(p, chunk, false, true);
     if (s != ACOM_OK) return s;
     cudaMemsetAsync(p->err, 0, sizeof(int), st);
     prof_begin(kKMisc, st);
@@ -400,7 +416,11 @@ acom_status acom_polar_spectra(acom_plan p, const acom_peaks_csr* peaks, float* 
         const int nb = (int)std::min<int64_t>(chunk, B - c0);
         PatternSource src{nullptr, 0, peaks->row_ptr + c0, peaks->qx, peaks->qy, peaks->I, nb,
                           (float)p->gamma_pow, (float)p->omega};
-        launch_raster_patterns(geo, src, p->ws.Xr, p->ws.Xi, p->ws.xnorm2, nullptr, p->err, st);
+        RasterOut ro;
+        ro.re = p->ws.Xr;
+        ro.im = p->ws.Xi;
+        ro.sumsq = p->ws.xnorm2;
+        launch_raster_patterns(geo, src, ro, p->err, st);
         launch_spectra_export(p->ws.Xr, p->ws.Xi, nb, p->F, p->Spad, p->S,
                               dst + 2 * c0 * (int64_t)p->S * p->F, st);
         if (xnorm) {
@@ -446,7 +466,8 @@ acom_status acom_match(acom_plan p, const acom_peaks_csr* peaks, const acom_matc
     if (chunk > 65536) return set_error(ACOM_ERR_INVALID_ARG, "chunk must be <= 65536");
     chunk = (int)std::min<int64_t>(chunk, B);
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    s = ensure_workspace(p, chunk, exhaustive);
+    const bool fp32_contraction = exhaustive || p->precision == ACOM_PREC_FP32;
+    s = ensure_workspace(p, chunk, exhaustive, fp32_contraction);
     if (s != ACOM_OK) return s;
     cudaMemsetAsync(p->err, 0, sizeof(int), st);
     cudaMemsetAsync(p->ws.n_eval, 0, sizeof(int), st);
@@ -460,7 +481,15 @@ acom_status acom_match(acom_plan p, const acom_peaks_csr* peaks, const acom_matc
         const bool tc = !exhaustive && p->precision == ACOM_PREC_BF16;
         PatternSource src{tc ? p->ws.XB : nullptr, p->ws.PTs, peaks->row_ptr + c0, peaks->qx,
                           peaks->qy, peaks->I, nb, (float)p->gamma_pow, (float)p->omega};
-        launch_raster_patterns(geo, src, p->ws.Xr, p->ws.Xi, p->ws.xnorm2, p->ws.xfn, p->err, st);
+        RasterOut ro;
+        ro.re = fp32_contraction ? p->ws.Xr : nullptr;
+        ro.im = fp32_contraction ? p->ws.Xi : nullptr;
+        ro.sre = p->ws.Xsr;
+        ro.sim = p->ws.Xsi;
+        ro.sumsq = p->ws.xnorm2;
+        ro.fnorm = p->ws.xfn;
+        ro.srange = p->ws.srange;
+        launch_raster_patterns(geo, src, ro, p->err, st);
         if (exhaustive) {
             cudaMemsetAsync(p->ws.best, 0, sizeof(unsigned long long) * nb, st);
             launch_contract_fp32(p, p->ws.Xr, p->ws.Xi, nb, p->ws.Chat, wchunk, st);
@@ -475,7 +504,7 @@ acom_status acom_match(acom_plan p, const acom_peaks_csr* peaks, const acom_matc
                 launch_contract_bound_tc(p, p->ws.map_x, p->ws.PTs, nb, p->ws.U, st);
             else
                 launch_contract_bound_fp32(p, p->ws.Xr, p->ws.Xi, nb, p->ws.U, st);
-            launch_select_exact(p, p->ws.Xr, p->ws.Xi, p->ws.U, p->ws.xfn, p->pfmax,
+            launch_select_exact(p, p->ws.Xsr, p->ws.Xsi, p->ws.U, p->ws.xfn, p->ws.srange, p->pfmax,
                                 p->ws.xnorm2, nb, tc ? kappa_bf16(p) : kappa_fp32(p), refine,
                                 *out, c0, p->ws.n_eval, st);
         }
@@ -498,19 +527,23 @@ acom_status acom_bounds(acom_plan p, const acom_peaks_csr* peaks, float* dst, vo
     if (B == 0) return ACOM_OK;
     const int chunk = (int)std::min<int64_t>(B, 8192);
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    s = ensure_workspace(p, chunk, false);
+    const bool tc = p->precision == ACOM_PREC_BF16;
+    s = ensure_workspace(p, chunk, false, !tc);
     if (s != ACOM_OK) return s;
     cudaMemsetAsync(p->err, 0, sizeof(int), st);
     prof_begin(kKMisc, st);
     k_check_row0<<<1, 1, 0, st>>>(peaks->row_ptr, p->err);
     prof_end(kKMisc, st);
     RasterGeom geo{p->S, p->Spad, p->N, p->F, (float)p->dq, (float)p->delta, (float)p->gamma_pow, 0};
-    const bool tc = p->precision == ACOM_PREC_BF16;
     for (int64_t c0 = 0; c0 < B; c0 += chunk) {
         const int nb = (int)std::min<int64_t>(chunk, B - c0);
         PatternSource src{tc ? p->ws.XB : nullptr, p->ws.PTs, peaks->row_ptr + c0, peaks->qx,
                           peaks->qy, peaks->I, nb, (float)p->gamma_pow, (float)p->omega};
-        launch_raster_patterns(geo, src, p->ws.Xr, p->ws.Xi, p->ws.xnorm2, p->ws.xfn, p->err, st);
+        RasterOut ro;
+        ro.re = tc ? nullptr : p->ws.Xr;
+        ro.im = tc ? nullptr : p->ws.Xi;
+        ro.sumsq = p->ws.xnorm2;
+        launch_raster_patterns(geo, src, ro, p->err, st);
         float* U = dst + c0 * (int64_t)p->Z;
         if (tc)
             launch_contract_bound_tc(p, p->ws.map_x, p->ws.PTs, nb, U, st);

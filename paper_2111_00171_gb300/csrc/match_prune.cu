@@ -152,19 +152,24 @@ void launch_plan_fnorm_max(const acom_plan_s* p, float* out, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
-// Selection and exact evaluation, one CTA per pattern.
+// Selection and exact evaluation, one CTA per pattern.  Candidate axes are
+// evaluated in batches of up to kBatch per pass over the pattern's spectrum:
+// one thread per frequency runs down the shells (spectra stored shell-major,
+// so the loads of a warp are contiguous) and accumulates the four real
+// products for every candidate of the batch.
 // ---------------------------------------------------------------------------
-constexpr int kSelThreads = 256;
+constexpr int kSelThreads = 192;
+constexpr int kBatch = 8;
 
 struct SelSmem {
     float* U;        // [Z] bound, replaced by the exact score once evaluated
-    uint8_t* ev;     // [Z] evaluated flag
+    uint8_t* ev;     // [Z] 0 pending, 1 evaluated, 2 in the current batch
     float2* tw;      // [N] (cos, sin) of 2 pi i / N
-    float2* y0;      // [N] spectrum c_dir + i c_mir, then transform ping-pong
-    float2* y1;      // [N]
-    float2* res;     // points at the buffer holding C_dir[k] + i C_mir[k]
+    float2* y;       // [kBatch][N] spectra c_dir + i c_mir of the batch
+    float2* tmp;     // [N] transform ping-pong
     float* red_v;    // [32]
     int* red_i;      // [32]
+    int* cand;       // [kBatch]
 };
 
 constexpr int kMaxRadix = 12;
@@ -217,49 +222,76 @@ __device__ void block_argmax(float& v, unsigned& i, float* red_v, int* red_i) {
     __syncthreads();
 }
 
-// Full FP32 correlation of axis z with pattern b: its spectra (direct and
-// mirror) over shells, then both inverse transforms at once as one complex
-// transform of y = c_dir + i c_mir (both correlations are real), by a
-// Stockham mixed-radix FFT (radices 4, 2, 3, 5) when N factors so, otherwise
-// directly.  sm.res receives C_dir[k] + i C_mir[k]; returns the best value
-// and mir * N + k (lowest index on ties).
-__device__ void evaluate_axis(const float* __restrict__ Pr, const float* __restrict__ Pi,
-                              const float* __restrict__ Xr, const float* __restrict__ Xi,
-                              int z, int64_t b, int F, int N, int Spad, const Radix& rad,
-                              SelSmem& sm, float& best_v, unsigned& best_i) {
+// Spectra c_dir + i c_mir (both correlations are real, so one complex
+// transform carries both) of the nc candidate axes of the batch, scaled by 1/N.
+template <int KB>
+__device__ void batch_spectra(const float* __restrict__ Psr, const float* __restrict__ Psi,
+                              const float* __restrict__ Xsr, const float* __restrict__ Xsi,
+                              int64_t b, int nc, int F, int N, int s_lo, int s_hi, int Spad,
+                              SelSmem& sm) {
     const float invN = 1.0f / (float)N;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nw = blockDim.x >> 5;
-    for (int f = warp; f < F; f += nw) {
-        const float* pr = Pr + ((int64_t)z * F + f) * Spad;
-        const float* pi = Pi + ((int64_t)z * F + f) * Spad;
-        const float* xr = Xr + (b * F + f) * Spad;
-        const float* xi = Xi + (b * F + f) * Spad;
-        float a = 0.f, bb = 0.f, c = 0.f, d = 0.f;
-        for (int s = lane; s < Spad; s += 32) {
-            const float p1 = pr[s], p2 = pi[s], x1 = xr[s], x2 = xi[s];
-            a = fmaf(p1, x1, a);
-            bb = fmaf(p2, x2, bb);
-            c = fmaf(p1, x2, c);
-            d = fmaf(p2, x1, d);
+    const int pstride = Spad * F;
+    const float* xr = Xsr + b * (int64_t)pstride;
+    const float* xi = Xsi + b * (int64_t)pstride;
+    for (int f = threadIdx.x; f < F; f += blockDim.x) {
+        float A[KB], B[KB], C[KB], D[KB];
+        int off[KB];
+#pragma unroll
+        for (int c = 0; c < KB; ++c) {
+            A[c] = B[c] = C[c] = D[c] = 0.f;
+            off[c] = (c < nc ? sm.cand[c] : sm.cand[0]) * pstride + f;
+        }
+        // rows of shells outside [s_lo, s_hi) are zero in the pattern spectrum
+        int s = s_lo;
+        for (; s + 1 < s_hi; s += 2) {
+            const int o0 = s * F, o1 = o0 + F;
+            const float x1a = xr[o0 + f], x2a = xi[o0 + f], x1b = xr[o1 + f], x2b = xi[o1 + f];
+#pragma unroll
+            for (int c = 0; c < KB; ++c) {
+                if (c < nc) {
+                    const float p1a = Psr[off[c] + o0], p2a = Psi[off[c] + o0];
+                    const float p1b = Psr[off[c] + o1], p2b = Psi[off[c] + o1];
+                    A[c] = fmaf(p1a, x1a, fmaf(p1b, x1b, A[c]));
+                    B[c] = fmaf(p2a, x2a, fmaf(p2b, x2b, B[c]));
+                    C[c] = fmaf(p1a, x2a, fmaf(p1b, x2b, C[c]));
+                    D[c] = fmaf(p2a, x1a, fmaf(p2b, x1b, D[c]));
+                }
+            }
+        }
+        if (s < s_hi) {
+            const int o0 = s * F;
+            const float x1 = xr[o0 + f], x2 = xi[o0 + f];
+#pragma unroll
+            for (int c = 0; c < KB; ++c) {
+                if (c < nc) {
+                    const float p1 = Psr[off[c] + o0], p2 = Psi[off[c] + o0];
+                    A[c] = fmaf(p1, x1, A[c]);
+                    B[c] = fmaf(p2, x2, B[c]);
+                    C[c] = fmaf(p1, x2, C[c]);
+                    D[c] = fmaf(p2, x1, D[c]);
+                }
+            }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_xor_sync(0xffffffffu, a, o);
-            bb += __shfl_xor_sync(0xffffffffu, bb, o);
-            c += __shfl_xor_sync(0xffffffffu, c, o);
-            d += __shfl_xor_sync(0xffffffffu, d, o);
-        }
-        if (lane == 0) {
-            const float dre = (a + bb) * invN, dim = (c - d) * invN;      // c_dir / N
-            const float mre = (a - bb) * invN, mim = -(c + d) * invN;     // c_mir / N
-            sm.y0[f] = make_float2(dre - mim, dim + mre);
-            if (f > 0 && 2 * f < N) sm.y0[N - f] = make_float2(dre + mim, mre - dim);
+        for (int c = 0; c < KB; ++c) {
+            if (c < nc) {
+                const float dre = (A[c] + B[c]) * invN, dim = (C[c] - D[c]) * invN;
+                const float mre = (A[c] - B[c]) * invN, mim = -(C[c] + D[c]) * invN;
+                float2* y = sm.y + c * N;
+                y[f] = make_float2(dre - mim, dim + mre);
+                if (f > 0 && 2 * f < N) y[N - f] = make_float2(dre + mim, mre - dim);
+            }
         }
     }
     __syncthreads();
-    float2* src = sm.y0;
-    float2* dst = sm.y1;
+}
+
+// In-place (through sm.tmp) inverse transform of y: returns the buffer that
+// holds C_dir[k] + i C_mir[k].  Stockham mixed radix when N factors into
+// 4, 2, 3, 5, otherwise direct.
+__device__ float2* inverse_transform(float2* y, int N, const Radix& rad, SelSmem& sm) {
+    float2* src = y;
+    float2* dst = sm.tmp;
     if (rad.n > 0) {
         int Ns = 1;
         for (int stg = 0; stg < rad.n; ++stg) {
@@ -295,38 +327,27 @@ __device__ void evaluate_axis(const float* __restrict__ Pr, const float* __restr
                 }
             }
             __syncthreads();
-            float2* tmp = src;
+            float2* t2 = src;
             src = dst;
-            dst = tmp;
+            dst = t2;
             Ns *= R;
         }
-    } else {
-        for (int k = threadIdx.x; k < N; k += blockDim.x) {
-            float2 acc = make_float2(0.f, 0.f);
-            int idx = 0;
-            for (int f = 0; f < N; ++f) {
-                const float2 x = src[f], t = sm.tw[idx];
-                acc.x = fmaf(x.x, t.x, fmaf(-x.y, t.y, acc.x));
-                acc.y = fmaf(x.x, t.y, fmaf(x.y, t.x, acc.y));
-                idx += k;
-                if (idx >= N) idx -= N;
-            }
-            dst[k] = acc;
-        }
-        __syncthreads();
-        src = dst;
+        return src;
     }
-    sm.res = src;
-    float bv = -CUDART_INF_F;
-    unsigned bi = 0xffffffffu;
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        const float2 y = src[k];
-        if (better(y.x, (unsigned)k, bv, bi)) { bv = y.x; bi = (unsigned)k; }
-        if (better(y.y, (unsigned)(N + k), bv, bi)) { bv = y.y; bi = (unsigned)(N + k); }
+        float2 acc = make_float2(0.f, 0.f);
+        int idx = 0;
+        for (int f = 0; f < N; ++f) {
+            const float2 x = src[f], t = sm.tw[idx];
+            acc.x = fmaf(x.x, t.x, fmaf(-x.y, t.y, acc.x));
+            acc.y = fmaf(x.x, t.y, fmaf(x.y, t.x, acc.y));
+            idx += k;
+            if (idx >= N) idx -= N;
+        }
+        dst[k] = acc;
     }
-    block_argmax(bv, bi, sm.red_v, sm.red_i);
-    best_v = bv;
-    best_i = bi;
+    __syncthreads();
+    return dst;
 }
 
 __device__ inline void matmul3d(const double* a, const double* b, double* c) {
@@ -336,16 +357,17 @@ __device__ inline void matmul3d(const double* a, const double* b, double* c) {
 }
 
 struct SelectArgs {
-    const float *Pr, *Pi, *Xr, *Xi;   // FP32 spectra, [.][F][Spad]
+    const float *Psr, *Psi, *Xsr, *Xsi;   // FP32 spectra, shell-major [.][Spad][F]
     const float* U;                   // [nb][Z] bounds
     const float* xfn;                 // [nb][F] ||X^_bf||
+    const int2* srange;               // [nb] non-zero shell range
     const float* pfmax;               // [F] max_z ||P^_zf||
     const float* xnorm2;              // [nb] ||X||^2
     const double* za;                 // [Z][3]
     const double* frames;             // [Z][9]
     const int* nbr_ptr;
     const int* nbr_idx;
-    int Z, F, N, Spad, nb, refine;
+    int Z, F, N, S, Spad, nb, refine;
     float kappa;                      // contraction rounding constant
     Radix rad;                        // inverse-transform factorisation
     acom_result out;
@@ -353,18 +375,61 @@ struct SelectArgs {
     int* n_eval;                      // optional: total axes evaluated
 };
 
-__global__ void __launch_bounds__(kSelThreads) k_select_exact(SelectArgs a) {
+// Evaluate the axes listed in sm.cand[0..nc) in full; record each exact score
+// in sm.U and fold the best into (T, Tidx, bz, bk, bm, best3).
+__device__ void evaluate_batch(const SelectArgs& a, int64_t b, int nc, SelSmem& sm, float& T,
+                               unsigned& Tidx, int& bz, int& bk, int& bm, float* best3) {
+    const int N = a.N;
+    const int2 sr = a.srange[b];
+    if (nc <= 4)
+        batch_spectra<4>(a.Psr, a.Psi, a.Xsr, a.Xsi, b, nc, a.F, N, sr.x, sr.y, a.Spad, sm);
+    else
+        batch_spectra<kBatch>(a.Psr, a.Psi, a.Xsr, a.Xsi, b, nc, a.F, N, sr.x, sr.y, a.Spad, sm);
+    for (int c = 0; c < nc; ++c) {
+        const int z = sm.cand[c];
+        const float2* y = inverse_transform(sm.y + c * N, N, a.rad, sm);
+        float bv = -CUDART_INF_F;
+        unsigned bi = 0xffffffffu;
+        for (int k = threadIdx.x; k < N; k += blockDim.x) {
+            const float2 v = y[k];
+            if (better(v.x, (unsigned)k, bv, bi)) { bv = v.x; bi = (unsigned)k; }
+            if (better(v.y, (unsigned)(N + k), bv, bi)) { bv = v.y; bi = (unsigned)(N + k); }
+        }
+        block_argmax(bv, bi, sm.red_v, sm.red_i);
+        const unsigned gidx = (unsigned)z * 2u * (unsigned)N + bi;
+        if (better(bv, gidx, T, Tidx)) {
+            T = bv;
+            Tidx = gidx;
+            bz = z;
+            bm = (int)(bi / (unsigned)N);
+            bk = (int)(bi - (unsigned)bm * N);
+            if (threadIdx.x == 0) {
+                const float2 ym = y[(bk + N - 1) % N], y0 = y[bk], yp = y[(bk + 1) % N];
+                best3[0] = bm ? ym.y : ym.x;
+                best3[1] = bm ? y0.y : y0.x;
+                best3[2] = bm ? yp.y : yp.x;
+            }
+        }
+        if (threadIdx.x == 0) {
+            sm.U[z] = bv;
+            sm.ev[z] = 1;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kSelThreads, 3) k_select_exact(SelectArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Z = a.Z, F = a.F, N = a.N;
     SelSmem sm;
     sm.tw = reinterpret_cast<float2*>(smem_raw);
-    sm.y0 = sm.tw + N;
-    sm.y1 = sm.y0 + N;
-    sm.res = sm.y0;
-    sm.U = reinterpret_cast<float*>(sm.y1 + N);
+    sm.y = sm.tw + N;
+    sm.tmp = sm.y + kBatch * N;
+    sm.U = reinterpret_cast<float*>(sm.tmp + N);
     sm.red_v = sm.U + Z;
     sm.red_i = reinterpret_cast<int*>(sm.red_v + 32);
-    sm.ev = reinterpret_cast<uint8_t*>(sm.red_i + 32);
+    sm.cand = sm.red_i + 32;
+    sm.ev = reinterpret_cast<uint8_t*>(sm.cand + kBatch);
     __shared__ float s_best3[3];
     __shared__ double s_w[3];
 
@@ -399,61 +464,62 @@ __global__ void __launch_bounds__(kSelThreads) k_select_exact(SelectArgs a) {
     __syncthreads();
 
     float T = -CUDART_INF_F;            // best exact score so far
-    unsigned Tkey_idx = 0xffffffffu;    // (z * 2 + mir) * N + k of the best
+    unsigned Tidx = 0xffffffffu;        // (z * 2 + mir) * N + k of the best
     int bz = 0, bk = 0, bm = 0;
     int evals = 0;
-    for (;;) {
-        float v = -CUDART_INF_F;
-        unsigned zi = 0xffffffffu;
-        for (int z = threadIdx.x; z < Z; z += blockDim.x)
-            if (!sm.ev[z] && better(sm.U[z], (unsigned)z, v, zi)) {
-                v = sm.U[z];
-                zi = (unsigned)z;
-            }
-        block_argmax(v, zi, sm.red_v, sm.red_i);
-        if (zi == 0xffffffffu) break;
-        if (T != -CUDART_INF_F && v * rel + Emax < T) break;    // no axis left can win
-        const int z = (int)zi;
-        float sv;
-        unsigned si;
-        evaluate_axis(a.Pr, a.Pi, a.Xr, a.Xi, z, b, F, N, a.Spad, a.rad, sm, sv, si);
-        ++evals;
-        const unsigned gidx = (unsigned)z * 2u * (unsigned)N + si;
-        if (better(sv, gidx, T, Tkey_idx)) {
-            T = sv;
-            Tkey_idx = gidx;
-            bz = z;
-            bm = (int)(si / (unsigned)N);
-            bk = (int)(si - (unsigned)bm * N);
+    // batches in decreasing bound: the first takes the 4 largest bounds, later
+    // ones every axis whose bound can still reach the best exact score
+    for (int batch = 0;; ++batch) {
+        const int cap = batch == 0 ? 4 : kBatch;
+        int nc = 0;
+        while (nc < cap) {
+            float v = -CUDART_INF_F;
+            unsigned zi = 0xffffffffu;
+            for (int z = threadIdx.x; z < Z; z += blockDim.x)
+                if (sm.ev[z] == 0 && better(sm.U[z], (unsigned)z, v, zi)) {
+                    v = sm.U[z];
+                    zi = (unsigned)z;
+                }
+            block_argmax(v, zi, sm.red_v, sm.red_i);
+            if (zi == 0xffffffffu) break;
+            if (T != -CUDART_INF_F && v * rel + Emax < T) break;     // nothing left can win
             if (threadIdx.x == 0) {
-                const float2* y = sm.res;
-                const float2 ym = y[(bk + N - 1) % N], y0 = y[bk], yp = y[(bk + 1) % N];
-                s_best3[0] = bm ? ym.y : ym.x;
-                s_best3[1] = bm ? y0.y : y0.x;
-                s_best3[2] = bm ? yp.y : yp.x;
+                sm.cand[nc] = (int)zi;
+                sm.ev[zi] = 2;
             }
+            __syncthreads();
+            ++nc;
         }
-        if (threadIdx.x == 0) {
-            sm.U[z] = sv;
-            sm.ev[z] = 1;
-        }
-        __syncthreads();
+        if (nc == 0) break;
+        evaluate_batch(a, b, nc, sm, T, Tidx, bz, bk, bm, s_best3);
+        evals += nc;
+        // an all-zero image: every axis ties at 0 and the lowest index has won
+        if (T == 0.f && Tidx == 0u) break;
     }
     // zone-axis neighbours that may reach 0.9 of the best need their exact score
     const bool want_ref = (a.out.phi3 != nullptr) || (a.out.orient != nullptr);
     if (want_ref && a.refine && T > 0.f) {
-        for (int q = a.nbr_ptr[bz]; q < a.nbr_ptr[bz + 1]; ++q) {
-            const int z2 = a.nbr_idx[q];
-            if (sm.ev[z2] || sm.U[z2] * rel + Emax < 0.9f * T) continue;
-            float sv;
-            unsigned si;
-            evaluate_axis(a.Pr, a.Pi, a.Xr, a.Xi, z2, b, F, N, a.Spad, a.rad, sm, sv, si);
-            ++evals;
-            if (threadIdx.x == 0) {
-                sm.U[z2] = sv;
-                sm.ev[z2] = 1;
+        int q = a.nbr_ptr[bz];
+        const int qe = a.nbr_ptr[bz + 1];
+        for (;;) {
+            int nc = 0;
+            for (; q < qe && nc < kBatch; ++q) {
+                const int z2 = a.nbr_idx[q];
+                if (sm.ev[z2] || sm.U[z2] * rel + Emax < 0.9f * T) continue;
+                if (threadIdx.x == 0) {
+                    sm.cand[nc] = z2;
+                    sm.ev[z2] = 2;
+                }
+                ++nc;
             }
             __syncthreads();
+            if (nc == 0) break;
+            float Tn = T;
+            unsigned Tin = Tidx;
+            int z0 = bz, k0 = bk, m0 = bm;
+            float dummy[3];
+            evaluate_batch(a, b, nc, sm, Tn, Tin, z0, k0, m0, dummy);
+            evals += nc;
         }
     }
     // outputs
@@ -536,8 +602,8 @@ __global__ void __launch_bounds__(kSelThreads) k_select_exact(SelectArgs a) {
 }
 
 size_t select_smem_bytes(int Z, int N, int F) {
-    return sizeof(float2) * 3 * (size_t)N + sizeof(float) * ((size_t)Z + 32) + sizeof(int) * 32 +
-           Z + 16;
+    return sizeof(float2) * (kBatch + 2) * (size_t)N + sizeof(float) * ((size_t)Z + 32) +
+           sizeof(int) * (32 + kBatch) + Z + 16;
 }
 
 static Radix factor_radices(int N) {
@@ -553,13 +619,15 @@ static Radix factor_radices(int N) {
     return r;
 }
 
-void launch_select_exact(const acom_plan_s* p, const float* Xr, const float* Xi, const float* U,
-                         const float* xfn, const float* pfmax, const float* xnorm2, int nb,
+void launch_select_exact(const acom_plan_s* p, const float* Xsr, const float* Xsi, const float* U,
+                         const float* xfn, const int2* srange, const float* pfmax,
+                         const float* xnorm2, int nb,
                          float kappa, int refine, acom_result out, int64_t off, int* n_eval,
                          cudaStream_t st) {
-    SelectArgs a{p->Pr, p->Pi, Xr, Xi, U, xfn, pfmax, xnorm2, p->za, p->frames, p->nbr_ptr,
-                 p->nbr_idx, p->Z, p->F, p->N, p->Spad, nb, refine, kappa, factor_radices(p->N),
-                 out, off, n_eval};
+    SelectArgs a{p->Psr, p->Psi, Xsr, Xsi, U, xfn, srange, pfmax, xnorm2, p->za, p->frames,
+                 p->nbr_ptr,
+                 p->nbr_idx, p->Z, p->F, p->N, p->S, p->Spad, nb, refine, kappa,
+                 factor_radices(p->N), out, off, n_eval};
     const size_t smem = select_smem_bytes(p->Z, p->N, p->F);
     cudaFuncSetAttribute(k_select_exact, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     prof_begin(kKSelect, st);

@@ -220,9 +220,16 @@ acom_status build_plan_device(acom_plan_s* p, const acom_crystal* cr, cudaStream
         RasterGeom geo{p->S, p->Spad, p->N, p->F, (float)p->dq, (float)p->delta,
                        (float)p->gamma_pow, 1};
         PlanSource src{p->refl_g, p->refl_amp, p->frames, p->G, p->lambda};
-        launch_raster_plan(geo, src, p->Z, p->Pr, p->Pi, d_sumsq, p->err, st);
+        RasterOut ro;
+        ro.re = p->Pr;
+        ro.im = p->Pi;
+        ro.sre = p->Psr;
+        ro.sim = p->Psi;
+        ro.sumsq = d_sumsq;
+        launch_raster_plan(geo, src, p->Z, ro, p->err, st);
         ACOM_TRY(cudaGetLastError());
         launch_scale_rows(p->Pr, p->Pi, d_sumsq, p->Z, p->F * p->Spad, st);
+        launch_scale_rows(p->Psr, p->Psi, d_sumsq, p->Z, p->F * p->Spad, st);
         ACOM_TRY(cudaGetLastError());
         int herr = 0;
         ACOM_TRY(cudaMemcpyAsync(&herr, p->err, sizeof(int), cudaMemcpyDeviceToHost, st));

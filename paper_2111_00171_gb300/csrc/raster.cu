@@ -145,15 +145,17 @@ size_t raster_smem_bytes(int N, int F) {
     b += sizeof(float) * W * N;        // tap values
     b += sizeof(float) * 2 * W * F;    // staged spectra
     b += sizeof(float) * F;            // per-frequency norms
-    b += sizeof(int) * 64;             // scratch
+    b += sizeof(int) * 64;             // scratch (warp sums, compaction, shell range)
     return b;
 }
 
 template <class Loader, int NF2>
 __global__ void __launch_bounds__(kRasterThreads)
-k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, float* __restrict__ out_re,
-             float* __restrict__ out_im, float* __restrict__ sumsq, float* __restrict__ fnorm,
-             int* err) {
+k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, int* err) {
+    float* __restrict__ out_re = out.re;
+    float* __restrict__ out_im = out.im;
+    float* __restrict__ sumsq = out.sumsq;
+    float* __restrict__ fnorm = out.fnorm;
     extern __shared__ __align__(16) unsigned char smem[];
     const int N = geo.N, F = geo.F, S = geo.S, Spad = geo.Spad;
     constexpr int W = kRasterThreads / 32;
@@ -196,6 +198,10 @@ k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, float* __restrict__ out
     for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int np = ld.load(item, sp, s_int, err);
         float warp_sq = 0.f;                 // lane 0's running sum of squares
+        if (threadIdx.x == 0) {
+            s_int[40] = Spad;                // first shell with a non-zero row
+            s_int[41] = 0;                   // one past the last
+        }
         for (int f = threadIdx.x; f < F; f += blockDim.x) fn2[f] = 0.f;
         for (int s0 = 0; s0 < Spad; s0 += W) {
             const int s = s0 + warp;
@@ -249,7 +255,13 @@ k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, float* __restrict__ out
                     ntap += __popc(msk);
                     nrun += __popc(smk);
                 }
-                if (lane == 0) my_tj[nrun] = ntap << 16;       // sentinel
+                if (lane == 0) {
+                    my_tj[nrun] = ntap << 16;       // sentinel
+                    if (ntap > 0) {
+                        atomicMin(&s_int[40], s);
+                        atomicMax(&s_int[41], s + 1);
+                    }
+                }
                 for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
                 warp_sq += sq;
             }
@@ -328,8 +340,18 @@ k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, float* __restrict__ out
             const int64_t obase = item * (int64_t)F * Spad + s0;
             for (int e = threadIdx.x; e < F * W; e += blockDim.x) {
                 const int f = e / W, w = e - f * W;
-                out_re[obase + (int64_t)f * Spad + w] = st_re[w * F + f];
-                out_im[obase + (int64_t)f * Spad + w] = st_im[w * F + f];
+                if (out_re) {
+                    out_re[obase + (int64_t)f * Spad + w] = st_re[w * F + f];
+                    out_im[obase + (int64_t)f * Spad + w] = st_im[w * F + f];
+                }
+            }
+            if (out.sre) {
+                const int64_t sbase = (item * (int64_t)Spad + s0) * F;
+                for (int e = threadIdx.x; e < F * W; e += blockDim.x) {
+                    const int w = e / F, f = e - w * F;
+                    out.sre[sbase + (int64_t)w * F + f] = st_re[w * F + f];
+                    out.sim[sbase + (int64_t)w * F + f] = st_im[w * F + f];
+                }
             }
             __syncthreads();
         }
@@ -338,6 +360,10 @@ k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, float* __restrict__ out
         if (fnorm)
             for (int f = threadIdx.x; f < F; f += blockDim.x)
                 fnorm[item * (int64_t)F + f] = sqrtf(fn2[f]);
+        if (out.srange && threadIdx.x == 0) {
+            const int lo = s_int[40], hi = s_int[41];
+            out.srange[item] = lo < hi ? make_int2(lo, hi) : make_int2(0, 0);
+        }
         if (threadIdx.x == 0 && sumsq) {
             float tot = 0.f;
             for (int w = 0; w < W; ++w) tot += s_sum[w];
@@ -349,8 +375,7 @@ k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, float* __restrict__ out
 
 template <class Loader, int NF2>
 static void launch_raster_nf(const RasterGeom& geo, const Loader& ld, int64_t n_items,
-                             float* out_re, float* out_im, float* sumsq, float* fnorm, int* err,
-                             cudaStream_t st, int cls) {
+                             const RasterOut& out, int* err, cudaStream_t st, int cls) {
     size_t smem = raster_smem_bytes(geo.N, geo.F);
     cudaFuncSetAttribute(k_raster_dft<Loader, NF2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
@@ -364,37 +389,36 @@ static void launch_raster_nf(const RasterGeom& geo, const Loader& ld, int64_t n_
     if (grid > n_items) grid = n_items;
     prof_begin(cls, st);
     k_raster_dft<Loader, NF2><<<(unsigned)grid, kRasterThreads, smem, st>>>(
-        geo, ld, n_items, out_re, out_im, sumsq, fnorm, err);
+        geo, ld, n_items, out, err);
     prof_end(cls, st);
 }
 
 // frequencies per lane: the smallest compiled count covering F = N/2 + 1
 template <class Loader>
 static void launch_raster(const RasterGeom& geo, const Loader& ld, int64_t n_items,
-                          float* out_re, float* out_im, float* sumsq, float* fnorm, int* err,
-                          cudaStream_t st, int cls) {
+                          const RasterOut& out, int* err, cudaStream_t st, int cls) {
     if (n_items <= 0) return;
     const int nf2 = (geo.F + 31) / 32;
     if (nf2 <= 2)
-        launch_raster_nf<Loader, 2>(geo, ld, n_items, out_re, out_im, sumsq, fnorm, err, st, cls);
+        launch_raster_nf<Loader, 2>(geo, ld, n_items, out, err, st, cls);
     else if (nf2 <= 3)
-        launch_raster_nf<Loader, 3>(geo, ld, n_items, out_re, out_im, sumsq, fnorm, err, st, cls);
+        launch_raster_nf<Loader, 3>(geo, ld, n_items, out, err, st, cls);
     else if (nf2 <= 6)
-        launch_raster_nf<Loader, 6>(geo, ld, n_items, out_re, out_im, sumsq, fnorm, err, st, cls);
+        launch_raster_nf<Loader, 6>(geo, ld, n_items, out, err, st, cls);
     else
-        launch_raster_nf<Loader, 12>(geo, ld, n_items, out_re, out_im, sumsq, fnorm, err, st, cls);
+        launch_raster_nf<Loader, 12>(geo, ld, n_items, out, err, st, cls);
 }
 
-void launch_raster_plan(const RasterGeom& geo, const PlanSource& src, int Z, float* out_re,
-                        float* out_im, float* sumsq, int* err, cudaStream_t st) {
+void launch_raster_plan(const RasterGeom& geo, const PlanSource& src, int Z,
+                        const RasterOut& out, int* err, cudaStream_t st) {
     PlanLoader ld{src, geo.delta};
-    launch_raster(geo, ld, Z, out_re, out_im, sumsq, nullptr, err, st, kKRasterPlan);
+    launch_raster(geo, ld, Z, out, err, st, kKRasterPlan);
 }
 
-void launch_raster_patterns(const RasterGeom& geo, const PatternSource& src, float* out_re,
-                            float* out_im, float* sumsq, float* fnorm, int* err, cudaStream_t st) {
+void launch_raster_patterns(const RasterGeom& geo, const PatternSource& src,
+                            const RasterOut& out, int* err, cudaStream_t st) {
     PatternLoader ld{src};
-    launch_raster(geo, ld, src.n_items, out_re, out_im, sumsq, fnorm, err, st, kKRasterPatterns);
+    launch_raster(geo, ld, src.n_items, out, err, st, kKRasterPatterns);
 }
 
 // P = A P0 with A = 1/||P0||_2 (0 for an empty slice): the transform is
