@@ -12,13 +12,14 @@
 // Plan" for a reflection (r = |g'_xy|, gam = gamma_g, e = s_g^2, weight
 // |V_g|^omega, rows scaled by q_s^gamma) under uniform shells.
 //
-// Each warp owns one shell row of N bins in shared memory; peaks whose tent
-// reaches the shell add into the bins inside their angular window (lanes own
-// distinct bins, peaks are visited in order, so the sums are deterministic).
-// The row's non-zero bins are compacted and transformed directly,
-// X^(s, f) = sum_j X(s, j) exp(-2 pi i f j / N), f = 0..N/2, with a shared
-// twiddle table; eight shells are staged and written as 32-byte runs of the
-// [item][f][Spad] output.
+// Peaks are sorted by radius, so the peaks reaching a shell are a contiguous
+// run.  Each warp owns one shell: for every peak reaching it, the lanes
+// evaluate the tent on 32 consecutive bins of the peak's angular window, and
+// the window's contribution to X^(s, f) = sum_j X(s, j) exp(-2 pi i f j / N),
+// f = 0..N/2, is added by Horner's rule (the transform is linear, so
+// overlapping windows simply add; peaks are visited in a fixed order, so the
+// sums are deterministic).  Eight shells are staged in shared memory and
+// written in the requested layouts; ||X||^2 follows by Parseval.
 #include <cuda_bf16.h>
 #include <math_constants.h>
 
@@ -138,37 +139,29 @@ struct PlanLoader {
 size_t raster_smem_bytes(int N, int F) {
     const int W = kRasterThreads / 32;
     size_t b = 0;
-    b += sizeof(Peak) * kMaxPeaks;     // peaks
-    b += sizeof(float) * 2 * N;        // twiddles
-    b += sizeof(float) * W * N;        // rows
-    b += sizeof(int) * W * N;          // tap bins
-    b += sizeof(float) * W * N;        // tap values
-    b += sizeof(float) * 2 * W * F;    // staged spectra
-    b += sizeof(float) * F;            // per-frequency norms
-    b += sizeof(int) * 64;             // scratch (warp sums, compaction, shell range)
+    b += sizeof(Peak) * 2 * kMaxPeaks; // peaks as loaded, and sorted by radius
+    b += sizeof(float2) * N;           // twiddles
+    b += sizeof(float) * W * 32;       // tent values of the current window chunk
+    b += sizeof(float) * 2 * W * F;    // staged spectra of a shell group
+    b += sizeof(float) * F;            // per-frequency sums of |X^|^2 over shells
+    b += sizeof(int) * 64;             // scratch (compaction, shell range, sums)
     return b;
 }
 
 template <class Loader, int NF2>
 __global__ void __launch_bounds__(kRasterThreads)
 k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, int* err) {
-    float* __restrict__ out_re = out.re;
-    float* __restrict__ out_im = out.im;
-    float* __restrict__ sumsq = out.sumsq;
-    float* __restrict__ fnorm = out.fnorm;
     extern __shared__ __align__(16) unsigned char smem[];
     const int N = geo.N, F = geo.F, S = geo.S, Spad = geo.Spad;
     constexpr int W = kRasterThreads / 32;
     Peak* sp = reinterpret_cast<Peak*>(smem);
-    float2* tw = reinterpret_cast<float2*>(sp + kMaxPeaks);    // (cos, sin) of 2 pi i / N
-    float* rows = reinterpret_cast<float*>(tw + N);
-    int* tapj = reinterpret_cast<int*>(rows + W * N);
-    float* tapv = reinterpret_cast<float*>(tapj + W * N);
-    float* st_re = tapv + W * N;
+    Peak* ss = sp + kMaxPeaks;                                // sorted by radius
+    float2* tw = reinterpret_cast<float2*>(ss + kMaxPeaks);   // (cos, sin) of 2 pi i / N
+    float* tbuf = reinterpret_cast<float*>(tw + N);
+    float* st_re = tbuf + W * 32;
     float* st_im = st_re + W * F;
-    float* fn2 = st_im + W * F;                         // [F] sum over shells of |X^|^2
+    float* fn2 = st_im + W * F;
     int* s_int = reinterpret_cast<int*>(fn2 + F);
-    float* s_sum = reinterpret_cast<float*>(s_int + 32);
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
@@ -177,7 +170,6 @@ k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, int* err
         tw[i] = make_float2((float)c, (float)s);
     }
     __syncthreads();
-
     // z_f = exp(-2 pi i f / N) for this lane's frequencies f = lane + 32 g
     float zr[NF2], zi[NF2];
 #pragma unroll
@@ -191,31 +183,50 @@ k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, int* err
     const float dphi = two_pi / (float)N;
     const float inv_dphi = (float)N / two_pi;
     const float invN = 1.0f / (float)N;
-    float* row = rows + warp * N;
-    int* my_tj = tapj + warp * N;
-    float* my_tv = tapv + warp * N;
+    float* my_t = tbuf + warp * 32;
 
     for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int np = ld.load(item, sp, s_int, err);
-        float warp_sq = 0.f;                 // lane 0's running sum of squares
+        // rank sort by (radius, index): the peaks reaching a shell are then a
+        // contiguous run of the sorted list
+        for (int i = threadIdx.x; i < np; i += blockDim.x) {
+            const float ri = sp[i].r;
+            int rank = 0;
+            for (int j = 0; j < np; ++j) {
+                const float rj = sp[j].r;
+                rank += (rj < ri) || (rj == ri && j < i);
+            }
+            ss[rank] = sp[i];
+        }
+        for (int f = threadIdx.x; f < F; f += blockDim.x) fn2[f] = 0.f;
         if (threadIdx.x == 0) {
             s_int[40] = Spad;                // first shell with a non-zero row
             s_int[41] = 0;                   // one past the last
         }
-        for (int f = threadIdx.x; f < F; f += blockDim.x) fn2[f] = 0.f;
+        __syncthreads();
         for (int s0 = 0; s0 < Spad; s0 += W) {
             const int s = s0 + warp;
-            for (int j = lane; j < N; j += 32) row[j] = 0.f;
-            __syncwarp();
-            int ntap = 0, nrun = 0;
+            float ar[NF2], ai[NF2];
+#pragma unroll
+            for (int g = 0; g < NF2; ++g) ar[g] = ai[g] = 0.f;
+            bool nonzero = false;
             if (s < S) {
                 const float qs = (float)(s + 1) * geo.dq;
                 const float qs2 = qs * qs;
-                for (int m = 0; m < np; ++m) {
-                    const Peak pk = sp[m];
+                const float rscale = geo.shell_power ? powf(qs, geo.gamma_pow) : 1.0f;
+                // sorted peaks with |r - q_s| < delta
+                int lo = 0, hi = 0;
+                for (int base = 0; base < np; base += 32) {
+                    const int m = base + lane;
+                    const float r = m < np ? ss[m].r : CUDART_INF_F;
+                    lo += __popc(__ballot_sync(0xffffffffu, r <= qs - delta));
+                    hi += __popc(__ballot_sync(0xffffffffu, r < qs + delta));
+                }
+                for (int m = lo; m < hi; ++m) {
+                    const Peak pk = ss[m];
                     const float dr = pk.r - qs;
                     const float a2 = dr * dr + pk.e;
-                    if (!(a2 < d2) || pk.w == 0.f) continue;       // tent is zero on this shell
+                    if (!(a2 < d2) || pk.w == 0.f) continue;          // tent is zero on this shell
                     const float hw = sqrtf(d2 - a2) / qs;            // angular half width
                     int jlo, cnt;
                     if (hw >= CUDART_PI_F) {
@@ -223,105 +234,77 @@ k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, int* err
                         cnt = N;
                     } else {
                         jlo = (int)floorf((pk.gam - hw) * inv_dphi) - 1;
-                        int jhi = (int)ceilf((pk.gam + hw) * inv_dphi) + 1;
+                        const int jhi = (int)ceilf((pk.gam + hw) * inv_dphi) + 1;
                         cnt = min(jhi - jlo + 1, N);
                     }
-                    for (int t = lane; t < cnt; t += 32) {
-                        int j = jlo + t;
-                        j %= N;
-                        if (j < 0) j += N;
-                        float d = (float)j * dphi - pk.gam;
-                        d -= two_pi * floorf((d + CUDART_PI_F) / two_pi);   // wrap to [-pi, pi)
-                        float tv = 1.0f - sqrtf(a2 + d * d * qs2) * inv_delta;
-                        if (tv > 0.f) row[j] += pk.w * tv;
-                    }
-                    __syncwarp();
-                }
-                const float rscale = geo.shell_power ? powf(qs, geo.gamma_pow) : 1.0f;
-                float sq = 0.f;
-                // non-zero bins in bin order; runs of consecutive bins are
-                // recorded as (first tap << 16 | first bin)
-                for (int base = 0; base < N; base += 32) {
-                    int j = base + lane;
-                    float v = (j < N) ? row[j] * rscale : 0.f;
-                    sq += v * v;
-                    const bool start = v != 0.f && (j == 0 || row[j - 1] == 0.f);
-                    unsigned msk = __ballot_sync(0xffffffffu, v != 0.f);
-                    unsigned smk = __ballot_sync(0xffffffffu, start);
-                    const unsigned lt = (1u << lane) - 1u;
-                    const int pos = ntap + __popc(msk & lt);
-                    if (v != 0.f) my_tv[pos] = v;
-                    if (start) my_tj[nrun + __popc(smk & lt)] = (pos << 16) | j;
-                    ntap += __popc(msk);
-                    nrun += __popc(smk);
-                }
-                if (lane == 0) {
-                    my_tj[nrun] = ntap << 16;       // sentinel
-                    if (ntap > 0) {
-                        atomicMin(&s_int[40], s);
-                        atomicMax(&s_int[41], s + 1);
-                    }
-                }
-                for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-                warp_sq += sq;
-            }
-            __syncwarp();
-            // transform of the non-zero bins.  Lane l owns the frequencies
-            // f = l + 32 g.  A run of consecutive bins j0 .. j0+L-1 contributes
-            // exp(-2 pi i f j0 / N) P(z_f), P(z) = sum_m v_m z^m, z_f =
-            // exp(-2 pi i f / N), evaluated by Horner's rule (4 FMA per bin and
-            // frequency, no table access); one table read per run and frequency.
-            __syncwarp();
-            {
-                float ar[NF2], ai[NF2];
+                    const float wgt = pk.w * rscale;
+                    jlo %= N;                                       // first bin in [0, N)
+                    if (jlo < 0) jlo += N;
+                    // chunks of 32 consecutive bins (mod N, which the transform
+                    // sees as consecutive): tent values, then Horner's rule
+                    for (int c0 = 0; c0 < cnt; c0 += 32) {
+                        const int t = c0 + lane;
+                        float tv = 0.f;
+                        if (t < cnt) {
+                            int j = jlo + t;                    // t < cnt <= N
+                            if (j >= N) j -= N;
+                            float d = (float)j * dphi - pk.gam;
+                            d -= two_pi * floorf((d + CUDART_PI_F) / two_pi);   // wrap to [-pi, pi)
+                            const float tt = 1.0f - sqrtf(a2 + d * d * qs2) * inv_delta;
+                            tv = tt > 0.f ? wgt * tt : 0.f;
+                        }
+                        my_t[lane] = tv;
+                        __syncwarp();
+                        const int L = min(32, cnt - c0);
+                        float hr[NF2], hi_[NF2];
 #pragma unroll
-                for (int g = 0; g < NF2; ++g) ar[g] = ai[g] = 0.f;
-                for (int rn = 0; rn < nrun; ++rn) {
-                    const int info = my_tj[rn];
-                    const int p0 = info >> 16, j0 = info & 0xffff;
-                    const int p1 = my_tj[rn + 1] >> 16;
-                    float hr[NF2], hi[NF2];
+                        for (int g = 0; g < NF2; ++g) hr[g] = hi_[g] = 0.f;
+                        for (int p = L - 1; p >= 0; --p) {
+                            const float v = my_t[p];
 #pragma unroll
-                    for (int g = 0; g < NF2; ++g) hr[g] = hi[g] = 0.f;
-                    for (int p = p1 - 1; p >= p0; --p) {
-                        const float v = my_tv[p];
+                            for (int g = 0; g < NF2; ++g) {
+                                const float tq = fmaf(hr[g], zr[g], fmaf(-hi_[g], zi[g], v));
+                                hi_[g] = fmaf(hr[g], zi[g], hi_[g] * zr[g]);
+                                hr[g] = tq;
+                            }
+                        }
+                        __syncwarp();
+                        int j0 = jlo + c0;
+                        if (j0 >= N) j0 -= N;
 #pragma unroll
                         for (int g = 0; g < NF2; ++g) {
-                            const float t = fmaf(hr[g], zr[g], fmaf(-hi[g], zi[g], v));
-                            hi[g] = fmaf(hr[g], zi[g], hi[g] * zr[g]);
-                            hr[g] = t;
+                            const int prod = (lane + 32 * g) * j0;
+                            const int q = __float2int_rz((float)prod * invN);
+                            int idx = prod - q * N;
+                            if (idx >= N) idx -= N;
+                            if (idx < 0) idx += N;
+                            const float2 w = tw[idx];            // exp(+i theta): conjugate it
+                            ar[g] = fmaf(hr[g], w.x, fmaf(hi_[g], w.y, ar[g]));
+                            ai[g] = fmaf(hi_[g], w.x, fmaf(-hr[g], w.y, ai[g]));
                         }
                     }
-#pragma unroll
-                    for (int g = 0; g < NF2; ++g) {
-                        const int prod = (lane + 32 * g) * j0;
-                        const int q = __float2int_rz((float)prod * invN);
-                        int idx = prod - q * N;
-                        if (idx >= N) idx -= N;
-                        if (idx < 0) idx += N;
-                        const float2 w = tw[idx];                // exp(+i theta): conjugate it
-                        ar[g] = fmaf(hr[g], w.x, fmaf(hi[g], w.y, ar[g]));
-                        ai[g] = fmaf(hi[g], w.x, fmaf(-hr[g], w.y, ai[g]));
-                    }
+                    nonzero = true;
                 }
+                if (lane == 0 && nonzero) {
+                    atomicMin(&s_int[40], s);
+                    atomicMax(&s_int[41], s + 1);
+                }
+            }
 #pragma unroll
-                for (int g = 0; g < NF2; ++g) {
-                    const int f = lane + 32 * g;
-                    if (f < F) {
-                        st_re[warp * F + f] = ar[g];
-                        st_im[warp * F + f] = ai[g];
-                    }
+            for (int g = 0; g < NF2; ++g) {
+                const int f = lane + 32 * g;
+                if (f < F) {
+                    st_re[warp * F + f] = ar[g];
+                    st_im[warp * F + f] = ai[g];
                 }
             }
             __syncthreads();
-            if (fnorm) {
-                for (int f = threadIdx.x; f < F; f += blockDim.x) {
-                    float acc = fn2[f];
-                    for (int w = 0; w < W; ++w)
-                        acc = fmaf(st_re[w * F + f], st_re[w * F + f],
-                                   fmaf(st_im[w * F + f], st_im[w * F + f], acc));
-                    fn2[f] = acc;
-                }
+            for (int f = threadIdx.x; f < F; f += blockDim.x) {
+                float acc = fn2[f];
+                for (int w = 0; w < W; ++w)
+                    acc = fmaf(st_re[w * F + f], st_re[w * F + f],
+                               fmaf(st_im[w * F + f], st_im[w * F + f], acc));
+                fn2[f] = acc;
             }
             if (ld.xb_out()) {
                 // BF16 copy in the tensor-core tile layout: rows (re, im) of 64-pattern tiles
@@ -337,12 +320,12 @@ k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, int* err
                                               row * Spad + s0) = *reinterpret_cast<uint4*>(v);
                 }
             }
-            const int64_t obase = item * (int64_t)F * Spad + s0;
-            for (int e = threadIdx.x; e < F * W; e += blockDim.x) {
-                const int f = e / W, w = e - f * W;
-                if (out_re) {
-                    out_re[obase + (int64_t)f * Spad + w] = st_re[w * F + f];
-                    out_im[obase + (int64_t)f * Spad + w] = st_im[w * F + f];
+            if (out.re) {
+                const int64_t obase = item * (int64_t)F * Spad + s0;
+                for (int e = threadIdx.x; e < F * W; e += blockDim.x) {
+                    const int f = e / W, w = e - f * W;
+                    out.re[obase + (int64_t)f * Spad + w] = st_re[w * F + f];
+                    out.im[obase + (int64_t)f * Spad + w] = st_im[w * F + f];
                 }
             }
             if (out.sre) {
@@ -355,19 +338,28 @@ k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, int* err
             }
             __syncthreads();
         }
-        if (lane == 0) s_sum[warp] = warp_sq;
-        __syncthreads();
-        if (fnorm)
+        if (out.fnorm)
             for (int f = threadIdx.x; f < F; f += blockDim.x)
-                fnorm[item * (int64_t)F + f] = sqrtf(fn2[f]);
-        if (out.srange && threadIdx.x == 0) {
-            const int lo = s_int[40], hi = s_int[41];
-            out.srange[item] = lo < hi ? make_int2(lo, hi) : make_int2(0, 0);
+                out.fnorm[item * (int64_t)F + f] = sqrtf(fn2[f]);
+        if (threadIdx.x == 0) {
+            if (out.srange) {
+                const int lo = s_int[40], hi = s_int[41];
+                out.srange[item] = lo < hi ? make_int2(lo, hi) : make_int2(0, 0);
+            }
         }
-        if (threadIdx.x == 0 && sumsq) {
-            float tot = 0.f;
-            for (int w = 0; w < W; ++w) tot += s_sum[w];
-            sumsq[item] = tot;
+        if (out.sumsq) {
+            // Parseval: sum_j X^2 = (1/N) sum_f w_f sum_s |X^_f|^2
+            float e = 0.f;
+            for (int f = threadIdx.x; f < F; f += blockDim.x)
+                e += ((f == 0 || 2 * f == N) ? 1.f : 2.f) * fn2[f];
+            for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+            if (lane == 0) st_re[warp] = e;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                float t = 0.f;
+                for (int w = 0; w < W; ++w) t += st_re[w];
+                out.sumsq[item] = t * invN;
+            }
         }
         __syncthreads();
     }
