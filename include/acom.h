@@ -263,6 +263,34 @@ int64_t acom_kernel_launches(void);
 acom_status acom_bounds(acom_plan plan, const acom_peaks_csr* peaks, float* dst,
                         void* cuda_stream);
 
+/*
+ * acom_bounds_static - the same result as acom_bounds, computed without
+ * allocating any device memory.  The paper has no counterpart: this entry
+ * point exists for callers that must not allocate while they run, such as an
+ * acquisition loop that reserved its whole device-memory budget up front, or
+ * a host process whose device memory is held by another allocator (a
+ * cudaMalloc there could fail or stall).  The plan must already exist; the
+ * caller passes the peaks and ``dst`` ([n_patterns][Z] FP32, DEVICE), as for
+ * acom_bounds.
+ *
+ * Scratch: the pattern spectra of one chunk live in a file-scope device array
+ * of 32 MiB that every device loading the library keeps until the process
+ * exits.  Patterns are processed in chunks of as many as that array holds for
+ * the plan's geometry (a multiple of 64); plans whose geometry leaves room for
+ * fewer than 64 patterns are rejected with ACOM_ERR_UNSUPPORTED.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any stream
+ * capture.  All calls share the one array and leave the last call's contents
+ * in it (every value a call reads it writes first), so calls whose work
+ * overlaps on the GPU - on different streams, or from different threads -
+ * race on the array and must be ordered by the caller.  The call performs no
+ * cudaMalloc, cudaFree or other allocating library call, records no profiling
+ * events, and synchronises ``cuda_stream`` once to read the error word.
+ */
+acom_status acom_bounds_static(acom_plan plan, const acom_peaks_csr* peaks, float* dst,
+                               void* cuda_stream);
+
 const char* acom_status_str(acom_status status);
 const char* acom_last_error(void);
 

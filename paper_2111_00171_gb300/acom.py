@@ -24,7 +24,8 @@ STATUS = {0: "ACOM_OK", 1: "ACOM_ERR_INVALID_ARG", 2: "ACOM_ERR_OOM", 3: "ACOM_E
 
 EXPORTED = ("acom_plan_create", "acom_plan_destroy", "acom_plan_get_info",
             "acom_plan_get_zone_axes", "acom_plan_get_spectra", "acom_match",
-            "acom_polar_spectra", "acom_bounds", "acom_status_str", "acom_last_error",
+            "acom_polar_spectra", "acom_bounds", "acom_bounds_static", "acom_status_str",
+            "acom_last_error",
             "acom_version", "acom_profile_enable", "acom_profile_reset", "acom_profile_read",
             "acom_kernel_launches")
 
@@ -104,6 +105,7 @@ def load_library():
     lib.acom_match.argtypes = [P, C.POINTER(PeaksCSR), C.POINTER(MatchOpts), C.POINTER(Result), P]
     lib.acom_polar_spectra.argtypes = [P, C.POINTER(PeaksCSR), P, P, P]
     lib.acom_bounds.argtypes = [P, C.POINTER(PeaksCSR), P, P]
+    lib.acom_bounds_static.argtypes = [P, C.POINTER(PeaksCSR), P, P]
     lib.acom_profile_enable.argtypes = [C.c_int32]
     lib.acom_profile_enable.restype = None
     lib.acom_profile_reset.restype = None
@@ -114,7 +116,7 @@ def load_library():
     lib.acom_version.restype = C.c_int32
     for name in ("acom_plan_create", "acom_plan_destroy", "acom_plan_get_info",
                  "acom_plan_get_zone_axes", "acom_plan_get_spectra", "acom_match",
-                 "acom_polar_spectra", "acom_bounds"):
+                 "acom_polar_spectra", "acom_bounds", "acom_bounds_static"):
         getattr(lib, name).restype = C.c_int
     _LIB = lib
     return lib
@@ -261,6 +263,14 @@ class Plan:
         pk = self._csr(row_ptr, qx, qy, I)
         out = torch.empty((pk.n_patterns, self.info["n_za"]), dtype=torch.float32, device="cuda")
         _check(self._lib.acom_bounds(self.handle, C.byref(pk), _ptr(out), _stream_ptr(stream)))
+        return out
+
+    def bounds_static(self, row_ptr, qx, qy, I, out, stream=None):
+        """acom_bounds_static into the caller's [B][Z] tensor ``out`` (no device
+        allocation inside the library call)."""
+        pk = self._csr(row_ptr, qx, qy, I)
+        _check(self._lib.acom_bounds_static(self.handle, C.byref(pk), _ptr(out),
+                                            _stream_ptr(stream)))
         return out
 
     def alloc_result(self, n, za_scores=False, orient=True):

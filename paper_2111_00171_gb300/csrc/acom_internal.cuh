@@ -125,6 +125,7 @@ enum KernelClass {
 void prof_begin(int cls, cudaStream_t st);
 void prof_end(int cls, cudaStream_t st);
 void prof_resolve();
+void prof_suppress(bool on);   // this thread's launches record no events (no event creation)
 
 // ---- error reporting (api.cu) ----
 acom_status set_error(acom_status s, const std::string& msg);

@@ -39,9 +39,13 @@ cudaEvent_t take() {
 }
 }  // namespace
 
+thread_local bool t_suppress = false;
+
+void prof_suppress(bool on) { t_suppress = on; }
+
 void prof_begin(int cls, cudaStream_t st) {
     ++g_launches;
-    if (!g_on) return;
+    if (!g_on || t_suppress) return;
     cudaEvent_t a = take();
     cudaEventRecord(a, st);
     g_open[cls] = a;
@@ -49,7 +53,7 @@ void prof_begin(int cls, cudaStream_t st) {
 }
 
 void prof_end(int cls, cudaStream_t st) {
-    if (!g_on || !g_has_open[cls]) return;
+    if (!g_on || t_suppress || !g_has_open[cls]) return;
     cudaEvent_t b = take();
     cudaEventRecord(b, st);
     g_pending.push_back({cls, g_open[cls], b});
