@@ -175,7 +175,7 @@ typedef struct {
  *             With certified pruning (the default) the value is exact for
  *             every axis that was evaluated (the winner and every axis whose
  *             bound could reach it) and is otherwise an upper bound of the
- *             axis' maximum, (1/N) sum_f w_f |c_f| plus a rounding margin.
+ *             axis' maximum (the bound of acom_bounds plus a rounding margin).
  * Ties: the lowest zone-axis index wins, then C before C_mirror, then the
  * lowest phi3 bin.
  */
@@ -206,8 +206,9 @@ typedef struct {
  * the refinement of the winner into an orientation matrix.
  *
  * Certified pruning (default): the contraction reduces each (zone axis,
- * pattern) pair to the bound U = (1/N) sum_f w_f |c_f| >= max_k C[k] of its
- * correlation spectrum c_f (w_0 = w_{N/2} = 1, else 2) plus a rounding margin;
+ * pattern) pair to the bound U = (1/N) sum_f w_f max(|c_f^dir|, |c_f^mir|)
+ * >= max_k max(C[k], C_mirror[k]) of its correlation spectra (w_0 = w_{N/2} =
+ * 1, else 2) plus a rounding margin;
  * axes are then evaluated in full, in decreasing U, until no remaining bound
  * can reach the best score.  The winner equals that of the exhaustive
  * evaluation.  Zone-axis counts above 16384 require exhaustive mode.
@@ -253,9 +254,10 @@ int64_t acom_kernel_launches(void);
 
 /*
  * acom_bounds - the shell contraction alone: for every pattern and zone axis
- * the spectral bound U = max over {direct, mirror} of (1/N) sum_f w_f |c_f|,
- * which is >= max over phi3 of C (section "Correlation Pattern Matching";
- * w_0 = w_{N/2} = 1, else 2).  Computed at the plan's precision (FP32 CUDA
+ * the spectral bound U = (1/N) sum_f w_f max(|c_f^dir|, |c_f^mir|) of the
+ * direct and mirror correlation spectra, which is >= max over phi3 of both C
+ * and C_mirror (section "Correlation Pattern Matching"; w_0 = w_{N/2} = 1,
+ * else 2).  Computed at the plan's precision (FP32 CUDA
  * cores, or BF16 tensor cores with FP32 accumulation) without any rounding
  * margin.  ``dst``: DEVICE [n_patterns][Z] FP32.  Stream-ordered; synchronises
  * once to read the error word.

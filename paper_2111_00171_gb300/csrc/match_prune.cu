@@ -4,10 +4,11 @@
 // transforms of the spectra c_f = sum_s FFT{P}^*_sf FFT{X}_sf (direct) and of
 // its mirror counterpart, so for every bin k
 //
-//   C[k] = (1/N) sum_f w_f Re(c_f e^{2 pi i f k / N}) <= (1/N) sum_f w_f |c_f| =: U(z, b)
+//   C[k] = (1/N) sum_f w_f Re(c_f e^{2 pi i f k / N}) <= (1/N) sum_f w_f |c_f|
 //
 // (w_0 = w_{N/2} = 1, else 2).  The contraction kernels reduce every (z, b)
-// pair to U = max(U_direct, U_mirror) while the spectra are on chip; the full
+// pair to U = (1/N) sum_f w_f max(|c_f^dir|, |c_f^mir|), which bounds both
+// correlations at once, while the spectra are on chip; the full
 // correlation of an axis is then evaluated (in FP32) only while its bound can
 // still beat the best score found so far.  Rounding of the contraction is
 // covered by a margin E_b = kappa (1/N) sum_f w_f max_z ||P^_zf|| ||X^_bf||,
@@ -40,11 +41,11 @@ k_contract_bound_fp32(const float* __restrict__ Pr, const float* __restrict__ Pi
     const int t = threadIdx.x, tz = t & 15, tb = t >> 4;
     const int lr = t >> 2, lc = (t & 3) * 4;
     const bool bvalid = (b0 + lr) < nb;
-    float Ud[4][4], Um[4][4];
+    float Ud[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) Ud[i][j] = Um[i][j] = 0.f;
+        for (int j = 0; j < 4; ++j) Ud[i][j] = 0.f;
 
     for (int f = 0; f < F; ++f) {
         float A[4][4], B[4][4], C[4][4], D[4][4];
@@ -94,10 +95,11 @@ k_contract_bound_fp32(const float* __restrict__ Pr, const float* __restrict__ Pi
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const float dre = A[i][j] + B[i][j], dim = C[i][j] - D[i][j];
-                const float mre = A[i][j] - B[i][j], mim = C[i][j] + D[i][j];
-                Ud[i][j] = fmaf(w, sqrtf(fmaf(dre, dre, dim * dim)), Ud[i][j]);
-                Um[i][j] = fmaf(w, sqrtf(fmaf(mre, mre, mim * mim)), Um[i][j]);
+                // max(|c_dir|, |c_mir|)^2 = p + 2 |AB - CD|, p = A^2 + B^2 + C^2 + D^2
+                const float a_ = A[i][j], b_ = B[i][j], c_ = C[i][j], d_ = D[i][j];
+                const float p = fmaf(a_, a_, fmaf(b_, b_, fmaf(c_, c_, d_ * d_)));
+                const float q = fmaf(a_, b_, -c_ * d_);
+                Ud[i][j] = fmaf(w, sqrtf(fmaf(2.0f, fabsf(q), p)), Ud[i][j]);
             }
     }
     const float invN = 1.0f / (float)N;
@@ -108,7 +110,7 @@ k_contract_bound_fp32(const float* __restrict__ Pr, const float* __restrict__ Pi
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int z = z0 + tz * 4 + i;
-            if (z < Z) U[(int64_t)b * Z + z] = fmaxf(Ud[i][j], Um[i][j]) * invN;
+            if (z < Z) U[(int64_t)b * Z + z] = Ud[i][j] * invN;
         }
     }
 }

@@ -8,12 +8,12 @@
 //   D2 = Pi_f [Xr_f ; Xi_f]^T   -> columns (D = Pi.Xr | B = Pi.Xi)
 // with FP32 accumulation in tensor memory.  Both MMAs put a zone axis in the
 // same TMEM lane, so one epilogue thread owns all four products of its pairs
-// and accumulates w_f |(A+B) + i(C-D)| and w_f |(A-B) - i(C+D)| over f.  The
-// spectra never leave the chip; only U = max(U_dir, U_mir)/N is written.
+// and accumulates w_f max(|(A+B) + i(C-D)|, |(A-B) - i(C+D)|) over f.  The
+// spectra never leave the chip; only U is written.
 //
 // CTA: one TMA producer warp, one MMA-issuing warp, sixteen epilogue warps;
 // persistent over (128-axis x 64-pattern) tiles; operands stream through a
-// 6-stage shared-memory ring (K tiles of 32 BF16 = 64-byte rows, 64-byte
+// 8-stage shared-memory ring (K tiles of 32 BF16 = 64-byte rows, 64-byte
 // swizzle); accumulators are double-buffered over f in 512 TMEM columns.
 // Every mbarrier wait is bounded: a timeout sets the device error word, stops
 // all roles, drains copies and MMAs in flight, frees TMEM and returns.
@@ -30,7 +30,7 @@ namespace tc {
 constexpr int kM = 128;               // zone axes per tile (MMA M)
 constexpr int kNP = 64;               // patterns per tile (MMA N = 128 rows: re, im)
 constexpr int kKT = 32;               // BF16 per K tile row (64 bytes)
-constexpr int kStages = 6;
+constexpr int kStages = 8;
 constexpr int kTileBytes = 128 * kKT * 2;      // 8 KB
 constexpr int kStageBytes = 3 * kTileBytes;    // Pr, Pi, X
 constexpr int kEpiWarps = 16;
@@ -152,13 +152,24 @@ __device__ __forceinline__ void fence_after() {
                  :                                                                         \
                  : "memory")
 
-// |c| from |c|^2 with one MUFU operation: q rsqrt(q), q = |c|^2 + 1e-30 (the
-// offset keeps q > 0 and only raises the bound by < 1e-15)
+// |c| from |c|^2 (approximate square root, relative error ~2^-23, covered by
+// the bound's rounding margin)
 __device__ __forceinline__ float mag_from_sq(float x) {
-    const float q = x + 1e-30f;
     float r;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(q));
-    return q * r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// w max(|c_dir|, |c_mir|) added to the bound: with p = A^2+B^2+C^2+D^2 and
+// q = AB - CD, |c_dir|^2 = |(A+B) + i(C-D)|^2 = p + 2q and
+// |c_mir|^2 = |(A-B) - i(C+D)|^2 = p - 2q, so the larger is p + 2|q|
+__device__ __forceinline__ void accumulate_pair(uint32_t ua, uint32_t uc, uint32_t ud_,
+                                                uint32_t ub, float w, float& acc) {
+    const float fa = __uint_as_float(ua), fc = __uint_as_float(uc);
+    const float fd = __uint_as_float(ud_), fb = __uint_as_float(ub);
+    const float p = fmaf(fa, fa, fmaf(fb, fb, fmaf(fc, fc, fd * fd)));
+    const float q = fmaf(fa, fb, -fc * fd);
+    acc = fmaf(w, mag_from_sq(fmaf(2.0f, fabsf(q), p)), acc);
 }
 
 struct TcArgs {
@@ -316,9 +327,9 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
         const int sp = warp & 3;                 // TMEM lane quarter this warp may access
         const int qtr = (warp - 2) >> 2;         // patterns [16 qtr, 16 qtr + 16)
         const float invN = 1.0f / (float)a.N;
-        float ud[16], um[16];
+        float ud[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) ud[j] = um[j] = 0.f;
+        for (int j = 0; j < 16; ++j) ud[j] = 0.f;
         uint32_t tph[2] = {0, 0};
         int fcount = 0;
         bool ok = true;
@@ -334,39 +345,36 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
                 fence_after();
                 const float w = (f == 0 || 2 * f == a.N) ? 1.f : 2.f;
                 const uint32_t tb = tmem + ((uint32_t)(sp * 32) << 16) + buf * 256 + qtr * 16;
+                // two pieces of 8 patterns; the second piece's loads are in
+                // flight while the first is reduced
+                uint32_t A0[8], C0[8], D0[8], B0[8], A1[8], C1[8], D1[8], B1[8];
+                ACOM_TMEM_LD8(tb, A0);
+                ACOM_TMEM_LD8(tb + 64, C0);
+                ACOM_TMEM_LD8(tb + 128, D0);
+                ACOM_TMEM_LD8(tb + 192, B0);
+                ACOM_TMEM_WAIT32(A0, C0, D0, B0);
+                ACOM_TMEM_LD8(tb + 8, A1);
+                ACOM_TMEM_LD8(tb + 64 + 8, C1);
+                ACOM_TMEM_LD8(tb + 128 + 8, D1);
+                ACOM_TMEM_LD8(tb + 192 + 8, B1);
 #pragma unroll
-                for (int piece = 0; piece < 2; ++piece) {
-                    uint32_t A[8], Cc[8], D[8], B[8];
-                    ACOM_TMEM_LD8(tb + piece * 8, A);
-                    ACOM_TMEM_LD8(tb + 64 + piece * 8, Cc);
-                    ACOM_TMEM_LD8(tb + 128 + piece * 8, D);
-                    ACOM_TMEM_LD8(tb + 192 + piece * 8, B);
-                    ACOM_TMEM_WAIT32(A, Cc, D, B);
-                    if (piece == 1) {
-                        fence_before();
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(smem_u32(tempty + buf));
-                    }
+                for (int j = 0; j < 8; ++j)
+                    accumulate_pair(A0[j], C0[j], D0[j], B0[j], w, ud[j]);
+                ACOM_TMEM_WAIT32(A1, C1, D1, B1);
+                fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(tempty + buf));
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const float fa = __uint_as_float(A[j]), fc = __uint_as_float(Cc[j]);
-                        const float fd = __uint_as_float(D[j]), fb = __uint_as_float(B[j]);
-                        const float dre = fa + fb, dim = fc - fd;
-                        const float mre = fa - fb, mim = fc + fd;
-                        ud[piece * 8 + j] =
-                            fmaf(w, mag_from_sq(fmaf(dre, dre, dim * dim)), ud[piece * 8 + j]);
-                        um[piece * 8 + j] =
-                            fmaf(w, mag_from_sq(fmaf(mre, mre, mim * mim)), um[piece * 8 + j]);
-                    }
-                }
+                for (int j = 0; j < 8; ++j)
+                    accumulate_pair(A1[j], C1[j], D1[j], B1[j], w, ud[8 + j]);
             }
             if (!ok) break;
             const int z = zt * kM + sp * 32 + lane;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const int b = pt * kNP + qtr * 16 + j;
-                if (b < a.nb && z < a.Z) a.U[(int64_t)b * a.Z + z] = fmaxf(ud[j], um[j]) * invN;
-                ud[j] = um[j] = 0.f;
+                if (b < a.nb && z < a.Z) a.U[(int64_t)b * a.Z + z] = ud[j] * invN;
+                ud[j] = 0.f;
             }
         }
     }
