@@ -13,8 +13,8 @@
 //
 // CTA: one TMA producer warp, one MMA-issuing warp, sixteen epilogue warps;
 // persistent over (128-axis x 64-pattern) tiles; operands stream through a
-// 8-stage shared-memory ring (K tiles of 32 BF16 = 64-byte rows, 64-byte
-// swizzle); accumulators are double-buffered over f in 512 TMEM columns.
+// 4-stage shared-memory ring (K tiles of 64 BF16 = 128-byte rows, 128-byte
+// swizzle; the last tile of 160 shells is half zero fill); accumulators are double-buffered over f in 512 TMEM columns.
 // Every mbarrier wait is bounded: a timeout sets the device error word, stops
 // all roles, drains copies and MMAs in flight, frees TMEM and returns.
 #include <cuda.h>
@@ -29,9 +29,9 @@ namespace tc {
 
 constexpr int kM = 128;               // zone axes per tile (MMA M)
 constexpr int kNP = 64;               // patterns per tile (MMA N = 128 rows: re, im)
-constexpr int kKT = 32;               // BF16 per K tile row (64 bytes)
-constexpr int kStages = 8;
-constexpr int kTileBytes = 128 * kKT * 2;      // 8 KB
+constexpr int kKT = 64;               // BF16 per K tile row (128 bytes)
+constexpr int kStages = 4;
+constexpr int kTileBytes = 128 * kKT * 2;      // 16 KB
 constexpr int kStageBytes = 3 * kTileBytes;    // Pr, Pi, X
 constexpr int kEpiWarps = 16;
 constexpr int kThreads = (2 + kEpiWarps) * 32;
@@ -98,13 +98,13 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
-// shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups 512 B apart
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
     d |= (uint64_t)1 << 16;               // leading byte offset (unused with swizzle)
-    d |= (uint64_t)(512 >> 4) << 32;      // stride byte offset
+    d |= (uint64_t)(1024 >> 4) << 32;     // stride byte offset
     d |= (uint64_t)1 << 46;               // descriptor version
-    d |= (uint64_t)4 << 61;               // 64-byte swizzle
+    d |= (uint64_t)2 << 61;               // 128-byte swizzle
     return d;
 }
 
@@ -175,6 +175,7 @@ __device__ __forceinline__ void accumulate_pair(uint32_t ua, uint32_t uc, uint32
 struct TcArgs {
     int F, N, Z, nb, ZT, PT, KT;   // frequencies, bins, axes, patterns, axis tiles, pattern tiles, K tiles
     int PTs;                       // pattern tiles per frequency in the pattern map (row stride)
+    int Spad;                      // shells (K) in the operand rows
     int Zrows;                     // rows per frequency in the plan map (ZT * 128)
     float* U;                      // [nb][Z]
     int* err;
@@ -297,8 +298,10 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
                         }
                         fence_after();
                         const uint32_t sb = smem_u32(ring + stage * kStageBytes);
-#pragma unroll
-                        for (int k16 = 0; k16 < 2; ++k16) {
+                        // K steps of 16 inside the shells (the tail of the last
+                        // tile is TMA zero fill)
+                        const int nk16 = min(kKT, a.Spad - kt * kKT) / 16;
+                        for (int k16 = 0; k16 < nk16; ++k16) {
                             const uint64_t ar = sdesc(sb + k16 * 32);
                             const uint64_t ai = sdesc(sb + kTileBytes + k16 * 32);
                             const uint64_t bx = sdesc(sb + 2 * kTileBytes + k16 * 32);
@@ -412,8 +415,8 @@ static bool get_encoder() {
     return true;
 }
 
-// 2-D BF16 map: rows x cols (cols contiguous), boxes of 32 cols x 128 rows,
-// 64-byte swizzle.
+// 2-D BF16 map: rows x cols (cols contiguous), boxes of 64 cols x 128 rows,
+// 128-byte swizzle; boxes reaching past the last column are zero-filled.
 acom_status make_bf16_map(void* map_storage, const void* base, uint64_t rows, uint64_t cols) {
     if (!get_encoder()) return set_error(ACOM_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
     if ((cols * 2) % 16 != 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0)
@@ -425,7 +428,7 @@ acom_status make_bf16_map(void* map_storage, const void* base, uint64_t rows, ui
     const cuuint32_t estr[2] = {1, 1};
     CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
                           strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(ACOM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
     return ACOM_OK;
@@ -443,7 +446,8 @@ void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_st
     a.ZT = p->Zp / tc::kM;
     a.PT = (nb + tc::kNP - 1) / tc::kNP;
     a.PTs = pt_stride;
-    a.KT = p->Spad / tc::kKT;
+    a.KT = (p->Spad + tc::kKT - 1) / tc::kKT;
+    a.Spad = p->Spad;
     a.Zrows = p->Zp;
     a.U = U;
     a.err = p->err;
