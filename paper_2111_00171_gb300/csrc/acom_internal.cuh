@@ -53,7 +53,7 @@ struct PlanSource {            // reflections rotated into each zone-axis frame
 };
 
 struct PatternSource {         // one chunk of CSR patterns
-    void* xb;                  // optional BF16 [F][PTs][128][Spad] output
+    void* xb;                  // optional BF16 [F][PTs][128][Spad] output (16-row groups: 8 re, 8 im)
     int PTs;
     const int64_t* row_ptr;    // global row_ptr, already offset to the chunk start
     const float* qx;
@@ -73,7 +73,7 @@ struct Workspace {
     float* xnorm2 = nullptr;       // [chunk]
     float* Chat = nullptr;         // [4][F][chunk][Zp] (exhaustive mode only)
     float* U = nullptr;            // [chunk][Z] spectral bounds
-    void* XB = nullptr;            // BF16 [F][PTs][128][Spad] (tensor-core operand)
+    void* XB = nullptr;            // BF16 [F][PTs][128][Spad] (tensor-core operand, 16-row groups: 8 re, 8 im)
     int PTs = 0;                   // pattern tiles of 64 in XB
     alignas(64) unsigned char map_x[128];   // TMA map of XB
     float* xfn = nullptr;          // [chunk][F] ||X^_bf|| over shells

@@ -2,19 +2,29 @@
 // epilogue (section "Correlation Pattern Matching"; see match_prune.cu for the
 // bound).
 //
-// Per frequency f the plan spectrum (zone axes x shells, BF16) meets the
-// pattern spectra (shells x patterns, BF16) on the 5th-generation tensor cores:
-//   D1 = Pr_f [Xr_f ; Xi_f]^T   -> columns (A = Pr.Xr | C = Pr.Xi)
-//   D2 = Pi_f [Xr_f ; Xi_f]^T   -> columns (D = Pi.Xr | B = Pi.Xi)
-// with FP32 accumulation in tensor memory.  Both MMAs put a zone axis in the
-// same TMEM lane, so one epilogue thread owns all four products of its pairs
-// and accumulates w_f max(|(A+B) + i(C-D)|, |(A-B) - i(C+D)|) over f.  The
-// spectra never leave the chip; only U is written.
+// Per frequency f the pattern spectra (shells x patterns, BF16) meet the plan
+// spectra (zone axes x shells, BF16) on the 5th-generation tensor cores in one
+// MMA per 16 shells:
+//   D = X_f [Pr_f ; Pi_f]^T,  M = 128 pattern rows, N = 256 axis rows,
+// FP32 accumulation in tensor memory.  Each 16-row group of the pattern tile
+// holds the real parts of 8 patterns and then their imaginary parts, so TMEM
+// lanes L and L + 8 carry Xr and Xi of one pattern; D columns 0..127 are the
+// axes' real parts and 128..255 their imaginary parts.  A 16x256b TMEM load
+// hands one thread (Xr.Pr, Xi.Pr) of lanes (L, L + 8), and the same load 128
+// columns on gives (Xr.Pi, Xi.Pi): the four products A = Pr.Xr, C = Pr.Xi,
+// D = Pi.Xr, B = Pi.Xi of a pair meet in one thread, which accumulates
+// w_f max(|(A+B) + i(C-D)|, |(A-B) - i(C+D)|) over f.  The spectra never leave
+// the chip; only U is written.
+//
+// One N = 256 MMA per 16 shells instead of two N = 128 MMAs halves the
+// instructions the single issuing thread has to send; at N = 128 that thread,
+// not the tensor core, set the pace.
 //
 // CTA: one TMA producer warp, one MMA-issuing warp, sixteen epilogue warps;
-// persistent over (128-axis x 64-pattern) tiles; operands stream through a
+// persistent over (64-pattern x 128-axis) tiles; operands stream through a
 // 4-stage shared-memory ring (K tiles of 64 BF16 = 128-byte rows, 128-byte
-// swizzle; the last tile of 160 shells is half zero fill); accumulators are double-buffered over f in 512 TMEM columns.
+// swizzle; the last tile of 160 shells is half zero fill); accumulators are
+// double-buffered over f in 512 TMEM columns.
 // Every mbarrier wait is bounded: a timeout sets the device error word, stops
 // all roles, drains copies and MMAs in flight, frees TMEM and returns.
 #include <cuda.h>
@@ -27,19 +37,19 @@
 namespace acom {
 namespace tc {
 
-constexpr int kM = 128;               // zone axes per tile (MMA M)
-constexpr int kNP = 64;               // patterns per tile (MMA N = 128 rows: re, im)
+constexpr int kM = 128;               // zone axes per tile (MMA N = 256 rows: re, im)
+constexpr int kNP = 64;               // patterns per tile (MMA M = 128 rows: re, im)
 constexpr int kKT = 64;               // BF16 per K tile row (128 bytes)
 constexpr int kStages = 4;
 constexpr int kTileBytes = 128 * kKT * 2;      // 16 KB
-constexpr int kStageBytes = 3 * kTileBytes;    // Pr, Pi, X
+constexpr int kStageBytes = 3 * kTileBytes;    // X, then Pr and Pi as one 256-row operand
 constexpr int kEpiWarps = 16;
 constexpr int kThreads = (2 + kEpiWarps) * 32;
 constexpr uint32_t kTmemCols = 512;
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
 
-// instruction descriptor: D f32, A bf16, B bf16, both K-major, N = 128, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) |
+// instruction descriptor: D f32, A bf16, B bf16, both K-major, N = 256, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) |
                             ((128u >> 4) << 24);
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -133,22 +143,27 @@ __device__ __forceinline__ void fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-#define ACOM_TMEM_LD8(taddr, r)                                                             \
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"   \
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),  \
-                   "=r"(r[6]), "=r"(r[7])                                                   \
+// 16 TMEM lanes x 32 columns: thread t receives, for n = 0..3, lane t/4 at
+// columns 8n + 2(t%4) + {0, 1} in r[4n], r[4n+1] and lane t/4 + 8 at the same
+// columns in r[4n+2], r[4n+3]
+#define ACOM_TMEM_LD16x256_X4(taddr, r)                                                      \
+    asm volatile("tcgen05.ld.sync.aligned.16x256b.x4.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,"    \
+                 "%10,%11,%12,%13,%14,%15}, [%16];"                                          \
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),   \
+                   "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), \
+                   "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])                        \
                  : "r"(taddr))
 
 // wait for this thread's TMEM loads; the registers are tied to the wait so no
 // use can be scheduled before it
-#define ACOM_TMEM_WAIT32(a, c, d, b)                                                       \
+#define ACOM_TMEM_WAIT32(p, q)                                                             \
     asm volatile("tcgen05.wait::ld.sync.aligned;"                                          \
-                 : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), \
-                   "+r"(a[6]), "+r"(a[7]), "+r"(c[0]), "+r"(c[1]), "+r"(c[2]), "+r"(c[3]), \
-                   "+r"(c[4]), "+r"(c[5]), "+r"(c[6]), "+r"(c[7]), "+r"(d[0]), "+r"(d[1]), \
-                   "+r"(d[2]), "+r"(d[3]), "+r"(d[4]), "+r"(d[5]), "+r"(d[6]), "+r"(d[7]), \
-                   "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]), "+r"(b[4]), "+r"(b[5]), \
-                   "+r"(b[6]), "+r"(b[7])                                                  \
+                 : "+r"(p[0]), "+r"(p[1]), "+r"(p[2]), "+r"(p[3]), "+r"(p[4]), "+r"(p[5]), \
+                   "+r"(p[6]), "+r"(p[7]), "+r"(p[8]), "+r"(p[9]), "+r"(p[10]),            \
+                   "+r"(p[11]), "+r"(p[12]), "+r"(p[13]), "+r"(p[14]), "+r"(p[15]),        \
+                   "+r"(q[0]), "+r"(q[1]), "+r"(q[2]), "+r"(q[3]), "+r"(q[4]), "+r"(q[5]), \
+                   "+r"(q[6]), "+r"(q[7]), "+r"(q[8]), "+r"(q[9]), "+r"(q[10]),            \
+                   "+r"(q[11]), "+r"(q[12]), "+r"(q[13]), "+r"(q[14]), "+r"(q[15])         \
                  :                                                                         \
                  : "memory")
 
@@ -249,9 +264,9 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
                         const uint32_t fb = smem_u32(full + stage);
                         mbar_expect_tx(fb, kStageBytes);
                         unsigned char* sbuf = ring + stage * kStageBytes;
-                        tma_load_2d(smem_u32(sbuf), &map_pr, kt * kKT, prow, fb);
-                        tma_load_2d(smem_u32(sbuf + kTileBytes), &map_pi, kt * kKT, prow, fb);
-                        tma_load_2d(smem_u32(sbuf + 2 * kTileBytes), &map_x, kt * kKT, xrow, fb);
+                        tma_load_2d(smem_u32(sbuf), &map_x, kt * kKT, xrow, fb);
+                        tma_load_2d(smem_u32(sbuf + kTileBytes), &map_pr, kt * kKT, prow, fb);
+                        tma_load_2d(smem_u32(sbuf + 2 * kTileBytes), &map_pi, kt * kKT, prow, fb);
                         issued_mask |= 1u << stage;
                         last_par = (last_par & ~(1u << stage)) | (phase << stage);
                         if (++stage == kStages) {
@@ -290,7 +305,7 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
                     }
                     tph[buf] ^= 1u;
                     fence_after();
-                    const uint32_t d1 = tmem + buf * 256, d2 = d1 + 128;
+                    const uint32_t dacc = tmem + buf * 256;
                     for (int kt = 0; kt < a.KT; ++kt) {
                         if (!mbar_wait(smem_u32(full + stage), phase, abort_flag, a.err)) {
                             ok = false;
@@ -299,16 +314,14 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
                         fence_after();
                         const uint32_t sb = smem_u32(ring + stage * kStageBytes);
                         // K steps of 16 inside the shells (the tail of the last
-                        // tile is TMA zero fill)
-                        const int nk16 = min(kKT, a.Spad - kt * kKT) / 16;
-                        for (int k16 = 0; k16 < nk16; ++k16) {
-                            const uint64_t ar = sdesc(sb + k16 * 32);
-                            const uint64_t ai = sdesc(sb + kTileBytes + k16 * 32);
-                            const uint64_t bx = sdesc(sb + 2 * kTileBytes + k16 * 32);
-                            const uint32_t acc = (kt | k16) ? 1u : 0u;
-                            mma_bf16(d1, ar, bx, acc);
-                            mma_bf16(d2, ai, bx, acc);
-                        }
+                        // tile is TMA zero fill); a step of 16 BF16 moves the
+                        // descriptors' start address by 32 bytes (2 units of 16)
+                        const int nk16 = min(kKT, a.Spad - kt * kKT) >> 4;
+                        const uint64_t xa = sdesc(sb), pb = sdesc(sb + kTileBytes);
+#pragma unroll
+                        for (int k16 = 0; k16 < kKT / 16; ++k16)
+                            if (k16 < nk16)
+                                mma_bf16(dacc, xa + 2 * k16, pb + 2 * k16, (kt | k16) ? 1u : 0u);
                         mma_commit(smem_u32(empty + stage));       // frees the stage
                         if (++stage == kStages) {
                             stage = 0;
@@ -327,8 +340,8 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
         __syncwarp();
     } else {
         // ------------------------------------------------ epilogue
-        const int sp = warp & 3;                 // TMEM lane quarter this warp may access
-        const int qtr = (warp - 2) >> 2;         // patterns [16 qtr, 16 qtr + 16)
+        const int q = warp & 3;                  // TMEM lane quarter: patterns 16q .. 16q + 15
+        const int zq = (warp - 2) >> 2;          // axis columns 32 zq .. 32 zq + 31
         const float invN = 1.0f / (float)a.N;
         float ud[16];
 #pragma unroll
@@ -347,37 +360,44 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
                 tph[buf] ^= 1u;
                 fence_after();
                 const float w = (f == 0 || 2 * f == a.N) ? 1.f : 2.f;
-                const uint32_t tb = tmem + ((uint32_t)(sp * 32) << 16) + buf * 256 + qtr * 16;
-                // two pieces of 8 patterns; the second piece's loads are in
-                // flight while the first is reduced
-                uint32_t A0[8], C0[8], D0[8], B0[8], A1[8], C1[8], D1[8], B1[8];
-                ACOM_TMEM_LD8(tb, A0);
-                ACOM_TMEM_LD8(tb + 64, C0);
-                ACOM_TMEM_LD8(tb + 128, D0);
-                ACOM_TMEM_LD8(tb + 192, B0);
-                ACOM_TMEM_WAIT32(A0, C0, D0, B0);
-                ACOM_TMEM_LD8(tb + 8, A1);
-                ACOM_TMEM_LD8(tb + 64 + 8, C1);
-                ACOM_TMEM_LD8(tb + 128 + 8, D1);
-                ACOM_TMEM_LD8(tb + 192 + 8, B1);
+                const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + buf * 256 + zq * 32;
+                // two halves of 8 patterns (16 lanes each); the second half's
+                // loads are in flight while the first is reduced
+                uint32_t R0[16], I0[16], R1[16], I1[16];
+                ACOM_TMEM_LD16x256_X4(tb, R0);                          // (Xr, Xi) . Pr
+                ACOM_TMEM_LD16x256_X4(tb + 128, I0);                    // (Xr, Xi) . Pi
+                ACOM_TMEM_WAIT32(R0, I0);
+                ACOM_TMEM_LD16x256_X4(tb + (16u << 16), R1);
+                ACOM_TMEM_LD16x256_X4(tb + (16u << 16) + 128, I1);
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    accumulate_pair(A0[j], C0[j], D0[j], B0[j], w, ud[j]);
-                ACOM_TMEM_WAIT32(A1, C1, D1, B1);
+                for (int n = 0; n < 4; ++n)
+#pragma unroll
+                    for (int e = 0; e < 2; ++e)
+                        accumulate_pair(R0[4 * n + e], R0[4 * n + 2 + e], I0[4 * n + e],
+                                        I0[4 * n + 2 + e], w, ud[2 * n + e]);
+                ACOM_TMEM_WAIT32(R1, I1);
                 fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(tempty + buf));
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    accumulate_pair(A1[j], C1[j], D1[j], B1[j], w, ud[8 + j]);
+                for (int n = 0; n < 4; ++n)
+#pragma unroll
+                    for (int e = 0; e < 2; ++e)
+                        accumulate_pair(R1[4 * n + e], R1[4 * n + 2 + e], I1[4 * n + e],
+                                        I1[4 * n + 2 + e], w, ud[8 + 2 * n + e]);
             }
             if (!ok) break;
-            const int z = zt * kM + sp * 32 + lane;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int b = pt * kNP + qtr * 16 + j;
-                if (b < a.nb && z < a.Z) a.U[(int64_t)b * a.Z + z] = ud[j] * invN;
-                ud[j] = 0.f;
+            for (int h = 0; h < 2; ++h) {
+                const int b = pt * kNP + 8 * (2 * q + h) + (lane >> 2);
+#pragma unroll
+                for (int n = 0; n < 4; ++n)
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const int z = zt * kM + zq * 32 + 8 * n + 2 * (lane & 3) + e;
+                        if (b < a.nb && z < a.Z) a.U[(int64_t)b * a.Z + z] = ud[h * 8 + 2 * n + e] * invN;
+                        ud[h * 8 + 2 * n + e] = 0.f;
+                    }
             }
         }
     }

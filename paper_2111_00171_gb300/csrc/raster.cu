@@ -307,7 +307,8 @@ k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, int* err
                 fn2[f] = acc;
             }
             if (ld.xb_out()) {
-                // BF16 copy in the tensor-core tile layout: rows (re, im) of 64-pattern tiles
+                // BF16 copy in the tensor-core tile layout: 64-pattern tiles whose
+                // 16-row groups hold 8 patterns' real rows, then their imaginary rows
                 const int64_t tile = item / 64, r = item % 64;
                 for (int e = threadIdx.x; e < 2 * F; e += blockDim.x) {
                     const int f = e >> 1, c = e & 1;
@@ -315,7 +316,7 @@ k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, int* err
                     __align__(16) __nv_bfloat16 v[8];
 #pragma unroll
                     for (int w = 0; w < 8; ++w) v[w] = __float2bfloat16_rn(srcv[w * F + f]);
-                    const int64_t row = ((int64_t)f * ld.xb_tiles() + tile) * 128 + c * 64 + r;
+                    const int64_t row = ((int64_t)f * ld.xb_tiles() + tile) * 128 + (r >> 3) * 16 + c * 8 + (r & 7);
                     *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(ld.xb_out()) +
                                               row * Spad + s0) = *reinterpret_cast<uint4*>(v);
                 }
@@ -709,7 +710,9 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, RasterRa
                 fn2[f] = acc;
             }
             if (ld.xb_out()) {
-                // BF16 copy in the tensor-core tile layout: two 8-shell runs per row
+                // BF16 copy in the tensor-core tile layout (64-pattern tiles whose
+                // 16-row groups hold 8 patterns' real rows, then their imaginary
+                // rows): two 8-shell runs per row
                 const int64_t tile = item / 64, r = item % 64;
                 for (int e = threadIdx.x; e < 4 * F; e += blockDim.x) {
                     const int f = e >> 2, c = (e >> 1) & 1, hh = e & 1;
@@ -717,7 +720,7 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, RasterRa
                     __align__(16) __nv_bfloat16 v[8];
 #pragma unroll
                     for (int w = 0; w < 8; ++w) v[w] = __float2bfloat16_rn(srcv[w * F + f]);
-                    const int64_t row = ((int64_t)f * ld.xb_tiles() + tile) * 128 + c * 64 + r;
+                    const int64_t row = ((int64_t)f * ld.xb_tiles() + tile) * 128 + (r >> 3) * 16 + c * 8 + (r & 7);
                     *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(ld.xb_out()) +
                                               row * Spad + s0 + hh * 8) =
                         *reinterpret_cast<uint4*>(v);
