@@ -8,11 +8,13 @@ step is the whole path: plan build (reflections, plan raster + transform,
 normalisation) and the match of every pattern (sparse polar raster +
 transform, shell contraction, inverse transform + argmax, refinement).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32]
   python bench.py --impl reference ...   # the FP64 CPU oracle as the reference arm
 
-Under torchrun (N > 1) every rank matches its own scan (weak scaling); there is
-no collective on the data path; rank 0 prints one JSON line.
+The default precision is BF16 operands on the tensor cores for the certified
+bound, with every winner evaluated exactly in FP32.  Under torchrun (N > 1)
+every rank matches its own scan (weak scaling, scan seed + rank); there is no
+collective on the data path; rank 0 prints one JSON line.
 """
 
 import argparse
@@ -44,7 +46,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--exhaustive", action="store_true",
                     help="inverse-transform every zone axis (no certified pruning)")
@@ -197,10 +199,15 @@ def cpu_baseline(scan, gpu_res, n_sample):
         f"{agree}/{n_sample}"
 
 
+def rank_seed(rank):
+    """Scan seed of ``rank`` under weak scaling: every rank its own scan."""
+    return W["seed"] + rank
+
+
 def reference_arm(args):
-    """--impl reference: the oracle timed on the host cores."""
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    """--impl reference: the oracle timed on the host cores (rank 0 only)."""
+    from paper_2111_00171_gb300.ranks import rank_env
+    if rank_env()[1] != 0:
         return
     import synth
     from oracle import acom_oracle as O
@@ -251,10 +258,9 @@ def main():
 
     import synth
     from paper_2111_00171_gb300 import acom
+    from paper_2111_00171_gb300.ranks import barrier, max_over_ranks, rank_env
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -262,7 +268,7 @@ def main():
     prec = acom.ACOM_PREC_BF16 if args.precision == "bf16" else acom.ACOM_PREC_FP32
 
     H, Wd = (int(v) for v in args.scan.split("x"))
-    scan = synth.grain_scan(W["seed"] + rank, H=H, W=Wd)
+    scan = synth.grain_scan(rank_seed(rank), H=H, W=Wd)
     B = scan.n_patterns
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     d_in = (dev(scan.row_ptr), dev(scan.qx), dev(scan.qy), dev(scan.I))
@@ -301,8 +307,7 @@ def main():
     lib.acom_profile_enable(1)
     launches0 = lib.acom_kernel_launches()
     clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
-    if world > 1:
-        dist.barrier()
+    barrier()
     torch.cuda.synchronize()
     ev = []
     w0 = time.perf_counter()
@@ -316,24 +321,18 @@ def main():
         ev.append((e0, e1))
     torch.cuda.synchronize()
     wall = time.perf_counter() - w0
-    if world > 1:
-        dist.barrier()
+    barrier()
     ck = clocks.stop() if clocks else None
     launches = lib.acom_kernel_launches() - launches0
     lib.acom_profile_enable(0)
     prof = read_profile(lib, acom)
-    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
-    t_max = torch.tensor([dev_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    dev_ms = float(t_max.item())
+    dev_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev))
 
     # ---- e2e: host buffers through the public API, copies inside the region
     d_buf = tuple(torch.empty_like(t, device="cuda") for t in h_in)
     h_out = {k: torch.empty(out[k].shape, dtype=out[k].dtype).pin_memory() for k in out_keys}
     d2h = sum(t.numel() * t.element_size() for t in h_out.values())
-    if world > 1:
-        dist.barrier()
+    barrier()
     torch.cuda.synchronize()
     e2e_ms = 0.0
     for _ in range(args.steps):
@@ -347,11 +346,8 @@ def main():
             h_out[k].copy_(out[k], non_blocking=True)
         torch.cuda.synchronize()
         e2e_ms += (time.perf_counter() - t0) * 1e3
-    t_e = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t_e, op=dist.ReduceOp.MAX)
-        dist.barrier()
-    e2e_ms = float(t_e.item())
+    e2e_ms = max_over_ranks(e2e_ms)
+    barrier()
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -421,6 +417,14 @@ def kernel_roofline(name, cnt, ms, peaks, src, B, K, nnz):
     elif name == "contract_fp32":
         work, unit, bound, peak = 8.0 * Z * S * F * pats, "TFLOP/s", "alu", fp32_peak
         note = "8 Z S F flops per pattern; FP32 FMA peak 152 SMs x 128 lanes x 2 x max clock"
+    elif name == "select_exact":
+        # compulsory HBM bytes: each pattern's FP32 shell-major spectra read
+        # once (S x F x re/im) and the plan's FP32 spectra once per launch;
+        # the repeated reads of an axis' spectra are served by L2
+        work = (S * F * 8 * pats + Z * S * F * 8) / 1e9
+        unit, bound, peak = "GB/s", "hbm", peaks["hbm_gbs"]
+        note = (f"pattern FP32 spectra once per pattern + plan FP32 spectra once per launch; "
+                f"HBM peak ({src})")
     elif name == "raster_patterns":
         # algorithmic bytes: CSR in (8 B row pointer + 12 B per peak) and the
         # spectra out (FP32 re/im, S x F; BF16 copy when the tensor path runs)
