@@ -25,6 +25,11 @@ constexpr int kErrTooManyPeaks = 4; // more than kMaxPeaks peaks in a pattern
 constexpr int kErrTimeout = 8;      // a bounded device wait gave up
 
 // Parameters of the sparse polar raster shared by plan and pattern sources.
+// Row stride (in floats) of the shell-major spectra [item][Spad][Fs]: F
+// rounded up to a multiple of 4, so every row starts on a 16-byte boundary and
+// the exact evaluation can load four frequencies at once.  Pad entries are 0.
+__host__ __device__ inline int shell_row_stride(int F) { return (F + 3) & ~3; }
+
 struct RasterGeom {
     int S, Spad, N, F;
     float dq;          // shells q_s = (s + 1) dq
@@ -37,7 +42,7 @@ struct RasterGeom {
 struct RasterOut {
     float* re = nullptr;       // [item][F][Spad] (frequency-major rows of shells)
     float* im = nullptr;
-    float* sre = nullptr;      // [item][Spad][F] (shell-major rows of frequencies)
+    float* sre = nullptr;      // [item][Spad][Fs] (shell-major rows of frequencies, Fs = shell_row_stride(F))
     float* sim = nullptr;
     float* sumsq = nullptr;    // [item] sum of squares of the polar image
     float* fnorm = nullptr;    // [item][F] ||X^_f|| over shells
@@ -68,7 +73,7 @@ struct Workspace {
     int chunk = 0;                 // capacity in patterns
     float* Xr = nullptr;           // [chunk][F][Spad] (FP32 contraction only)
     float* Xi = nullptr;
-    float* Xsr = nullptr;          // [chunk][Spad][F] (exact evaluation)
+    float* Xsr = nullptr;          // [chunk][Spad][Fs] (exact evaluation)
     float* Xsi = nullptr;
     float* xnorm2 = nullptr;       // [chunk]
     float* Chat = nullptr;         // [4][F][chunk][Zp] (exhaustive mode only)
@@ -96,7 +101,7 @@ struct acom_plan_s {
     // device memory
     float* Pr = nullptr;              // [Zp][F][Spad], zero rows beyond Z
     float* Pi = nullptr;
-    float* Psr = nullptr;             // [Zp][Spad][F] (exact evaluation)
+    float* Psr = nullptr;             // [Zp][Spad][Fs] (exact evaluation)
     float* Psi = nullptr;
     double* za = nullptr;             // [Z][3]
     double* frames = nullptr;         // [Z][9]

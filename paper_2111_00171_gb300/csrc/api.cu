@@ -119,11 +119,15 @@ static acom_status ensure_workspace(acom_plan_s* p, int chunk, bool need_chat, b
     Workspace& ws = p->ws;
     size_t acc = 0;
     const size_t spec = (size_t)chunk * p->F * p->Spad;
+    const size_t sspec = (size_t)chunk * shell_row_stride(p->F) * p->Spad;
     cudaError_t e = cudaSuccess;
     if (need_fmajor && (e = dalloc(&ws.Xr, spec, &acc)) != cudaSuccess) goto fail;
     if (need_fmajor && (e = dalloc(&ws.Xi, spec, &acc)) != cudaSuccess) goto fail;
-    if ((e = dalloc(&ws.Xsr, spec, &acc)) != cudaSuccess) goto fail;
-    if ((e = dalloc(&ws.Xsi, spec, &acc)) != cudaSuccess) goto fail;
+    if ((e = dalloc(&ws.Xsr, sspec, &acc)) != cudaSuccess) goto fail;
+    if ((e = dalloc(&ws.Xsi, sspec, &acc)) != cudaSuccess) goto fail;
+    // the pad frequencies of the shell-major rows are read, never written
+    if ((e = cudaMemset(ws.Xsr, 0, sizeof(float) * sspec)) != cudaSuccess) goto fail;
+    if ((e = cudaMemset(ws.Xsi, 0, sizeof(float) * sspec)) != cudaSuccess) goto fail;
     if ((e = dalloc(&ws.xnorm2, (size_t)chunk, &acc)) != cudaSuccess) goto fail;
     if (need_chat &&
         (e = dalloc(&ws.Chat, (size_t)4 * p->F * chunk * p->Zp, &acc)) != cudaSuccess)
@@ -274,6 +278,7 @@ acom_status acom_plan_create(const acom_crystal* crystal, const acom_za_grid* gr
     cudaError_t e = cudaSuccess;
     acom_status s;
     const size_t pelems = (size_t)p->Zp * p->F * p->Spad;
+    const size_t selems = (size_t)p->Zp * shell_row_stride(p->F) * p->Spad;
 #define ACOM_CK(x)                                     \
     do {                                               \
         e = (x);                                       \
@@ -281,8 +286,8 @@ acom_status acom_plan_create(const acom_crystal* crystal, const acom_za_grid* gr
     } while (0)
     ACOM_CK(dalloc(&p->Pr, pelems, &p->bytes));
     ACOM_CK(dalloc(&p->Pi, pelems, &p->bytes));
-    ACOM_CK(dalloc(&p->Psr, pelems, &p->bytes));
-    ACOM_CK(dalloc(&p->Psi, pelems, &p->bytes));
+    ACOM_CK(dalloc(&p->Psr, selems, &p->bytes));
+    ACOM_CK(dalloc(&p->Psi, selems, &p->bytes));
     ACOM_CK(dalloc(&p->za, za.size(), &p->bytes));
     ACOM_CK(dalloc(&p->frames, frames.size(), &p->bytes));
     ACOM_CK(dalloc(&p->nbr_ptr, nptr.size(), &p->bytes));
@@ -291,8 +296,8 @@ acom_status acom_plan_create(const acom_crystal* crystal, const acom_za_grid* gr
     ACOM_CK(dalloc(&p->pfmax, (size_t)p->F, &p->bytes));
     ACOM_CK(cudaMemsetAsync(p->Pr, 0, sizeof(float) * pelems, st));
     ACOM_CK(cudaMemsetAsync(p->Pi, 0, sizeof(float) * pelems, st));
-    ACOM_CK(cudaMemsetAsync(p->Psr, 0, sizeof(float) * pelems, st));
-    ACOM_CK(cudaMemsetAsync(p->Psi, 0, sizeof(float) * pelems, st));
+    ACOM_CK(cudaMemsetAsync(p->Psr, 0, sizeof(float) * selems, st));
+    ACOM_CK(cudaMemsetAsync(p->Psi, 0, sizeof(float) * selems, st));
     ACOM_CK(cudaMemsetAsync(p->err, 0, sizeof(int), st));
     ACOM_CK(cudaMemcpyAsync(p->za, za.data(), sizeof(double) * za.size(), cudaMemcpyHostToDevice, st));
     ACOM_CK(cudaMemcpyAsync(p->frames, frames.data(), sizeof(double) * frames.size(),

@@ -20,6 +20,7 @@
 #include <cmath>
 
 #include "acom_internal.cuh"
+#include "fft_warp.cuh"
 
 namespace acom {
 
@@ -154,212 +155,140 @@ void launch_plan_fnorm_max(const acom_plan_s* p, float* out, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
-// Selection and exact evaluation, one CTA per pattern.  Candidate axes are
-// evaluated in batches of up to kBatch per pass over the pattern's spectrum:
-// one thread per frequency runs down the shells (spectra stored shell-major,
-// so the loads of a warp are contiguous) and accumulates the four real
-// products for every candidate of the batch.
+// Selection and exact evaluation.  Persistent CTAs take the patterns in turn.
+// The candidate axes of a pattern are evaluated in batches of up to kBatch:
+//  * spectra: thread (shell part, candidate, frequency quad) runs down its
+//    share of the pattern's non-zero shells with 16-byte loads of the
+//    shell-major rows (four frequencies at once; the pattern's rows are shared
+//    by the candidates through L1) and accumulates the four real products;
+//    the shell parts are summed in shared memory;
+//  * transform: one warp per candidate takes the inverse transform along phi3
+//    of c_dir + i c_mir (both correlations are real, so one complex transform
+//    carries both) and the argmax over (phi3, mirror);
+//  * selection: a block-wide top-K of the pending bounds, two barriers.
 // ---------------------------------------------------------------------------
-constexpr int kSelThreads = 192;
+constexpr int kSelThreads = 384;
+constexpr int kSelWarps = kSelThreads / 32;
 constexpr int kBatch = 8;
 
-struct SelSmem {
-    float* U;        // [Z] bound, replaced by the exact score once evaluated
-    uint8_t* ev;     // [Z] 0 pending, 1 evaluated, 2 in the current batch
-    float2* tw;      // [N] (cos, sin) of 2 pi i / N
-    float2* y;       // [kBatch][N] spectra c_dir + i c_mir of the batch
-    float2* tmp;     // [N] transform ping-pong
-    float* red_v;    // [32]
-    int* red_i;      // [32]
-    int* cand;       // [kBatch]
+struct SelState {
+    float T;             // best exact score so far
+    unsigned Tidx;       // (z * 2 + mirror) * N + k of the best
+    int bz, bk, bm;      // its axis, bin and mirror flag
+    int nc;              // candidates of the current main batch
+    int nref;            // candidates of the current refinement batch (a field of
+                         // its own: thread 0 fills it right after the main loop's
+                         // last barrier, while slower threads may still read nc)
+    int q;               // next neighbour to consider (refinement batches)
+    float best3[3];      // winning correlation at bins k - 1, k, k + 1
+    float Emax;          // rounding margin of the bounds
 };
 
-constexpr int kMaxRadix = 12;
-struct Radix {
-    int n;                 // number of stages (0: no factorisation, direct transform)
-    int r[kMaxRadix];      // radices 4, 2, 3, 5
+struct SelSmem {
+    float2* tw;      // [N] (cos, sin)(2 pi i / N)
+    float2* y;       // [kBatch][N] spectra of the batch, transformed in place
+    float2* yt;      // [kBatch][N] transform ping-pong (shares space with part)
+    float4* part;    // [items][4] partial (A, B, C, D) of a shell part
+    float* U;        // [Z] bound, replaced by the exact score once evaluated
+    uint8_t* ev;     // [Z] 0 pending, 1 evaluated, 2 in the current batch
+    float* wv;       // [kSelWarps][kBatch] per-warp top-K values
+    int* wi;         // [kSelWarps][kBatch] and axes
+    int* cand;       // [kBatch]
+    float* res;      // [kBatch][5] best value, its index bits, values at k - 1, k, k + 1
+    float* red;      // [kSelWarps]
+    SelState* st;
 };
 
 __device__ inline bool better(float v, unsigned i, float bv, unsigned bi) {
     return v > bv || (v == bv && i < bi);
 }
 
-// block-wide argmax of (value, index) with the lowest index on ties
-__device__ void block_argmax(float& v, unsigned& i, float* red_v, int* red_i) {
+__device__ inline void warp_argmax(float& v, unsigned& i) {
     for (int o = 16; o > 0; o >>= 1) {
-        float ov = __shfl_xor_sync(0xffffffffu, v, o);
-        unsigned oi = __shfl_xor_sync(0xffffffffu, i, o);
+        const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const unsigned oi = __shfl_xor_sync(0xffffffffu, i, o);
         if (better(ov, oi, v, i)) {
             v = ov;
             i = oi;
         }
     }
+}
+
+// The up to K pending axes (ev == 0) of largest bound with U rel + Emax >= thr,
+// in decreasing bound (ties: lowest axis), into cand and st->nc; marks them
+// ev = 2.  Each warp takes its K best by repeated argmax over entries strictly
+// below its previous pick; warp 0 merges the warps' lists the same way.
+__device__ void block_topk(SelSmem& sm, int Z, int K, float thr, float rel, float Emax) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) {
-        red_v[warp] = v;
-        red_i[warp] = (int)i;
+    float lv = CUDART_INF_F;
+    unsigned li = 0u;                       // previous pick (nothing is above it)
+    for (int r = 0; r < K; ++r) {
+        float v = -CUDART_INF_F;
+        unsigned zi = 0xffffffffu;
+        for (int z = warp * 32 + lane; z < Z; z += kSelThreads) {
+            if (sm.ev[z] != 0) continue;
+            const float u = sm.U[z];
+            if (u * rel + Emax < thr || !better(lv, li, u, (unsigned)z)) continue;
+            if (better(u, (unsigned)z, v, zi)) {
+                v = u;
+                zi = (unsigned)z;
+            }
+        }
+        warp_argmax(v, zi);
+        if (lane == 0) {
+            sm.wv[warp * kBatch + r] = v;
+            sm.wi[warp * kBatch + r] = (int)zi;
+        }
+        if (zi == 0xffffffffu) {
+            for (int r2 = r + 1 + lane; r2 < K; r2 += 32) sm.wi[warp * kBatch + r2] = -1;
+            break;
+        }
+        lv = v;
+        li = zi;
     }
     __syncthreads();
     if (warp == 0) {
-        const int nw = blockDim.x >> 5;
-        v = lane < nw ? red_v[lane] : -CUDART_INF_F;
-        i = lane < nw ? (unsigned)red_i[lane] : 0xffffffffu;
-        for (int o = 16; o > 0; o >>= 1) {
-            float ov = __shfl_xor_sync(0xffffffffu, v, o);
-            unsigned oi = __shfl_xor_sync(0xffffffffu, i, o);
-            if (better(ov, oi, v, i)) {
-                v = ov;
-                i = oi;
-            }
-        }
-        if (lane == 0) {
-            red_v[0] = v;
-            red_i[0] = (int)i;
-        }
-    }
-    __syncthreads();
-    v = red_v[0];
-    i = (unsigned)red_i[0];
-    __syncthreads();
-}
-
-// Spectra c_dir + i c_mir (both correlations are real, so one complex
-// transform carries both) of the nc candidate axes of the batch, scaled by 1/N.
-template <int KB>
-__device__ void batch_spectra(const float* __restrict__ Psr, const float* __restrict__ Psi,
-                              const float* __restrict__ Xsr, const float* __restrict__ Xsi,
-                              int64_t b, int nc, int F, int N, int s_lo, int s_hi, int Spad,
-                              SelSmem& sm) {
-    const float invN = 1.0f / (float)N;
-    const int pstride = Spad * F;
-    const float* xr = Xsr + b * (int64_t)pstride;
-    const float* xi = Xsi + b * (int64_t)pstride;
-    for (int f = threadIdx.x; f < F; f += blockDim.x) {
-        float A[KB], B[KB], C[KB], D[KB];
-        int off[KB];
-#pragma unroll
-        for (int c = 0; c < KB; ++c) {
-            A[c] = B[c] = C[c] = D[c] = 0.f;
-            off[c] = (c < nc ? sm.cand[c] : sm.cand[0]) * pstride + f;
-        }
-        // rows of shells outside [s_lo, s_hi) are zero in the pattern spectrum
-        int s = s_lo;
-        for (; s + 1 < s_hi; s += 2) {
-            const int o0 = s * F, o1 = o0 + F;
-            const float x1a = xr[o0 + f], x2a = xi[o0 + f], x1b = xr[o1 + f], x2b = xi[o1 + f];
-#pragma unroll
-            for (int c = 0; c < KB; ++c) {
-                if (c < nc) {
-                    const float p1a = Psr[off[c] + o0], p2a = Psi[off[c] + o0];
-                    const float p1b = Psr[off[c] + o1], p2b = Psi[off[c] + o1];
-                    A[c] = fmaf(p1a, x1a, fmaf(p1b, x1b, A[c]));
-                    B[c] = fmaf(p2a, x2a, fmaf(p2b, x2b, B[c]));
-                    C[c] = fmaf(p1a, x2a, fmaf(p1b, x2b, C[c]));
-                    D[c] = fmaf(p2a, x1a, fmaf(p2b, x1b, D[c]));
+        const int ne = kSelWarps * K;
+        lv = CUDART_INF_F;
+        li = 0u;
+        int n = 0;
+        for (int r = 0; r < K; ++r) {
+            float v = -CUDART_INF_F;
+            unsigned zi = 0xffffffffu;
+            for (int e = lane; e < ne; e += 32) {
+                const int w = e / K, j = e - w * K;
+                const int z = sm.wi[w * kBatch + j];
+                if (z < 0) continue;
+                const float u = sm.wv[w * kBatch + j];
+                if (better(lv, li, u, (unsigned)z) && better(u, (unsigned)z, v, zi)) {
+                    v = u;
+                    zi = (unsigned)z;
                 }
             }
-        }
-        if (s < s_hi) {
-            const int o0 = s * F;
-            const float x1 = xr[o0 + f], x2 = xi[o0 + f];
-#pragma unroll
-            for (int c = 0; c < KB; ++c) {
-                if (c < nc) {
-                    const float p1 = Psr[off[c] + o0], p2 = Psi[off[c] + o0];
-                    A[c] = fmaf(p1, x1, A[c]);
-                    B[c] = fmaf(p2, x2, B[c]);
-                    C[c] = fmaf(p1, x2, C[c]);
-                    D[c] = fmaf(p2, x1, D[c]);
-                }
+            warp_argmax(v, zi);
+            if (zi == 0xffffffffu) break;
+            if (lane == 0) {
+                sm.cand[n] = (int)zi;
+                sm.ev[zi] = 2;
             }
+            ++n;
+            lv = v;
+            li = zi;
         }
-#pragma unroll
-        for (int c = 0; c < KB; ++c) {
-            if (c < nc) {
-                const float dre = (A[c] + B[c]) * invN, dim = (C[c] - D[c]) * invN;
-                const float mre = (A[c] - B[c]) * invN, mim = -(C[c] + D[c]) * invN;
-                float2* y = sm.y + c * N;
-                y[f] = make_float2(dre - mim, dim + mre);
-                if (f > 0 && 2 * f < N) y[N - f] = make_float2(dre + mim, mre - dim);
-            }
-        }
+        if (lane == 0) sm.st->nc = n;
     }
     __syncthreads();
 }
 
-// In-place (through sm.tmp) inverse transform of y: returns the buffer that
-// holds C_dir[k] + i C_mir[k].  Stockham mixed radix when N factors into
-// 4, 2, 3, 5, otherwise direct.
-__device__ float2* inverse_transform(float2* y, int N, const Radix& rad, SelSmem& sm) {
-    float2* src = y;
-    float2* dst = sm.tmp;
-    if (rad.n > 0) {
-        int Ns = 1;
-        for (int stg = 0; stg < rad.n; ++stg) {
-            const int R = rad.r[stg];
-            const int NR = N / R;
-            const int tstep = N / (Ns * R);
-            for (int j = threadIdx.x; j < NR; j += blockDim.x) {
-                const int jm = j % Ns;
-                float2 v[5];
-#pragma unroll
-                for (int r = 0; r < 5; ++r) {
-                    if (r < R) {
-                        const float2 x = src[j + r * NR];
-                        const float2 t = sm.tw[r * jm * tstep];
-                        v[r] = make_float2(x.x * t.x - x.y * t.y, x.x * t.y + x.y * t.x);
-                    }
-                }
-                const int idxD = (j / Ns) * Ns * R + jm;
-#pragma unroll
-                for (int mo = 0; mo < 5; ++mo) {
-                    if (mo < R) {
-                        float2 o = v[0];
-#pragma unroll
-                        for (int r = 1; r < 5; ++r) {
-                            if (r < R) {
-                                const float2 t = sm.tw[((r * mo) % R) * NR];
-                                o.x = fmaf(v[r].x, t.x, fmaf(-v[r].y, t.y, o.x));
-                                o.y = fmaf(v[r].x, t.y, fmaf(v[r].y, t.x, o.y));
-                            }
-                        }
-                        dst[idxD + mo * Ns] = o;
-                    }
-                }
-            }
-            __syncthreads();
-            float2* t2 = src;
-            src = dst;
-            dst = t2;
-            Ns *= R;
-        }
-        return src;
-    }
-    for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        float2 acc = make_float2(0.f, 0.f);
-        int idx = 0;
-        for (int f = 0; f < N; ++f) {
-            const float2 x = src[f], t = sm.tw[idx];
-            acc.x = fmaf(x.x, t.x, fmaf(-x.y, t.y, acc.x));
-            acc.y = fmaf(x.x, t.y, fmaf(x.y, t.x, acc.y));
-            idx += k;
-            if (idx >= N) idx -= N;
-        }
-        dst[k] = acc;
-    }
-    __syncthreads();
-    return dst;
-}
-
-__device__ inline void matmul3d(const double* a, const double* b, double* c) {
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j)
-            c[3 * i + j] = a[3 * i] * b[j] + a[3 * i + 1] * b[3 + j] + a[3 * i + 2] * b[6 + j];
+__device__ __forceinline__ void fma4(float4& acc, const float4 p, const float4 x) {
+    acc.x = fmaf(p.x, x.x, acc.x);
+    acc.y = fmaf(p.y, x.y, acc.y);
+    acc.z = fmaf(p.z, x.z, acc.z);
+    acc.w = fmaf(p.w, x.w, acc.w);
 }
 
 struct SelectArgs {
-    const float *Psr, *Psi, *Xsr, *Xsi;   // FP32 spectra, shell-major [.][Spad][F]
+    const float *Psr, *Psi, *Xsr, *Xsi;   // FP32 spectra, shell-major [.][Spad][Fs]
     const float* U;                   // [nb][Z] bounds
     const float* xfn;                 // [nb][F] ||X^_bf||
     const int2* srange;               // [nb] non-zero shell range
@@ -371,167 +300,201 @@ struct SelectArgs {
     const int* nbr_idx;
     int Z, F, N, S, Spad, nb, refine;
     float kappa;                      // contraction rounding constant
-    Radix rad;                        // inverse-transform factorisation
+    FftRadix rad;                     // inverse-transform factorisation
     acom_result out;
     int64_t off;
     int* n_eval;                      // optional: total axes evaluated
 };
 
-// Evaluate the axes listed in sm.cand[0..nc) in full; record each exact score
-// in sm.U and fold the best into (T, Tidx, bz, bk, bm, best3).
-__device__ void evaluate_batch(const SelectArgs& a, int64_t b, int nc, SelSmem& sm, float& T,
-                               unsigned& Tidx, int& bz, int& bk, int& bm, float* best3) {
-    const int N = a.N;
-    const int2 sr = a.srange[b];
-    if (nc <= 4)
-        batch_spectra<4>(a.Psr, a.Psi, a.Xsr, a.Xsi, b, nc, a.F, N, sr.x, sr.y, a.Spad, sm);
-    else
-        batch_spectra<kBatch>(a.Psr, a.Psi, a.Xsr, a.Xsi, b, nc, a.F, N, sr.x, sr.y, a.Spad, sm);
-    for (int c = 0; c < nc; ++c) {
-        const int z = sm.cand[c];
-        const float2* y = inverse_transform(sm.y + c * N, N, a.rad, sm);
+// Spectra c_dir + i c_mir of the batch's candidate axes, scaled by 1/N, into
+// the rows y[c] (both halves of the conjugate-symmetric spectrum).
+__device__ void batch_spectra(const SelectArgs& a, int64_t b, int nc, int s_lo, int s_hi,
+                              SelSmem& sm) {
+    const int F = a.F, N = a.N, Fq = shell_row_stride(F) >> 2;
+    const int items = nc * Fq;
+    const int len = s_hi - s_lo;
+    int h = kSelThreads / items;
+    h = h < 1 ? 1 : (h > 8 ? 8 : h);
+    if (h > len) h = len > 1 ? len : 1;
+    const int total = items * h;
+    const int64_t blk = (int64_t)a.Spad * Fq;       // float4 per pattern or axis
+    const float4* xr0 = reinterpret_cast<const float4*>(a.Xsr) + b * blk;
+    const float4* xi0 = reinterpret_cast<const float4*>(a.Xsi) + b * blk;
+    for (int idx = threadIdx.x; idx < total; idx += kSelThreads) {
+        const int hh = idx / items, rem = idx - hh * items;
+        const int c = rem / Fq, fq = rem - c * Fq;
+        const int sa = s_lo + (len * hh) / h, se = s_lo + (len * (hh + 1)) / h;
+        const int64_t pb = (int64_t)sm.cand[c] * blk + fq;
+        const float4* pr = reinterpret_cast<const float4*>(a.Psr) + pb;
+        const float4* pi = reinterpret_cast<const float4*>(a.Psi) + pb;
+        const float4* xr = xr0 + fq;
+        const float4* xi = xi0 + fq;
+        float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = A, C = A, D = A;
+        int s = sa;
+        for (; s + 1 < se; s += 2) {
+            const int o0 = s * Fq, o1 = o0 + Fq;
+            const float4 x1a = __ldg(xr + o0), x2a = __ldg(xi + o0);
+            const float4 x1b = __ldg(xr + o1), x2b = __ldg(xi + o1);
+            const float4 p1a = __ldg(pr + o0), p2a = __ldg(pi + o0);
+            const float4 p1b = __ldg(pr + o1), p2b = __ldg(pi + o1);
+            fma4(A, p1a, x1a);
+            fma4(B, p2a, x2a);
+            fma4(C, p1a, x2a);
+            fma4(D, p2a, x1a);
+            fma4(A, p1b, x1b);
+            fma4(B, p2b, x2b);
+            fma4(C, p1b, x2b);
+            fma4(D, p2b, x1b);
+        }
+        if (s < se) {
+            const int o0 = s * Fq;
+            const float4 x1 = __ldg(xr + o0), x2 = __ldg(xi + o0);
+            const float4 p1 = __ldg(pr + o0), p2 = __ldg(pi + o0);
+            fma4(A, p1, x1);
+            fma4(B, p2, x2);
+            fma4(C, p1, x2);
+            fma4(D, p2, x1);
+        }
+        float4* q = sm.part + 4 * idx;
+        q[0] = A;
+        q[1] = B;
+        q[2] = C;
+        q[3] = D;
+    }
+    __syncthreads();
+    const float invN = 1.0f / (float)N;
+    for (int e = threadIdx.x; e < nc * F; e += kSelThreads) {
+        const int c = e / F, f = e - c * F, l = f & 3;
+        float A = 0.f, B = 0.f, C = 0.f, D = 0.f;
+        for (int hh = 0; hh < h; ++hh) {
+            const float* q = reinterpret_cast<const float*>(sm.part + 4 * (hh * items + c * Fq + (f >> 2)));
+            A += q[l];
+            B += q[4 + l];
+            C += q[8 + l];
+            D += q[12 + l];
+        }
+        const float dre = (A + B) * invN, dim = (C - D) * invN;
+        const float mre = (A - B) * invN, mim = -(C + D) * invN;
+        float2* y = sm.y + c * N;
+        y[f] = make_float2(dre - mim, dim + mre);
+        if (f > 0 && 2 * f < N) y[N - f] = make_float2(dre + mim, mre - dim);
+    }
+    __syncthreads();
+}
+
+// One warp per candidate: C_dir[k] + i C_mir[k] = sum_f y_f exp(2 pi i f k / N),
+// taken as the conjugate of the forward transform of conj(y); the argmax over
+// (k, mirror) with the correlation at k - 1, k, k + 1 goes to res[c].
+__device__ void batch_transforms(const SelectArgs& a, int nc, SelSmem& sm) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, N = a.N;
+    for (int c = warp; c < nc; c += kSelWarps) {
+        float2* row = sm.y + c * N;
+        float2* alt = sm.yt + c * N;
+        for (int i = lane; i < N; i += 32) row[i].y = -row[i].y;
+        __syncwarp();
+        const float2* out;
+        if (a.rad.n > 0) {
+            out = warp_fft_fixed(row, alt, N, a.rad, sm.tw, lane);
+        } else {
+            for (int k = lane; k < N; k += 32) {
+                float2 acc = make_float2(0.f, 0.f);
+                int idx = 0;
+                for (int f = 0; f < N; ++f) {
+                    const float2 t = cmul_conj(row[f], sm.tw[idx]);
+                    acc.x += t.x;
+                    acc.y += t.y;
+                    idx += k;
+                    if (idx >= N) idx -= N;
+                }
+                alt[k] = acc;
+            }
+            __syncwarp();
+            out = alt;
+        }
         float bv = -CUDART_INF_F;
         unsigned bi = 0xffffffffu;
-        for (int k = threadIdx.x; k < N; k += blockDim.x) {
-            const float2 v = y[k];
-            if (better(v.x, (unsigned)k, bv, bi)) { bv = v.x; bi = (unsigned)k; }
-            if (better(v.y, (unsigned)(N + k), bv, bi)) { bv = v.y; bi = (unsigned)(N + k); }
-        }
-        block_argmax(bv, bi, sm.red_v, sm.red_i);
-        const unsigned gidx = (unsigned)z * 2u * (unsigned)N + bi;
-        if (better(bv, gidx, T, Tidx)) {
-            T = bv;
-            Tidx = gidx;
-            bz = z;
-            bm = (int)(bi / (unsigned)N);
-            bk = (int)(bi - (unsigned)bm * N);
-            if (threadIdx.x == 0) {
-                const float2 ym = y[(bk + N - 1) % N], y0 = y[bk], yp = y[(bk + 1) % N];
-                best3[0] = bm ? ym.y : ym.x;
-                best3[1] = bm ? y0.y : y0.x;
-                best3[2] = bm ? yp.y : yp.x;
+        for (int k = lane; k < N; k += 32) {
+            const float2 v = out[k];
+            if (better(v.x, (unsigned)k, bv, bi)) {
+                bv = v.x;
+                bi = (unsigned)k;
+            }
+            if (better(-v.y, (unsigned)(N + k), bv, bi)) {
+                bv = -v.y;
+                bi = (unsigned)(N + k);
             }
         }
-        if (threadIdx.x == 0) {
+        warp_argmax(bv, bi);
+        if (lane == 0) {
+            const int m = (int)(bi / (unsigned)N), k = (int)bi - m * N;
+            const float2 ym = out[(k + N - 1) % N], y0 = out[k], yp = out[(k + 1) % N];
+            float* r = sm.res + 5 * c;
+            r[0] = bv;
+            r[1] = __uint_as_float(bi);
+            r[2] = m ? -ym.y : ym.x;
+            r[3] = m ? -y0.y : y0.x;
+            r[4] = m ? -yp.y : yp.x;
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+}
+
+// Record the batch's exact scores; with update, fold them into the best.
+__device__ void fold_batch(int nc, int N, bool update, SelSmem& sm) {
+    if (threadIdx.x == 0) {
+        SelState& st = *sm.st;
+        for (int c = 0; c < nc; ++c) {
+            const int z = sm.cand[c];
+            const float* r = sm.res + 5 * c;
+            const float bv = r[0];
+            const unsigned bi = __float_as_uint(r[1]);
+            const unsigned gidx = (unsigned)z * 2u * (unsigned)N + bi;
+            if (update && better(bv, gidx, st.T, st.Tidx)) {
+                st.T = bv;
+                st.Tidx = gidx;
+                st.bz = z;
+                st.bm = (int)(bi / (unsigned)N);
+                st.bk = (int)(bi - (unsigned)st.bm * N);
+                st.best3[0] = r[2];
+                st.best3[1] = r[3];
+                st.best3[2] = r[4];
+            }
             sm.U[z] = bv;
             sm.ev[z] = 1;
         }
-        __syncthreads();
     }
+    __syncthreads();
 }
 
-__global__ void __launch_bounds__(kSelThreads, 3) k_select_exact(SelectArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int Z = a.Z, F = a.F, N = a.N;
-    SelSmem sm;
-    sm.tw = reinterpret_cast<float2*>(smem_raw);
-    sm.y = sm.tw + N;
-    sm.tmp = sm.y + kBatch * N;
-    sm.U = reinterpret_cast<float*>(sm.tmp + N);
-    sm.red_v = sm.U + Z;
-    sm.red_i = reinterpret_cast<int*>(sm.red_v + 32);
-    sm.cand = sm.red_i + 32;
-    sm.ev = reinterpret_cast<uint8_t*>(sm.cand + kBatch);
-    __shared__ float s_best3[3];
-    __shared__ double s_w[3];
+__device__ inline void matmul3d(const double* a, const double* b, double* c) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            c[3 * i + j] = a[3 * i] * b[j] + a[3 * i + 1] * b[3 + j] + a[3 * i + 2] * b[6 + j];
+}
 
-    const int64_t b = blockIdx.x;
-    if (b >= a.nb) return;
-    for (int z = threadIdx.x; z < Z; z += blockDim.x) {
-        sm.U[z] = a.U[b * Z + z];
-        sm.ev[z] = 0;
+// Orientation of the winner (thread 0): parabolic phi3 offset, zone axis
+// refined toward the score-weighted mean of the neighbours within 0.9 of the
+// best, composed in FP64.
+__device__ __noinline__ void write_outputs(const SelectArgs& a, int64_t b, const SelSmem& sm,
+                                           bool want_ref) {
+    const SelState& st = *sm.st;
+    const int N = a.N, bz = st.bz, bk = st.bk, bm = st.bm;
+    const float T = st.T;
+    const int64_t o = a.off + b;
+    const float score = T == -CUDART_INF_F ? 0.f : T;
+    a.out.za_idx[o] = bz;
+    a.out.phi3_bin[o] = bk;
+    a.out.mirror[o] = (uint8_t)bm;
+    a.out.score[o] = score;
+    if (a.out.score_cos) {
+        const float xn = sqrtf(a.xnorm2[b]);
+        a.out.score_cos[o] = xn > 0.f ? score / xn : 0.f;
     }
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        double s, c;
-        sincospi(2.0 * (double)i / (double)N, &s, &c);
-        sm.tw[i] = make_float2((float)c, (float)s);
-    }
-    // E_b: rounding margin valid for every axis
-    float e = 0.f;
-    for (int f = threadIdx.x; f < F; f += blockDim.x) {
-        const float w = (f == 0 || 2 * f == N) ? 1.f : 2.f;
-        e = fmaf(w * a.pfmax[f], a.xfn[b * F + f], e);
-    }
-    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-    if ((threadIdx.x & 31) == 0) sm.red_v[threadIdx.x >> 5] = e;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float t = 0.f;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sm.red_v[w];
-        sm.red_v[0] = t;
-    }
-    __syncthreads();
-    const float Emax = a.kappa * sm.red_v[0] / (float)N * 1.01f;
-    const float rel = 1.0f + 1e-5f;     // FP32 accumulation of U and of the scores
-    __syncthreads();
-
-    float T = -CUDART_INF_F;            // best exact score so far
-    unsigned Tidx = 0xffffffffu;        // (z * 2 + mir) * N + k of the best
-    int bz = 0, bk = 0, bm = 0;
-    int evals = 0;
-    // batches in decreasing bound: the first takes the 4 largest bounds, later
-    // ones every axis whose bound can still reach the best exact score
-    for (int batch = 0;; ++batch) {
-        const int cap = batch == 0 ? 4 : kBatch;
-        int nc = 0;
-        while (nc < cap) {
-            float v = -CUDART_INF_F;
-            unsigned zi = 0xffffffffu;
-            for (int z = threadIdx.x; z < Z; z += blockDim.x)
-                if (sm.ev[z] == 0 && better(sm.U[z], (unsigned)z, v, zi)) {
-                    v = sm.U[z];
-                    zi = (unsigned)z;
-                }
-            block_argmax(v, zi, sm.red_v, sm.red_i);
-            if (zi == 0xffffffffu) break;
-            if (T != -CUDART_INF_F && v * rel + Emax < T) break;     // nothing left can win
-            if (threadIdx.x == 0) {
-                sm.cand[nc] = (int)zi;
-                sm.ev[zi] = 2;
-            }
-            __syncthreads();
-            ++nc;
-        }
-        if (nc == 0) break;
-        evaluate_batch(a, b, nc, sm, T, Tidx, bz, bk, bm, s_best3);
-        evals += nc;
-        // an all-zero image: every axis ties at 0 and the lowest index has won
-        if (T == 0.f && Tidx == 0u) break;
-    }
-    // zone-axis neighbours that may reach 0.9 of the best need their exact score
-    const bool want_ref = (a.out.phi3 != nullptr) || (a.out.orient != nullptr);
-    if (want_ref && a.refine && T > 0.f) {
-        int q = a.nbr_ptr[bz];
-        const int qe = a.nbr_ptr[bz + 1];
-        for (;;) {
-            int nc = 0;
-            for (; q < qe && nc < kBatch; ++q) {
-                const int z2 = a.nbr_idx[q];
-                if (sm.ev[z2] || sm.U[z2] * rel + Emax < 0.9f * T) continue;
-                if (threadIdx.x == 0) {
-                    sm.cand[nc] = z2;
-                    sm.ev[z2] = 2;
-                }
-                ++nc;
-            }
-            __syncthreads();
-            if (nc == 0) break;
-            float Tn = T;
-            unsigned Tin = Tidx;
-            int z0 = bz, k0 = bk, m0 = bm;
-            float dummy[3];
-            evaluate_batch(a, b, nc, sm, Tn, Tin, z0, k0, m0, dummy);
-            evals += nc;
-        }
-    }
-    // outputs
-    if (a.out.za_scores)
-        for (int z = threadIdx.x; z < Z; z += blockDim.x)
-            a.out.za_scores[(a.off + b) * Z + z] = sm.ev[z] ? sm.U[z] : sm.U[z] * rel + Emax;
-    if (threadIdx.x == 0 && a.n_eval) atomicAdd(a.n_eval, evals);
-    double dk = 0.0;
-    if (threadIdx.x == 0 && want_ref && a.refine) {
-        const double cm = s_best3[0], c0 = s_best3[1], cp = s_best3[2];
+    if (!want_ref) return;
+    double dk = 0.0, wref[3];
+    if (a.refine) {
+        const double cm = st.best3[0], c0 = st.best3[1], cp = st.best3[2];
         const double den = cm - 2.0 * c0 + cp;
         if (den < 0.0) {
             dk = (cm - cp) / (2.0 * den);
@@ -549,27 +512,13 @@ __global__ void __launch_bounds__(kSelThreads, 3) k_select_exact(SelectArgs a) {
             }
         }
         const double nrm = sqrt(a0 * a0 + a1 * a1 + a2 * a2);
-        s_w[0] = nrm > 0 ? a0 / nrm : a.za[3 * bz];
-        s_w[1] = nrm > 0 ? a1 / nrm : a.za[3 * bz + 1];
-        s_w[2] = nrm > 0 ? a2 / nrm : a.za[3 * bz + 2];
-    }
-    if (threadIdx.x != 0) return;
-    const int64_t o = a.off + b;
-    const float score = T == -CUDART_INF_F ? 0.f : T;
-    a.out.za_idx[o] = bz;
-    a.out.phi3_bin[o] = bk;
-    a.out.mirror[o] = (uint8_t)bm;
-    a.out.score[o] = score;
-    if (a.out.score_cos) {
-        const float xn = sqrtf(a.xnorm2[b]);
-        a.out.score_cos[o] = xn > 0.f ? score / xn : 0.f;
-    }
-    if (!want_ref) return;
-    double wref[3];
-    if (a.refine) {
-        wref[0] = s_w[0]; wref[1] = s_w[1]; wref[2] = s_w[2];
+        wref[0] = nrm > 0 ? a0 / nrm : a.za[3 * bz];
+        wref[1] = nrm > 0 ? a1 / nrm : a.za[3 * bz + 1];
+        wref[2] = nrm > 0 ? a2 / nrm : a.za[3 * bz + 2];
     } else {
-        wref[0] = a.za[3 * bz]; wref[1] = a.za[3 * bz + 1]; wref[2] = a.za[3 * bz + 2];
+        wref[0] = a.za[3 * bz];
+        wref[1] = a.za[3 * bz + 1];
+        wref[2] = a.za[3 * bz + 2];
     }
     const double phi3 = -2.0 * CUDART_PI * ((double)bk + dk) / (double)N;
     if (a.out.phi3) a.out.phi3[o] = (float)phi3;
@@ -603,22 +552,135 @@ __global__ void __launch_bounds__(kSelThreads, 3) k_select_exact(SelectArgs a) {
     for (int i = 0; i < 9; ++i) a.out.orient[9 * o + i] = (float)m2[i];
 }
 
-size_t select_smem_bytes(int Z, int N, int F) {
-    return sizeof(float2) * (kBatch + 2) * (size_t)N + sizeof(float) * ((size_t)Z + 32) +
-           sizeof(int) * (32 + kBatch) + Z + 16;
+__host__ __device__ inline size_t sel_items(int F) {
+    const int Fq = shell_row_stride(F) >> 2;
+    return (size_t)(kSelThreads > kBatch * Fq ? kSelThreads : kBatch * Fq);
 }
 
-static Radix factor_radices(int N) {
-    Radix r{};
-    int n = N;
-    const int cand[4] = {4, 2, 3, 5};
-    for (int c = 0; c < 4; ++c)
-        while (n % cand[c] == 0 && r.n < kMaxRadix) {
-            r.r[r.n++] = cand[c];
-            n /= cand[c];
+__global__ void __launch_bounds__(kSelThreads, 2) k_select_exact(SelectArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Z = a.Z, F = a.F, N = a.N;
+    SelSmem sm;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        unsigned char* p = smem_raw + off;
+        off += (bytes + 15) & ~(size_t)15;
+        return p;
+    };
+    sm.tw = reinterpret_cast<float2*>(take(sizeof(float2) * N));
+    sm.y = reinterpret_cast<float2*>(take(sizeof(float2) * kBatch * N));
+    {
+        const size_t pb = sizeof(float4) * 4 * sel_items(F), yb = sizeof(float2) * kBatch * N;
+        unsigned char* shared_area = take(pb > yb ? pb : yb);
+        sm.part = reinterpret_cast<float4*>(shared_area);
+        sm.yt = reinterpret_cast<float2*>(shared_area);
+    }
+    sm.U = reinterpret_cast<float*>(take(sizeof(float) * Z));
+    sm.wv = reinterpret_cast<float*>(take(sizeof(float) * kSelWarps * kBatch));
+    sm.wi = reinterpret_cast<int*>(take(sizeof(int) * kSelWarps * kBatch));
+    sm.cand = reinterpret_cast<int*>(take(sizeof(int) * kBatch));
+    sm.res = reinterpret_cast<float*>(take(sizeof(float) * 5 * kBatch));
+    sm.red = reinterpret_cast<float*>(take(sizeof(float) * kSelWarps));
+    sm.st = reinterpret_cast<SelState*>(take(sizeof(SelState)));
+    sm.ev = take(Z);
+
+    for (int i = threadIdx.x; i < N; i += kSelThreads) {
+        double s, c;
+        sincospi(2.0 * (double)i / (double)N, &s, &c);
+        sm.tw[i] = make_float2((float)c, (float)s);
+    }
+    const float rel = 1.0f + 1e-5f;     // FP32 accumulation of U and of the scores
+    const bool want_ref = (a.out.phi3 != nullptr) || (a.out.orient != nullptr);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    for (int64_t b = blockIdx.x; b < a.nb; b += gridDim.x) {
+        for (int z = threadIdx.x; z < Z; z += kSelThreads) {
+            sm.U[z] = a.U[b * Z + z];
+            sm.ev[z] = 0;
         }
-    if (n != 1) r.n = 0;
-    return r;
+        // E_b: rounding margin valid for every axis
+        float e = 0.f;
+        for (int f = threadIdx.x; f < F; f += kSelThreads) {
+            const float w = (f == 0 || 2 * f == N) ? 1.f : 2.f;
+            e = fmaf(w * a.pfmax[f], a.xfn[b * F + f], e);
+        }
+        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+        if (lane == 0) sm.red[warp] = e;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t = 0.f;
+            for (int w = 0; w < kSelWarps; ++w) t += sm.red[w];
+            SelState& st = *sm.st;
+            st.Emax = a.kappa * t / (float)N * 1.01f;
+            st.T = -CUDART_INF_F;
+            st.Tidx = 0xffffffffu;
+            st.bz = st.bk = st.bm = 0;
+            st.best3[0] = st.best3[1] = st.best3[2] = 0.f;
+        }
+        __syncthreads();
+        const float Emax = sm.st->Emax;
+        const int2 sr = a.srange[b];
+        int evals = 0;
+        // batches in decreasing bound: the first takes the 4 largest bounds, later
+        // ones every axis whose bound can still reach the best exact score
+        for (int batch = 0;; ++batch) {
+            const float thr = batch == 0 ? -CUDART_INF_F : sm.st->T;
+            block_topk(sm, Z, batch == 0 ? 4 : kBatch, thr, rel, Emax);
+            const int nc = sm.st->nc;
+            if (nc == 0) break;
+            batch_spectra(a, b, nc, sr.x, sr.y, sm);
+            batch_transforms(a, nc, sm);
+            fold_batch(nc, N, true, sm);
+            evals += nc;
+            // an all-zero image: every axis ties at 0 and the lowest index has won
+            if (sm.st->T == 0.f && sm.st->Tidx == 0u) break;
+        }
+        // zone-axis neighbours that may reach 0.9 of the best need their exact score
+        const float T = sm.st->T;
+        if (want_ref && a.refine && T > 0.f) {
+            const int bz = sm.st->bz;
+            const int qe = a.nbr_ptr[bz + 1];
+            if (threadIdx.x == 0) sm.st->q = a.nbr_ptr[bz];
+            for (;;) {
+                // thread 0 gathers the next batch; every thread then runs it
+                if (threadIdx.x == 0) {
+                    int q = sm.st->q, nc = 0;
+                    for (; q < qe && nc < kBatch; ++q) {
+                        const int z2 = a.nbr_idx[q];
+                        if (sm.ev[z2] || sm.U[z2] * rel + Emax < 0.9f * T) continue;
+                        sm.cand[nc++] = z2;
+                        sm.ev[z2] = 2;
+                    }
+                    sm.st->q = q;
+                    sm.st->nref = nc;
+                }
+                __syncthreads();
+                const int nc = sm.st->nref;
+                if (nc == 0) break;
+                batch_spectra(a, b, nc, sr.x, sr.y, sm);
+                batch_transforms(a, nc, sm);
+                fold_batch(nc, N, false, sm);
+                evals += nc;
+            }
+        }
+        if (a.out.za_scores)
+            for (int z = threadIdx.x; z < Z; z += kSelThreads)
+                a.out.za_scores[(a.off + b) * Z + z] = sm.ev[z] ? sm.U[z] : sm.U[z] * rel + Emax;
+        if (threadIdx.x == 0) {
+            if (a.n_eval) atomicAdd(a.n_eval, evals);
+            write_outputs(a, b, sm, want_ref);
+        }
+        __syncthreads();
+    }
+}
+
+size_t select_smem_bytes(int Z, int N, int F) {
+    auto r16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    const size_t pb = sizeof(float4) * 4 * sel_items(F), yb = sizeof(float2) * kBatch * (size_t)N;
+    return r16(sizeof(float2) * N) + r16(sizeof(float2) * kBatch * (size_t)N) + r16(pb > yb ? pb : yb) +
+           r16(sizeof(float) * Z) + 2 * r16(sizeof(float) * kSelWarps * kBatch) +
+           r16(sizeof(int) * kBatch) + r16(sizeof(float) * 5 * kBatch) +
+           r16(sizeof(float) * kSelWarps) + r16(sizeof(SelState)) + r16(Z);
 }
 
 void launch_select_exact(const acom_plan_s* p, const float* Xsr, const float* Xsi, const float* U,
@@ -629,11 +691,18 @@ void launch_select_exact(const acom_plan_s* p, const float* Xsr, const float* Xs
     SelectArgs a{p->Psr, p->Psi, Xsr, Xsi, U, xfn, srange, pfmax, xnorm2, p->za, p->frames,
                  p->nbr_ptr,
                  p->nbr_idx, p->Z, p->F, p->N, p->S, p->Spad, nb, refine, kappa,
-                 factor_radices(p->N), out, off, n_eval};
+                 fft_radices(p->N), out, off, n_eval};
     const size_t smem = select_smem_bytes(p->Z, p->N, p->F);
     cudaFuncSetAttribute(k_select_exact, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_select_exact, kSelThreads, smem);
+    int64_t grid = (int64_t)nsm * (per_sm > 0 ? per_sm : 1);
+    if (grid > nb) grid = nb;
+    if (grid <= 0) return;
     prof_begin(kKSelect, st);
-    k_select_exact<<<nb, kSelThreads, smem, st>>>(a);
+    k_select_exact<<<(int)grid, kSelThreads, smem, st>>>(a);
     prof_end(kKSelect, st);
 }
 

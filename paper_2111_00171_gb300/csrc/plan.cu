@@ -229,7 +229,7 @@ acom_status build_plan_device(acom_plan_s* p, const acom_crystal* cr, cudaStream
         launch_raster_plan(geo, src, p->Z, ro, p->err, st);
         ACOM_TRY(cudaGetLastError());
         launch_scale_rows(p->Pr, p->Pi, d_sumsq, p->Z, p->F * p->Spad, st);
-        launch_scale_rows(p->Psr, p->Psi, d_sumsq, p->Z, p->F * p->Spad, st);
+        launch_scale_rows(p->Psr, p->Psi, d_sumsq, p->Z, shell_row_stride(p->F) * p->Spad, st);
         ACOM_TRY(cudaGetLastError());
         int herr = 0;
         ACOM_TRY(cudaMemcpyAsync(&herr, p->err, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -24,6 +24,7 @@
 #include <math_constants.h>
 
 #include "acom_internal.cuh"
+#include "fft_warp.cuh"
 
 namespace acom {
 
@@ -330,11 +331,12 @@ k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, int* err
                 }
             }
             if (out.sre) {
-                const int64_t sbase = (item * (int64_t)Spad + s0) * F;
+                const int Fs = shell_row_stride(F);
+                const int64_t sbase = (item * (int64_t)Spad + s0) * Fs;
                 for (int e = threadIdx.x; e < F * W; e += blockDim.x) {
                     const int w = e / F, f = e - w * F;
-                    out.sre[sbase + (int64_t)w * F + f] = st_re[w * F + f];
-                    out.sim[sbase + (int64_t)w * F + f] = st_im[w * F + f];
+                    out.sre[sbase + (int64_t)w * Fs + f] = st_re[w * F + f];
+                    out.sim[sbase + (int64_t)w * Fs + f] = st_im[w * F + f];
                 }
             }
             __syncthreads();
@@ -394,212 +396,57 @@ static void launch_raster_nf(const RasterGeom& geo, const Loader& ld, int64_t n_
 // rows are separated by the conjugate symmetry of real transforms.
 // ---------------------------------------------------------------------------
 
-struct RasterRadix {
-    int n;
-    int r[12];
-};
-
-__device__ __forceinline__ float2 cmul_conj(float2 x, float2 t) {   // x * conj(t)
-    return make_float2(fmaf(x.x, t.x, x.y * t.y), fmaf(x.y, t.x, -x.x * t.y));
-}
-
-// forward transform of src (length N) within one warp; returns the buffer
-// holding sum_j src[j] exp(-2 pi i f j / N)
-__device__ float2* warp_fft_forward(float2* src, float2* dst, int N, const RasterRadix& rad,
-                                    const float2* __restrict__ tw, int lane) {
-    int Ns = 1;
-    for (int stg = 0; stg < rad.n; ++stg) {
-        const int R = rad.r[stg];
-        const int NR = N / R;
-        const int tstep = N / (Ns * R);
-        for (int j = lane; j < NR; j += 32) {
-            const int jq = j / Ns;
-            const int jm = j - jq * Ns;
-            float2 v[5];
-#pragma unroll
-            for (int r = 0; r < 5; ++r)
-                if (r < R) v[r] = cmul_conj(src[j + r * NR], tw[r * jm * tstep]);
-            const int idxD = jq * Ns * R + jm;
-            if (R == 4) {
-                const float2 a = make_float2(v[0].x + v[2].x, v[0].y + v[2].y);
-                const float2 b = make_float2(v[0].x - v[2].x, v[0].y - v[2].y);
-                const float2 c = make_float2(v[1].x + v[3].x, v[1].y + v[3].y);
-                const float2 d = make_float2(v[1].x - v[3].x, v[1].y - v[3].y);
-                dst[idxD] = make_float2(a.x + c.x, a.y + c.y);
-                dst[idxD + Ns] = make_float2(b.x + d.y, b.y - d.x);
-                dst[idxD + 2 * Ns] = make_float2(a.x - c.x, a.y - c.y);
-                dst[idxD + 3 * Ns] = make_float2(b.x - d.y, b.y + d.x);
-            } else if (R == 2) {
-                dst[idxD] = make_float2(v[0].x + v[1].x, v[0].y + v[1].y);
-                dst[idxD + Ns] = make_float2(v[0].x - v[1].x, v[0].y - v[1].y);
-            } else {
-#pragma unroll
-                for (int mo = 0; mo < 5; ++mo) {
-                    if (mo < R) {
-                        float2 o = v[0];
-#pragma unroll
-                        for (int r = 1; r < 5; ++r) {
-                            if (r < R) {
-                                const float2 t = cmul_conj(v[r], tw[((r * mo) % R) * NR]);
-                                o.x += t.x;
-                                o.y += t.y;
-                            }
-                        }
-                        dst[idxD + mo * Ns] = o;
-                    }
-                }
-            }
-        }
-        __syncwarp();
-        float2* t2 = src;
-        src = dst;
-        dst = t2;
-        Ns *= R;
-    }
-    return src;
-}
-
-
-// Compile-time Stockham stages for the bin counts used in practice: constant
-// strides turn the index arithmetic into multiplies and shifts.
-template <int R>
-__device__ __forceinline__ void dft_small(float2* v) {
-    if constexpr (R == 2) {
-        const float2 a = v[0], b = v[1];
-        v[0] = make_float2(a.x + b.x, a.y + b.y);
-        v[1] = make_float2(a.x - b.x, a.y - b.y);
-    } else if constexpr (R == 4) {
-        const float2 a = make_float2(v[0].x + v[2].x, v[0].y + v[2].y);
-        const float2 b = make_float2(v[0].x - v[2].x, v[0].y - v[2].y);
-        const float2 c = make_float2(v[1].x + v[3].x, v[1].y + v[3].y);
-        const float2 d = make_float2(v[1].x - v[3].x, v[1].y - v[3].y);
-        v[0] = make_float2(a.x + c.x, a.y + c.y);
-        v[1] = make_float2(b.x + d.y, b.y - d.x);
-        v[2] = make_float2(a.x - c.x, a.y - c.y);
-        v[3] = make_float2(b.x - d.y, b.y + d.x);
-    } else if constexpr (R == 3) {
-        // exp(-2 pi i / 3) = -1/2 - i sqrt(3)/2
-        const float h = 0.8660254037844386f;
-        const float2 t1 = make_float2(v[1].x + v[2].x, v[1].y + v[2].y);
-        const float2 t2 = make_float2(v[1].x - v[2].x, v[1].y - v[2].y);
-        const float2 m1 = make_float2(v[0].x - 0.5f * t1.x, v[0].y - 0.5f * t1.y);
-        v[0] = make_float2(v[0].x + t1.x, v[0].y + t1.y);
-        v[1] = make_float2(m1.x + h * t2.y, m1.y - h * t2.x);
-        v[2] = make_float2(m1.x - h * t2.y, m1.y + h * t2.x);
-    } else {
-        static_assert(R == 5, "radix");
-        // exp(-2 pi i k / 5)
-        const float c1 = 0.30901699437494745f, s1 = 0.9510565162951535f;
-        const float c2 = -0.8090169943749475f, s2 = 0.5877852522924732f;
-        const float2 a1 = make_float2(v[1].x + v[4].x, v[1].y + v[4].y);
-        const float2 b1 = make_float2(v[1].x - v[4].x, v[1].y - v[4].y);
-        const float2 a2 = make_float2(v[2].x + v[3].x, v[2].y + v[3].y);
-        const float2 b2 = make_float2(v[2].x - v[3].x, v[2].y - v[3].y);
-        const float2 x0 = v[0];
-        const float2 m1 = make_float2(x0.x + c1 * a1.x + c2 * a2.x, x0.y + c1 * a1.y + c2 * a2.y);
-        const float2 m2 = make_float2(x0.x + c2 * a1.x + c1 * a2.x, x0.y + c2 * a1.y + c1 * a2.y);
-        // -i (s1 b1 + s2 b2) and -i (s2 b1 - s1 b2)
-        const float2 n1 = make_float2(s1 * b1.x + s2 * b2.x, s1 * b1.y + s2 * b2.y);
-        const float2 n2 = make_float2(s2 * b1.x - s1 * b2.x, s2 * b1.y - s1 * b2.y);
-        v[0] = make_float2(x0.x + a1.x + a2.x, x0.y + a1.y + a2.y);
-        v[1] = make_float2(m1.x + n1.y, m1.y - n1.x);
-        v[4] = make_float2(m1.x - n1.y, m1.y + n1.x);
-        v[2] = make_float2(m2.x + n2.y, m2.y - n2.x);
-        v[3] = make_float2(m2.x - n2.y, m2.y + n2.x);
-    }
-}
-
-template <int N, int Ns, int R>
-__device__ __forceinline__ void fft_stage(const float2* __restrict__ src, float2* __restrict__ dst,
-                                          const float2* __restrict__ tw, int lane) {
-    constexpr int NR = N / R;
-    constexpr int tstep = N / (Ns * R);
-    for (int j = lane; j < NR; j += 32) {
-        const int jq = j / Ns;
-        const int jm = j - jq * Ns;
-        float2 v[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const float2 x = src[j + r * NR];
-            v[r] = (Ns == 1 || r == 0) ? x : cmul_conj(x, tw[r * jm * tstep]);
-        }
-        dft_small<R>(v);
-        const int idxD = jq * Ns * R + jm;
-#pragma unroll
-        for (int r = 0; r < R; ++r) dst[idxD + r * Ns] = v[r];
-    }
-    __syncwarp();
-}
-
-template <int N, int Ns, int R, int... Rest>
-__device__ __forceinline__ float2* fft_run(float2* src, float2* dst, const float2* tw, int lane) {
-    fft_stage<N, Ns, R>(src, dst, tw, lane);
-    if constexpr (sizeof...(Rest) == 0) {
-        return dst;
-    } else {
-        return fft_run<N, Ns * R, Rest...>(dst, src, tw, lane);
-    }
-}
-
-__device__ __forceinline__ float2* warp_fft_fixed(float2* src, float2* dst, int N,
-                                                  const RasterRadix& rad, const float2* tw,
-                                                  int lane) {
-    switch (N) {
-        case 360: return fft_run<360, 1, 4, 2, 3, 3, 5>(src, dst, tw, lane);
-        case 180: return fft_run<180, 1, 4, 3, 3, 5>(src, dst, tw, lane);
-        case 72: return fft_run<72, 1, 4, 2, 3, 3>(src, dst, tw, lane);
-        case 720: return fft_run<720, 1, 4, 4, 3, 3, 5>(src, dst, tw, lane);
-        default: return warp_fft_forward(src, dst, N, rad, tw, lane);
-    }
-}
-
-constexpr int kFftGroup = 16;   // shells per CTA pass: two per warp
+constexpr int kFftTile = 32;      // shells per BF16 staging tile: 16 pairs, two per warp
+constexpr int kFftStageWords = kFftTile / 2 + 1;   // words per staged row: 16 shell pairs + pad
+constexpr int kMaxFPerLane = 12;  // F <= 361 (N <= 720)
 
 size_t raster_fft_smem_bytes(int N, int F) {
     const int W = kRasterThreads / 32;
     size_t b = 0;
-    b += sizeof(Peak) * kMaxPeaks;           // peaks as loaded
-    b += sizeof(int) * kMaxPeaks;            // their order by radius
-    b += sizeof(float2) * N;                 // twiddles
-    b += sizeof(float2) * 2 * W * N;         // per-warp row and transform buffer
-    b += sizeof(float) * 2 * kFftGroup * F;  // staged spectra of a shell group
-    b += sizeof(float) * F;                  // per-frequency sums of |X^|^2
-    b += sizeof(int) * 64;                   // scratch
+    b += sizeof(Peak) * kMaxPeaks;                       // peaks as loaded
+    b += sizeof(int) * kMaxPeaks;                        // their order by radius
+    b += sizeof(float2) * N;                             // twiddles
+    b += sizeof(float2) * 2 * W * N;                     // per-warp row and transform buffer
+    b += sizeof(uint32_t) * 2 * F * kFftStageWords;      // BF16 staging of a shell tile
+    b += sizeof(int) * 64;                               // scratch
     return b;
 }
 
 template <class Loader>
-__global__ void __launch_bounds__(kRasterThreads)
-k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, RasterRadix rad,
+__global__ void __launch_bounds__(kRasterThreads, 2)
+k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix rad,
              int* err) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int N = geo.N, F = geo.F, S = geo.S, Spad = geo.Spad;
+    const int Fs = shell_row_stride(F);
     constexpr int W = kRasterThreads / 32;
-    constexpr int G = kFftGroup;
     Peak* sp = reinterpret_cast<Peak*>(smem);
     int* sidx = reinterpret_cast<int*>(sp + kMaxPeaks);
     float2* tw = reinterpret_cast<float2*>(sidx + kMaxPeaks);
     float2* zb = tw + N;
     float2* zt = zb + W * N;
-    float* st_re = reinterpret_cast<float*>(zt + W * N);
-    float* st_im = st_re + G * F;
-    float* fn2 = st_im + G * F;
-    int* s_int = reinterpret_cast<int*>(fn2 + F);
+    uint32_t* stage = reinterpret_cast<uint32_t*>(zt + W * N);   // [2F][kFftStageWords]
+    int* s_int = reinterpret_cast<int*>(stage + 2 * F * kFftStageWords);
+    float* scratch = reinterpret_cast<float*>(zb);     // after the last transform of an item
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        double c, s;
-        sincospi(2.0 * (double)i / (double)N, &s, &c);
-        tw[i] = make_float2((float)c, (float)s);
+        double c, sn;
+        sincospi(2.0 * (double)i / (double)N, &sn, &c);
+        tw[i] = make_float2((float)c, (float)sn);
     }
     __syncthreads();
     const float delta = geo.delta, d2 = delta * delta, inv_delta = 1.0f / delta;
     const float two_pi = 2.0f * CUDART_PI_F;
     const float dphi = two_pi / (float)N;
     const float inv_dphi = (float)N / two_pi;
+    // windows narrower than this never reach an angle offset of pi, so the
+    // offsets need no wrapping
+    const float hw_nowrap = CUDART_PI_F - 3.0f * dphi;
     const float invN = 1.0f / (float)N;
     float2* z = zb + warp * N;
     float2* zz = zt + warp * N;
+    __nv_bfloat16* xb = reinterpret_cast<__nv_bfloat16*>(ld.xb_out());
 
     for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int np = ld.load(item, sp, s_int, err);
@@ -612,154 +459,182 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, RasterRa
             }
             sidx[rank] = i;
         }
-        for (int f = threadIdx.x; f < F; f += blockDim.x) fn2[f] = 0.f;
         if (threadIdx.x == 0) {
             s_int[40] = Spad;
             s_int[41] = 0;
         }
         __syncthreads();
-        for (int s0 = 0; s0 < Spad; s0 += G) {
-            for (int j = lane; j < N; j += 32) z[j] = make_float2(0.f, 0.f);
-            __syncwarp();
-            bool any = false;
+        float fa[kMaxFPerLane];         // sum over this warp's shells of |X^_sf|^2, f = lane + 32 k
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int s = s0 + 2 * warp + h;
-                if (s >= S) continue;
-                const float qs = (float)(s + 1) * geo.dq;
-                const float qs2 = qs * qs;
-                const float rscale = geo.shell_power ? powf(qs, geo.gamma_pow) : 1.0f;
-                int lo = 0, hi = 0;
-                for (int base = 0; base < np; base += 32) {
-                    const int m = base + lane;
-                    const float r = m < np ? sp[sidx[m]].r : CUDART_INF_F;
-                    lo += __popc(__ballot_sync(0xffffffffu, r <= qs - delta));
-                    hi += __popc(__ballot_sync(0xffffffffu, r < qs + delta));
-                }
-                bool shell_any = false;
-                for (int m = lo; m < hi; ++m) {
-                    const Peak pk = sp[sidx[m]];
-                    const float dr = pk.r - qs;
-                    const float a2 = dr * dr + pk.e;
-                    if (!(a2 < d2) || pk.w == 0.f) continue;
-                    const float hw = sqrtf(d2 - a2) / qs;
-                    int jlo, cnt;
-                    if (hw >= CUDART_PI_F) {
-                        jlo = 0;
-                        cnt = N;
-                    } else {
-                        jlo = (int)floorf((pk.gam - hw) * inv_dphi) - 1;
-                        const int jhi = (int)ceilf((pk.gam + hw) * inv_dphi) + 1;
-                        cnt = min(jhi - jlo + 1, N);
+        for (int k = 0; k < kMaxFPerLane; ++k) fa[k] = 0.f;
+        int w_lo = Spad, w_hi = 0;      // this warp's non-zero shells
+
+        for (int t0 = 0; t0 < Spad; t0 += kFftTile) {
+            // pairs warp and warp + W of the tile
+            for (int pp = warp; pp < kFftTile / 2; pp += W) {
+                const int sA = t0 + 2 * pp;
+                for (int j = lane; j < N; j += 32) z[j] = make_float2(0.f, 0.f);
+                __syncwarp();
+                bool any = false;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int s = sA + h;
+                    if (s >= S) continue;
+                    const float qs = (float)(s + 1) * geo.dq;
+                    const float qs2 = qs * qs, inv_qs = 1.0f / qs;
+                    const float rscale = geo.shell_power ? powf(qs, geo.gamma_pow) : 1.0f;
+                    // peaks with |r - q_s| < delta are a contiguous run in radius order
+                    int lo = 0, hi = 0;
+                    for (int base = 0; base < np; base += 32) {
+                        const int m = base + lane;
+                        const float r = m < np ? sp[sidx[m]].r : CUDART_INF_F;
+                        lo += __popc(__ballot_sync(0xffffffffu, r <= qs - delta));
+                        hi += __popc(__ballot_sync(0xffffffffu, r < qs + delta));
                     }
-                    jlo %= N;
-                    if (jlo < 0) jlo += N;
-                    const float wgt = pk.w * rscale;
-                    for (int t = lane; t < cnt; t += 32) {
-                        int j = jlo + t;
-                        if (j >= N) j -= N;
-                        float d = (float)j * dphi - pk.gam;
-                        d -= two_pi * floorf((d + CUDART_PI_F) / two_pi);   // wrap to [-pi, pi)
-                        float sq;
-                        asm("sqrt.approx.f32 %0, %1;" : "=f"(sq) : "f"(fmaf(d * d, qs2, a2)));
-                        const float tt = 1.0f - sq * inv_delta;
-                        if (tt > 0.f) {
-                            if (h == 0) z[j].x += wgt * tt;
-                            else z[j].y += wgt * tt;
+                    bool shell_any = false;
+                    for (int m = lo; m < hi; ++m) {
+                        const Peak pk = sp[sidx[m]];
+                        const float dr = pk.r - qs;
+                        const float a2 = fmaf(dr, dr, pk.e);
+                        if (!(a2 < d2) || pk.w == 0.f) continue;
+                        const float hw = sqrtf(d2 - a2) * inv_qs;
+                        const float wgt = pk.w * rscale;
+                        shell_any = true;
+                        if (hw < hw_nowrap) {
+                            // bins jlo .. jlo + cnt - 1 around gamma; the offset of bin
+                            // jlo + t is d0 + t dphi, within (-pi, pi) by the bound on hw
+                            const int jlo = __float2int_rd((pk.gam - hw) * inv_dphi) - 1;
+                            const int jhi = __float2int_ru((pk.gam + hw) * inv_dphi) + 1;
+                            const int cnt = jhi - jlo + 1;
+                            const float d0 = fmaf((float)jlo, dphi, -pk.gam);
+                            int jw = jlo;
+                            if (jw < 0) jw += N;
+                            if (jw < 0) jw += N;
+                            for (int t = lane; t < cnt; t += 32) {
+                                int j = jw + t;
+                                if (j >= N) j -= N;
+                                const float d = fmaf((float)t, dphi, d0);
+                                float sq;
+                                asm("sqrt.approx.f32 %0, %1;" : "=f"(sq) : "f"(fmaf(d * d, qs2, a2)));
+                                const float tt = 1.0f - sq * inv_delta;
+                                if (tt > 0.f) {
+                                    if (h == 0) z[j].x += wgt * tt;
+                                    else z[j].y += wgt * tt;
+                                }
+                            }
+                        } else {
+                            // a window of (nearly) the whole circle: every bin, offsets wrapped
+                            for (int j = lane; j < N; j += 32) {
+                                float d = fmaf((float)j, dphi, -pk.gam);
+                                if (d >= CUDART_PI_F) d -= two_pi;
+                                if (d < -CUDART_PI_F) d += two_pi;
+                                float sq;
+                                asm("sqrt.approx.f32 %0, %1;" : "=f"(sq) : "f"(fmaf(d * d, qs2, a2)));
+                                const float tt = 1.0f - sq * inv_delta;
+                                if (tt > 0.f) {
+                                    if (h == 0) z[j].x += wgt * tt;
+                                    else z[j].y += wgt * tt;
+                                }
+                            }
+                        }
+                        __syncwarp();
+                    }
+                    if (shell_any) {
+                        w_lo = min(w_lo, s);
+                        w_hi = max(w_hi, s + 1);
+                    }
+                    any = any || shell_any;
+                }
+                const float2* Z = any ? warp_fft_fixed(z, zz, N, rad, tw, lane) : nullptr;
+                // real rows a (shell sA), b (shell sA + 1) from Z = FFT(a + i b):
+                //   A_f = (Z_f + conj Z_{N-f}) / 2,  B_f = -i (Z_f - conj Z_{N-f}) / 2
+                const int64_t srow = (item * (int64_t)Spad + sA) * Fs;
+                const int pw = pp;                               // word of the pair in a staged row
+#pragma unroll
+                for (int k = 0; k < kMaxFPerLane; ++k) {
+                    const int f = lane + 32 * k;
+                    if (f >= Fs) break;
+                    float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
+                    if (any && f < F) {
+                        const float2 zf = Z[f];
+                        const float2 zc = Z[f == 0 ? 0 : N - f];
+                        ar = 0.5f * (zf.x + zc.x);
+                        ai = 0.5f * (zf.y - zc.y);
+                        br = 0.5f * (zf.y + zc.y);
+                        bi = 0.5f * (zc.x - zf.x);
+                    }
+                    if (out.sre) {
+                        out.sre[srow + f] = ar;
+                        out.sim[srow + f] = ai;
+                        out.sre[srow + Fs + f] = br;
+                        out.sim[srow + Fs + f] = bi;
+                    }
+                    if (f < F) {
+                        fa[k] = fmaf(ar, ar, fmaf(ai, ai, fmaf(br, br, fmaf(bi, bi, fa[k]))));
+                        if (out.re) {
+                            const int64_t o = (item * (int64_t)F + f) * Spad + sA;
+                            out.re[o] = ar;
+                            out.re[o + 1] = br;
+                            out.im[o] = ai;
+                            out.im[o + 1] = bi;
+                        }
+                        if (xb) {
+                            const __nv_bfloat162 vr = __floats2bfloat162_rn(ar, br);
+                            const __nv_bfloat162 vi = __floats2bfloat162_rn(ai, bi);
+                            stage[f * kFftStageWords + pw] = *reinterpret_cast<const uint32_t*>(&vr);
+                            stage[(F + f) * kFftStageWords + pw] = *reinterpret_cast<const uint32_t*>(&vi);
                         }
                     }
-                    __syncwarp();
-                    shell_any = true;
                 }
-                if (shell_any && lane == 0) {
-                    atomicMin(&s_int[40], s);
-                    atomicMax(&s_int[41], s + 1);
-                }
-                any = any || shell_any;
+                __syncwarp();
             }
-            float* rA_re = st_re + (2 * warp) * F;
-            float* rA_im = st_im + (2 * warp) * F;
-            float* rB_re = rA_re + F;
-            float* rB_im = rA_im + F;
-            if (any) {
-                const float2* Z = warp_fft_fixed(z, zz, N, rad, tw, lane);
-                // real rows a, b from Z = FFT(a + i b):
-                //   A_f = (Z_f + conj Z_{N-f}) / 2,  B_f = -i (Z_f - conj Z_{N-f}) / 2
-                for (int f = lane; f < F; f += 32) {
-                    const float2 zf = Z[f];
-                    const float2 zc = Z[f == 0 ? 0 : N - f];
-                    rA_re[f] = 0.5f * (zf.x + zc.x);
-                    rA_im[f] = 0.5f * (zf.y - zc.y);
-                    rB_re[f] = 0.5f * (zf.y + zc.y);
-                    rB_im[f] = 0.5f * (zc.x - zf.x);
-                }
-            } else {
-                for (int f = lane; f < F; f += 32) {
-                    rA_re[f] = 0.f;
-                    rA_im[f] = 0.f;
-                    rB_re[f] = 0.f;
-                    rB_im[f] = 0.f;
-                }
-            }
-            __syncthreads();
-            for (int f = threadIdx.x; f < F; f += blockDim.x) {
-                float acc = fn2[f];
-                for (int w = 0; w < G; ++w)
-                    acc = fmaf(st_re[w * F + f], st_re[w * F + f],
-                               fmaf(st_im[w * F + f], st_im[w * F + f], acc));
-                fn2[f] = acc;
-            }
-            if (ld.xb_out()) {
-                // BF16 copy in the tensor-core tile layout (64-pattern tiles whose
-                // 16-row groups hold 8 patterns' real rows, then their imaginary
-                // rows): two 8-shell runs per row
+            if (xb) {
+                // the tile's BF16 copy in the tensor-core layout (64-pattern tiles whose
+                // 16-row groups hold 8 patterns' real rows, then their imaginary rows):
+                // 64 bytes (32 shells) per row
+                __syncthreads();
                 const int64_t tile = item / 64, r = item % 64;
-                for (int e = threadIdx.x; e < 4 * F; e += blockDim.x) {
-                    const int f = e >> 2, c = (e >> 1) & 1, hh = e & 1;
-                    const float* srcv = (c ? st_im : st_re) + hh * 8 * F;
-                    __align__(16) __nv_bfloat16 v[8];
-#pragma unroll
-                    for (int w = 0; w < 8; ++w) v[w] = __float2bfloat16_rn(srcv[w * F + f]);
-                    const int64_t row = ((int64_t)f * ld.xb_tiles() + tile) * 128 + (r >> 3) * 16 + c * 8 + (r & 7);
-                    *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(ld.xb_out()) +
-                                              row * Spad + s0 + hh * 8) =
-                        *reinterpret_cast<uint4*>(v);
+                const int64_t rbase = (r >> 3) * 16 + (r & 7);
+                for (int e = threadIdx.x; e < 2 * F * 4; e += blockDim.x) {
+                    const int row = e >> 2, q = e & 3;
+                    const int c = row >= F, f = row - c * F;
+                    const uint32_t* src = stage + row * kFftStageWords + 4 * q;
+                    const uint4 v = make_uint4(src[0], src[1], src[2], src[3]);
+                    const int64_t grow = ((int64_t)f * ld.xb_tiles() + tile) * 128 + rbase + c * 8;
+                    *reinterpret_cast<uint4*>(xb + grow * Spad + t0 + 8 * q) = v;
                 }
+                __syncthreads();
             }
-            if (out.re) {
-                const int64_t obase = item * (int64_t)F * Spad + s0;
-                for (int e = threadIdx.x; e < F * G; e += blockDim.x) {
-                    const int f = e / G, w = e - f * G;
-                    out.re[obase + (int64_t)f * Spad + w] = st_re[w * F + f];
-                    out.im[obase + (int64_t)f * Spad + w] = st_im[w * F + f];
-                }
-            }
-            if (out.sre) {
-                const int64_t sbase = (item * (int64_t)Spad + s0) * F;
-                for (int e = threadIdx.x; e < F * G; e += blockDim.x) {
-                    out.sre[sbase + e] = st_re[e];
-                    out.sim[sbase + e] = st_im[e];
-                }
-            }
-            __syncthreads();
         }
-        if (out.fnorm)
-            for (int f = threadIdx.x; f < F; f += blockDim.x)
-                out.fnorm[item * (int64_t)F + f] = sqrtf(fn2[f]);
+        if (w_lo < w_hi) {
+            atomicMin(&s_int[40], w_lo);
+            atomicMax(&s_int[41], w_hi);
+        }
+        __syncthreads();                 // every transform of the item is done
+#pragma unroll
+        for (int k = 0; k < kMaxFPerLane; ++k) {
+            const int f = lane + 32 * k;
+            if (f < F) scratch[warp * F + f] = fa[k];
+        }
+        __syncthreads();
+        float e = 0.f;
+        for (int f = threadIdx.x; f < F; f += blockDim.x) {
+            float fn2 = 0.f;
+            for (int w = 0; w < W; ++w) fn2 += scratch[w * F + f];
+            if (out.fnorm) out.fnorm[item * (int64_t)F + f] = sqrtf(fn2);
+            e += ((f == 0 || 2 * f == N) ? 1.f : 2.f) * fn2;
+        }
         if (threadIdx.x == 0 && out.srange) {
             const int lo = s_int[40], hi = s_int[41];
             out.srange[item] = lo < hi ? make_int2(lo, hi) : make_int2(0, 0);
         }
         if (out.sumsq) {
-            float e = 0.f;
-            for (int f = threadIdx.x; f < F; f += blockDim.x)
-                e += ((f == 0 || 2 * f == N) ? 1.f : 2.f) * fn2[f];
             for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-            if (lane == 0) st_re[warp] = e;
+            if (lane == 0) s_int[48 + warp] = __float_as_int(e);
             __syncthreads();
             if (threadIdx.x == 0) {
                 float t = 0.f;
-                for (int w = 0; w < W; ++w) t += st_re[w];
+                for (int w = 0; w < W; ++w) t += __int_as_float(s_int[48 + w]);
                 out.sumsq[item] = t * invN;
             }
         }
@@ -767,24 +642,11 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, RasterRa
     }
 }
 
-static RasterRadix raster_radices(int N) {
-    RasterRadix r{};
-    int n = N;
-    const int cand[4] = {4, 2, 3, 5};
-    for (int c = 0; c < 4; ++c)
-        while (n % cand[c] == 0 && r.n < 12) {
-            r.r[r.n++] = cand[c];
-            n /= cand[c];
-        }
-    if (n != 1) r.n = 0;
-    return r;
-}
-
 template <class Loader>
 static bool launch_raster_fft(const RasterGeom& geo, const Loader& ld, int64_t n_items,
                               const RasterOut& out, int* err, cudaStream_t st, int cls) {
-    const RasterRadix rad = raster_radices(geo.N);
-    if (rad.n == 0 || geo.Spad % kFftGroup != 0) return false;
+    const FftRadix rad = fft_radices(geo.N);
+    if (rad.n == 0 || geo.Spad % kFftTile != 0 || geo.F > 32 * kMaxFPerLane) return false;
     const size_t smem = raster_fft_smem_bytes(geo.N, geo.F);
     if (smem > 227 * 1024) return false;
     cudaFuncSetAttribute(k_raster_fft<Loader>, cudaFuncAttributeMaxDynamicSharedMemorySize,
