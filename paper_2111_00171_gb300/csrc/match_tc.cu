@@ -16,11 +16,19 @@
 // w_f max(|(A+B) + i(C-D)|, |(A-B) - i(C+D)|) over f.  The spectra never leave
 // the chip; only U is written.
 //
-// One N = 256 MMA per 16 shells instead of two N = 128 MMAs halves the
-// instructions the single issuing thread has to send; at N = 128 that thread,
-// not the tensor core, set the pace.
+// A thread issues one tcgen05.mma per ~120 cycles whatever its size, about the
+// time an M = 128, N = 256, K = 16 MMA takes on the tensor core, and every
+// barrier round trip and commit between MMAs leaves the tensor core idle.  So
+// one N = 256 MMA per 16 shells, and two issuing warps: warp 1 takes the even
+// frequencies into TMEM buffer 0, warp 2 the odd ones into buffer 1, and their
+// MMAs interleave in the tensor pipe.  Both consume stages of one operand ring
+// in the producer's order; each issuer has its own full barrier per ring slot
+// (the producer signals the stage's owner), so every full barrier has one
+// consumer and its phases are consumed in order.  A slot's empty barrier is
+// committed by the owner of each use; the producer issues the next use only
+// after that commit, so those phases are ordered too.
 //
-// CTA: one TMA producer warp, one MMA-issuing warp, sixteen epilogue warps;
+// CTA: one TMA producer warp, two MMA-issuing warps, sixteen epilogue warps;
 // persistent over (64-pattern x 128-axis) tiles; operands stream through a
 // 4-stage shared-memory ring (K tiles of 64 BF16 = 128-byte rows, 128-byte
 // swizzle; the last tile of 160 shells is half zero fill); accumulators are
@@ -44,7 +52,8 @@ constexpr int kStages = 4;
 constexpr int kTileBytes = 128 * kKT * 2;      // 16 KB
 constexpr int kStageBytes = 3 * kTileBytes;    // X, then Pr and Pi as one 256-row operand
 constexpr int kEpiWarps = 16;
-constexpr int kThreads = (2 + kEpiWarps) * 32;
+constexpr int kIssuers = 2;                    // MMA-issuing warps, one per TMEM buffer
+constexpr int kThreads = (1 + kIssuers + kEpiWarps) * 32;
 constexpr uint32_t kTmemCols = 512;
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
 
@@ -206,25 +215,23 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char* ring = base;
     uint64_t* bars = reinterpret_cast<uint64_t*>(ring + kStages * kStageBytes);
-    uint64_t* full = bars;                      // [kStages]
-    uint64_t* empty = bars + kStages;           // [kStages]
-    uint64_t* tfull = bars + 2 * kStages;       // [2]
-    uint64_t* tempty = tfull + 2;               // [2]
-    uint64_t* drain = tempty + 2;               // [1]
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    uint64_t* full = bars;                      // [kIssuers][kStages]
+    uint64_t* empty = bars + kIssuers * kStages;   // [kStages]
+    uint64_t* tfull = empty + kStages;          // [kIssuers]
+    uint64_t* tempty = tfull + kIssuers;        // [kIssuers]
+    uint64_t* drain = tempty + kIssuers;        // [kIssuers]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + kIssuers);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
-            mbar_init(smem_u32(full + s), 1);
-            mbar_init(smem_u32(empty + s), 1);
-        }
-        for (int b = 0; b < 2; ++b) {
+        for (int s = 0; s < kIssuers * kStages; ++s) mbar_init(smem_u32(full + s), 1);
+        for (int s = 0; s < kStages; ++s) mbar_init(smem_u32(empty + s), 1);
+        for (int b = 0; b < kIssuers; ++b) {
             mbar_init(smem_u32(tfull + b), 1);
             mbar_init(smem_u32(tempty + b), kEpiWarps);
+            mbar_init(smem_u32(drain + b), 1);
         }
-        mbar_init(smem_u32(drain), 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_pr)));
@@ -249,26 +256,34 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
         if (lane == 0) {
             int stage = 0;
             uint32_t phase = 0;
-            uint32_t issued_mask = 0, last_par = 0;
+            // per issuer and slot: the parity of the owner's next full phase;
+            // the last stage issued into each slot and its owner, for the drain
+            uint32_t fpar[kIssuers] = {0u, 0u};
+            uint32_t issued_mask = 0, last_par = 0, last_own = 0;
+            int fcount = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
                 const int zt = t % a.ZT, pt = t / a.ZT;
-                for (int f = 0; f < a.F && ok; ++f) {
+                for (int f = 0; f < a.F && ok; ++f, ++fcount) {
                     const int prow = f * a.Zrows + zt * kM;
                     const int xrow = (f * a.PTs + pt) * 128;
+                    const int own = fcount & 1;
                     for (int kt = 0; kt < a.KT; ++kt) {
                         if (!mbar_wait(smem_u32(empty + stage), phase ^ 1u, abort_flag, a.err)) {
                             ok = false;
                             break;
                         }
-                        const uint32_t fb = smem_u32(full + stage);
+                        const uint32_t fb = smem_u32(full + own * kStages + stage);
                         mbar_expect_tx(fb, kStageBytes);
                         unsigned char* sbuf = ring + stage * kStageBytes;
                         tma_load_2d(smem_u32(sbuf), &map_x, kt * kKT, xrow, fb);
                         tma_load_2d(smem_u32(sbuf + kTileBytes), &map_pr, kt * kKT, prow, fb);
                         tma_load_2d(smem_u32(sbuf + 2 * kTileBytes), &map_pi, kt * kKT, prow, fb);
                         issued_mask |= 1u << stage;
-                        last_par = (last_par & ~(1u << stage)) | (phase << stage);
+                        const uint32_t par = (fpar[own] >> stage) & 1u;
+                        last_par = (last_par & ~(1u << stage)) | (par << stage);
+                        last_own = (last_own & ~(1u << stage)) | ((uint32_t)own << stage);
+                        fpar[own] ^= 1u << stage;
                         if (++stage == kStages) {
                             stage = 0;
                             phase ^= 1u;
@@ -281,36 +296,48 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
                 for (int s = 0; s < kStages; ++s)
                     if (issued_mask & (1u << s)) {
                         const uint32_t par = (last_par >> s) & 1u;
+                        const int own = (last_own >> s) & 1u;
                         const long long t0 = clock64();
-                        while (!mbar_try(smem_u32(full + s), par) && clock64() - t0 < kWaitCycles) {
+                        while (!mbar_try(smem_u32(full + own * kStages + s), par) &&
+                               clock64() - t0 < kWaitCycles) {
                         }
                     }
             }
         }
         __syncwarp();
-    } else if (warp == 1) {
-        // ------------------------------------------------ MMA issuer
+    } else if (warp <= kIssuers) {
+        // ------------------------------------------------ MMA issuers
+        // issuer mi takes the frequencies with fcount % 2 == mi into TMEM
+        // buffer mi; it walks the ring in the producer's order and waits only
+        // on its own full barriers
+        const int mi = warp - 1;
         if (lane == 0) {
             int stage = 0;
-            uint32_t phase = 0;
-            uint32_t tph[2] = {0, 0};
+            uint32_t fpar = 0;           // bit s: parity of this issuer's next phase of slot s
+            uint32_t tph = 0;
             int fcount = 0;
             bool ok = true;
+            uint64_t* myfull = full + mi * kStages;
             for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
                 for (int f = 0; f < a.F && ok; ++f, ++fcount) {
-                    const int buf = fcount & 1;
-                    if (!mbar_wait(smem_u32(tempty + buf), tph[buf] ^ 1u, abort_flag, a.err)) {
+                    if ((fcount & 1) != mi) {
+                        stage = (stage + a.KT) % kStages;
+                        continue;
+                    }
+                    if (!mbar_wait(smem_u32(tempty + mi), tph ^ 1u, abort_flag, a.err)) {
                         ok = false;
                         break;
                     }
-                    tph[buf] ^= 1u;
+                    tph ^= 1u;
                     fence_after();
-                    const uint32_t dacc = tmem + buf * 256;
+                    const uint32_t dacc = tmem + mi * 256;
                     for (int kt = 0; kt < a.KT; ++kt) {
-                        if (!mbar_wait(smem_u32(full + stage), phase, abort_flag, a.err)) {
+                        if (!mbar_wait(smem_u32(myfull + stage), (fpar >> stage) & 1u, abort_flag,
+                                       a.err)) {
                             ok = false;
                             break;
                         }
+                        fpar ^= 1u << stage;
                         fence_after();
                         const uint32_t sb = smem_u32(ring + stage * kStageBytes);
                         // K steps of 16 inside the shells (the tail of the last
@@ -323,25 +350,22 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
                             if (k16 < nk16)
                                 mma_bf16(dacc, xa + 2 * k16, pb + 2 * k16, (kt | k16) ? 1u : 0u);
                         mma_commit(smem_u32(empty + stage));       // frees the stage
-                        if (++stage == kStages) {
-                            stage = 0;
-                            phase ^= 1u;
-                        }
+                        if (++stage == kStages) stage = 0;
                     }
-                    if (ok) mma_commit(smem_u32(tfull + buf));     // accumulators ready
+                    if (ok) mma_commit(smem_u32(tfull + mi));     // accumulators ready
                 }
             }
             // all MMAs issued by this thread complete before TMEM is released
-            mma_commit(smem_u32(drain));
+            mma_commit(smem_u32(drain + mi));
             const long long t0 = clock64();
-            while (!mbar_try(smem_u32(drain), 0) && clock64() - t0 < kWaitCycles) {
+            while (!mbar_try(smem_u32(drain + mi), 0) && clock64() - t0 < kWaitCycles) {
             }
         }
         __syncwarp();
     } else {
         // ------------------------------------------------ epilogue
         const int q = warp & 3;                  // TMEM lane quarter: patterns 16q .. 16q + 15
-        const int zq = (warp - 2) >> 2;          // axis columns 32 zq .. 32 zq + 31
+        const int zq = (warp - 1 - kIssuers) >> 2;   // axis columns 32 zq .. 32 zq + 31
         const float invN = 1.0f / (float)a.N;
         float ud[16];
 #pragma unroll
@@ -412,7 +436,8 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
 }
 
 size_t tc_smem_bytes() {
-    return 1024 + (size_t)kStages * kStageBytes + 8 * (2 * kStages + 5) + 16;
+    return 1024 + (size_t)kStages * kStageBytes + 8 * ((kIssuers + 1) * kStages + 3 * kIssuers) +
+           16;
 }
 
 }  // namespace tc
