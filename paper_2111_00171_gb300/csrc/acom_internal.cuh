@@ -30,6 +30,11 @@ constexpr int kErrTimeout = 8;      // a bounded device wait gave up
 // the exact evaluation can load four frequencies at once.  Pad entries are 0.
 __host__ __device__ inline int shell_row_stride(int F) { return (F + 3) & ~3; }
 
+// Device memory of plans and match workspaces: stream-ordered allocations from
+// one pool per device that keeps freed blocks for reuse (api.cu).
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t st);
+void pool_free(void* p, cudaStream_t st);
+
 struct RasterGeom {
     int S, Spad, N, F;
     float dq;          // shells q_s = (s + 1) dq

@@ -2,6 +2,7 @@
 // (host FP64), plan ownership, and the chunked match loop.
 #include <cmath>
 #include <cstdio>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -84,69 +85,110 @@ static void za_frame(const double* w, double* R) {
     R[6] = 0;  R[7] = -s2;      R[8] = c2;
 }
 
+// One pool per device; freed blocks stay in it (up to kPoolKeepBytes) so that
+// a plan built per scan, and its workspace, reuse memory instead of paying for
+// cudaMalloc and cudaFree every time.
+constexpr uint64_t kPoolKeepBytes = 32ull << 30;
+constexpr int kMaxDevices = 64;
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[kMaxDevices];
+
+static cudaMemPool_t device_pool() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
+        uint64_t keep = kPoolKeepBytes;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pool[dev] = pool;
+    }
+    return g_pool[dev];
+}
+
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t st) {
+    *p = nullptr;
+    cudaMemPool_t pool = device_pool();
+    if (!pool) return cudaErrorMemoryAllocation;
+    return cudaMallocFromPoolAsync(p, bytes ? bytes : 1, pool, st);
+}
+
+void pool_free(void* p, cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
+}
+
 template <class T>
-static cudaError_t dalloc(T** p, size_t n, size_t* acc) {
-    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (n ? n : 1));
-    if (e == cudaSuccess) *acc += sizeof(T) * (n ? n : 1);
+static cudaError_t dalloc(T** p, size_t n, size_t* acc, cudaStream_t st) {
+    const size_t b = sizeof(T) * (n ? n : 1);
+    cudaError_t e = pool_alloc(reinterpret_cast<void**>(p), b, st);
+    if (e == cudaSuccess) *acc += b;
     return e;
 }
 
-static void free_workspace(Workspace& ws) {
-    cudaFree(ws.Xr);
-    cudaFree(ws.Xi);
-    cudaFree(ws.Xsr);
-    cudaFree(ws.Xsi);
-    cudaFree(ws.xnorm2);
-    cudaFree(ws.Chat);
-    cudaFree(ws.U);
-    cudaFree(ws.xfn);
-    cudaFree(ws.n_eval);
-    cudaFree(ws.srange);
-    cudaFree(ws.best);
-    cudaFree(ws.za_scores);
-    cudaFree(ws.XB);
+static void free_workspace(Workspace& ws, cudaStream_t st) {
+    pool_free(ws.Xr, st);
+    pool_free(ws.Xi, st);
+    pool_free(ws.Xsr, st);
+    pool_free(ws.Xsi, st);
+    pool_free(ws.xnorm2, st);
+    pool_free(ws.Chat, st);
+    pool_free(ws.U, st);
+    pool_free(ws.xfn, st);
+    pool_free(ws.n_eval, st);
+    pool_free(ws.srange, st);
+    pool_free(ws.best, st);
+    pool_free(ws.za_scores, st);
+    pool_free(ws.XB, st);
     ws = Workspace{};
 }
 
 // need_fmajor: the frequency-major pattern spectra (FP32 contraction, export)
-static acom_status ensure_workspace(acom_plan_s* p, int chunk, bool need_chat, bool need_fmajor) {
+static acom_status ensure_workspace(acom_plan_s* p, int chunk, bool need_chat, bool need_fmajor,
+                                    cudaStream_t st) {
     if (p->ws.chunk >= chunk && (!need_chat || p->ws.Chat) && (!need_fmajor || p->ws.Xr))
         return ACOM_OK;
     need_chat = need_chat || p->ws.Chat;
     need_fmajor = need_fmajor || need_chat || p->ws.Xr;
     if (p->ws.chunk > chunk) chunk = p->ws.chunk;
-    free_workspace(p->ws);
+    free_workspace(p->ws, st);
     Workspace& ws = p->ws;
     size_t acc = 0;
     const size_t spec = (size_t)chunk * p->F * p->Spad;
     const size_t sspec = (size_t)chunk * shell_row_stride(p->F) * p->Spad;
     cudaError_t e = cudaSuccess;
-    if (need_fmajor && (e = dalloc(&ws.Xr, spec, &acc)) != cudaSuccess) goto fail;
-    if (need_fmajor && (e = dalloc(&ws.Xi, spec, &acc)) != cudaSuccess) goto fail;
-    if ((e = dalloc(&ws.Xsr, sspec, &acc)) != cudaSuccess) goto fail;
-    if ((e = dalloc(&ws.Xsi, sspec, &acc)) != cudaSuccess) goto fail;
-    // the pad frequencies of the shell-major rows are read, never written
-    if ((e = cudaMemset(ws.Xsr, 0, sizeof(float) * sspec)) != cudaSuccess) goto fail;
-    if ((e = cudaMemset(ws.Xsi, 0, sizeof(float) * sspec)) != cudaSuccess) goto fail;
-    if ((e = dalloc(&ws.xnorm2, (size_t)chunk, &acc)) != cudaSuccess) goto fail;
+    // Every raster writes whole rows of its layouts (the pad frequencies of the
+    // shell-major rows as zeros; every shell of the BF16 tiles), so nothing here
+    // needs clearing.  Rows of the BF16 tiles past the last pattern of a chunk
+    // keep stale values: each MMA row depends on its own pattern row only, and
+    // those patterns' bounds are never written.
+    if (need_fmajor && (e = dalloc(&ws.Xr, spec, &acc, st)) != cudaSuccess) goto fail;
+    if (need_fmajor && (e = dalloc(&ws.Xi, spec, &acc, st)) != cudaSuccess) goto fail;
+    if ((e = dalloc(&ws.Xsr, sspec, &acc, st)) != cudaSuccess) goto fail;
+    if ((e = dalloc(&ws.Xsi, sspec, &acc, st)) != cudaSuccess) goto fail;
+    if ((e = dalloc(&ws.xnorm2, (size_t)chunk, &acc, st)) != cudaSuccess) goto fail;
     if (need_chat &&
-        (e = dalloc(&ws.Chat, (size_t)4 * p->F * chunk * p->Zp, &acc)) != cudaSuccess)
+        (e = dalloc(&ws.Chat, (size_t)4 * p->F * chunk * p->Zp, &acc, st)) != cudaSuccess)
         goto fail;
-    if ((e = dalloc(&ws.U, (size_t)chunk * p->Z, &acc)) != cudaSuccess) goto fail;
-    if ((e = dalloc(&ws.xfn, (size_t)chunk * p->F, &acc)) != cudaSuccess) goto fail;
-    if ((e = dalloc(&ws.n_eval, (size_t)1, &acc)) != cudaSuccess) goto fail;
-    if ((e = dalloc(&ws.srange, (size_t)chunk, &acc)) != cudaSuccess) goto fail;
-    if ((e = dalloc(&ws.best, (size_t)chunk, &acc)) != cudaSuccess) goto fail;
-    if ((e = dalloc(&ws.za_scores, (size_t)chunk * p->Z, &acc)) != cudaSuccess) goto fail;
+    if ((e = dalloc(&ws.U, (size_t)chunk * p->Z, &acc, st)) != cudaSuccess) goto fail;
+    if ((e = dalloc(&ws.xfn, (size_t)chunk * p->F, &acc, st)) != cudaSuccess) goto fail;
+    if ((e = dalloc(&ws.n_eval, (size_t)1, &acc, st)) != cudaSuccess) goto fail;
+    if ((e = dalloc(&ws.srange, (size_t)chunk, &acc, st)) != cudaSuccess) goto fail;
+    if ((e = dalloc(&ws.best, (size_t)chunk, &acc, st)) != cudaSuccess) goto fail;
+    if ((e = dalloc(&ws.za_scores, (size_t)chunk * p->Z, &acc, st)) != cudaSuccess) goto fail;
     if (p->precision == ACOM_PREC_BF16) {
         ws.PTs = (chunk + 63) / 64;
         const size_t rows = (size_t)p->F * ws.PTs * 128;
-        if ((e = cudaMalloc(&ws.XB, rows * p->Spad * 2)) != cudaSuccess) goto fail;
+        if ((e = pool_alloc(&ws.XB, rows * p->Spad * 2, st)) != cudaSuccess) goto fail;
         acc += rows * p->Spad * 2;
-        if ((e = cudaMemset(ws.XB, 0, rows * p->Spad * 2)) != cudaSuccess) goto fail;
         acom_status ms = make_bf16_map(ws.map_x, ws.XB, rows, (uint64_t)p->Spad);
         if (ms != ACOM_OK) {
-            free_workspace(p->ws);
+            free_workspace(p->ws, st);
             return ms;
         }
     }
@@ -154,27 +196,30 @@ static acom_status ensure_workspace(acom_plan_s* p, int chunk, bool need_chat, b
     ws.bytes = acc;
     return ACOM_OK;
 fail:
-    free_workspace(p->ws);
+    free_workspace(p->ws, st);
     return cuda_error(e, "match workspace allocation");
 }
 
+// Every library call has synchronised its stream before returning, so the
+// plan's memory goes back to the pool in the order of the default stream.
 static void destroy_plan(acom_plan_s* p) {
     if (!p) return;
-    free_workspace(p->ws);
-    cudaFree(p->Pr);
-    cudaFree(p->Pi);
-    cudaFree(p->Psr);
-    cudaFree(p->Psi);
-    cudaFree(p->za);
-    cudaFree(p->frames);
-    cudaFree(p->nbr_ptr);
-    cudaFree(p->nbr_idx);
-    cudaFree(p->refl_g);
-    cudaFree(p->refl_amp);
-    cudaFree(p->err);
-    cudaFree(p->pfmax);
-    cudaFree(p->Pb_r);
-    cudaFree(p->Pb_i);
+    const cudaStream_t st = 0;
+    free_workspace(p->ws, st);
+    pool_free(p->Pr, st);
+    pool_free(p->Pi, st);
+    pool_free(p->Psr, st);
+    pool_free(p->Psi, st);
+    pool_free(p->za, st);
+    pool_free(p->frames, st);
+    pool_free(p->nbr_ptr, st);
+    pool_free(p->nbr_idx, st);
+    pool_free(p->refl_g, st);
+    pool_free(p->refl_amp, st);
+    pool_free(p->err, st);
+    pool_free(p->pfmax, st);
+    pool_free(p->Pb_r, st);
+    pool_free(p->Pb_i, st);
     delete p;
 }
 
@@ -284,16 +329,16 @@ acom_status acom_plan_create(const acom_crystal* crystal, const acom_za_grid* gr
         e = (x);                                       \
         if (e != cudaSuccess) goto cuda_fail;          \
     } while (0)
-    ACOM_CK(dalloc(&p->Pr, pelems, &p->bytes));
-    ACOM_CK(dalloc(&p->Pi, pelems, &p->bytes));
-    ACOM_CK(dalloc(&p->Psr, selems, &p->bytes));
-    ACOM_CK(dalloc(&p->Psi, selems, &p->bytes));
-    ACOM_CK(dalloc(&p->za, za.size(), &p->bytes));
-    ACOM_CK(dalloc(&p->frames, frames.size(), &p->bytes));
-    ACOM_CK(dalloc(&p->nbr_ptr, nptr.size(), &p->bytes));
-    ACOM_CK(dalloc(&p->nbr_idx, nidx.size(), &p->bytes));
-    ACOM_CK(dalloc(&p->err, 1, &p->bytes));
-    ACOM_CK(dalloc(&p->pfmax, (size_t)p->F, &p->bytes));
+    ACOM_CK(dalloc(&p->Pr, pelems, &p->bytes, st));
+    ACOM_CK(dalloc(&p->Pi, pelems, &p->bytes, st));
+    ACOM_CK(dalloc(&p->Psr, selems, &p->bytes, st));
+    ACOM_CK(dalloc(&p->Psi, selems, &p->bytes, st));
+    ACOM_CK(dalloc(&p->za, za.size(), &p->bytes, st));
+    ACOM_CK(dalloc(&p->frames, frames.size(), &p->bytes, st));
+    ACOM_CK(dalloc(&p->nbr_ptr, nptr.size(), &p->bytes, st));
+    ACOM_CK(dalloc(&p->nbr_idx, nidx.size(), &p->bytes, st));
+    ACOM_CK(dalloc(&p->err, 1, &p->bytes, st));
+    ACOM_CK(dalloc(&p->pfmax, (size_t)p->F, &p->bytes, st));
     ACOM_CK(cudaMemsetAsync(p->Pr, 0, sizeof(float) * pelems, st));
     ACOM_CK(cudaMemsetAsync(p->Pi, 0, sizeof(float) * pelems, st));
     ACOM_CK(cudaMemsetAsync(p->Psr, 0, sizeof(float) * selems, st));
@@ -315,8 +360,8 @@ acom_status acom_plan_create(const acom_crystal* crystal, const acom_za_grid* gr
     ACOM_CK(cudaGetLastError());
     if (p->precision == ACOM_PREC_BF16) {
         const size_t n = (size_t)p->F * p->Zp * p->Spad;
-        ACOM_CK(cudaMalloc(&p->Pb_r, n * 2));
-        ACOM_CK(cudaMalloc(&p->Pb_i, n * 2));
+        ACOM_CK(pool_alloc(&p->Pb_r, n * 2, st));
+        ACOM_CK(pool_alloc(&p->Pb_i, n * 2, st));
         p->bytes += 4 * n;
         launch_plan_to_bf16(p->Pr, p->Zp, p->F, p->Spad, p->Pb_r, st);
         launch_plan_to_bf16(p->Pi, p->Zp, p->F, p->Spad, p->Pb_i, st);
@@ -410,7 +455,7 @@ acom_status acom_polar_spectra(acom_plan p, const acom_peaks_csr* peaks, float* 
     if (B == 0) return ACOM_OK;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const int chunk = (int)std::min<int64_t>(B, 1024);
-    s = ensure_workspace(p, chunk, false, true);
+    s = ensure_workspace(p, chunk, false, true, st);
     if (s != ACOM_OK) return s;
     cudaMemsetAsync(p->err, 0, sizeof(int), st);
     prof_begin(kKMisc, st);
@@ -472,7 +517,7 @@ acom_status acom_match(acom_plan p, const acom_peaks_csr* peaks, const acom_matc
     chunk = (int)std::min<int64_t>(chunk, B);
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const bool fp32_contraction = exhaustive || p->precision == ACOM_PREC_FP32;
-    s = ensure_workspace(p, chunk, exhaustive, fp32_contraction);
+    s = ensure_workspace(p, chunk, exhaustive, fp32_contraction, st);
     if (s != ACOM_OK) return s;
     cudaMemsetAsync(p->err, 0, sizeof(int), st);
     cudaMemsetAsync(p->ws.n_eval, 0, sizeof(int), st);
@@ -533,7 +578,7 @@ acom_status acom_bounds(acom_plan p, const acom_peaks_csr* peaks, float* dst, vo
     const int chunk = (int)std::min<int64_t>(B, 8192);
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const bool tc = p->precision == ACOM_PREC_BF16;
-    s = ensure_workspace(p, chunk, false, !tc);
+    s = ensure_workspace(p, chunk, false, !tc, st);
     if (s != ACOM_OK) return s;
     cudaMemsetAsync(p->err, 0, sizeof(int), st);
     prof_begin(kKMisc, st);

@@ -185,12 +185,12 @@ acom_status build_plan_device(acom_plan_s* p, const acom_crystal* cr, cudaStream
         if (e != cudaSuccess) goto fail;                   \
     } while (0)
     {
-        ACOM_TRY(cudaMalloc(&d_atoms, sizeof(double) * atoms.size()));
-        ACOM_TRY(cudaMalloc(&d_tmp_g, sizeof(double) * 3 * cand));
-        ACOM_TRY(cudaMalloc(&d_tmp_F, sizeof(double) * cand));
-        ACOM_TRY(cudaMalloc(&d_g, sizeof(double) * 3 * cand));
-        ACOM_TRY(cudaMalloc(&d_amp, sizeof(double) * cand));
-        ACOM_TRY(cudaMalloc(&d_cnt, sizeof(int)));
+        ACOM_TRY(pool_alloc(reinterpret_cast<void**>(&d_atoms), sizeof(double) * atoms.size(), st));
+        ACOM_TRY(pool_alloc(reinterpret_cast<void**>(&d_tmp_g), sizeof(double) * 3 * cand, st));
+        ACOM_TRY(pool_alloc(reinterpret_cast<void**>(&d_tmp_F), sizeof(double) * cand, st));
+        ACOM_TRY(pool_alloc(reinterpret_cast<void**>(&d_g), sizeof(double) * 3 * cand, st));
+        ACOM_TRY(pool_alloc(reinterpret_cast<void**>(&d_amp), sizeof(double) * cand, st));
+        ACOM_TRY(pool_alloc(reinterpret_cast<void**>(&d_cnt), sizeof(int), st));
         ACOM_TRY(cudaMemcpyAsync(d_atoms, atoms.data(), sizeof(double) * atoms.size(),
                                  cudaMemcpyHostToDevice, st));
         prof_begin(kKReflections, st);
@@ -206,16 +206,16 @@ acom_status build_plan_device(acom_plan_s* p, const acom_crystal* cr, cudaStream
         p->refl_amp = d_amp;
         p->bytes += sizeof(double) * 4 * cand;
         d_g = d_amp = nullptr;
-        cudaFree(d_atoms);
-        cudaFree(d_tmp_g);
-        cudaFree(d_tmp_F);
-        cudaFree(d_cnt);
+        pool_free(d_atoms, st);
+        pool_free(d_tmp_g, st);
+        pool_free(d_tmp_F, st);
+        pool_free(d_cnt, st);
         d_atoms = d_tmp_g = d_tmp_F = nullptr;
         d_cnt = nullptr;
 
         // P0 -> FFT along phi3 -> scale by A
         float* d_sumsq = nullptr;
-        ACOM_TRY(cudaMalloc(&d_sumsq, sizeof(float) * p->Zp));
+        ACOM_TRY(pool_alloc(reinterpret_cast<void**>(&d_sumsq), sizeof(float) * p->Zp, st));
         ACOM_TRY(cudaMemsetAsync(d_sumsq, 0, sizeof(float) * p->Zp, st));
         RasterGeom geo{p->S, p->Spad, p->N, p->F, (float)p->dq, (float)p->delta,
                        (float)p->gamma_pow, 1};
@@ -235,19 +235,19 @@ acom_status build_plan_device(acom_plan_s* p, const acom_crystal* cr, cudaStream
         ACOM_TRY(cudaMemcpyAsync(&herr, p->err, sizeof(int), cudaMemcpyDeviceToHost, st));
         ACOM_TRY(cudaStreamSynchronize(st));
         prof_resolve();
-        cudaFree(d_sumsq);
+        pool_free(d_sumsq, st);
         if (herr & kErrTooManyPeaks)
             return set_error(ACOM_ERR_UNSUPPORTED,
                              "more than 1024 reflections near the Ewald sphere for one zone axis");
         return ACOM_OK;
     }
 fail:
-    cudaFree(d_atoms);
-    cudaFree(d_tmp_g);
-    cudaFree(d_tmp_F);
-    cudaFree(d_g);
-    cudaFree(d_amp);
-    cudaFree(d_cnt);
+    pool_free(d_atoms, st);
+    pool_free(d_tmp_g, st);
+    pool_free(d_tmp_F, st);
+    pool_free(d_g, st);
+    pool_free(d_amp, st);
+    pool_free(d_cnt, st);
     if (e == cudaErrorMemoryAllocation) return set_error(ACOM_ERR_OOM, "plan: device allocation");
     return cuda_error(e, "plan build");
 #undef ACOM_TRY

@@ -331,12 +331,14 @@ k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, int* err
                 }
             }
             if (out.sre) {
+                // whole padded rows, the pad frequencies as zeros
                 const int Fs = shell_row_stride(F);
                 const int64_t sbase = (item * (int64_t)Spad + s0) * Fs;
-                for (int e = threadIdx.x; e < F * W; e += blockDim.x) {
-                    const int w = e / F, f = e - w * F;
-                    out.sre[sbase + (int64_t)w * Fs + f] = st_re[w * F + f];
-                    out.sim[sbase + (int64_t)w * Fs + f] = st_im[w * F + f];
+                for (int e = threadIdx.x; e < Fs * W; e += blockDim.x) {
+                    const int w = e / Fs, f = e - w * Fs;
+                    const bool in = f < F;
+                    out.sre[sbase + (int64_t)w * Fs + f] = in ? st_re[w * F + f] : 0.f;
+                    out.sim[sbase + (int64_t)w * Fs + f] = in ? st_im[w * F + f] : 0.f;
                 }
             }
             __syncthreads();
