@@ -475,33 +475,50 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
             // pairs warp and warp + W of the tile
             for (int pp = warp; pp < kFftTile / 2; pp += W) {
                 const int sA = t0 + 2 * pp;
-                for (int j = lane; j < N; j += 32) z[j] = make_float2(0.f, 0.f);
+                for (int j = lane; j < N; j += 32) {
+                    z[j] = make_float2(0.f, 0.f);
+                    zz[j] = make_float2(0.f, 0.f);
+                }
                 __syncwarp();
-                bool any = false;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int s = sA + h;
-                    if (s >= S) continue;
-                    const float qs = (float)(s + 1) * geo.dq;
-                    const float qs2 = qs * qs, inv_qs = 1.0f / qs;
-                    const float rscale = geo.shell_power ? powf(qs, geo.gamma_pow) : 1.0f;
-                    // peaks with |r - q_s| < delta are a contiguous run in radius order
+                // One pass over the peaks reaching either shell of the pair (radius
+                // within delta of q_A or q_B): the half-warps take alternate peaks,
+                // each into its own row (z, zz), and every bin of a peak's window
+                // gets both shells' tents (x: shell sA, y: shell sA + 1).  The two
+                // rows are summed before the transform, a fixed order.
+                bool inA_any = false, inB_any = false;
+                if (sA < S) {
+                    const bool vB = sA + 1 < S;
+                    const float qA = (float)(sA + 1) * geo.dq, qB = (float)(sA + 2) * geo.dq;
+                    const float qA2 = qA * qA, qB2 = qB * qB;
+                    const float iqA = 1.0f / qA, iqB = 1.0f / qB;
+                    const float rsA = geo.shell_power ? powf(qA, geo.gamma_pow) : 1.0f;
+                    const float rsB = geo.shell_power ? powf(qB, geo.gamma_pow) : 1.0f;
+                    const float qhi = vB ? qB : qA;
                     int lo = 0, hi = 0;
                     for (int base = 0; base < np; base += 32) {
                         const int m = base + lane;
                         const float r = m < np ? sp[sidx[m]].r : CUDART_INF_F;
-                        lo += __popc(__ballot_sync(0xffffffffu, r <= qs - delta));
-                        hi += __popc(__ballot_sync(0xffffffffu, r < qs + delta));
+                        lo += __popc(__ballot_sync(0xffffffffu, r <= qA - delta));
+                        hi += __popc(__ballot_sync(0xffffffffu, r < qhi + delta));
                     }
-                    bool shell_any = false;
-                    for (int m = lo; m < hi; ++m) {
+                    const int half = lane >> 4, hl = lane & 15;
+                    const unsigned hmask = 0xffffu << (16 * half);
+                    float2* acc = half ? zz : z;
+                    // every condition below is uniform over a half-warp (its lanes
+                    // share the peak), so the half-warp syncs pair up; they order a
+                    // bin's updates by different lanes for successive peaks
+                    for (int m = lo + half; m < hi; m += 2) {
                         const Peak pk = sp[sidx[m]];
-                        const float dr = pk.r - qs;
-                        const float a2 = fmaf(dr, dr, pk.e);
-                        if (!(a2 < d2) || pk.w == 0.f) continue;
-                        const float hw = sqrtf(d2 - a2) * inv_qs;
-                        const float wgt = pk.w * rscale;
-                        shell_any = true;
+                        const float drA = pk.r - qA, drB = pk.r - qB;
+                        const float a2A = fmaf(drA, drA, pk.e), a2B = fmaf(drB, drB, pk.e);
+                        const bool inA = a2A < d2 && pk.w != 0.f, inB = vB && a2B < d2 && pk.w != 0.f;
+                        if (!inA && !inB) continue;
+                        inA_any |= inA;
+                        inB_any |= inB;
+                        const float hwA = inA ? sqrtf(d2 - a2A) * iqA : 0.f;
+                        const float hwB = inB ? sqrtf(d2 - a2B) * iqB : 0.f;
+                        const float hw = fmaxf(hwA, hwB);
+                        const float wA = inA ? pk.w * rsA : 0.f, wB = inB ? pk.w * rsB : 0.f;
                         if (hw < hw_nowrap) {
                             // bins jlo .. jlo + cnt - 1 around gamma; the offset of bin
                             // jlo + t is d0 + t dphi, within (-pi, pi) by the bound on hw
@@ -512,40 +529,66 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
                             int jw = jlo;
                             if (jw < 0) jw += N;
                             if (jw < 0) jw += N;
-                            for (int t = lane; t < cnt; t += 32) {
+                            for (int t = hl; t < cnt; t += 16) {
                                 int j = jw + t;
                                 if (j >= N) j -= N;
-                                const float d = fmaf((float)t, dphi, d0);
-                                float sq;
-                                asm("sqrt.approx.f32 %0, %1;" : "=f"(sq) : "f"(fmaf(d * d, qs2, a2)));
-                                const float tt = 1.0f - sq * inv_delta;
-                                if (tt > 0.f) {
-                                    if (h == 0) z[j].x += wgt * tt;
-                                    else z[j].y += wgt * tt;
+                                const float d = fmaf((float)t, dphi, d0), dd = d * d;
+                                float sa, sb;
+                                asm("sqrt.approx.f32 %0, %1;" : "=f"(sa) : "f"(fmaf(dd, qA2, a2A)));
+                                asm("sqrt.approx.f32 %0, %1;" : "=f"(sb) : "f"(fmaf(dd, qB2, a2B)));
+                                const float ta = inA ? 1.0f - sa * inv_delta : 0.f;
+                                const float tb = inB ? 1.0f - sb * inv_delta : 0.f;
+                                if (ta > 0.f || tb > 0.f) {
+                                    float2 v = acc[j];
+                                    if (ta > 0.f) v.x = fmaf(wA, ta, v.x);
+                                    if (tb > 0.f) v.y = fmaf(wB, tb, v.y);
+                                    acc[j] = v;
                                 }
                             }
                         } else {
                             // a window of (nearly) the whole circle: every bin, offsets wrapped
-                            for (int j = lane; j < N; j += 32) {
+                            for (int j = hl; j < N; j += 16) {
                                 float d = fmaf((float)j, dphi, -pk.gam);
                                 if (d >= CUDART_PI_F) d -= two_pi;
                                 if (d < -CUDART_PI_F) d += two_pi;
-                                float sq;
-                                asm("sqrt.approx.f32 %0, %1;" : "=f"(sq) : "f"(fmaf(d * d, qs2, a2)));
-                                const float tt = 1.0f - sq * inv_delta;
-                                if (tt > 0.f) {
-                                    if (h == 0) z[j].x += wgt * tt;
-                                    else z[j].y += wgt * tt;
+                                const float dd = d * d;
+                                float sa, sb;
+                                asm("sqrt.approx.f32 %0, %1;" : "=f"(sa) : "f"(fmaf(dd, qA2, a2A)));
+                                asm("sqrt.approx.f32 %0, %1;" : "=f"(sb) : "f"(fmaf(dd, qB2, a2B)));
+                                const float ta = inA ? 1.0f - sa * inv_delta : 0.f;
+                                const float tb = inB ? 1.0f - sb * inv_delta : 0.f;
+                                if (ta > 0.f || tb > 0.f) {
+                                    float2 v = acc[j];
+                                    if (ta > 0.f) v.x = fmaf(wA, ta, v.x);
+                                    if (tb > 0.f) v.y = fmaf(wB, tb, v.y);
+                                    acc[j] = v;
                                 }
                             }
                         }
-                        __syncwarp();
+                        __syncwarp(hmask);
                     }
-                    if (shell_any) {
-                        w_lo = min(w_lo, s);
-                        w_hi = max(w_hi, s + 1);
+                }
+                const bool anyA = __any_sync(0xffffffffu, inA_any);
+                const bool anyB = __any_sync(0xffffffffu, inB_any);
+                if (anyA) {
+                    w_lo = min(w_lo, sA);
+                    w_hi = max(w_hi, sA + 1);
+                }
+                if (anyB) {
+                    w_lo = min(w_lo, sA + 1);
+                    w_hi = max(w_hi, sA + 2);
+                }
+                const bool any = anyA || anyB;
+                if (any) {
+                    __syncwarp();
+                    for (int j = lane; j < N; j += 32) {
+                        const float2 u = zz[j];
+                        float2 v = z[j];
+                        v.x += u.x;
+                        v.y += u.y;
+                        z[j] = v;
                     }
-                    any = any || shell_any;
+                    __syncwarp();
                 }
                 const float2* Z = any ? warp_fft_fixed(z, zz, N, rad, tw, lane) : nullptr;
                 // real rows a (shell sA), b (shell sA + 1) from Z = FFT(a + i b):

@@ -213,9 +213,11 @@ def test_pruned_equals_exhaustive(c1):
     kb = np.stack([b[k].cpu().numpy().astype(np.int64) for k in ("za_idx", "phi3_bin", "mirror")], 1)
     np.testing.assert_allclose(a["score"].cpu().numpy(), b["score"].cpu().numpy(), rtol=1e-5)
     diff = np.nonzero(np.any(ka != kb, axis=1))[0]
-    assert len(diff) <= 4, diff
+    # the two paths sum in different orders, so exact (symmetry) ties resolve
+    # either way; a few per cent of random patterns have one
+    assert len(diff) <= len(ka) // 20, diff
     oplan = oracle_plan("au_2deg_75x180")
-    for i in diff:          # a difference must be an FP32-level tie in the oracle
+    for i in diff:          # a difference must be an FP32-level tie in the oracle (R10)
         mt = O.match_pattern(oplan, *scan.pattern(i))
         assert check_argmax(mt, *ka[i]) and check_argmax(mt, *kb[i]), (i, ka[i], kb[i])
     same = np.setdiff1d(np.arange(len(ka)), diff)
