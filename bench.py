@@ -402,6 +402,35 @@ def read_profile(lib, acom):
     return {e.name.decode(): (e.launches, e.total_ms) for e in arr}
 
 
+# DRAM bytes per pattern (read + write) of kernels whose traffic grows with
+# the patterns of a launch, from the ncu capture summarised in
+# profiles/ncu_full_bf16_au_scan_64x64_1deg.md, with a hash of the kernel's
+# sources at capture time: a changed kernel reports no traffic.
+TRAFFIC_PER_PATTERN = {
+    "select_exact": (360129.0, ("match_prune.cu",), "5e7d52402f6b7e18"),
+    "raster_patterns": (340288.0, ("raster.cu",), "dcbe18b5cad1cdf8"),
+}
+
+
+def sources_hash(files):
+    import hashlib
+    d = os.path.join(ROOT, "paper_2111_00171_gb300", "csrc")
+    m = hashlib.sha256()
+    for f in tuple(files) + ("acom_internal.cuh", "fft_warp.cuh"):
+        with open(os.path.join(d, f), "rb") as fh:
+            m.update(fh.read())
+    return m.hexdigest()[:16]
+
+
+def kernel_traffic(name, pats):
+    """DRAM bytes of one launch of ``pats`` patterns, scaled from the capture
+    (traffic of these kernels grows in proportion to the patterns), or None."""
+    t = TRAFFIC_PER_PATTERN.get(name)
+    if t is None or sources_hash(t[1]) != t[2]:
+        return None
+    return t[0] * pats
+
+
 def kernel_roofline(name, cnt, ms, peaks, src, B, K, nnz):
     """Achieved rate of one kernel class: algorithmic work per launch over its
     event-timed average launch duration."""
@@ -436,7 +465,7 @@ def kernel_roofline(name, cnt, ms, peaks, src, B, K, nnz):
         return None
     ach = work / avg_s / (1e12 if unit == "TFLOP/s" else 1.0)
     return {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
-            "frac": ach / peak, "traffic": None, "avg_launch_ms": avg_s * 1e3,
+            "frac": ach / peak, "traffic": kernel_traffic(name, pats), "avg_launch_ms": avg_s * 1e3,
             "launches": cnt, "peak_source": note}
 
 
