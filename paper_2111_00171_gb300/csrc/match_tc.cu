@@ -184,16 +184,39 @@ __device__ __forceinline__ float mag_from_sq(float x) {
     return r;
 }
 
-// w max(|c_dir|, |c_mir|) added to the bound: with p = A^2+B^2+C^2+D^2 and
+// w max(|c_dir|, |c_mir|) added to the bound of two pairs (axes z and z + 1,
+// adjacent registers of a 16x256b load): with p = A^2+B^2+C^2+D^2 and
 // q = AB - CD, |c_dir|^2 = |(A+B) + i(C-D)|^2 = p + 2q and
-// |c_mir|^2 = |(A-B) - i(C+D)|^2 = p - 2q, so the larger is p + 2|q|
-__device__ __forceinline__ void accumulate_pair(uint32_t ua, uint32_t uc, uint32_t ud_,
-                                                uint32_t ub, float w, float& acc) {
-    const float fa = __uint_as_float(ua), fc = __uint_as_float(uc);
-    const float fd = __uint_as_float(ud_), fb = __uint_as_float(ub);
-    const float p = fmaf(fa, fa, fmaf(fb, fb, fmaf(fc, fc, fd * fd)));
-    const float q = fmaf(fa, fb, -fc * fd);
-    acc = fmaf(w, mag_from_sq(fmaf(2.0f, fabsf(q), p)), acc);
+// |c_mir|^2 = |(A-B) - i(C+D)|^2 = p - 2q, so the larger is p + 2|q|.  Packed
+// FP32x2 arithmetic halves the epilogue's instructions, which share the issue
+// slots with the MMA-issuing warps.
+__device__ __forceinline__ void accumulate_pair2(uint32_t a0, uint32_t a1, uint32_t c0,
+                                                 uint32_t c1, uint32_t d0, uint32_t d1,
+                                                 uint32_t b0, uint32_t b1, float w, float& acc0,
+                                                 float& acc1) {
+    float t0, t1;
+    asm("{\n"
+        ".reg .b64 A, B, C, D, P, Q, R;\n"
+        "mov.b64 A, {%2, %3};\n"
+        "mov.b64 C, {%4, %5};\n"
+        "mov.b64 D, {%6, %7};\n"
+        "mov.b64 B, {%8, %9};\n"
+        "mul.rn.f32x2 P, D, D;\n"
+        "fma.rn.f32x2 P, C, C, P;\n"
+        "fma.rn.f32x2 P, B, B, P;\n"
+        "fma.rn.f32x2 P, A, A, P;\n"
+        "mul.rn.f32x2 Q, C, D;\n"
+        "mul.rn.f32x2 R, A, B;\n"
+        "sub.rn.f32x2 Q, R, Q;\n"
+        "and.b64 Q, Q, 0x7FFFFFFF7FFFFFFF;\n"
+        "add.rn.f32x2 Q, Q, Q;\n"
+        "add.rn.f32x2 P, P, Q;\n"
+        "mov.b64 {%0, %1}, P;\n"
+        "}\n"
+        : "=f"(t0), "=f"(t1)
+        : "r"(a0), "r"(a1), "r"(c0), "r"(c1), "r"(d0), "r"(d1), "r"(b0), "r"(b1));
+    acc0 = fmaf(w, mag_from_sq(t0), acc0);
+    acc1 = fmaf(w, mag_from_sq(t1), acc1);
 }
 
 struct TcArgs {
@@ -395,20 +418,18 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
                 ACOM_TMEM_LD16x256_X4(tb + (16u << 16) + 128, I1);
 #pragma unroll
                 for (int n = 0; n < 4; ++n)
-#pragma unroll
-                    for (int e = 0; e < 2; ++e)
-                        accumulate_pair(R0[4 * n + e], R0[4 * n + 2 + e], I0[4 * n + e],
-                                        I0[4 * n + 2 + e], w, ud[2 * n + e]);
+                    accumulate_pair2(R0[4 * n], R0[4 * n + 1], R0[4 * n + 2], R0[4 * n + 3],
+                                     I0[4 * n], I0[4 * n + 1], I0[4 * n + 2], I0[4 * n + 3], w,
+                                     ud[2 * n], ud[2 * n + 1]);
                 ACOM_TMEM_WAIT32(R1, I1);
                 fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(tempty + buf));
 #pragma unroll
                 for (int n = 0; n < 4; ++n)
-#pragma unroll
-                    for (int e = 0; e < 2; ++e)
-                        accumulate_pair(R1[4 * n + e], R1[4 * n + 2 + e], I1[4 * n + e],
-                                        I1[4 * n + 2 + e], w, ud[8 + 2 * n + e]);
+                    accumulate_pair2(R1[4 * n], R1[4 * n + 1], R1[4 * n + 2], R1[4 * n + 3],
+                                     I1[4 * n], I1[4 * n + 1], I1[4 * n + 2], I1[4 * n + 3], w,
+                                     ud[8 + 2 * n], ud[8 + 2 * n + 1]);
             }
             if (!ok) break;
 #pragma unroll
