@@ -8,11 +8,12 @@ step is the whole path: plan build (reflections, plan raster + transform,
 normalisation) and the match of every pattern (sparse polar raster +
 transform, shell contraction, inverse transform + argmax, refinement).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp16|fp32]
   python bench.py --impl reference ...   # the FP64 CPU oracle as the reference arm
 
 The default precision is BF16 operands on the tensor cores for the certified
-bound, with every winner evaluated exactly in FP32.  Under torchrun (N > 1)
+bound, with every winner evaluated exactly in FP32; fp16 takes FP16 operands
+with per-pattern power-of-two scaling instead.  Under torchrun (N > 1)
 every rank matches its own scan (weak scaling, scan seed + rank); there is no
 collective on the data path; rank 0 prints one JSON line.
 """
@@ -46,7 +47,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp32"])
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--exhaustive", action="store_true",
                     help="inverse-transform every zone axis (no certified pruning)")
@@ -265,7 +266,8 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     lib = acom.load_library()
-    prec = acom.ACOM_PREC_BF16 if args.precision == "bf16" else acom.ACOM_PREC_FP32
+    prec = {"bf16": acom.ACOM_PREC_BF16, "fp16": acom.ACOM_PREC_FP16,
+            "fp32": acom.ACOM_PREC_FP32}[args.precision]
 
     H, Wd = (int(v) for v in args.scan.split("x"))
     scan = synth.grain_scan(rank_seed(rank), H=H, W=Wd)
@@ -362,7 +364,8 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "patterns/s", "n_gpus": world,
             "steps": K, "warmup": args.warmup, "ms_per_step": dev_ms / K,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.precision == "fp32" else "bf16", "data": "synthetic",
+            "dtype": {"fp32": "f32", "fp16": "f16", "bf16": "bf16"}[args.precision],
+            "data": "synthetic",
             "config": {"workload": WORKLOAD_TEXT, "patterns_per_gpu": B,
                        "peaks_nnz": int(scan.row_ptr[-1]), "zone_axes": 903, "shells": W["S"],
                        "n_phi": W["N"], "precision": args.precision,
@@ -405,10 +408,11 @@ def read_profile(lib, acom):
 # DRAM bytes per pattern (read + write) of kernels whose traffic grows with
 # the patterns of a launch, from the ncu capture summarised in
 # profiles/ncu_full_bf16_au_scan_64x64_1deg.md, with a hash of the kernel's
-# sources at capture time: a changed kernel reports no traffic.
+# sources at capture time and the precision of the captured run: a changed
+# kernel, or a run at another precision, reports no traffic.
 TRAFFIC_PER_PATTERN = {
-    "select_exact": (360129.0, ("match_prune.cu",), "5e7d52402f6b7e18"),
-    "raster_patterns": (340288.0, ("raster.cu",), "dcbe18b5cad1cdf8"),
+    "select_exact": (360076.0, ("match_prune.cu",), "e9c572a4179f2cc6", "bf16"),
+    "raster_patterns": (340215.0, ("raster.cu",), "3c26ac06f0283b45", "bf16"),
 }
 
 
@@ -422,16 +426,16 @@ def sources_hash(files):
     return m.hexdigest()[:16]
 
 
-def kernel_traffic(name, pats):
+def kernel_traffic(name, pats, precision):
     """DRAM bytes of one launch of ``pats`` patterns, scaled from the capture
     (traffic of these kernels grows in proportion to the patterns), or None."""
     t = TRAFFIC_PER_PATTERN.get(name)
-    if t is None or sources_hash(t[1]) != t[2]:
+    if t is None or sources_hash(t[1]) != t[2] or precision != t[3]:
         return None
     return t[0] * pats
 
 
-def kernel_roofline(name, cnt, ms, peaks, src, B, K, nnz):
+def kernel_roofline(name, cnt, ms, peaks, src, B, K, nnz, precision):
     """Achieved rate of one kernel class: algorithmic work per launch over its
     event-timed average launch duration."""
     Z, S, N = 903, W["S"], W["N"]
@@ -442,7 +446,8 @@ def kernel_roofline(name, cnt, ms, peaks, src, B, K, nnz):
     if name == "contract_bf16":
         work, unit, bound, peak = 8.0 * Z * S * F * pats, "TFLOP/s", "tensor", \
             peaks["bf16_tflops_sustained"]
-        note = f"8 Z S F flops per pattern; bf16 sustained peak ({src})"
+        note = (f"8 Z S F flops per pattern; bf16 sustained peak, which FP16 operands "
+                f"share ({src})")
     elif name == "contract_fp32":
         work, unit, bound, peak = 8.0 * Z * S * F * pats, "TFLOP/s", "alu", fp32_peak
         note = "8 Z S F flops per pattern; FP32 FMA peak 152 SMs x 128 lanes x 2 x max clock"
@@ -460,12 +465,13 @@ def kernel_roofline(name, cnt, ms, peaks, src, B, K, nnz):
         out_b = S * F * 2 * (4 + 2)
         work = (nnz / B * 12 + 8 + out_b) * pats / 1e9
         unit, bound, peak = "GB/s", "hbm", peaks["hbm_gbs"]
-        note = f"CSR in + FP32 and BF16 spectra out per pattern; HBM peak ({src})"
+        note = f"CSR in + FP32 and 16-bit spectra out per pattern; HBM peak ({src})"
     else:
         return None
     ach = work / avg_s / (1e12 if unit == "TFLOP/s" else 1.0)
     return {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
-            "frac": ach / peak, "traffic": kernel_traffic(name, pats), "avg_launch_ms": avg_s * 1e3,
+            "frac": ach / peak, "traffic": kernel_traffic(name, pats, precision),
+            "avg_launch_ms": avg_s * 1e3,
             "launches": cnt, "peak_source": note}
 
 
@@ -474,7 +480,9 @@ def roofline(prof, peaks, src, B, K, precision, nnz):
     the kernels with a stated roofline), plus every other kernel's share."""
     rows = []
     for name, (cnt, ms) in prof.items():
-        r = kernel_roofline(name, cnt, ms, peaks, src, B, K, nnz)
+        if cnt == 0:
+            continue
+        r = kernel_roofline(name, cnt, ms, peaks, src, B, K, nnz, precision)
         if r is not None:
             r["total_ms"] = ms
             rows.append(r)

@@ -37,8 +37,12 @@ typedef enum {
 /* Arithmetic used by the shell contraction and the inverse transform. */
 typedef enum {
     ACOM_PREC_FP32 = 0,   /* FP32 CUDA-core path (reference GPU path)               */
-    ACOM_PREC_BF16 = 1    /* BF16 operands on tcgen05 tensor cores, FP32 accumulate,
+    ACOM_PREC_BF16 = 1,   /* BF16 operands on tcgen05 tensor cores, FP32 accumulate,
                              top candidates re-scored in FP32                       */
+    ACOM_PREC_FP16 = 2    /* FP16 operands on tcgen05 tensor cores, FP32 accumulate;
+                             pattern and plan spectra are scaled by powers of two
+                             into FP16 range and the bound scaled back; top
+                             candidates re-scored in FP32                           */
 } acom_precision;
 
 typedef struct acom_plan_s* acom_plan;
@@ -258,8 +262,8 @@ int64_t acom_kernel_launches(void);
  * direct and mirror correlation spectra, which is >= max over phi3 of both C
  * and C_mirror (section "Correlation Pattern Matching"; w_0 = w_{N/2} = 1,
  * else 2).  Computed at the plan's precision (FP32 CUDA
- * cores, or BF16 tensor cores with FP32 accumulation) without any rounding
- * margin.  ``dst``: DEVICE [n_patterns][Z] FP32.  Stream-ordered; synchronises
+ * cores, or BF16 / FP16 tensor cores with FP32 accumulation) without any
+ * rounding margin.  ``dst``: DEVICE [n_patterns][Z] FP32.  Stream-ordered; synchronises
  * once to read the error word.
  */
 acom_status acom_bounds(acom_plan plan, const acom_peaks_csr* peaks, float* dst,
@@ -273,7 +277,8 @@ acom_status acom_bounds(acom_plan plan, const acom_peaks_csr* peaks, float* dst,
  * a host process whose device memory is held by another allocator (a
  * cudaMalloc there could fail or stall).  The plan must already exist; the
  * caller passes the peaks and ``dst`` ([n_patterns][Z] FP32, DEVICE), as for
- * acom_bounds.
+ * acom_bounds.  FP32 and BF16 plans get their own precision's bounds; for an
+ * FP16 plan the bounds are computed on the FP32 path.
  *
  * Scratch: the pattern spectra of one chunk live in a file-scope device array
  * of 32 MiB that every device loading the library keeps until the process

@@ -19,6 +19,7 @@ from . import build as _build
 ACOM_OK = 0
 ACOM_PREC_FP32 = 0
 ACOM_PREC_BF16 = 1
+ACOM_PREC_FP16 = 2
 STATUS = {0: "ACOM_OK", 1: "ACOM_ERR_INVALID_ARG", 2: "ACOM_ERR_OOM", 3: "ACOM_ERR_CUDA",
           4: "ACOM_ERR_TIMEOUT", 5: "ACOM_ERR_UNSUPPORTED", 6: "ACOM_ERR_BAD_INPUT"}
 

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -71,7 +72,29 @@ struct PatternSource {         // one chunk of CSR patterns
     const float* I;
     int64_t n_items;
     float gamma_pow, omega;
+    int xb_fp16 = 0;           // xb holds FP16 of 2^e_b X^ instead of BF16 of X^
+    float* xscale = nullptr;   // [n_items] 2^e_b of each pattern (with xb_fp16)
 };
+
+// FP16 operands of the tensor-core contraction: each pattern's spectrum is
+// stored as FP16(2^e X^) with 2^e B <= 2^14, B an a-priori bound on |X^_sf|
+// (X >= 0, so |X^_sf| <= X^_s0 = sum_j X(s, j) <= sum_m w_m n_m, n_m the most
+// bins a peak's tent can cover), and the plan's as FP16(2^k P^) with
+// 2^k sqrt(N) <= 2^14 (||P_z|| = 1 and P >= 0 bound |P^_zsf| by sqrt(N)).
+// The bound U is divided by 2^(e+k) again; both scales are powers of two, so
+// scaling and unscaling are exact.
+constexpr float kFp16Target = 16384.0f;
+// Absolute error of an FP16 operand below the normal range (|x| < 2^-14),
+// whether the value is rounded to a subnormal or flushed to zero
+constexpr double kFp16Eta = 6.103515625e-05;   // 2^-14
+
+// 2^k of the plan's FP16 spectra: the largest power of two with 2^k sqrt(N) <= 2^14
+inline float fp16_plan_scale(int N) {
+    double s = 1.0;
+    while (2.0 * s * std::sqrt((double)N) <= kFp16Target) s *= 2.0;
+    while (s * std::sqrt((double)N) > kFp16Target) s *= 0.5;
+    return (float)s;
+}
 
 // Workspace for one chunk of patterns.
 struct Workspace {
@@ -91,8 +114,14 @@ struct Workspace {
     int2* srange = nullptr;        // [chunk] non-zero shell range of each pattern
     unsigned long long* best = nullptr;  // [chunk] packed (score, index)
     float* za_scores = nullptr;    // [chunk][Z]
+    float* xscale = nullptr;       // [chunk] 2^e of each pattern's FP16 spectrum
     size_t bytes = 0;
 };
+
+// precisions whose contraction runs on the tensor cores
+inline bool tc_precision(int precision) {
+    return precision == ACOM_PREC_BF16 || precision == ACOM_PREC_FP16;
+}
 
 }  // namespace acom
 
@@ -116,7 +145,8 @@ struct acom_plan_s {
     double* refl_amp = nullptr;       // [G]
     int* err = nullptr;               // device error word
     float* pfmax = nullptr;           // [F] max over axes of ||P^_zf|| over shells
-    void* Pb_r = nullptr;             // BF16 [F][Zp][Spad] (tensor-core operand)
+    float pscale = 1.0f;              // 2^k of the FP16 plan spectra (1 otherwise)
+    void* Pb_r = nullptr;             // BF16 or FP16 [F][Zp][Spad] (tensor-core operand)
     void* Pb_i = nullptr;
     alignas(64) unsigned char map_pr[128];  // TMA maps of Pb_r, Pb_i
     alignas(64) unsigned char map_pi[128];
@@ -164,15 +194,19 @@ void launch_contract_bound_fp32(const acom_plan_s* p, const float* Xr, const flo
                                 float* U, cudaStream_t st);
 void launch_plan_fnorm_max(const acom_plan_s* p, float* out, cudaStream_t st);
 // match_tc.cu
-acom_status make_bf16_map(void* map_storage, const void* base, uint64_t rows, uint64_t cols);
+acom_status make_bf16_map(void* map_storage, const void* base, uint64_t rows, uint64_t cols,
+                          bool fp16 = false);
+// xscale: per-pattern 2^e of FP16 pattern spectra (nullptr: BF16, no scale)
 void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_stride, int nb,
-                              float* U, cudaStream_t st);
-void launch_plan_to_bf16(const float* src, int Zp, int F, int Spad, void* dst, cudaStream_t st);
+                              float* U, cudaStream_t st, const float* xscale = nullptr);
+// fp16: FP16 of scale * src instead of BF16 of src
+void launch_plan_to_bf16(const float* src, int Zp, int F, int Spad, void* dst, cudaStream_t st,
+                         bool fp16 = false, float scale = 1.0f);
 void launch_select_exact(const acom_plan_s* p, const float* Xsr, const float* Xsi, const float* U,
                          const float* xfn, const int2* srange, const float* pfmax,
                          const float* xnorm2, int nb,
                          float kappa, int refine, acom_result out, int64_t off, int* n_eval,
-                         cudaStream_t st);
+                         cudaStream_t st, const float* xscale = nullptr);
 void launch_refine(const acom_plan_s* p, const float* Chat, int nb, int chunk,
                    const float* za_scores, const unsigned long long* best, const float* xnorm2,
                    int refine, acom_result out, int64_t out_offset, cudaStream_t st);

@@ -145,6 +145,7 @@ static void free_workspace(Workspace& ws, cudaStream_t st) {
     pool_free(ws.best, st);
     pool_free(ws.za_scores, st);
     pool_free(ws.XB, st);
+    pool_free(ws.xscale, st);
     ws = Workspace{};
 }
 
@@ -181,12 +182,14 @@ static acom_status ensure_workspace(acom_plan_s* p, int chunk, bool need_chat, b
     if ((e = dalloc(&ws.srange, (size_t)chunk, &acc, st)) != cudaSuccess) goto fail;
     if ((e = dalloc(&ws.best, (size_t)chunk, &acc, st)) != cudaSuccess) goto fail;
     if ((e = dalloc(&ws.za_scores, (size_t)chunk * p->Z, &acc, st)) != cudaSuccess) goto fail;
-    if (p->precision == ACOM_PREC_BF16) {
+    if (tc_precision(p->precision)) {
+        const bool fp16 = p->precision == ACOM_PREC_FP16;
         ws.PTs = (chunk + 63) / 64;
         const size_t rows = (size_t)p->F * ws.PTs * 128;
         if ((e = pool_alloc(&ws.XB, rows * p->Spad * 2, st)) != cudaSuccess) goto fail;
         acc += rows * p->Spad * 2;
-        acom_status ms = make_bf16_map(ws.map_x, ws.XB, rows, (uint64_t)p->Spad);
+        if (fp16 && (e = dalloc(&ws.xscale, (size_t)chunk, &acc, st)) != cudaSuccess) goto fail;
+        acom_status ms = make_bf16_map(ws.map_x, ws.XB, rows, (uint64_t)p->Spad, fp16);
         if (ms != ACOM_OK) {
             free_workspace(p->ws, st);
             return ms;
@@ -279,7 +282,7 @@ acom_status acom_plan_create(const acom_crystal* crystal, const acom_za_grid* gr
     if (!finite_pos(opts->delta) || !finite_pos(opts->lambda) || !finite_pos(opts->q_max) ||
         !std::isfinite(opts->gamma_pow) || !std::isfinite(opts->omega) || opts->omega < 0)
         return set_error(ACOM_ERR_INVALID_ARG, "opts: delta, lambda, q_max > 0; finite powers");
-    if (opts->precision != ACOM_PREC_FP32 && opts->precision != ACOM_PREC_BF16)
+    if (opts->precision != ACOM_PREC_FP32 && !tc_precision(opts->precision))
         return set_error(ACOM_ERR_INVALID_ARG, "opts: unknown precision");
 
     std::vector<double> za = zone_axes(grid);
@@ -358,17 +361,20 @@ acom_status acom_plan_create(const acom_crystal* crystal, const acom_za_grid* gr
     }
     launch_plan_fnorm_max(p, p->pfmax, st);
     ACOM_CK(cudaGetLastError());
-    if (p->precision == ACOM_PREC_BF16) {
+    if (tc_precision(p->precision)) {
+        const bool fp16 = p->precision == ACOM_PREC_FP16;
+        p->pscale = fp16 ? fp16_plan_scale(p->N) : 1.0f;
         const size_t n = (size_t)p->F * p->Zp * p->Spad;
         ACOM_CK(pool_alloc(&p->Pb_r, n * 2, st));
         ACOM_CK(pool_alloc(&p->Pb_i, n * 2, st));
         p->bytes += 4 * n;
-        launch_plan_to_bf16(p->Pr, p->Zp, p->F, p->Spad, p->Pb_r, st);
-        launch_plan_to_bf16(p->Pi, p->Zp, p->F, p->Spad, p->Pb_i, st);
+        launch_plan_to_bf16(p->Pr, p->Zp, p->F, p->Spad, p->Pb_r, st, fp16, p->pscale);
+        launch_plan_to_bf16(p->Pi, p->Zp, p->F, p->Spad, p->Pb_i, st, fp16, p->pscale);
         ACOM_CK(cudaGetLastError());
-        s = make_bf16_map(p->map_pr, p->Pb_r, (uint64_t)p->F * p->Zp, (uint64_t)p->Spad);
+        s = make_bf16_map(p->map_pr, p->Pb_r, (uint64_t)p->F * p->Zp, (uint64_t)p->Spad, fp16);
         if (s == ACOM_OK)
-            s = make_bf16_map(p->map_pi, p->Pb_i, (uint64_t)p->F * p->Zp, (uint64_t)p->Spad);
+            s = make_bf16_map(p->map_pi, p->Pb_i, (uint64_t)p->F * p->Zp, (uint64_t)p->Spad,
+                              fp16);
         if (s != ACOM_OK) {
             destroy_plan(p);
             return s;
@@ -498,6 +504,18 @@ static float kappa_bf16(const acom_plan_s* p) {
                    (3.0 * (p->Spad + 2) + 2.0 * p->F) * std::ldexp(1.0, -21));
 }
 
+// FP16 operands: relative rounding 2^-11 per operand gives 2^-10 per product
+// and 2^-9 for the complex spectrum, as for BF16; values below the normal range
+// are charged separately by the select kernel (an absolute term per pattern).
+static float kappa_fp16(const acom_plan_s* p) {
+    return (float)(std::ldexp(1.0, -9) +
+                   (3.0 * (p->Spad + 2) + 2.0 * p->F) * std::ldexp(1.0, -21));
+}
+
+static float kappa_tc(const acom_plan_s* p) {
+    return p->precision == ACOM_PREC_FP16 ? kappa_fp16(p) : kappa_bf16(p);
+}
+
 acom_status acom_match(acom_plan p, const acom_peaks_csr* peaks, const acom_match_opts* opts,
                        acom_result* out, void* cuda_stream) {
     g_last_error.clear();
@@ -528,9 +546,11 @@ acom_status acom_match(acom_plan p, const acom_peaks_csr* peaks, const acom_matc
     const int wchunk = p->ws.chunk;
     for (int64_t c0 = 0; c0 < B; c0 += chunk) {
         const int nb = (int)std::min<int64_t>(chunk, B - c0);
-        const bool tc = !exhaustive && p->precision == ACOM_PREC_BF16;
+        const bool tc = !exhaustive && tc_precision(p->precision);
+        float* xscale = tc && p->precision == ACOM_PREC_FP16 ? p->ws.xscale : nullptr;
         PatternSource src{tc ? p->ws.XB : nullptr, p->ws.PTs, peaks->row_ptr + c0, peaks->qx,
-                          peaks->qy, peaks->I, nb, (float)p->gamma_pow, (float)p->omega};
+                          peaks->qy, peaks->I, nb, (float)p->gamma_pow, (float)p->omega,
+                          xscale ? 1 : 0, xscale};
         RasterOut ro;
         ro.re = fp32_contraction ? p->ws.Xr : nullptr;
         ro.im = fp32_contraction ? p->ws.Xi : nullptr;
@@ -551,12 +571,12 @@ acom_status acom_match(acom_plan p, const acom_peaks_csr* peaks, const acom_matc
                                 sizeof(float) * (size_t)nb * p->Z, cudaMemcpyDeviceToDevice, st);
         } else {
             if (tc)
-                launch_contract_bound_tc(p, p->ws.map_x, p->ws.PTs, nb, p->ws.U, st);
+                launch_contract_bound_tc(p, p->ws.map_x, p->ws.PTs, nb, p->ws.U, st, xscale);
             else
                 launch_contract_bound_fp32(p, p->ws.Xr, p->ws.Xi, nb, p->ws.U, st);
             launch_select_exact(p, p->ws.Xsr, p->ws.Xsi, p->ws.U, p->ws.xfn, p->ws.srange, p->pfmax,
-                                p->ws.xnorm2, nb, tc ? kappa_bf16(p) : kappa_fp32(p), refine,
-                                *out, c0, p->ws.n_eval, st);
+                                p->ws.xnorm2, nb, tc ? kappa_tc(p) : kappa_fp32(p), refine,
+                                *out, c0, p->ws.n_eval, st, xscale);
         }
     }
     cudaError_t e = cudaGetLastError();
@@ -577,7 +597,7 @@ acom_status acom_bounds(acom_plan p, const acom_peaks_csr* peaks, float* dst, vo
     if (B == 0) return ACOM_OK;
     const int chunk = (int)std::min<int64_t>(B, 8192);
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    const bool tc = p->precision == ACOM_PREC_BF16;
+    const bool tc = tc_precision(p->precision);
     s = ensure_workspace(p, chunk, false, !tc, st);
     if (s != ACOM_OK) return s;
     cudaMemsetAsync(p->err, 0, sizeof(int), st);
@@ -587,8 +607,10 @@ acom_status acom_bounds(acom_plan p, const acom_peaks_csr* peaks, float* dst, vo
     RasterGeom geo{p->S, p->Spad, p->N, p->F, (float)p->dq, (float)p->delta, (float)p->gamma_pow, 0};
     for (int64_t c0 = 0; c0 < B; c0 += chunk) {
         const int nb = (int)std::min<int64_t>(chunk, B - c0);
+        float* xscale = tc && p->precision == ACOM_PREC_FP16 ? p->ws.xscale : nullptr;
         PatternSource src{tc ? p->ws.XB : nullptr, p->ws.PTs, peaks->row_ptr + c0, peaks->qx,
-                          peaks->qy, peaks->I, nb, (float)p->gamma_pow, (float)p->omega};
+                          peaks->qy, peaks->I, nb, (float)p->gamma_pow, (float)p->omega,
+                          xscale ? 1 : 0, xscale};
         RasterOut ro;
         ro.re = tc ? nullptr : p->ws.Xr;
         ro.im = tc ? nullptr : p->ws.Xi;
@@ -596,7 +618,7 @@ acom_status acom_bounds(acom_plan p, const acom_peaks_csr* peaks, float* dst, vo
         launch_raster_patterns(geo, src, ro, p->err, st);
         float* U = dst + c0 * (int64_t)p->Z;
         if (tc)
-            launch_contract_bound_tc(p, p->ws.map_x, p->ws.PTs, nb, U, st);
+            launch_contract_bound_tc(p, p->ws.map_x, p->ws.PTs, nb, U, st, xscale);
         else
             launch_contract_bound_fp32(p, p->ws.Xr, p->ws.Xi, nb, U, st);
     }

@@ -195,7 +195,7 @@ struct SelSmem {
     int* wi;         // [kSelWarps][kBatch] and axes
     int* cand;       // [kBatch]
     float* res;      // [kBatch][5] best value, its index bits, values at k - 1, k, k + 1
-    float* red;      // [kSelWarps]
+    float* red;      // [2][kSelWarps]
     SelState* st;
 };
 
@@ -304,6 +304,8 @@ struct SelectArgs {
     acom_result out;
     int64_t off;
     int* n_eval;                      // optional: total axes evaluated
+    const float* xscale;              // [nb] 2^e of FP16 pattern spectra, or nullptr
+    float inv_pscale;                 // 2^-k of FP16 plan spectra
 };
 
 // Spectra c_dir + i c_mir of the batch's candidate axes, scaled by 1/N, into
@@ -580,7 +582,7 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_select_exact(SelectArgs a) {
     sm.wi = reinterpret_cast<int*>(take(sizeof(int) * kSelWarps * kBatch));
     sm.cand = reinterpret_cast<int*>(take(sizeof(int) * kBatch));
     sm.res = reinterpret_cast<float*>(take(sizeof(float) * 5 * kBatch));
-    sm.red = reinterpret_cast<float*>(take(sizeof(float) * kSelWarps));
+    sm.red = reinterpret_cast<float*>(take(sizeof(float) * 2 * kSelWarps));
     sm.st = reinterpret_cast<SelState*>(take(sizeof(SelState)));
     sm.ev = take(Z);
 
@@ -598,20 +600,40 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_select_exact(SelectArgs a) {
             sm.U[z] = a.U[b * Z + z];
             sm.ev[z] = 0;
         }
-        // E_b: rounding margin valid for every axis
-        float e = 0.f;
+        // E_b: rounding margin valid for every axis.  FP16 operands add an
+        // absolute term for values below the normal range: an operand x is off
+        // by at most 2^-11 |x| + eta, so a dot product over Spad shells of
+        // 2^e X^ and 2^k P^ gains eta sqrt(Spad) (2^e ||X^_bf|| + 2^k ||P^_zf||)
+        // + Spad eta^2, i.e. after dividing by 2^(e+k)
+        //   eta sqrt(Spad) (||X^_bf|| 2^-k + ||P^_zf|| 2^-e + sqrt(Spad) eta 2^-(e+k)),
+        // charged four times for the four real products of c_f
+        const float inv_sc = a.xscale ? 1.0f / a.xscale[b] : 0.f;
+        const float tiny = (float)(kFp16Eta * sqrt((double)a.Spad)) * inv_sc * a.inv_pscale;
+        float e = 0.f, ea = 0.f;
         for (int f = threadIdx.x; f < F; f += kSelThreads) {
             const float w = (f == 0 || 2 * f == N) ? 1.f : 2.f;
             e = fmaf(w * a.pfmax[f], a.xfn[b * F + f], e);
+            ea = fmaf(w, a.xfn[b * F + f] * a.inv_pscale + a.pfmax[f] * inv_sc + tiny, ea);
         }
-        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-        if (lane == 0) sm.red[warp] = e;
+        for (int o = 16; o > 0; o >>= 1) {
+            e += __shfl_xor_sync(0xffffffffu, e, o);
+            ea += __shfl_xor_sync(0xffffffffu, ea, o);
+        }
+        if (lane == 0) {
+            sm.red[warp] = e;
+            sm.red[kSelWarps + warp] = ea;
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
-            float t = 0.f;
-            for (int w = 0; w < kSelWarps; ++w) t += sm.red[w];
+            float t = 0.f, ta = 0.f;
+            for (int w = 0; w < kSelWarps; ++w) {
+                t += sm.red[w];
+                ta += sm.red[kSelWarps + w];
+            }
             SelState& st = *sm.st;
-            st.Emax = a.kappa * t / (float)N * 1.01f;
+            const float abs_term =
+                a.xscale ? (float)(4.0 * kFp16Eta * sqrt((double)a.Spad)) * ta : 0.f;
+            st.Emax = (a.kappa * t + abs_term) / (float)N * 1.01f;
             st.T = -CUDART_INF_F;
             st.Tidx = 0xffffffffu;
             st.bz = st.bk = st.bm = 0;
@@ -680,18 +702,18 @@ size_t select_smem_bytes(int Z, int N, int F) {
     return r16(sizeof(float2) * N) + r16(sizeof(float2) * kBatch * (size_t)N) + r16(pb > yb ? pb : yb) +
            r16(sizeof(float) * Z) + 2 * r16(sizeof(float) * kSelWarps * kBatch) +
            r16(sizeof(int) * kBatch) + r16(sizeof(float) * 5 * kBatch) +
-           r16(sizeof(float) * kSelWarps) + r16(sizeof(SelState)) + r16(Z);
+           r16(sizeof(float) * 2 * kSelWarps) + r16(sizeof(SelState)) + r16(Z);
 }
 
 void launch_select_exact(const acom_plan_s* p, const float* Xsr, const float* Xsi, const float* U,
                          const float* xfn, const int2* srange, const float* pfmax,
                          const float* xnorm2, int nb,
                          float kappa, int refine, acom_result out, int64_t off, int* n_eval,
-                         cudaStream_t st) {
+                         cudaStream_t st, const float* xscale) {
     SelectArgs a{p->Psr, p->Psi, Xsr, Xsi, U, xfn, srange, pfmax, xnorm2, p->za, p->frames,
                  p->nbr_ptr,
                  p->nbr_idx, p->Z, p->F, p->N, p->S, p->Spad, nb, refine, kappa,
-                 fft_radices(p->N), out, off, n_eval};
+                 fft_radices(p->N), out, off, n_eval, xscale, 1.0f / p->pscale};
     const size_t smem = select_smem_bytes(p->Z, p->N, p->F);
     cudaFuncSetAttribute(k_select_exact, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int dev = 0, nsm = 0, per_sm = 0;

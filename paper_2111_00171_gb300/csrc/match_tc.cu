@@ -37,6 +37,7 @@
 // all roles, drains copies and MMAs in flight, frees TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 #include <math_constants.h>
 
@@ -57,9 +58,10 @@ constexpr int kThreads = (1 + kIssuers + kEpiWarps) * 32;
 constexpr uint32_t kTmemCols = 512;
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
 
-// instruction descriptor: D f32, A bf16, B bf16, both K-major, N = 256, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((256u >> 3) << 17) |
-                            ((128u >> 4) << 24);
+// instruction descriptors: D f32, A and B both bf16 (format 1) or both f16
+// (format 0), both K-major, N = 256, M = 128
+constexpr uint32_t kIdescF16 = (1u << 4) | ((256u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t kIdescBF16 = kIdescF16 | (1u << 7) | (1u << 10);
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -127,15 +129,15 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     return d;
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t accumulate) {
+__device__ __forceinline__ void mma_f16kind(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                            uint32_t idesc, uint32_t accumulate) {
     asm volatile(
         "{\n"
         ".reg .pred p;\n"
         "setp.ne.b32 p, %4, 0;\n"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
         "}\n" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 
@@ -226,6 +228,9 @@ struct TcArgs {
     int Zrows;                     // rows per frequency in the plan map (ZT * 128)
     float* U;                      // [nb][Z]
     int* err;
+    uint32_t idesc;                // MMA instruction descriptor (operand format)
+    const float* xscale;           // [nb] 2^e of FP16 pattern spectra, or nullptr
+    float inv_pscale;              // 2^-k of FP16 plan spectra (1 for BF16)
 };
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -371,7 +376,8 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
 #pragma unroll
                         for (int k16 = 0; k16 < kKT / 16; ++k16)
                             if (k16 < nk16)
-                                mma_bf16(dacc, xa + 2 * k16, pb + 2 * k16, (kt | k16) ? 1u : 0u);
+                                mma_f16kind(dacc, xa + 2 * k16, pb + 2 * k16, a.idesc,
+                                            (kt | k16) ? 1u : 0u);
                         mma_commit(smem_u32(empty + stage));       // frees the stage
                         if (++stage == kStages) stage = 0;
                     }
@@ -435,12 +441,15 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int b = pt * kNP + 8 * (2 * q + h) + (lane >> 2);
+                // FP16 spectra carry power-of-two scales: divide them out
+                const float sc =
+                    (a.xscale && b < a.nb) ? invN * a.inv_pscale / a.xscale[b] : invN;
 #pragma unroll
                 for (int n = 0; n < 4; ++n)
 #pragma unroll
                     for (int e = 0; e < 2; ++e) {
                         const int z = zt * kM + zq * 32 + 8 * n + 2 * (lane & 3) + e;
-                        if (b < a.nb && z < a.Z) a.U[(int64_t)b * a.Z + z] = ud[h * 8 + 2 * n + e] * invN;
+                        if (b < a.nb && z < a.Z) a.U[(int64_t)b * a.Z + z] = ud[h * 8 + 2 * n + e] * sc;
                         ud[h * 8 + 2 * n + e] = 0.f;
                     }
             }
@@ -481,9 +490,11 @@ static bool get_encoder() {
     return true;
 }
 
-// 2-D BF16 map: rows x cols (cols contiguous), boxes of 64 cols x 128 rows,
-// 128-byte swizzle; boxes reaching past the last column are zero-filled.
-acom_status make_bf16_map(void* map_storage, const void* base, uint64_t rows, uint64_t cols) {
+// 2-D BF16 (or FP16) map: rows x cols (cols contiguous), boxes of 64 cols x
+// 128 rows, 128-byte swizzle; boxes reaching past the last column are
+// zero-filled.
+acom_status make_bf16_map(void* map_storage, const void* base, uint64_t rows, uint64_t cols,
+                          bool fp16) {
     if (!get_encoder()) return set_error(ACOM_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
     if ((cols * 2) % 16 != 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0)
         return set_error(ACOM_ERR_INVALID_ARG, "tensor map: stride or base not 16-byte aligned");
@@ -492,7 +503,8 @@ acom_status make_bf16_map(void* map_storage, const void* base, uint64_t rows, ui
     const cuuint64_t strides[1] = {cols * 2};
     const cuuint32_t box[2] = {(cuuint32_t)tc::kKT, 128};
     const cuuint32_t estr[2] = {1, 1};
-    CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
+    CUresult r = g_encode(m, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                          2, const_cast<void*>(base), dims,
                           strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -503,7 +515,7 @@ acom_status make_bf16_map(void* map_storage, const void* base, uint64_t rows, ui
 size_t tensor_map_bytes() { return sizeof(CUtensorMap); }
 
 void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_stride, int nb,
-                              float* U, cudaStream_t st) {
+                              float* U, cudaStream_t st, const float* xscale) {
     tc::TcArgs a;
     a.F = p->F;
     a.N = p->N;
@@ -517,6 +529,9 @@ void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_st
     a.Zrows = p->Zp;
     a.U = U;
     a.err = p->err;
+    a.idesc = p->precision == ACOM_PREC_FP16 ? tc::kIdescF16 : tc::kIdescBF16;
+    a.xscale = xscale;
+    a.inv_pscale = 1.0f / p->pscale;
     const size_t smem = tc::tc_smem_bytes();
     cudaFuncSetAttribute(tc::k_contract_bound_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
@@ -534,9 +549,22 @@ void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_st
     prof_end(kKContractBf16, st);
 }
 
-// FP32 [Zp][F][Spad] planar -> BF16 [F][Zp][Spad] (frequency-major tiles)
+// FP32 [Zp][F][Spad] planar -> BF16 or FP16 of scale x [F][Zp][Spad]
+// (frequency-major tiles); scale is a power of two, exact in FP32.
+template <class T>
+__device__ __forceinline__ T to_half_type(float x);
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_half_type<__nv_bfloat16>(float x) {
+    return __float2bfloat16_rn(x);
+}
+template <>
+__device__ __forceinline__ __half to_half_type<__half>(float x) {
+    return __float2half_rn(x);
+}
+
+template <class T>
 __global__ void k_plan_to_bf16(const float* __restrict__ src, int Zp, int F, int Spad,
-                               __nv_bfloat16* __restrict__ dst) {
+                               T* __restrict__ dst, float scale) {
     const int64_t total = (int64_t)Zp * F * Spad;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -544,16 +572,21 @@ __global__ void k_plan_to_bf16(const float* __restrict__ src, int Zp, int F, int
         const int64_t t = i / Spad;
         const int z = (int)(t % Zp);
         const int f = (int)(t / Zp);
-        dst[i] = __float2bfloat16_rn(src[((int64_t)z * F + f) * Spad + s]);
+        dst[i] = to_half_type<T>(scale * src[((int64_t)z * F + f) * Spad + s]);
     }
 }
 
-void launch_plan_to_bf16(const float* src, int Zp, int F, int Spad, void* dst, cudaStream_t st) {
+void launch_plan_to_bf16(const float* src, int Zp, int F, int Spad, void* dst, cudaStream_t st,
+                         bool fp16, float scale) {
     const int64_t total = (int64_t)Zp * F * Spad;
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
     prof_begin(kKMisc, st);
-    k_plan_to_bf16<<<blocks, 256, 0, st>>>(src, Zp, F, Spad,
-                                           reinterpret_cast<__nv_bfloat16*>(dst));
+    if (fp16)
+        k_plan_to_bf16<__half><<<blocks, 256, 0, st>>>(src, Zp, F, Spad,
+                                                        reinterpret_cast<__half*>(dst), scale);
+    else
+        k_plan_to_bf16<__nv_bfloat16><<<blocks, 256, 0, st>>>(
+            src, Zp, F, Spad, reinterpret_cast<__nv_bfloat16*>(dst), 1.0f);
     prof_end(kKMisc, st);
 }
 

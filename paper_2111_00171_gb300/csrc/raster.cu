@@ -21,6 +21,7 @@
 // sums are deterministic).  Eight shells are staged in shared memory and
 // written in the requested layouts; ||X||^2 follows by Parseval.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <math_constants.h>
 
 #include "acom_internal.cuh"
@@ -60,6 +61,8 @@ struct PatternLoader {
     PatternSource src;
     __device__ void* xb_out() const { return src.xb; }
     __device__ int xb_tiles() const { return src.PTs; }
+    __device__ bool xb_half() const { return src.xb_fp16 != 0; }
+    __device__ float* xscale_out() const { return src.xscale; }
     __device__ int load(int64_t item, Peak* sp, int* s_warp, int* err) const {
         const int64_t b0 = src.row_ptr[item];
         const int64_t b1 = src.row_ptr[item + 1];
@@ -97,6 +100,8 @@ struct PlanLoader {
     float delta;
     __device__ void* xb_out() const { return nullptr; }
     __device__ int xb_tiles() const { return 0; }
+    __device__ bool xb_half() const { return false; }
+    __device__ float* xscale_out() const { return nullptr; }
     __device__ int load(int64_t item, Peak* sp, int* s_warp, int* err) const {
         const double* R = src.frames + 9 * item;
         double R00 = R[0], R01 = R[1], R02 = R[2], R10 = R[3], R11 = R[4], R12 = R[5],
@@ -147,6 +152,33 @@ size_t raster_smem_bytes(int N, int F) {
     b += sizeof(float) * F;            // per-frequency sums of |X^|^2 over shells
     b += sizeof(int) * 64;             // scratch (compaction, shell range, sums)
     return b;
+}
+
+// 2^e for the FP16 copy of pattern item's spectrum (every thread of the CTA,
+// one barrier): 2^e B <= kFp16Target with B = sum_m w_m n_m >= max |X^_sf|,
+// n_m = min(N, 2 delta / (max(r_m - delta, dq) dphi) + 3) the most bins a
+// peak's tent covers on any shell it reaches (tents are at most 1 and X >= 0).
+__device__ float fp16_pattern_scale(const Peak* sp, int np, const RasterGeom& geo, float dphi,
+                                    int* red) {
+    float b = 0.f;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        const Peak pk = sp[i];
+        const float qmin = fmaxf(pk.r - geo.delta, geo.dq);
+        const float n = fminf((float)geo.N, floorf(2.0f * geo.delta / (qmin * dphi)) + 3.0f);
+        b = fmaf(fabsf(pk.w), n, b);
+    }
+    for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = __float_as_int(b);
+    __syncthreads();
+    float tot = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += __int_as_float(red[w]);
+    if (!(tot > 0.f) || !isfinite(tot)) return 1.0f;
+    int e = (int)floorf(log2f(kFp16Target / tot));
+    e = e < -100 ? -100 : (e > 100 ? 100 : e);
+    float sc = ldexpf(1.0f, e);
+    if (sc * tot > kFp16Target) sc *= 0.5f;      // guard the log2 rounding
+    return sc;
 }
 
 template <class Loader, int NF2>
@@ -205,6 +237,12 @@ k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, int* err
             s_int[41] = 0;                   // one past the last
         }
         __syncthreads();
+        const bool half = ld.xb_out() && ld.xb_half();
+        float xsc = 1.0f;
+        if (half) {
+            xsc = fp16_pattern_scale(sp, np, geo, dphi, s_int + 56);
+            if (threadIdx.x == 0) ld.xscale_out()[item] = xsc;
+        }
         for (int s0 = 0; s0 < Spad; s0 += W) {
             const int s = s0 + warp;
             float ar[NF2], ai[NF2];
@@ -314,11 +352,15 @@ k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, int* err
                 for (int e = threadIdx.x; e < 2 * F; e += blockDim.x) {
                     const int f = e >> 1, c = e & 1;
                     const float* srcv = c ? st_im : st_re;
-                    __align__(16) __nv_bfloat16 v[8];
+                    __align__(16) unsigned short v[8];
 #pragma unroll
-                    for (int w = 0; w < 8; ++w) v[w] = __float2bfloat16_rn(srcv[w * F + f]);
+                    for (int w = 0; w < 8; ++w) {
+                        const float x = srcv[w * F + f];
+                        v[w] = half ? __half_as_ushort(__float2half_rn(x * xsc))
+                                    : __bfloat16_as_ushort(__float2bfloat16_rn(x));
+                    }
                     const int64_t row = ((int64_t)f * ld.xb_tiles() + tile) * 128 + (r >> 3) * 16 + c * 8 + (r & 7);
-                    *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(ld.xb_out()) +
+                    *reinterpret_cast<uint4*>(reinterpret_cast<unsigned short*>(ld.xb_out()) +
                                               row * Spad + s0) = *reinterpret_cast<uint4*>(v);
                 }
             }
@@ -466,6 +508,12 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
             s_int[41] = 0;
         }
         __syncthreads();
+        const bool half = xb && ld.xb_half();
+        float xsc = 1.0f;
+        if (half) {
+            xsc = fp16_pattern_scale(sp, np, geo, dphi, s_int + 56);
+            if (threadIdx.x == 0) ld.xscale_out()[item] = xsc;
+        }
         float fa[kMaxFPerLane];         // sum over this warp's shells of |X^_sf|^2, f = lane + 32 k
 #pragma unroll
         for (int k = 0; k < kMaxFPerLane; ++k) fa[k] = 0.f;
@@ -623,7 +671,12 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
                             out.im[o] = ai;
                             out.im[o + 1] = bi;
                         }
-                        if (xb) {
+                        if (half) {
+                            const __half2 vr = __floats2half2_rn(ar * xsc, br * xsc);
+                            const __half2 vi = __floats2half2_rn(ai * xsc, bi * xsc);
+                            stage[f * kFftStageWords + pw] = *reinterpret_cast<const uint32_t*>(&vr);
+                            stage[(F + f) * kFftStageWords + pw] = *reinterpret_cast<const uint32_t*>(&vi);
+                        } else if (xb) {
                             const __nv_bfloat162 vr = __floats2bfloat162_rn(ar, br);
                             const __nv_bfloat162 vi = __floats2bfloat162_rn(ai, bi);
                             stage[f * kFftStageWords + pw] = *reinterpret_cast<const uint32_t*>(&vr);

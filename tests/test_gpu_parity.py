@@ -269,21 +269,68 @@ def test_full_size_scan_sampled(full_scan):
     plan.close()
 
 
-# ----------------------------------------------------------------- BF16 path
+# ---------------------------------------------- tensor-core paths: BF16, FP16
 
+TC_PRECISIONS = [1, 2]
+TC_IDS = ["bf16", "fp16"]
+# relative error of the bounds against FP32: BF16 rounds each operand to 2^-8,
+# FP16 to 2^-11, so a product is off by at most 2^-7 and 2^-10
+TC_BOUND_TOL = {1: (2.0 ** -6, 2.0 ** -9), 2: (2.0 ** -9, 2.0 ** -12)}
+
+
+@pytest.mark.parametrize("precision", TC_PRECISIONS, ids=TC_IDS)
 @pytest.mark.parametrize("name", ["au_6deg_40x72", "au_2deg_75x180"])
-def test_bf16_bounds_track_fp32(name):
+def test_tc_bounds_track_fp32(name, precision):
     """The tcgen05 contraction's spectral bounds agree with the FP32 CUDA-core
-    bounds to BF16 operand rounding (relative error well under 2^-6)."""
+    bounds to the operands' rounding."""
     p32 = gpu_plan(name)
-    p16 = gpu_plan(name, precision=1)
+    p16 = gpu_plan(name, precision=precision)
     scan = synth.random_patterns(1001, n_patterns=100)
     u32 = p32.bounds(*to_dev(scan)).cpu().numpy()
     u16 = p16.bounds(*to_dev(scan)).cpu().numpy()
     rel = np.abs(u16 - u32) / np.maximum(np.abs(u32), 1e-30)
-    print(f"bf16 bound rel err {name}: max {rel.max():.3e} mean {rel.mean():.3e}")
+    print(f"{TC_IDS[precision - 1]} bound rel err {name}: max {rel.max():.3e} "
+          f"mean {rel.mean():.3e}")
     assert np.all(np.isfinite(u16))
-    assert rel.max() < 2.0 ** -6 and rel.mean() < 2.0 ** -9
+    tmax, tmean = TC_BOUND_TOL[precision]
+    assert rel.max() < tmax and rel.mean() < tmean
+    p32.close()
+    p16.close()
+
+
+@pytest.mark.parametrize("factor", [1e-6, 1.0, 1e6])
+def test_fp16_scaling_extreme_intensities(factor):
+    """FP16 operands carry a power-of-two scale per pattern: intensities of
+    1e6 (FP16 overflows at 65504) or 1e-6 (below its normal range) give the
+    bounds of the FP32 path on the same intensities, and the FP32 path's
+    winners."""
+    import torch
+    p32 = gpu_plan("au_2deg_75x180")
+    p16 = gpu_plan("au_2deg_75x180", precision=2)
+    scan = synth.random_patterns(1003, n_patterns=100)
+    rp, qx, qy, I = to_dev(scan)
+    Is = I * factor
+    u32 = p32.bounds(rp, qx, qy, Is).cpu().numpy()
+    u16 = p16.bounds(rp, qx, qy, Is).cpu().numpy()
+    assert np.all(np.isfinite(u16))
+    rel = np.abs(u16 - u32) / np.maximum(np.abs(u32), 1e-30 * factor)
+    assert rel.max() < 2.0 ** -9, rel.max()
+    a = p32.match(rp, qx, qy, Is)
+    torch.cuda.synchronize()
+    ev32 = p32.get_info()["last_evaluated"]
+    b = p16.match(rp, qx, qy, Is)
+    torch.cuda.synchronize()
+    ev = p16.get_info()["last_evaluated"]
+    np.testing.assert_allclose(b["score"].cpu().numpy(), a["score"].cpu().numpy(), rtol=1e-5)
+    ka = np.stack([a[k].cpu().numpy().astype(np.int64) for k in ("za_idx", "phi3_bin", "mirror")], 1)
+    kb = np.stack([b[k].cpu().numpy().astype(np.int64) for k in ("za_idx", "phi3_bin", "mirror")], 1)
+    op = oracle_plan("au_2deg_75x180")
+    for i in np.nonzero(np.any(ka != kb, axis=1))[0]:
+        mt = O.match_pattern(op, *scan.pattern(i))
+        assert check_argmax(mt, *ka[i]) and check_argmax(mt, *kb[i]), i
+    # the scale keeps the margin small: few axes beyond the FP32 bound's survivors
+    print(f"fp16 factor {factor:g}: {ev} axes evaluated, fp32 bound {ev32}")
+    assert ev <= 1.5 * ev32 + 20
     p32.close()
     p16.close()
 
@@ -298,28 +345,29 @@ def test_fp32_bounds_dominate_oracle_maxima(c1):
         assert np.all(u[b] >= mt.za_scores - 1e-5 * abs(mt.score)), b
 
 
-@pytest.fixture(scope="module")
-def c1_bf16():
-    plan = gpu_plan("au_2deg_75x180", precision=1)
+@pytest.fixture(scope="module", params=TC_PRECISIONS, ids=TC_IDS)
+def c1_tc(request):
+    plan = gpu_plan("au_2deg_75x180", precision=request.param)
     yield plan
     plan.close()
 
 
 @pytest.mark.parametrize("chunk", [0, 48])
-def test_match_bf16_matches_oracle(c1_bf16, chunk):
-    """BF16 tensor-core bounds + FP32 evaluation of the survivors: the oracle's
-    winner (up to ties) and FP32-level scores."""
+def test_match_tc_matches_oracle(c1_tc, chunk):
+    """BF16 or FP16 tensor-core bounds + FP32 evaluation of the survivors: the
+    oracle's winner (up to ties) and FP32-level scores."""
     scan = synth.random_patterns(1001, n_patterns=100)
-    _match_and_compare(c1_bf16, oracle_plan("au_2deg_75x180"), scan, chunk=chunk,
+    _match_and_compare(c1_tc, oracle_plan("au_2deg_75x180"), scan, chunk=chunk,
                        exhaustive=False)
 
 
-def test_full_size_bf16_equals_fp32(full_scan):
-    """The 256x256 scan, 1-degree plan: BF16 certified pruning returns the FP32
-    winners (differences only at FP32 ties, checked against the oracle)."""
+@pytest.mark.parametrize("precision", TC_PRECISIONS, ids=TC_IDS)
+def test_full_size_tc_equals_fp32(full_scan, precision):
+    """The 256x256 scan, 1-degree plan: BF16 or FP16 certified pruning returns
+    the FP32 winners (differences only at FP32 ties, checked against the oracle)."""
     import torch
     p32 = gpu_plan("au_1deg_150x360")
-    p16 = gpu_plan("au_1deg_150x360", precision=1)
+    p16 = gpu_plan("au_1deg_150x360", precision=precision)
     a = p32.match(*to_dev(full_scan))
     b = p16.match(*to_dev(full_scan))
     torch.cuda.synchronize()
@@ -333,7 +381,7 @@ def test_full_size_bf16_equals_fp32(full_scan):
         mt = O.match_pattern(op, *full_scan.pattern(i))
         assert check_argmax(mt, *ka[i]) and check_argmax(mt, *kb[i]), i
     ev = p16.get_info()["last_evaluated"] / full_scan.n_patterns
-    print(f"bf16 axes evaluated per pattern: {ev:.2f}")
+    print(f"{TC_IDS[precision - 1]} axes evaluated per pattern: {ev:.2f}")
     assert ev < 40
     p32.close()
     p16.close()

@@ -45,3 +45,20 @@ def test_bounds_static_matches_bounds_twice(precision):
     free1, _ = torch.cuda.mem_get_info()
     assert free1 >= free0
     plan.close()
+
+
+def test_bounds_static_fp16_plan_takes_fp32_path():
+    """An FP16 plan's static bounds are computed on the FP32 path: they equal
+    an FP32 plan's bounds."""
+    import torch
+    p16 = gpu_plan("au_2deg_75x180", precision=2)
+    p32 = gpu_plan("au_2deg_75x180", precision=0)
+    inputs = to_dev(synth.random_patterns(4243, n_patterns=200))
+    ref = p32.bounds(*inputs)
+    out = torch.full_like(ref, float("nan"))
+    p16.bounds_static(*inputs, out=out)
+    torch.cuda.synchronize()
+    b = ref.cpu().numpy()
+    np.testing.assert_allclose(out.cpu().numpy(), b, rtol=1e-6, atol=1e-6 * np.abs(b).max())
+    p16.close()
+    p32.close()
