@@ -30,6 +30,8 @@ polar_image               sparse polar image X (Correlation Pattern Matching)
 correlogram               C and C_mirror (Correlation Pattern Matching)
 direct_correlation        the same correlations as plain circular sums
 best_match                maximum over (zone axis, phi3, mirror)
+match_multi               several phases: one plan and one match per crystal
+                          structure (ACOM Integration); phase decision (reading)
 refine                    sub-grid refinement (the paper is silent; reading)
 orientation_matrix        Eq. 9/10 composition of the result
 kinematical_pattern       forward model (Calculation of Kinematical
@@ -424,10 +426,51 @@ def best_match(C, Cm, X=None):
                  C=C, Cm=Cm)
 
 
-def match_pattern(plan: Plan, qx, qy, I):
-    X = polar_image(qx, qy, I, plan.params)
+def match_image(plan: Plan, X):
     C, Cm = correlogram(plan.P_hat, X)
     return best_match(C, Cm, X)
+
+
+def match_pattern(plan: Plan, qx, qy, I):
+    return match_image(plan, polar_image(qx, qy, I, plan.params))
+
+
+# --------------------------------------------------------------------------
+# Several phases (ACOM Integration)
+# --------------------------------------------------------------------------
+
+
+@dataclass
+class MultiMatch:
+    phase: int                 # the phase decision
+    match: Match               # that phase's best (zone-axis index within the phase)
+    phase_scores: np.ndarray   # [n_phases] best raw correlation of each phase
+    matches: list              # every phase's Match
+
+
+def match_multi_image(plans, X):
+    """Match a polar image against the plan of every phase (ACOM Integration:
+    with several crystal structures, a plan and a correlation match per
+    structure).
+
+    reading (phase decision): the phase whose plan gives the highest raw
+    correlation.  Every slice of every plan has unit norm, so the scores of
+    different phases are comparable; an exact tie goes to the lower phase
+    index.  The plans must share shells, bins and image exponents, so one
+    polar image serves them all."""
+    p0 = plans[0].params
+    for p in plans[1:]:
+        q = p.params
+        assert (q.n_shells, q.dq, q.n_phi, q.delta, q.gamma_pow, q.omega) == \
+            (p0.n_shells, p0.dq, p0.n_phi, p0.delta, p0.gamma_pow, p0.omega)
+    ms = [match_image(p, X) for p in plans]
+    sc = np.array([m.score for m in ms])
+    ph = int(np.argmax(sc))        # the first maximum: lower phase on ties
+    return MultiMatch(phase=ph, match=ms[ph], phase_scores=sc, matches=ms)
+
+
+def match_multi(plans, qx, qy, I):
+    return match_multi_image(plans, polar_image(qx, qy, I, plans[0].params))
 
 
 # --------------------------------------------------------------------------

@@ -202,6 +202,29 @@ def random_patterns(seed, n_patterns=100, crystal=None, q_max=1.5, lam=0.01969,
                 f"{n_patterns} random {spec.name} patterns, seed {seed}")
 
 
+def mixed_patterns(seed, n_patterns=100, crystals=None, q_max=1.5, lam=0.01969,
+                   sigma=0.02, rel_threshold=1e-3, max_peaks=40,
+                   pos_noise=0.005, int_noise=0.1):
+    """Independent patterns whose phase is drawn uniformly from ``crystals``
+    (50/50 for two), each at a uniformly random orientation, with the peak
+    rules of ``random_patterns``."""
+    rng = np.random.default_rng(seed)
+    specs = tuple(crystals or (au_fcc(), mg_hcp()))
+    tables = [reflection_table(s, q_max) for s in specs]
+    phase = rng.integers(0, len(specs), n_patterns).astype(np.int32)
+    R = random_rotations(rng, n_patterns)
+    lists, counts = [], []
+    for b in range(n_patterns):
+        x, y, i = _sorted_list(*tables[phase[b]], R[b], lam, sigma)
+        n = min(int(np.sum(i > rel_threshold * i[0])), max_peaks)
+        lists.append((x, y, i))
+        counts.append(n)
+    rp, qx, qy, I = _assemble(lists, np.array(counts), rng, pos_noise, int_noise)
+    names = "/".join(s.name for s in specs)
+    return Scan(rp, qx, qy, I, R, phase, specs,
+                f"{n_patterns} random patterns of {names}, seed {seed}")
+
+
 def grain_scan(seed, H=256, W=256, n_grains=200, crystals=None, q_max=1.5,
                lam=0.01969, sigma=0.02, peaks="uniform10-60",
                pos_noise=0.005, int_noise=0.1):

@@ -440,3 +440,72 @@ def test_refinement_reduces_offgrid_error(c1_plan):
         grid_err.append(O.misorientation_deg(mg, m, ops, True))
         ref_err.append(O.misorientation_deg(rf.m, m, ops, True))
     assert np.mean(ref_err) < np.mean(grid_err)
+
+
+# ---------------------------------------------------------- several phases --
+
+@pytest.fixture(scope="module")
+def two_phase_plans():
+    """fcc Au (cubic triangle) and hcp Mg (hexagonal triangle) plans on 6-degree
+    grids with the same shells, bins and tent, so one polar image serves both."""
+    prm = O.PlanParams(n_shells=40, dq=0.0375, n_phi=72, delta=0.08, lam=LAM)
+    v0, v1, v2, om = O.cubic_triangle()
+    au = O.orientation_plan(au_reflections(), O.zone_axis_grid(v0, v1, v2, 6.0, om), prm)
+    mg_refl = O.reflections(mg_lattice(), MG_POS, [12.0] * 2, [0.3] * 2, 1.5)
+    v0, v1, v2, om = O.hexagonal_triangle()
+    mg = O.orientation_plan(mg_refl, O.zone_axis_grid(v0, v1, v2, 6.0, om), prm)
+    return (au, mg), (au_reflections(), mg_refl)
+
+
+def test_multi_phase_self_indexing(two_phase_plans):
+    """X := P_z of phase p scores exactly 1 in phase p (Cauchy-Schwarz with
+    unit-norm slices) and strictly less in the other phase, whose slices all
+    differ from it: the decision is p."""
+    plans, _ = two_phase_plans
+    rng = np.random.default_rng(11)
+    for p in (0, 1):
+        for z in rng.choice(len(plans[p].za), 4, replace=False):
+            mm = O.match_multi_image(plans, plans[p].P[z])
+            assert mm.phase == p
+            assert abs(mm.phase_scores[p] - 1.0) < 1e-12
+            assert mm.phase_scores[1 - p] < 1.0 - 1e-6
+            assert mm.match is mm.matches[p]
+
+
+def test_multi_phase_scores_are_brute_force_maxima(two_phase_plans):
+    """Each phase's score is the maximum over that phase's axes, phi3 bins and
+    mirror of the plain circular sums; the decision is the larger one."""
+    plans, _ = two_phase_plans
+    prm = plans[0].params
+    rng = np.random.default_rng(12)
+    q = rng.uniform(0.3, 1.4, 20)
+    g = rng.uniform(-math.pi, math.pi, 20)
+    X = O.polar_image(q * np.cos(g), q * np.sin(g), rng.uniform(1, 5, 20), prm)
+    mm = O.match_multi_image(plans, X)
+    best = []
+    for p, plan in enumerate(plans):
+        C, Cm = O.direct_correlation(plan.P, X)
+        best.append(max(C.max(), Cm.max()))
+        assert mm.phase_scores[p] == pytest.approx(best[p], rel=1e-12)
+    assert mm.phase == int(np.argmax(best))
+
+
+def test_multi_phase_tie_goes_to_lower_phase(two_phase_plans):
+    (au, _), _ = two_phase_plans
+    mm = O.match_multi_image([au, au], au.P[3])
+    assert mm.phase == 0 and mm.phase_scores[0] == mm.phase_scores[1]
+
+
+def test_multi_phase_noiseless_patterns_get_their_phase(two_phase_plans):
+    """Noiseless kinematical patterns of either phase at grid orientations
+    are assigned the phase they were generated from."""
+    plans, refls = two_phase_plans
+    rng = np.random.default_rng(13)
+    for p in (0, 1):
+        za = plans[p].za
+        N = plans[p].params.n_phi
+        for z in rng.choice(len(za), 6, replace=False):
+            m = O.orientation_matrix(za[z], -2 * math.pi * int(rng.integers(N)) / N,
+                                     int(rng.integers(2)))
+            qx, qy, I = O.kinematical_pattern(refls[p], m, LAM, 0.02, 1e-3)
+            assert O.match_multi(plans, qx, qy, I).phase == p, (p, z)
