@@ -10,12 +10,19 @@ transform, shell contraction, inverse transform + argmax, refinement).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp16|fp32]
   python bench.py --impl reference ...   # the FP64 CPU oracle as the reference arm
+  python bench.py --workload mixed ...   # two phases in one plan (see below)
 
 The default precision is BF16 operands on the tensor cores for the certified
 bound, with every winner evaluated exactly in FP32; fp16 takes FP16 operands
 with per-pattern power-of-two scaling instead.  Under torchrun (N > 1)
 every rank matches its own scan (weak scaling, scan seed + rank); there is no
 collective on the data path; rank 0 prints one JSON line.
+
+--workload mixed: 65,536 independent patterns drawn 50/50 from fcc Au and hcp
+Mg (peaks above 1e-3 of the strongest, at most 40) matched against one plan
+holding the Au 2-degree grid (231 axes) and the Mg 1-degree grid (1770 axes),
+75 shells of 0.02 1/A, 180 bins; every pattern gets each phase's best score
+and a phase decision.
 """
 
 import argparse
@@ -34,10 +41,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "patterns indexed/s on 1 GB300, % of roofline, mean misorientation (deg)"
-W = dict(name="au_scan_256x256_1deg", step=1.0, S=150, dq=0.01, N=360, seed=1002, H=256,
-         Wd=256, grains=200, delta=0.08, lam=0.01969, q_max=1.5)
-WORKLOAD_TEXT = ("fcc Au 256x256 scan (65,536 patterns, 10-60 peaks each, CSR, 200 Voronoi "
-                 "grains) vs 1-degree plan (903 zone axes, 150 shells x 0.01 1/A, 360 phi3 bins)")
+W = dict(name="au_scan_256x256_1deg", phases=(("Au", 1.0),), Z=903, step=1.0, S=150, dq=0.01,
+         N=360, seed=1002, H=256, Wd=256, grains=200, delta=0.08, lam=0.01969, q_max=1.5,
+         text=("fcc Au 256x256 scan (65,536 patterns, 10-60 peaks each, CSR, 200 Voronoi "
+               "grains) vs 1-degree plan (903 zone axes, 150 shells x 0.01 1/A, 360 phi3 bins)"))
+MIXED = dict(name="au2deg_mg1deg_mixed_65536", phases=(("Au", 2.0), ("Mg", 1.0)), Z=231 + 1770,
+             step=None, S=75, dq=0.02, N=180, seed=1003, n_patterns=65536,
+             text=("65,536 patterns, 50/50 fcc Au / hcp Mg (peaks > 1e-3 of the strongest, "
+                   "at most 40, CSR) vs one plan of the Au 2-degree (231 axes) and Mg "
+                   "1-degree (1770 axes) grids, 75 shells x 0.02 1/A, 180 phi3 bins"))
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -55,7 +67,19 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=16)
     ap.add_argument("--scan", default="256x256",
                     help="scan size HxW (smaller sizes are for profiling captures only)")
-    return ap.parse_args()
+    ap.add_argument("--workload", default="au_scan", choices=["au_scan", "mixed"])
+    args = ap.parse_args()
+    if args.workload == "mixed":
+        W.update(MIXED)
+    return args
+
+
+def make_scan(seed, args):
+    import synth
+    if "n_patterns" in W:
+        return synth.mixed_patterns(seed, n_patterns=W["n_patterns"])
+    H, Wd = (int(v) for v in args.scan.split("x"))
+    return synth.grain_scan(seed, H=H, W=Wd)
 
 
 def peaks_file():
@@ -132,10 +156,20 @@ def cubic_ops():
     return np.array(ops)
 
 
-def misorientation(m_est, m_true):
+def hexagonal_ops():
+    """The 12 proper rotations of 622 (c along z, a along x)."""
+    ops = []
+    for k in range(6):
+        c, s = math.cos(k * math.pi / 3), math.sin(k * math.pi / 3)
+        Rz = np.array([[c, -s, 0], [s, c, 0], [0, 0, 1.0]])
+        ops += [Rz, Rz @ np.diag([1.0, -1.0, -1.0])]
+    return np.array(ops)
+
+
+def misorientation(m_est, m_true, ops=None):
     """Mean symmetry-reduced misorientation (deg), also reduced over the
     in-plane Friedel twin m Rz(pi), and the zone-axis tilt error."""
-    ops = cubic_ops()
+    ops = cubic_ops() if ops is None else ops
     me = m_est.astype(np.float64)
     # re-orthonormalise the FP32-stored matrices before taking angles
     u, _, vt = np.linalg.svd(me)
@@ -161,31 +195,51 @@ def misorientation(m_est, m_true):
 
 # ------------------------------------------------------------- oracle leg
 
-def oracle_plan(za_subset=None):
+def oracle_plans(stride=1):
+    """The oracle's plan of every phase of the workload (every stride-th
+    zone axis)."""
     from oracle import acom_oracle as O
-    refl = O.reflections(np.eye(3) * 4.08, [[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0]],
-                         [79.0] * 4, [0.25] * 4, W["q_max"])
-    v0, v1, v2, om = O.cubic_triangle()
-    za = O.zone_axis_grid(v0, v1, v2, W["step"], om)
-    if za_subset is not None:
-        za = za[za_subset]
-    return O.orientation_plan(refl, za, O.PlanParams(W["S"], W["dq"], W["N"], W["delta"],
-                                                     lam=W["lam"]))
+    plans = []
+    for phase, step in W["phases"]:
+        if phase == "Au":
+            refl = O.reflections(np.eye(3) * 4.08,
+                                 [[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0]],
+                                 [79.0] * 4, [0.25] * 4, W["q_max"])
+            v0, v1, v2, om = O.cubic_triangle()
+        else:
+            a, c = 3.21, 5.21
+            L = np.array([[a, 0, 0], [-a / 2, a * math.sqrt(3) / 2, 0], [0, 0, c]])
+            refl = O.reflections(L, [[1 / 3, 2 / 3, .25], [2 / 3, 1 / 3, .75]], [12.0] * 2,
+                                 [0.3] * 2, W["q_max"])
+            v0, v1, v2, om = O.hexagonal_triangle()
+        za = O.zone_axis_grid(v0, v1, v2, step, om)[::stride]
+        plans.append(O.orientation_plan(refl, za, O.PlanParams(W["S"], W["dq"], W["N"],
+                                                               W["delta"], lam=W["lam"])))
+    return plans
+
+
+def oracle_match(plans, qx, qy, I):
+    """The oracle's best over all phases' axes (global axis index)."""
+    from oracle import acom_oracle as O
+    if len(plans) == 1:
+        return O.match_pattern(plans[0], qx, qy, I)
+    mm = O.match_multi(plans, qx, qy, I)
+    return O.best_match(np.concatenate([m.C for m in mm.matches]),
+                        np.concatenate([m.Cm for m in mm.matches]))
 
 
 def cpu_baseline(scan, gpu_res, n_sample):
     """The oracle as it stands on this host: full plan build timed once, then
     n_sample patterns matched; extrapolated to the whole scan."""
-    from oracle import acom_oracle as O
     t0 = time.perf_counter()
-    plan = oracle_plan()
+    plans = oracle_plans()
     t_plan = time.perf_counter() - t0
     rng = np.random.default_rng(0)
     idx = rng.choice(scan.n_patterns, n_sample, replace=False)
     agree = 0
     t0 = time.perf_counter()
     for b in idx:
-        mt = O.match_pattern(plan, *scan.pattern(b))
+        mt = oracle_match(plans, *scan.pattern(b))
         z, k, m = (int(gpu_res["za_idx"][b]), int(gpu_res["phi3_bin"][b]),
                    int(gpu_res["mirror"][b]))
         val = (mt.Cm if m else mt.C)[z, k]
@@ -194,8 +248,8 @@ def cpu_baseline(scan, gpu_res, n_sample):
     B = scan.n_patterns
     value = B / (t_plan + B * t_match)
     return {"value": value, "unit": "patterns/s", "cores": 1, "kind": "oracle",
-            "sample": (f"FP64 NumPy oracle, single thread: full 903-axis plan build timed "
-                       f"once ({t_plan:.1f} s) + {n_sample} sampled patterns matched "
+            "sample": (f"FP64 NumPy oracle, single thread: full {W['Z']}-axis plan build "
+                       f"timed once ({t_plan:.1f} s) + {n_sample} sampled patterns matched "
                        f"({t_match * 1e3:.0f} ms each), extrapolated to {B} patterns")}, \
         f"{agree}/{n_sample}"
 
@@ -210,36 +264,33 @@ def reference_arm(args):
     from paper_2111_00171_gb300.ranks import rank_env
     if rank_env()[1] != 0:
         return
-    import synth
-    from oracle import acom_oracle as O
-    scan = synth.grain_scan(W["seed"])
-    full = oracle_plan()                    # set-up: the plan the sampled patterns match against
-    Z = len(full.za)
-    sub = np.arange(0, Z, 16)
+    scan = make_scan(W["seed"], args)
+    full = oracle_plans()                   # set-up: the plans the sampled patterns match against
+    Z = sum(len(p.za) for p in full)
     rng = np.random.default_rng(1)
     vals = []
     tot = 0.0
     for it in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        oracle_plan(sub)
-        t_plan = (time.perf_counter() - t0) * Z / len(sub)
+        nsub = sum(len(p.za) for p in oracle_plans(16))
+        t_plan = (time.perf_counter() - t0) * Z / nsub
         bs = rng.choice(scan.n_patterns, 2, replace=False)
         t0 = time.perf_counter()
         for b in bs:
-            O.match_pattern(full, *scan.pattern(b))
+            oracle_match(full, *scan.pattern(b))
         t_p = (time.perf_counter() - t0) / len(bs)
         if it >= args.warmup:
             B = scan.n_patterns
             vals.append(B / (t_plan + B * t_p))
             tot += t_plan + B * t_p
     v = float(np.mean(vals))
-    sample = (f"each step: plan build on {len(sub)} of {Z} zone axes (scaled by {Z / len(sub):.1f}) "
+    sample = (f"each step: plan build on every 16th of {Z} zone axes (scaled up) "
               f"+ 2 sampled patterns; extrapolated to {scan.n_patterns} patterns")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "patterns/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_TEXT, "patterns": scan.n_patterns},
+            "config": {"workload": W["text"], "patterns": scan.n_patterns},
             "cpu_baseline": {"value": v, "unit": "patterns/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": "patterns/s", "h2d_bytes_per_step": 0,
@@ -269,36 +320,47 @@ def main():
     prec = {"bf16": acom.ACOM_PREC_BF16, "fp16": acom.ACOM_PREC_FP16,
             "fp32": acom.ACOM_PREC_FP32}[args.precision]
 
-    H, Wd = (int(v) for v in args.scan.split("x"))
-    scan = synth.grain_scan(rank_seed(rank), H=H, W=Wd)
+    scan = make_scan(rank_seed(rank), args)
     B = scan.n_patterns
+    mixed = len(W["phases"]) > 1
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     d_in = (dev(scan.row_ptr), dev(scan.qx), dev(scan.qy), dev(scan.I))
     h_in = tuple(torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
                  for a in (scan.row_ptr, scan.qx, scan.qy, scan.I))
     h2d = sum(t.numel() * t.element_size() for t in h_in)
-    v, om = acom.cubic_triangle()
-    cr = acom.au_crystal()
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def make_plan():
-        return acom.Plan(cr, v, om, W["step"], W["S"], W["dq"], W["N"], delta=W["delta"],
-                         lam=W["lam"], q_max=W["q_max"], precision=prec)
+        parts = []
+        for phase, step_deg in W["phases"]:
+            v, om = acom.cubic_triangle() if phase == "Au" else acom.hexagonal_triangle()
+            cr = acom.au_crystal() if phase == "Au" else acom.mg_crystal()
+            parts.append(acom.Plan(cr, v, om, step_deg, W["S"], W["dq"], W["N"],
+                                   delta=W["delta"], lam=W["lam"], q_max=W["q_max"],
+                                   precision=prec))
+        if len(parts) == 1:
+            return parts[0]
+        p = acom.Plan.concat(parts)
+        for q in parts:
+            q.close()
+        return p
 
-    out_keys = ("za_idx", "phi3_bin", "mirror", "score", "score_cos", "phi3", "orient")
+    out_keys = ("za_idx", "phi3_bin", "mirror", "score", "score_cos", "phi3", "orient") + \
+        (("phase", "phase_score") if mixed else ())
 
     stats = {}
 
     def step(inputs, out):
         p = make_plan()
-        p.match(*inputs, chunk=args.chunk, out=out, exhaustive=args.exhaustive)
+        p.match(*inputs, chunk=args.chunk, out=out, exhaustive=args.exhaustive,
+                phase_scores=mixed)
         stats["evaluated"] = p.get_info()["last_evaluated"]
         p.close()
         return out
 
     probe = make_plan()
-    out = probe.alloc_result(B)
+    out = probe.alloc_result(B, phase_scores=mixed)
     probe.close()
     for _ in range(args.warmup):
         step(d_in, out)
@@ -356,7 +418,22 @@ def main():
         return
 
     res = {k: out[k].cpu().numpy() for k in out_keys}
-    mis, mis_twin, tilt = misorientation(res["orient"], scan.truth)
+    if mixed:
+        ph = res["phase"]
+        ok = ph == scan.phase
+        accuracy = {"phase_decision_correct": float(ok.mean())}
+        for p, (name, _) in enumerate(W["phases"]):
+            sel = ok & (scan.phase == p)
+            if not sel.any():
+                continue
+            m, mt, t = misorientation(res["orient"][sel], scan.truth[sel],
+                                      cubic_ops() if name == "Au" else hexagonal_ops())
+            accuracy[name] = {"mean_misorientation_deg": m, "mean_misorientation_friedel_deg": mt,
+                              "mean_za_tilt_deg": t, "patterns": int(sel.sum())}
+    else:
+        mis, mis_twin, tilt = misorientation(res["orient"], scan.truth)
+        accuracy = {"mean_misorientation_deg": mis, "mean_misorientation_friedel_deg": mis_twin,
+                    "mean_za_tilt_deg": tilt}
     peaks, src = peaks_file()
     K = args.steps
     value = world * B * K / (dev_ms / 1e3)
@@ -366,8 +443,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "fp16": "f16", "bf16": "bf16"}[args.precision],
             "data": "synthetic",
-            "config": {"workload": WORKLOAD_TEXT, "patterns_per_gpu": B,
-                       "peaks_nnz": int(scan.row_ptr[-1]), "zone_axes": 903, "shells": W["S"],
+            "config": {"workload": W["text"], "patterns_per_gpu": B,
+                       "peaks_nnz": int(scan.row_ptr[-1]), "zone_axes": W["Z"], "shells": W["S"],
                        "n_phi": W["N"], "precision": args.precision,
                        "chunk": args.chunk or (1024 if args.exhaustive else 8192),
                        "mode": "exhaustive" if args.exhaustive else "certified pruning",
@@ -381,8 +458,7 @@ def main():
             "gpu_launches": int(launches),
             "clocks": ck,
             "kernels_ms_per_step": {n: round(ms / K, 3) for n, (c, ms) in prof.items() if c},
-            "accuracy": {"mean_misorientation_deg": mis, "mean_misorientation_friedel_deg": mis_twin,
-                         "mean_za_tilt_deg": tilt}}
+            "accuracy": accuracy}
     if not args.no_cpu_baseline and world == 1:
         cb, agree = cpu_baseline(scan, res, args.cpu_sample)
         line["cpu_baseline"] = cb
@@ -408,11 +484,13 @@ def read_profile(lib, acom):
 # DRAM bytes per pattern (read + write) of kernels whose traffic grows with
 # the patterns of a launch, from the ncu capture summarised in
 # profiles/ncu_full_bf16_au_scan_64x64_1deg.md, with a hash of the kernel's
-# sources at capture time and the precision of the captured run: a changed
-# kernel, or a run at another precision, reports no traffic.
+# sources at capture time, the precision and the workload of the captured
+# run: a changed kernel, or another precision or workload, reports no traffic.
 TRAFFIC_PER_PATTERN = {
-    "select_exact": (360076.0, ("match_prune.cu",), "e9c572a4179f2cc6", "bf16"),
-    "raster_patterns": (340215.0, ("raster.cu",), "3c26ac06f0283b45", "bf16"),
+    "select_exact": (360076.0, ("match_prune.cu",), "e9c572a4179f2cc6", "bf16",
+                     "au_scan_256x256_1deg"),
+    "raster_patterns": (340215.0, ("raster.cu",), "3c26ac06f0283b45", "bf16",
+                        "au_scan_256x256_1deg"),
 }
 
 
@@ -430,7 +508,7 @@ def kernel_traffic(name, pats, precision):
     """DRAM bytes of one launch of ``pats`` patterns, scaled from the capture
     (traffic of these kernels grows in proportion to the patterns), or None."""
     t = TRAFFIC_PER_PATTERN.get(name)
-    if t is None or sources_hash(t[1]) != t[2] or precision != t[3]:
+    if t is None or sources_hash(t[1]) != t[2] or precision != t[3] or W["name"] != t[4]:
         return None
     return t[0] * pats
 
@@ -438,7 +516,7 @@ def kernel_traffic(name, pats, precision):
 def kernel_roofline(name, cnt, ms, peaks, src, B, K, nnz, precision):
     """Achieved rate of one kernel class: algorithmic work per launch over its
     event-timed average launch duration."""
-    Z, S, N = 903, W["S"], W["N"]
+    Z, S, N = W["Z"], W["S"], W["N"]
     F = N // 2 + 1
     avg_s = ms / cnt / 1e3 if cnt else float("nan")
     pats = B * K / cnt if cnt else 0          # patterns per launch

@@ -134,9 +134,40 @@ typedef struct {
     int32_t precision;
     int64_t device_bytes;     /* device memory owned by the plan                */
     int64_t last_evaluated;   /* zone axes evaluated in full by the last match  */
+    int32_t n_phases;         /* crystal structures (1 unless concatenated)     */
 } acom_plan_info;
 
 acom_status acom_plan_get_info(acom_plan plan, acom_plan_info* info);
+
+/*
+ * acom_plan_concat - one plan for a sample of several phases (section "ACOM
+ * Integration": with several crystal structures there is one orientation plan
+ * and one correlation match per structure).  The zone axes of plans[0] come
+ * first, then those of plans[1], and so on; phase p owns the axes
+ * [offset_p, offset_{p+1}) (acom_plan_get_phases).  One acom_match on the
+ * result rasterises each pattern once, contracts it against every phase's
+ * axes in the same launches, and returns the best over all phases (so the
+ * phase decision is the phase of the winning axis: the highest raw
+ * correlation, ties to the lower phase) and, on request, each phase's best
+ * score.
+ *
+ *   plans     : n_plans (1..8 phases in total; an input may itself be a
+ *               concatenation) plans on the current device with equal n_shells,
+ *               dq, n_phi, delta, gamma_pow, omega and precision, so that one
+ *               polar image serves them all; ACOM_ERR_INVALID_ARG otherwise.
+ *               They are read, not taken: the caller still owns and destroys
+ *               them.
+ *   cuda_stream: stream of the copies; the call synchronises it once.
+ *   out       : receives the new plan, which owns copies of the inputs'
+ *               spectra, axes, frames and neighbour lists (neighbours stay
+ *               within their phase).
+ */
+acom_status acom_plan_concat(const acom_plan* plans, int32_t n_plans, void* cuda_stream,
+                             acom_plan* out);
+
+/* Copy the phase offsets (n_phases + 1 values: 0, Z_0, Z_0 + Z_1, ..., Z) to
+ * HOST memory ``dst``.  Synchronous. */
+acom_status acom_plan_get_phases(acom_plan plan, int32_t* dst);
 
 /* Copy the zone axes (unit vectors, crystal Cartesian) to HOST memory
  * ``dst`` [Z][3].  Synchronous. */
@@ -180,6 +211,12 @@ typedef struct {
  *             every axis that was evaluated (the winner and every axis whose
  *             bound could reach it) and is otherwise an upper bound of the
  *             axis' maximum (the bound of acom_bounds plus a rounding margin).
+ *   phase     optional: the phase of za_idx (0 for a single-phase plan)
+ *   phase_score optional: [n_patterns][n_phases] the best score of each
+ *             phase (its maximum over its axes, phi3 and mirror).  With
+ *             certified pruning, asking for it makes the search certify every
+ *             phase's best, not only the overall winner; 0 for an all-zero
+ *             image.
  * Ties: the lowest zone-axis index wins, then C before C_mirror, then the
  * lowest phi3 bin.
  */
@@ -192,6 +229,8 @@ typedef struct {
     float* phi3;
     float* orient;
     float* za_scores;
+    int32_t* phase;
+    float* phase_score;
 } acom_result;
 
 typedef struct {

@@ -28,7 +28,7 @@ EXPORTED = ("acom_plan_create", "acom_plan_destroy", "acom_plan_get_info",
             "acom_polar_spectra", "acom_bounds", "acom_bounds_static", "acom_status_str",
             "acom_last_error",
             "acom_version", "acom_profile_enable", "acom_profile_reset", "acom_profile_read",
-            "acom_kernel_launches")
+            "acom_kernel_launches", "acom_plan_concat", "acom_plan_get_phases")
 
 
 class AcomError(RuntimeError):
@@ -60,7 +60,8 @@ class PlanOpts(C.Structure):
 class PlanInfo(C.Structure):
     _fields_ = [("n_za", C.c_int32), ("n_shells", C.c_int32), ("n_phi", C.c_int32),
                 ("n_freq", C.c_int32), ("n_reflections", C.c_int32), ("precision", C.c_int32),
-                ("device_bytes", C.c_int64), ("last_evaluated", C.c_int64)]
+                ("device_bytes", C.c_int64), ("last_evaluated", C.c_int64),
+                ("n_phases", C.c_int32)]
 
 
 class PeaksCSR(C.Structure):
@@ -71,7 +72,8 @@ class PeaksCSR(C.Structure):
 class Result(C.Structure):
     _fields_ = [("za_idx", C.c_void_p), ("phi3_bin", C.c_void_p), ("mirror", C.c_void_p),
                 ("score", C.c_void_p), ("score_cos", C.c_void_p), ("phi3", C.c_void_p),
-                ("orient", C.c_void_p), ("za_scores", C.c_void_p)]
+                ("orient", C.c_void_p), ("za_scores", C.c_void_p), ("phase", C.c_void_p),
+                ("phase_score", C.c_void_p)]
 
 
 class MatchOpts(C.Structure):
@@ -101,6 +103,8 @@ def load_library():
                                      C.POINTER(P)]
     lib.acom_plan_destroy.argtypes = [P]
     lib.acom_plan_get_info.argtypes = [P, C.POINTER(PlanInfo)]
+    lib.acom_plan_concat.argtypes = [C.POINTER(P), C.c_int32, P, C.POINTER(P)]
+    lib.acom_plan_get_phases.argtypes = [P, C.POINTER(C.c_int32)]
     lib.acom_plan_get_zone_axes.argtypes = [P, P]
     lib.acom_plan_get_spectra.argtypes = [P, P, P]
     lib.acom_match.argtypes = [P, C.POINTER(PeaksCSR), C.POINTER(MatchOpts), C.POINTER(Result), P]
@@ -116,6 +120,7 @@ def load_library():
     lib.acom_last_error.restype = C.c_char_p
     lib.acom_version.restype = C.c_int32
     for name in ("acom_plan_create", "acom_plan_destroy", "acom_plan_get_info",
+                 "acom_plan_concat", "acom_plan_get_phases",
                  "acom_plan_get_zone_axes", "acom_plan_get_spectra", "acom_match",
                  "acom_polar_spectra", "acom_bounds", "acom_bounds_static"):
         getattr(lib, name).restype = C.c_int
@@ -200,6 +205,27 @@ class Plan:
         self.step_deg = float(step_deg)
         self.info = self.get_info()
 
+    @classmethod
+    def concat(cls, plans, stream=None):
+        """One plan over the zone axes of several phases' plans
+        (acom_plan_concat); the inputs stay owned by the caller."""
+        lib = load_library()
+        arr = (C.c_void_p * len(plans))(*(p.handle.value for p in plans))
+        h = C.c_void_p()
+        _check(lib.acom_plan_concat(arr, len(plans), _stream_ptr(stream), C.byref(h)))
+        self = cls.__new__(cls)
+        self._lib = lib
+        self.handle = h
+        self.step_deg = plans[0].step_deg
+        self.info = self.get_info()
+        return self
+
+    def phases(self):
+        """Phase offsets [n_phases + 1]: phase p owns axes [off[p], off[p+1])."""
+        out = (C.c_int32 * (self.info["n_phases"] + 1))()
+        _check(self._lib.acom_plan_get_phases(self.handle, out))
+        return np.array(out[:], dtype=np.int64)
+
     def close(self):
         if getattr(self, "handle", None) and self.handle.value:
             _check(self._lib.acom_plan_destroy(self.handle))
@@ -274,7 +300,7 @@ class Plan:
                                             _stream_ptr(stream)))
         return out
 
-    def alloc_result(self, n, za_scores=False, orient=True):
+    def alloc_result(self, n, za_scores=False, orient=True, phase_scores=False):
         import torch
         dev = "cuda"
         r = {"za_idx": torch.empty(n, dtype=torch.int32, device=dev),
@@ -287,13 +313,19 @@ class Plan:
             r["orient"] = torch.empty((n, 3, 3), dtype=torch.float32, device=dev)
         if za_scores:
             r["za_scores"] = torch.empty((n, self.info["n_za"]), dtype=torch.float32, device=dev)
+        if phase_scores:
+            r["phase"] = torch.empty(n, dtype=torch.int32, device=dev)
+            r["phase_score"] = torch.empty((n, self.info["n_phases"]), dtype=torch.float32,
+                                           device=dev)
         return r
 
     def match(self, row_ptr, qx, qy, I, refine=True, chunk=0, za_scores=False, out=None,
-              exhaustive=False, stream=None):
-        """acom_match on device CSR tensors; returns a dict of device tensors."""
+              exhaustive=False, phase_scores=False, stream=None):
+        """acom_match on device CSR tensors; returns a dict of device tensors
+        (with phase_scores: the phase of each winner and every phase's best)."""
         pk = self._csr(row_ptr, qx, qy, I)
-        r = out if out is not None else self.alloc_result(pk.n_patterns, za_scores=za_scores)
+        r = out if out is not None else self.alloc_result(pk.n_patterns, za_scores=za_scores,
+                                                          phase_scores=phase_scores)
         res = Result(*(_ptr(r.get(k)) for k, _ in Result._fields_))
         opts = MatchOpts(1 if refine else 0, int(chunk), 1 if exhaustive else 0)
         _check(self._lib.acom_match(self.handle, C.byref(pk), C.byref(opts), C.byref(res),

@@ -118,6 +118,9 @@ struct Workspace {
     size_t bytes = 0;
 };
 
+// phases of one plan (acom_plan_concat)
+constexpr int kMaxPhases = 8;
+
 // precisions whose contraction runs on the tensor cores
 inline bool tc_precision(int precision) {
     return precision == ACOM_PREC_BF16 || precision == ACOM_PREC_FP16;
@@ -150,6 +153,9 @@ struct acom_plan_s {
     void* Pb_i = nullptr;
     alignas(64) unsigned char map_pr[128];  // TMA maps of Pb_r, Pb_i
     alignas(64) unsigned char map_pi[128];
+    int n_phases = 1;                 // crystal structures (phases) in this plan
+    std::vector<int> phase_off_host;  // [n_phases + 1] first axis of each phase, then Z
+    int* phase_off = nullptr;         // the same on the device
     int64_t last_evaluated = 0;       // axes evaluated exactly in the last match
     size_t bytes = 0;
     acom::Workspace ws;
@@ -207,6 +213,9 @@ void launch_select_exact(const acom_plan_s* p, const float* Xsr, const float* Xs
                          const float* xnorm2, int nb,
                          float kappa, int refine, acom_result out, int64_t off, int* n_eval,
                          cudaStream_t st, const float* xscale = nullptr);
+// exhaustive mode: phase of each winner and each phase's best score
+void launch_phase_outputs(const acom_plan_s* p, const float* za_scores, int nb, acom_result out,
+                          int64_t off, cudaStream_t st);
 void launch_refine(const acom_plan_s* p, const float* Chat, int nb, int chunk,
                    const float* za_scores, const unsigned long long* best, const float* xnorm2,
                    int refine, acom_result out, int64_t out_offset, cudaStream_t st);

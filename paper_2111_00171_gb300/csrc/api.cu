@@ -1,5 +1,6 @@
 // C ABI of libacom: argument validation, the zone-axis grid and its frames
 // (host FP64), plan ownership, and the chunked match loop.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <mutex>
@@ -223,6 +224,7 @@ static void destroy_plan(acom_plan_s* p) {
     pool_free(p->pfmax, st);
     pool_free(p->Pb_r, st);
     pool_free(p->Pb_i, st);
+    pool_free(p->phase_off, st);
     delete p;
 }
 
@@ -342,6 +344,10 @@ acom_status acom_plan_create(const acom_crystal* crystal, const acom_za_grid* gr
     ACOM_CK(dalloc(&p->nbr_idx, nidx.size(), &p->bytes, st));
     ACOM_CK(dalloc(&p->err, 1, &p->bytes, st));
     ACOM_CK(dalloc(&p->pfmax, (size_t)p->F, &p->bytes, st));
+    p->phase_off_host = {0, Z};
+    ACOM_CK(dalloc(&p->phase_off, 2, &p->bytes, st));
+    ACOM_CK(cudaMemcpyAsync(p->phase_off, p->phase_off_host.data(), sizeof(int) * 2,
+                            cudaMemcpyHostToDevice, st));
     ACOM_CK(cudaMemsetAsync(p->Pr, 0, sizeof(float) * pelems, st));
     ACOM_CK(cudaMemsetAsync(p->Pi, 0, sizeof(float) * pelems, st));
     ACOM_CK(cudaMemsetAsync(p->Psr, 0, sizeof(float) * selems, st));
@@ -390,6 +396,168 @@ cuda_fail:
 #undef ACOM_CK
 }
 
+acom_status acom_plan_concat(const acom_plan* plans, int32_t n_plans, void* cuda_stream,
+                             acom_plan* out) {
+    g_last_error.clear();
+    if (!plans || !out || n_plans < 1)
+        return set_error(ACOM_ERR_INVALID_ARG, "concat: plans, n_plans >= 1 and out required");
+    const acom_plan_s* a = plans[0];
+    if (!a) return set_error(ACOM_ERR_INVALID_ARG, "concat: null plan");
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int Z = 0, nph = 0, G = 0;
+    for (int i = 0; i < n_plans; ++i) {
+        const acom_plan_s* q = plans[i];
+        if (!q) return set_error(ACOM_ERR_INVALID_ARG, "concat: null plan");
+        if (q->device != dev)
+            return set_error(ACOM_ERR_INVALID_ARG, "concat: a plan lives on another device");
+        if (q->S != a->S || q->N != a->N || q->dq != a->dq || q->delta != a->delta ||
+            q->gamma_pow != a->gamma_pow || q->omega != a->omega || q->precision != a->precision)
+            return set_error(ACOM_ERR_INVALID_ARG,
+                             "concat: plans differ in shells, bins, tent, exponents or precision");
+        Z += q->Z;
+        nph += q->n_phases;
+        G += q->G;
+    }
+    if (nph > kMaxPhases) return set_error(ACOM_ERR_INVALID_ARG, "concat: more than 8 phases");
+    if (Z > 65535) return set_error(ACOM_ERR_UNSUPPORTED, "concat: more than 65535 zone axes");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    acom_plan_s* p = new acom_plan_s();
+    p->device = dev;
+    p->Z = Z;
+    p->S = a->S;
+    p->N = a->N;
+    p->F = a->F;
+    p->Spad = a->Spad;
+    p->Zp = (Z + 127) / 128 * 128;
+    p->G = G;
+    p->delta = a->delta;
+    p->gamma_pow = a->gamma_pow;
+    p->omega = a->omega;
+    p->lambda = a->lambda;
+    p->q_max = a->q_max;
+    p->sigma_exc = a->sigma_exc;
+    p->step_deg = a->step_deg;
+    p->dq = a->dq;
+    p->precision = a->precision;
+    p->pscale = a->pscale;
+    p->n_phases = nph;
+    const int F = p->F, Spad = p->Spad, Fs = shell_row_stride(F);
+    const size_t pelems = (size_t)p->Zp * F * Spad, selems = (size_t)p->Zp * Fs * Spad;
+    std::vector<int> nptr(1, 0), nidx, qptr, qidx;
+    std::vector<float> fmax((size_t)F, 0.f), qf((size_t)F);
+    p->phase_off_host.assign(1, 0);
+    cudaError_t e = cudaSuccess;
+#define ACOM_CK(x)                                     \
+    do {                                               \
+        e = (x);                                       \
+        if (e != cudaSuccess) goto cuda_fail;          \
+    } while (0)
+    // host side: axes, phase offsets, neighbour lists (offset into the
+    // concatenation, so neighbours stay within their phase) and max_z ||P^_zf||
+    for (int i = 0, base = 0; i < n_plans; base += plans[i]->Z, ++i) {
+        const acom_plan_s* q = plans[i];
+        p->za_host.insert(p->za_host.end(), q->za_host.begin(), q->za_host.end());
+        for (int k = 1; k <= q->n_phases; ++k) p->phase_off_host.push_back(base + q->phase_off_host[k]);
+        qptr.resize((size_t)q->Z + 1);
+        ACOM_CK(cudaMemcpyAsync(qptr.data(), q->nbr_ptr, sizeof(int) * qptr.size(),
+                                cudaMemcpyDeviceToHost, st));
+        ACOM_CK(cudaStreamSynchronize(st));
+        qidx.resize((size_t)qptr.back());
+        if (!qidx.empty())
+            ACOM_CK(cudaMemcpyAsync(qidx.data(), q->nbr_idx, sizeof(int) * qidx.size(),
+                                    cudaMemcpyDeviceToHost, st));
+        ACOM_CK(cudaMemcpyAsync(qf.data(), q->pfmax, sizeof(float) * F, cudaMemcpyDeviceToHost, st));
+        ACOM_CK(cudaStreamSynchronize(st));
+        const int ibase = (int)nidx.size();
+        for (int z = 0; z < q->Z; ++z) nptr.push_back(ibase + qptr[(size_t)z + 1]);
+        for (int v : qidx) nidx.push_back(base + v);
+        for (int f = 0; f < F; ++f) fmax[f] = std::max(fmax[f], qf[f]);
+    }
+    ACOM_CK(dalloc(&p->Pr, pelems, &p->bytes, st));
+    ACOM_CK(dalloc(&p->Pi, pelems, &p->bytes, st));
+    ACOM_CK(dalloc(&p->Psr, selems, &p->bytes, st));
+    ACOM_CK(dalloc(&p->Psi, selems, &p->bytes, st));
+    ACOM_CK(dalloc(&p->za, (size_t)3 * Z, &p->bytes, st));
+    ACOM_CK(dalloc(&p->frames, (size_t)9 * Z, &p->bytes, st));
+    ACOM_CK(dalloc(&p->nbr_ptr, nptr.size(), &p->bytes, st));
+    ACOM_CK(dalloc(&p->nbr_idx, nidx.size(), &p->bytes, st));
+    ACOM_CK(dalloc(&p->err, 1, &p->bytes, st));
+    ACOM_CK(dalloc(&p->pfmax, (size_t)F, &p->bytes, st));
+    ACOM_CK(dalloc(&p->phase_off, p->phase_off_host.size(), &p->bytes, st));
+    ACOM_CK(cudaMemsetAsync(p->Pr, 0, sizeof(float) * pelems, st));
+    ACOM_CK(cudaMemsetAsync(p->Pi, 0, sizeof(float) * pelems, st));
+    ACOM_CK(cudaMemsetAsync(p->Psr, 0, sizeof(float) * selems, st));
+    ACOM_CK(cudaMemsetAsync(p->Psi, 0, sizeof(float) * selems, st));
+    ACOM_CK(cudaMemsetAsync(p->err, 0, sizeof(int), st));
+    ACOM_CK(cudaMemcpyAsync(p->nbr_ptr, nptr.data(), sizeof(int) * nptr.size(),
+                            cudaMemcpyHostToDevice, st));
+    if (!nidx.empty())
+        ACOM_CK(cudaMemcpyAsync(p->nbr_idx, nidx.data(), sizeof(int) * nidx.size(),
+                                cudaMemcpyHostToDevice, st));
+    ACOM_CK(cudaMemcpyAsync(p->pfmax, fmax.data(), sizeof(float) * F, cudaMemcpyHostToDevice, st));
+    ACOM_CK(cudaMemcpyAsync(p->phase_off, p->phase_off_host.data(),
+                            sizeof(int) * p->phase_off_host.size(), cudaMemcpyHostToDevice, st));
+    // device side: each input's rows at its offset (zone-axis-major layouts
+    // are one contiguous block per input)
+    for (int i = 0, base = 0; i < n_plans; base += plans[i]->Z, ++i) {
+        const acom_plan_s* q = plans[i];
+        const size_t zr = (size_t)q->Z;
+        ACOM_CK(cudaMemcpyAsync(p->Pr + (size_t)base * F * Spad, q->Pr, sizeof(float) * zr * F * Spad,
+                                cudaMemcpyDeviceToDevice, st));
+        ACOM_CK(cudaMemcpyAsync(p->Pi + (size_t)base * F * Spad, q->Pi, sizeof(float) * zr * F * Spad,
+                                cudaMemcpyDeviceToDevice, st));
+        ACOM_CK(cudaMemcpyAsync(p->Psr + (size_t)base * Fs * Spad, q->Psr,
+                                sizeof(float) * zr * Fs * Spad, cudaMemcpyDeviceToDevice, st));
+        ACOM_CK(cudaMemcpyAsync(p->Psi + (size_t)base * Fs * Spad, q->Psi,
+                                sizeof(float) * zr * Fs * Spad, cudaMemcpyDeviceToDevice, st));
+        ACOM_CK(cudaMemcpyAsync(p->za + (size_t)3 * base, q->za, sizeof(double) * 3 * zr,
+                                cudaMemcpyDeviceToDevice, st));
+        ACOM_CK(cudaMemcpyAsync(p->frames + (size_t)9 * base, q->frames, sizeof(double) * 9 * zr,
+                                cudaMemcpyDeviceToDevice, st));
+    }
+    if (tc_precision(p->precision)) {
+        // [F][Zp][Spad] 16-bit tiles: per frequency, each input's Z rows at its offset
+        const bool fp16 = p->precision == ACOM_PREC_FP16;
+        const size_t n = (size_t)F * p->Zp * Spad;
+        ACOM_CK(pool_alloc(&p->Pb_r, n * 2, st));
+        ACOM_CK(pool_alloc(&p->Pb_i, n * 2, st));
+        p->bytes += 4 * n;
+        ACOM_CK(cudaMemsetAsync(p->Pb_r, 0, n * 2, st));
+        ACOM_CK(cudaMemsetAsync(p->Pb_i, 0, n * 2, st));
+        const size_t row = (size_t)Spad * 2;
+        for (int i = 0, base = 0; i < n_plans; base += plans[i]->Z, ++i) {
+            const acom_plan_s* q = plans[i];
+            ACOM_CK(cudaMemcpy2DAsync(static_cast<char*>(p->Pb_r) + base * row, p->Zp * row, q->Pb_r,
+                                      q->Zp * row, q->Z * row, F, cudaMemcpyDeviceToDevice, st));
+            ACOM_CK(cudaMemcpy2DAsync(static_cast<char*>(p->Pb_i) + base * row, p->Zp * row, q->Pb_i,
+                                      q->Zp * row, q->Z * row, F, cudaMemcpyDeviceToDevice, st));
+        }
+        acom_status s = make_bf16_map(p->map_pr, p->Pb_r, (uint64_t)F * p->Zp, (uint64_t)Spad, fp16);
+        if (s == ACOM_OK)
+            s = make_bf16_map(p->map_pi, p->Pb_i, (uint64_t)F * p->Zp, (uint64_t)Spad, fp16);
+        if (s != ACOM_OK) {
+            cudaStreamSynchronize(st);
+            destroy_plan(p);
+            return s;
+        }
+    }
+    ACOM_CK(cudaStreamSynchronize(st));
+    *out = p;
+    return ACOM_OK;
+cuda_fail:
+    cudaStreamSynchronize(st);
+    destroy_plan(p);
+    return cuda_error(e, "plan_concat");
+#undef ACOM_CK
+}
+
+acom_status acom_plan_get_phases(acom_plan p, int32_t* dst) {
+    if (!p || !dst) return set_error(ACOM_ERR_INVALID_ARG, "null argument");
+    for (size_t i = 0; i < p->phase_off_host.size(); ++i) dst[i] = p->phase_off_host[i];
+    return ACOM_OK;
+}
+
 acom_status acom_plan_destroy(acom_plan plan) {
     if (!plan) return set_error(ACOM_ERR_INVALID_ARG, "null plan");
     destroy_plan(plan);
@@ -406,6 +574,7 @@ acom_status acom_plan_get_info(acom_plan p, acom_plan_info* info) {
     info->precision = p->precision;
     info->device_bytes = (int64_t)(p->bytes + p->ws.bytes);
     info->last_evaluated = p->last_evaluated;
+    info->n_phases = p->n_phases;
     return ACOM_OK;
 }
 
@@ -569,6 +738,8 @@ acom_status acom_match(acom_plan p, const acom_peaks_csr* peaks, const acom_matc
             if (out->za_scores)
                 cudaMemcpyAsync(out->za_scores + c0 * (int64_t)p->Z, p->ws.za_scores,
                                 sizeof(float) * (size_t)nb * p->Z, cudaMemcpyDeviceToDevice, st);
+            if (out->phase || out->phase_score)
+                launch_phase_outputs(p, p->ws.za_scores, nb, *out, c0, st);
         } else {
             if (tc)
                 launch_contract_bound_tc(p, p->ws.map_x, p->ws.PTs, nb, p->ws.U, st, xscale);

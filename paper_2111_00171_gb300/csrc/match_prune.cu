@@ -182,6 +182,7 @@ struct SelState {
     int q;               // next neighbour to consider (refinement batches)
     float best3[3];      // winning correlation at bins k - 1, k, k + 1
     float Emax;          // rounding margin of the bounds
+    float Tp[kMaxPhases];  // best exact score so far of each phase
 };
 
 struct SelSmem {
@@ -196,8 +197,16 @@ struct SelSmem {
     int* cand;       // [kBatch]
     float* res;      // [kBatch][5] best value, its index bits, values at k - 1, k, k + 1
     float* red;      // [2][kSelWarps]
+    int* poff;       // [kMaxPhases + 1] first axis of each phase, then Z
     SelState* st;
 };
+
+// Phase of axis z: the last p with poff[p] <= z.
+__device__ __forceinline__ int phase_of(const int* poff, int nph, int z) {
+    int p = 0;
+    while (p + 1 < nph && z >= poff[p + 1]) ++p;
+    return p;
+}
 
 __device__ inline bool better(float v, unsigned i, float bv, unsigned bi) {
     return v > bv || (v == bv && i < bi);
@@ -214,11 +223,13 @@ __device__ inline void warp_argmax(float& v, unsigned& i) {
     }
 }
 
-// The up to K pending axes (ev == 0) of largest bound with U rel + Emax >= thr,
-// in decreasing bound (ties: lowest axis), into cand and st->nc; marks them
+// The up to K pending axes (ev == 0) of largest bound with U rel + Emax >= thr
+// (with per_phase, thr is the best score so far of the axis' own phase), in
+// decreasing bound (ties: lowest axis), into cand and st->nc; marks them
 // ev = 2.  Each warp takes its K best by repeated argmax over entries strictly
 // below its previous pick; warp 0 merges the warps' lists the same way.
-__device__ void block_topk(SelSmem& sm, int Z, int K, float thr, float rel, float Emax) {
+__device__ void block_topk(SelSmem& sm, int Z, int K, float thr, float rel, float Emax,
+                           bool per_phase, int nph) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float lv = CUDART_INF_F;
     unsigned li = 0u;                       // previous pick (nothing is above it)
@@ -228,7 +239,8 @@ __device__ void block_topk(SelSmem& sm, int Z, int K, float thr, float rel, floa
         for (int z = warp * 32 + lane; z < Z; z += kSelThreads) {
             if (sm.ev[z] != 0) continue;
             const float u = sm.U[z];
-            if (u * rel + Emax < thr || !better(lv, li, u, (unsigned)z)) continue;
+            const float tz = per_phase ? sm.st->Tp[phase_of(sm.poff, nph, z)] : thr;
+            if (u * rel + Emax < tz || !better(lv, li, u, (unsigned)z)) continue;
             if (better(u, (unsigned)z, v, zi)) {
                 v = u;
                 zi = (unsigned)z;
@@ -298,6 +310,8 @@ struct SelectArgs {
     const double* frames;             // [Z][9]
     const int* nbr_ptr;
     const int* nbr_idx;
+    const int* phase_off;             // [n_phases + 1]
+    int n_phases;
     int Z, F, N, S, Spad, nb, refine;
     float kappa;                      // contraction rounding constant
     FftRadix rad;                     // inverse-transform factorisation
@@ -443,13 +457,16 @@ __device__ void batch_transforms(const SelectArgs& a, int nc, SelSmem& sm) {
 }
 
 // Record the batch's exact scores; with update, fold them into the best.
-__device__ void fold_batch(int nc, int N, bool update, SelSmem& sm) {
+// Every score also updates its phase's best.
+__device__ void fold_batch(int nc, int N, bool update, int nph, SelSmem& sm) {
     if (threadIdx.x == 0) {
         SelState& st = *sm.st;
         for (int c = 0; c < nc; ++c) {
             const int z = sm.cand[c];
             const float* r = sm.res + 5 * c;
             const float bv = r[0];
+            float& tp = st.Tp[phase_of(sm.poff, nph, z)];
+            tp = bv > tp ? bv : tp;
             const unsigned bi = __float_as_uint(r[1]);
             const unsigned gidx = (unsigned)z * 2u * (unsigned)N + bi;
             if (update && better(bv, gidx, st.T, st.Tidx)) {
@@ -489,6 +506,10 @@ __device__ __noinline__ void write_outputs(const SelectArgs& a, int64_t b, const
     a.out.phi3_bin[o] = bk;
     a.out.mirror[o] = (uint8_t)bm;
     a.out.score[o] = score;
+    if (a.out.phase) a.out.phase[o] = phase_of(sm.poff, a.n_phases, bz);
+    if (a.out.phase_score)
+        for (int p = 0; p < a.n_phases; ++p)      // a phase left unevaluated: all-zero image
+            a.out.phase_score[o * a.n_phases + p] = st.Tp[p] == -CUDART_INF_F ? 0.f : st.Tp[p];
     if (a.out.score_cos) {
         const float xn = sqrtf(a.xnorm2[b]);
         a.out.score_cos[o] = xn > 0.f ? score / xn : 0.f;
@@ -583,8 +604,13 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_select_exact(SelectArgs a) {
     sm.cand = reinterpret_cast<int*>(take(sizeof(int) * kBatch));
     sm.res = reinterpret_cast<float*>(take(sizeof(float) * 5 * kBatch));
     sm.red = reinterpret_cast<float*>(take(sizeof(float) * 2 * kSelWarps));
+    sm.poff = reinterpret_cast<int*>(take(sizeof(int) * (kMaxPhases + 1)));
     sm.st = reinterpret_cast<SelState*>(take(sizeof(SelState)));
     sm.ev = take(Z);
+    const int nph = a.n_phases;
+    for (int i = threadIdx.x; i <= nph; i += kSelThreads) sm.poff[i] = a.phase_off[i];
+    // with per-phase scores requested, every phase's best is certified
+    const bool per_phase = a.out.phase_score != nullptr && nph > 1;
 
     for (int i = threadIdx.x; i < N; i += kSelThreads) {
         double s, c;
@@ -638,6 +664,7 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_select_exact(SelectArgs a) {
             st.Tidx = 0xffffffffu;
             st.bz = st.bk = st.bm = 0;
             st.best3[0] = st.best3[1] = st.best3[2] = 0.f;
+            for (int p = 0; p < kMaxPhases; ++p) st.Tp[p] = -CUDART_INF_F;
         }
         __syncthreads();
         const float Emax = sm.st->Emax;
@@ -647,12 +674,13 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_select_exact(SelectArgs a) {
         // ones every axis whose bound can still reach the best exact score
         for (int batch = 0;; ++batch) {
             const float thr = batch == 0 ? -CUDART_INF_F : sm.st->T;
-            block_topk(sm, Z, batch == 0 ? 4 : kBatch, thr, rel, Emax);
+            block_topk(sm, Z, batch == 0 ? 4 : kBatch, thr, rel, Emax, per_phase && batch > 0,
+                       nph);
             const int nc = sm.st->nc;
             if (nc == 0) break;
             batch_spectra(a, b, nc, sr.x, sr.y, sm);
             batch_transforms(a, nc, sm);
-            fold_batch(nc, N, true, sm);
+            fold_batch(nc, N, true, nph, sm);
             evals += nc;
             // an all-zero image: every axis ties at 0 and the lowest index has won
             if (sm.st->T == 0.f && sm.st->Tidx == 0u) break;
@@ -681,7 +709,7 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_select_exact(SelectArgs a) {
                 if (nc == 0) break;
                 batch_spectra(a, b, nc, sr.x, sr.y, sm);
                 batch_transforms(a, nc, sm);
-                fold_batch(nc, N, false, sm);
+                fold_batch(nc, N, false, nph, sm);
                 evals += nc;
             }
         }
@@ -696,13 +724,43 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_select_exact(SelectArgs a) {
     }
 }
 
+// Exhaustive mode: each phase's best score, the maximum of the exact per-axis
+// scores over its axes, and the phase of the winning axis.  One warp per
+// pattern.
+__global__ void k_phase_outputs(const float* __restrict__ za_scores, int Z, int nb,
+                                const int* __restrict__ poff, int nph, acom_result out,
+                                int64_t off) {
+    const int lane = threadIdx.x & 31;
+    const int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (b >= nb) return;
+    const int64_t o = off + b;
+    if (out.phase && lane == 0) out.phase[o] = phase_of(poff, nph, out.za_idx[o]);
+    if (!out.phase_score) return;
+    for (int p = 0; p < nph; ++p) {
+        float m = -CUDART_INF_F;
+        for (int z = poff[p] + lane; z < poff[p + 1]; z += 32) m = fmaxf(m, za_scores[b * Z + z]);
+        for (int s = 16; s > 0; s >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, s));
+        if (lane == 0) out.phase_score[o * nph + p] = m;
+    }
+}
+
+void launch_phase_outputs(const acom_plan_s* p, const float* za_scores, int nb, acom_result out,
+                          int64_t off, cudaStream_t st) {
+    if (nb <= 0) return;
+    prof_begin(kKMisc, st);
+    k_phase_outputs<<<(nb + 3) / 4, 128, 0, st>>>(za_scores, p->Z, nb, p->phase_off, p->n_phases,
+                                                   out, off);
+    prof_end(kKMisc, st);
+}
+
 size_t select_smem_bytes(int Z, int N, int F) {
     auto r16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
     const size_t pb = sizeof(float4) * 4 * sel_items(F), yb = sizeof(float2) * kBatch * (size_t)N;
     return r16(sizeof(float2) * N) + r16(sizeof(float2) * kBatch * (size_t)N) + r16(pb > yb ? pb : yb) +
            r16(sizeof(float) * Z) + 2 * r16(sizeof(float) * kSelWarps * kBatch) +
            r16(sizeof(int) * kBatch) + r16(sizeof(float) * 5 * kBatch) +
-           r16(sizeof(float) * 2 * kSelWarps) + r16(sizeof(SelState)) + r16(Z);
+           r16(sizeof(float) * 2 * kSelWarps) + r16(sizeof(int) * (kMaxPhases + 1)) +
+           r16(sizeof(SelState)) + r16(Z);
 }
 
 void launch_select_exact(const acom_plan_s* p, const float* Xsr, const float* Xsi, const float* U,
@@ -712,7 +770,7 @@ void launch_select_exact(const acom_plan_s* p, const float* Xsr, const float* Xs
                          cudaStream_t st, const float* xscale) {
     SelectArgs a{p->Psr, p->Psi, Xsr, Xsi, U, xfn, srange, pfmax, xnorm2, p->za, p->frames,
                  p->nbr_ptr,
-                 p->nbr_idx, p->Z, p->F, p->N, p->S, p->Spad, nb, refine, kappa,
+                 p->nbr_idx, p->phase_off, p->n_phases, p->Z, p->F, p->N, p->S, p->Spad, nb, refine, kappa,
                  fft_radices(p->N), out, off, n_eval, xscale, 1.0f / p->pscale};
     const size_t smem = select_smem_bytes(p->Z, p->N, p->F);
     cudaFuncSetAttribute(k_select_exact, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -90,3 +90,17 @@ def test_match_rejects_null_plan(lib):
     pk = acom.PeaksCSR(0, None, None, None, None)
     res = acom.Result()
     assert lib.acom_match(None, C.byref(pk), None, C.byref(res), None) == 1
+
+
+def test_concat_rejects_invalid_arguments_on_host(lib):
+    """acom_plan_concat and acom_plan_get_phases check their arguments before
+    any device work."""
+    h = C.c_void_p()
+    assert lib.acom_plan_concat(None, 1, None, C.byref(h)) == 1
+    arr = (C.c_void_p * 1)(None)
+    assert lib.acom_plan_concat(arr, 0, None, C.byref(h)) == 1
+    assert lib.acom_plan_concat(arr, 1, None, C.byref(h)) == 1     # a null plan
+    assert lib.acom_plan_concat(arr, 1, None, None) == 1
+    assert not h.value
+    out = (C.c_int32 * 2)()
+    assert lib.acom_plan_get_phases(None, out) == 1
