@@ -509,3 +509,95 @@ def test_multi_phase_noiseless_patterns_get_their_phase(two_phase_plans):
                                      int(rng.integers(2)))
             qx, qy, I = O.kinematical_pattern(refls[p], m, LAM, 0.02, 1e-3)
             assert O.match_multi(plans, qx, qy, I).phase == p, (p, z)
+
+
+# ------------------------------------------------- continuous refinement --
+
+def _rand_rot(rng):
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def _score_case(seed):
+    refl = au_reflections()
+    rng = np.random.default_rng(seed)
+    m = _rand_rot(rng)
+    qx, qy, I = O.kinematical_pattern(refl, m, LAM, AU["sigma"], 1e-3)
+    qx = qx + rng.normal(0, 0.005, len(qx))
+    qy = qy + rng.normal(0, 0.005, len(qy))
+    return refl, m, qx, qy, I * np.exp(0.1 * rng.normal(size=len(I)))
+
+
+def test_score_gradient_matches_finite_differences():
+    """dS/dw for R -> Exp(w) R against central differences of the score."""
+    refl, m, qx, qy, I = _score_case(21)
+    R = O.so3_exp([0.01, -0.015, 0.02]) @ m.T
+    for rho in (0.02, 0.08):
+        sc = O.kinematical_score(R, qx, qy, I, refl, LAM, 0.02, rho)
+        h = 1e-6
+        fd = np.array([(O.kinematical_score(O.so3_exp(h * e) @ R, qx, qy, I, refl, LAM, 0.02, rho).S
+                        - O.kinematical_score(O.so3_exp(-h * e) @ R, qx, qy, I, refl, LAM, 0.02,
+                                              rho).S) / (2 * h) for e in np.eye(3)])
+        np.testing.assert_allclose(sc.grad, fd, rtol=1e-6, atol=1e-7 * np.abs(fd).max())
+
+
+def test_score_axis_angle_gradient_matches_finite_differences():
+    """dS/dr at r != 0, where the left Jacobian of SO(3) enters."""
+    refl, m, qx, qy, I = _score_case(22)
+    r = np.array([0.2, -0.1, 0.15])
+    S, g = O.kinematical_score_r(r, m, qx, qy, I, refl, LAM, 0.02, 0.05)
+    h = 1e-6
+    fd = np.array([(O.kinematical_score_r(r + h * e, m, qx, qy, I, refl, LAM, 0.02, 0.05)[0]
+                    - O.kinematical_score_r(r - h * e, m, qx, qy, I, refl, LAM, 0.02, 0.05)[0])
+                   / (2 * h) for e in np.eye(3)])
+    np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-7 * np.abs(fd).max())
+
+
+def test_score_single_peak_single_reflection_closed_form():
+    """One reflection and one peak: b / ||b|| = 1, so S = a exp(-|d|^2/2rho^2)."""
+    g = np.array([[0.5, 0.2, 0.01]])
+    refl = O.Reflections(g=g, hkl=np.zeros((1, 3)), F=np.array([7.0 + 0j]))
+    R = O.so3_exp([0.1, 0.2, -0.3])
+    v = R @ g[0]
+    qx, qy, I = np.array([v[0] + 0.01]), np.array([v[1] - 0.02]), np.array([9.0])
+    q = math.hypot(qx[0], qy[0])
+    sc = O.kinematical_score(R, qx, qy, I, refl, LAM, 0.02, 0.03)
+    assert sc.S == pytest.approx(q * 3.0 * math.exp(-(0.01 ** 2 + 0.02 ** 2) / (2 * 0.03 ** 2)),
+                                 rel=1e-12)
+
+
+def test_score_invariant_under_crystal_rotations():
+    """R and R S give the same score for every proper rotation S of m-3m: the
+    reflection set and |F| are invariant under the point group."""
+    refl, m, qx, qy, I = _score_case(23)
+    R = m.T
+    base = O.kinematical_score(R, qx, qy, I, refl, LAM, 0.02, 0.03).S
+    for S in O.proper_point_group("cubic")[:8]:
+        assert O.kinematical_score(R @ S, qx, qy, I, refl, LAM, 0.02, 0.03).S == \
+            pytest.approx(base, rel=1e-10)
+
+
+def test_refinement_recovers_noiseless_orientations_and_their_twin():
+    """Noiseless patterns at random (off-grid) orientations, started 1.5
+    degrees off or from the Friedel twin of such a start: the refinement
+    returns the true orientation, and the score picks it over the twin."""
+    refl = au_reflections()
+    ops = O.proper_point_group("cubic")
+    prm = O.RefineParams()
+    rng = np.random.default_rng(31)
+    close = twin_ok = 0
+    for _ in range(8):
+        m = _rand_rot(rng)
+        qx, qy, I = O.kinematical_pattern(refl, m, LAM, AU["sigma"], 1e-3)
+        w = rng.normal(size=3)
+        m0 = m @ O.so3_exp(w * math.radians(1.5) / np.linalg.norm(w))
+        mr, _, _ = O.refine_with_twin(m0, qx, qy, I, refl, LAM, prm)
+        close += O.misorientation_deg(mr, m, ops) < 0.05
+        mt, _, chose_twin = O.refine_with_twin(m0 @ np.diag([-1.0, -1.0, 1.0]), qx, qy, I, refl,
+                                               LAM, prm)
+        twin_ok += chose_twin and O.misorientation_deg(mt, m, ops) < 0.05
+    assert close >= 7 and twin_ok >= 7
