@@ -8,13 +8,15 @@ step is the whole path: plan build (reflections, plan raster + transform,
 normalisation) and the match of every pattern (sparse polar raster +
 transform, shell contraction, inverse transform + argmax, refinement).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp16|fp32]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp16|bf16|fp32]
   python bench.py --impl reference ...   # the FP64 CPU oracle as the reference arm
   python bench.py --workload mixed ...   # two phases in one plan (see below)
+  python bench.py --workload refine ...  # coarse 3-degree match + continuous refinement
 
-The default precision is BF16 operands on the tensor cores for the certified
-bound, with every winner evaluated exactly in FP32; fp16 takes FP16 operands
-with per-pattern power-of-two scaling instead.  Under torchrun (N > 1)
+The default precision is FP16 operands (per-pattern and per-plan power-of-two
+scaling) on the tensor cores for the certified bound, with every winner
+evaluated exactly in FP32; bf16 takes BF16 operands instead, fp32 the FP32
+CUDA-core contraction.  Under torchrun (N > 1)
 every rank matches its own scan (weak scaling, scan seed + rank); there is no
 collective on the data path; rank 0 prints one JSON line.
 
@@ -23,6 +25,12 @@ Mg (peaks above 1e-3 of the strongest, at most 40) matched against one plan
 holding the Au 2-degree grid (231 axes) and the Mg 1-degree grid (1770 axes),
 75 shells of 0.02 1/A, 180 bins; every pattern gets each phase's best score
 and a phase decision.
+
+--workload refine: the same 256x256 scan matched on the 3-degree plan (105
+axes) and then refined (20 Gauss-Newton steps of the continuous kinematical
+score, from the match, from the runner-up zone axis outside the match's grid
+neighbourhood, and from the Friedel twin of each); the line also carries the
+plain FP32 1-degree grid path measured in the same run.
 """
 
 import argparse
@@ -45,6 +53,13 @@ W = dict(name="au_scan_256x256_1deg", phases=(("Au", 1.0),), Z=903, step=1.0, S=
          N=360, seed=1002, H=256, Wd=256, grains=200, delta=0.08, lam=0.01969, q_max=1.5,
          text=("fcc Au 256x256 scan (65,536 patterns, 10-60 peaks each, CSR, 200 Voronoi "
                "grains) vs 1-degree plan (903 zone axes, 150 shells x 0.01 1/A, 360 phi3 bins)"))
+REFINE = dict(name="au_scan_256x256_3deg_refined", phases=(("Au", 3.0),), Z=105, step=3.0,
+              refine=True,
+              text=("fcc Au 256x256 scan (65,536 patterns, 10-60 peaks each, CSR, 200 Voronoi "
+                    "grains, continuous orientations) matched on the 3-degree plan (105 zone "
+                    "axes, 150 shells x 0.01 1/A, 360 phi3 bins), then refined: 20 Gauss-Newton "
+                    "steps of the continuous kinematical score from the match, the runner-up "
+                    "axis and their Friedel twins"))
 MIXED = dict(name="au2deg_mg1deg_mixed_65536", phases=(("Au", 2.0), ("Mg", 1.0)), Z=231 + 1770,
              step=None, S=75, dq=0.02, N=180, seed=1003, n_patterns=65536,
              text=("65,536 patterns, 50/50 fcc Au / hcp Mg (peaks > 1e-3 of the strongest, "
@@ -59,7 +74,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp32"])
+    ap.add_argument("--precision", default="fp16", choices=["bf16", "fp16", "fp32"])
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--exhaustive", action="store_true",
                     help="inverse-transform every zone axis (no certified pruning)")
@@ -67,10 +82,12 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=16)
     ap.add_argument("--scan", default="256x256",
                     help="scan size HxW (smaller sizes are for profiling captures only)")
-    ap.add_argument("--workload", default="au_scan", choices=["au_scan", "mixed"])
+    ap.add_argument("--workload", default="au_scan", choices=["au_scan", "mixed", "refine"])
     args = ap.parse_args()
     if args.workload == "mixed":
         W.update(MIXED)
+    elif args.workload == "refine":
+        W.update(REFINE)
     return args
 
 
@@ -218,6 +235,16 @@ def oracle_plans(stride=1):
     return plans
 
 
+def oracle_refine(plan, mt, qx, qy, I):
+    """The oracle's grid refinement of match ``mt`` followed by its
+    continuous refinement (match and Friedel twin)."""
+    from oracle import acom_oracle as O
+    rf = O.refine(mt, plan.za, W["step"])
+    refl = O.reflections(np.eye(3) * 4.08, [[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0]],
+                         [79.0] * 4, [0.25] * 4, W["q_max"])
+    return O.refine_with_twin(rf.m, qx, qy, I, refl, W["lam"], O.RefineParams())
+
+
 def oracle_match(plans, qx, qy, I):
     """The oracle's best over all phases' axes (global axis index)."""
     from oracle import acom_oracle as O
@@ -240,6 +267,8 @@ def cpu_baseline(scan, gpu_res, n_sample):
     t0 = time.perf_counter()
     for b in idx:
         mt = oracle_match(plans, *scan.pattern(b))
+        if W.get("refine"):
+            oracle_refine(plans[0], mt, *scan.pattern(b))
         z, k, m = (int(gpu_res["za_idx"][b]), int(gpu_res["phi3_bin"][b]),
                    int(gpu_res["mirror"][b]))
         val = (mt.Cm if m else mt.C)[z, k]
@@ -277,7 +306,9 @@ def reference_arm(args):
         bs = rng.choice(scan.n_patterns, 2, replace=False)
         t0 = time.perf_counter()
         for b in bs:
-            oracle_match(full, *scan.pattern(b))
+            mt = oracle_match(full, *scan.pattern(b))
+            if W.get("refine"):
+                oracle_refine(full[0], mt, *scan.pattern(b))
         t_p = (time.perf_counter() - t0) / len(bs)
         if it >= args.warmup:
             B = scan.n_patterns
@@ -356,11 +387,14 @@ def main():
         p.match(*inputs, chunk=args.chunk, out=out, exhaustive=args.exhaustive,
                 phase_scores=mixed)
         stats["evaluated"] = p.get_info()["last_evaluated"]
+        if W.get("refine"):
+            p.refine(*inputs, out["orient"], orient_alt=out["runner_orient"])
+            stats["refine_pairs"] = p.get_info()["last_refine_pairs"]
         p.close()
         return out
 
     probe = make_plan()
-    out = probe.alloc_result(B, phase_scores=mixed)
+    out = probe.alloc_result(B, phase_scores=mixed, runner=bool(W.get("refine")))
     probe.close()
     for _ in range(args.warmup):
         step(d_in, out)
@@ -418,6 +452,7 @@ def main():
         return
 
     res = {k: out[k].cpu().numpy() for k in out_keys}
+    grid_path = grid_fp32_path(args, acom, scan, d_in, flush, stream) if W.get("refine") else None
     if mixed:
         ph = res["phase"]
         ok = ph == scan.phase
@@ -437,7 +472,8 @@ def main():
     peaks, src = peaks_file()
     K = args.steps
     value = world * B * K / (dev_ms / 1e3)
-    roof = roofline(prof, peaks, src, B, K, args.precision, int(scan.row_ptr[-1]))
+    roof = roofline(prof, peaks, src, B, K, args.precision, int(scan.row_ptr[-1]),
+                    stats.get("refine_pairs", 0))
     line = {"metric": METRIC, "value": value, "unit": "patterns/s", "n_gpus": world,
             "steps": K, "warmup": args.warmup, "ms_per_step": dev_ms / K,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -459,6 +495,8 @@ def main():
             "clocks": ck,
             "kernels_ms_per_step": {n: round(ms / K, 3) for n, (c, ms) in prof.items() if c},
             "accuracy": accuracy}
+    if grid_path is not None:
+        line["grid_fp32_1deg"] = grid_path
     if not args.no_cpu_baseline and world == 1:
         cb, agree = cpu_baseline(scan, res, args.cpu_sample)
         line["cpu_baseline"] = cb
@@ -466,6 +504,46 @@ def main():
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def grid_fp32_path(args, acom, scan, d_in, flush, stream):
+    """The plain FP32 path on the 1-degree grid (plan build + match with the
+    FP32 contraction and grid refinement) on the same scan: its patterns/s
+    (CUDA events, same L2 flush) and misorientation."""
+    import torch
+    v, om = acom.cubic_triangle()
+    cr = acom.au_crystal()
+
+    def plan():
+        return acom.Plan(cr, v, om, 1.0, W["S"], W["dq"], W["N"], delta=W["delta"],
+                         lam=W["lam"], q_max=W["q_max"], precision=acom.ACOM_PREC_FP32)
+    B = scan.n_patterns
+    probe = plan()
+    out = probe.alloc_result(B)
+    probe.close()
+
+    def step():
+        p = plan()
+        p.match(*d_in, out=out)
+        p.close()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+    mis, mis_twin, tilt = misorientation(out["orient"].cpu().numpy(), scan.truth)
+    return {"value": B * args.steps / (ms / 1e3), "unit": "patterns/s",
+            "ms_per_step": ms / args.steps, "zone_axes": 903, "precision": "fp32",
+            "accuracy": {"mean_misorientation_deg": mis, "mean_misorientation_friedel_deg": mis_twin,
+                         "mean_za_tilt_deg": tilt}}
 
 
 def read_profile(lib, acom):
@@ -513,7 +591,7 @@ def kernel_traffic(name, pats, precision):
     return t[0] * pats
 
 
-def kernel_roofline(name, cnt, ms, peaks, src, B, K, nnz, precision):
+def kernel_roofline(name, cnt, ms, peaks, src, B, K, nnz, precision, refine_pairs=0):
     """Achieved rate of one kernel class: algorithmic work per launch over its
     event-timed average launch duration."""
     Z, S, N = W["Z"], W["S"], W["N"]
@@ -537,6 +615,13 @@ def kernel_roofline(name, cnt, ms, peaks, src, B, K, nnz, precision):
         unit, bound, peak = "GB/s", "hbm", peaks["hbm_gbs"]
         note = (f"pattern FP32 spectra once per pattern + plan FP32 spectra once per launch; "
                 f"HBM peak ({src})")
+    elif name == "refine_orient" and refine_pairs:
+        # every (contributing reflection, peak) pair of every score evaluation:
+        # 13 FP32 operations and one exp (counted by the kernel itself)
+        work = 13.0 * refine_pairs * (K / cnt)
+        unit, bound, peak = "TFLOP/s", "alu", fp32_peak
+        note = ("13 flop per (reflection, peak) pair summed (the kernel counts the pairs); "
+                "FP32 FMA peak 152 SMs x 128 lanes x 2 x max clock")
     elif name == "raster_patterns":
         # algorithmic bytes: CSR in (8 B row pointer + 12 B per peak) and the
         # spectra out (FP32 re/im, S x F; BF16 copy when the tensor path runs)
@@ -553,14 +638,14 @@ def kernel_roofline(name, cnt, ms, peaks, src, B, K, nnz, precision):
             "launches": cnt, "peak_source": note}
 
 
-def roofline(prof, peaks, src, B, K, precision, nnz):
+def roofline(prof, peaks, src, B, K, precision, nnz, refine_pairs=0):
     """The dominant kernel's roofline (the largest event-timed total among
     the kernels with a stated roofline), plus every other kernel's share."""
     rows = []
     for name, (cnt, ms) in prof.items():
         if cnt == 0:
             continue
-        r = kernel_roofline(name, cnt, ms, peaks, src, B, K, nnz, precision)
+        r = kernel_roofline(name, cnt, ms, peaks, src, B, K, nnz, precision, refine_pairs)
         if r is not None:
             r["total_ms"] = ms
             rows.append(r)

@@ -135,6 +135,8 @@ typedef struct {
     int64_t device_bytes;     /* device memory owned by the plan                */
     int64_t last_evaluated;   /* zone axes evaluated in full by the last match  */
     int32_t n_phases;         /* crystal structures (1 unless concatenated)     */
+    int64_t last_refine_pairs; /* (reflection, peak) pairs the last acom_refine
+                                  summed over all its score evaluations        */
 } acom_plan_info;
 
 acom_status acom_plan_get_info(acom_plan plan, acom_plan_info* info);
@@ -211,6 +213,12 @@ typedef struct {
  *             every axis that was evaluated (the winner and every axis whose
  *             bound could reach it) and is otherwise an upper bound of the
  *             axis' maximum (the bound of acom_bounds plus a rounding margin).
+ *   runner_za, runner_score, runner_orient  optional (certified pruning
+ *             only; ACOM_ERR_UNSUPPORTED with exhaustive): the best evaluated
+ *             zone axis outside the winner's grid neighbourhood (-1 if none),
+ *             its exact score, and its grid orientation [n_patterns][9] (no
+ *             sub-grid refinement; the winner's when there is none): a second
+ *             start for acom_refine
  *   phase     optional: the phase of za_idx (0 for a single-phase plan)
  *   phase_score optional: [n_patterns][n_phases] the best score of each
  *             phase (its maximum over its axes, phi3 and mirror).  With
@@ -231,6 +239,9 @@ typedef struct {
     float* za_scores;
     int32_t* phase;
     float* phase_score;
+    int32_t* runner_za;
+    float* runner_score;
+    float* runner_orient;
 } acom_result;
 
 typedef struct {
@@ -294,6 +305,67 @@ void acom_profile_enable(int32_t on);
 void acom_profile_reset(void);
 int32_t acom_profile_read(acom_profile_entry* out, int32_t max);
 int64_t acom_kernel_launches(void);
+
+/*
+ * Continuous refinement of orientations (the paper stops at the grid and its
+ * sub-grid refinement; this makes the orientation a continuous variable).
+ * The kinematical correlation score of a pattern with an orientation m
+ * (R = m^T, crystal to lab) is
+ *
+ *   S(R) = sum_m sum_g a_m b_g exp(-|p_m - (R g)_xy|^2 / (2 rho^2)) / ||b||
+ *
+ * with p_m the peak positions, a_m = q_m^gamma I_m^(omega/2) the peak weights
+ * of the polar image, and b_g = |g|^gamma |F_g|^omega D(s_g)^(omega/2) the
+ * weight of the kinematical intensity of reflection g: D the Gaussian shape
+ * factor (Eq. 8) with the plan's sigma_exc, s_g the excitation error of R g
+ * (Eq. 6, beam along -z, the plan's lambda).  The reflections, gamma and omega
+ * are the plan's (a single-phase plan; ACOM_ERR_UNSUPPORTED for a
+ * concatenation).  FP32 arithmetic; rotations composed in FP64.
+ */
+typedef struct {
+    int32_t steps;            /* damped Gauss-Newton ascent steps              */
+    float rho_start;          /* spot width at the first step (1/Angstrom)     */
+    float rho_end;            /* at the last step (geometric in between)       */
+    float damping;            /* Levenberg-Marquardt damping of the step       */
+    float max_step_deg;       /* cap on the rotation of one step               */
+    int32_t twin;             /* 1: also refine m Rz(pi) (the in-plane Friedel
+                                 twin a grid match cannot tell apart) and keep
+                                 the higher final score                      */
+} acom_refine_opts;
+
+/* 20 steps, rho 0.15 -> 0.03, damping 0.3, 1 degree per step, twin on. */
+acom_refine_opts acom_refine_defaults(void);
+
+/*
+ * acom_refine - for every pattern, `steps` ascent steps of S from the
+ * orientation in ``orient`` ([n_patterns][9] FP32 row-major m, DEVICE, e.g.
+ * acom_match's output), each w = (H + damping diag H)^-1 dS/dw applied as
+ * R <- Exp(w) R (H the Gauss-Newton matrix, |w| capped), rho shrinking
+ * geometrically; with ``orient_alt`` (optional, [n_patterns][9], e.g. the
+ * match's runner_orient) the same from that second start; with opts->twin
+ * also from the Friedel twin of each start.  The start whose refinement ends
+ * with the highest S wins (ties: orient before its twin before orient_alt)
+ * and its refined m overwrites ``orient``.  ``score`` (optional,
+ * [n_patterns]) receives S at rho_end, ``start`` (optional, uint8) the
+ * winning start: bit 0 twin, bit 1 orient_alt.  ``opts`` may be NULL
+ * (defaults).  Stream-ordered; synchronises once to read the error word (bad
+ * peak data: ACOM_ERR_BAD_INPUT).
+ */
+acom_status acom_refine(acom_plan plan, const acom_peaks_csr* peaks, const acom_refine_opts* opts,
+                        float* orient, const float* orient_alt, float* score, uint8_t* start,
+                        void* cuda_stream);
+
+/*
+ * acom_kinematical_score - S at R = Exp(r) m^T for each pattern, with m from
+ * ``orient`` ([n][9], DEVICE) and r from ``r`` ([n][3] axis-angle, DEVICE;
+ * NULL means r = 0), at spot width ``rho``.  Writes ``score`` [n], ``grad``
+ * [n][3] = dS/dr (through the left Jacobian of SO(3)) and ``gn`` [n][6], the
+ * Gauss-Newton matrix for a lab-frame rotation (xx, xy, xz, yy, yz, zz);
+ * each output may be NULL.  Stream-ordered; synchronises once.
+ */
+acom_status acom_kinematical_score(acom_plan plan, const acom_peaks_csr* peaks, const float* orient,
+                                   const float* r, float rho, float* score, float* grad,
+                                   float* gn, void* cuda_stream);
 
 /*
  * acom_bounds - the shell contraction alone: for every pattern and zone axis

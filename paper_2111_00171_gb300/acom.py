@@ -28,7 +28,8 @@ EXPORTED = ("acom_plan_create", "acom_plan_destroy", "acom_plan_get_info",
             "acom_polar_spectra", "acom_bounds", "acom_bounds_static", "acom_status_str",
             "acom_last_error",
             "acom_version", "acom_profile_enable", "acom_profile_reset", "acom_profile_read",
-            "acom_kernel_launches", "acom_plan_concat", "acom_plan_get_phases")
+            "acom_kernel_launches", "acom_plan_concat", "acom_plan_get_phases", "acom_refine",
+            "acom_refine_defaults", "acom_kinematical_score")
 
 
 class AcomError(RuntimeError):
@@ -61,7 +62,7 @@ class PlanInfo(C.Structure):
     _fields_ = [("n_za", C.c_int32), ("n_shells", C.c_int32), ("n_phi", C.c_int32),
                 ("n_freq", C.c_int32), ("n_reflections", C.c_int32), ("precision", C.c_int32),
                 ("device_bytes", C.c_int64), ("last_evaluated", C.c_int64),
-                ("n_phases", C.c_int32)]
+                ("n_phases", C.c_int32), ("last_refine_pairs", C.c_int64)]
 
 
 class PeaksCSR(C.Structure):
@@ -73,11 +74,17 @@ class Result(C.Structure):
     _fields_ = [("za_idx", C.c_void_p), ("phi3_bin", C.c_void_p), ("mirror", C.c_void_p),
                 ("score", C.c_void_p), ("score_cos", C.c_void_p), ("phi3", C.c_void_p),
                 ("orient", C.c_void_p), ("za_scores", C.c_void_p), ("phase", C.c_void_p),
-                ("phase_score", C.c_void_p)]
+                ("phase_score", C.c_void_p), ("runner_za", C.c_void_p),
+                ("runner_score", C.c_void_p), ("runner_orient", C.c_void_p)]
 
 
 class MatchOpts(C.Structure):
     _fields_ = [("refine", C.c_int32), ("chunk", C.c_int32), ("exhaustive", C.c_int32)]
+
+
+class RefineOpts(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("rho_start", C.c_float), ("rho_end", C.c_float),
+                ("damping", C.c_float), ("max_step_deg", C.c_float), ("twin", C.c_int32)]
 
 
 _LIB = None
@@ -105,6 +112,9 @@ def load_library():
     lib.acom_plan_get_info.argtypes = [P, C.POINTER(PlanInfo)]
     lib.acom_plan_concat.argtypes = [C.POINTER(P), C.c_int32, P, C.POINTER(P)]
     lib.acom_plan_get_phases.argtypes = [P, C.POINTER(C.c_int32)]
+    lib.acom_refine.argtypes = [P, C.POINTER(PeaksCSR), C.POINTER(RefineOpts), P, P, P, P, P]
+    lib.acom_refine_defaults.restype = RefineOpts
+    lib.acom_kinematical_score.argtypes = [P, C.POINTER(PeaksCSR), P, P, C.c_float, P, P, P, P]
     lib.acom_plan_get_zone_axes.argtypes = [P, P]
     lib.acom_plan_get_spectra.argtypes = [P, P, P]
     lib.acom_match.argtypes = [P, C.POINTER(PeaksCSR), C.POINTER(MatchOpts), C.POINTER(Result), P]
@@ -120,7 +130,8 @@ def load_library():
     lib.acom_last_error.restype = C.c_char_p
     lib.acom_version.restype = C.c_int32
     for name in ("acom_plan_create", "acom_plan_destroy", "acom_plan_get_info",
-                 "acom_plan_concat", "acom_plan_get_phases",
+                 "acom_plan_concat", "acom_plan_get_phases", "acom_refine",
+                 "acom_kinematical_score",
                  "acom_plan_get_zone_axes", "acom_plan_get_spectra", "acom_match",
                  "acom_polar_spectra", "acom_bounds", "acom_bounds_static"):
         getattr(lib, name).restype = C.c_int
@@ -300,7 +311,7 @@ class Plan:
                                             _stream_ptr(stream)))
         return out
 
-    def alloc_result(self, n, za_scores=False, orient=True, phase_scores=False):
+    def alloc_result(self, n, za_scores=False, orient=True, phase_scores=False, runner=False):
         import torch
         dev = "cuda"
         r = {"za_idx": torch.empty(n, dtype=torch.int32, device=dev),
@@ -313,6 +324,10 @@ class Plan:
             r["orient"] = torch.empty((n, 3, 3), dtype=torch.float32, device=dev)
         if za_scores:
             r["za_scores"] = torch.empty((n, self.info["n_za"]), dtype=torch.float32, device=dev)
+        if runner:
+            r["runner_za"] = torch.empty(n, dtype=torch.int32, device=dev)
+            r["runner_score"] = torch.empty(n, dtype=torch.float32, device=dev)
+            r["runner_orient"] = torch.empty((n, 3, 3), dtype=torch.float32, device=dev)
         if phase_scores:
             r["phase"] = torch.empty(n, dtype=torch.int32, device=dev)
             r["phase_score"] = torch.empty((n, self.info["n_phases"]), dtype=torch.float32,
@@ -320,17 +335,91 @@ class Plan:
         return r
 
     def match(self, row_ptr, qx, qy, I, refine=True, chunk=0, za_scores=False, out=None,
-              exhaustive=False, phase_scores=False, stream=None):
+              exhaustive=False, phase_scores=False, runner=False, stream=None):
         """acom_match on device CSR tensors; returns a dict of device tensors
-        (with phase_scores: the phase of each winner and every phase's best)."""
+        (with phase_scores: the phase of each winner and every phase's best;
+        with runner: the runner-up axis, score and grid orientation)."""
         pk = self._csr(row_ptr, qx, qy, I)
         r = out if out is not None else self.alloc_result(pk.n_patterns, za_scores=za_scores,
-                                                          phase_scores=phase_scores)
+                                                          phase_scores=phase_scores,
+                                                          runner=runner)
         res = Result(*(_ptr(r.get(k)) for k, _ in Result._fields_))
         opts = MatchOpts(1 if refine else 0, int(chunk), 1 if exhaustive else 0)
         _check(self._lib.acom_match(self.handle, C.byref(pk), C.byref(opts), C.byref(res),
                                     _stream_ptr(stream)))
         return r
+
+
+    # ---- continuous refinement (acom_refine, acom_kinematical_score)
+
+    def refine(self, row_ptr, qx, qy, I, orient, orient_alt=None, steps=20, rho_start=0.15,
+               rho_end=0.03, damping=0.3, max_step_deg=1.0, twin=True, stream=None):
+        """acom_refine: ascent of the kinematical score from ``orient``
+        ([B][3][3] FP32 CUDA tensor, overwritten with the refined m) and, if
+        given, from ``orient_alt`` (e.g. the match's runner_orient); returns
+        (orient, score [B], winning start [B] uint8: bit 0 twin, bit 1 alt)."""
+        import torch
+        pk = self._csr(row_ptr, qx, qy, I)
+        if orient.dtype != torch.float32 or not orient.is_cuda or not orient.is_contiguous():
+            raise ValueError("orient must be a contiguous float32 CUDA tensor [B][3][3]")
+        score = torch.empty(pk.n_patterns, dtype=torch.float32, device="cuda")
+        tw = torch.empty(pk.n_patterns, dtype=torch.uint8, device="cuda")
+        opts = RefineOpts(int(steps), float(rho_start), float(rho_end), float(damping),
+                          float(max_step_deg), 1 if twin else 0)
+        alt = None if orient_alt is None else orient_alt.contiguous()
+        _check(self._lib.acom_refine(self.handle, C.byref(pk), C.byref(opts), _ptr(orient),
+                                     _ptr(alt), _ptr(score), _ptr(tw), _stream_ptr(stream)))
+        return orient, score, tw
+
+    def kinematical_score(self, row_ptr, qx, qy, I, orient, r=None, rho=0.03, stream=None):
+        """acom_kinematical_score at Exp(r) m^T: (score [B], dS/dr [B][3],
+        Gauss-Newton matrix [B][6])."""
+        import torch
+        pk = self._csr(row_ptr, qx, qy, I)
+        n = pk.n_patterns
+        score = torch.empty(n, dtype=torch.float32, device="cuda")
+        grad = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+        gn = torch.empty((n, 6), dtype=torch.float32, device="cuda")
+        rr = None if r is None else r.detach().to(torch.float32).contiguous()
+        _check(self._lib.acom_kinematical_score(self.handle, C.byref(pk),
+                                                _ptr(orient.contiguous()), _ptr(rr), float(rho),
+                                                _ptr(score), _ptr(grad), _ptr(gn),
+                                                _stream_ptr(stream)))
+        return score, grad, gn
+
+
+def _autograd_function():
+    import torch
+
+    class KinematicalScore(torch.autograd.Function):
+        """S(r) = kinematical score at Exp(r) m^T for each pattern, with its
+        hand-written gradient dS/dr from the same kernel launch."""
+
+        @staticmethod
+        def forward(ctx, r, plan, peaks, orient, rho):
+            s, g, _ = plan.kinematical_score(*peaks, orient, r=r, rho=rho)
+            ctx.save_for_backward(g)
+            return s
+
+        @staticmethod
+        def backward(ctx, gs):
+            (g,) = ctx.saved_tensors
+            return gs[:, None] * g, None, None, None, None
+
+    return KinematicalScore
+
+
+def kinematical_score(r, plan, peaks, orient, rho=0.03):
+    """Differentiable S(r) (torch.autograd.Function): ``peaks`` is the
+    (row_ptr, qx, qy, I) tuple of CUDA tensors, ``orient`` the [B][3][3] base
+    orientations, ``r`` [B][3] axis-angle vectors."""
+    global _KIN
+    if _KIN is None:
+        _KIN = _autograd_function()
+    return _KIN.apply(r, plan, peaks, orient, rho)
+
+
+_KIN = None
 
 
 def au_crystal(a=4.08):

@@ -153,6 +153,9 @@ struct acom_plan_s {
     void* Pb_i = nullptr;
     alignas(64) unsigned char map_pr[128];  // TMA maps of Pb_r, Pb_i
     alignas(64) unsigned char map_pi[128];
+    float4* refl_tab = nullptr;       // [G] FP32 (g, |g|^gamma |F_g|^omega) for refinement
+    unsigned long long* refine_pairs = nullptr;  // (reflection, peak) pairs of the last refine
+    int64_t last_refine_pairs = 0;
     int n_phases = 1;                 // crystal structures (phases) in this plan
     std::vector<int> phase_off_host;  // [n_phases + 1] first axis of each phase, then Z
     int* phase_off = nullptr;         // the same on the device
@@ -166,7 +169,7 @@ namespace acom {
 // ---- per-kernel timing and launch count (profile.cu) ----
 enum KernelClass {
     kKReflections, kKRasterPlan, kKScale, kKRasterPatterns, kKContract, kKIdft, kKRefine,
-    kKMisc, kKContractBf16, kKIdftBf16, kKRescore, kKSelect, kKCount
+    kKMisc, kKContractBf16, kKIdftBf16, kKRescore, kKSelect, kKRefineOrient, kKCount
 };
 void prof_begin(int cls, cudaStream_t st);
 void prof_end(int cls, cudaStream_t st);
@@ -213,6 +216,15 @@ void launch_select_exact(const acom_plan_s* p, const float* Xsr, const float* Xs
                          const float* xnorm2, int nb,
                          float kappa, int refine, acom_result out, int64_t off, int* n_eval,
                          cudaStream_t st, const float* xscale = nullptr);
+// refine.cu: continuous refinement on the plan's reflections
+acom_status refine_table(acom_plan_s* p, cudaStream_t st);
+void launch_refine_orient(const acom_plan_s* p, const acom_peaks_csr* pk, int steps,
+                          float rho_start, float rho_end, float damping, float max_step, int twin,
+                          float* orient, const float* orient_alt, float* score, uint8_t* start_out,
+                          cudaStream_t st);
+void launch_kin_score(const acom_plan_s* p, const acom_peaks_csr* pk, const float* orient,
+                      const float* r, float rho, float* score, float* grad, float* gn,
+                      cudaStream_t st);
 // exhaustive mode: phase of each winner and each phase's best score
 void launch_phase_outputs(const acom_plan_s* p, const float* za_scores, int nb, acom_result out,
                           int64_t off, cudaStream_t st);

@@ -225,6 +225,8 @@ static void destroy_plan(acom_plan_s* p) {
     pool_free(p->Pb_r, st);
     pool_free(p->Pb_i, st);
     pool_free(p->phase_off, st);
+    pool_free(p->refl_tab, st);
+    pool_free(p->refine_pairs, st);
     delete p;
 }
 
@@ -575,6 +577,7 @@ acom_status acom_plan_get_info(acom_plan p, acom_plan_info* info) {
     info->device_bytes = (int64_t)(p->bytes + p->ws.bytes);
     info->last_evaluated = p->last_evaluated;
     info->n_phases = p->n_phases;
+    info->last_refine_pairs = p->last_refine_pairs;
     return ACOM_OK;
 }
 
@@ -697,6 +700,8 @@ acom_status acom_match(acom_plan p, const acom_peaks_csr* peaks, const acom_matc
     if (B == 0) return ACOM_OK;
     const int refine = opts ? opts->refine : 1;
     const bool exhaustive = opts && opts->exhaustive;
+    if (exhaustive && (out->runner_za || out->runner_score || out->runner_orient))
+        return set_error(ACOM_ERR_UNSUPPORTED, "runner-up outputs need certified pruning");
     if (!exhaustive && p->Z > 16384)
         return set_error(ACOM_ERR_UNSUPPORTED, "pruned mode supports at most 16384 zone axes");
     int chunk = opts && opts->chunk > 0 ? opts->chunk : (exhaustive ? 1024 : 8192);
@@ -796,6 +801,73 @@ acom_status acom_bounds(acom_plan p, const acom_peaks_csr* peaks, float* dst, vo
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "bounds launch");
     return read_error_word(p, st);
+}
+
+acom_status acom_refine(acom_plan p, const acom_peaks_csr* peaks, const acom_refine_opts* opts,
+                        float* orient, const float* orient_alt, float* score, uint8_t* start,
+                        void* cuda_stream) {
+    g_last_error.clear();
+    if (!p || !orient) return set_error(ACOM_ERR_INVALID_ARG, "null argument");
+    acom_status s = check_peaks(peaks);
+    if (s != ACOM_OK) return s;
+    acom_refine_opts o = opts ? *opts : acom_refine_defaults();
+    if (o.steps < 0 || o.steps > 1000 || !(o.rho_start > 0) || !(o.rho_end > 0) ||
+        !std::isfinite(o.rho_start) || !std::isfinite(o.rho_end) || !(o.damping >= 0) ||
+        !std::isfinite(o.damping) || !(o.max_step_deg > 0) || !std::isfinite(o.max_step_deg))
+        return set_error(ACOM_ERR_INVALID_ARG,
+                         "refine opts: steps 0..1000, rho > 0, damping >= 0, max_step_deg > 0");
+    if (peaks->n_patterns == 0) return ACOM_OK;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    s = refine_table(p, st);
+    if (s != ACOM_OK) return s;
+    cudaMemsetAsync(p->err, 0, sizeof(int), st);
+    cudaMemsetAsync(p->refine_pairs, 0, sizeof(unsigned long long), st);
+    prof_begin(kKMisc, st);
+    k_check_row0<<<1, 1, 0, st>>>(peaks->row_ptr, p->err);
+    prof_end(kKMisc, st);
+    launch_refine_orient(p, peaks, o.steps, o.rho_start, o.rho_end, o.damping,
+                         (float)(o.max_step_deg * M_PI / 180.0), o.twin ? 1 : 0, orient,
+                         orient_alt, score, start, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "refine launch");
+    unsigned long long pairs = 0;
+    cudaMemcpyAsync(&pairs, p->refine_pairs, sizeof(pairs), cudaMemcpyDeviceToHost, st);
+    s = read_error_word(p, st);
+    p->last_refine_pairs = (int64_t)pairs;
+    return s;
+}
+
+acom_status acom_kinematical_score(acom_plan p, const acom_peaks_csr* peaks, const float* orient,
+                                   const float* r, float rho, float* score, float* grad,
+                                   float* gn, void* cuda_stream) {
+    g_last_error.clear();
+    if (!p || !orient) return set_error(ACOM_ERR_INVALID_ARG, "null argument");
+    acom_status s = check_peaks(peaks);
+    if (s != ACOM_OK) return s;
+    if (!(rho > 0) || !std::isfinite(rho)) return set_error(ACOM_ERR_INVALID_ARG, "rho must be > 0");
+    if (peaks->n_patterns == 0) return ACOM_OK;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    s = refine_table(p, st);
+    if (s != ACOM_OK) return s;
+    cudaMemsetAsync(p->err, 0, sizeof(int), st);
+    prof_begin(kKMisc, st);
+    k_check_row0<<<1, 1, 0, st>>>(peaks->row_ptr, p->err);
+    prof_end(kKMisc, st);
+    launch_kin_score(p, peaks, orient, r, rho, score, grad, gn, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "score launch");
+    return read_error_word(p, st);
+}
+
+acom_refine_opts acom_refine_defaults(void) {
+    acom_refine_opts o;
+    o.steps = 20;
+    o.rho_start = 0.15f;
+    o.rho_end = 0.03f;
+    o.damping = 0.3f;
+    o.max_step_deg = 1.0f;
+    o.twin = 1;
+    return o;
 }
 
 }  // extern "C"

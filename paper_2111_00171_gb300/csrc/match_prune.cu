@@ -183,6 +183,8 @@ struct SelState {
     float best3[3];      // winning correlation at bins k - 1, k, k + 1
     float Emax;          // rounding margin of the bounds
     float Tp[kMaxPhases];  // best exact score so far of each phase
+    int ru_z;            // runner-up: best evaluated axis outside the winner's
+    float ru_v;          // grid neighbourhood (-1: none), and its score
 };
 
 struct SelSmem {
@@ -192,6 +194,7 @@ struct SelSmem {
     float4* part;    // [items][4] partial (A, B, C, D) of a shell part
     float* U;        // [Z] bound, replaced by the exact score once evaluated
     uint8_t* ev;     // [Z] 0 pending, 1 evaluated, 2 in the current batch
+    uint16_t* kb;    // [Z] bin + mirror * N of each evaluated axis' maximum
     float* wv;       // [kSelWarps][kBatch] per-warp top-K values
     int* wi;         // [kSelWarps][kBatch] and axes
     int* cand;       // [kBatch]
@@ -480,6 +483,7 @@ __device__ void fold_batch(int nc, int N, bool update, int nph, SelSmem& sm) {
                 st.best3[2] = r[4];
             }
             sm.U[z] = bv;
+            sm.kb[z] = (uint16_t)bi;
             sm.ev[z] = 1;
         }
     }
@@ -507,6 +511,33 @@ __device__ __noinline__ void write_outputs(const SelectArgs& a, int64_t b, const
     a.out.mirror[o] = (uint8_t)bm;
     a.out.score[o] = score;
     if (a.out.phase) a.out.phase[o] = phase_of(sm.poff, a.n_phases, bz);
+    if (a.out.runner_za || a.out.runner_score || a.out.runner_orient) {
+        // the runner-up's grid orientation frame Rz(-2 pi k / N) [Ry(pi)] in
+        // FP32 (a start for refinement); the winner's grid orientation when
+        // there is no runner-up
+        const int rz = st.ru_z;
+        const int z = rz >= 0 ? rz : bz;
+        const int kbz = rz >= 0 ? (int)sm.kb[rz] : bk + bm * N;
+        const int mm = kbz >= N ? 1 : 0, kk = kbz - mm * N;
+        if (a.out.runner_za) a.out.runner_za[o] = rz;
+        if (a.out.runner_score) a.out.runner_score[o] = rz >= 0 ? st.ru_v : 0.f;
+        if (a.out.runner_orient) {
+            float sp, cp;
+            sincospif(-2.0f * (float)kk / (float)N, &sp, &cp);
+            const double* Fz = a.frames + 9 * z;
+            for (int i = 0; i < 3; ++i) {
+                const float f0 = (float)Fz[3 * i], f1 = (float)Fz[3 * i + 1], f2 = (float)Fz[3 * i + 2];
+                float c0 = f0 * cp + f1 * sp, c1 = f1 * cp - f0 * sp, c2 = f2;
+                if (mm) {
+                    c0 = -c0;
+                    c2 = -c2;
+                }
+                a.out.runner_orient[9 * o + 3 * i] = c0;
+                a.out.runner_orient[9 * o + 3 * i + 1] = c1;
+                a.out.runner_orient[9 * o + 3 * i + 2] = c2;
+            }
+        }
+    }
     if (a.out.phase_score)
         for (int p = 0; p < a.n_phases; ++p)      // a phase left unevaluated: all-zero image
             a.out.phase_score[o * a.n_phases + p] = st.Tp[p] == -CUDART_INF_F ? 0.f : st.Tp[p];
@@ -607,6 +638,7 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_select_exact(SelectArgs a) {
     sm.poff = reinterpret_cast<int*>(take(sizeof(int) * (kMaxPhases + 1)));
     sm.st = reinterpret_cast<SelState*>(take(sizeof(SelState)));
     sm.ev = take(Z);
+    sm.kb = reinterpret_cast<uint16_t*>(take(sizeof(uint16_t) * Z));
     const int nph = a.n_phases;
     for (int i = threadIdx.x; i <= nph; i += kSelThreads) sm.poff[i] = a.phase_off[i];
     // with per-phase scores requested, every phase's best is certified
@@ -716,6 +748,42 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_select_exact(SelectArgs a) {
         if (a.out.za_scores)
             for (int z = threadIdx.x; z < Z; z += kSelThreads)
                 a.out.za_scores[(a.off + b) * Z + z] = sm.ev[z] ? sm.U[z] : sm.U[z] * rel + Emax;
+        if (a.out.runner_za || a.out.runner_score || a.out.runner_orient) {
+            // runner-up: the best evaluated axis other than the winner and its
+            // grid neighbours (bit 4 of ev marks them while this runs)
+            const int bz = sm.st->bz;
+            const int q0 = a.nbr_ptr[bz], q1 = a.nbr_ptr[bz + 1];
+            for (int q = q0 + threadIdx.x; q < q1; q += kSelThreads) sm.ev[a.nbr_idx[q]] |= 4;
+            if (threadIdx.x == 0) sm.ev[bz] |= 4;
+            __syncthreads();
+            float v = -CUDART_INF_F;
+            unsigned zi = 0xffffffffu;
+            for (int z = threadIdx.x; z < Z; z += kSelThreads)
+                if (sm.ev[z] == 1 && better(sm.U[z], (unsigned)z, v, zi)) {
+                    v = sm.U[z];
+                    zi = (unsigned)z;
+                }
+            warp_argmax(v, zi);
+            if (lane == 0) {
+                sm.wv[warp * kBatch] = v;
+                sm.wi[warp * kBatch] = (int)zi;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                float bv = -CUDART_INF_F;
+                unsigned bi = 0xffffffffu;
+                for (int w = 0; w < kSelWarps; ++w)
+                    if (better(sm.wv[w * kBatch], (unsigned)sm.wi[w * kBatch], bv, bi)) {
+                        bv = sm.wv[w * kBatch];
+                        bi = (unsigned)sm.wi[w * kBatch];
+                    }
+                sm.st->ru_z = bi == 0xffffffffu ? -1 : (int)bi;
+                sm.st->ru_v = bv;
+            }
+            for (int q = q0 + threadIdx.x; q < q1; q += kSelThreads) sm.ev[a.nbr_idx[q]] &= 3;
+            if (threadIdx.x == 0) sm.ev[bz] &= 3;
+            __syncthreads();
+        }
         if (threadIdx.x == 0) {
             if (a.n_eval) atomicAdd(a.n_eval, evals);
             write_outputs(a, b, sm, want_ref);
@@ -760,7 +828,7 @@ size_t select_smem_bytes(int Z, int N, int F) {
            r16(sizeof(float) * Z) + 2 * r16(sizeof(float) * kSelWarps * kBatch) +
            r16(sizeof(int) * kBatch) + r16(sizeof(float) * 5 * kBatch) +
            r16(sizeof(float) * 2 * kSelWarps) + r16(sizeof(int) * (kMaxPhases + 1)) +
-           r16(sizeof(SelState)) + r16(Z);
+           r16(sizeof(SelState)) + r16(Z) + r16(sizeof(uint16_t) * Z);
 }
 
 void launch_select_exact(const acom_plan_s* p, const float* Xsr, const float* Xsi, const float* U,

@@ -104,3 +104,16 @@ def test_concat_rejects_invalid_arguments_on_host(lib):
     assert not h.value
     out = (C.c_int32 * 2)()
     assert lib.acom_plan_get_phases(None, out) == 1
+
+
+def test_refine_defaults_and_argument_checks_on_host(lib):
+    """acom_refine_defaults is host-only; acom_refine and
+    acom_kinematical_score reject a null plan before any device work."""
+    from paper_2111_00171_gb300 import acom
+    d = lib.acom_refine_defaults()
+    assert (d.steps, d.twin) == (20, 1)
+    assert (d.rho_start, d.rho_end, d.damping, d.max_step_deg) == pytest.approx((0.15, 0.03, 0.3, 1.0))
+    pk = acom.PeaksCSR(0, None, None, None, None)
+    assert lib.acom_refine(None, C.byref(pk), None, None, None, None, None, None) == 1
+    assert lib.acom_kinematical_score(None, C.byref(pk), None, None, 0.03, None, None, None,
+                                      None) == 1
