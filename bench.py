@@ -54,7 +54,7 @@ W = dict(name="au_scan_256x256_1deg", phases=(("Au", 1.0),), Z=903, step=1.0, S=
          text=("fcc Au 256x256 scan (65,536 patterns, 10-60 peaks each, CSR, 200 Voronoi "
                "grains) vs 1-degree plan (903 zone axes, 150 shells x 0.01 1/A, 360 phi3 bins)"))
 REFINE = dict(name="au_scan_256x256_3deg_refined", phases=(("Au", 3.0),), Z=105, step=3.0,
-              refine=True,
+              refine=True, precision="bf16",
               text=("fcc Au 256x256 scan (65,536 patterns, 10-60 peaks each, CSR, 200 Voronoi "
                     "grains, continuous orientations) matched on the 3-degree plan (105 zone "
                     "axes, 150 shells x 0.01 1/A, 360 phi3 bins), then refined: 20 Gauss-Newton "
@@ -74,7 +74,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="fp16", choices=["bf16", "fp16", "fp32"])
+    ap.add_argument("--precision", default=None, choices=["bf16", "fp16", "fp32"],
+                    help="contraction operands (default: the workload's, fp16 for au_scan "
+                         "and mixed, bf16 for refine)")
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--exhaustive", action="store_true",
                     help="inverse-transform every zone axis (no certified pruning)")
@@ -88,6 +90,8 @@ def parse():
         W.update(MIXED)
     elif args.workload == "refine":
         W.update(REFINE)
+    if args.precision is None:
+        args.precision = W.get("precision", "fp16")
     return args
 
 
@@ -561,13 +565,13 @@ def read_profile(lib, acom):
 
 # DRAM bytes per pattern (read + write) of kernels whose traffic grows with
 # the patterns of a launch, from the ncu capture summarised in
-# profiles/ncu_full_bf16_au_scan_64x64_1deg.md, with a hash of the kernel's
+# profiles/ncu_full_fp16_au_scan_64x64_1deg.md, with a hash of the kernel's
 # sources at capture time, the precision and the workload of the captured
 # run: a changed kernel, or another precision or workload, reports no traffic.
 TRAFFIC_PER_PATTERN = {
-    "select_exact": (360076.0, ("match_prune.cu",), "e9c572a4179f2cc6", "bf16",
+    "select_exact": (321362.0, ("match_prune.cu",), "6b57984d95e2ce61", "fp16",
                      "au_scan_256x256_1deg"),
-    "raster_patterns": (340215.0, ("raster.cu",), "3c26ac06f0283b45", "bf16",
+    "raster_patterns": (340316.0, ("raster.cu",), "9e13818ce7a0dba0", "fp16",
                         "au_scan_256x256_1deg"),
 }
 
