@@ -43,6 +43,10 @@ kinematical_score         continuous correlation of the peaks with the
 refine_continuous         gradient ascent of that score from a grid match
 refine_with_twin          the same from the match and from its in-plane
                           Friedel twin m Rz(pi), keeping the higher score
+forward_spots, delete_peaks, match_multiple
+                          several matches per pattern by iterative peak
+                          deletion (Matching of Overlapping Diffraction
+                          Patterns)
 misorientation_deg        symmetry-reduced misorientation (reading)
 
 Parity status: structure factors, plan, image, correlation and best match are
@@ -750,6 +754,79 @@ def refine_with_twin(m0, qx, qy, I, refl: Reflections, lam, prm: RefineParams, g
     mb, sb = refine_continuous(np.asarray(m0, dtype=np.float64) @ np.diag([-1.0, -1.0, 1.0]),
                                qx, qy, I, refl, lam, prm, gamma_pow, omega)
     return (mb, sb, True) if sb > sa else (ma, sa, False)
+
+
+# --------------------------------------------------------------------------
+# Several matches per pattern (Matching of Overlapping Diffraction Patterns)
+# --------------------------------------------------------------------------
+
+
+def forward_spots(refl: Reflections, m, lam, sigma, d_min=1e-3):
+    """Detector positions (R g)_xy, R = m^T, of the reflections of the
+    forward pattern of orientation m.  reading: a reflection belongs to the
+    forward pattern when its Gaussian shape factor D(s_g) (Eq. 8) is at least
+    d_min."""
+    v = refl.g @ np.asarray(m, dtype=np.float64)
+    s = excitation_error(v, beam_vector(lam))
+    keep = shape_factor_gaussian(s, sigma) >= d_min
+    return v[keep, :2]
+
+
+def delete_peaks(qx, qy, I, spots, r_del, delta):
+    """Peaks within r_del of a forward spot are removed; peaks between r_del
+    and the correlation kernel size delta keep (d - r_del) / (delta - r_del)
+    of their intensity, d the distance to the nearest spot; the others are
+    unchanged."""
+    qx = np.asarray(qx, dtype=np.float64)
+    qy = np.asarray(qy, dtype=np.float64)
+    I = np.asarray(I, dtype=np.float64)
+    if len(spots) == 0 or len(qx) == 0:
+        return qx, qy, I
+    d = np.min(np.hypot(qx[:, None] - spots[None, :, 0], qy[:, None] - spots[None, :, 1]), axis=1)
+    keep = d >= r_del
+    f = np.where(d < delta, (d - r_del) / (delta - r_del), 1.0)
+    return qx[keep], qy[keep], (I * f)[keep]
+
+
+@dataclass
+class MatchN:
+    za: int
+    k: int
+    mirror: int
+    score: float          # correlation of the original, full pattern at (za, k, mirror)
+    score_cos: float      # the same over ||X|| of the full pattern
+    reduced_score: float  # the maximum of the reduced pattern that found it
+    m: np.ndarray         # grid orientation
+
+
+def match_multiple(plan: Plan, refl: Reflections, qx, qy, I, n_matches, r_del, lam, sigma,
+                   d_min=1e-3):
+    """Up to n_matches orientations: match, compute the forward pattern of the
+    match, delete or weaken the peaks it explains, match again.  Stops early
+    when no peak is left or the best correlation of what is left is 0 (no
+    further orientation).  Each match is reported with the correlation of the
+    original full pattern at its (zone axis, phi3 bin, mirror), as the paper
+    does, and with the maximum of the reduced pattern that found it.
+    reading: the forward pattern is that of the grid orientation of the match."""
+    X = polar_image(qx, qy, I, plan.params)
+    C, Cm = correlogram(plan.P_hat, X)
+    xn = float(np.sqrt(np.sum(X * X)))
+    N = plan.params.n_phi
+    cur = (np.asarray(qx, np.float64), np.asarray(qy, np.float64), np.asarray(I, np.float64))
+    out = []
+    for _ in range(n_matches):
+        if len(cur[0]) == 0:
+            break
+        mt = match_pattern(plan, *cur)
+        if not mt.score > 0:
+            break
+        full = float((Cm if mt.mirror else C)[mt.za, mt.k])
+        m = orientation_matrix(plan.za[mt.za], -2 * math.pi * mt.k / N, mt.mirror)
+        out.append(MatchN(mt.za, mt.k, mt.mirror, full, full / xn if xn > 0 else 0.0,
+                          mt.score, m))
+        cur = delete_peaks(*cur, forward_spots(refl, m, lam, sigma, d_min), r_del,
+                           plan.params.delta)
+    return out
 
 
 # --------------------------------------------------------------------------

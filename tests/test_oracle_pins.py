@@ -601,3 +601,66 @@ def test_refinement_recovers_noiseless_orientations_and_their_twin():
                                                LAM, prm)
         twin_ok += chose_twin and O.misorientation_deg(mt, m, ops) < 0.05
     assert close >= 7 and twin_ok >= 7
+
+
+# ------------------------------------------- several matches per pattern --
+
+def test_delete_peaks_distances():
+    """Removed within r_del, intensity times (d - r_del)/(delta - r_del) up to
+    delta, unchanged beyond (hand-computed distances to one spot at the
+    origin)."""
+    spots = np.array([[0.0, 0.0]])
+    qx = np.array([0.01, 0.05, 0.06, 0.2])
+    qy = np.array([0.0, 0.0, 0.08, 0.0])          # distances 0.01, 0.05, 0.1, 0.2
+    I = np.array([1.0, 2.0, 3.0, 4.0])
+    x, y, i = O.delete_peaks(qx, qy, I, spots, r_del=0.04, delta=0.08)
+    np.testing.assert_allclose(x, [0.05, 0.06, 0.2])
+    np.testing.assert_allclose(i, [2.0 * (0.05 - 0.04) / 0.04, 3.0, 4.0])
+
+
+@pytest.fixture(scope="module")
+def au_6deg_plan():
+    v0, v1, v2, om = O.cubic_triangle()
+    za = O.zone_axis_grid(v0, v1, v2, 6.0, om)
+    return O.orientation_plan(au_reflections(), za,
+                              O.PlanParams(n_shells=40, dq=0.0375, n_phi=72, delta=0.08, lam=LAM))
+
+
+def test_two_overlapping_grid_patterns_are_both_found(au_6deg_plan):
+    """Peaks of two noiseless patterns at grid orientations, superimposed:
+    two rounds of match and deletion return both orientations (up to the
+    crystal's symmetry), each with the full pattern's correlation at it."""
+    plan = au_6deg_plan
+    refl = au_reflections()
+    ops = O.proper_point_group("cubic")
+    N = plan.params.n_phi
+    rng = np.random.default_rng(41)
+    found = 0
+    for _ in range(4):
+        zs = rng.choice(len(plan.za), 2, replace=False)
+        ms = [O.orientation_matrix(plan.za[z], -2 * math.pi * int(rng.integers(N)) / N, 0)
+              for z in zs]
+        pats = [O.kinematical_pattern(refl, m, LAM, AU["sigma"], 1e-3) for m in ms]
+        qx, qy, I = (np.concatenate([p[i] for p in pats]) for i in range(3))
+        res = O.match_multiple(plan, refl, qx, qy, I, 2, r_del=0.04, lam=LAM, sigma=AU["sigma"])
+        assert len(res) == 2
+        got = [min(O.misorientation_deg(r.m, m, ops) for m in ms) for r in res]
+        found += sum(g < 1e-3 for g in got)
+        X = O.polar_image(qx, qy, I, plan.params)
+        C, Cm = O.correlogram(plan.P_hat, X)
+        for r in res:
+            assert r.score == pytest.approx((Cm if r.mirror else C)[r.za, r.k], rel=1e-12)
+    assert found >= 7
+
+
+def test_single_pattern_second_match_is_weak(au_6deg_plan):
+    """One noiseless pattern: after its peaks are deleted little or nothing
+    is left, so a second match, if any, scores far below the first."""
+    plan = au_6deg_plan
+    refl = au_reflections()
+    N = plan.params.n_phi
+    m = O.orientation_matrix(plan.za[5], -2 * math.pi * 7 / N, 0)
+    qx, qy, I = O.kinematical_pattern(refl, m, LAM, AU["sigma"], 1e-3)
+    res = O.match_multiple(plan, refl, qx, qy, I, 3, r_del=0.04, lam=LAM, sigma=AU["sigma"])
+    assert len(res) >= 1
+    assert all(r.reduced_score < 0.2 * res[0].reduced_score for r in res[1:])
