@@ -276,6 +276,34 @@ acom_status acom_match(acom_plan plan, const acom_peaks_csr* peaks,
                        void* cuda_stream);
 
 /*
+ * acom_match_multi - several orientations per pattern (section "Matching of
+ * Overlapping Diffraction Patterns"): match; compute the forward pattern of
+ * the match's grid orientation (the reflections of the plan whose Gaussian
+ * shape factor D(s_g), Eq. 8 with the plan's sigma_exc, is at least 1e-3);
+ * remove every peak within ``r_del`` of a forward spot and keep (d - r_del) /
+ * (delta - r_del) of the intensity of those within the plan's delta; match
+ * the rest again, n_matches times in all.
+ *
+ *   results   : n_matches (1..8) result structs as for acom_match (za_idx,
+ *               phi3_bin, mirror, score required; the other fields optional).
+ *               results[j] holds the j-th match of every pattern.  ``score``
+ *               and ``score_cos`` are those of the ORIGINAL full pattern at
+ *               the match's (zone axis, phi3 bin, mirror), as the paper
+ *               reports them; orient/phi3 refine the match as acom_match does.
+ *               za_idx = -1 marks "no further orientation": the best
+ *               correlation of what was left was 0 (score 0).
+ *   r_del     : deletion radius (1/Angstrom), 0 <= r_del < delta.
+ *   opts      : as for acom_match (certified pruning or exhaustive).
+ *
+ * A single-phase plan (ACOM_ERR_UNSUPPORTED otherwise).  The peaks are read,
+ * not changed (a working copy is made).  Synchronises the stream once per
+ * match and once at the end.
+ */
+acom_status acom_match_multi(acom_plan plan, const acom_peaks_csr* peaks,
+                             const acom_match_opts* opts, int32_t n_matches, float r_del,
+                             acom_result* results, void* cuda_stream);
+
+/*
  * acom_polar_spectra - the first half of acom_match alone: the sparse polar
  * image of every pattern and its Fourier transform along phi3, written to
  * DEVICE memory ``dst`` laid out [n_patterns][S][F][2] FP32, and optionally

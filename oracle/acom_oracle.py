@@ -797,6 +797,7 @@ class MatchN:
     score_cos: float      # the same over ||X|| of the full pattern
     reduced_score: float  # the maximum of the reduced pattern that found it
     m: np.ndarray         # grid orientation
+    match: Match = None   # the match of the reduced pattern (its correlogram)
 
 
 def match_multiple(plan: Plan, refl: Reflections, qx, qy, I, n_matches, r_del, lam, sigma,
@@ -823,7 +824,7 @@ def match_multiple(plan: Plan, refl: Reflections, qx, qy, I, n_matches, r_del, l
         full = float((Cm if mt.mirror else C)[mt.za, mt.k])
         m = orientation_matrix(plan.za[mt.za], -2 * math.pi * mt.k / N, mt.mirror)
         out.append(MatchN(mt.za, mt.k, mt.mirror, full, full / xn if xn > 0 else 0.0,
-                          mt.score, m))
+                          mt.score, m, mt))
         cur = delete_peaks(*cur, forward_spots(refl, m, lam, sigma, d_min), r_del,
                            plan.params.delta)
     return out

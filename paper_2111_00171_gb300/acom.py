@@ -29,7 +29,7 @@ EXPORTED = ("acom_plan_create", "acom_plan_destroy", "acom_plan_get_info",
             "acom_last_error",
             "acom_version", "acom_profile_enable", "acom_profile_reset", "acom_profile_read",
             "acom_kernel_launches", "acom_plan_concat", "acom_plan_get_phases", "acom_refine",
-            "acom_refine_defaults", "acom_kinematical_score")
+            "acom_refine_defaults", "acom_kinematical_score", "acom_match_multi")
 
 
 class AcomError(RuntimeError):
@@ -115,6 +115,8 @@ def load_library():
     lib.acom_refine.argtypes = [P, C.POINTER(PeaksCSR), C.POINTER(RefineOpts), P, P, P, P, P]
     lib.acom_refine_defaults.restype = RefineOpts
     lib.acom_kinematical_score.argtypes = [P, C.POINTER(PeaksCSR), P, P, C.c_float, P, P, P, P]
+    lib.acom_match_multi.argtypes = [P, C.POINTER(PeaksCSR), C.POINTER(MatchOpts), C.c_int32,
+                                     C.c_float, C.POINTER(Result), P]
     lib.acom_plan_get_zone_axes.argtypes = [P, P]
     lib.acom_plan_get_spectra.argtypes = [P, P, P]
     lib.acom_match.argtypes = [P, C.POINTER(PeaksCSR), C.POINTER(MatchOpts), C.POINTER(Result), P]
@@ -131,7 +133,7 @@ def load_library():
     lib.acom_version.restype = C.c_int32
     for name in ("acom_plan_create", "acom_plan_destroy", "acom_plan_get_info",
                  "acom_plan_concat", "acom_plan_get_phases", "acom_refine",
-                 "acom_kinematical_score",
+                 "acom_kinematical_score", "acom_match_multi",
                  "acom_plan_get_zone_axes", "acom_plan_get_spectra", "acom_match",
                  "acom_polar_spectra", "acom_bounds", "acom_bounds_static"):
         getattr(lib, name).restype = C.c_int
@@ -349,6 +351,21 @@ class Plan:
                                     _stream_ptr(stream)))
         return r
 
+
+    def match_multi(self, row_ptr, qx, qy, I, n_matches=3, r_del=0.04, refine=True, chunk=0,
+                    exhaustive=False, stream=None):
+        """acom_match_multi: up to n_matches orientations per pattern by
+        iterative peak deletion; returns one result dict per match (score and
+        score_cos of the original pattern; za_idx -1 where nothing was left)."""
+        pk = self._csr(row_ptr, qx, qy, I)
+        outs = [self.alloc_result(pk.n_patterns) for _ in range(n_matches)]
+        arr = (Result * n_matches)(*[Result(*(_ptr(r.get(k)) for k, _ in Result._fields_))
+                                     for r in outs])
+        opts = MatchOpts(1 if refine else 0, int(chunk), 1 if exhaustive else 0)
+        _check(self._lib.acom_match_multi(self.handle, C.byref(pk), C.byref(opts),
+                                          int(n_matches), float(r_del), arr,
+                                          _stream_ptr(stream)))
+        return outs
 
     # ---- continuous refinement (acom_refine, acom_kinematical_score)
 

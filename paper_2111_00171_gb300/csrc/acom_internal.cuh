@@ -120,6 +120,8 @@ struct Workspace {
 
 // phases of one plan (acom_plan_concat)
 constexpr int kMaxPhases = 8;
+// matches per pattern of acom_match_multi
+constexpr int kMaxMatches = 8;
 
 // precisions whose contraction runs on the tensor cores
 inline bool tc_precision(int precision) {
@@ -225,6 +227,12 @@ void launch_refine_orient(const acom_plan_s* p, const acom_peaks_csr* pk, int st
 void launch_kin_score(const acom_plan_s* p, const acom_peaks_csr* pk, const float* orient,
                       const float* r, float rho, float* score, float* grad, float* gn,
                       cudaStream_t st);
+// multimatch.cu: peak deletion after a match, full-pattern score at a match
+void launch_delete_peaks(const acom_plan_s* p, const acom_peaks_csr* work, const acom_result& r,
+                         float r_del, float d_min, cudaStream_t st);
+void launch_score_at(const acom_plan_s* p, const float* Xsr, const float* Xsi, const int2* srange,
+                     const float* xnorm2, int nb, const acom_result* res, int n_matches,
+                     int64_t off, cudaStream_t st);
 // exhaustive mode: phase of each winner and each phase's best score
 void launch_phase_outputs(const acom_plan_s* p, const float* za_scores, int nb, acom_result out,
                           int64_t off, cudaStream_t st);

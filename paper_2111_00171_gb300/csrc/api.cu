@@ -870,4 +870,90 @@ acom_refine_opts acom_refine_defaults(void) {
     return o;
 }
 
+acom_status acom_match_multi(acom_plan p, const acom_peaks_csr* peaks,
+                             const acom_match_opts* opts, int32_t n_matches, float r_del,
+                             acom_result* results, void* cuda_stream) {
+    g_last_error.clear();
+    if (!p || !results) return set_error(ACOM_ERR_INVALID_ARG, "null argument");
+    acom_status s = check_peaks(peaks);
+    if (s != ACOM_OK) return s;
+    if (n_matches < 1 || n_matches > kMaxMatches)
+        return set_error(ACOM_ERR_INVALID_ARG, "n_matches must be 1..8");
+    if (!(r_del >= 0.0f) || !(r_del < (float)p->delta))
+        return set_error(ACOM_ERR_INVALID_ARG, "r_del must be in [0, delta)");
+    const int64_t B = peaks->n_patterns;
+    for (int j = 0; j < n_matches; ++j)
+        if (B > 0 && (!results[j].za_idx || !results[j].phi3_bin || !results[j].mirror ||
+                      !results[j].score))
+            return set_error(ACOM_ERR_INVALID_ARG,
+                             "each result needs za_idx, phi3_bin, mirror and score");
+    if (B == 0) return ACOM_OK;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    s = refine_table(p, st);
+    if (s != ACOM_OK) return s;
+    int64_t nnz = 0;
+    cudaError_t e = cudaMemcpyAsync(&nnz, peaks->row_ptr + B, sizeof(int64_t),
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_error(e, "match_multi: reading row_ptr");
+    if (nnz < 0) return set_error(ACOM_ERR_BAD_INPUT, "bad peak data: row_ptr decreasing");
+    // working copy of the peaks: deletion changes it between matches
+    float *wx = nullptr, *wy = nullptr, *wI = nullptr;
+    const size_t bytes = sizeof(float) * (size_t)(nnz > 0 ? nnz : 1);
+    if ((e = pool_alloc(reinterpret_cast<void**>(&wx), bytes, st)) != cudaSuccess ||
+        (e = pool_alloc(reinterpret_cast<void**>(&wy), bytes, st)) != cudaSuccess ||
+        (e = pool_alloc(reinterpret_cast<void**>(&wI), bytes, st)) != cudaSuccess) {
+        pool_free(wx, st);
+        pool_free(wy, st);
+        pool_free(wI, st);
+        return cuda_error(e, "match_multi: working peaks");
+    }
+    auto release = [&]() {
+        pool_free(wx, st);
+        pool_free(wy, st);
+        pool_free(wI, st);
+    };
+    if (nnz > 0) {
+        cudaMemcpyAsync(wx, peaks->qx, sizeof(float) * nnz, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(wy, peaks->qy, sizeof(float) * nnz, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(wI, peaks->I, sizeof(float) * nnz, cudaMemcpyDeviceToDevice, st);
+    }
+    acom_peaks_csr work{B, peaks->row_ptr, wx, wy, wI};
+    for (int j = 0; j < n_matches; ++j) {
+        s = acom_match(p, &work, opts, &results[j], cuda_stream);
+        if (s != ACOM_OK) {
+            release();
+            return s;
+        }
+        launch_delete_peaks(p, &work, results[j], r_del, 1e-3f, st);
+    }
+    // the full pattern's correlation at every match
+    const int chunk = (int)std::min<int64_t>(B, 8192);
+    s = ensure_workspace(p, chunk, false, false, st);
+    if (s != ACOM_OK) {
+        release();
+        return s;
+    }
+    cudaMemsetAsync(p->err, 0, sizeof(int), st);
+    RasterGeom geo{p->S, p->Spad, p->N, p->F, (float)p->dq, (float)p->delta, (float)p->gamma_pow, 0};
+    for (int64_t c0 = 0; c0 < B; c0 += chunk) {
+        const int nb = (int)std::min<int64_t>(chunk, B - c0);
+        PatternSource src{nullptr, p->ws.PTs, peaks->row_ptr + c0, peaks->qx, peaks->qy, peaks->I, nb,
+                          (float)p->gamma_pow, (float)p->omega};
+        RasterOut ro;
+        ro.sre = p->ws.Xsr;
+        ro.sim = p->ws.Xsi;
+        ro.sumsq = p->ws.xnorm2;
+        ro.fnorm = p->ws.xfn;
+        ro.srange = p->ws.srange;
+        launch_raster_patterns(geo, src, ro, p->err, st);
+        launch_score_at(p, p->ws.Xsr, p->ws.Xsi, p->ws.srange, p->ws.xnorm2, nb, results, n_matches,
+                        c0, st);
+    }
+    e = cudaGetLastError();
+    release();
+    if (e != cudaSuccess) return cuda_error(e, "match_multi launch");
+    return read_error_word(p, st);
+}
+
 }  // extern "C"
