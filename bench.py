@@ -12,6 +12,7 @@ transform, shell contraction, inverse transform + argmax, refinement).
   python bench.py --impl reference ...   # the FP64 CPU oracle as the reference arm
   python bench.py --workload mixed ...   # two phases in one plan (see below)
   python bench.py --workload refine ...  # coarse 3-degree match + continuous refinement
+  python bench.py --workload sweep ...   # 512x512 scan: 1 and 0.5 degree plans x precisions
 
 The default precision is FP16 operands (per-pattern and per-plan power-of-two
 scaling) on the tensor cores for the certified bound, with every winner
@@ -31,6 +32,11 @@ axes) and then refined (20 Gauss-Newton steps of the continuous kinematical
 score, from the match, from the runner-up zone axis outside the match's grid
 neighbourhood, and from the Friedel twin of each); the line also carries the
 plain FP32 1-degree grid path measured in the same run.
+
+--workload sweep: a 512x512 grain scan (262,144 patterns, Poisson(30) peaks
+clipped to 5..80) against the 1-degree (903 axes) and 0.5-degree (3486 axes)
+plans with FP32, BF16 and FP16 contraction operands; the line's value is the
+0.5-degree FP16 step and its "sweep" object holds every combination.
 """
 
 import argparse
@@ -60,6 +66,12 @@ REFINE = dict(name="au_scan_256x256_3deg_refined", phases=(("Au", 3.0),), Z=105,
                     "axes, 150 shells x 0.01 1/A, 360 phi3 bins), then refined: 20 Gauss-Newton "
                     "steps of the continuous kinematical score from the match, the runner-up "
                     "axis and their Friedel twins"))
+SWEEP = dict(name="au_scan_512x512_halfdeg_sweep", phases=(("Au", 0.5),), Z=3486, step=0.5,
+             seed=1005, H=512, Wd=512, peaks="poisson30", sweep=True,
+             text=("fcc Au 512x512 scan (262,144 patterns, Poisson(30) peaks clipped to 5..80, "
+                   "CSR, 200 Voronoi grains) vs the 0.5-degree plan (3486 zone axes, 150 shells "
+                   "x 0.01 1/A, 360 phi3 bins); sweep over 1 and 0.5 degree plans and FP32, "
+                   "BF16 and FP16 operands"))
 MIXED = dict(name="au2deg_mg1deg_mixed_65536", phases=(("Au", 2.0), ("Mg", 1.0)), Z=231 + 1770,
              step=None, S=75, dq=0.02, N=180, seed=1003, n_patterns=65536,
              text=("65,536 patterns, 50/50 fcc Au / hcp Mg (peaks > 1e-3 of the strongest, "
@@ -82,14 +94,20 @@ def parse():
                     help="inverse-transform every zone axis (no certified pruning)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=16)
-    ap.add_argument("--scan", default="256x256",
-                    help="scan size HxW (smaller sizes are for profiling captures only)")
-    ap.add_argument("--workload", default="au_scan", choices=["au_scan", "mixed", "refine"])
+    ap.add_argument("--scan", default=None,
+                    help="scan size HxW (default: the workload's; smaller sizes are for "
+                         "profiling captures only)")
+    ap.add_argument("--workload", default="au_scan",
+                    choices=["au_scan", "mixed", "refine", "sweep"])
     args = ap.parse_args()
     if args.workload == "mixed":
         W.update(MIXED)
     elif args.workload == "refine":
         W.update(REFINE)
+    elif args.workload == "sweep":
+        W.update(SWEEP)
+    if args.scan is None:
+        args.scan = f"{W['H']}x{W['Wd']}"
     if args.precision is None:
         args.precision = W.get("precision", "fp16")
     return args
@@ -100,7 +118,7 @@ def make_scan(seed, args):
     if "n_patterns" in W:
         return synth.mixed_patterns(seed, n_patterns=W["n_patterns"])
     H, Wd = (int(v) for v in args.scan.split("x"))
-    return synth.grain_scan(seed, H=H, W=Wd)
+    return synth.grain_scan(seed, H=H, W=Wd, peaks=W.get("peaks", "uniform10-60"))
 
 
 def peaks_file():
@@ -457,6 +475,8 @@ def main():
 
     res = {k: out[k].cpu().numpy() for k in out_keys}
     grid_path = grid_fp32_path(args, acom, scan, d_in, flush, stream) if W.get("refine") else None
+    sweep = sweep_combos(args, acom, lib, scan, d_in, flush, stream, prof, res) \
+        if W.get("sweep") else None
     if mixed:
         ph = res["phase"]
         ok = ph == scan.phase
@@ -501,6 +521,8 @@ def main():
             "accuracy": accuracy}
     if grid_path is not None:
         line["grid_fp32_1deg"] = grid_path
+    if sweep is not None:
+        line["sweep"] = sweep
     if not args.no_cpu_baseline and world == 1:
         cb, agree = cpu_baseline(scan, res, args.cpu_sample)
         line["cpu_baseline"] = cb
@@ -508,6 +530,102 @@ def main():
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def sweep_combos(args, acom, lib, scan, d_in, flush, stream, main_prof, main_res):
+    """Every (plan step, precision) of the sweep: patterns/s of plan build +
+    match (CUDA events, L2 flushed; one warm-up and one timed step for the
+    combinations beside the line's own), the contraction's fraction of its
+    roofline, axes evaluated, misorientation, and the oracle's argmax
+    agreement on 16 sampled patterns per plan (the certified winner does not
+    depend on the operand precision)."""
+    import torch
+    peaks, src = peaks_file()
+    v, om = acom.cubic_triangle()
+    cr = acom.au_crystal()
+    B = scan.n_patterns
+    F, S, N = W["N"] // 2 + 1, W["S"], W["N"]
+    fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    out_rows = []
+    for step_deg, Z in ((1.0, 903), (0.5, 3486)):
+        agree = oracle_agreement(scan, step_deg, main_res if step_deg == W["step"] else None,
+                                 acom, d_in)
+        for prec in ("fp32", "bf16", "fp16"):
+            code = {"bf16": acom.ACOM_PREC_BF16, "fp16": acom.ACOM_PREC_FP16,
+                    "fp32": acom.ACOM_PREC_FP32}[prec]
+
+            def plan():
+                return acom.Plan(cr, v, om, step_deg, S, W["dq"], N, delta=W["delta"],
+                                 lam=W["lam"], q_max=W["q_max"], precision=code)
+            probe = plan()
+            out = probe.alloc_result(B)
+            probe.close()
+            info = {}
+
+            def step():
+                p = plan()
+                p.match(*d_in, out=out)
+                info["ev"] = p.get_info()["last_evaluated"]
+                p.close()
+            step()
+            torch.cuda.synchronize()
+            lib.acom_profile_reset()
+            lib.acom_profile_enable(1)
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            lib.acom_profile_enable(0)
+            prof = read_profile(lib, acom)
+            name = "contract_fp32" if prec == "fp32" else "contract_bf16"
+            cnt, cms = prof.get(name, (0, 0.0))
+            flops = 8.0 * Z * S * F * B
+            tflops = flops / (cms / 1e3) / 1e12 if cms else 0.0
+            peak = fp32_peak if prec == "fp32" else peaks["bf16_tflops_sustained"]
+            mis, mis_twin, tilt = misorientation(out["orient"].cpu().numpy(), scan.truth)
+            out_rows.append({"plan_step_deg": step_deg, "zone_axes": Z, "precision": prec,
+                             "patterns_per_s": B / (ms / 1e3), "ms_per_step": ms,
+                             "contraction_tflops": tflops, "contraction_frac": tflops / peak,
+                             "contraction_bound": "alu" if prec == "fp32" else "tensor",
+                             "axes_evaluated_per_pattern": info["ev"] / B,
+                             "mean_misorientation_deg": mis,
+                             "mean_misorientation_friedel_deg": mis_twin,
+                             "oracle_argmax_agreement": agree})
+    out_rows.append({"precision": "fp8", "built": False,
+                     "note": "FP8 (e4m3) operands are not built: their 2^-4 rounding would make "
+                             "the certified margin about a quarter of the bound"})
+    return out_rows
+
+
+def oracle_agreement(scan, step_deg, res, acom, d_in, n=16):
+    """Argmax agreement (ties within 1e-5 count) of the FP16 match with the
+    oracle on n sampled patterns of the plan with this step."""
+    from oracle import acom_oracle as O
+    refl = O.reflections(np.eye(3) * 4.08, [[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0]],
+                         [79.0] * 4, [0.25] * 4, W["q_max"])
+    v0, v1, v2, om = O.cubic_triangle()
+    plan = O.orientation_plan(refl, O.zone_axis_grid(v0, v1, v2, step_deg, om),
+                              O.PlanParams(W["S"], W["dq"], W["N"], W["delta"], lam=W["lam"]))
+    if res is None:
+        v, omg = acom.cubic_triangle()
+        p = acom.Plan(acom.au_crystal(), v, omg, step_deg, W["S"], W["dq"], W["N"],
+                      delta=W["delta"], lam=W["lam"], q_max=W["q_max"],
+                      precision=acom.ACOM_PREC_FP16)
+        r = p.match(*d_in)
+        res = {k: r[k].cpu().numpy() for k in ("za_idx", "phi3_bin", "mirror")}
+        p.close()
+    rng = np.random.default_rng(0)
+    agree = 0
+    for b in rng.choice(scan.n_patterns, n, replace=False):
+        mt = O.match_pattern(plan, *scan.pattern(b))
+        z, k, m = int(res["za_idx"][b]), int(res["phi3_bin"][b]), int(res["mirror"][b])
+        val = (mt.Cm if m else mt.C)[z, k]
+        agree += int((z, k, m) == (mt.za, mt.k, mt.mirror) or val >= mt.score * (1 - 1e-5))
+    return f"{agree}/{n}"
 
 
 def grid_fp32_path(args, acom, scan, d_in, flush, stream):
