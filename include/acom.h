@@ -39,10 +39,15 @@ typedef enum {
     ACOM_PREC_FP32 = 0,   /* FP32 CUDA-core path (reference GPU path)               */
     ACOM_PREC_BF16 = 1,   /* BF16 operands on tcgen05 tensor cores, FP32 accumulate,
                              top candidates re-scored in FP32                       */
-    ACOM_PREC_FP16 = 2    /* FP16 operands on tcgen05 tensor cores, FP32 accumulate;
+    ACOM_PREC_FP16 = 2,   /* FP16 operands on tcgen05 tensor cores, FP32 accumulate;
                              pattern and plan spectra are scaled by powers of two
                              into FP16 range and the bound scaled back; top
                              candidates re-scored in FP32                           */
+    ACOM_PREC_FP8 = 3     /* experiment: E4M3 operands (the FP16 operands times
+                             2^-6, exact) on the tensor cores, FP32 accumulate.
+                             Their 2^-4 rounding makes the certified margin about
+                             a quarter of the bound, so certified pruning
+                             evaluates most axes; use rescore_top            */
 } acom_precision;
 
 typedef struct acom_plan_s* acom_plan;
@@ -249,6 +254,11 @@ typedef struct {
     int32_t chunk;            /* patterns per internal chunk, 0 = default       */
     int32_t exhaustive;       /* 1: inverse-transform every zone axis (test and
                                  reference mode); 0: certified pruning         */
+    int32_t rescore_top;      /* > 0 (with exhaustive = 0): no certification;
+                                 only the rescore_top axes of largest bound are
+                                 evaluated exactly in FP32 and the best of them
+                                 wins (the grid neighbours of the winner are
+                                 evaluated for the refinement as usual)       */
 } acom_match_opts;
 
 /*

@@ -20,6 +20,7 @@ ACOM_OK = 0
 ACOM_PREC_FP32 = 0
 ACOM_PREC_BF16 = 1
 ACOM_PREC_FP16 = 2
+ACOM_PREC_FP8 = 3
 STATUS = {0: "ACOM_OK", 1: "ACOM_ERR_INVALID_ARG", 2: "ACOM_ERR_OOM", 3: "ACOM_ERR_CUDA",
           4: "ACOM_ERR_TIMEOUT", 5: "ACOM_ERR_UNSUPPORTED", 6: "ACOM_ERR_BAD_INPUT"}
 
@@ -79,7 +80,8 @@ class Result(C.Structure):
 
 
 class MatchOpts(C.Structure):
-    _fields_ = [("refine", C.c_int32), ("chunk", C.c_int32), ("exhaustive", C.c_int32)]
+    _fields_ = [("refine", C.c_int32), ("chunk", C.c_int32), ("exhaustive", C.c_int32),
+                ("rescore_top", C.c_int32)]
 
 
 class RefineOpts(C.Structure):
@@ -337,7 +339,7 @@ class Plan:
         return r
 
     def match(self, row_ptr, qx, qy, I, refine=True, chunk=0, za_scores=False, out=None,
-              exhaustive=False, phase_scores=False, runner=False, stream=None):
+              exhaustive=False, phase_scores=False, runner=False, rescore_top=0, stream=None):
         """acom_match on device CSR tensors; returns a dict of device tensors
         (with phase_scores: the phase of each winner and every phase's best;
         with runner: the runner-up axis, score and grid orientation)."""
@@ -346,7 +348,7 @@ class Plan:
                                                           phase_scores=phase_scores,
                                                           runner=runner)
         res = Result(*(_ptr(r.get(k)) for k, _ in Result._fields_))
-        opts = MatchOpts(1 if refine else 0, int(chunk), 1 if exhaustive else 0)
+        opts = MatchOpts(1 if refine else 0, int(chunk), 1 if exhaustive else 0, int(rescore_top))
         _check(self._lib.acom_match(self.handle, C.byref(pk), C.byref(opts), C.byref(res),
                                     _stream_ptr(stream)))
         return r

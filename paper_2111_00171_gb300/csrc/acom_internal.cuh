@@ -87,6 +87,11 @@ constexpr float kFp16Target = 16384.0f;
 // Absolute error of an FP16 operand below the normal range (|x| < 2^-14),
 // whether the value is rounded to a subnormal or flushed to zero
 constexpr double kFp16Eta = 6.103515625e-05;   // 2^-14
+// E4M3 operands: the FP16 operands times 2^-6 (|x| <= 2^8 < 448, exact), so
+// the pattern and plan scales are the FP16 ones times 2^-6; below E4M3's
+// normal range (2^-6) an operand is off by at most 2^-6
+constexpr float kFp8Shift = 0.015625f;          // 2^-6
+constexpr double kFp8Eta = 0.015625;            // 2^-6
 
 // 2^k of the plan's FP16 spectra: the largest power of two with 2^k sqrt(N) <= 2^14
 inline float fp16_plan_scale(int N) {
@@ -115,6 +120,7 @@ struct Workspace {
     unsigned long long* best = nullptr;  // [chunk] packed (score, index)
     float* za_scores = nullptr;    // [chunk][Z]
     float* xscale = nullptr;       // [chunk] 2^e of each pattern's FP16 spectrum
+    void* XB8 = nullptr;           // E4M3 copy of XB (FP8 plans)
     size_t bytes = 0;
 };
 
@@ -125,7 +131,14 @@ constexpr int kMaxMatches = 8;
 
 // precisions whose contraction runs on the tensor cores
 inline bool tc_precision(int precision) {
-    return precision == ACOM_PREC_BF16 || precision == ACOM_PREC_FP16;
+    return precision == ACOM_PREC_BF16 || precision == ACOM_PREC_FP16 ||
+           precision == ACOM_PREC_FP8;
+}
+// bytes per tensor-core operand element
+inline int tc_elem_bytes(int precision) { return precision == ACOM_PREC_FP8 ? 1 : 2; }
+// make_bf16_map / launch_plan_to_bf16 operand kind: 0 BF16, 1 FP16, 2 E4M3
+inline int tc_kind(int precision) {
+    return precision == ACOM_PREC_FP8 ? 2 : (precision == ACOM_PREC_FP16 ? 1 : 0);
 }
 
 }  // namespace acom
@@ -206,18 +219,19 @@ void launch_contract_bound_fp32(const acom_plan_s* p, const float* Xr, const flo
 void launch_plan_fnorm_max(const acom_plan_s* p, float* out, cudaStream_t st);
 // match_tc.cu
 acom_status make_bf16_map(void* map_storage, const void* base, uint64_t rows, uint64_t cols,
-                          bool fp16 = false);
+                          int kind = 0);
+void launch_half_to_e4m3(const void* src, void* dst, int64_t n, float mul, cudaStream_t st);
 // xscale: per-pattern 2^e of FP16 pattern spectra (nullptr: BF16, no scale)
 void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_stride, int nb,
                               float* U, cudaStream_t st, const float* xscale = nullptr);
-// fp16: FP16 of scale * src instead of BF16 of src
+// kind 1 / 2: FP16 / E4M3 of scale * src instead of BF16 of src
 void launch_plan_to_bf16(const float* src, int Zp, int F, int Spad, void* dst, cudaStream_t st,
-                         bool fp16 = false, float scale = 1.0f);
+                         int kind = 0, float scale = 1.0f);
 void launch_select_exact(const acom_plan_s* p, const float* Xsr, const float* Xsi, const float* U,
                          const float* xfn, const int2* srange, const float* pfmax,
                          const float* xnorm2, int nb,
                          float kappa, int refine, acom_result out, int64_t off, int* n_eval,
-                         cudaStream_t st, const float* xscale = nullptr);
+                         cudaStream_t st, const float* xscale = nullptr, int rescore_top = 0);
 // refine.cu: continuous refinement on the plan's reflections
 acom_status refine_table(acom_plan_s* p, cudaStream_t st);
 void launch_refine_orient(const acom_plan_s* p, const acom_peaks_csr* pk, int steps,

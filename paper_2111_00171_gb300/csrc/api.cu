@@ -147,6 +147,7 @@ static void free_workspace(Workspace& ws, cudaStream_t st) {
     pool_free(ws.za_scores, st);
     pool_free(ws.XB, st);
     pool_free(ws.xscale, st);
+    pool_free(ws.XB8, st);
     ws = Workspace{};
 }
 
@@ -184,13 +185,21 @@ static acom_status ensure_workspace(acom_plan_s* p, int chunk, bool need_chat, b
     if ((e = dalloc(&ws.best, (size_t)chunk, &acc, st)) != cudaSuccess) goto fail;
     if ((e = dalloc(&ws.za_scores, (size_t)chunk * p->Z, &acc, st)) != cudaSuccess) goto fail;
     if (tc_precision(p->precision)) {
-        const bool fp16 = p->precision == ACOM_PREC_FP16;
+        // the raster writes BF16, or FP16 with a per-pattern scale; E4M3
+        // operands are converted from the FP16 rows
+        const bool scaled = p->precision != ACOM_PREC_BF16;
+        const bool fp8 = p->precision == ACOM_PREC_FP8;
         ws.PTs = (chunk + 63) / 64;
         const size_t rows = (size_t)p->F * ws.PTs * 128;
         if ((e = pool_alloc(&ws.XB, rows * p->Spad * 2, st)) != cudaSuccess) goto fail;
         acc += rows * p->Spad * 2;
-        if (fp16 && (e = dalloc(&ws.xscale, (size_t)chunk, &acc, st)) != cudaSuccess) goto fail;
-        acom_status ms = make_bf16_map(ws.map_x, ws.XB, rows, (uint64_t)p->Spad, fp16);
+        if (fp8) {
+            if ((e = pool_alloc(&ws.XB8, rows * p->Spad, st)) != cudaSuccess) goto fail;
+            acc += rows * p->Spad;
+        }
+        if (scaled && (e = dalloc(&ws.xscale, (size_t)chunk, &acc, st)) != cudaSuccess) goto fail;
+        acom_status ms = make_bf16_map(ws.map_x, fp8 ? ws.XB8 : ws.XB, rows, (uint64_t)p->Spad,
+                                       tc_kind(p->precision));
         if (ms != ACOM_OK) {
             free_workspace(p->ws, st);
             return ms;
@@ -370,19 +379,20 @@ acom_status acom_plan_create(const acom_crystal* crystal, const acom_za_grid* gr
     launch_plan_fnorm_max(p, p->pfmax, st);
     ACOM_CK(cudaGetLastError());
     if (tc_precision(p->precision)) {
-        const bool fp16 = p->precision == ACOM_PREC_FP16;
-        p->pscale = fp16 ? fp16_plan_scale(p->N) : 1.0f;
-        const size_t n = (size_t)p->F * p->Zp * p->Spad;
-        ACOM_CK(pool_alloc(&p->Pb_r, n * 2, st));
-        ACOM_CK(pool_alloc(&p->Pb_i, n * 2, st));
-        p->bytes += 4 * n;
-        launch_plan_to_bf16(p->Pr, p->Zp, p->F, p->Spad, p->Pb_r, st, fp16, p->pscale);
-        launch_plan_to_bf16(p->Pi, p->Zp, p->F, p->Spad, p->Pb_i, st, fp16, p->pscale);
+        const int kind = tc_kind(p->precision);
+        p->pscale = kind == 0 ? 1.0f
+                              : fp16_plan_scale(p->N) * (kind == 2 ? kFp8Shift : 1.0f);
+        const size_t n = (size_t)p->F * p->Zp * p->Spad * tc_elem_bytes(p->precision);
+        ACOM_CK(pool_alloc(&p->Pb_r, n, st));
+        ACOM_CK(pool_alloc(&p->Pb_i, n, st));
+        p->bytes += 2 * n;
+        launch_plan_to_bf16(p->Pr, p->Zp, p->F, p->Spad, p->Pb_r, st, kind, p->pscale);
+        launch_plan_to_bf16(p->Pi, p->Zp, p->F, p->Spad, p->Pb_i, st, kind, p->pscale);
         ACOM_CK(cudaGetLastError());
-        s = make_bf16_map(p->map_pr, p->Pb_r, (uint64_t)p->F * p->Zp, (uint64_t)p->Spad, fp16);
+        s = make_bf16_map(p->map_pr, p->Pb_r, (uint64_t)p->F * p->Zp, (uint64_t)p->Spad, kind);
         if (s == ACOM_OK)
             s = make_bf16_map(p->map_pi, p->Pb_i, (uint64_t)p->F * p->Zp, (uint64_t)p->Spad,
-                              fp16);
+                              kind);
         if (s != ACOM_OK) {
             destroy_plan(p);
             return s;
@@ -519,15 +529,16 @@ acom_status acom_plan_concat(const acom_plan* plans, int32_t n_plans, void* cuda
                                 cudaMemcpyDeviceToDevice, st));
     }
     if (tc_precision(p->precision)) {
-        // [F][Zp][Spad] 16-bit tiles: per frequency, each input's Z rows at its offset
-        const bool fp16 = p->precision == ACOM_PREC_FP16;
+        // [F][Zp][Spad] operand tiles: per frequency, each input's Z rows at its offset
+        const int kind = tc_kind(p->precision);
+        const size_t eb = (size_t)tc_elem_bytes(p->precision);
         const size_t n = (size_t)F * p->Zp * Spad;
-        ACOM_CK(pool_alloc(&p->Pb_r, n * 2, st));
-        ACOM_CK(pool_alloc(&p->Pb_i, n * 2, st));
-        p->bytes += 4 * n;
-        ACOM_CK(cudaMemsetAsync(p->Pb_r, 0, n * 2, st));
-        ACOM_CK(cudaMemsetAsync(p->Pb_i, 0, n * 2, st));
-        const size_t row = (size_t)Spad * 2;
+        ACOM_CK(pool_alloc(&p->Pb_r, n * eb, st));
+        ACOM_CK(pool_alloc(&p->Pb_i, n * eb, st));
+        p->bytes += 2 * n * eb;
+        ACOM_CK(cudaMemsetAsync(p->Pb_r, 0, n * eb, st));
+        ACOM_CK(cudaMemsetAsync(p->Pb_i, 0, n * eb, st));
+        const size_t row = (size_t)Spad * eb;
         for (int i = 0, base = 0; i < n_plans; base += plans[i]->Z, ++i) {
             const acom_plan_s* q = plans[i];
             ACOM_CK(cudaMemcpy2DAsync(static_cast<char*>(p->Pb_r) + base * row, p->Zp * row, q->Pb_r,
@@ -535,9 +546,9 @@ acom_status acom_plan_concat(const acom_plan* plans, int32_t n_plans, void* cuda
             ACOM_CK(cudaMemcpy2DAsync(static_cast<char*>(p->Pb_i) + base * row, p->Zp * row, q->Pb_i,
                                       q->Zp * row, q->Z * row, F, cudaMemcpyDeviceToDevice, st));
         }
-        acom_status s = make_bf16_map(p->map_pr, p->Pb_r, (uint64_t)F * p->Zp, (uint64_t)Spad, fp16);
+        acom_status s = make_bf16_map(p->map_pr, p->Pb_r, (uint64_t)F * p->Zp, (uint64_t)Spad, kind);
         if (s == ACOM_OK)
-            s = make_bf16_map(p->map_pi, p->Pb_i, (uint64_t)F * p->Zp, (uint64_t)Spad, fp16);
+            s = make_bf16_map(p->map_pi, p->Pb_i, (uint64_t)F * p->Zp, (uint64_t)Spad, kind);
         if (s != ACOM_OK) {
             cudaStreamSynchronize(st);
             destroy_plan(p);
@@ -684,8 +695,25 @@ static float kappa_fp16(const acom_plan_s* p) {
                    (3.0 * (p->Spad + 2) + 2.0 * p->F) * std::ldexp(1.0, -21));
 }
 
+// E4M3 operands: relative rounding 2^-4 per operand, 2^-3 per product and
+// 2^-2 for the complex spectrum; values below the normal range are charged
+// by the select kernel's absolute term (eta 2^-6)
+static float kappa_fp8(const acom_plan_s* p) {
+    return (float)(std::ldexp(1.0, -2) +
+                   (3.0 * (p->Spad + 2) + 2.0 * p->F) * std::ldexp(1.0, -21));
+}
+
 static float kappa_tc(const acom_plan_s* p) {
-    return p->precision == ACOM_PREC_FP16 ? kappa_fp16(p) : kappa_bf16(p);
+    return p->precision == ACOM_PREC_FP8    ? kappa_fp8(p)
+           : p->precision == ACOM_PREC_FP16 ? kappa_fp16(p)
+                                            : kappa_bf16(p);
+}
+
+// the FP16 raster rows of a chunk into the E4M3 operand (FP8 plans)
+static void convert_fp8(acom_plan_s* p, cudaStream_t st) {
+    if (p->precision != ACOM_PREC_FP8) return;
+    const int64_t n = (int64_t)p->F * p->ws.PTs * 128 * p->Spad;
+    launch_half_to_e4m3(p->ws.XB, p->ws.XB8, n, kFp8Shift, st);
 }
 
 acom_status acom_match(acom_plan p, const acom_peaks_csr* peaks, const acom_match_opts* opts,
@@ -700,6 +728,8 @@ acom_status acom_match(acom_plan p, const acom_peaks_csr* peaks, const acom_matc
     if (B == 0) return ACOM_OK;
     const int refine = opts ? opts->refine : 1;
     const bool exhaustive = opts && opts->exhaustive;
+    const int rescore_top = opts && !exhaustive ? opts->rescore_top : 0;
+    if (rescore_top < 0) return set_error(ACOM_ERR_INVALID_ARG, "rescore_top must be >= 0");
     if (exhaustive && (out->runner_za || out->runner_score || out->runner_orient))
         return set_error(ACOM_ERR_UNSUPPORTED, "runner-up outputs need certified pruning");
     if (!exhaustive && p->Z > 16384)
@@ -721,7 +751,7 @@ acom_status acom_match(acom_plan p, const acom_peaks_csr* peaks, const acom_matc
     for (int64_t c0 = 0; c0 < B; c0 += chunk) {
         const int nb = (int)std::min<int64_t>(chunk, B - c0);
         const bool tc = !exhaustive && tc_precision(p->precision);
-        float* xscale = tc && p->precision == ACOM_PREC_FP16 ? p->ws.xscale : nullptr;
+        float* xscale = tc && p->precision != ACOM_PREC_BF16 ? p->ws.xscale : nullptr;
         PatternSource src{tc ? p->ws.XB : nullptr, p->ws.PTs, peaks->row_ptr + c0, peaks->qx,
                           peaks->qy, peaks->I, nb, (float)p->gamma_pow, (float)p->omega,
                           xscale ? 1 : 0, xscale};
@@ -746,13 +776,15 @@ acom_status acom_match(acom_plan p, const acom_peaks_csr* peaks, const acom_matc
             if (out->phase || out->phase_score)
                 launch_phase_outputs(p, p->ws.za_scores, nb, *out, c0, st);
         } else {
-            if (tc)
+            if (tc) {
+                convert_fp8(p, st);
                 launch_contract_bound_tc(p, p->ws.map_x, p->ws.PTs, nb, p->ws.U, st, xscale);
-            else
+            } else {
                 launch_contract_bound_fp32(p, p->ws.Xr, p->ws.Xi, nb, p->ws.U, st);
+            }
             launch_select_exact(p, p->ws.Xsr, p->ws.Xsi, p->ws.U, p->ws.xfn, p->ws.srange, p->pfmax,
                                 p->ws.xnorm2, nb, tc ? kappa_tc(p) : kappa_fp32(p), refine,
-                                *out, c0, p->ws.n_eval, st, xscale);
+                                *out, c0, p->ws.n_eval, st, xscale, rescore_top);
         }
     }
     cudaError_t e = cudaGetLastError();
@@ -783,7 +815,7 @@ acom_status acom_bounds(acom_plan p, const acom_peaks_csr* peaks, float* dst, vo
     RasterGeom geo{p->S, p->Spad, p->N, p->F, (float)p->dq, (float)p->delta, (float)p->gamma_pow, 0};
     for (int64_t c0 = 0; c0 < B; c0 += chunk) {
         const int nb = (int)std::min<int64_t>(chunk, B - c0);
-        float* xscale = tc && p->precision == ACOM_PREC_FP16 ? p->ws.xscale : nullptr;
+        float* xscale = tc && p->precision != ACOM_PREC_BF16 ? p->ws.xscale : nullptr;
         PatternSource src{tc ? p->ws.XB : nullptr, p->ws.PTs, peaks->row_ptr + c0, peaks->qx,
                           peaks->qy, peaks->I, nb, (float)p->gamma_pow, (float)p->omega,
                           xscale ? 1 : 0, xscale};
@@ -793,10 +825,12 @@ acom_status acom_bounds(acom_plan p, const acom_peaks_csr* peaks, float* dst, vo
         ro.sumsq = p->ws.xnorm2;
         launch_raster_patterns(geo, src, ro, p->err, st);
         float* U = dst + c0 * (int64_t)p->Z;
-        if (tc)
+        if (tc) {
+            convert_fp8(p, st);
             launch_contract_bound_tc(p, p->ws.map_x, p->ws.PTs, nb, U, st, xscale);
-        else
+        } else {
             launch_contract_bound_fp32(p, p->ws.Xr, p->ws.Xi, nb, U, st);
+        }
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "bounds launch");

@@ -322,7 +322,10 @@ struct SelectArgs {
     int64_t off;
     int* n_eval;                      // optional: total axes evaluated
     const float* xscale;              // [nb] 2^e of FP16 pattern spectra, or nullptr
-    float inv_pscale;                 // 2^-k of FP16 plan spectra
+    float inv_pscale;                 // 2^-k of the plan operand's scale
+    float xs_mul;                     // the pattern operand holds xscale * xs_mul times X^
+    float eta;                        // absolute error of an operand below its normal range
+    int rescore_top;                  // > 0: evaluate only the top axes by bound (no certificate)
 };
 
 // Spectra c_dir + i c_mir of the batch's candidate axes, scaled by 1/N, into
@@ -665,8 +668,8 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_select_exact(SelectArgs a) {
         // + Spad eta^2, i.e. after dividing by 2^(e+k)
         //   eta sqrt(Spad) (||X^_bf|| 2^-k + ||P^_zf|| 2^-e + sqrt(Spad) eta 2^-(e+k)),
         // charged four times for the four real products of c_f
-        const float inv_sc = a.xscale ? 1.0f / a.xscale[b] : 0.f;
-        const float tiny = (float)(kFp16Eta * sqrt((double)a.Spad)) * inv_sc * a.inv_pscale;
+        const float inv_sc = a.xscale ? 1.0f / (a.xscale[b] * a.xs_mul) : 0.f;
+        const float tiny = (float)((double)a.eta * sqrt((double)a.Spad)) * inv_sc * a.inv_pscale;
         float e = 0.f, ea = 0.f;
         for (int f = threadIdx.x; f < F; f += kSelThreads) {
             const float w = (f == 0 || 2 * f == N) ? 1.f : 2.f;
@@ -690,7 +693,7 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_select_exact(SelectArgs a) {
             }
             SelState& st = *sm.st;
             const float abs_term =
-                a.xscale ? (float)(4.0 * kFp16Eta * sqrt((double)a.Spad)) * ta : 0.f;
+                a.xscale ? (float)(4.0 * (double)a.eta * sqrt((double)a.Spad)) * ta : 0.f;
             st.Emax = (a.kappa * t + abs_term) / (float)N * 1.01f;
             st.T = -CUDART_INF_F;
             st.Tidx = 0xffffffffu;
@@ -705,8 +708,13 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_select_exact(SelectArgs a) {
         // batches in decreasing bound: the first takes the 4 largest bounds, later
         // ones every axis whose bound can still reach the best exact score
         for (int batch = 0;; ++batch) {
-            const float thr = batch == 0 ? -CUDART_INF_F : sm.st->T;
-            block_topk(sm, Z, batch == 0 ? 4 : kBatch, thr, rel, Emax, per_phase && batch > 0,
+            // rescore_top: the top axes by bound only, taken kBatch at a time
+            const int left = a.rescore_top - evals;
+            if (a.rescore_top > 0 && left <= 0) break;
+            const float thr = (batch == 0 || a.rescore_top > 0) ? -CUDART_INF_F : sm.st->T;
+            const int K = a.rescore_top > 0 ? (left < kBatch ? left : kBatch)
+                                            : (batch == 0 ? 4 : kBatch);
+            block_topk(sm, Z, K, thr, rel, Emax, per_phase && batch > 0 && a.rescore_top == 0,
                        nph);
             const int nc = sm.st->nc;
             if (nc == 0) break;
@@ -835,11 +843,13 @@ void launch_select_exact(const acom_plan_s* p, const float* Xsr, const float* Xs
                          const float* xfn, const int2* srange, const float* pfmax,
                          const float* xnorm2, int nb,
                          float kappa, int refine, acom_result out, int64_t off, int* n_eval,
-                         cudaStream_t st, const float* xscale) {
+                         cudaStream_t st, const float* xscale, int rescore_top) {
     SelectArgs a{p->Psr, p->Psi, Xsr, Xsi, U, xfn, srange, pfmax, xnorm2, p->za, p->frames,
                  p->nbr_ptr,
                  p->nbr_idx, p->phase_off, p->n_phases, p->Z, p->F, p->N, p->S, p->Spad, nb, refine, kappa,
-                 fft_radices(p->N), out, off, n_eval, xscale, 1.0f / p->pscale};
+                 fft_radices(p->N), out, off, n_eval, xscale, 1.0f / p->pscale,
+                 p->precision == ACOM_PREC_FP8 ? kFp8Shift : 1.0f,
+                 (float)(p->precision == ACOM_PREC_FP8 ? kFp8Eta : kFp16Eta), rescore_top};
     const size_t smem = select_smem_bytes(p->Z, p->N, p->F);
     cudaFuncSetAttribute(k_select_exact, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int dev = 0, nsm = 0, per_sm = 0;

@@ -38,6 +38,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <cudaTypedefs.h>
 #include <math_constants.h>
 
@@ -48,7 +49,8 @@ namespace tc {
 
 constexpr int kM = 128;               // zone axes per tile (MMA N = 256 rows: re, im)
 constexpr int kNP = 64;               // patterns per tile (MMA M = 128 rows: re, im)
-constexpr int kKT = 64;               // BF16 per K tile row (128 bytes)
+constexpr int kKT = 64;               // 16-bit operands per K tile row (128 bytes)
+constexpr int kKT8 = 128;             // 8-bit operands per K tile row (128 bytes)
 constexpr int kStages = 4;
 constexpr int kTileBytes = 128 * kKT * 2;      // 16 KB
 constexpr int kStageBytes = 3 * kTileBytes;    // X, then Pr and Pi as one 256-row operand
@@ -136,6 +138,20 @@ __device__ __forceinline__ void mma_f16kind(uint32_t tmem_d, uint64_t adesc, uin
         ".reg .pred p;\n"
         "setp.ne.b32 p, %4, 0;\n"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+        "}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// E4M3 x E4M3 -> FP32 (both operands the same type; K = 32 per instruction,
+// the same 32 bytes of each operand row as K = 16 of a 16-bit type)
+__device__ __forceinline__ void mma_f8kind(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                           uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n"
         "}\n" ::"r"(tmem_d),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
@@ -230,9 +246,14 @@ struct TcArgs {
     int* err;
     uint32_t idesc;                // MMA instruction descriptor (operand format)
     const float* xscale;           // [nb] 2^e of FP16 pattern spectra, or nullptr
-    float inv_pscale;              // 2^-k of FP16 plan spectra (1 for BF16)
+    float xs_mul;                  // the operands hold xscale * xs_mul times X^
+    float inv_pscale;              // 2^-k of the plan operand's scale (1 for BF16)
 };
 
+// F8: E4M3 operands (kind::f8f6f4, 128 elements per K tile), else 16-bit
+// (kind::f16, 64 elements per K tile); a template parameter, so the MMA issue
+// loop carries no branch on it
+template <bool F8>
 __global__ void __launch_bounds__(kThreads, 1)
 k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
                     const __grid_constant__ CUtensorMap map_pi,
@@ -304,9 +325,11 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
                         const uint32_t fb = smem_u32(full + own * kStages + stage);
                         mbar_expect_tx(fb, kStageBytes);
                         unsigned char* sbuf = ring + stage * kStageBytes;
-                        tma_load_2d(smem_u32(sbuf), &map_x, kt * kKT, xrow, fb);
-                        tma_load_2d(smem_u32(sbuf + kTileBytes), &map_pr, kt * kKT, prow, fb);
-                        tma_load_2d(smem_u32(sbuf + 2 * kTileBytes), &map_pi, kt * kKT, prow, fb);
+                        constexpr int ktel = F8 ? kKT8 : kKT;
+                        tma_load_2d(smem_u32(sbuf), &map_x, kt * ktel, xrow, fb);
+                        tma_load_2d(smem_u32(sbuf + kTileBytes), &map_pr, kt * ktel, prow, fb);
+                        tma_load_2d(smem_u32(sbuf + 2 * kTileBytes), &map_pi, kt * ktel, prow,
+                                    fb);
                         issued_mask |= 1u << stage;
                         const uint32_t par = (fpar[own] >> stage) & 1u;
                         last_par = (last_par & ~(1u << stage)) | (par << stage);
@@ -368,16 +391,23 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
                         fpar ^= 1u << stage;
                         fence_after();
                         const uint32_t sb = smem_u32(ring + stage * kStageBytes);
-                        // K steps of 16 inside the shells (the tail of the last
-                        // tile is TMA zero fill); a step of 16 BF16 moves the
-                        // descriptors' start address by 32 bytes (2 units of 16)
-                        const int nk16 = min(kKT, a.Spad - kt * kKT) >> 4;
+                        // K steps of 32 bytes inside the shells (16 16-bit or 32
+                        // 8-bit elements; the tail of the last tile is TMA zero
+                        // fill); a step moves the descriptors' start address by
+                        // 32 bytes (2 units of 16)
+                        constexpr int ktel = F8 ? kKT8 : kKT;
+                        const int nk = (min(ktel, a.Spad - kt * ktel) * (F8 ? 1 : 2)) >> 5;
                         const uint64_t xa = sdesc(sb), pb = sdesc(sb + kTileBytes);
 #pragma unroll
-                        for (int k16 = 0; k16 < kKT / 16; ++k16)
-                            if (k16 < nk16)
-                                mma_f16kind(dacc, xa + 2 * k16, pb + 2 * k16, a.idesc,
-                                            (kt | k16) ? 1u : 0u);
+                        for (int k4 = 0; k4 < 4; ++k4)
+                            if (k4 < nk) {
+                                if constexpr (F8)
+                                    mma_f8kind(dacc, xa + 2 * k4, pb + 2 * k4, a.idesc,
+                                               (kt | k4) ? 1u : 0u);
+                                else
+                                    mma_f16kind(dacc, xa + 2 * k4, pb + 2 * k4, a.idesc,
+                                                (kt | k4) ? 1u : 0u);
+                            }
                         mma_commit(smem_u32(empty + stage));       // frees the stage
                         if (++stage == kStages) stage = 0;
                     }
@@ -442,8 +472,9 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
             for (int h = 0; h < 2; ++h) {
                 const int b = pt * kNP + 8 * (2 * q + h) + (lane >> 2);
                 // FP16 spectra carry power-of-two scales: divide them out
-                const float sc =
-                    (a.xscale && b < a.nb) ? invN * a.inv_pscale / a.xscale[b] : invN;
+                const float sc = (a.xscale && b < a.nb)
+                                     ? invN * a.inv_pscale / (a.xscale[b] * a.xs_mul)
+                                     : invN * a.inv_pscale;
 #pragma unroll
                 for (int n = 0; n < 4; ++n)
 #pragma unroll
@@ -490,21 +521,25 @@ static bool get_encoder() {
     return true;
 }
 
-// 2-D BF16 (or FP16) map: rows x cols (cols contiguous), boxes of 64 cols x
-// 128 rows, 128-byte swizzle; boxes reaching past the last column are
-// zero-filled.
+// 2-D operand map: rows x cols (cols contiguous), boxes of 128 bytes x 128
+// rows (64 16-bit or 128 8-bit columns), 128-byte swizzle; boxes reaching
+// past the last column are zero-filled.  kind: 0 BF16, 1 FP16, 2 E4M3 (as
+// bytes).
 acom_status make_bf16_map(void* map_storage, const void* base, uint64_t rows, uint64_t cols,
-                          bool fp16) {
+                          int kind) {
     if (!get_encoder()) return set_error(ACOM_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
-    if ((cols * 2) % 16 != 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0)
+    const uint64_t eb = kind == 2 ? 1 : 2;
+    if ((cols * eb) % 16 != 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0)
         return set_error(ACOM_ERR_INVALID_ARG, "tensor map: stride or base not 16-byte aligned");
     CUtensorMap* m = reinterpret_cast<CUtensorMap*>(map_storage);
     const cuuint64_t dims[2] = {cols, rows};
-    const cuuint64_t strides[1] = {cols * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)tc::kKT, 128};
+    const cuuint64_t strides[1] = {cols * eb};
+    const cuuint32_t box[2] = {(cuuint32_t)(kind == 2 ? tc::kKT8 : tc::kKT), 128};
     const cuuint32_t estr[2] = {1, 1};
-    CUresult r = g_encode(m, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
-                          2, const_cast<void*>(base), dims,
+    const CUtensorMapDataType dt = kind == 2   ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                   : kind == 1 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                               : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    CUresult r = g_encode(m, dt, 2, const_cast<void*>(base), dims,
                           strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -524,17 +559,21 @@ void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_st
     a.ZT = p->Zp / tc::kM;
     a.PT = (nb + tc::kNP - 1) / tc::kNP;
     a.PTs = pt_stride;
-    a.KT = (p->Spad + tc::kKT - 1) / tc::kKT;
+    const bool f8 = p->precision == ACOM_PREC_FP8;
+    const int ktel = f8 ? tc::kKT8 : tc::kKT;
+    a.KT = (p->Spad + ktel - 1) / ktel;
     a.Spad = p->Spad;
     a.Zrows = p->Zp;
     a.U = U;
     a.err = p->err;
-    a.idesc = p->precision == ACOM_PREC_FP16 ? tc::kIdescF16 : tc::kIdescBF16;
+    // E4M3 is format 0 for A and B, the same bits as F16
+    a.idesc = p->precision == ACOM_PREC_BF16 ? tc::kIdescBF16 : tc::kIdescF16;
     a.xscale = xscale;
+    a.xs_mul = f8 ? kFp8Shift : 1.0f;
     a.inv_pscale = 1.0f / p->pscale;
     const size_t smem = tc::tc_smem_bytes();
-    cudaFuncSetAttribute(tc::k_contract_bound_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
+    auto kern = f8 ? tc::k_contract_bound_tc<true> : tc::k_contract_bound_tc<false>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -542,7 +581,7 @@ void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_st
     const int grid = n_tiles < nsm ? n_tiles : nsm;
     if (grid <= 0) return;
     prof_begin(kKContractBf16, st);
-    tc::k_contract_bound_tc<<<grid, tc::kThreads, smem, st>>>(
+    kern<<<grid, tc::kThreads, smem, st>>>(
         *reinterpret_cast<const CUtensorMap*>(p->map_pr),
         *reinterpret_cast<const CUtensorMap*>(p->map_pi),
         *reinterpret_cast<const CUtensorMap*>(map_x), a);
@@ -561,6 +600,10 @@ template <>
 __device__ __forceinline__ __half to_half_type<__half>(float x) {
     return __float2half_rn(x);
 }
+template <>
+__device__ __forceinline__ __nv_fp8_e4m3 to_half_type<__nv_fp8_e4m3>(float x) {
+    return __nv_fp8_e4m3(x);           // round to nearest, saturating to +-448
+}
 
 template <class T>
 __global__ void k_plan_to_bf16(const float* __restrict__ src, int Zp, int F, int Spad,
@@ -577,16 +620,48 @@ __global__ void k_plan_to_bf16(const float* __restrict__ src, int Zp, int F, int
 }
 
 void launch_plan_to_bf16(const float* src, int Zp, int F, int Spad, void* dst, cudaStream_t st,
-                         bool fp16, float scale) {
+                         int kind, float scale) {
     const int64_t total = (int64_t)Zp * F * Spad;
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
     prof_begin(kKMisc, st);
-    if (fp16)
+    if (kind == 2)
+        k_plan_to_bf16<__nv_fp8_e4m3><<<blocks, 256, 0, st>>>(
+            src, Zp, F, Spad, reinterpret_cast<__nv_fp8_e4m3*>(dst), scale);
+    else if (kind == 1)
         k_plan_to_bf16<__half><<<blocks, 256, 0, st>>>(src, Zp, F, Spad,
                                                         reinterpret_cast<__half*>(dst), scale);
     else
         k_plan_to_bf16<__nv_bfloat16><<<blocks, 256, 0, st>>>(
             src, Zp, F, Spad, reinterpret_cast<__nv_bfloat16*>(dst), 1.0f);
+    prof_end(kKMisc, st);
+}
+
+// FP16 operand rows -> E4M3 rows times mul (a power of two, exact), 8 per thread.
+__global__ void k_half_to_e4m3(const __half* __restrict__ src, uint8_t* __restrict__ dst,
+                               int64_t n8, float mul) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n8;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 v = reinterpret_cast<const uint4*>(src)[i];
+        const __half2* h = reinterpret_cast<const __half2*>(&v);
+        uint16_t o[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float2 f = __half22float2(h[j]);
+            f.x *= mul;
+            f.y *= mul;
+            o[j] = (uint16_t)__nv_cvt_float2_to_fp8x2(f, __NV_SATFINITE, __NV_E4M3);
+        }
+        reinterpret_cast<uint2*>(dst)[i] = *reinterpret_cast<const uint2*>(o);
+    }
+}
+
+void launch_half_to_e4m3(const void* src, void* dst, int64_t n, float mul, cudaStream_t st) {
+    const int64_t n8 = n / 8;
+    if (n8 <= 0) return;
+    const int blocks = (int)std::min<int64_t>((n8 + 255) / 256, 152 * 32);
+    prof_begin(kKMisc, st);
+    k_half_to_e4m3<<<blocks, 256, 0, st>>>(reinterpret_cast<const __half*>(src),
+                                            reinterpret_cast<uint8_t*>(dst), n8, mul);
     prof_end(kKMisc, st);
 }
 

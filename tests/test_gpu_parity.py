@@ -385,3 +385,58 @@ def test_full_size_tc_equals_fp32(full_scan, precision):
     assert ev < 40
     p32.close()
     p16.close()
+
+
+# ------------------------------------------------ E4M3 operands (experiment)
+
+def test_fp8_bounds_track_fp32():
+    """E4M3 operands (FP16 operands times 2^-6) on kind::f8f6f4: bounds within
+    their 2^-4-per-operand rounding of the FP32 bounds."""
+    p32 = gpu_plan("au_2deg_75x180")
+    p8 = gpu_plan("au_2deg_75x180", precision=3)
+    scan = synth.random_patterns(1001, n_patterns=100)
+    u32 = p32.bounds(*to_dev(scan)).cpu().numpy()
+    u8 = p8.bounds(*to_dev(scan)).cpu().numpy()
+    rel = np.abs(u8 - u32) / np.maximum(np.abs(u32), 1e-30)
+    print(f"fp8 bound rel err: max {rel.max():.3e} mean {rel.mean():.3e}")
+    assert np.all(np.isfinite(u8))
+    assert rel.max() < 2.0 ** -2 and rel.mean() < 2.0 ** -5
+    p32.close()
+    p8.close()
+
+
+def test_fp8_certified_and_rescored_winners():
+    """Certified pruning on E4M3 bounds still returns the FP32 winners (with
+    many more exact evaluations); rescoring only the top 8 bounds is an
+    uncertified experiment whose agreement is reported."""
+    import torch
+    p32 = gpu_plan("au_2deg_75x180")
+    p8 = gpu_plan("au_2deg_75x180", precision=3)
+    scan = synth.random_patterns(1001, n_patterns=100)
+    a = p32.match(*to_dev(scan))
+    torch.cuda.synchronize()
+    ev32 = p32.get_info()["last_evaluated"]
+    b = p8.match(*to_dev(scan))
+    torch.cuda.synchronize()
+    ev8 = p8.get_info()["last_evaluated"]
+    c = p8.match(*to_dev(scan), rescore_top=8)
+    torch.cuda.synchronize()
+    keys = ("za_idx", "phi3_bin", "mirror")
+    ka = np.stack([a[k].cpu().numpy().astype(np.int64) for k in keys], 1)
+    kb = np.stack([b[k].cpu().numpy().astype(np.int64) for k in keys], 1)
+    kc = np.stack([c[k].cpu().numpy().astype(np.int64) for k in keys], 1)
+    op = oracle_plan("au_2deg_75x180")
+    for i in np.nonzero(np.any(ka != kb, axis=1))[0]:
+        mt = O.match_pattern(op, *scan.pattern(i))
+        assert check_argmax(mt, *ka[i]) and check_argmax(mt, *kb[i]), i
+    agree = 0
+    for i in range(scan.n_patterns):
+        if np.array_equal(kc[i], ka[i]):
+            agree += 1
+        else:
+            agree += check_argmax(O.match_pattern(op, *scan.pattern(i)), *kc[i])
+    print(f"fp8 certified: {ev8 / 100:.1f} axes evaluated per pattern (fp32 bound {ev32 / 100:.1f});"
+          f" top-8 rescoring agrees on {agree}/100")
+    assert agree >= 80
+    p32.close()
+    p8.close()
