@@ -286,6 +286,22 @@ acom_status acom_match(acom_plan plan, const acom_peaks_csr* peaks,
                        void* cuda_stream);
 
 /*
+ * acom_match_async - acom_match without its final synchronisation: the work
+ * is enqueued on ``cuda_stream`` and the call returns.  The error word and the
+ * evaluation count go to pinned memory owned by the plan; acom_sync waits for
+ * the stream and returns the status acom_match would have returned (and sets
+ * last_evaluated).  Once the plan's workspace fits (after one acom_match with
+ * the same chunk and mode) the call allocates nothing and makes no host
+ * synchronisation, so it can be captured into a CUDA graph and the graph
+ * replayed on new contents of the same peak and result buffers; under
+ * capture it records no profiling events, and it refuses
+ * (ACOM_ERR_INVALID_ARG) a workspace that would need allocating.
+ */
+acom_status acom_match_async(acom_plan plan, const acom_peaks_csr* peaks,
+                             const acom_match_opts* opts, acom_result* out, void* cuda_stream);
+acom_status acom_sync(acom_plan plan, void* cuda_stream);
+
+/*
  * acom_match_multi - several orientations per pattern (section "Matching of
  * Overlapping Diffraction Patterns"): match; compute the forward pattern of
  * the match's grid orientation (the reflections of the plan whose Gaussian

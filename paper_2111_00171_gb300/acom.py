@@ -30,7 +30,8 @@ EXPORTED = ("acom_plan_create", "acom_plan_destroy", "acom_plan_get_info",
             "acom_last_error",
             "acom_version", "acom_profile_enable", "acom_profile_reset", "acom_profile_read",
             "acom_kernel_launches", "acom_plan_concat", "acom_plan_get_phases", "acom_refine",
-            "acom_refine_defaults", "acom_kinematical_score", "acom_match_multi")
+            "acom_refine_defaults", "acom_kinematical_score", "acom_match_multi",
+            "acom_match_async", "acom_sync")
 
 
 class AcomError(RuntimeError):
@@ -119,6 +120,9 @@ def load_library():
     lib.acom_kinematical_score.argtypes = [P, C.POINTER(PeaksCSR), P, P, C.c_float, P, P, P, P]
     lib.acom_match_multi.argtypes = [P, C.POINTER(PeaksCSR), C.POINTER(MatchOpts), C.c_int32,
                                      C.c_float, C.POINTER(Result), P]
+    lib.acom_match_async.argtypes = [P, C.POINTER(PeaksCSR), C.POINTER(MatchOpts),
+                                     C.POINTER(Result), P]
+    lib.acom_sync.argtypes = [P, P]
     lib.acom_plan_get_zone_axes.argtypes = [P, P]
     lib.acom_plan_get_spectra.argtypes = [P, P, P]
     lib.acom_match.argtypes = [P, C.POINTER(PeaksCSR), C.POINTER(MatchOpts), C.POINTER(Result), P]
@@ -135,7 +139,7 @@ def load_library():
     lib.acom_version.restype = C.c_int32
     for name in ("acom_plan_create", "acom_plan_destroy", "acom_plan_get_info",
                  "acom_plan_concat", "acom_plan_get_phases", "acom_refine",
-                 "acom_kinematical_score", "acom_match_multi",
+                 "acom_kinematical_score", "acom_match_multi", "acom_match_async", "acom_sync",
                  "acom_plan_get_zone_axes", "acom_plan_get_spectra", "acom_match",
                  "acom_polar_spectra", "acom_bounds", "acom_bounds_static"):
         getattr(lib, name).restype = C.c_int
@@ -353,6 +357,22 @@ class Plan:
                                     _stream_ptr(stream)))
         return r
 
+
+    def match_async(self, row_ptr, qx, qy, I, out, refine=True, chunk=0, exhaustive=False,
+                    rescore_top=0, stream=None):
+        """acom_match_async into the result dict ``out`` (alloc_result): the
+        work is only enqueued; sync() returns its status.  Capturable into a
+        CUDA graph once a synchronous match has sized the workspace."""
+        pk = self._csr(row_ptr, qx, qy, I)
+        res = Result(*(_ptr(out.get(k)) for k, _ in Result._fields_))
+        opts = MatchOpts(1 if refine else 0, int(chunk), 1 if exhaustive else 0, int(rescore_top))
+        _check(self._lib.acom_match_async(self.handle, C.byref(pk), C.byref(opts), C.byref(res),
+                                          _stream_ptr(stream)))
+        return out
+
+    def sync(self, stream=None):
+        """acom_sync: wait for the stream; the status of the last async match."""
+        _check(self._lib.acom_sync(self.handle, _stream_ptr(stream)))
 
     def match_multi(self, row_ptr, qx, qy, I, n_matches=3, r_del=0.04, refine=True, chunk=0,
                     exhaustive=False, stream=None):

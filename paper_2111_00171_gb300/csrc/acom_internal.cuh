@@ -164,6 +164,7 @@ struct acom_plan_s {
     int* err = nullptr;               // device error word
     float* pfmax = nullptr;           // [F] max over axes of ||P^_zf|| over shells
     float pscale = 1.0f;              // 2^k of the FP16 plan spectra (1 otherwise)
+    uint32_t* smask = nullptr;        // [Zp][Spad / 32] bit s: shell row s of the axis not zero
     void* Pb_r = nullptr;             // BF16 or FP16 [F][Zp][Spad] (tensor-core operand)
     void* Pb_i = nullptr;
     alignas(64) unsigned char map_pr[128];  // TMA maps of Pb_r, Pb_i
@@ -175,6 +176,9 @@ struct acom_plan_s {
     std::vector<int> phase_off_host;  // [n_phases + 1] first axis of each phase, then Z
     int* phase_off = nullptr;         // the same on the device
     int64_t last_evaluated = 0;       // axes evaluated exactly in the last match
+    int* host_words = nullptr;        // pinned [2]: error word and evaluations of the last
+                                      // match (read by acom_sync / acom_match)
+    int64_t async_exhaustive_evals = -1;  // exhaustive: evaluations of the last match
     size_t bytes = 0;
     acom::Workspace ws;
 };
@@ -190,6 +194,29 @@ void prof_begin(int cls, cudaStream_t st);
 void prof_end(int cls, cudaStream_t st);
 void prof_resolve();
 void prof_suppress(bool on);   // this thread's launches record no events (no event creation)
+
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per kernel, device and
+// size: repeated launches make no host attribute call (stream capture).
+// Process-global, not thread-safe.
+inline void set_max_dynamic_smem(const void* func, size_t bytes) {
+    struct Done {
+        const void* f;
+        int dev;
+        size_t bytes;
+    };
+    static std::vector<Done> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    for (auto& d : done)
+        if (d.f == func && d.dev == dev) {
+            if (d.bytes >= bytes) return;
+            cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+            d.bytes = bytes;
+            return;
+        }
+    cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    done.push_back({func, dev, bytes});
+}
 
 // ---- error reporting (api.cu) ----
 acom_status set_error(acom_status s, const std::string& msg);
@@ -217,6 +244,8 @@ void launch_idft_argmax_fp32(const acom_plan_s* p, const float* Chat, int nb, in
 void launch_contract_bound_fp32(const acom_plan_s* p, const float* Xr, const float* Xi, int nb,
                                 float* U, cudaStream_t st);
 void launch_plan_fnorm_max(const acom_plan_s* p, float* out, cudaStream_t st);
+// p->smask from the plan's shell-major spectra (p->smask allocated, Zp x Spad/32)
+void launch_plan_shell_mask(const acom_plan_s* p, cudaStream_t st);
 // match_tc.cu
 acom_status make_bf16_map(void* map_storage, const void* base, uint64_t rows, uint64_t cols,
                           int kind = 0);
@@ -231,7 +260,8 @@ void launch_select_exact(const acom_plan_s* p, const float* Xsr, const float* Xs
                          const float* xfn, const int2* srange, const float* pfmax,
                          const float* xnorm2, int nb,
                          float kappa, int refine, acom_result out, int64_t off, int* n_eval,
-                         cudaStream_t st, const float* xscale = nullptr, int rescore_top = 0);
+                         cudaStream_t st, const float* xscale, int rescore_top,
+                         const acom_peaks_csr* chunk_peaks);
 // refine.cu: continuous refinement on the plan's reflections
 acom_status refine_table(acom_plan_s* p, cudaStream_t st);
 void launch_refine_orient(const acom_plan_s* p, const acom_peaks_csr* pk, int steps,

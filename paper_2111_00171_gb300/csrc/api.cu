@@ -236,6 +236,8 @@ static void destroy_plan(acom_plan_s* p) {
     pool_free(p->phase_off, st);
     pool_free(p->refl_tab, st);
     pool_free(p->refine_pairs, st);
+    pool_free(p->smask, st);
+    if (p->host_words) cudaFreeHost(p->host_words);
     delete p;
 }
 
@@ -357,6 +359,8 @@ acom_status acom_plan_create(const acom_crystal* crystal, const acom_za_grid* gr
     ACOM_CK(dalloc(&p->pfmax, (size_t)p->F, &p->bytes, st));
     p->phase_off_host = {0, Z};
     ACOM_CK(dalloc(&p->phase_off, 2, &p->bytes, st));
+    ACOM_CK(cudaMallocHost(reinterpret_cast<void**>(&p->host_words), 2 * sizeof(int)));
+    p->host_words[0] = p->host_words[1] = 0;
     ACOM_CK(cudaMemcpyAsync(p->phase_off, p->phase_off_host.data(), sizeof(int) * 2,
                             cudaMemcpyHostToDevice, st));
     ACOM_CK(cudaMemsetAsync(p->Pr, 0, sizeof(float) * pelems, st));
@@ -377,6 +381,8 @@ acom_status acom_plan_create(const acom_crystal* crystal, const acom_za_grid* gr
         return s;
     }
     launch_plan_fnorm_max(p, p->pfmax, st);
+    ACOM_CK(dalloc(&p->smask, (size_t)p->Zp * (p->Spad / 32), &p->bytes, st));
+    launch_plan_shell_mask(p, st);
     ACOM_CK(cudaGetLastError());
     if (tc_precision(p->precision)) {
         const int kind = tc_kind(p->precision);
@@ -497,6 +503,8 @@ acom_status acom_plan_concat(const acom_plan* plans, int32_t n_plans, void* cuda
     ACOM_CK(dalloc(&p->err, 1, &p->bytes, st));
     ACOM_CK(dalloc(&p->pfmax, (size_t)F, &p->bytes, st));
     ACOM_CK(dalloc(&p->phase_off, p->phase_off_host.size(), &p->bytes, st));
+    ACOM_CK(cudaMallocHost(reinterpret_cast<void**>(&p->host_words), 2 * sizeof(int)));
+    p->host_words[0] = p->host_words[1] = 0;
     ACOM_CK(cudaMemsetAsync(p->Pr, 0, sizeof(float) * pelems, st));
     ACOM_CK(cudaMemsetAsync(p->Pi, 0, sizeof(float) * pelems, st));
     ACOM_CK(cudaMemsetAsync(p->Psr, 0, sizeof(float) * selems, st));
@@ -528,6 +536,8 @@ acom_status acom_plan_concat(const acom_plan* plans, int32_t n_plans, void* cuda
         ACOM_CK(cudaMemcpyAsync(p->frames + (size_t)9 * base, q->frames, sizeof(double) * 9 * zr,
                                 cudaMemcpyDeviceToDevice, st));
     }
+    ACOM_CK(dalloc(&p->smask, (size_t)p->Zp * (Spad / 32), &p->bytes, st));
+    launch_plan_shell_mask(p, st);
     if (tc_precision(p->precision)) {
         // [F][Zp][Spad] operand tiles: per frequency, each input's Z rows at its offset
         const int kind = tc_kind(p->precision);
@@ -716,16 +726,23 @@ static void convert_fp8(acom_plan_s* p, cudaStream_t st) {
     launch_half_to_e4m3(p->ws.XB, p->ws.XB8, n, kFp8Shift, st);
 }
 
-acom_status acom_match(acom_plan p, const acom_peaks_csr* peaks, const acom_match_opts* opts,
-                       acom_result* out, void* cuda_stream) {
-    g_last_error.clear();
+// Everything acom_match does up to the read of the error word: validation,
+// workspace, launches.  With capture set (stream capture in progress) the
+// workspace must already fit and no profiling events are recorded.
+static acom_status match_enqueue(acom_plan p, const acom_peaks_csr* peaks,
+                                 const acom_match_opts* opts, acom_result* out,
+                                 cudaStream_t st, bool capture, bool* empty) {
+    *empty = false;
     if (!p || !out) return set_error(ACOM_ERR_INVALID_ARG, "null argument");
     acom_status s = check_peaks(peaks);
     if (s != ACOM_OK) return s;
     const int64_t B = peaks->n_patterns;
     if (B > 0 && (!out->za_idx || !out->phi3_bin || !out->mirror || !out->score))
         return set_error(ACOM_ERR_INVALID_ARG, "result: za_idx, phi3_bin, mirror, score required");
-    if (B == 0) return ACOM_OK;
+    if (B == 0) {
+        *empty = true;
+        return ACOM_OK;
+    }
     const int refine = opts ? opts->refine : 1;
     const bool exhaustive = opts && opts->exhaustive;
     const int rescore_top = opts && !exhaustive ? opts->rescore_top : 0;
@@ -737,8 +754,12 @@ acom_status acom_match(acom_plan p, const acom_peaks_csr* peaks, const acom_matc
     int chunk = opts && opts->chunk > 0 ? opts->chunk : (exhaustive ? 1024 : 8192);
     if (chunk > 65536) return set_error(ACOM_ERR_INVALID_ARG, "chunk must be <= 65536");
     chunk = (int)std::min<int64_t>(chunk, B);
-    cudaStream_t st = (cudaStream_t)cuda_stream;
     const bool fp32_contraction = exhaustive || p->precision == ACOM_PREC_FP32;
+    if (capture && !(p->ws.chunk >= chunk && (!exhaustive || p->ws.Chat) &&
+                     (!fp32_contraction || p->ws.Xr)))
+        return set_error(ACOM_ERR_INVALID_ARG,
+                         "match_async under stream capture: the workspace is not sized yet "
+                         "(run acom_match once with the same chunk and mode first)");
     s = ensure_workspace(p, chunk, exhaustive, fp32_contraction, st);
     if (s != ACOM_OK) return s;
     cudaMemsetAsync(p->err, 0, sizeof(int), st);
@@ -782,18 +803,68 @@ acom_status acom_match(acom_plan p, const acom_peaks_csr* peaks, const acom_matc
             } else {
                 launch_contract_bound_fp32(p, p->ws.Xr, p->ws.Xi, nb, p->ws.U, st);
             }
+            const acom_peaks_csr cp{nb, peaks->row_ptr + c0, peaks->qx, peaks->qy, peaks->I};
             launch_select_exact(p, p->ws.Xsr, p->ws.Xsi, p->ws.U, p->ws.xfn, p->ws.srange, p->pfmax,
                                 p->ws.xnorm2, nb, tc ? kappa_tc(p) : kappa_fp32(p), refine,
-                                *out, c0, p->ws.n_eval, st, xscale, rescore_top);
+                                *out, c0, p->ws.n_eval, st, xscale, rescore_top, &cp);
         }
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "match launch");
-    int nev = 0;
-    cudaMemcpyAsync(&nev, p->ws.n_eval, sizeof(int), cudaMemcpyDeviceToHost, st);
-    s = read_error_word(p, st);
-    p->last_evaluated = exhaustive ? (int64_t)B * p->Z : nev;
+    // error word and evaluations into the plan's pinned words
+    cudaMemcpyAsync(p->host_words, p->err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(p->host_words + 1, p->ws.n_eval, sizeof(int), cudaMemcpyDeviceToHost, st);
+    p->async_exhaustive_evals = exhaustive ? (int64_t)B * p->Z : -1;
+    return ACOM_OK;
+}
+
+// Status of the words the last enqueued match copied to pinned memory.
+static acom_status finish_words(acom_plan_s* p, cudaStream_t st) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_error(e, "match");
+    prof_resolve();
+    const int herr = p->host_words[0];
+    p->last_evaluated =
+        p->async_exhaustive_evals >= 0 ? p->async_exhaustive_evals : (int64_t)p->host_words[1];
+    if (herr & kErrTimeout) return set_error(ACOM_ERR_TIMEOUT, "device wait timed out");
+    if (herr & (kErrRowPtr | kErrNonFinite | kErrTooManyPeaks)) {
+        std::string m = "bad peak data:";
+        if (herr & kErrRowPtr) m += " row_ptr not starting at 0 or decreasing;";
+        if (herr & kErrNonFinite) m += " non-finite qx/qy/I;";
+        if (herr & kErrTooManyPeaks) m += " more than 1024 peaks in a pattern;";
+        return set_error(ACOM_ERR_BAD_INPUT, m);
+    }
+    return ACOM_OK;
+}
+
+acom_status acom_match(acom_plan p, const acom_peaks_csr* peaks, const acom_match_opts* opts,
+                       acom_result* out, void* cuda_stream) {
+    g_last_error.clear();
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    bool empty = false;
+    acom_status s = match_enqueue(p, peaks, opts, out, st, false, &empty);
+    if (s != ACOM_OK || empty) return s;
+    return finish_words(p, st);
+}
+
+acom_status acom_match_async(acom_plan p, const acom_peaks_csr* peaks,
+                             const acom_match_opts* opts, acom_result* out, void* cuda_stream) {
+    g_last_error.clear();
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cap);
+    const bool capture = cap != cudaStreamCaptureStatusNone;
+    prof_suppress(capture);
+    bool empty = false;
+    acom_status s = match_enqueue(p, peaks, opts, out, st, capture, &empty);
+    prof_suppress(false);
     return s;
+}
+
+acom_status acom_sync(acom_plan p, void* cuda_stream) {
+    g_last_error.clear();
+    if (!p) return set_error(ACOM_ERR_INVALID_ARG, "null plan");
+    return finish_words(p, (cudaStream_t)cuda_stream);
 }
 
 acom_status acom_bounds(acom_plan p, const acom_peaks_csr* peaks, float* dst, void* cuda_stream) {

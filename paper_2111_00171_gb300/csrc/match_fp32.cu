@@ -246,8 +246,7 @@ k_idft_argmax_fp32(const float* __restrict__ Chat, int F, int N, int Z, int Zp, 
 void launch_idft_argmax_fp32(const acom_plan_s* p, const float* Chat, int nb, int chunk,
                              float* za_scores, unsigned long long* best, cudaStream_t st) {
     size_t smem = sizeof(float) * (4 * p->F * kIdPairs + 2 * p->N);
-    cudaFuncSetAttribute(k_idft_argmax_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
+    set_max_dynamic_smem((const void*)k_idft_argmax_fp32, smem);
     dim3 grid(p->Zp / kIdPairs, nb);
     prof_begin(kKIdft, st);
     k_idft_argmax_fp32<<<grid, 256, smem, st>>>(Chat, p->F, p->N, p->Z, p->Zp, chunk, za_scores,

@@ -148,6 +148,31 @@ __global__ void k_plan_fnorm_max(const float* __restrict__ Pr, const float* __re
     if (threadIdx.x == 0) out[f] = red[0] * 1.0001f;   // rounding of the norm itself
 }
 
+// bit s of word [z][s / 32]: shell row s of axis z (re or im) has a non-zero
+// entry; one warp per row
+__global__ void k_plan_shell_mask(const float* __restrict__ Pr, const float* __restrict__ Pi,
+                                  int64_t rows, int Spad, int Fs, uint32_t* __restrict__ mask) {
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= rows) return;
+    bool nz = false;
+    for (int f = lane; f < Fs; f += 32) nz |= Pr[row * Fs + f] != 0.f || Pi[row * Fs + f] != 0.f;
+    if (__any_sync(0xffffffffu, nz) && lane == 0) {
+        const int64_t z = row / Spad;
+        const int s = (int)(row - z * Spad);
+        atomicOr(mask + z * (Spad >> 5) + (s >> 5), 1u << (s & 31));
+    }
+}
+
+void launch_plan_shell_mask(const acom_plan_s* p, cudaStream_t st) {
+    const int64_t rows = (int64_t)p->Zp * p->Spad;
+    cudaMemsetAsync(p->smask, 0, sizeof(uint32_t) * (size_t)p->Zp * (p->Spad / 32), st);
+    prof_begin(kKMisc, st);
+    k_plan_shell_mask<<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(
+        p->Psr, p->Psi, rows, p->Spad, shell_row_stride(p->F), p->smask);
+    prof_end(kKMisc, st);
+}
+
 void launch_plan_fnorm_max(const acom_plan_s* p, float* out, cudaStream_t st) {
     prof_begin(kKMisc, st);
     k_plan_fnorm_max<<<p->F, 256, 0, st>>>(p->Pr, p->Pi, p->Z, p->F, p->Spad, out);
@@ -201,6 +226,11 @@ struct SelSmem {
     float* res;      // [kBatch][5] best value, its index bits, values at k - 1, k, k + 1
     float* red;      // [2][kSelWarps]
     int* poff;       // [kMaxPhases + 1] first axis of each phase, then Z
+    uint32_t* pmask; // [Spad / 32] shells the pattern's peaks reach (a superset of its
+                     // non-zero rows)
+    uint16_t* slist; // [kBatch][Spad] shells of each candidate: pattern and plan rows both
+                     // not zero
+    int* slen;       // [kBatch]
     SelState* st;
 };
 
@@ -326,6 +356,10 @@ struct SelectArgs {
     float xs_mul;                     // the pattern operand holds xscale * xs_mul times X^
     float eta;                        // absolute error of an operand below its normal range
     int rescore_top;                  // > 0: evaluate only the top axes by bound (no certificate)
+    const uint32_t* smask;            // [Zp][Spad / 32] non-zero plan shells
+    const int64_t* row_ptr;           // the chunk's peaks (row_ptr offset to the chunk)
+    const float *qx, *qy;
+    float dq, delta;                  // shells q_s = (s + 1) dq, tent size
 };
 
 // Spectra c_dir + i c_mir of the batch's candidate axes, scaled by 1/N, into
@@ -339,22 +373,51 @@ __device__ void batch_spectra(const SelectArgs& a, int64_t b, int nc, int s_lo, 
     h = h < 1 ? 1 : (h > 8 ? 8 : h);
     if (h > len) h = len > 1 ? len : 1;
     const int total = items * h;
+    // each candidate's shells: rows of both the pattern and the axis not zero
+    // (a product with a zero row is exactly 0 and is skipped); warp c lists
+    // candidate c in increasing shell order
+    {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, MW = a.Spad >> 5;
+        for (int c = warp; c < nc; c += kSelWarps) {
+            const uint32_t* pm = a.smask + (int64_t)sm.cand[c] * MW;
+            const uint32_t m = lane < MW ? (sm.pmask[lane] & pm[lane]) : 0u;
+            const int cnt = __popc(m);
+            int off = cnt;                              // inclusive scan over the lanes
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, off, o);
+                if (lane >= o) off += v;
+            }
+            const int tot = __shfl_sync(0xffffffffu, off, 31);
+            off -= cnt;
+            uint16_t* L = sm.slist + c * a.Spad;
+            uint32_t mm = m;
+            while (mm) {
+                const int bit = __ffs(mm) - 1;
+                mm &= mm - 1;
+                L[off++] = (uint16_t)(32 * lane + bit);
+            }
+            if (lane == 0) sm.slen[c] = tot;
+        }
+        __syncthreads();
+    }
     const int64_t blk = (int64_t)a.Spad * Fq;       // float4 per pattern or axis
     const float4* xr0 = reinterpret_cast<const float4*>(a.Xsr) + b * blk;
     const float4* xi0 = reinterpret_cast<const float4*>(a.Xsi) + b * blk;
     for (int idx = threadIdx.x; idx < total; idx += kSelThreads) {
         const int hh = idx / items, rem = idx - hh * items;
         const int c = rem / Fq, fq = rem - c * Fq;
-        const int sa = s_lo + (len * hh) / h, se = s_lo + (len * (hh + 1)) / h;
+        const uint16_t* L = sm.slist + c * a.Spad;
+        const int ln = sm.slen[c];
+        const int sa = (ln * hh) / h, se = (ln * (hh + 1)) / h;   // positions in the list
         const int64_t pb = (int64_t)sm.cand[c] * blk + fq;
         const float4* pr = reinterpret_cast<const float4*>(a.Psr) + pb;
         const float4* pi = reinterpret_cast<const float4*>(a.Psi) + pb;
         const float4* xr = xr0 + fq;
         const float4* xi = xi0 + fq;
         float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = A, C = A, D = A;
-        int s = sa;
-        for (; s + 1 < se; s += 2) {
-            const int o0 = s * Fq, o1 = o0 + Fq;
+        int i = sa;
+        for (; i + 1 < se; i += 2) {
+            const int o0 = L[i] * Fq, o1 = L[i + 1] * Fq;
             const float4 x1a = __ldg(xr + o0), x2a = __ldg(xi + o0);
             const float4 x1b = __ldg(xr + o1), x2b = __ldg(xi + o1);
             const float4 p1a = __ldg(pr + o0), p2a = __ldg(pi + o0);
@@ -368,8 +431,8 @@ __device__ void batch_spectra(const SelectArgs& a, int64_t b, int nc, int s_lo, 
             fma4(C, p1b, x2b);
             fma4(D, p2b, x1b);
         }
-        if (s < se) {
-            const int o0 = s * Fq;
+        if (i < se) {
+            const int o0 = L[i] * Fq;
             const float4 x1 = __ldg(xr + o0), x2 = __ldg(xi + o0);
             const float4 p1 = __ldg(pr + o0), p2 = __ldg(pi + o0);
             fma4(A, p1, x1);
@@ -639,6 +702,9 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_select_exact(SelectArgs a) {
     sm.res = reinterpret_cast<float*>(take(sizeof(float) * 5 * kBatch));
     sm.red = reinterpret_cast<float*>(take(sizeof(float) * 2 * kSelWarps));
     sm.poff = reinterpret_cast<int*>(take(sizeof(int) * (kMaxPhases + 1)));
+    sm.pmask = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (a.Spad >> 5)));
+    sm.slist = reinterpret_cast<uint16_t*>(take(sizeof(uint16_t) * kBatch * a.Spad));
+    sm.slen = reinterpret_cast<int*>(take(sizeof(int) * kBatch));
     sm.st = reinterpret_cast<SelState*>(take(sizeof(SelState)));
     sm.ev = take(Z);
     sm.kb = reinterpret_cast<uint16_t*>(take(sizeof(uint16_t) * Z));
@@ -660,6 +726,23 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_select_exact(SelectArgs a) {
         for (int z = threadIdx.x; z < Z; z += kSelThreads) {
             sm.U[z] = a.U[b * Z + z];
             sm.ev[z] = 0;
+        }
+        // shells within the tent of some peak (|r_m - q_s| < delta), widened
+        // by one shell on each side against rounding: every row the raster can
+        // have made non-zero
+        for (int w = threadIdx.x; w < (a.Spad >> 5); w += kSelThreads) sm.pmask[w] = 0u;
+        __syncthreads();
+        {
+            const int64_t p0 = a.row_ptr[b], p1 = a.row_ptr[b + 1];
+            for (int64_t m = p0 + threadIdx.x; m < p1; m += kSelThreads) {
+                const float r = sqrtf(a.qx[m] * a.qx[m] + a.qy[m] * a.qy[m]);
+                if (!(r < 1e30f)) continue;
+                int lo = (int)floorf((r - a.delta) / a.dq) - 2;
+                int hi = (int)ceilf((r + a.delta) / a.dq);
+                lo = lo < 0 ? 0 : lo;
+                hi = hi > a.S - 1 ? a.S - 1 : hi;
+                for (int s = lo; s <= hi; ++s) atomicOr(&sm.pmask[s >> 5], 1u << (s & 31));
+            }
         }
         // E_b: rounding margin valid for every axis.  FP16 operands add an
         // absolute term for values below the normal range: an operand x is off
@@ -829,13 +912,15 @@ void launch_phase_outputs(const acom_plan_s* p, const float* za_scores, int nb, 
     prof_end(kKMisc, st);
 }
 
-size_t select_smem_bytes(int Z, int N, int F) {
+size_t select_smem_bytes(int Z, int N, int F, int Spad) {
     auto r16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
     const size_t pb = sizeof(float4) * 4 * sel_items(F), yb = sizeof(float2) * kBatch * (size_t)N;
     return r16(sizeof(float2) * N) + r16(sizeof(float2) * kBatch * (size_t)N) + r16(pb > yb ? pb : yb) +
            r16(sizeof(float) * Z) + 2 * r16(sizeof(float) * kSelWarps * kBatch) +
            r16(sizeof(int) * kBatch) + r16(sizeof(float) * 5 * kBatch) +
            r16(sizeof(float) * 2 * kSelWarps) + r16(sizeof(int) * (kMaxPhases + 1)) +
+           r16(sizeof(uint32_t) * (Spad >> 5)) + r16(sizeof(uint16_t) * kBatch * Spad) +
+           r16(sizeof(int) * kBatch) +
            r16(sizeof(SelState)) + r16(Z) + r16(sizeof(uint16_t) * Z);
 }
 
@@ -843,15 +928,17 @@ void launch_select_exact(const acom_plan_s* p, const float* Xsr, const float* Xs
                          const float* xfn, const int2* srange, const float* pfmax,
                          const float* xnorm2, int nb,
                          float kappa, int refine, acom_result out, int64_t off, int* n_eval,
-                         cudaStream_t st, const float* xscale, int rescore_top) {
+                         cudaStream_t st, const float* xscale, int rescore_top,
+                         const acom_peaks_csr* cp) {
     SelectArgs a{p->Psr, p->Psi, Xsr, Xsi, U, xfn, srange, pfmax, xnorm2, p->za, p->frames,
                  p->nbr_ptr,
                  p->nbr_idx, p->phase_off, p->n_phases, p->Z, p->F, p->N, p->S, p->Spad, nb, refine, kappa,
                  fft_radices(p->N), out, off, n_eval, xscale, 1.0f / p->pscale,
                  p->precision == ACOM_PREC_FP8 ? kFp8Shift : 1.0f,
-                 (float)(p->precision == ACOM_PREC_FP8 ? kFp8Eta : kFp16Eta), rescore_top};
-    const size_t smem = select_smem_bytes(p->Z, p->N, p->F);
-    cudaFuncSetAttribute(k_select_exact, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                 (float)(p->precision == ACOM_PREC_FP8 ? kFp8Eta : kFp16Eta), rescore_top,
+                 p->smask, cp->row_ptr, cp->qx, cp->qy, (float)p->dq, (float)p->delta};
+    const size_t smem = select_smem_bytes(p->Z, p->N, p->F, p->Spad);
+    set_max_dynamic_smem((const void*)k_select_exact, smem);
     int dev = 0, nsm = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);

@@ -573,7 +573,7 @@ void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_st
     a.inv_pscale = 1.0f / p->pscale;
     const size_t smem = tc::tc_smem_bytes();
     auto kern = f8 ? tc::k_contract_bound_tc<true> : tc::k_contract_bound_tc<false>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    set_max_dynamic_smem((const void*)kern, smem);
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);

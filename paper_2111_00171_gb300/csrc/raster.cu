@@ -416,8 +416,7 @@ template <class Loader, int NF2>
 static void launch_raster_nf(const RasterGeom& geo, const Loader& ld, int64_t n_items,
                              const RasterOut& out, int* err, cudaStream_t st, int cls) {
     size_t smem = raster_smem_bytes(geo.N, geo.F);
-    cudaFuncSetAttribute(k_raster_dft<Loader, NF2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
+    set_max_dynamic_smem((const void*)k_raster_dft<Loader, NF2>, smem);
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -747,8 +746,7 @@ static bool launch_raster_fft(const RasterGeom& geo, const Loader& ld, int64_t n
     if (rad.n == 0 || geo.Spad % kFftTile != 0 || geo.F > 32 * kMaxFPerLane) return false;
     const size_t smem = raster_fft_smem_bytes(geo.N, geo.F);
     if (smem > 227 * 1024) return false;
-    cudaFuncSetAttribute(k_raster_fft<Loader>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
+    set_max_dynamic_smem((const void*)k_raster_fft<Loader>, smem);
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);

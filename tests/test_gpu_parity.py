@@ -440,3 +440,33 @@ def test_fp8_certified_and_rescored_winners():
     assert agree >= 80
     p32.close()
     p8.close()
+
+
+# ------------------------------------------------------ CUDA graph capture
+
+def test_match_async_captured_in_cuda_graph():
+    """acom_match_async captured into a CUDA graph: replaying it on new
+    contents of the same peak buffers gives what a synchronous match of those
+    peaks gives, and acom_sync reports the replay's status."""
+    import torch
+    plan = gpu_plan("au_2deg_75x180", precision=2)
+    a = synth.random_patterns(1301, n_patterns=64)
+    # a second scan with the same CSR layout: the same peaks rotated in plane
+    ang = 0.37
+    bx = (np.cos(ang) * a.qx - np.sin(ang) * a.qy).astype(np.float32)
+    by = (np.sin(ang) * a.qx + np.cos(ang) * a.qy).astype(np.float32)
+    rp, qx, qy, I = to_dev(a)
+    plan.match(rp, qx, qy, I)                    # sizes the workspace
+    out = plan.alloc_result(a.n_patterns)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="relaxed"):
+        plan.match_async(rp, qx, qy, I, out)
+    qx.copy_(torch.from_numpy(bx).cuda())
+    qy.copy_(torch.from_numpy(by).cuda())
+    g.replay()
+    plan.sync()
+    ref = plan.match(rp, qx, qy, I)
+    torch.cuda.synchronize()
+    for k in ("za_idx", "phi3_bin", "mirror", "score", "orient"):
+        assert torch.equal(out[k], ref[k]), k
+    plan.close()
