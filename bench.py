@@ -407,7 +407,7 @@ def main():
     def step(inputs, out):
         p = make_plan()
         p.match(*inputs, chunk=args.chunk, out=out, exhaustive=args.exhaustive,
-                phase_scores=mixed)
+                phase_scores=mixed, tile_order=tuned["tile_order"] if tuned else 0)
         stats["evaluated"] = p.get_info()["last_evaluated"]
         if W.get("refine"):
             p.refine(*inputs, out["orient"], orient_alt=out["runner_orient"])
@@ -417,6 +417,12 @@ def main():
 
     probe = make_plan()
     out = probe.alloc_result(B, phase_scores=mixed, runner=bool(W.get("refine")))
+    # the contraction's schedule (chunk, tile order) by acom_autotune on this
+    # scan, unless --chunk fixes it or the FP32 / exhaustive paths run
+    tuned = None
+    if args.chunk == 0 and not args.exhaustive and args.precision != "fp32":
+        tuned, trials = probe.autotune(*d_in)
+        args.chunk = tuned["chunk"]
     probe.close()
     for _ in range(args.warmup):
         step(d_in, out)
@@ -506,6 +512,9 @@ def main():
                        "peaks_nnz": int(scan.row_ptr[-1]), "zone_axes": W["Z"], "shells": W["S"],
                        "n_phi": W["N"], "precision": args.precision,
                        "chunk": args.chunk or (1024 if args.exhaustive else 8192),
+                       "autotuned": ({"chunk": tuned["chunk"], "tile_order": tuned["tile_order"],
+                                      "trials_ms": {f"{t['chunk']}/{t['tile_order']}": round(t["ms"], 2)
+                                                    for t in trials}} if tuned else None),
                        "mode": "exhaustive" if args.exhaustive else "certified pruning",
                        "axes_evaluated_per_pattern": stats.get("evaluated", 0) / B,
                        "l2": "flushed between steps (256 MiB write outside the timed events)",

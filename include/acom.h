@@ -259,7 +259,27 @@ typedef struct {
                                  evaluated exactly in FP32 and the best of them
                                  wins (the grid neighbours of the winner are
                                  evaluated for the refinement as usual)       */
+    int32_t tile_order;       /* tensor-core contraction schedule: 0 consecutive
+                                 tiles share a pattern tile (default), 1 they
+                                 share a zone-axis tile                       */
 } acom_match_opts;
+
+/*
+ * acom_autotune - the contraction's schedule picked by measurement: the
+ * match of ``peaks`` (a representative sample, DEVICE) is timed (CUDA events,
+ * after a warm-up match) for chunk sizes 4096, 8192 and 16384 and both tile
+ * orders, with the other options from ``base`` (may be NULL).  ``best``
+ * receives the fastest (chunk, tile_order, ms), ``trials`` (optional, 6
+ * entries) every one.  Pass best's chunk and tile_order in acom_match_opts.
+ */
+typedef struct {
+    int32_t chunk;
+    int32_t tile_order;
+    float ms;
+} acom_tune_result;
+
+acom_status acom_autotune(acom_plan plan, const acom_peaks_csr* peaks, const acom_match_opts* base,
+                          acom_tune_result* best, acom_tune_result* trials, void* cuda_stream);
 
 /*
  * acom_match - sparse correlation match (section "Correlation Pattern

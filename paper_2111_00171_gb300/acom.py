@@ -31,7 +31,7 @@ EXPORTED = ("acom_plan_create", "acom_plan_destroy", "acom_plan_get_info",
             "acom_version", "acom_profile_enable", "acom_profile_reset", "acom_profile_read",
             "acom_kernel_launches", "acom_plan_concat", "acom_plan_get_phases", "acom_refine",
             "acom_refine_defaults", "acom_kinematical_score", "acom_match_multi",
-            "acom_match_async", "acom_sync")
+            "acom_match_async", "acom_sync", "acom_autotune")
 
 
 class AcomError(RuntimeError):
@@ -82,7 +82,11 @@ class Result(C.Structure):
 
 class MatchOpts(C.Structure):
     _fields_ = [("refine", C.c_int32), ("chunk", C.c_int32), ("exhaustive", C.c_int32),
-                ("rescore_top", C.c_int32)]
+                ("rescore_top", C.c_int32), ("tile_order", C.c_int32)]
+
+
+class TuneResult(C.Structure):
+    _fields_ = [("chunk", C.c_int32), ("tile_order", C.c_int32), ("ms", C.c_float)]
 
 
 class RefineOpts(C.Structure):
@@ -123,6 +127,8 @@ def load_library():
     lib.acom_match_async.argtypes = [P, C.POINTER(PeaksCSR), C.POINTER(MatchOpts),
                                      C.POINTER(Result), P]
     lib.acom_sync.argtypes = [P, P]
+    lib.acom_autotune.argtypes = [P, C.POINTER(PeaksCSR), C.POINTER(MatchOpts),
+                                  C.POINTER(TuneResult), C.POINTER(TuneResult), P]
     lib.acom_plan_get_zone_axes.argtypes = [P, P]
     lib.acom_plan_get_spectra.argtypes = [P, P, P]
     lib.acom_match.argtypes = [P, C.POINTER(PeaksCSR), C.POINTER(MatchOpts), C.POINTER(Result), P]
@@ -140,6 +146,7 @@ def load_library():
     for name in ("acom_plan_create", "acom_plan_destroy", "acom_plan_get_info",
                  "acom_plan_concat", "acom_plan_get_phases", "acom_refine",
                  "acom_kinematical_score", "acom_match_multi", "acom_match_async", "acom_sync",
+                 "acom_autotune",
                  "acom_plan_get_zone_axes", "acom_plan_get_spectra", "acom_match",
                  "acom_polar_spectra", "acom_bounds", "acom_bounds_static"):
         getattr(lib, name).restype = C.c_int
@@ -343,7 +350,8 @@ class Plan:
         return r
 
     def match(self, row_ptr, qx, qy, I, refine=True, chunk=0, za_scores=False, out=None,
-              exhaustive=False, phase_scores=False, runner=False, rescore_top=0, stream=None):
+              exhaustive=False, phase_scores=False, runner=False, rescore_top=0, tile_order=0,
+              stream=None):
         """acom_match on device CSR tensors; returns a dict of device tensors
         (with phase_scores: the phase of each winner and every phase's best;
         with runner: the runner-up axis, score and grid orientation)."""
@@ -352,23 +360,36 @@ class Plan:
                                                           phase_scores=phase_scores,
                                                           runner=runner)
         res = Result(*(_ptr(r.get(k)) for k, _ in Result._fields_))
-        opts = MatchOpts(1 if refine else 0, int(chunk), 1 if exhaustive else 0, int(rescore_top))
+        opts = MatchOpts(1 if refine else 0, int(chunk), 1 if exhaustive else 0, int(rescore_top),
+                         int(tile_order))
         _check(self._lib.acom_match(self.handle, C.byref(pk), C.byref(opts), C.byref(res),
                                     _stream_ptr(stream)))
         return r
 
 
     def match_async(self, row_ptr, qx, qy, I, out, refine=True, chunk=0, exhaustive=False,
-                    rescore_top=0, stream=None):
+                    rescore_top=0, tile_order=0, stream=None):
         """acom_match_async into the result dict ``out`` (alloc_result): the
         work is only enqueued; sync() returns its status.  Capturable into a
         CUDA graph once a synchronous match has sized the workspace."""
         pk = self._csr(row_ptr, qx, qy, I)
         res = Result(*(_ptr(out.get(k)) for k, _ in Result._fields_))
-        opts = MatchOpts(1 if refine else 0, int(chunk), 1 if exhaustive else 0, int(rescore_top))
+        opts = MatchOpts(1 if refine else 0, int(chunk), 1 if exhaustive else 0, int(rescore_top),
+                         int(tile_order))
         _check(self._lib.acom_match_async(self.handle, C.byref(pk), C.byref(opts), C.byref(res),
                                           _stream_ptr(stream)))
         return out
+
+    def autotune(self, row_ptr, qx, qy, I, stream=None):
+        """acom_autotune on a sample of peaks: (best, trials), each a dict of
+        chunk, tile_order and ms."""
+        pk = self._csr(row_ptr, qx, qy, I)
+        best = TuneResult()
+        trials = (TuneResult * 6)()
+        _check(self._lib.acom_autotune(self.handle, C.byref(pk), None, C.byref(best), trials,
+                                       _stream_ptr(stream)))
+        as_dict = lambda t: {"chunk": t.chunk, "tile_order": t.tile_order, "ms": t.ms}
+        return as_dict(best), [as_dict(t) for t in trials]
 
     def sync(self, stream=None):
         """acom_sync: wait for the stream; the status of the last async match."""

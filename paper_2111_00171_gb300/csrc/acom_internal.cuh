@@ -252,7 +252,8 @@ acom_status make_bf16_map(void* map_storage, const void* base, uint64_t rows, ui
 void launch_half_to_e4m3(const void* src, void* dst, int64_t n, float mul, cudaStream_t st);
 // xscale: per-pattern 2^e of FP16 pattern spectra (nullptr: BF16, no scale)
 void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_stride, int nb,
-                              float* U, cudaStream_t st, const float* xscale = nullptr);
+                              float* U, cudaStream_t st, const float* xscale = nullptr,
+                              int tile_order = 0);
 // kind 1 / 2: FP16 / E4M3 of scale * src instead of BF16 of src
 void launch_plan_to_bf16(const float* src, int Zp, int F, int Spad, void* dst, cudaStream_t st,
                          int kind = 0, float scale = 1.0f);

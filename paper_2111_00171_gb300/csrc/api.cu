@@ -747,6 +747,9 @@ static acom_status match_enqueue(acom_plan p, const acom_peaks_csr* peaks,
     const bool exhaustive = opts && opts->exhaustive;
     const int rescore_top = opts && !exhaustive ? opts->rescore_top : 0;
     if (rescore_top < 0) return set_error(ACOM_ERR_INVALID_ARG, "rescore_top must be >= 0");
+    const int tile_order = opts ? opts->tile_order : 0;
+    if (tile_order < 0 || tile_order > 1)
+        return set_error(ACOM_ERR_INVALID_ARG, "tile_order must be 0 or 1");
     if (exhaustive && (out->runner_za || out->runner_score || out->runner_orient))
         return set_error(ACOM_ERR_UNSUPPORTED, "runner-up outputs need certified pruning");
     if (!exhaustive && p->Z > 16384)
@@ -799,7 +802,8 @@ static acom_status match_enqueue(acom_plan p, const acom_peaks_csr* peaks,
         } else {
             if (tc) {
                 convert_fp8(p, st);
-                launch_contract_bound_tc(p, p->ws.map_x, p->ws.PTs, nb, p->ws.U, st, xscale);
+                launch_contract_bound_tc(p, p->ws.map_x, p->ws.PTs, nb, p->ws.U, st, xscale,
+                                         tile_order);
             } else {
                 launch_contract_bound_fp32(p, p->ws.Xr, p->ws.Xi, nb, p->ws.U, st);
             }
@@ -1059,6 +1063,68 @@ acom_status acom_match_multi(acom_plan p, const acom_peaks_csr* peaks,
     release();
     if (e != cudaSuccess) return cuda_error(e, "match_multi launch");
     return read_error_word(p, st);
+}
+
+acom_status acom_autotune(acom_plan p, const acom_peaks_csr* peaks, const acom_match_opts* base,
+                          acom_tune_result* best, acom_tune_result* trials, void* cuda_stream) {
+    g_last_error.clear();
+    if (!p || !peaks || !best) return set_error(ACOM_ERR_INVALID_ARG, "null argument");
+    if (peaks->n_patterns <= 0) return set_error(ACOM_ERR_INVALID_ARG, "empty sample");
+    const int64_t B = peaks->n_patterns;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    // results of the trial matches go to scratch owned by this call
+    int32_t *za = nullptr, *kb = nullptr;
+    uint8_t* mi = nullptr;
+    float* sc = nullptr;
+    cudaError_t e;
+    if ((e = pool_alloc(reinterpret_cast<void**>(&za), sizeof(int32_t) * B, st)) != cudaSuccess ||
+        (e = pool_alloc(reinterpret_cast<void**>(&kb), sizeof(int32_t) * B, st)) != cudaSuccess ||
+        (e = pool_alloc(reinterpret_cast<void**>(&mi), B, st)) != cudaSuccess ||
+        (e = pool_alloc(reinterpret_cast<void**>(&sc), sizeof(float) * B, st)) != cudaSuccess) {
+        pool_free(za, st);
+        pool_free(kb, st);
+        pool_free(mi, st);
+        pool_free(sc, st);
+        return cuda_error(e, "autotune scratch");
+    }
+    acom_result r{};
+    r.za_idx = za;
+    r.phi3_bin = kb;
+    r.mirror = mi;
+    r.score = sc;
+    acom_match_opts o = base ? *base : acom_match_opts{1, 0, 0, 0, 0};
+    const int chunks[3] = {4096, 8192, 16384};
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    acom_status s = ACOM_OK;
+    best->ms = -1.0f;
+    int n = 0;
+    for (int ci = 0; ci < 3 && s == ACOM_OK; ++ci)
+        for (int order = 0; order < 2 && s == ACOM_OK; ++order) {
+            o.chunk = chunks[ci];
+            o.tile_order = order;
+            s = acom_match(p, peaks, &o, &r, cuda_stream);           // warm-up, sizes the workspace
+            if (s != ACOM_OK) break;
+            cudaEventRecord(t0, st);
+            s = acom_match(p, peaks, &o, &r, cuda_stream);
+            cudaEventRecord(t1, st);
+            cudaEventSynchronize(t1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, t0, t1);
+            const acom_tune_result tr{o.chunk, order, ms};
+            if (trials) trials[n] = tr;
+            ++n;
+            if (best->ms < 0.f || ms < best->ms) *best = tr;
+        }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    pool_free(za, st);
+    pool_free(kb, st);
+    pool_free(mi, st);
+    pool_free(sc, st);
+    cudaStreamSynchronize(st);
+    return s;
 }
 
 }  // extern "C"

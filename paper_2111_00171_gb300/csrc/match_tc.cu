@@ -248,6 +248,8 @@ struct TcArgs {
     const float* xscale;           // [nb] 2^e of FP16 pattern spectra, or nullptr
     float xs_mul;                  // the operands hold xscale * xs_mul times X^
     float inv_pscale;              // 2^-k of the plan operand's scale (1 for BF16)
+    int zmajor;                    // tile order: 0 consecutive tiles share a pattern
+                                   // tile, 1 they share an axis tile
 };
 
 // F8: E4M3 operands (kind::f8f6f4, 128 elements per K tile), else 16-bit
@@ -312,7 +314,8 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
             int fcount = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-                const int zt = t % a.ZT, pt = t / a.ZT;
+                const int zt = a.zmajor ? t / a.PT : t % a.ZT;
+                const int pt = a.zmajor ? t % a.PT : t / a.ZT;
                 for (int f = 0; f < a.F && ok; ++f, ++fcount) {
                     const int prow = f * a.Zrows + zt * kM;
                     const int xrow = (f * a.PTs + pt) * 128;
@@ -433,7 +436,8 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
         int fcount = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-            const int zt = t % a.ZT, pt = t / a.ZT;
+            const int zt = a.zmajor ? t / a.PT : t % a.ZT;
+            const int pt = a.zmajor ? t % a.PT : t / a.ZT;
             for (int f = 0; f < a.F; ++f, ++fcount) {
                 const int buf = fcount & 1;
                 if (!mbar_wait(smem_u32(tfull + buf), tph[buf], abort_flag, a.err)) {
@@ -550,8 +554,9 @@ acom_status make_bf16_map(void* map_storage, const void* base, uint64_t rows, ui
 size_t tensor_map_bytes() { return sizeof(CUtensorMap); }
 
 void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_stride, int nb,
-                              float* U, cudaStream_t st, const float* xscale) {
+                              float* U, cudaStream_t st, const float* xscale, int tile_order) {
     tc::TcArgs a;
+    a.zmajor = tile_order == 1 ? 1 : 0;
     a.F = p->F;
     a.N = p->N;
     a.Z = p->Z;

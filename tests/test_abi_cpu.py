@@ -117,3 +117,17 @@ def test_refine_defaults_and_argument_checks_on_host(lib):
     assert lib.acom_refine(None, C.byref(pk), None, None, None, None, None, None) == 1
     assert lib.acom_kinematical_score(None, C.byref(pk), None, None, 0.03, None, None, None,
                                       None) == 1
+
+
+def test_autotune_and_tile_order_argument_checks_on_host(lib):
+    """acom_autotune rejects a null plan or result before any device work; the
+    ctypes mirror of acom_match_opts carries all five fields of the header's
+    struct, tile_order last."""
+    from paper_2111_00171_gb300 import acom
+    pk = acom.PeaksCSR(0, None, None, None, None)
+    best = acom.TuneResult()
+    assert lib.acom_autotune(None, C.byref(pk), None, C.byref(best), None, None) == 1
+    assert lib.acom_last_error()
+    assert [f for f, _ in acom.MatchOpts._fields_] == ["refine", "chunk", "exhaustive",
+                                                        "rescore_top", "tile_order"]
+    assert C.sizeof(acom.MatchOpts) == 20 and C.sizeof(acom.TuneResult) == 12

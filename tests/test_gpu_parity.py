@@ -470,3 +470,21 @@ def test_match_async_captured_in_cuda_graph():
     for k in ("za_idx", "phi3_bin", "mirror", "score", "orient"):
         assert torch.equal(out[k], ref[k]), k
     plan.close()
+
+
+def test_autotune_trials_and_tile_orders():
+    """acom_autotune times six schedules and returns the fastest; both tile
+    orders of the contraction give bit-identical results."""
+    import torch
+    plan = gpu_plan("au_2deg_75x180", precision=2)
+    scan = synth.random_patterns(1401, n_patterns=200)
+    inp = to_dev(scan)
+    best, trials = plan.autotune(*inp)
+    assert len(trials) == 6 and all(t["ms"] > 0 for t in trials)
+    assert best["ms"] == min(t["ms"] for t in trials)
+    a = plan.match(*inp, tile_order=0)
+    b = plan.match(*inp, tile_order=1, chunk=best["chunk"])
+    torch.cuda.synchronize()
+    for k in ("za_idx", "phi3_bin", "mirror", "score"):
+        assert torch.equal(a[k], b[k]), k
+    plan.close()
