@@ -108,6 +108,12 @@ def parse():
         W.update(SWEEP)
     if args.scan is None:
         args.scan = f"{W['H']}x{W['Wd']}"
+    elif "n_patterns" not in W:
+        # a scan of another size, same recipe: the workload text names its size
+        H, Wd = (int(v) for v in args.scan.split("x"))
+        old = f"{W['H']}x{W['Wd']} scan ({W['H'] * W['Wd']:,} patterns"
+        assert old in W["text"]
+        W["text"] = W["text"].replace(old, f"{H}x{Wd} scan ({H * Wd:,} patterns")
     if args.precision is None:
         args.precision = W.get("precision", "fp16")
     return args
@@ -119,6 +125,25 @@ def make_scan(seed, args):
         return synth.mixed_patterns(seed, n_patterns=W["n_patterns"])
     H, Wd = (int(v) for v in args.scan.split("x"))
     return synth.grain_scan(seed, H=H, W=Wd, peaks=W.get("peaks", "uniform10-60"))
+
+
+def pattern_shell_rows(scan):
+    """Mean number of shell rows per pattern that its sparse polar image can
+    make non-zero: shells s with |r_m - q_s| < delta for some peak m, q_s =
+    (s + 1) dq.  These are the only rows of a pattern's spectra that the exact
+    evaluation multiplies (a zero row contributes exactly 0)."""
+    S, dq, delta = W["S"], W["dq"], W["delta"]
+    rp = np.asarray(scan.row_ptr, dtype=np.int64)
+    B = len(rp) - 1
+    r = np.hypot(np.asarray(scan.qx, np.float64), np.asarray(scan.qy, np.float64))
+    b = np.repeat(np.arange(B), np.diff(rp))
+    lo = np.clip(np.floor((r - delta) / dq - 1.0).astype(np.int64) + 1, 0, S)
+    hi = np.clip(np.ceil((r + delta) / dq - 1.0).astype(np.int64) - 1, -1, S - 1)
+    ok = hi >= lo
+    diff = np.zeros((B, S + 1), np.int32)
+    np.add.at(diff, (b[ok], lo[ok]), 1)
+    np.add.at(diff, (b[ok], hi[ok] + 1), -1)
+    return float((np.cumsum(diff[:, :S], axis=1) > 0).sum() / max(B, 1))
 
 
 def peaks_file():
@@ -502,7 +527,7 @@ def main():
     K = args.steps
     value = world * B * K / (dev_ms / 1e3)
     roof = roofline(prof, peaks, src, B, K, args.precision, int(scan.row_ptr[-1]),
-                    stats.get("refine_pairs", 0))
+                    stats.get("refine_pairs", 0), pattern_shell_rows(scan))
     line = {"metric": METRIC, "value": value, "unit": "patterns/s", "n_gpus": world,
             "steps": K, "warmup": args.warmup, "ms_per_step": dev_ms / K,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -722,7 +747,8 @@ def kernel_traffic(name, pats, precision):
     return t[0] * pats
 
 
-def kernel_roofline(name, cnt, ms, peaks, src, B, K, nnz, precision, refine_pairs=0):
+def kernel_roofline(name, cnt, ms, peaks, src, B, K, nnz, precision, refine_pairs=0,
+                    rows_nz=None):
     """Achieved rate of one kernel class: algorithmic work per launch over its
     event-timed average launch duration."""
     Z, S, N = W["Z"], W["S"], W["N"]
@@ -739,13 +765,15 @@ def kernel_roofline(name, cnt, ms, peaks, src, B, K, nnz, precision, refine_pair
         work, unit, bound, peak = 8.0 * Z * S * F * pats, "TFLOP/s", "alu", fp32_peak
         note = "8 Z S F flops per pattern; FP32 FMA peak 152 SMs x 128 lanes x 2 x max clock"
     elif name == "select_exact":
-        # compulsory HBM bytes: each pattern's FP32 shell-major spectra read
-        # once (S x F x re/im) and the plan's FP32 spectra once per launch;
-        # the repeated reads of an axis' spectra are served by L2
-        work = (S * F * 8 * pats + Z * S * F * 8) / 1e9
+        # compulsory HBM bytes: each pattern's FP32 shell-major spectra on
+        # the shells its peaks reach (rows_nz of S, re/im) read once, and the
+        # plan's FP32 spectra once per launch; the repeated reads of an axis'
+        # spectra are served by L2
+        rows = S if rows_nz is None else rows_nz
+        work = (rows * F * 8 * pats + Z * S * F * 8) / 1e9
         unit, bound, peak = "GB/s", "hbm", peaks["hbm_gbs"]
-        note = (f"pattern FP32 spectra once per pattern + plan FP32 spectra once per launch; "
-                f"HBM peak ({src})")
+        note = (f"pattern FP32 spectra on its non-zero shells ({rows:.1f} of {S} on average) "
+                f"once per pattern + plan FP32 spectra once per launch; HBM peak ({src})")
     elif name == "refine_orient" and refine_pairs:
         # every (contributing reflection, peak) pair of every score evaluation:
         # 13 FP32 operations and one exp (counted by the kernel itself)
@@ -769,14 +797,15 @@ def kernel_roofline(name, cnt, ms, peaks, src, B, K, nnz, precision, refine_pair
             "launches": cnt, "peak_source": note}
 
 
-def roofline(prof, peaks, src, B, K, precision, nnz, refine_pairs=0):
+def roofline(prof, peaks, src, B, K, precision, nnz, refine_pairs=0, rows_nz=None):
     """The dominant kernel's roofline (the largest event-timed total among
     the kernels with a stated roofline), plus every other kernel's share."""
     rows = []
     for name, (cnt, ms) in prof.items():
         if cnt == 0:
             continue
-        r = kernel_roofline(name, cnt, ms, peaks, src, B, K, nnz, precision, refine_pairs)
+        r = kernel_roofline(name, cnt, ms, peaks, src, B, K, nnz, precision, refine_pairs,
+                            rows_nz)
         if r is not None:
             r["total_ms"] = ms
             rows.append(r)

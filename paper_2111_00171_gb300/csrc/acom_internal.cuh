@@ -101,6 +101,15 @@ inline float fp16_plan_scale(int N) {
     return (float)s;
 }
 
+// What the select kernel hands the orientation kernel for one pattern: the
+// winner (axis z, bin + mirror * N), the correlation at bins k - 1, k, k + 1
+// and the score-weighted sum of the neighbour axes within 0.9 of the best.
+struct OrientIn {
+    double w[3];
+    float c3[3];
+    int z, km, pad;
+};
+
 // Workspace for one chunk of patterns.
 struct Workspace {
     int chunk = 0;                 // capacity in patterns
@@ -121,6 +130,7 @@ struct Workspace {
     float* za_scores = nullptr;    // [chunk][Z]
     float* xscale = nullptr;       // [chunk] 2^e of each pattern's FP16 spectrum
     void* XB8 = nullptr;           // E4M3 copy of XB (FP8 plans)
+    OrientIn* oin = nullptr;       // [chunk] winners for the orientation kernel
     size_t bytes = 0;
 };
 
@@ -257,12 +267,14 @@ void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_st
 // kind 1 / 2: FP16 / E4M3 of scale * src instead of BF16 of src
 void launch_plan_to_bf16(const float* src, int Zp, int F, int Spad, void* dst, cudaStream_t st,
                          int kind = 0, float scale = 1.0f);
+void launch_orient_compose(const acom_plan_s* p, const OrientIn* oin, int nb, int refine,
+                           acom_result out, int64_t off, cudaStream_t st);
 void launch_select_exact(const acom_plan_s* p, const float* Xsr, const float* Xsi, const float* U,
                          const float* xfn, const int2* srange, const float* pfmax,
                          const float* xnorm2, int nb,
                          float kappa, int refine, acom_result out, int64_t off, int* n_eval,
                          cudaStream_t st, const float* xscale, int rescore_top,
-                         const acom_peaks_csr* chunk_peaks);
+                         const acom_peaks_csr* chunk_peaks, OrientIn* oin);
 // refine.cu: continuous refinement on the plan's reflections
 acom_status refine_table(acom_plan_s* p, cudaStream_t st);
 void launch_refine_orient(const acom_plan_s* p, const acom_peaks_csr* pk, int steps,

@@ -148,6 +148,7 @@ static void free_workspace(Workspace& ws, cudaStream_t st) {
     pool_free(ws.XB, st);
     pool_free(ws.xscale, st);
     pool_free(ws.XB8, st);
+    pool_free(ws.oin, st);
     ws = Workspace{};
 }
 
@@ -184,6 +185,7 @@ static acom_status ensure_workspace(acom_plan_s* p, int chunk, bool need_chat, b
     if ((e = dalloc(&ws.srange, (size_t)chunk, &acc, st)) != cudaSuccess) goto fail;
     if ((e = dalloc(&ws.best, (size_t)chunk, &acc, st)) != cudaSuccess) goto fail;
     if ((e = dalloc(&ws.za_scores, (size_t)chunk * p->Z, &acc, st)) != cudaSuccess) goto fail;
+    if ((e = dalloc(&ws.oin, (size_t)chunk, &acc, st)) != cudaSuccess) goto fail;
     if (tc_precision(p->precision)) {
         // the raster writes BF16, or FP16 with a per-pattern scale; E4M3
         // operands are converted from the FP16 rows
@@ -810,7 +812,10 @@ static acom_status match_enqueue(acom_plan p, const acom_peaks_csr* peaks,
             const acom_peaks_csr cp{nb, peaks->row_ptr + c0, peaks->qx, peaks->qy, peaks->I};
             launch_select_exact(p, p->ws.Xsr, p->ws.Xsi, p->ws.U, p->ws.xfn, p->ws.srange, p->pfmax,
                                 p->ws.xnorm2, nb, tc ? kappa_tc(p) : kappa_fp32(p), refine,
-                                *out, c0, p->ws.n_eval, st, xscale, rescore_top, &cp);
+                                *out, c0, p->ws.n_eval, st, xscale, rescore_top, &cp,
+                                p->ws.oin);
+            if (out->phi3 || out->orient)
+                launch_orient_compose(p, p->ws.oin, nb, refine, *out, c0, st);
         }
     }
     cudaError_t e = cudaGetLastError();

@@ -360,6 +360,7 @@ struct SelectArgs {
     const int64_t* row_ptr;           // the chunk's peaks (row_ptr offset to the chunk)
     const float *qx, *qy;
     float dq, delta;                  // shells q_s = (s + 1) dq, tent size
+    OrientIn* oin;                    // [nb] the winners, for k_orient_compose
 };
 
 // Spectra c_dir + i c_mir of the batch's candidate axes, scaled by 1/N, into
@@ -562,16 +563,38 @@ __device__ inline void matmul3d(const double* a, const double* b, double* c) {
             c[3 * i + j] = a[3 * i] * b[j] + a[3 * i + 1] * b[3 + j] + a[3 * i + 2] * b[6 + j];
 }
 
-// Orientation of the winner (thread 0): parabolic phi3 offset, zone axis
-// refined toward the score-weighted mean of the neighbours within 0.9 of the
-// best, composed in FP64.
+// Outputs of the winner (warp 0).  For the orientation, the score-weighted
+// sum of the neighbour axes within 0.9 of the best (the lanes take the
+// neighbours and a butterfly sums them, so every lane holds the same FP64
+// sum) and the correlation at bins k - 1, k, k + 1 go to oin[b]; the FP64
+// composition runs in k_orient_compose, one thread per pattern, so that it
+// does not hold up the block.
 __device__ __noinline__ void write_outputs(const SelectArgs& a, int64_t b, const SelSmem& sm,
-                                           bool want_ref) {
+                                           bool want_ref, int lane) {
     const SelState& st = *sm.st;
     const int N = a.N, bz = st.bz, bk = st.bk, bm = st.bm;
     const float T = st.T;
     const int64_t o = a.off + b;
     const float score = T == -CUDART_INF_F ? 0.f : T;
+    double a0 = 0, a1 = 0, a2 = 0;
+    if (want_ref && a.refine) {
+        for (int q = a.nbr_ptr[bz] + lane; q < a.nbr_ptr[bz + 1]; q += 32) {
+            const int z2 = a.nbr_idx[q];
+            if (!sm.ev[z2]) continue;             // its true score is below 0.9 of the best
+            const float sc = sm.U[z2];
+            if (sc >= 0.9f * T) {
+                a0 += (double)sc * a.za[3 * z2];
+                a1 += (double)sc * a.za[3 * z2 + 1];
+                a2 += (double)sc * a.za[3 * z2 + 2];
+            }
+        }
+        for (int w = 16; w > 0; w >>= 1) {
+            a0 += __shfl_xor_sync(0xffffffffu, a0, w);
+            a1 += __shfl_xor_sync(0xffffffffu, a1, w);
+            a2 += __shfl_xor_sync(0xffffffffu, a2, w);
+        }
+    }
+    if (lane != 0) return;
     a.out.za_idx[o] = bz;
     a.out.phi3_bin[o] = bk;
     a.out.mirror[o] = (uint8_t)bm;
@@ -612,49 +635,62 @@ __device__ __noinline__ void write_outputs(const SelectArgs& a, int64_t b, const
         a.out.score_cos[o] = xn > 0.f ? score / xn : 0.f;
     }
     if (!want_ref) return;
+    OrientIn& r = a.oin[b];
+    r.w[0] = a0;
+    r.w[1] = a1;
+    r.w[2] = a2;
+    r.c3[0] = st.best3[0];
+    r.c3[1] = st.best3[1];
+    r.c3[2] = st.best3[2];
+    r.z = bz;
+    r.km = bk + bm * N;
+}
+
+// Orientation of each winner, one thread per pattern: parabolic phi3 offset
+// from the correlation at k - 1, k, k + 1; the zone axis refined toward the
+// normalised score-weighted neighbour sum; m = T frame Rz(phi3) [Ry(pi)]
+// composed in FP64.
+__global__ void k_orient_compose(const OrientIn* __restrict__ oin, int nb, int N, int refine,
+                                 const double* __restrict__ za, const double* __restrict__ frames,
+                                 acom_result out, int64_t off) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const OrientIn r = oin[b];
+    const int bz = r.z, bm = r.km >= N ? 1 : 0, bk = r.km - bm * N;
+    const int64_t o = off + b;
     double dk = 0.0, wref[3];
-    if (a.refine) {
-        const double cm = st.best3[0], c0 = st.best3[1], cp = st.best3[2];
+    if (refine) {
+        const double cm = r.c3[0], c0 = r.c3[1], cp = r.c3[2];
         const double den = cm - 2.0 * c0 + cp;
         if (den < 0.0) {
             dk = (cm - cp) / (2.0 * den);
             dk = dk > 0.5 ? 0.5 : (dk < -0.5 ? -0.5 : dk);
         }
-        double a0 = 0, a1 = 0, a2 = 0;
-        for (int q = a.nbr_ptr[bz]; q < a.nbr_ptr[bz + 1]; ++q) {
-            const int z2 = a.nbr_idx[q];
-            if (!sm.ev[z2]) continue;             // its true score is below 0.9 of the best
-            const float sc = sm.U[z2];
-            if (sc >= 0.9f * T) {
-                a0 += (double)sc * a.za[3 * z2];
-                a1 += (double)sc * a.za[3 * z2 + 1];
-                a2 += (double)sc * a.za[3 * z2 + 2];
-            }
-        }
+        const double a0 = r.w[0], a1 = r.w[1], a2 = r.w[2];
         const double nrm = sqrt(a0 * a0 + a1 * a1 + a2 * a2);
-        wref[0] = nrm > 0 ? a0 / nrm : a.za[3 * bz];
-        wref[1] = nrm > 0 ? a1 / nrm : a.za[3 * bz + 1];
-        wref[2] = nrm > 0 ? a2 / nrm : a.za[3 * bz + 2];
+        wref[0] = nrm > 0 ? a0 / nrm : za[3 * bz];
+        wref[1] = nrm > 0 ? a1 / nrm : za[3 * bz + 1];
+        wref[2] = nrm > 0 ? a2 / nrm : za[3 * bz + 2];
     } else {
-        wref[0] = a.za[3 * bz];
-        wref[1] = a.za[3 * bz + 1];
-        wref[2] = a.za[3 * bz + 2];
+        wref[0] = za[3 * bz];
+        wref[1] = za[3 * bz + 1];
+        wref[2] = za[3 * bz + 2];
     }
     const double phi3 = -2.0 * CUDART_PI * ((double)bk + dk) / (double)N;
-    if (a.out.phi3) a.out.phi3[o] = (float)phi3;
-    if (!a.out.orient) return;
+    if (out.phi3) out.phi3[o] = (float)phi3;
+    if (!out.orient) return;
     double Rz[9], m1[9], m2[9], Tm[9];
     double c3, s3;
     sincos(phi3, &s3, &c3);
     Rz[0] = c3; Rz[1] = -s3; Rz[2] = 0; Rz[3] = s3; Rz[4] = c3; Rz[5] = 0; Rz[6] = 0; Rz[7] = 0; Rz[8] = 1;
-    matmul3d(a.frames + 9 * bz, Rz, m1);
+    matmul3d(frames + 9 * bz, Rz, m1);
     if (bm) {
         for (int i = 0; i < 3; ++i) {
             m1[3 * i] = -m1[3 * i];
             m1[3 * i + 2] = -m1[3 * i + 2];
         }
     }
-    const double u0 = a.za[3 * bz], u1 = a.za[3 * bz + 1], u2 = a.za[3 * bz + 2];
+    const double u0 = za[3 * bz], u1 = za[3 * bz + 1], u2 = za[3 * bz + 2];
     double ax0 = u1 * wref[2] - u2 * wref[1];
     double ax1 = u2 * wref[0] - u0 * wref[2];
     double ax2 = u0 * wref[1] - u1 * wref[0];
@@ -669,7 +705,16 @@ __device__ __noinline__ void write_outputs(const SelectArgs& a, int64_t b, const
         for (int i = 0; i < 9; ++i) Tm[i] += sn * K[i] + (1.0 - cs) * K2[i];
     }
     matmul3d(Tm, m1, m2);
-    for (int i = 0; i < 9; ++i) a.out.orient[9 * o + i] = (float)m2[i];
+    for (int i = 0; i < 9; ++i) out.orient[9 * o + i] = (float)m2[i];
+}
+
+void launch_orient_compose(const acom_plan_s* p, const OrientIn* oin, int nb, int refine,
+                           acom_result out, int64_t off, cudaStream_t st) {
+    if (nb <= 0) return;
+    prof_begin(kKRefine, st);
+    k_orient_compose<<<(nb + 127) / 128, 128, 0, st>>>(oin, nb, p->N, refine, p->za, p->frames,
+                                                       out, off);
+    prof_end(kKRefine, st);
 }
 
 __host__ __device__ inline size_t sel_items(int F) {
@@ -731,20 +776,9 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_select_exact(SelectArgs a) {
         // by one shell on each side against rounding: every row the raster can
         // have made non-zero
         for (int w = threadIdx.x; w < (a.Spad >> 5); w += kSelThreads) sm.pmask[w] = 0u;
-        __syncthreads();
-        {
-            const int64_t p0 = a.row_ptr[b], p1 = a.row_ptr[b + 1];
-            for (int64_t m = p0 + threadIdx.x; m < p1; m += kSelThreads) {
-                const float r = sqrtf(a.qx[m] * a.qx[m] + a.qy[m] * a.qy[m]);
-                if (!(r < 1e30f)) continue;
-                int lo = (int)floorf((r - a.delta) / a.dq) - 2;
-                int hi = (int)ceilf((r + a.delta) / a.dq);
-                lo = lo < 0 ? 0 : lo;
-                hi = hi > a.S - 1 ? a.S - 1 : hi;
-                for (int s = lo; s <= hi; ++s) atomicOr(&sm.pmask[s >> 5], 1u << (s & 31));
-            }
-        }
-        // E_b: rounding margin valid for every axis.  FP16 operands add an
+        const int64_t p0 = a.row_ptr[b], p1 = a.row_ptr[b + 1];
+        // E_b: rounding margin valid for every axis (its partial sums load
+        // together with the bounds, before the first barrier).  FP16 operands add an
         // absolute term for values below the normal range: an operand x is off
         // by at most 2^-11 |x| + eta, so a dot product over Spad shells of
         // 2^e X^ and 2^k P^ gains eta sqrt(Spad) (2^e ||X^_bf|| + 2^k ||P^_zf||)
@@ -768,6 +802,15 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_select_exact(SelectArgs a) {
             sm.red[kSelWarps + warp] = ea;
         }
         __syncthreads();
+        for (int64_t m = p0 + threadIdx.x; m < p1; m += kSelThreads) {
+            const float r = sqrtf(a.qx[m] * a.qx[m] + a.qy[m] * a.qy[m]);
+            if (!(r < 1e30f)) continue;
+            int lo = (int)floorf((r - a.delta) / a.dq) - 2;
+            int hi = (int)ceilf((r + a.delta) / a.dq);
+            lo = lo < 0 ? 0 : lo;
+            hi = hi > a.S - 1 ? a.S - 1 : hi;
+            for (int s = lo; s <= hi; ++s) atomicOr(&sm.pmask[s >> 5], 1u << (s & 31));
+        }
         if (threadIdx.x == 0) {
             float t = 0.f, ta = 0.f;
             for (int w = 0; w < kSelWarps; ++w) {
@@ -875,9 +918,9 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_select_exact(SelectArgs a) {
             if (threadIdx.x == 0) sm.ev[bz] &= 3;
             __syncthreads();
         }
-        if (threadIdx.x == 0) {
-            if (a.n_eval) atomicAdd(a.n_eval, evals);
-            write_outputs(a, b, sm, want_ref);
+        if (warp == 0) {
+            if (lane == 0 && a.n_eval) atomicAdd(a.n_eval, evals);
+            write_outputs(a, b, sm, want_ref, lane);
         }
         __syncthreads();
     }
@@ -929,14 +972,14 @@ void launch_select_exact(const acom_plan_s* p, const float* Xsr, const float* Xs
                          const float* xnorm2, int nb,
                          float kappa, int refine, acom_result out, int64_t off, int* n_eval,
                          cudaStream_t st, const float* xscale, int rescore_top,
-                         const acom_peaks_csr* cp) {
+                         const acom_peaks_csr* cp, OrientIn* oin) {
     SelectArgs a{p->Psr, p->Psi, Xsr, Xsi, U, xfn, srange, pfmax, xnorm2, p->za, p->frames,
                  p->nbr_ptr,
                  p->nbr_idx, p->phase_off, p->n_phases, p->Z, p->F, p->N, p->S, p->Spad, nb, refine, kappa,
                  fft_radices(p->N), out, off, n_eval, xscale, 1.0f / p->pscale,
                  p->precision == ACOM_PREC_FP8 ? kFp8Shift : 1.0f,
                  (float)(p->precision == ACOM_PREC_FP8 ? kFp8Eta : kFp16Eta), rescore_top,
-                 p->smask, cp->row_ptr, cp->qx, cp->qy, (float)p->dq, (float)p->delta};
+                 p->smask, cp->row_ptr, cp->qx, cp->qy, (float)p->dq, (float)p->delta, oin};
     const size_t smem = select_smem_bytes(p->Z, p->N, p->F, p->Spad);
     set_max_dynamic_smem((const void*)k_select_exact, smem);
     int dev = 0, nsm = 0, per_sm = 0;
