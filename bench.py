@@ -715,16 +715,21 @@ def read_profile(lib, acom):
     return {e.name.decode(): (e.launches, e.total_ms) for e in arr}
 
 
-# DRAM bytes per pattern (read + write) of kernels whose traffic grows with
-# the patterns of a launch, from the ncu capture summarised in
-# profiles/ncu_full_fp16_au_scan_64x64_1deg.md, with a hash of the kernel's
+# DRAM bytes (read + write) of one launch of 16,384 patterns, from the
+# single-pass ncu capture of the full-size run summarised in
+# profiles/dram_fp16_au_scan_256x256_1deg.md, with a hash of the kernel's
 # sources at capture time, the precision and the workload of the captured
-# run: a changed kernel, or another precision or workload, reports no traffic.
-TRAFFIC_PER_PATTERN = {
-    "select_exact": (321362.0, ("match_prune.cu",), "6b57984d95e2ce61", "fp16",
-                     "au_scan_256x256_1deg"),
-    "raster_patterns": (340316.0, ("raster.cu",), "9e13818ce7a0dba0", "fp16",
-                        "au_scan_256x256_1deg"),
+# run: a changed kernel, or another precision or workload, reports no
+# traffic.  The last field says whether the traffic grows in proportion to
+# the patterns of a launch (then another chunk size is scaled); the
+# contraction's does not (the plan is re-read once per tile wave).
+TRAFFIC_PER_LAUNCH = {
+    "select_exact": (2.54e9 + 60.29e6, 16384, ("match_prune.cu",), "57adb74d7e5e33f6", "fp16",
+                     "au_scan_256x256_1deg", True),
+    "raster_patterns": (10.43e6 + 5.72e9, 16384, ("raster.cu",), "a6cb89414c136fb4", "fp16",
+                        "au_scan_256x256_1deg", True),
+    "contract_bf16": (3.56e9 + 57.53e6, 16384, ("match_tc.cu",), "3bf1531fe4c8a3f9", "fp16",
+                      "au_scan_256x256_1deg", False),
 }
 
 
@@ -739,12 +744,14 @@ def sources_hash(files):
 
 
 def kernel_traffic(name, pats, precision):
-    """DRAM bytes of one launch of ``pats`` patterns, scaled from the capture
-    (traffic of these kernels grows in proportion to the patterns), or None."""
-    t = TRAFFIC_PER_PATTERN.get(name)
-    if t is None or sources_hash(t[1]) != t[2] or precision != t[3] or W["name"] != t[4]:
+    """DRAM bytes of one launch of ``pats`` patterns: the captured launch's,
+    scaled to ``pats`` where traffic grows in proportion, else None."""
+    t = TRAFFIC_PER_LAUNCH.get(name)
+    if t is None or sources_hash(t[2]) != t[3] or precision != t[4] or W["name"] != t[5]:
         return None
-    return t[0] * pats
+    if abs(pats - t[1]) < 0.5:
+        return t[0]
+    return t[0] * pats / t[1] if t[6] else None
 
 
 def kernel_roofline(name, cnt, ms, peaks, src, B, K, nnz, precision, refine_pairs=0,
