@@ -29,8 +29,16 @@
 
 namespace acom {
 
+// A reflection of the plan: radius, angle, weight and squared excitation error.
 struct Peak {
     float r, gam, w, e;
+};
+
+// A pattern peak: no excitation error (12 bytes, so that a pattern's peak list
+// takes less shared memory).
+struct PeakXY {
+    float r, gam, w;
+    static constexpr float e = 0.f;
 };
 
 // Block-ordered compaction: returns this thread's slot among the threads with
@@ -58,12 +66,14 @@ __device__ inline int block_compact(bool keep, int* s_warp, int* total) {
 }
 
 struct PatternLoader {
+    using PeakT = PeakXY;
+    static constexpr int kMinBlocks = 3;   // FFT raster CTAs per SM (74.5 KB of shared memory)
     PatternSource src;
     __device__ void* xb_out() const { return src.xb; }
     __device__ int xb_tiles() const { return src.PTs; }
     __device__ bool xb_half() const { return src.xb_fp16 != 0; }
     __device__ float* xscale_out() const { return src.xscale; }
-    __device__ int load(int64_t item, Peak* sp, int* s_warp, int* err) const {
+    __device__ int load(int64_t item, PeakXY* sp, int* s_warp, int* err) const {
         const int64_t b0 = src.row_ptr[item];
         const int64_t b1 = src.row_ptr[item + 1];
         int64_t cnt = b1 - b0;
@@ -78,15 +88,14 @@ struct PatternLoader {
         const float half_omega = 0.5f * src.omega;
         for (int i = threadIdx.x; i < (int)cnt; i += blockDim.x) {
             float x = src.qx[b0 + i], y = src.qy[b0 + i], I = src.I[b0 + i];
-            Peak pk;
+            PeakXY pk;
             if (!(isfinite(x) && isfinite(y) && isfinite(I))) {
                 atomicOr(err, kErrNonFinite);
-                pk.r = 0.f; pk.gam = 0.f; pk.w = 0.f; pk.e = 0.f;
+                pk.r = 0.f; pk.gam = 0.f; pk.w = 0.f;
             } else {
                 pk.r = sqrtf(x * x + y * y);
                 pk.gam = atan2f(y, x);
                 pk.w = powf(pk.r, src.gamma_pow) * powf(fmaxf(I, 0.f), half_omega);
-                pk.e = 0.f;
             }
             sp[i] = pk;
         }
@@ -96,6 +105,8 @@ struct PatternLoader {
 };
 
 struct PlanLoader {
+    using PeakT = Peak;
+    static constexpr int kMinBlocks = 2;
     PlanSource src;
     float delta;
     __device__ void* xb_out() const { return nullptr; }
@@ -158,11 +169,12 @@ size_t raster_smem_bytes(int N, int F) {
 // one barrier): 2^e B <= kFp16Target with B = sum_m w_m n_m >= max |X^_sf|,
 // n_m = min(N, 2 delta / (max(r_m - delta, dq) dphi) + 3) the most bins a
 // peak's tent covers on any shell it reaches (tents are at most 1 and X >= 0).
-__device__ float fp16_pattern_scale(const Peak* sp, int np, const RasterGeom& geo, float dphi,
+template <class PeakT>
+__device__ float fp16_pattern_scale(const PeakT* sp, int np, const RasterGeom& geo, float dphi,
                                     int* red) {
     float b = 0.f;
     for (int i = threadIdx.x; i < np; i += blockDim.x) {
-        const Peak pk = sp[i];
+        const PeakT pk = sp[i];
         const float qmin = fmaxf(pk.r - geo.delta, geo.dq);
         const float n = fminf((float)geo.N, floorf(2.0f * geo.delta / (qmin * dphi)) + 3.0f);
         b = fmaf(fabsf(pk.w), n, b);
@@ -187,8 +199,9 @@ k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, int* err
     extern __shared__ __align__(16) unsigned char smem[];
     const int N = geo.N, F = geo.F, S = geo.S, Spad = geo.Spad;
     constexpr int W = kRasterThreads / 32;
-    Peak* sp = reinterpret_cast<Peak*>(smem);
-    Peak* ss = sp + kMaxPeaks;                                // sorted by radius
+    using PeakT = typename Loader::PeakT;
+    PeakT* sp = reinterpret_cast<PeakT*>(smem);
+    PeakT* ss = sp + kMaxPeaks;                               // sorted by radius
     float2* tw = reinterpret_cast<float2*>(ss + kMaxPeaks);   // (cos, sin) of 2 pi i / N
     float* tbuf = reinterpret_cast<float*>(tw + N);
     float* st_re = tbuf + W * 32;
@@ -262,7 +275,7 @@ k_raster_dft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, int* err
                     hi += __popc(__ballot_sync(0xffffffffu, r < qs + delta));
                 }
                 for (int m = lo; m < hi; ++m) {
-                    const Peak pk = ss[m];
+                    const PeakT pk = ss[m];
                     const float dr = pk.r - qs;
                     const float a2 = dr * dr + pk.e;
                     if (!(a2 < d2) || pk.w == 0.f) continue;          // tent is zero on this shell
@@ -439,15 +452,15 @@ static void launch_raster_nf(const RasterGeom& geo, const Loader& ld, int64_t n_
 // rows are separated by the conjugate symmetry of real transforms.
 // ---------------------------------------------------------------------------
 
-constexpr int kFftTile = 32;      // shells per BF16 staging tile: 16 pairs, two per warp
-constexpr int kFftStageWords = kFftTile / 2 + 1;   // words per staged row: 16 shell pairs + pad
+constexpr int kFftTile = 16;      // shells per 16-bit staging tile: 8 pairs, one per warp
+constexpr int kFftStageWords = kFftTile / 2 + 1;   // words per staged row: 8 shell pairs + pad
+constexpr int kPeakSortPerThread = (kMaxPeaks + kRasterThreads - 1) / kRasterThreads;
 constexpr int kMaxFPerLane = 12;  // F <= 361 (N <= 720)
 
-size_t raster_fft_smem_bytes(int N, int F) {
+size_t raster_fft_smem_bytes(int N, int F, size_t peak_bytes) {
     const int W = kRasterThreads / 32;
     size_t b = 0;
-    b += sizeof(Peak) * kMaxPeaks;                       // peaks as loaded
-    b += sizeof(int) * kMaxPeaks;                        // their order by radius
+    b += peak_bytes * kMaxPeaks;                         // peaks, sorted in place by radius
     b += sizeof(float2) * N;                             // twiddles
     b += sizeof(float2) * 2 * W * N;                     // per-warp row and transform buffer
     b += sizeof(uint32_t) * 2 * F * kFftStageWords;      // BF16 staging of a shell tile
@@ -456,16 +469,16 @@ size_t raster_fft_smem_bytes(int N, int F) {
 }
 
 template <class Loader>
-__global__ void __launch_bounds__(kRasterThreads, 2)
+__global__ void __launch_bounds__(kRasterThreads, Loader::kMinBlocks)
 k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix rad,
              int* err) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int N = geo.N, F = geo.F, S = geo.S, Spad = geo.Spad;
     const int Fs = shell_row_stride(F);
     constexpr int W = kRasterThreads / 32;
-    Peak* sp = reinterpret_cast<Peak*>(smem);
-    int* sidx = reinterpret_cast<int*>(sp + kMaxPeaks);
-    float2* tw = reinterpret_cast<float2*>(sidx + kMaxPeaks);
+    using PeakT = typename Loader::PeakT;
+    PeakT* sp = reinterpret_cast<PeakT*>(smem);
+    float2* tw = reinterpret_cast<float2*>(sp + kMaxPeaks);
     float2* zb = tw + N;
     float2* zt = zb + W * N;
     uint32_t* stage = reinterpret_cast<uint32_t*>(zt + W * N);   // [2F][kFftStageWords]
@@ -493,14 +506,30 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
 
     for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int np = ld.load(item, sp, s_int, err);
-        for (int i = threadIdx.x; i < np; i += blockDim.x) {
-            const float ri = sp[i].r;
-            int rank = 0;
-            for (int j = 0; j < np; ++j) {
-                const float rj = sp[j].r;
-                rank += (rj < ri) || (rj == ri && j < i);
+        // rank sort by (radius, index), in place: every thread holds its peaks
+        // and their ranks in registers across the barrier, then stores them
+        {
+            PeakT mine[kPeakSortPerThread];
+            int rk[kPeakSortPerThread];
+#pragma unroll
+            for (int k = 0; k < kPeakSortPerThread; ++k) {
+                const int i = threadIdx.x + k * kRasterThreads;
+                rk[k] = -1;
+                if (i < np) {
+                    mine[k] = sp[i];
+                    const float ri = mine[k].r;
+                    int rank = 0;
+                    for (int j = 0; j < np; ++j) {
+                        const float rj = sp[j].r;
+                        rank += (rj < ri) || (rj == ri && j < i);
+                    }
+                    rk[k] = rank;
+                }
             }
-            sidx[rank] = i;
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < kPeakSortPerThread; ++k)
+                if (rk[k] >= 0) sp[rk[k]] = mine[k];
         }
         if (threadIdx.x == 0) {
             s_int[40] = Spad;
@@ -544,7 +573,7 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
                     int lo = 0, hi = 0;
                     for (int base = 0; base < np; base += 32) {
                         const int m = base + lane;
-                        const float r = m < np ? sp[sidx[m]].r : CUDART_INF_F;
+                        const float r = m < np ? sp[m].r : CUDART_INF_F;
                         lo += __popc(__ballot_sync(0xffffffffu, r <= qA - delta));
                         hi += __popc(__ballot_sync(0xffffffffu, r < qhi + delta));
                     }
@@ -555,7 +584,7 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
                     // share the peak), so the half-warp syncs pair up; they order a
                     // bin's updates by different lanes for successive peaks
                     for (int m = lo + half; m < hi; m += 2) {
-                        const Peak pk = sp[sidx[m]];
+                        const PeakT pk = sp[m];
                         const float drA = pk.r - qA, drB = pk.r - qB;
                         const float a2A = fmaf(drA, drA, pk.e), a2B = fmaf(drB, drB, pk.e);
                         const bool inA = a2A < d2 && pk.w != 0.f, inB = vB && a2B < d2 && pk.w != 0.f;
@@ -688,12 +717,12 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
             if (xb) {
                 // the tile's BF16 copy in the tensor-core layout (64-pattern tiles whose
                 // 16-row groups hold 8 patterns' real rows, then their imaginary rows):
-                // 64 bytes (32 shells) per row
+                // 32 bytes (16 shells) per row
                 __syncthreads();
                 const int64_t tile = item / 64, r = item % 64;
                 const int64_t rbase = (r >> 3) * 16 + (r & 7);
-                for (int e = threadIdx.x; e < 2 * F * 4; e += blockDim.x) {
-                    const int row = e >> 2, q = e & 3;
+                for (int e = threadIdx.x; e < 2 * F * 2; e += blockDim.x) {
+                    const int row = e >> 1, q = e & 1;
                     const int c = row >= F, f = row - c * F;
                     const uint32_t* src = stage + row * kFftStageWords + 4 * q;
                     const uint4 v = make_uint4(src[0], src[1], src[2], src[3]);
@@ -744,7 +773,7 @@ static bool launch_raster_fft(const RasterGeom& geo, const Loader& ld, int64_t n
                               const RasterOut& out, int* err, cudaStream_t st, int cls) {
     const FftRadix rad = fft_radices(geo.N);
     if (rad.n == 0 || geo.Spad % kFftTile != 0 || geo.F > 32 * kMaxFPerLane) return false;
-    const size_t smem = raster_fft_smem_bytes(geo.N, geo.F);
+    const size_t smem = raster_fft_smem_bytes(geo.N, geo.F, sizeof(typename Loader::PeakT));
     if (smem > 227 * 1024) return false;
     set_max_dynamic_smem((const void*)k_raster_fft<Loader>, smem);
     int dev = 0, nsm = 0;
