@@ -724,11 +724,11 @@ def read_profile(lib, acom):
 # the patterns of a launch (then another chunk size is scaled); the
 # contraction's does not (the plan is re-read once per tile wave).
 TRAFFIC_PER_LAUNCH = {
-    "select_exact": (2.54e9 + 60.29e6, 16384, ("match_prune.cu",), "57adb74d7e5e33f6", "fp16",
+    "select_exact": (2.54e9 + 61.45e6, 16384, ("match_prune.cu",), "57adb74d7e5e33f6", "fp16",
                      "au_scan_256x256_1deg", True),
-    "raster_patterns": (10.43e6 + 5.72e9, 16384, ("raster.cu",), "a6cb89414c136fb4", "fp16",
+    "raster_patterns": (10.61e6 + 5.72e9, 16384, ("raster.cu",), "d1f5f69d85fbd3dc", "fp16",
                         "au_scan_256x256_1deg", True),
-    "contract_bf16": (3.56e9 + 57.53e6, 16384, ("match_tc.cu",), "3bf1531fe4c8a3f9", "fp16",
+    "contract_bf16": (3.56e9 + 57.51e6, 16384, ("match_tc.cu",), "3bf1531fe4c8a3f9", "fp16",
                       "au_scan_256x256_1deg", False),
 }
 
