@@ -488,3 +488,45 @@ def test_autotune_trials_and_tile_orders():
     for k in ("za_idx", "phi3_bin", "mirror", "score"):
         assert torch.equal(a[k], b[k]), k
     plan.close()
+
+
+def test_many_peaks_and_radius_ties(c1):
+    """Patterns at the 1024-peak limit and at counts that are not multiples
+    of the block size (several peaks per thread in the raster's radius sort),
+    with every radius present twice (peak pairs at opposite angles): polar
+    spectra and match scores against the oracle."""
+    rng = np.random.default_rng(77)
+    rows = []
+    for n in (1024, 777, 257, 2):
+        h = n // 2
+        r = rng.uniform(0.1, 1.45, h)
+        t = rng.uniform(-np.pi, np.pi, h)
+        x = np.concatenate([r * np.cos(t), -r * np.cos(t)])
+        y = np.concatenate([r * np.sin(t), -r * np.sin(t)])
+        i = rng.lognormal(0.0, 1.0, 2 * h)
+        perm = rng.permutation(2 * h)
+        rows.append((x[perm].astype(np.float32), y[perm].astype(np.float32),
+                     i[perm].astype(np.float32)))
+    rp = np.zeros(len(rows) + 1, dtype=np.int64)
+    rp[1:] = np.cumsum([len(r[0]) for r in rows])
+    qx = np.concatenate([r[0] for r in rows])
+    qy = np.concatenate([r[1] for r in rows])
+    I = np.concatenate([r[2] for r in rows])
+    scan = synth.Scan(rp, qx, qy, I, np.tile(np.eye(3), (len(rows), 1, 1)),
+                      np.zeros(len(rows), np.int32), (synth.au_fcc(),), "many peaks")
+    sp, xn = c1.polar_spectra(*to_dev(scan))
+    sp = sp.cpu().numpy()
+    oplan = oracle_plan("au_2deg_75x180")
+    prm = oplan.params
+    r = c1.match(*to_dev(scan))
+    sc = r["score"].cpu().numpy()
+    za = r["za_idx"].cpu().numpy()
+    kk = r["phi3_bin"].cpu().numpy()
+    mi = r["mirror"].cpu().numpy()
+    for b in range(scan.n_patterns):
+        X = O.polar_image(*scan.pattern(b), prm)
+        Xh = np.fft.rfft(X, axis=1)
+        assert rel_err(sp[b], np.stack([Xh.real, Xh.imag], axis=-1)) < 1e-5, b
+        mt = O.match_pattern(oplan, *scan.pattern(b))
+        assert math.isclose(sc[b], mt.score, rel_tol=1e-4), b
+        assert check_argmax(mt, za[b], kk[b], mi[b], 1e-5), b
