@@ -76,7 +76,8 @@ __device__ inline float2* warp_fft_forward(float2* src, float2* dst, int N, cons
 
 
 // Compile-time Stockham stages for the bin counts used in practice: constant
-// strides turn the index arithmetic into multiplies and shifts.
+// strides turn the index arithmetic into multiplies and shifts.  The rows must
+// start on a 16-byte boundary (the first stage stores 16 bytes at a time).
 template <int R>
 __device__ __forceinline__ void dft_small(float2* v) {
     if constexpr (R == 2) {
@@ -140,8 +141,17 @@ __device__ __forceinline__ void fft_stage(const float2* __restrict__ src, float2
         }
         dft_small<R>(v);
         const int idxD = jq * Ns * R + jm;
+        if constexpr (Ns == 1 && R % 2 == 0) {
+            // the first stage's outputs of a lane are consecutive: 16-byte
+            // stores (half the instructions and bank wavefronts of 8-byte ones)
+            float4* d4 = reinterpret_cast<float4*>(dst + idxD);
 #pragma unroll
-        for (int r = 0; r < R; ++r) dst[idxD + r * Ns] = v[r];
+            for (int r = 0; r < R / 2; ++r)
+                d4[r] = make_float4(v[2 * r].x, v[2 * r].y, v[2 * r + 1].x, v[2 * r + 1].y);
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) dst[idxD + r * Ns] = v[r];
+        }
     }
     __syncwarp();
 }

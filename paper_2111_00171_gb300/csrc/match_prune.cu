@@ -364,7 +364,8 @@ struct SelectArgs {
 };
 
 // Spectra c_dir + i c_mir of the batch's candidate axes, scaled by 1/N, into
-// the rows y[c] (both halves of the conjugate-symmetric spectrum).
+// the rows y[c] (both halves of the conjugate-symmetric spectrum), stored as
+// their complex conjugates.
 __device__ void batch_spectra(const SelectArgs& a, int64_t b, int nc, int s_lo, int s_hi,
                               SelSmem& sm) {
     const int F = a.F, N = a.N, Fq = shell_row_stride(F) >> 2;
@@ -461,23 +462,23 @@ __device__ void batch_spectra(const SelectArgs& a, int64_t b, int nc, int s_lo, 
         }
         const float dre = (A + B) * invN, dim = (C - D) * invN;
         const float mre = (A - B) * invN, mim = -(C + D) * invN;
+        // stored conjugated: the inverse transform runs as a forward one
         float2* y = sm.y + c * N;
-        y[f] = make_float2(dre - mim, dim + mre);
-        if (f > 0 && 2 * f < N) y[N - f] = make_float2(dre + mim, mre - dim);
+        y[f] = make_float2(dre - mim, -(dim + mre));
+        if (f > 0 && 2 * f < N) y[N - f] = make_float2(dre + mim, dim - mre);
     }
     __syncthreads();
 }
 
 // One warp per candidate: C_dir[k] + i C_mir[k] = sum_f y_f exp(2 pi i f k / N),
-// taken as the conjugate of the forward transform of conj(y); the argmax over
+// taken as the conjugate of the forward transform of conj(y) (the rows hold
+// conj(y)); the argmax over
 // (k, mirror) with the correlation at k - 1, k, k + 1 goes to res[c].
 __device__ void batch_transforms(const SelectArgs& a, int nc, SelSmem& sm) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, N = a.N;
     for (int c = warp; c < nc; c += kSelWarps) {
         float2* row = sm.y + c * N;
         float2* alt = sm.yt + c * N;
-        for (int i = lane; i < N; i += 32) row[i].y = -row[i].y;
-        __syncwarp();
         const float2* out;
         if (a.rad.n > 0) {
             out = warp_fft_fixed(row, alt, N, a.rad, sm.tw, lane);

@@ -551,9 +551,19 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
             // pairs warp and warp + W of the tile
             for (int pp = warp; pp < kFftTile / 2; pp += W) {
                 const int sA = t0 + 2 * pp;
-                for (int j = lane; j < N; j += 32) {
-                    z[j] = make_float2(0.f, 0.f);
-                    zz[j] = make_float2(0.f, 0.f);
+                // rows start on 16-byte boundaries (N even: 16-byte accesses)
+                if ((N & 1) == 0) {
+                    float4* z4 = reinterpret_cast<float4*>(z);
+                    float4* zz4 = reinterpret_cast<float4*>(zz);
+                    for (int j = lane; j < N / 2; j += 32) {
+                        z4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        zz4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                } else {
+                    for (int j = lane; j < N; j += 32) {
+                        z[j] = make_float2(0.f, 0.f);
+                        zz[j] = make_float2(0.f, 0.f);
+                    }
                 }
                 __syncwarp();
                 // One pass over the peaks reaching either shell of the pair (radius
@@ -657,12 +667,26 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
                 const bool any = anyA || anyB;
                 if (any) {
                     __syncwarp();
-                    for (int j = lane; j < N; j += 32) {
-                        const float2 u = zz[j];
-                        float2 v = z[j];
-                        v.x += u.x;
-                        v.y += u.y;
-                        z[j] = v;
+                    if ((N & 1) == 0) {
+                        float4* z4 = reinterpret_cast<float4*>(z);
+                        const float4* zz4 = reinterpret_cast<const float4*>(zz);
+                        for (int j = lane; j < N / 2; j += 32) {
+                            const float4 u = zz4[j];
+                            float4 v = z4[j];
+                            v.x += u.x;
+                            v.y += u.y;
+                            v.z += u.z;
+                            v.w += u.w;
+                            z4[j] = v;
+                        }
+                    } else {
+                        for (int j = lane; j < N; j += 32) {
+                            const float2 u = zz[j];
+                            float2 v = z[j];
+                            v.x += u.x;
+                            v.y += u.y;
+                            z[j] = v;
+                        }
                     }
                     __syncwarp();
                 }
