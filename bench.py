@@ -724,11 +724,11 @@ def read_profile(lib, acom):
 # the patterns of a launch (then another chunk size is scaled); the
 # contraction's does not (the plan is re-read once per tile wave).
 TRAFFIC_PER_LAUNCH = {
-    "select_exact": (2.54e9 + 61.45e6, 16384, ("match_prune.cu",), "57adb74d7e5e33f6", "fp16",
+    "select_exact": (2.54e9 + 61.46e6, 16384, ("match_prune.cu",), "6b63e7655bbedf67", "fp16",
                      "au_scan_256x256_1deg", True),
-    "raster_patterns": (10.61e6 + 5.72e9, 16384, ("raster.cu",), "d1f5f69d85fbd3dc", "fp16",
+    "raster_patterns": (10.39e6 + 5.72e9, 16384, ("raster.cu",), "56e2c3cbab7aa848", "fp16",
                         "au_scan_256x256_1deg", True),
-    "contract_bf16": (3.56e9 + 57.51e6, 16384, ("match_tc.cu",), "3bf1531fe4c8a3f9", "fp16",
+    "contract_bf16": (3.56e9 + 57.59e6, 16384, ("match_tc.cu",), "a6890ff94d6b0f7f", "fp16",
                       "au_scan_256x256_1deg", False),
 }
 
