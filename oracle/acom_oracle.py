@@ -51,9 +51,12 @@ misorientation_deg        symmetry-reduced misorientation (reading)
 
 Parity status: structure factors, plan, image, correlation and best match are
 pinned by the tests under ``tests/test_oracle_pins.py`` (closed forms, brute
-force, Cauchy-Schwarz self-indexing, grid recovery, symmetry).  ``refine`` is
-the one function whose formula the paper does not fix: parity unpinned beyond
-its own closed-form properties (exact parabola vertex, symmetric neighbours).
+force, Cauchy-Schwarz self-indexing, grid recovery, symmetry).  The paper
+fixes no formula for ``refine`` or ``misorientation_deg`` (readings): they are
+pinned by closed forms instead (exact parabola vertex, Rodrigues rotation,
+point-group closure, symmetry equivalents at zero angle, small rotations at
+their own angle) and by noiseless off-grid patterns refined closer to the
+truth than the grid on average.
 """
 
 from __future__ import annotations

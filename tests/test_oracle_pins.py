@@ -664,3 +664,63 @@ def test_single_pattern_second_match_is_weak(au_6deg_plan):
     res = O.match_multiple(plan, refl, qx, qy, I, 3, r_del=0.04, lam=LAM, sigma=AU["sigma"])
     assert len(res) >= 1
     assert all(r.reduced_score < 0.2 * res[0].reduced_score for r in res[1:])
+
+
+def _random_rotation(rng):
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+@pytest.mark.parametrize("kind,order", [("cubic", 24), ("hexagonal", 12)])
+def test_misorientation_metric_closed_forms(kind, order):
+    """Reading R13 pinned by closed forms: the proper point groups O and 622
+    have 24 and 12 distinct rotations and are closed under products; an
+    orientation and any symmetry equivalent of it are 0 apart; a small extra
+    rotation about any axis is its own angle apart (every non-identity
+    operation of these groups turns by at least 60 degrees, more than twice
+    the largest extra rotation tried); the in-plane Friedel twin m Rz(pi) is
+    0 apart once reduced over the twin.  Zero
+    angles are compared at 1e-4 degrees: the angle comes from acos of the
+    trace, which near the identity turns rounding of order 1e-16 into about
+    1e-6 degrees."""
+    ops = O.proper_point_group(kind)
+    assert len(ops) == order
+    for S in ops:
+        assert abs(np.linalg.det(S) - 1) < 1e-12
+        np.testing.assert_allclose(S @ S.T, np.eye(3), atol=1e-12)
+    keys = {tuple(np.round(S, 9).ravel()) for S in ops}
+    assert len(keys) == order
+    for A, B in itertools.product(ops, ops):
+        assert tuple(np.round(A @ B, 9).ravel()) in keys
+    rng = np.random.default_rng(13)
+    for _ in range(6):
+        m = _random_rotation(rng)
+        for S in ops:
+            assert O.misorientation_deg(S @ m, m, ops) < 1e-4
+        axis = rng.normal(size=3)
+        axis /= np.linalg.norm(axis)
+        theta = math.radians(rng.uniform(0.1, 20.0))
+        d = O.misorientation_deg(m @ O.so3_exp(theta * axis), m, ops)
+        assert abs(d - math.degrees(theta)) < 1e-6
+        assert O.misorientation_deg(m @ O.rot_z(math.pi), m, ops, True) < 1e-4
+
+
+def test_bench_misorientation_equals_the_oracle_definition():
+    """The vectorised metric the benchmark reports (host logic) equals the
+    oracle's definition pattern by pattern: the mean misorientation, the
+    mean reduced over the Friedel twin and the mean zone-axis tilt."""
+    import bench
+    rng = np.random.default_rng(21)
+    ops = O.proper_point_group("cubic")
+    truth = np.stack([_random_rotation(rng) for _ in range(12)])
+    est = np.stack([t @ O.so3_exp(rng.normal(scale=0.3, size=3)) for t in truth])
+    est[::3] = est[::3] @ O.rot_z(math.pi)          # some Friedel twins
+    m, mt, tilt = bench.misorientation(est.astype(np.float32), truth, ops)
+    ref = np.mean([O.misorientation_deg(e, t, ops) for e, t in zip(est, truth)])
+    ref_t = np.mean([O.misorientation_deg(e, t, ops, True) for e, t in zip(est, truth)])
+    ref_z = np.mean([O.za_tilt_error_deg(e, t, ops) for e, t in zip(est, truth)])
+    assert abs(m - ref) < 1e-3 and abs(mt - ref_t) < 1e-3 and abs(tilt - ref_z) < 1e-3
