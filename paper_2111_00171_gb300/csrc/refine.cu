@@ -91,7 +91,7 @@ struct Acc {
 
 // Adds reflection g's terms to acc: this lane sums over all M peaks.
 __device__ __forceinline__ void add_reflection(const RefArgs& a, const float R[9], float4 g,
-                                               float inv_r2, float half_inv_r2, bool exc,
+                                               float inv_r2, float l2_half_inv_r2, bool exc,
                                                float inv_se2, int64_t p0, int M, const float* px,
                                                const float* py, const float* pa, Acc& acc) {
     const float vx = R[0] * g.x + R[1] * g.y + R[2] * g.z;
@@ -111,7 +111,7 @@ __device__ __forceinline__ void add_reflection(const RefArgs& a, const float R[9
 #pragma unroll 4
     for (int m = 0; m < Ms; ++m) {               // every lane reads the same peak
         const float dx = px[m] - vx, dy = py[m] - vy;
-        const float e = pa[m] * expf(-(dx * dx + dy * dy) * half_inv_r2);
+        const float e = pa[m] * exp2f(-(dx * dx + dy * dy) * l2_half_inv_r2);
         sE += e;
         sEx = fmaf(e, dx, sEx);
         sEy = fmaf(e, dy, sEy);
@@ -120,7 +120,7 @@ __device__ __forceinline__ void add_reflection(const RefArgs& a, const float R[9
         const float x = a.qx[p0 + m], y = a.qy[p0 + m];
         const float w = peak_weight(x, y, a.I[p0 + m], a.gamma_pow, a.omega);
         const float dx = x - vx, dy = y - vy;
-        const float e = w * expf(-(dx * dx + dy * dy) * half_inv_r2);
+        const float e = w * exp2f(-(dx * dx + dy * dy) * l2_half_inv_r2);
         sE += e;
         sEx = fmaf(e, dx, sEx);
         sEy = fmaf(e, dy, sEy);
@@ -170,7 +170,9 @@ __device__ void score_at(const RefArgs& a, const float R[9], float rho, int64_t 
                          float grad[3], float H[6]) {
     const int lane = threadIdx.x & 31;
     const float inv_r2 = 1.0f / (rho * rho);
-    const float half_inv_r2 = 0.5f * inv_r2;
+    // exp(-x / (2 rho^2)) = 2^(-x log2(e) / (2 rho^2)): the spot Gaussian as one
+    // base-2 exponential of a pre-scaled argument
+    const float l2_half_inv_r2 = 0.5f * inv_r2 * 1.4426950408889634f;
     const bool exc = a.omega > 0.0f;
     const float inv_se2 = exc ? 1.0f / a.se2 : 0.0f;
     Acc acc{};
@@ -199,7 +201,7 @@ __device__ void score_at(const RefArgs& a, const float R[9], float rho, int64_t 
         __syncwarp();
         if (a.pairs && lane == 0) atomicAdd(a.pairs, (unsigned long long)n * (unsigned long long)M);
         for (int j = lane; j < n; j += 32)
-            add_reflection(a, R, __ldg(a.refl + act[j]), inv_r2, half_inv_r2, exc, inv_se2, p0, M,
+            add_reflection(a, R, __ldg(a.refl + act[j]), inv_r2, l2_half_inv_r2, exc, inv_se2, p0, M,
                            px, py, pa, acc);
         __syncwarp();
     }
@@ -344,7 +346,7 @@ __device__ int load_peaks(const RefArgs& a, int64_t b, int64_t& p0, float* px, f
     return M;
 }
 
-__global__ void __launch_bounds__(kRefWarps * 32) k_refine(RefArgs a) {
+__global__ void __launch_bounds__(kRefWarps * 32, 3) k_refine(RefArgs a) {
     __shared__ float s_px[kRefWarps][kRefPeakSmem], s_py[kRefWarps][kRefPeakSmem],
         s_pa[kRefWarps][kRefPeakSmem];
     __shared__ int s_act[kRefWarps][kRefActCap];
