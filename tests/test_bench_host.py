@@ -1,0 +1,41 @@
+"""Host logic of bench.py that the reported numbers depend on (CPU only):
+the algorithmic-bytes model of the exact evaluation and the traffic table.
+"""
+
+import numpy as np
+
+import bench
+import synth
+from oracle import acom_oracle as O
+
+
+def test_pattern_shell_rows_counts_the_rows_the_image_reaches():
+    """The non-zero shell rows that the select kernel's compulsory bytes are
+    counted from: every row where the oracle's polar image of the pattern is
+    non-zero is counted, and the count exceeds those rows by less than 1 %
+    (rows the tent reaches only at weight zero)."""
+    W = bench.W
+    scan = synth.grain_scan(1002, H=6, W=6, peaks="uniform10-60")
+    prm = O.PlanParams(W["S"], W["dq"], W["N"], W["delta"], lam=W["lam"])
+    rows = []
+    for b in range(scan.n_patterns):
+        X = O.polar_image(*scan.pattern(b), prm)
+        rows.append(int((np.abs(X).sum(axis=1) > 0).sum()))
+    est = bench.pattern_shell_rows(scan)
+    assert est >= np.mean(rows) - 1e-9
+    assert est <= 1.01 * np.mean(rows)
+
+
+def test_traffic_table_is_tied_to_its_sources():
+    """A traffic figure is reported only for the captured kernel sources,
+    precision and workload, and scaled only where it grows with the
+    patterns of a launch."""
+    for name, (byts, pats, files, digest, prec, wl, prop) in bench.TRAFFIC_PER_LAUNCH.items():
+        assert byts > 0 and pats > 0 and len(digest) == 16
+        ok = bench.sources_hash(files) == digest and bench.W["name"] == wl
+        t = bench.kernel_traffic(name, pats, prec)
+        assert (t == byts) if ok else (t is None)
+        half = bench.kernel_traffic(name, pats / 2, prec)
+        if ok:
+            assert (half == byts / 2) if prop else (half is None)
+        assert bench.kernel_traffic(name, pats, "bf16" if prec != "bf16" else "fp16") is None
