@@ -89,7 +89,7 @@ def test_random_patterns_three_rounds_match_oracle():
     scan = synth.random_patterns(1201, n_patterns=40)
     res = plan.match_multi(*to_dev(scan), n_matches=3, r_del=0.04)
     _compare(res, scan, op, 3, 0.04)
-    # the peaks are not changed: a plain match afterwards equals round 1
+    # the peaks are not changed: a plain match afterwards equals the first match
     import torch
     r = plan.match(*to_dev(scan))
     torch.cuda.synchronize()
