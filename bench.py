@@ -330,6 +330,13 @@ def cpu_baseline(scan, gpu_res, n_sample):
         f"{agree}/{n_sample}"
 
 
+def workload_config(scan):
+    """The workload keys of the JSON line's config, shared by both arms."""
+    return {"workload": W["text"], "patterns_per_gpu": scan.n_patterns,
+            "peaks_nnz": int(scan.row_ptr[-1]), "zone_axes": W["Z"], "shells": W["S"],
+            "n_phi": W["N"]}
+
+
 def rank_seed(rank):
     """Scan seed of ``rank`` under weak scaling: every rank its own scan."""
     return W["seed"] + rank
@@ -368,7 +375,9 @@ def reference_arm(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": W["text"], "patterns": scan.n_patterns},
+            "config": {**workload_config(scan), "precision": "fp64",
+                       "step": "plan build + match of every pattern, extrapolated from the "
+                               "sample"},
             "cpu_baseline": {"value": v, "unit": "patterns/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": "patterns/s", "h2d_bytes_per_step": 0,
@@ -533,9 +542,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "fp16": "f16", "bf16": "bf16"}[args.precision],
             "data": "synthetic",
-            "config": {"workload": W["text"], "patterns_per_gpu": B,
-                       "peaks_nnz": int(scan.row_ptr[-1]), "zone_axes": W["Z"], "shells": W["S"],
-                       "n_phi": W["N"], "precision": args.precision,
+            "config": {**workload_config(scan), "precision": args.precision,
                        "chunk": args.chunk or (1024 if args.exhaustive else 8192),
                        "autotuned": ({"chunk": tuned["chunk"], "tile_order": tuned["tile_order"],
                                       "trials_ms": {f"{t['chunk']}/{t['tile_order']}": round(t["ms"], 2)

@@ -39,3 +39,35 @@ def test_traffic_table_is_tied_to_its_sources():
         if ok:
             assert (half == byts / 2) if prop else (half is None)
         assert bench.kernel_traffic(name, pats, "bf16" if prec != "bf16" else "fp16") is None
+
+
+def test_reference_arm_line_keys(monkeypatch, capsys):
+    """The reference arm prints the contract's keys, with the GPU arm's
+    workload description (a tiny scan and sample keep this fast)."""
+    import argparse
+    import json
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("LOCAL_RANK", "0")
+    monkeypatch.setattr(bench, "oracle_plans", lambda stride=1: _tiny_plans())
+    bench.reference_arm(argparse.Namespace(warmup=0, steps=1, gpus=1, scan="4x4"))
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+              "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert {"workload", "patterns_per_gpu", "peaks_nnz", "zone_axes", "shells",
+            "n_phi"} <= set(line["config"])
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def _tiny_plans():
+    """A small oracle plan (6-degree grid, 40 shells, 72 bins) standing in for
+    the workload's plans, so that the test exercises the arm, not the oracle's
+    speed."""
+    refl = O.reflections(np.eye(3) * 4.08, [[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0]],
+                         [79.0] * 4, [0.25] * 4, 1.5)
+    v0, v1, v2, om = O.cubic_triangle()
+    za = O.zone_axis_grid(v0, v1, v2, 6.0, om)
+    return [O.orientation_plan(refl, za, O.PlanParams(40, 0.0375, 72, 0.08, lam=0.01969))]
