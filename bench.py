@@ -622,12 +622,12 @@ def sweep_combos(args, acom, lib, scan, d_in, flush, stream):
             ms = e0.elapsed_time(e1)
             lib.acom_profile_enable(0)
             prof = read_profile(lib, acom)
-            name = "contract_fp32" if prec == "fp32" else "contract_bf16"
+            name = "contract_fp32" if prec == "fp32" else "contract_tc"
             cnt, cms = prof.get(name, (0, 0.0))
             flops = 8.0 * Z * S * F * B
             tflops = flops / (cms / 1e3) / 1e12 if cms else 0.0
             # E4M3's dense rate is twice BF16's (4.5 vs 2.25 PFLOP/s nominal)
-            peak = fp32_peak if prec == "fp32" else peaks["bf16_tflops_sustained"] * \
+            peak = fp32_peak if prec == "fp32" else peaks["bf16_tflops"] * \
                 (2.0 if prec == "fp8" else 1.0)
             mis, mis_twin, tilt = misorientation(out["orient"].cpu().numpy(), scan.truth)
             agree = oracle_agreement(oracle, {k: out[k].cpu().numpy()
@@ -722,9 +722,9 @@ def read_profile(lib, acom):
     return {e.name.decode(): (e.launches, e.total_ms) for e in arr}
 
 
-# DRAM bytes (read + write) of one launch of 16,384 patterns, from the
-# single-pass ncu capture of the full-size run summarised in
-# profiles/dram_fp16_au_scan_256x256_1deg.md, with a hash of the kernel's
+# DRAM bytes (read + write) of one launch of 16,384 patterns, from a
+# single-pass ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# full-size run, with a hash of the kernel's
 # sources at capture time, the precision and the workload of the captured
 # run: a changed kernel, or another precision or workload, reports no
 # traffic.  The last field says whether the traffic grows in proportion to
@@ -735,7 +735,7 @@ TRAFFIC_PER_LAUNCH = {
                      "au_scan_256x256_1deg", True),
     "raster_patterns": (10.39e6 + 5.72e9, 16384, ("raster.cu",), "56e2c3cbab7aa848", "fp16",
                         "au_scan_256x256_1deg", True),
-    "contract_bf16": (3.56e9 + 57.59e6, 16384, ("match_tc.cu",), "a6890ff94d6b0f7f", "fp16",
+    "contract_tc": (3.56e9 + 57.59e6, 16384, ("match_tc.cu",), "a6890ff94d6b0f7f", "fp16",
                       "au_scan_256x256_1deg", False),
 }
 
@@ -770,10 +770,12 @@ def kernel_roofline(name, cnt, ms, peaks, src, B, K, nnz, precision, refine_pair
     avg_s = ms / cnt / 1e3 if cnt else float("nan")
     pats = B * K / cnt if cnt else 0          # patterns per launch
     fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    if name == "contract_bf16":
+    if name == "contract_tc":
+        # the kernel runs for a few ms at a time within a short step, at the
+        # maximum SM clock (clocks sampled beside): the burst peak applies
         work, unit, bound, peak = 8.0 * Z * S * F * pats, "TFLOP/s", "tensor", \
-            peaks["bf16_tflops_sustained"]
-        note = (f"8 Z S F flops per pattern; bf16 sustained peak, which FP16 operands "
+            peaks["bf16_tflops"]
+        note = (f"8 Z S F flops per pattern; bf16 burst peak, which FP16 operands "
                 f"share ({src})")
     elif name == "contract_fp32":
         work, unit, bound, peak = 8.0 * Z * S * F * pats, "TFLOP/s", "alu", fp32_peak

@@ -381,6 +381,14 @@ int32_t acom_profile_read(acom_profile_entry* out, int32_t max);
 int64_t acom_kernel_launches(void);
 
 /*
+ * acom_device_allocations - how many device-memory (stream-ordered pool) and
+ * pinned host allocations the library has requested in this process, whether
+ * the pool served them from cached blocks or not.  A diagnostic: a caller
+ * checks that a call allocated nothing by reading it before and after.
+ */
+int64_t acom_device_allocations(void);
+
+/*
  * Continuous refinement of orientations (the paper stops at the grid and its
  * sub-grid refinement; this makes the orientation a continuous variable).
  * The kinematical correlation score of a pattern with an orientation m
@@ -462,8 +470,11 @@ acom_status acom_bounds(acom_plan plan, const acom_peaks_csr* peaks, float* dst,
  * a host process whose device memory is held by another allocator (a
  * cudaMalloc there could fail or stall).  The plan must already exist; the
  * caller passes the peaks and ``dst`` ([n_patterns][Z] FP32, DEVICE), as for
- * acom_bounds.  FP32 and BF16 plans get their own precision's bounds; for an
- * FP16 plan the bounds are computed on the FP32 path.
+ * acom_bounds.  FP32 and BF16 plans get their own precision's bounds; FP16
+ * and FP8 (E4M3) plans get the bounds of the FP32 path (every plan keeps its
+ * FP32 spectra), i.e. the values an FP32 plan's acom_bounds returns.  Peak data
+ * are checked as for acom_bounds (row_ptr[0] == 0, monotone rows, finite values,
+ * at most 1024 peaks per pattern): a violation returns ACOM_ERR_BAD_INPUT.
  *
  * Scratch: the pattern spectra of one chunk live in a file-scope device array
  * of 32 MiB that every device loading the library keeps until the process
@@ -473,7 +484,10 @@ acom_status acom_bounds(acom_plan plan, const acom_peaks_csr* peaks, float* dst,
  *
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) and caches it; make that first call before any stream
- * capture.  All calls share the one array and leave the last call's contents
+ * capture.  With CUDA's lazy module loading (the default) that first call is
+ * also when the device commits the 32 MiB array and loads the modules of the
+ * kernels it launches, so the first call on each device belongs in set-up;
+ * later calls take no device memory.  All calls share the one array and leave the last call's contents
  * in it (every value a call reads it writes first), so calls whose work
  * overlaps on the GPU - on different streams, or from different threads -
  * race on the array and must be ordered by the caller.  The call performs no

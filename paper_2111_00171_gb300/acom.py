@@ -31,7 +31,7 @@ EXPORTED = ("acom_plan_create", "acom_plan_destroy", "acom_plan_get_info",
             "acom_version", "acom_profile_enable", "acom_profile_reset", "acom_profile_read",
             "acom_kernel_launches", "acom_plan_concat", "acom_plan_get_phases", "acom_refine",
             "acom_refine_defaults", "acom_kinematical_score", "acom_match_multi",
-            "acom_match_async", "acom_sync", "acom_autotune")
+            "acom_match_async", "acom_sync", "acom_autotune", "acom_device_allocations")
 
 
 class AcomError(RuntimeError):
@@ -139,6 +139,7 @@ def load_library():
     lib.acom_profile_enable.restype = None
     lib.acom_profile_reset.restype = None
     lib.acom_kernel_launches.restype = C.c_int64
+    lib.acom_device_allocations.restype = C.c_int64
     lib.acom_status_str.restype = C.c_char_p
     lib.acom_status_str.argtypes = [C.c_int]
     lib.acom_last_error.restype = C.c_char_p
@@ -320,8 +321,18 @@ class Plan:
 
     def bounds_static(self, row_ptr, qx, qy, I, out, stream=None):
         """acom_bounds_static into the caller's [B][Z] tensor ``out`` (no device
-        allocation inside the library call)."""
+        allocation inside the library call).  ``out`` must be a contiguous
+        float32 CUDA tensor of shape (B, n_za) on the device current for the
+        plan: the library writes B x n_za values through its pointer."""
+        import torch
         pk = self._csr(row_ptr, qx, qy, I)
+        shape = (pk.n_patterns, self.info["n_za"])
+        if (not isinstance(out, torch.Tensor) or not out.is_cuda
+                or out.device.index != torch.cuda.current_device()
+                or out.dtype != torch.float32 or not out.is_contiguous()
+                or tuple(out.shape) != shape):
+            raise ValueError(f"out must be a contiguous float32 CUDA tensor of shape {shape} "
+                             "on the current device")
         _check(self._lib.acom_bounds_static(self.handle, C.byref(pk), _ptr(out),
                                             _stream_ptr(stream)))
         return out

@@ -231,6 +231,10 @@ inline void set_max_dynamic_smem(const void* func, size_t bytes) {
 // ---- error reporting (api.cu) ----
 acom_status set_error(acom_status s, const std::string& msg);
 acom_status cuda_error(cudaError_t e, const char* what);
+void clear_error();                 // acom_last_error() returns "" afterwards
+void count_allocation();            // one device or pinned allocation requested
+// device check that row_ptr[0] == 0 (sets kErrRowPtr in err); allocates nothing
+void launch_check_row0(const int64_t* row_ptr, int* err, cudaStream_t st);
 
 // ---- launchers (defined in the .cu files) ----
 // plan.cu

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -22,6 +23,12 @@ acom_status cuda_error(cudaError_t e, const char* what) {
     g_last_error = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
     return e == cudaErrorMemoryAllocation ? ACOM_ERR_OOM : ACOM_ERR_CUDA;
 }
+
+void clear_error() { g_last_error.clear(); }
+
+// device and pinned allocations the library has requested (acom_device_allocations)
+static std::atomic<long long> g_allocs{0};
+void count_allocation() { g_allocs.fetch_add(1, std::memory_order_relaxed); }
 
 static void normalize3(double* v) {
     double n = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
@@ -115,6 +122,7 @@ static cudaMemPool_t device_pool() {
 
 cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t st) {
     *p = nullptr;
+    count_allocation();
     cudaMemPool_t pool = device_pool();
     if (!pool) return cudaErrorMemoryAllocation;
     return cudaMallocFromPoolAsync(p, bytes ? bytes : 1, pool, st);
@@ -245,6 +253,18 @@ static void destroy_plan(acom_plan_s* p) {
 
 static bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
+// The first row pointer of a CSR batch must be 0 (the other row checks run in
+// the raster, per pattern); one thread, no allocation.
+__global__ void k_check_row0(const int64_t* row_ptr, int* err) {
+    if (row_ptr[0] != 0) atomicOr(err, kErrRowPtr);
+}
+
+void launch_check_row0(const int64_t* row_ptr, int* err, cudaStream_t st) {
+    prof_begin(kKMisc, st);
+    k_check_row0<<<1, 1, 0, st>>>(row_ptr, err);
+    prof_end(kKMisc, st);
+}
+
 }  // namespace acom
 
 using namespace acom;
@@ -252,6 +272,8 @@ using namespace acom;
 extern "C" {
 
 int32_t acom_version(void) { return 1; }
+
+int64_t acom_device_allocations(void) { return (int64_t)g_allocs.load(); }
 
 const char* acom_status_str(acom_status s) {
     switch (s) {
@@ -361,6 +383,7 @@ acom_status acom_plan_create(const acom_crystal* crystal, const acom_za_grid* gr
     ACOM_CK(dalloc(&p->pfmax, (size_t)p->F, &p->bytes, st));
     p->phase_off_host = {0, Z};
     ACOM_CK(dalloc(&p->phase_off, 2, &p->bytes, st));
+    count_allocation();
     ACOM_CK(cudaMallocHost(reinterpret_cast<void**>(&p->host_words), 2 * sizeof(int)));
     p->host_words[0] = p->host_words[1] = 0;
     ACOM_CK(cudaMemcpyAsync(p->phase_off, p->phase_off_host.data(), sizeof(int) * 2,
@@ -505,6 +528,7 @@ acom_status acom_plan_concat(const acom_plan* plans, int32_t n_plans, void* cuda
     ACOM_CK(dalloc(&p->err, 1, &p->bytes, st));
     ACOM_CK(dalloc(&p->pfmax, (size_t)F, &p->bytes, st));
     ACOM_CK(dalloc(&p->phase_off, p->phase_off_host.size(), &p->bytes, st));
+    count_allocation();
     ACOM_CK(cudaMallocHost(reinterpret_cast<void**>(&p->host_words), 2 * sizeof(int)));
     p->host_words[0] = p->host_words[1] = 0;
     ACOM_CK(cudaMemsetAsync(p->Pr, 0, sizeof(float) * pelems, st));
@@ -642,9 +666,6 @@ static acom_status read_error_word(acom_plan_s* p, cudaStream_t st) {
     return ACOM_OK;
 }
 
-__global__ void k_check_row0(const int64_t* row_ptr, int* err) {
-    if (row_ptr[0] != 0) atomicOr(err, kErrRowPtr);
-}
 
 acom_status acom_polar_spectra(acom_plan p, const acom_peaks_csr* peaks, float* dst, float* xnorm,
                                void* cuda_stream) {
@@ -659,9 +680,7 @@ acom_status acom_polar_spectra(acom_plan p, const acom_peaks_csr* peaks, float* 
     s = ensure_workspace(p, chunk, false, true, st);
     if (s != ACOM_OK) return s;
     cudaMemsetAsync(p->err, 0, sizeof(int), st);
-    prof_begin(kKMisc, st);
-    k_check_row0<<<1, 1, 0, st>>>(peaks->row_ptr, p->err);
-    prof_end(kKMisc, st);
+    launch_check_row0(peaks->row_ptr, p->err, st);
     RasterGeom geo{p->S, p->Spad, p->N, p->F, (float)p->dq, (float)p->delta, (float)p->gamma_pow, 0};
     for (int64_t c0 = 0; c0 < B; c0 += chunk) {
         const int nb = (int)std::min<int64_t>(chunk, B - c0);
@@ -769,9 +788,7 @@ static acom_status match_enqueue(acom_plan p, const acom_peaks_csr* peaks,
     if (s != ACOM_OK) return s;
     cudaMemsetAsync(p->err, 0, sizeof(int), st);
     cudaMemsetAsync(p->ws.n_eval, 0, sizeof(int), st);
-    prof_begin(kKMisc, st);
-    k_check_row0<<<1, 1, 0, st>>>(peaks->row_ptr, p->err);
-    prof_end(kKMisc, st);
+    launch_check_row0(peaks->row_ptr, p->err, st);
     RasterGeom geo{p->S, p->Spad, p->N, p->F, (float)p->dq, (float)p->delta, (float)p->gamma_pow, 0};
     const int wchunk = p->ws.chunk;
     for (int64_t c0 = 0; c0 < B; c0 += chunk) {
@@ -889,9 +906,7 @@ acom_status acom_bounds(acom_plan p, const acom_peaks_csr* peaks, float* dst, vo
     s = ensure_workspace(p, chunk, false, !tc, st);
     if (s != ACOM_OK) return s;
     cudaMemsetAsync(p->err, 0, sizeof(int), st);
-    prof_begin(kKMisc, st);
-    k_check_row0<<<1, 1, 0, st>>>(peaks->row_ptr, p->err);
-    prof_end(kKMisc, st);
+    launch_check_row0(peaks->row_ptr, p->err, st);
     RasterGeom geo{p->S, p->Spad, p->N, p->F, (float)p->dq, (float)p->delta, (float)p->gamma_pow, 0};
     for (int64_t c0 = 0; c0 < B; c0 += chunk) {
         const int nb = (int)std::min<int64_t>(chunk, B - c0);
@@ -936,9 +951,7 @@ acom_status acom_refine(acom_plan p, const acom_peaks_csr* peaks, const acom_ref
     if (s != ACOM_OK) return s;
     cudaMemsetAsync(p->err, 0, sizeof(int), st);
     cudaMemsetAsync(p->refine_pairs, 0, sizeof(unsigned long long), st);
-    prof_begin(kKMisc, st);
-    k_check_row0<<<1, 1, 0, st>>>(peaks->row_ptr, p->err);
-    prof_end(kKMisc, st);
+    launch_check_row0(peaks->row_ptr, p->err, st);
     launch_refine_orient(p, peaks, o.steps, o.rho_start, o.rho_end, o.damping,
                          (float)(o.max_step_deg * M_PI / 180.0), o.twin ? 1 : 0, orient,
                          orient_alt, score, start, st);
@@ -964,9 +977,7 @@ acom_status acom_kinematical_score(acom_plan p, const acom_peaks_csr* peaks, con
     s = refine_table(p, st);
     if (s != ACOM_OK) return s;
     cudaMemsetAsync(p->err, 0, sizeof(int), st);
-    prof_begin(kKMisc, st);
-    k_check_row0<<<1, 1, 0, st>>>(peaks->row_ptr, p->err);
-    prof_end(kKMisc, st);
+    launch_check_row0(peaks->row_ptr, p->err, st);
     launch_kin_score(p, peaks, orient, r, rho, score, grad, gn, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "score launch");

@@ -57,6 +57,7 @@ using namespace acom;
 
 extern "C" acom_status acom_bounds_static(acom_plan p, const acom_peaks_csr* peaks, float* dst,
                                           void* cuda_stream) {
+    clear_error();
     if (!p || !dst) return set_error(ACOM_ERR_INVALID_ARG, "null argument");
     if (!peaks) return set_error(ACOM_ERR_INVALID_ARG, "null peaks");
     if (peaks->n_patterns < 0) return set_error(ACOM_ERR_INVALID_ARG, "n_patterns < 0");
@@ -95,7 +96,13 @@ extern "C" acom_status acom_bounds_static(acom_plan p, const acom_peaks_csr* pea
         if (s != ACOM_OK) return s;
     }
     prof_suppress(true);
-    cudaMemsetAsync(p->err, 0, sizeof(int), st);
+    cudaError_t e = cudaMemsetAsync(p->err, 0, sizeof(int), st);
+    if (e != cudaSuccess) {
+        prof_suppress(false);
+        return cuda_error(e, "bounds_static: clearing the error word");
+    }
+    // row_ptr[0] == 0 (the raster checks the rest of the row pointers)
+    launch_check_row0(peaks->row_ptr, p->err, st);
     RasterGeom geo{p->S, p->Spad, p->N, p->F, (float)p->dq, (float)p->delta, (float)p->gamma_pow, 0};
     for (int64_t c0 = 0; c0 < B; c0 += chunk) {
         const int nb = (int)std::min<int64_t>(chunk, B - c0);
@@ -113,7 +120,7 @@ extern "C" acom_status acom_bounds_static(acom_plan p, const acom_peaks_csr* pea
             launch_contract_bound_fp32(p, Xr, Xi, nb, U, st);
     }
     prof_suppress(false);
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "bounds_static launch");
     int herr = 0;
     e = cudaMemcpyAsync(&herr, p->err, sizeof(int), cudaMemcpyDeviceToHost, st);

@@ -25,7 +25,7 @@ cudaEvent_t g_open[kKCount];
 bool g_has_open[kKCount] = {};
 const char* kNames[kKCount] = {"reflections", "raster_plan", "scale_plan", "raster_patterns",
                                "contract_fp32", "idft_argmax_fp32", "refine", "misc",
-                               "contract_bf16", "idft_argmax_bf16", "rescore_fp32", "select_exact",
+                               "contract_tc", "idft_argmax_tc", "rescore_fp32", "select_exact",
                                "refine_orient"};
 
 cudaEvent_t take() {
