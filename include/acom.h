@@ -389,6 +389,20 @@ int64_t acom_kernel_launches(void);
 int64_t acom_device_allocations(void);
 
 /*
+ * acom_set_device_wait_limit - failure detection of the tensor-core
+ * contraction.  Its producer, MMA-issuing and epilogue roles wait on each
+ * other through shared-memory barriers, every wait bounded by a budget of
+ * clock cycles (default, cycles <= 0: 4e9, about 2 s).  A wait that runs out
+ * sets the device error word and stops every role of its CTA; the CTA then
+ * waits (always with the full budget) for its copies and MMAs in flight,
+ * frees its tensor memory and exits, and the call returns ACOM_ERR_TIMEOUT
+ * with the plan still usable.  A short budget makes a wait run out on
+ * purpose (tests of that path); it applies to later launches of this
+ * process.  Not thread-safe.
+ */
+void acom_set_device_wait_limit(int64_t cycles);
+
+/*
  * Continuous refinement of orientations (the paper stops at the grid and its
  * sub-grid refinement; this makes the orientation a continuous variable).
  * The kinematical correlation score of a pattern with an orientation m

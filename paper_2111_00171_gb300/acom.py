@@ -31,7 +31,8 @@ EXPORTED = ("acom_plan_create", "acom_plan_destroy", "acom_plan_get_info",
             "acom_version", "acom_profile_enable", "acom_profile_reset", "acom_profile_read",
             "acom_kernel_launches", "acom_plan_concat", "acom_plan_get_phases", "acom_refine",
             "acom_refine_defaults", "acom_kinematical_score", "acom_match_multi",
-            "acom_match_async", "acom_sync", "acom_autotune", "acom_device_allocations")
+            "acom_match_async", "acom_sync", "acom_autotune", "acom_device_allocations",
+            "acom_set_device_wait_limit")
 
 
 class AcomError(RuntimeError):
@@ -140,6 +141,8 @@ def load_library():
     lib.acom_profile_reset.restype = None
     lib.acom_kernel_launches.restype = C.c_int64
     lib.acom_device_allocations.restype = C.c_int64
+    lib.acom_set_device_wait_limit.argtypes = [C.c_int64]
+    lib.acom_set_device_wait_limit.restype = None
     lib.acom_status_str.restype = C.c_char_p
     lib.acom_status_str.argtypes = [C.c_int]
     lib.acom_last_error.restype = C.c_char_p

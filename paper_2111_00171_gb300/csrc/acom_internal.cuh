@@ -264,6 +264,8 @@ void launch_plan_shell_mask(const acom_plan_s* p, cudaStream_t st);
 acom_status make_bf16_map(void* map_storage, const void* base, uint64_t rows, uint64_t cols,
                           int kind = 0);
 void launch_half_to_e4m3(const void* src, void* dst, int64_t n, float mul, cudaStream_t st);
+// budget in clock cycles of the tensor-core contraction's pipeline waits (0: default)
+void set_wait_cycles(long long cycles);
 // xscale: per-pattern 2^e of FP16 pattern spectra (nullptr: BF16, no scale)
 void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_stride, int nb,
                               float* U, cudaStream_t st, const float* xscale = nullptr,

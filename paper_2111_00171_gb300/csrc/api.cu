@@ -275,6 +275,8 @@ int32_t acom_version(void) { return 1; }
 
 int64_t acom_device_allocations(void) { return (int64_t)g_allocs.load(); }
 
+void acom_set_device_wait_limit(int64_t cycles) { set_wait_cycles((long long)cycles); }
+
 const char* acom_status_str(acom_status s) {
     switch (s) {
         case ACOM_OK: return "ACOM_OK";

@@ -96,15 +96,16 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait; false on timeout (recorded) or when another role aborted.
+// Bounded wait of at most `budget` clock cycles; false on timeout (recorded)
+// or when another role aborted.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                          int* err) {
+                                          int* err, long long budget) {
     if (mbar_try(bar, parity)) return true;
     const long long t0 = clock64();
     for (;;) {
         if (mbar_try(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (clock64() - t0 > kWaitCycles) {
+        if (clock64() - t0 > budget) {
             atomicOr(err, kErrTimeout);
             *abort_flag = 1;
             return false;
@@ -250,6 +251,8 @@ struct TcArgs {
     float inv_pscale;              // 2^-k of the plan operand's scale (1 for BF16)
     int zmajor;                    // tile order: 0 consecutive tiles share a pattern
                                    // tile, 1 they share an axis tile
+    long long wait_cycles;         // budget of each pipeline wait (the drain waits
+                                   // that precede the exit always take kWaitCycles)
 };
 
 // F8: E4M3 operands (kind::f8f6f4, 128 elements per K tile), else 16-bit
@@ -321,7 +324,7 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
                     const int xrow = (f * a.PTs + pt) * 128;
                     const int own = fcount & 1;
                     for (int kt = 0; kt < a.KT; ++kt) {
-                        if (!mbar_wait(smem_u32(empty + stage), phase ^ 1u, abort_flag, a.err)) {
+                        if (!mbar_wait(smem_u32(empty + stage), phase ^ 1u, abort_flag, a.err, a.wait_cycles)) {
                             ok = false;
                             break;
                         }
@@ -378,7 +381,7 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
                         stage = (stage + a.KT) % kStages;
                         continue;
                     }
-                    if (!mbar_wait(smem_u32(tempty + mi), tph ^ 1u, abort_flag, a.err)) {
+                    if (!mbar_wait(smem_u32(tempty + mi), tph ^ 1u, abort_flag, a.err, a.wait_cycles)) {
                         ok = false;
                         break;
                     }
@@ -387,7 +390,7 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
                     const uint32_t dacc = tmem + mi * 256;
                     for (int kt = 0; kt < a.KT; ++kt) {
                         if (!mbar_wait(smem_u32(myfull + stage), (fpar >> stage) & 1u, abort_flag,
-                                       a.err)) {
+                                       a.err, a.wait_cycles)) {
                             ok = false;
                             break;
                         }
@@ -440,7 +443,7 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
             const int pt = a.zmajor ? t % a.PT : t / a.ZT;
             for (int f = 0; f < a.F; ++f, ++fcount) {
                 const int buf = fcount & 1;
-                if (!mbar_wait(smem_u32(tfull + buf), tph[buf], abort_flag, a.err)) {
+                if (!mbar_wait(smem_u32(tfull + buf), tph[buf], abort_flag, a.err, a.wait_cycles)) {
                     ok = false;
                     break;
                 }
@@ -553,6 +556,11 @@ acom_status make_bf16_map(void* map_storage, const void* base, uint64_t rows, ui
 
 size_t tensor_map_bytes() { return sizeof(CUtensorMap); }
 
+// Budget of the contraction's pipeline waits (acom_set_device_wait_limit);
+// 0: the default of about 2 s.  Process-global.
+static long long g_wait_cycles = 0;
+void set_wait_cycles(long long cycles) { g_wait_cycles = cycles > 0 ? cycles : 0; }
+
 void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_stride, int nb,
                               float* U, cudaStream_t st, const float* xscale, int tile_order) {
     tc::TcArgs a;
@@ -576,6 +584,7 @@ void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_st
     a.xscale = xscale;
     a.xs_mul = f8 ? kFp8Shift : 1.0f;
     a.inv_pscale = 1.0f / p->pscale;
+    a.wait_cycles = g_wait_cycles > 0 ? g_wait_cycles : tc::kWaitCycles;
     const size_t smem = tc::tc_smem_bytes();
     auto kern = f8 ? tc::k_contract_bound_tc<true> : tc::k_contract_bound_tc<false>;
     set_max_dynamic_smem((const void*)kern, smem);

@@ -167,7 +167,7 @@ def test_mixed_full_size(precision):
     diff = np.nonzero(np.any(ka != kb, axis=1))[0]
     assert len(diff) <= 0.001 * len(ka), len(diff)
     op = _oracles("mg_1deg_75x180")
-    for i in diff[:4]:
+    for i in diff:          # every difference must be a documented tie in the oracle
         g = _global(O.match_multi(op, *scan.pattern(i)))
         assert check_argmax(g, *ka[i]) and check_argmax(g, *kb[i]), i
     rng = np.random.default_rng(3)

@@ -377,7 +377,7 @@ def test_full_size_tc_equals_fp32(full_scan, precision):
     assert len(diff) <= 0.001 * len(ka), len(diff)
     np.testing.assert_allclose(a["score"].cpu().numpy(), b["score"].cpu().numpy(), rtol=1e-5)
     op = oracle_plan("au_1deg_150x360")
-    for i in diff[:8]:
+    for i in diff:          # every difference must be a documented tie in the oracle
         mt = O.match_pattern(op, *full_scan.pattern(i))
         assert check_argmax(mt, *ka[i]) and check_argmax(mt, *kb[i]), i
     ev = p16.get_info()["last_evaluated"] / full_scan.n_patterns

@@ -1,0 +1,188 @@
+"""Parity of the CUDA path with the FP64 oracle at the geometries and sizes the
+benchmark times: the 1-degree plan (903 zone axes, 150 shells, 360 bins) with
+the 256 x 256 scan in the benchmark's launch configuration, and the
+0.5-degree plan (3486 zone axes) with the 512 x 512 scan.  The oracle runs in
+a pool of host processes (tests/oracle_pool.py).
+
+Tolerances as in test_gpu_parity: spectra within 1e-5 of their largest
+magnitude, scores within 1e-4 relative, the argmax exact except at documented
+ties (the oracle's own value at the GPU's choice within 1e-5 relative of its
+maximum).
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import acom_oracle as O
+
+from gpu_common import CONFIGS, gpu_plan, oracle_plan, rel_err, to_dev
+from oracle_pool import oracle_matches
+
+pytestmark = pytest.mark.gpu
+
+CONFIGS.setdefault("au_halfdeg_150x360", (0.5, 150, 0.01, 360))
+KEYS = ("za_idx", "phi3_bin", "mirror")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+
+
+@pytest.fixture(scope="module")
+def full_scan():
+    return synth.grain_scan(1002)
+
+
+def _choices(r):
+    return np.stack([r[k].cpu().numpy().astype(np.int64) for k in KEYS], 1)
+
+
+def _check_against_pool(res, choices, scores, idx, label):
+    """Argmax exact or a documented tie; score within 1e-4 relative."""
+    exact = ties = 0
+    for j, b in enumerate(idx):
+        za, k, m, score, val = res[int(b)]
+        c = tuple(int(v) for v in choices[j])
+        if c == (za, k, m):
+            exact += 1
+        else:
+            assert val >= score - 1e-5 * abs(score), (label, int(b), c, (za, k, m), val, score)
+            ties += 1
+        assert math.isclose(float(scores[j]), score, rel_tol=1e-4), (label, int(b))
+    print(f"{label}: {exact} exact, {ties} documented ties of {len(idx)}")
+    return exact, ties
+
+
+def test_plan_spectra_at_benchmark_geometry():
+    """The 1-degree plan's spectra (903 axes x 150 shells x 181 frequencies,
+    the N = 360 transform) element by element against the oracle."""
+    plan = gpu_plan("au_1deg_150x360")
+    op = oracle_plan("au_1deg_150x360")
+    sp = plan.spectra().cpu().numpy()
+    ref = np.stack([op.P_hat.real, op.P_hat.imag], axis=-1)
+    assert sp.shape == ref.shape == (903, 150, 181, 2)
+    err = np.abs(sp - ref).max(axis=(1, 2, 3)) / np.abs(ref).max()
+    print(f"plan spectra: max rel err {err.max():.2e}")
+    assert err.max() < 1e-5, int(err.argmax())
+    plan.close()
+
+
+def test_pattern_spectra_at_benchmark_geometry(full_scan):
+    """Pattern spectra of the scan (150 shells, N = 360) against the oracle's
+    polar image and its FFT, for 96 patterns spread over the scan."""
+    plan = gpu_plan("au_1deg_150x360")
+    prm = oracle_plan("au_1deg_150x360").params
+    idx = np.random.default_rng(5).choice(full_scan.n_patterns, 96, replace=False)
+    sub = full_scan.subset(idx)
+    sp, xn = plan.polar_spectra(*to_dev(sub))
+    sp = sp.cpu().numpy()
+    xn = xn.cpu().numpy()
+    worst = 0.0
+    for j in range(sub.n_patterns):
+        X = O.polar_image(*sub.pattern(j), prm)
+        Xh = np.fft.rfft(X, axis=1)
+        e = rel_err(sp[j], np.stack([Xh.real, Xh.imag], axis=-1))
+        worst = max(worst, e)
+        assert e < 1e-5, (j, e)
+        assert math.isclose(xn[j], np.sqrt((X * X).sum()), rel_tol=1e-5)
+    print(f"pattern spectra: max rel err {worst:.2e}")
+    plan.close()
+
+
+def test_headline_scan_1024_patterns_against_oracle(full_scan):
+    """The benchmark's default path (FP16 operands, certified pruning, chunks
+    of 16,384 patterns, the first tile order) on the whole 256 x 256 scan; 1,024
+    patterns sampled over the scan are matched by the oracle."""
+    import torch
+    plan = gpu_plan("au_1deg_150x360", precision=2)
+    r = plan.match(*to_dev(full_scan), chunk=16384, tile_order=0)
+    torch.cuda.synchronize()
+    idx = np.sort(np.random.default_rng(11).choice(full_scan.n_patterns, 1024, replace=False))
+    ch = _choices(r)[idx]
+    sc = r["score"].cpu().numpy()[idx]
+    res = oracle_matches("au_1deg_150x360", full_scan, idx, ch, workers=12)
+    exact, _ = _check_against_pool(res, ch, sc, idx, "1-degree FP16 headline")
+    assert exact >= 0.95 * len(idx)
+    plan.close()
+
+
+@pytest.fixture(scope="module")
+def sweep_head():
+    """The first 300 patterns of the 512 x 512 scan (Poisson(30) peaks)."""
+    scan = synth.grain_scan(1005, H=512, W=512, peaks="poisson30")
+    return scan.subset(np.arange(300))
+
+
+def test_halfdeg_plan_fp16_and_fp8_against_oracle(sweep_head):
+    """The 0.5-degree plan (3486 zone axes: 28 axis tiles per pattern tile in
+    the contraction) with FP16 certified pruning and with E4M3 operands and
+    top-8 rescoring, on 300 patterns of the sweep scan, against the oracle.
+    The certified path must give the oracle's argmax up to ties; the
+    uncertified top-8 path must agree on at least 97 %."""
+    import torch
+    idx = np.arange(sweep_head.n_patterns)
+    p16 = gpu_plan("au_halfdeg_150x360", precision=2)
+    assert p16.info["n_za"] == 3486
+    a = p16.match(*to_dev(sweep_head))
+    torch.cuda.synchronize()
+    p16.close()
+    p8 = gpu_plan("au_halfdeg_150x360", precision=3)
+    b = p8.match(*to_dev(sweep_head), rescore_top=8)
+    torch.cuda.synchronize()
+    p8.close()
+    ca, cb = _choices(a), _choices(b)
+    res = oracle_matches("au_halfdeg_150x360", sweep_head, idx, ca, workers=8)
+    _check_against_pool(res, ca, a["score"].cpu().numpy(), idx, "0.5-degree FP16 certified")
+    agree = 0
+    sb = b["score"].cpu().numpy()
+    for j in idx:
+        za, k, m, score, _ = res[int(j)]
+        if tuple(cb[j]) == (za, k, m) or tuple(cb[j]) == tuple(ca[j]):
+            agree += 1
+            assert math.isclose(float(sb[j]), score, rel_tol=1e-4), j
+    print(f"0.5-degree E4M3 top-8: agrees with the oracle on {agree}/{len(idx)}")
+    assert agree >= 0.97 * len(idx)
+
+
+def test_contraction_wait_timeout_then_plan_usable():
+    """Failure detection of the tensor-core contraction: with a one-cycle
+    budget its pipeline waits run out, every CTA stops, drains its copies and
+    MMAs, frees its tensor memory and exits, and the call reports
+    ACOM_ERR_TIMEOUT (match and bounds alike).  With the default budget back,
+    the same plan matches the same patterns as the oracle does."""
+    import torch
+    from paper_2111_00171_gb300 import acom
+    lib = acom.load_library()
+    plan = gpu_plan("au_2deg_75x180", precision=2)
+    scan = synth.random_patterns(1501, n_patterns=150)
+    inp = to_dev(scan)
+    lib.acom_set_device_wait_limit(1)
+    try:
+        with pytest.raises(acom.AcomError) as e1:
+            plan.match(*inp)
+        assert e1.value.status == 4, e1.value
+        with pytest.raises(acom.AcomError) as e2:
+            plan.bounds(*inp)
+        assert e2.value.status == 4, e2.value
+    finally:
+        lib.acom_set_device_wait_limit(0)
+    r = plan.match(*inp)
+    torch.cuda.synchronize()
+    op = oracle_plan("au_2deg_75x180")
+    ch = _choices(r)
+    sc = r["score"].cpu().numpy()
+    for b in range(scan.n_patterns):
+        mt = O.match_pattern(op, *scan.pattern(b))
+        z, k, m = (int(v) for v in ch[b])
+        val = (mt.Cm if m else mt.C)[z, k]
+        assert (z, k, m) == (mt.za, mt.k, mt.mirror) or val >= mt.score * (1 - 1e-5), b
+        assert math.isclose(sc[b], mt.score, rel_tol=1e-4), b
+    plan.close()
