@@ -23,6 +23,10 @@ excitation_error          Eq. 6 with alpha = 0
 shape_factor_gaussian     Eq. 8
 rot_z, rot_x, euler_zxz   Eq. 10 (the paper's sign convention)
 zone_axis_grid            "Generation of an Orientation Plan": SLERP grid
+unique_shell_radii, plan_slice_unique
+                          the paper's own shells (unique radii |g|, the sum
+                          over {g : |g| = q_s}); the CUDA path and the other
+                          functions here use uniform shells (reading R3)
 za_frame                  inverse of the first two terms of Eq. 10
 orientation_plan          P0, A and P = A P0 (Generation of an Orientation
                           Plan), then the FFT along phi3
@@ -51,12 +55,17 @@ misorientation_deg        symmetry-reduced misorientation (reading)
 
 Parity status: structure factors, plan, image, correlation and best match are
 pinned by the tests under ``tests/test_oracle_pins.py`` (closed forms, brute
-force, Cauchy-Schwarz self-indexing, grid recovery, symmetry).  The paper
-fixes no formula for ``refine`` or ``misorientation_deg`` (readings): they are
-pinned by closed forms instead (exact parabola vertex, Rodrigues rotation,
-point-group closure, symmetry equivalents at zero angle, small rotations at
-their own angle) and by noiseless off-grid patterns refined closer to the
-truth than the grid on average.
+force, Cauchy-Schwarz self-indexing, grid recovery, symmetry, and the paper's
+kinematical accuracy trend with k_max).  The paper fixes no formula for
+``refine``, ``misorientation_deg`` or ``za_tilt_error_deg`` (readings): they
+are pinned by closed forms instead (exact parabola vertex, Rodrigues
+rotation, the neighbour mean's angle and threshold, point-group closure,
+symmetry equivalents at zero angle, small rotations and tilts at their own
+angle) and by noiseless off-grid patterns refined closer to the truth than
+the grid on average.  The forward model's excitation cut (``forward_spots``)
+is pinned by the zero-order-Laue-zone closed form at [001]; the paper's
+unique-radius shells (``unique_shell_radii``, ``plan_slice_unique``) by the
+fcc radius set, the [001] slice and self-indexing.
 """
 
 from __future__ import annotations
@@ -275,8 +284,11 @@ class PlanParams:
     gamma_pow: float = 1.0
     omega: float = 1.0
     lam: float = 0.01969
+    radii: np.ndarray = None   # the paper's shells (unique_shell_radii); None: uniform
 
     def shells(self):
+        if self.radii is not None:
+            return np.asarray(self.radii, dtype=np.float64)
         return (np.arange(self.n_shells, dtype=np.float64) + 1.0) * self.dq
 
     def phis(self):
@@ -329,16 +341,68 @@ def plan_slice(refl: Reflections, w, prm: PlanParams):
     return P0
 
 
-def orientation_plan(refl: Reflections, za, prm: PlanParams):
+def unique_shell_radii(refl: Reflections, rtol=1e-9):
+    """The paper's shells (Generation of an Orientation Plan): the distinct
+    lengths |g| of the reflections, ascending.  Lengths within ``rtol``
+    (relative) of each other are one radius (rounding of the lattice sums).
+    reading R2: the extinct reflections are not among them."""
+    q = np.sort(np.linalg.norm(refl.g, axis=1))
+    out = [q[0]]
+    for v in q[1:]:
+        if v > out[-1] * (1.0 + rtol):
+            out.append(v)
+    return np.array(out)
+
+
+def paper_params(refl: Reflections, n_phi, delta, gamma_pow=1.0, omega=1.0, lam=0.01969):
+    """PlanParams whose shells are the paper's unique radii of ``refl``."""
+    radii = unique_shell_radii(refl)
+    return PlanParams(len(radii), float('nan'), n_phi, delta, gamma_pow, omega, lam, radii)
+
+
+def plan_slice_unique(refl: Reflections, w, prm: PlanParams, rtol=1e-9):
+    """P0 for one zone axis w as the paper prints it (Generation of an
+    Orientation Plan), over the unique radii q_s = prm.radii:
+
+        P0(s, j) = sum_{g : |g| = q_s} q_s^gamma |V_g|^omega
+                   max{1 - (1/delta) sqrt(s_g^2 + wrap(phi_j - gamma_g)^2 q_s^2), 0}
+
+    g' = R^T g, s_g from Eq. 6, gamma_g = atan2(g'_y, g'_x) as in plan_slice;
+    each reflection belongs to the one shell of its own length and has no
+    radial term."""
+    R = za_frame(w)
+    gp = refl.g @ R
+    s_g = excitation_error(gp, beam_vector(prm.lam))
+    gam = np.arctan2(gp[:, 1], gp[:, 0])
+    amp = np.abs(refl.F) ** prm.omega
+    qg = np.linalg.norm(refl.g, axis=1)
+    q_s = prm.shells()
+    phi = prm.phis()
+    P0 = np.zeros((len(q_s), prm.n_phi))
+    for gi in range(len(qg)):
+        on = np.nonzero(np.abs(q_s - qg[gi]) <= rtol * qg[gi])[0]
+        if len(on) == 0:
+            continue
+        s = on[0]
+        dphi = wrap_angle(phi - gam[gi])
+        tent = np.maximum(1.0 - np.sqrt(s_g[gi] ** 2 + dphi ** 2 * q_s[s] ** 2) / prm.delta, 0.0)
+        P0[s] += q_s[s] ** prm.gamma_pow * amp[gi] * tent
+    return P0
+
+
+def orientation_plan(refl: Reflections, za, prm: PlanParams, slice_fn=None):
     """P = A P0 with A = 1/sqrt(sum_{phi3, q_s} P0^2) (A = 0 for an empty
     slice), then the 1D Fourier transform along phi3 (numpy rfft: sum_j
-    P_j exp(-2 pi i f j / N))."""
+    P_j exp(-2 pi i f j / N)).  P0 per zone axis from ``slice_fn``: plan_slice
+    (uniform shells, the default) or plan_slice_unique (the paper's unique
+    radii, with prm from paper_params)."""
+    slice_fn = plan_slice if slice_fn is None else slice_fn
     za = np.asarray(za, dtype=np.float64)
     Z = len(za)
     P = np.zeros((Z, prm.n_shells, prm.n_phi))
     A = np.zeros(Z)
     for z in range(Z):
-        P0 = plan_slice(refl, za[z], prm)
+        P0 = slice_fn(refl, za[z], prm)
         nrm = math.sqrt(float(np.sum(P0 * P0)))
         A[z] = 1.0 / nrm if nrm > 0 else 0.0
         P[z] = A[z] * P0

@@ -18,6 +18,7 @@ CONFIGS = {
     "au_2deg_75x180": (2.0, 75, 0.02, 180),      # 100 random patterns, 231 zone axes
     "au_1deg_150x360": (1.0, 150, 0.01, 360),    # 256x256 Voronoi scan, 903 zone axes
     "au_6deg_40x72": (6.0, 40, 0.0375, 72),      # tiny case for quick checks
+    "au_halfdeg_150x360": (0.5, 150, 0.01, 360),  # 512x512 sweep scan, 3486 zone axes
 }
 
 

@@ -18,12 +18,11 @@ import pytest
 import synth
 from oracle import acom_oracle as O
 
-from gpu_common import CONFIGS, gpu_plan, oracle_plan, rel_err, to_dev
+from gpu_common import gpu_plan, oracle_plan, rel_err, to_dev
 from oracle_pool import oracle_matches
 
 pytestmark = pytest.mark.gpu
 
-CONFIGS.setdefault("au_halfdeg_150x360", (0.5, 150, 0.01, 360))
 KEYS = ("za_idx", "phi3_bin", "mirror")
 
 
