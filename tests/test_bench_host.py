@@ -49,9 +49,17 @@ def test_reference_arm_line_keys(monkeypatch, capsys):
     monkeypatch.setenv("WORLD_SIZE", "1")
     monkeypatch.setenv("RANK", "0")
     monkeypatch.setenv("LOCAL_RANK", "0")
+    import time
     monkeypatch.setattr(bench, "oracle_plans", lambda stride=1: _tiny_plans())
-    bench.reference_arm(argparse.Namespace(warmup=0, steps=1, gpus=1, scan="4x4"))
+    t0 = time.perf_counter()
+    # the worker processes build every 64th zone axis of the workload's plan
+    bench.reference_arm(argparse.Namespace(warmup=1, steps=2, gpus=1, scan="4x4",
+                                           oracle_stride=64))
+    wall = time.perf_counter() - t0
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    # ms_per_step is the time of the sample each step ran: it fits the run
+    assert 0 < line["ms_per_step"] * line["steps"] / 1e3 <= wall
+    assert line["cpu_baseline"]["cores"] >= 1
     for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
               "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
               "cpu_baseline", "e2e"):
