@@ -30,9 +30,11 @@
 //
 // CTA: one TMA producer warp, two MMA-issuing warps, sixteen epilogue warps;
 // persistent over (64-pattern x 128-axis) tiles; operands stream through a
-// 4-stage shared-memory ring (K tiles of 64 BF16 = 128-byte rows, 128-byte
-// swizzle; the last tile of 160 shells is half zero fill); accumulators are
-// double-buffered over f in 512 TMEM columns.
+// 9-stage shared-memory ring (K tiles of 32 16-bit operands = 64-byte rows,
+// 64-byte swizzle, so 160 shells are five whole tiles and a stage is 24 KB:
+// the ring holds more stages in flight against the load latency than 48 KB
+// stages of 128-byte rows did); accumulators are double-buffered over f in
+// 512 TMEM columns.
 // Every mbarrier wait is bounded: a timeout sets the device error word, stops
 // all roles, drains copies and MMAs in flight, frees TMEM and returns.
 #include <cuda.h>
@@ -49,10 +51,11 @@ namespace tc {
 
 constexpr int kM = 128;               // zone axes per tile (MMA N = 256 rows: re, im)
 constexpr int kNP = 64;               // patterns per tile (MMA M = 128 rows: re, im)
-constexpr int kKT = 64;               // 16-bit operands per K tile row (128 bytes)
-constexpr int kKT8 = 128;             // 8-bit operands per K tile row (128 bytes)
-constexpr int kStages = 4;
-constexpr int kTileBytes = 128 * kKT * 2;      // 16 KB
+constexpr int kKT = 32;               // 16-bit operands per K tile row (64 bytes)
+constexpr int kKT8 = 64;              // 8-bit operands per K tile row (64 bytes)
+constexpr int kRowBytes = 64;         // = the swizzle span
+constexpr int kStages = 9;
+constexpr int kTileBytes = 128 * kRowBytes;    // 8 KB
 constexpr int kStageBytes = 3 * kTileBytes;    // X, then Pr and Pi as one 256-row operand
 constexpr int kEpiWarps = 16;
 constexpr int kIssuers = 2;                    // MMA-issuing warps, one per TMEM buffer
@@ -122,13 +125,14 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
-// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+// shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups
+// 512 B apart
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
     d |= (uint64_t)1 << 16;               // leading byte offset (unused with swizzle)
-    d |= (uint64_t)(1024 >> 4) << 32;     // stride byte offset
+    d |= (uint64_t)((8 * kRowBytes) >> 4) << 32;   // stride byte offset
     d |= (uint64_t)1 << 46;               // descriptor version
-    d |= (uint64_t)2 << 61;               // 128-byte swizzle
+    d |= (uint64_t)4 << 61;               // 64-byte swizzle
     return d;
 }
 
@@ -398,14 +402,14 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
                         fence_after();
                         const uint32_t sb = smem_u32(ring + stage * kStageBytes);
                         // K steps of 32 bytes inside the shells (16 16-bit or 32
-                        // 8-bit elements; the tail of the last tile is TMA zero
-                        // fill); a step moves the descriptors' start address by
-                        // 32 bytes (2 units of 16)
+                        // 8-bit elements; the tail of a last 8-bit tile is TMA
+                        // zero fill); a step moves the descriptors' start address
+                        // by 32 bytes (2 units of 16)
                         constexpr int ktel = F8 ? kKT8 : kKT;
                         const int nk = (min(ktel, a.Spad - kt * ktel) * (F8 ? 1 : 2)) >> 5;
                         const uint64_t xa = sdesc(sb), pb = sdesc(sb + kTileBytes);
 #pragma unroll
-                        for (int k4 = 0; k4 < 4; ++k4)
+                        for (int k4 = 0; k4 < kRowBytes / 32; ++k4)
                             if (k4 < nk) {
                                 if constexpr (F8)
                                     mma_f8kind(dacc, xa + 2 * k4, pb + 2 * k4, a.idesc,
@@ -528,10 +532,9 @@ static bool get_encoder() {
     return true;
 }
 
-// 2-D operand map: rows x cols (cols contiguous), boxes of 128 bytes x 128
-// rows (64 16-bit or 128 8-bit columns), 128-byte swizzle; boxes reaching
-// past the last column are zero-filled.  kind: 0 BF16, 1 FP16, 2 E4M3 (as
-// bytes).
+// 2-D operand map: rows x cols (cols contiguous), boxes of 64 bytes x 128
+// rows (32 16-bit or 64 8-bit columns), 64-byte swizzle; boxes reaching past
+// the last column are zero-filled.  kind: 0 BF16, 1 FP16, 2 E4M3 (as bytes).
 acom_status make_bf16_map(void* map_storage, const void* base, uint64_t rows, uint64_t cols,
                           int kind) {
     if (!get_encoder()) return set_error(ACOM_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
@@ -548,7 +551,7 @@ acom_status make_bf16_map(void* map_storage, const void* base, uint64_t rows, ui
                                                : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     CUresult r = g_encode(m, dt, 2, const_cast<void*>(base), dims,
                           strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(ACOM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
     return ACOM_OK;
