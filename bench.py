@@ -330,12 +330,20 @@ def _pool_ready(_):
     return os.getpid()
 
 
-def _pool_match(pat):
-    qx, qy, I = pat
+def _pool_match(task):
+    """The oracle's match of one pattern; with the GPU's choice (za, k,
+    mirror) given, also whether that choice is the oracle's or a documented
+    tie (the oracle's value there within 1e-5 relative of its best)."""
+    (qx, qy, I), choice = task
     mt = oracle_match(_POOL_PLANS, qx, qy, I)
     if W.get("refine"):
         oracle_refine(_POOL_PLANS[0], mt, qx, qy, I)
-    return int(mt.za), int(mt.k), int(mt.mirror), float(mt.score)
+    ok = None
+    if choice is not None:
+        z, k, m = choice
+        val = (mt.Cm if m else mt.C)[z, k]
+        ok = (z, k, m) == (mt.za, mt.k, mt.mirror) or val >= mt.score * (1 - 1e-5)
+    return int(mt.za), int(mt.k), int(mt.mirror), float(mt.score), ok
 
 
 def oracle_pool(cores, stride=1):
@@ -390,15 +398,15 @@ def cpu_baseline(scan, gpu_res, n_sample):
     pool, cores, t_setup = oracle_pool(host_cores())
     try:
         idx2 = rng.choice(scan.n_patterns, 4 * cores, replace=False)
+        tasks = [(scan.pattern(b), (int(gpu_res["za_idx"][b]), int(gpu_res["phi3_bin"][b]),
+                                    int(gpu_res["mirror"][b]))) for b in idx2]
         t0 = time.perf_counter()
-        got = pool.map(_pool_match, [scan.pattern(b) for b in idx2], chunksize=1)
+        got = pool.map(_pool_match, tasks, chunksize=1)
         t_all = (time.perf_counter() - t0) / len(idx2)
     finally:
         pool.close()
         pool.join()
-    for b, (z, k, m, _) in zip(idx2, got):
-        agree += int((z, k, m) == (int(gpu_res["za_idx"][b]), int(gpu_res["phi3_bin"][b]),
-                                   int(gpu_res["mirror"][b])))
+    agree += sum(int(g[4]) for g in got)
     value = B / (t_setup + B * t_all)
     return {"value": value, "unit": "patterns/s", "cores": cores, "kind": "oracle",
             "sample": (f"FP64 NumPy oracle, {cores} worker processes (one per host core): "
@@ -445,7 +453,7 @@ def reference_arm(args):
             t_sub = time.perf_counter() - t0
             bs = rng.choice(scan.n_patterns, 2 * cores, replace=False)
             t1 = time.perf_counter()
-            pool.map(_pool_match, [scan.pattern(b) for b in bs], chunksize=1)
+            pool.map(_pool_match, [(scan.pattern(b), None) for b in bs], chunksize=1)
             t_p = (time.perf_counter() - t1) / len(bs)
             if it >= args.warmup:
                 B = scan.n_patterns

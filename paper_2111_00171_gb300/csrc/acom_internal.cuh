@@ -53,6 +53,11 @@ struct RasterOut {
     float* sumsq = nullptr;    // [item] sum of squares of the polar image
     float* fnorm = nullptr;    // [item][F] ||X^_f|| over shells
     int2* srange = nullptr;    // [item] first and one-past-last shell with a non-zero row
+    // [item][Spad / 32] bit s: some peak's tent reached shell s.  When given, the
+    // shell-major rows (sre, sim) are written only for shell pairs with such a
+    // shell, and a reader must skip every row whose bit is clear (those rows
+    // are exactly zero and their memory is left as it was).
+    uint32_t* rmask = nullptr;
 };
 
 struct PlanSource {            // reflections rotated into each zone-axis frame
@@ -122,10 +127,11 @@ struct Workspace {
     float* U = nullptr;            // [chunk][Z] spectral bounds
     void* XB = nullptr;            // BF16 [F][PTs][128][Spad] (tensor-core operand, 16-row groups: 8 re, 8 im)
     int PTs = 0;                   // pattern tiles of 64 in XB
-    alignas(64) unsigned char map_x[128];   // TMA map of XB
+    alignas(64) unsigned char map_x[2][128];  // TMA maps of XB: 128-byte rows, 64-byte rows
     float* xfn = nullptr;          // [chunk][F] ||X^_bf|| over shells
     int* n_eval = nullptr;         // axes evaluated exactly in the last match
     int2* srange = nullptr;        // [chunk] non-zero shell range of each pattern
+    uint32_t* rmask = nullptr;     // [chunk][Spad / 32] shells each pattern's tents reach
     unsigned long long* best = nullptr;  // [chunk] packed (score, index)
     float* za_scores = nullptr;    // [chunk][Z]
     float* xscale = nullptr;       // [chunk] 2^e of each pattern's FP16 spectrum
@@ -177,8 +183,12 @@ struct acom_plan_s {
     uint32_t* smask = nullptr;        // [Zp][Spad / 32] bit s: shell row s of the axis not zero
     void* Pb_r = nullptr;             // BF16 or FP16 [F][Zp][Spad] (tensor-core operand)
     void* Pb_i = nullptr;
-    alignas(64) unsigned char map_pr[128];  // TMA maps of Pb_r, Pb_i
-    alignas(64) unsigned char map_pi[128];
+    // TMA maps of Pb_r, Pb_i (make_plan_maps): [k][re/im], k = 0 128-row boxes of
+    // 128-byte rows, 1 the same with 64-byte rows, 2 and 3 the tail tile's
+    // boxes of tail_w rows with 128- and 64-byte rows
+    alignas(64) unsigned char tmaps[4][2][128];
+    int tail_w = 0;                   // axes of a narrow last axis tile (16), or 0
+    int ktail64 = 0;                  // 1: the last K tile (32 shells) loads 64-byte rows
     float4* refl_tab = nullptr;       // [G] FP32 (g, |g|^gamma |F_g|^omega) for refinement
     unsigned long long* refine_pairs = nullptr;  // (reflection, peak) pairs of the last refine
     int64_t last_refine_pairs = 0;
@@ -262,12 +272,16 @@ void launch_plan_fnorm_max(const acom_plan_s* p, float* out, cudaStream_t st);
 void launch_plan_shell_mask(const acom_plan_s* p, cudaStream_t st);
 // match_tc.cu
 acom_status make_bf16_map(void* map_storage, const void* base, uint64_t rows, uint64_t cols,
-                          int kind = 0);
+                          int kind = 0, int box_rows = 128, int row_bytes = 128);
+// the plan's operand maps (p->tmaps) and its tail / K-tile choices
+acom_status make_plan_maps(acom_plan_s* p);
+// both maps of a pattern operand XB (rows x Spad): [0] 128-byte rows, [1] 64-byte rows
+acom_status make_pattern_maps(void* maps2, const void* XB, uint64_t rows, int Spad, int kind);
 void launch_half_to_e4m3(const void* src, void* dst, int64_t n, float mul, cudaStream_t st);
 // budget in clock cycles of the tensor-core contraction's pipeline waits (0: default)
 void set_wait_cycles(long long cycles);
 // xscale: per-pattern 2^e of FP16 pattern spectra (nullptr: BF16, no scale)
-void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_stride, int nb,
+void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x2, int pt_stride, int nb,
                               float* U, cudaStream_t st, const float* xscale = nullptr,
                               int tile_order = 0);
 // kind 1 / 2: FP16 / E4M3 of scale * src instead of BF16 of src
@@ -276,11 +290,10 @@ void launch_plan_to_bf16(const float* src, int Zp, int F, int Spad, void* dst, c
 void launch_orient_compose(const acom_plan_s* p, const OrientIn* oin, int nb, int refine,
                            acom_result out, int64_t off, cudaStream_t st);
 void launch_select_exact(const acom_plan_s* p, const float* Xsr, const float* Xsi, const float* U,
-                         const float* xfn, const int2* srange, const float* pfmax,
-                         const float* xnorm2, int nb,
+                         const float* xfn, const int2* srange, const uint32_t* rmask,
+                         const float* pfmax, const float* xnorm2, int nb,
                          float kappa, int refine, acom_result out, int64_t off, int* n_eval,
-                         cudaStream_t st, const float* xscale, int rescore_top,
-                         const acom_peaks_csr* chunk_peaks, OrientIn* oin);
+                         cudaStream_t st, const float* xscale, int rescore_top, OrientIn* oin);
 // refine.cu: continuous refinement on the plan's reflections
 acom_status refine_table(acom_plan_s* p, cudaStream_t st);
 void launch_refine_orient(const acom_plan_s* p, const acom_peaks_csr* pk, int steps,

@@ -151,6 +151,7 @@ static void free_workspace(Workspace& ws, cudaStream_t st) {
     pool_free(ws.xfn, st);
     pool_free(ws.n_eval, st);
     pool_free(ws.srange, st);
+    pool_free(ws.rmask, st);
     pool_free(ws.best, st);
     pool_free(ws.za_scores, st);
     pool_free(ws.XB, st);
@@ -191,6 +192,7 @@ static acom_status ensure_workspace(acom_plan_s* p, int chunk, bool need_chat, b
     if ((e = dalloc(&ws.xfn, (size_t)chunk * p->F, &acc, st)) != cudaSuccess) goto fail;
     if ((e = dalloc(&ws.n_eval, (size_t)1, &acc, st)) != cudaSuccess) goto fail;
     if ((e = dalloc(&ws.srange, (size_t)chunk, &acc, st)) != cudaSuccess) goto fail;
+    if ((e = dalloc(&ws.rmask, (size_t)chunk * (p->Spad / 32), &acc, st)) != cudaSuccess) goto fail;
     if ((e = dalloc(&ws.best, (size_t)chunk, &acc, st)) != cudaSuccess) goto fail;
     if ((e = dalloc(&ws.za_scores, (size_t)chunk * p->Z, &acc, st)) != cudaSuccess) goto fail;
     if ((e = dalloc(&ws.oin, (size_t)chunk, &acc, st)) != cudaSuccess) goto fail;
@@ -208,8 +210,8 @@ static acom_status ensure_workspace(acom_plan_s* p, int chunk, bool need_chat, b
             acc += rows * p->Spad;
         }
         if (scaled && (e = dalloc(&ws.xscale, (size_t)chunk, &acc, st)) != cudaSuccess) goto fail;
-        acom_status ms = make_bf16_map(ws.map_x, fp8 ? ws.XB8 : ws.XB, rows, (uint64_t)p->Spad,
-                                       tc_kind(p->precision));
+        acom_status ms = make_pattern_maps(ws.map_x, fp8 ? ws.XB8 : ws.XB, rows, p->Spad,
+                                           tc_kind(p->precision));
         if (ms != ACOM_OK) {
             free_workspace(p->ws, st);
             return ms;
@@ -422,10 +424,7 @@ acom_status acom_plan_create(const acom_crystal* crystal, const acom_za_grid* gr
         launch_plan_to_bf16(p->Pr, p->Zp, p->F, p->Spad, p->Pb_r, st, kind, p->pscale);
         launch_plan_to_bf16(p->Pi, p->Zp, p->F, p->Spad, p->Pb_i, st, kind, p->pscale);
         ACOM_CK(cudaGetLastError());
-        s = make_bf16_map(p->map_pr, p->Pb_r, (uint64_t)p->F * p->Zp, (uint64_t)p->Spad, kind);
-        if (s == ACOM_OK)
-            s = make_bf16_map(p->map_pi, p->Pb_i, (uint64_t)p->F * p->Zp, (uint64_t)p->Spad,
-                              kind);
+        s = make_plan_maps(p);
         if (s != ACOM_OK) {
             destroy_plan(p);
             return s;
@@ -584,9 +583,7 @@ acom_status acom_plan_concat(const acom_plan* plans, int32_t n_plans, void* cuda
             ACOM_CK(cudaMemcpy2DAsync(static_cast<char*>(p->Pb_i) + base * row, p->Zp * row, q->Pb_i,
                                       q->Zp * row, q->Z * row, F, cudaMemcpyDeviceToDevice, st));
         }
-        acom_status s = make_bf16_map(p->map_pr, p->Pb_r, (uint64_t)F * p->Zp, (uint64_t)Spad, kind);
-        if (s == ACOM_OK)
-            s = make_bf16_map(p->map_pi, p->Pb_i, (uint64_t)F * p->Zp, (uint64_t)Spad, kind);
+        acom_status s = make_plan_maps(p);
         if (s != ACOM_OK) {
             cudaStreamSynchronize(st);
             destroy_plan(p);
@@ -808,6 +805,8 @@ static acom_status match_enqueue(acom_plan p, const acom_peaks_csr* peaks,
         ro.sumsq = p->ws.xnorm2;
         ro.fnorm = p->ws.xfn;
         ro.srange = p->ws.srange;
+        // select reads only the rows the pattern's tents reach
+        ro.rmask = exhaustive ? nullptr : p->ws.rmask;
         launch_raster_patterns(geo, src, ro, p->err, st);
         if (exhaustive) {
             cudaMemsetAsync(p->ws.best, 0, sizeof(unsigned long long) * nb, st);
@@ -828,11 +827,10 @@ static acom_status match_enqueue(acom_plan p, const acom_peaks_csr* peaks,
             } else {
                 launch_contract_bound_fp32(p, p->ws.Xr, p->ws.Xi, nb, p->ws.U, st);
             }
-            const acom_peaks_csr cp{nb, peaks->row_ptr + c0, peaks->qx, peaks->qy, peaks->I};
-            launch_select_exact(p, p->ws.Xsr, p->ws.Xsi, p->ws.U, p->ws.xfn, p->ws.srange, p->pfmax,
-                                p->ws.xnorm2, nb, tc ? kappa_tc(p) : kappa_fp32(p), refine,
-                                *out, c0, p->ws.n_eval, st, xscale, rescore_top, &cp,
-                                p->ws.oin);
+            launch_select_exact(p, p->ws.Xsr, p->ws.Xsi, p->ws.U, p->ws.xfn, p->ws.srange,
+                                p->ws.rmask, p->pfmax, p->ws.xnorm2, nb,
+                                tc ? kappa_tc(p) : kappa_fp32(p), refine, *out, c0,
+                                p->ws.n_eval, st, xscale, rescore_top, p->ws.oin);
             if (out->phi3 || out->orient)
                 launch_orient_compose(p, p->ws.oin, nb, refine, *out, c0, st);
         }

@@ -226,8 +226,8 @@ struct SelSmem {
     float* res;      // [kBatch][5] best value, its index bits, values at k - 1, k, k + 1
     float* red;      // [2][kSelWarps]
     int* poff;       // [kMaxPhases + 1] first axis of each phase, then Z
-    uint32_t* pmask; // [Spad / 32] shells the pattern's peaks reach (a superset of its
-                     // non-zero rows)
+    uint32_t* pmask; // [Spad / 32] shells the pattern's tents reach: its rows that may
+                     // be non-zero, and the only ones the raster wrote
     uint16_t* slist; // [kBatch][Spad] shells of each candidate: pattern and plan rows both
                      // not zero
     int* slen;       // [kBatch]
@@ -337,6 +337,7 @@ struct SelectArgs {
     const float* U;                   // [nb][Z] bounds
     const float* xfn;                 // [nb][F] ||X^_bf||
     const int2* srange;               // [nb] non-zero shell range
+    const uint32_t* rmask;            // [nb][Spad / 32] shells the pattern's tents reach
     const float* pfmax;               // [F] max_z ||P^_zf||
     const float* xnorm2;              // [nb] ||X||^2
     const double* za;                 // [Z][3]
@@ -357,9 +358,6 @@ struct SelectArgs {
     float eta;                        // absolute error of an operand below its normal range
     int rescore_top;                  // > 0: evaluate only the top axes by bound (no certificate)
     const uint32_t* smask;            // [Zp][Spad / 32] non-zero plan shells
-    const int64_t* row_ptr;           // the chunk's peaks (row_ptr offset to the chunk)
-    const float *qx, *qy;
-    float dq, delta;                  // shells q_s = (s + 1) dq, tent size
     OrientIn* oin;                    // [nb] the winners, for k_orient_compose
 };
 
@@ -773,11 +771,10 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_select_exact(SelectArgs a) {
             sm.U[z] = a.U[b * Z + z];
             sm.ev[z] = 0;
         }
-        // shells within the tent of some peak (|r_m - q_s| < delta), widened
-        // by one shell on each side against rounding: every row the raster can
-        // have made non-zero
-        for (int w = threadIdx.x; w < (a.Spad >> 5); w += kSelThreads) sm.pmask[w] = 0u;
-        const int64_t p0 = a.row_ptr[b], p1 = a.row_ptr[b + 1];
+        // the shells some peak's tent reached (recorded by the raster, which
+        // wrote only those rows; every other row of the pattern is zero)
+        for (int w = threadIdx.x; w < (a.Spad >> 5); w += kSelThreads)
+            sm.pmask[w] = a.rmask[b * (a.Spad >> 5) + w];
         // E_b: rounding margin valid for every axis (its partial sums load
         // together with the bounds, before the first barrier).  FP16 operands add an
         // absolute term for values below the normal range: an operand x is off
@@ -803,15 +800,6 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_select_exact(SelectArgs a) {
             sm.red[kSelWarps + warp] = ea;
         }
         __syncthreads();
-        for (int64_t m = p0 + threadIdx.x; m < p1; m += kSelThreads) {
-            const float r = sqrtf(a.qx[m] * a.qx[m] + a.qy[m] * a.qy[m]);
-            if (!(r < 1e30f)) continue;
-            int lo = (int)floorf((r - a.delta) / a.dq) - 2;
-            int hi = (int)ceilf((r + a.delta) / a.dq);
-            lo = lo < 0 ? 0 : lo;
-            hi = hi > a.S - 1 ? a.S - 1 : hi;
-            for (int s = lo; s <= hi; ++s) atomicOr(&sm.pmask[s >> 5], 1u << (s & 31));
-        }
         if (threadIdx.x == 0) {
             float t = 0.f, ta = 0.f;
             for (int w = 0; w < kSelWarps; ++w) {
@@ -969,18 +957,17 @@ size_t select_smem_bytes(int Z, int N, int F, int Spad) {
 }
 
 void launch_select_exact(const acom_plan_s* p, const float* Xsr, const float* Xsi, const float* U,
-                         const float* xfn, const int2* srange, const float* pfmax,
-                         const float* xnorm2, int nb,
+                         const float* xfn, const int2* srange, const uint32_t* rmask,
+                         const float* pfmax, const float* xnorm2, int nb,
                          float kappa, int refine, acom_result out, int64_t off, int* n_eval,
-                         cudaStream_t st, const float* xscale, int rescore_top,
-                         const acom_peaks_csr* cp, OrientIn* oin) {
-    SelectArgs a{p->Psr, p->Psi, Xsr, Xsi, U, xfn, srange, pfmax, xnorm2, p->za, p->frames,
+                         cudaStream_t st, const float* xscale, int rescore_top, OrientIn* oin) {
+    SelectArgs a{p->Psr, p->Psi, Xsr, Xsi, U, xfn, srange, rmask, pfmax, xnorm2, p->za, p->frames,
                  p->nbr_ptr,
                  p->nbr_idx, p->phase_off, p->n_phases, p->Z, p->F, p->N, p->S, p->Spad, nb, refine, kappa,
                  fft_radices(p->N), out, off, n_eval, xscale, 1.0f / p->pscale,
                  p->precision == ACOM_PREC_FP8 ? kFp8Shift : 1.0f,
                  (float)(p->precision == ACOM_PREC_FP8 ? kFp8Eta : kFp16Eta), rescore_top,
-                 p->smask, cp->row_ptr, cp->qx, cp->qy, (float)p->dq, (float)p->delta, oin};
+                 p->smask, oin};
     const size_t smem = select_smem_bytes(p->Z, p->N, p->F, p->Spad);
     set_max_dynamic_smem((const void*)k_select_exact, smem);
     int dev = 0, nsm = 0, per_sm = 0;

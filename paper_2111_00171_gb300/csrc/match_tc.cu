@@ -30,11 +30,14 @@
 //
 // CTA: one TMA producer warp, two MMA-issuing warps, sixteen epilogue warps;
 // persistent over (64-pattern x 128-axis) tiles; operands stream through a
-// 9-stage shared-memory ring (K tiles of 32 16-bit operands = 64-byte rows,
-// 64-byte swizzle, so 160 shells are five whole tiles and a stage is 24 KB:
-// the ring holds more stages in flight against the load latency than 48 KB
-// stages of 128-byte rows did); accumulators are double-buffered over f in
-// 512 TMEM columns.
+// 4-stage shared-memory ring (K tiles of 64 16-bit operands = 128-byte rows,
+// 128-byte swizzle); accumulators are double-buffered over f in 512 TMEM
+// columns.  The TMA engine's rate (about one cycle per box row plus about
+// 100 bytes per cycle per SM, measured) bounds this kernel, so box rows that
+// carry no work are avoided: a last K tile of 32 shells (160 = 64 + 64 + 32)
+// loads 64-byte rows with 64-byte swizzle instead of half-zero 128-byte rows,
+// and a last axis tile holding at most 16 axes (903 = 7 x 128 + 7) loads
+// 16-row boxes of the plan and runs N = 32 MMAs instead of N = 256.
 // Every mbarrier wait is bounded: a timeout sets the device error word, stops
 // all roles, drains copies and MMAs in flight, frees TMEM and returns.
 #include <cuda.h>
@@ -51,11 +54,10 @@ namespace tc {
 
 constexpr int kM = 128;               // zone axes per tile (MMA N = 256 rows: re, im)
 constexpr int kNP = 64;               // patterns per tile (MMA M = 128 rows: re, im)
-constexpr int kKT = 32;               // 16-bit operands per K tile row (64 bytes)
-constexpr int kKT8 = 64;              // 8-bit operands per K tile row (64 bytes)
-constexpr int kRowBytes = 64;         // = the swizzle span
-constexpr int kStages = 9;
-constexpr int kTileBytes = 128 * kRowBytes;    // 8 KB
+constexpr int kKT = 64;               // 16-bit operands per K tile row (128 bytes)
+constexpr int kKT8 = 128;             // 8-bit operands per K tile row (128 bytes)
+constexpr int kStages = 4;
+constexpr int kTileBytes = 128 * kKT * 2;      // 16 KB
 constexpr int kStageBytes = 3 * kTileBytes;    // X, then Pr and Pi as one 256-row operand
 constexpr int kEpiWarps = 16;
 constexpr int kIssuers = 2;                    // MMA-issuing warps, one per TMEM buffer
@@ -125,13 +127,22 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
-// shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups
-// 512 B apart
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
     d |= (uint64_t)1 << 16;               // leading byte offset (unused with swizzle)
-    d |= (uint64_t)((8 * kRowBytes) >> 4) << 32;   // stride byte offset
+    d |= (uint64_t)(1024 >> 4) << 32;     // stride byte offset
     d |= (uint64_t)1 << 46;               // descriptor version
+    d |= (uint64_t)2 << 61;               // 128-byte swizzle
+    return d;
+}
+
+// the same for 64-byte rows with 64-byte swizzle (8-row groups 512 B apart)
+__device__ __forceinline__ uint64_t sdesc64(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(512 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
     d |= (uint64_t)4 << 61;               // 64-byte swizzle
     return d;
 }
@@ -185,6 +196,21 @@ __device__ __forceinline__ void fence_after() {
                    "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), \
                    "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])                        \
                  : "r"(taddr))
+
+// 16 TMEM lanes x 16 columns: r[4n .. 4n+3] as for the x4 load, n = 0, 1
+#define ACOM_TMEM_LD16x256_X2(taddr, r)                                                     \
+    asm volatile("tcgen05.ld.sync.aligned.16x256b.x2.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];" \
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),  \
+                   "=r"(r[6]), "=r"(r[7])                                                   \
+                 : "r"(taddr))
+
+#define ACOM_TMEM_WAIT16(p, q)                                                              \
+    asm volatile("tcgen05.wait::ld.sync.aligned;"                                           \
+                 : "+r"(p[0]), "+r"(p[1]), "+r"(p[2]), "+r"(p[3]), "+r"(p[4]), "+r"(p[5]),  \
+                   "+r"(p[6]), "+r"(p[7]), "+r"(q[0]), "+r"(q[1]), "+r"(q[2]), "+r"(q[3]),  \
+                   "+r"(q[4]), "+r"(q[5]), "+r"(q[6]), "+r"(q[7])                          \
+                 :                                                                          \
+                 : "memory")
 
 // wait for this thread's TMEM loads; the registers are tied to the wait so no
 // use can be scheduled before it
@@ -257,6 +283,9 @@ struct TcArgs {
                                    // tile, 1 they share an axis tile
     long long wait_cycles;         // budget of each pipeline wait (the drain waits
                                    // that precede the exit always take kWaitCycles)
+    int tail_w;                    // axes of a narrow last axis tile (16), or 0
+    int ktail64;                   // 1: the last K tile (32 shells) has 64-byte rows
+    uint32_t idesc_tail;           // the narrow tile's MMA descriptor (N = 2 tail_w)
 };
 
 // F8: E4M3 operands (kind::f8f6f4, 128 elements per K tile), else 16-bit
@@ -266,7 +295,14 @@ template <bool F8>
 __global__ void __launch_bounds__(kThreads, 1)
 k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
                     const __grid_constant__ CUtensorMap map_pi,
-                    const __grid_constant__ CUtensorMap map_x, TcArgs a) {
+                    const __grid_constant__ CUtensorMap map_x,
+                    const __grid_constant__ CUtensorMap map_pr64,
+                    const __grid_constant__ CUtensorMap map_pi64,
+                    const __grid_constant__ CUtensorMap map_x64,
+                    const __grid_constant__ CUtensorMap map_prt,
+                    const __grid_constant__ CUtensorMap map_pit,
+                    const __grid_constant__ CUtensorMap map_prt64,
+                    const __grid_constant__ CUtensorMap map_pit64, TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte alignment of the operand ring
     unsigned char* base = reinterpret_cast<unsigned char*>(
@@ -295,6 +331,15 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_pr)));
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_pi)));
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_x)));
+        if (a.ktail64) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_pr64)));
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_pi64)));
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_x64)));
+        }
+        if (a.tail_w) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_prt)));
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_pit)));
+        }
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -323,6 +368,9 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
             for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
                 const int zt = a.zmajor ? t / a.PT : t % a.ZT;
                 const int pt = a.zmajor ? t % a.PT : t / a.ZT;
+                // the narrow last axis tile: tail_w plan rows of re and im
+                const bool tailt = a.tail_w > 0 && zt == a.ZT - 1;
+                const int prows = tailt ? a.tail_w : kM;
                 for (int f = 0; f < a.F && ok; ++f, ++fcount) {
                     const int prow = f * a.Zrows + zt * kM;
                     const int xrow = (f * a.PTs + pt) * 128;
@@ -333,12 +381,22 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
                             break;
                         }
                         const uint32_t fb = smem_u32(full + own * kStages + stage);
-                        mbar_expect_tx(fb, kStageBytes);
+                        // a last K tile of 32 shells: 64-byte rows
+                        const bool k64 = a.ktail64 && kt == a.KT - 1;
+                        const int rb = k64 ? 64 : 128;
+                        mbar_expect_tx(fb, (uint32_t)((128 + 2 * prows) * rb));
                         unsigned char* sbuf = ring + stage * kStageBytes;
                         constexpr int ktel = F8 ? kKT8 : kKT;
-                        tma_load_2d(smem_u32(sbuf), &map_x, kt * ktel, xrow, fb);
-                        tma_load_2d(smem_u32(sbuf + kTileBytes), &map_pr, kt * ktel, prow, fb);
-                        tma_load_2d(smem_u32(sbuf + 2 * kTileBytes), &map_pi, kt * ktel, prow,
+                        const CUtensorMap* mx = k64 ? &map_x64 : &map_x;
+                        const CUtensorMap* mr = tailt ? (k64 ? &map_prt64 : &map_prt)
+                                                      : (k64 ? &map_pr64 : &map_pr);
+                        const CUtensorMap* mi = tailt ? (k64 ? &map_pit64 : &map_pit)
+                                                      : (k64 ? &map_pi64 : &map_pi);
+                        // X rows at 0, then the B operand at kTileBytes: re rows,
+                        // then im rows right after them
+                        tma_load_2d(smem_u32(sbuf), mx, kt * ktel, xrow, fb);
+                        tma_load_2d(smem_u32(sbuf + kTileBytes), mr, kt * ktel, prow, fb);
+                        tma_load_2d(smem_u32(sbuf + kTileBytes + prows * rb), mi, kt * ktel, prow,
                                     fb);
                         issued_mask |= 1u << stage;
                         const uint32_t par = (fpar[own] >> stage) & 1u;
@@ -380,6 +438,9 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
             bool ok = true;
             uint64_t* myfull = full + mi * kStages;
             for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+                const int zt = a.zmajor ? t / a.PT : t % a.ZT;
+                const bool tailt = a.tail_w > 0 && zt == a.ZT - 1;
+                const uint32_t idesc = tailt ? a.idesc_tail : a.idesc;
                 for (int f = 0; f < a.F && ok; ++f, ++fcount) {
                     if ((fcount & 1) != mi) {
                         stage = (stage + a.KT) % kStages;
@@ -402,20 +463,22 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
                         fence_after();
                         const uint32_t sb = smem_u32(ring + stage * kStageBytes);
                         // K steps of 32 bytes inside the shells (16 16-bit or 32
-                        // 8-bit elements; the tail of a last 8-bit tile is TMA
-                        // zero fill); a step moves the descriptors' start address
-                        // by 32 bytes (2 units of 16)
+                        // 8-bit elements; the tail of the last tile is TMA zero
+                        // fill); a step moves the descriptors' start address by
+                        // 32 bytes (2 units of 16)
                         constexpr int ktel = F8 ? kKT8 : kKT;
                         const int nk = (min(ktel, a.Spad - kt * ktel) * (F8 ? 1 : 2)) >> 5;
-                        const uint64_t xa = sdesc(sb), pb = sdesc(sb + kTileBytes);
+                        const bool k64 = a.ktail64 && kt == a.KT - 1;
+                        const uint64_t xa = k64 ? sdesc64(sb) : sdesc(sb);
+                        const uint64_t pb = k64 ? sdesc64(sb + kTileBytes) : sdesc(sb + kTileBytes);
 #pragma unroll
-                        for (int k4 = 0; k4 < kRowBytes / 32; ++k4)
+                        for (int k4 = 0; k4 < 4; ++k4)
                             if (k4 < nk) {
                                 if constexpr (F8)
-                                    mma_f8kind(dacc, xa + 2 * k4, pb + 2 * k4, a.idesc,
+                                    mma_f8kind(dacc, xa + 2 * k4, pb + 2 * k4, idesc,
                                                (kt | k4) ? 1u : 0u);
                                 else
-                                    mma_f16kind(dacc, xa + 2 * k4, pb + 2 * k4, a.idesc,
+                                    mma_f16kind(dacc, xa + 2 * k4, pb + 2 * k4, idesc,
                                                 (kt | k4) ? 1u : 0u);
                             }
                         mma_commit(smem_u32(empty + stage));       // frees the stage
@@ -445,6 +508,7 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
         for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
             const int zt = a.zmajor ? t / a.PT : t % a.ZT;
             const int pt = a.zmajor ? t % a.PT : t / a.ZT;
+            const bool tailt = a.tail_w > 0 && zt == a.ZT - 1;
             for (int f = 0; f < a.F; ++f, ++fcount) {
                 const int buf = fcount & 1;
                 if (!mbar_wait(smem_u32(tfull + buf), tph[buf], abort_flag, a.err, a.wait_cycles)) {
@@ -455,6 +519,32 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
                 fence_after();
                 const float w = (f == 0 || 2 * f == a.N) ? 1.f : 2.f;
                 const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + buf * 256 + zq * 32;
+                if (tailt) {
+                    // N = 32: columns 0..15 the 16 axes' re products, 16..31 their im
+                    // products; the warps of the first 32 columns take them
+                    if (zq == 0) {
+                        uint32_t R0[8], I0[8], R1[8], I1[8];
+                        ACOM_TMEM_LD16x256_X2(tb, R0);
+                        ACOM_TMEM_LD16x256_X2(tb + 16, I0);
+                        ACOM_TMEM_LD16x256_X2(tb + (16u << 16), R1);
+                        ACOM_TMEM_LD16x256_X2(tb + (16u << 16) + 16, I1);
+                        ACOM_TMEM_WAIT16(R0, I0);
+                        ACOM_TMEM_WAIT16(R1, I1);
+#pragma unroll
+                        for (int n = 0; n < 2; ++n) {
+                            accumulate_pair2(R0[4 * n], R0[4 * n + 1], R0[4 * n + 2], R0[4 * n + 3],
+                                             I0[4 * n], I0[4 * n + 1], I0[4 * n + 2], I0[4 * n + 3],
+                                             w, ud[2 * n], ud[2 * n + 1]);
+                            accumulate_pair2(R1[4 * n], R1[4 * n + 1], R1[4 * n + 2], R1[4 * n + 3],
+                                             I1[4 * n], I1[4 * n + 1], I1[4 * n + 2], I1[4 * n + 3],
+                                             w, ud[8 + 2 * n], ud[8 + 2 * n + 1]);
+                        }
+                    }
+                    fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(tempty + buf));
+                    continue;
+                }
                 // two halves of 8 patterns (16 lanes each); the second half's
                 // loads are in flight while the first is reduced
                 uint32_t R0[16], I0[16], R1[16], I1[16];
@@ -532,29 +622,66 @@ static bool get_encoder() {
     return true;
 }
 
-// 2-D operand map: rows x cols (cols contiguous), boxes of 64 bytes x 128
-// rows (32 16-bit or 64 8-bit columns), 64-byte swizzle; boxes reaching past
-// the last column are zero-filled.  kind: 0 BF16, 1 FP16, 2 E4M3 (as bytes).
+// 2-D operand map: rows x cols (cols contiguous), boxes of row_bytes (128 or
+// 64) bytes x box_rows rows with the swizzle of that width; boxes reaching
+// past the last column are zero-filled.  kind: 0 BF16, 1 FP16, 2 E4M3 (as
+// bytes).
 acom_status make_bf16_map(void* map_storage, const void* base, uint64_t rows, uint64_t cols,
-                          int kind) {
+                          int kind, int box_rows, int row_bytes) {
     if (!get_encoder()) return set_error(ACOM_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
     const uint64_t eb = kind == 2 ? 1 : 2;
     if ((cols * eb) % 16 != 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0)
         return set_error(ACOM_ERR_INVALID_ARG, "tensor map: stride or base not 16-byte aligned");
+    if ((row_bytes != 128 && row_bytes != 64) || box_rows < 8 || box_rows > 256)
+        return set_error(ACOM_ERR_INVALID_ARG, "tensor map: unsupported box");
     CUtensorMap* m = reinterpret_cast<CUtensorMap*>(map_storage);
     const cuuint64_t dims[2] = {cols, rows};
     const cuuint64_t strides[1] = {cols * eb};
-    const cuuint32_t box[2] = {(cuuint32_t)(kind == 2 ? tc::kKT8 : tc::kKT), 128};
+    const cuuint32_t box[2] = {(cuuint32_t)(row_bytes / eb), (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     const CUtensorMapDataType dt = kind == 2   ? CU_TENSOR_MAP_DATA_TYPE_UINT8
                                    : kind == 1 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    CUresult r = g_encode(m, dt, 2, const_cast<void*>(base), dims,
-                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = g_encode(m, dt, 2, const_cast<void*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(ACOM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
     return ACOM_OK;
+}
+
+// 16-bit operands whose shells end in a 32-wide K tile load it as 64-byte rows
+static bool use_ktail64(int precision, int Spad) {
+    return precision != ACOM_PREC_FP8 && Spad % tc::kKT == 32;
+}
+
+acom_status make_plan_maps(acom_plan_s* p) {
+    const int kind = tc_kind(p->precision);
+    const uint64_t rows = (uint64_t)p->F * p->Zp, cols = (uint64_t)p->Spad;
+    // a last axis tile with at most 16 axes becomes a narrow tile (16-bit operands)
+    const int tail = p->Z - (p->Zp / tc::kM - 1) * tc::kM;
+    p->tail_w = (p->precision != ACOM_PREC_FP8 && tail > 0 && tail <= 16) ? 16 : 0;
+    p->ktail64 = use_ktail64(p->precision, p->Spad) ? 1 : 0;
+    const void* base[2] = {p->Pb_r, p->Pb_i};
+    for (int c = 0; c < 2; ++c) {
+        acom_status s = make_bf16_map(p->tmaps[0][c], base[c], rows, cols, kind, tc::kM, 128);
+        if (s == ACOM_OK && p->ktail64)
+            s = make_bf16_map(p->tmaps[1][c], base[c], rows, cols, kind, tc::kM, 64);
+        if (s == ACOM_OK && p->tail_w)
+            s = make_bf16_map(p->tmaps[2][c], base[c], rows, cols, kind, p->tail_w, 128);
+        if (s == ACOM_OK && p->tail_w && p->ktail64)
+            s = make_bf16_map(p->tmaps[3][c], base[c], rows, cols, kind, p->tail_w, 64);
+        if (s != ACOM_OK) return s;
+    }
+    return ACOM_OK;
+}
+
+acom_status make_pattern_maps(void* maps2, const void* XB, uint64_t rows, int Spad, int kind) {
+    unsigned char* m = reinterpret_cast<unsigned char*>(maps2);
+    acom_status s = make_bf16_map(m, XB, rows, (uint64_t)Spad, kind, 128, 128);
+    if (s == ACOM_OK && kind != 2 && Spad % tc::kKT == 32)
+        s = make_bf16_map(m + 128, XB, rows, (uint64_t)Spad, kind, 128, 64);
+    return s;
 }
 
 size_t tensor_map_bytes() { return sizeof(CUtensorMap); }
@@ -564,7 +691,7 @@ size_t tensor_map_bytes() { return sizeof(CUtensorMap); }
 static long long g_wait_cycles = 0;
 void set_wait_cycles(long long cycles) { g_wait_cycles = cycles > 0 ? cycles : 0; }
 
-void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_stride, int nb,
+void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x2, int pt_stride, int nb,
                               float* U, cudaStream_t st, const float* xscale, int tile_order) {
     tc::TcArgs a;
     a.zmajor = tile_order == 1 ? 1 : 0;
@@ -588,6 +715,10 @@ void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_st
     a.xs_mul = f8 ? kFp8Shift : 1.0f;
     a.inv_pscale = 1.0f / p->pscale;
     a.wait_cycles = g_wait_cycles > 0 ? g_wait_cycles : tc::kWaitCycles;
+    a.tail_w = p->tail_w;
+    a.ktail64 = p->ktail64;
+    // the narrow tile's descriptor: N = 2 tail_w instead of 256
+    a.idesc_tail = (a.idesc & ~(0x3Fu << 17)) | ((uint32_t)(2 * p->tail_w) >> 3) << 17;
     const size_t smem = tc::tc_smem_bytes();
     auto kern = f8 ? tc::k_contract_bound_tc<true> : tc::k_contract_bound_tc<false>;
     set_max_dynamic_smem((const void*)kern, smem);
@@ -597,11 +728,18 @@ void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_st
     const int n_tiles = a.ZT * a.PT;
     const int grid = n_tiles < nsm ? n_tiles : nsm;
     if (grid <= 0) return;
+    // maps a kernel does not use (no 64-byte K tile, no narrow tile) are
+    // passed as copies of the ones it uses and never read
+    const CUtensorMap* mx = reinterpret_cast<const CUtensorMap*>(map_x2);
+    const CUtensorMap* pm[4][2];
+    for (int k = 0; k < 4; ++k)
+        for (int c = 0; c < 2; ++c) pm[k][c] = reinterpret_cast<const CUtensorMap*>(p->tmaps[k][c]);
+    const CUtensorMap& x64 = p->ktail64 ? mx[1] : mx[0];
+    const int k64 = p->ktail64 ? 1 : 0, kt = p->tail_w ? 2 : 0, kt64 = p->tail_w ? 2 + k64 : 0;
     prof_begin(kKContractBf16, st);
-    kern<<<grid, tc::kThreads, smem, st>>>(
-        *reinterpret_cast<const CUtensorMap*>(p->map_pr),
-        *reinterpret_cast<const CUtensorMap*>(p->map_pi),
-        *reinterpret_cast<const CUtensorMap*>(map_x), a);
+    kern<<<grid, tc::kThreads, smem, st>>>(*pm[0][0], *pm[0][1], mx[0], *pm[k64][0], *pm[k64][1],
+                                           x64, *pm[kt][0], *pm[kt][1], *pm[kt64][0],
+                                           *pm[kt64][1], a);
     prof_end(kKContractBf16, st);
 }
 

@@ -535,6 +535,7 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
             s_int[40] = Spad;
             s_int[41] = 0;
         }
+        if (threadIdx.x < 16) s_int[16 + threadIdx.x] = 0;    // shells the tents reach
         __syncthreads();
         const bool half = xb && ld.xb_half();
         float xsc = 1.0f;
@@ -551,42 +552,45 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
             // pairs warp and warp + W of the tile
             for (int pp = warp; pp < kFftTile / 2; pp += W) {
                 const int sA = t0 + 2 * pp;
-                // rows start on 16-byte boundaries (N even: 16-byte accesses)
-                if ((N & 1) == 0) {
-                    float4* z4 = reinterpret_cast<float4*>(z);
-                    float4* zz4 = reinterpret_cast<float4*>(zz);
-                    for (int j = lane; j < N / 2; j += 32) {
-                        z4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        zz4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    }
-                } else {
-                    for (int j = lane; j < N; j += 32) {
-                        z[j] = make_float2(0.f, 0.f);
-                        zz[j] = make_float2(0.f, 0.f);
-                    }
-                }
-                __syncwarp();
                 // One pass over the peaks reaching either shell of the pair (radius
                 // within delta of q_A or q_B): the half-warps take alternate peaks,
                 // each into its own row (z, zz), and every bin of a peak's window
                 // gets both shells' tents (x: shell sA, y: shell sA + 1).  The two
-                // rows are summed before the transform, a fixed order.
+                // rows are summed before the transform, a fixed order.  A pair no
+                // peak's radius reaches is all zero: no rows, no transform.
                 bool inA_any = false, inB_any = false;
+                const bool vB = sA + 1 < S;
+                const float qA = (float)(sA + 1) * geo.dq, qB = (float)(sA + 2) * geo.dq;
+                int lo = 0, hi = 0;
                 if (sA < S) {
-                    const bool vB = sA + 1 < S;
-                    const float qA = (float)(sA + 1) * geo.dq, qB = (float)(sA + 2) * geo.dq;
-                    const float qA2 = qA * qA, qB2 = qB * qB;
-                    const float iqA = 1.0f / qA, iqB = 1.0f / qB;
-                    const float rsA = geo.shell_power ? powf(qA, geo.gamma_pow) : 1.0f;
-                    const float rsB = geo.shell_power ? powf(qB, geo.gamma_pow) : 1.0f;
                     const float qhi = vB ? qB : qA;
-                    int lo = 0, hi = 0;
                     for (int base = 0; base < np; base += 32) {
                         const int m = base + lane;
                         const float r = m < np ? sp[m].r : CUDART_INF_F;
                         lo += __popc(__ballot_sync(0xffffffffu, r <= qA - delta));
                         hi += __popc(__ballot_sync(0xffffffffu, r < qhi + delta));
                     }
+                }
+                if (hi > lo) {
+                    // rows start on 16-byte boundaries (N even: 16-byte accesses)
+                    if ((N & 1) == 0) {
+                        float4* z4 = reinterpret_cast<float4*>(z);
+                        float4* zz4 = reinterpret_cast<float4*>(zz);
+                        for (int j = lane; j < N / 2; j += 32) {
+                            z4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+                            zz4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
+                    } else {
+                        for (int j = lane; j < N; j += 32) {
+                            z[j] = make_float2(0.f, 0.f);
+                            zz[j] = make_float2(0.f, 0.f);
+                        }
+                    }
+                    __syncwarp();
+                    const float qA2 = qA * qA, qB2 = qB * qB;
+                    const float iqA = 1.0f / qA, iqB = 1.0f / qB;
+                    const float rsA = geo.shell_power ? powf(qA, geo.gamma_pow) : 1.0f;
+                    const float rsB = geo.shell_power ? powf(qB, geo.gamma_pow) : 1.0f;
                     const int half = lane >> 4, hl = lane & 15;
                     const unsigned hmask = 0xffffu << (16 * half);
                     float2* acc = half ? zz : z;
@@ -665,6 +669,9 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
                     w_hi = max(w_hi, sA + 2);
                 }
                 const bool any = anyA || anyB;
+                if (lane == 0 && any && out.rmask)
+                    atomicOr(reinterpret_cast<unsigned*>(s_int + 16 + (sA >> 5)),
+                             (anyA ? 1u << (sA & 31) : 0u) | (anyB ? 1u << ((sA + 1) & 31) : 0u));
                 if (any) {
                     __syncwarp();
                     if ((N & 1) == 0) {
@@ -708,7 +715,7 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
                         br = 0.5f * (zf.y + zc.y);
                         bi = 0.5f * (zc.x - zf.x);
                     }
-                    if (out.sre) {
+                    if (out.sre && (any || !out.rmask)) {
                         out.sre[srow + f] = ar;
                         out.sim[srow + f] = ai;
                         out.sre[srow + Fs + f] = br;
@@ -778,6 +785,8 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
             const int lo = s_int[40], hi = s_int[41];
             out.srange[item] = lo < hi ? make_int2(lo, hi) : make_int2(0, 0);
         }
+        if (out.rmask && threadIdx.x < (Spad >> 5))
+            out.rmask[item * (int64_t)(Spad >> 5) + threadIdx.x] = (uint32_t)s_int[16 + threadIdx.x];
         if (out.sumsq) {
             for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
             if (lane == 0) s_int[48 + warp] = __float_as_int(e);
