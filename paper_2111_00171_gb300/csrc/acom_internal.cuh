@@ -127,7 +127,7 @@ struct Workspace {
     float* U = nullptr;            // [chunk][Z] spectral bounds
     void* XB = nullptr;            // BF16 [F][PTs][128][Spad] (tensor-core operand, 16-row groups: 8 re, 8 im)
     int PTs = 0;                   // pattern tiles of 64 in XB
-    alignas(64) unsigned char map_x[2][128];  // TMA maps of XB: 128-byte rows, 64-byte rows
+    alignas(64) unsigned char map_x[128];   // TMA map of XB
     float* xfn = nullptr;          // [chunk][F] ||X^_bf|| over shells
     int* n_eval = nullptr;         // axes evaluated exactly in the last match
     int2* srange = nullptr;        // [chunk] non-zero shell range of each pattern
@@ -181,14 +181,11 @@ struct acom_plan_s {
     float* pfmax = nullptr;           // [F] max over axes of ||P^_zf|| over shells
     float pscale = 1.0f;              // 2^k of the FP16 plan spectra (1 otherwise)
     uint32_t* smask = nullptr;        // [Zp][Spad / 32] bit s: shell row s of the axis not zero
-    void* Pb_r = nullptr;             // BF16 or FP16 [F][Zp][Spad] (tensor-core operand)
-    void* Pb_i = nullptr;
-    // TMA maps of Pb_r, Pb_i (make_plan_maps): [k][re/im], k = 0 128-row boxes of
-    // 128-byte rows, 1 the same with 64-byte rows, 2 and 3 the tail tile's
-    // boxes of tail_w rows with 128- and 64-byte rows
-    alignas(64) unsigned char tmaps[4][2][128];
-    int tail_w = 0;                   // axes of a narrow last axis tile (16), or 0
-    int ktail64 = 0;                  // 1: the last K tile (32 shells) loads 64-byte rows
+    // tensor-core operand, BF16 / FP16 / E4M3 of 2^k P^: [F][Zp / 128][256][Spad],
+    // each 128-axis tile's real rows followed by its imaginary rows, so that one
+    // TMA box of 256 rows is the whole B operand of an MMA
+    void* Pb = nullptr;
+    alignas(64) unsigned char map_p[128];   // TMA map of Pb (boxes of 256 rows)
     float4* refl_tab = nullptr;       // [G] FP32 (g, |g|^gamma |F_g|^omega) for refinement
     unsigned long long* refine_pairs = nullptr;  // (reflection, peak) pairs of the last refine
     int64_t last_refine_pairs = 0;
@@ -272,21 +269,18 @@ void launch_plan_fnorm_max(const acom_plan_s* p, float* out, cudaStream_t st);
 void launch_plan_shell_mask(const acom_plan_s* p, cudaStream_t st);
 // match_tc.cu
 acom_status make_bf16_map(void* map_storage, const void* base, uint64_t rows, uint64_t cols,
-                          int kind = 0, int box_rows = 128, int row_bytes = 128);
-// the plan's operand maps (p->tmaps) and its tail / K-tile choices
-acom_status make_plan_maps(acom_plan_s* p);
-// both maps of a pattern operand XB (rows x Spad): [0] 128-byte rows, [1] 64-byte rows
-acom_status make_pattern_maps(void* maps2, const void* XB, uint64_t rows, int Spad, int kind);
+                          int kind = 0, int box_rows = 128);
 void launch_half_to_e4m3(const void* src, void* dst, int64_t n, float mul, cudaStream_t st);
 // budget in clock cycles of the tensor-core contraction's pipeline waits (0: default)
 void set_wait_cycles(long long cycles);
 // xscale: per-pattern 2^e of FP16 pattern spectra (nullptr: BF16, no scale)
-void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x2, int pt_stride, int nb,
+void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_stride, int nb,
                               float* U, cudaStream_t st, const float* xscale = nullptr,
                               int tile_order = 0);
-// kind 1 / 2: FP16 / E4M3 of scale * src instead of BF16 of src
-void launch_plan_to_bf16(const float* src, int Zp, int F, int Spad, void* dst, cudaStream_t st,
-                         int kind = 0, float scale = 1.0f);
+// the plan's FP32 spectra Pr, Pi [Zp][F][Spad] -> the merged operand p->Pb:
+// BF16 of P^ (kind 0), FP16 (1) or E4M3 (2) of scale * P^
+void launch_plan_to_operand(const float* Pr, const float* Pi, int Zp, int F, int Spad, void* dst,
+                            cudaStream_t st, int kind, float scale);
 void launch_orient_compose(const acom_plan_s* p, const OrientIn* oin, int nb, int refine,
                            acom_result out, int64_t off, cudaStream_t st);
 void launch_select_exact(const acom_plan_s* p, const float* Xsr, const float* Xsi, const float* U,

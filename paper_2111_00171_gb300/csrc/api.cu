@@ -162,15 +162,14 @@ static void free_workspace(Workspace& ws, cudaStream_t st) {
 }
 
 // need_fmajor: the frequency-major pattern spectra (FP32 contraction, export)
-static acom_status ensure_workspace(acom_plan_s* p, int chunk, bool need_chat, bool need_fmajor,
-                                    cudaStream_t st) {
-    if (p->ws.chunk >= chunk && (!need_chat || p->ws.Chat) && (!need_fmajor || p->ws.Xr))
+static acom_status ensure_ws(acom_plan_s* p, Workspace& ws, int chunk, bool need_chat,
+                             bool need_fmajor, cudaStream_t st) {
+    if (ws.chunk >= chunk && (!need_chat || ws.Chat) && (!need_fmajor || ws.Xr))
         return ACOM_OK;
-    need_chat = need_chat || p->ws.Chat;
-    need_fmajor = need_fmajor || need_chat || p->ws.Xr;
-    if (p->ws.chunk > chunk) chunk = p->ws.chunk;
-    free_workspace(p->ws, st);
-    Workspace& ws = p->ws;
+    need_chat = need_chat || ws.Chat;
+    need_fmajor = need_fmajor || need_chat || ws.Xr;
+    if (ws.chunk > chunk) chunk = ws.chunk;
+    free_workspace(ws, st);
     size_t acc = 0;
     const size_t spec = (size_t)chunk * p->F * p->Spad;
     const size_t sspec = (size_t)chunk * shell_row_stride(p->F) * p->Spad;
@@ -210,10 +209,10 @@ static acom_status ensure_workspace(acom_plan_s* p, int chunk, bool need_chat, b
             acc += rows * p->Spad;
         }
         if (scaled && (e = dalloc(&ws.xscale, (size_t)chunk, &acc, st)) != cudaSuccess) goto fail;
-        acom_status ms = make_pattern_maps(ws.map_x, fp8 ? ws.XB8 : ws.XB, rows, p->Spad,
-                                           tc_kind(p->precision));
+        acom_status ms = make_bf16_map(ws.map_x, fp8 ? ws.XB8 : ws.XB, rows, (uint64_t)p->Spad,
+                                       tc_kind(p->precision));
         if (ms != ACOM_OK) {
-            free_workspace(p->ws, st);
+            free_workspace(ws, st);
             return ms;
         }
     }
@@ -221,8 +220,13 @@ static acom_status ensure_workspace(acom_plan_s* p, int chunk, bool need_chat, b
     ws.bytes = acc;
     return ACOM_OK;
 fail:
-    free_workspace(p->ws, st);
+    free_workspace(ws, st);
     return cuda_error(e, "match workspace allocation");
+}
+
+static acom_status ensure_workspace(acom_plan_s* p, int chunk, bool need_chat, bool need_fmajor,
+                                    cudaStream_t st) {
+    return ensure_ws(p, p->ws, chunk, need_chat, need_fmajor, st);
 }
 
 // Every library call has synchronised its stream before returning, so the
@@ -243,8 +247,7 @@ static void destroy_plan(acom_plan_s* p) {
     pool_free(p->refl_amp, st);
     pool_free(p->err, st);
     pool_free(p->pfmax, st);
-    pool_free(p->Pb_r, st);
-    pool_free(p->Pb_i, st);
+    pool_free(p->Pb, st);
     pool_free(p->phase_off, st);
     pool_free(p->refl_tab, st);
     pool_free(p->refine_pairs, st);
@@ -418,13 +421,12 @@ acom_status acom_plan_create(const acom_crystal* crystal, const acom_za_grid* gr
         p->pscale = kind == 0 ? 1.0f
                               : fp16_plan_scale(p->N) * (kind == 2 ? kFp8Shift : 1.0f);
         const size_t n = (size_t)p->F * p->Zp * p->Spad * tc_elem_bytes(p->precision);
-        ACOM_CK(pool_alloc(&p->Pb_r, n, st));
-        ACOM_CK(pool_alloc(&p->Pb_i, n, st));
+        ACOM_CK(pool_alloc(&p->Pb, 2 * n, st));
         p->bytes += 2 * n;
-        launch_plan_to_bf16(p->Pr, p->Zp, p->F, p->Spad, p->Pb_r, st, kind, p->pscale);
-        launch_plan_to_bf16(p->Pi, p->Zp, p->F, p->Spad, p->Pb_i, st, kind, p->pscale);
+        launch_plan_to_operand(p->Pr, p->Pi, p->Zp, p->F, p->Spad, p->Pb, st, kind, p->pscale);
         ACOM_CK(cudaGetLastError());
-        s = make_plan_maps(p);
+        s = make_bf16_map(p->map_p, p->Pb, (uint64_t)p->F * p->Zp * 2, (uint64_t)p->Spad, kind,
+                          256);
         if (s != ACOM_OK) {
             destroy_plan(p);
             return s;
@@ -566,24 +568,18 @@ acom_status acom_plan_concat(const acom_plan* plans, int32_t n_plans, void* cuda
     ACOM_CK(dalloc(&p->smask, (size_t)p->Zp * (Spad / 32), &p->bytes, st));
     launch_plan_shell_mask(p, st);
     if (tc_precision(p->precision)) {
-        // [F][Zp][Spad] operand tiles: per frequency, each input's Z rows at its offset
+        // the merged [F][Zp / 128][256][Spad] operand of the concatenation
         const int kind = tc_kind(p->precision);
         const size_t eb = (size_t)tc_elem_bytes(p->precision);
         const size_t n = (size_t)F * p->Zp * Spad;
-        ACOM_CK(pool_alloc(&p->Pb_r, n * eb, st));
-        ACOM_CK(pool_alloc(&p->Pb_i, n * eb, st));
+        ACOM_CK(pool_alloc(&p->Pb, 2 * n * eb, st));
         p->bytes += 2 * n * eb;
-        ACOM_CK(cudaMemsetAsync(p->Pb_r, 0, n * eb, st));
-        ACOM_CK(cudaMemsetAsync(p->Pb_i, 0, n * eb, st));
-        const size_t row = (size_t)Spad * eb;
-        for (int i = 0, base = 0; i < n_plans; base += plans[i]->Z, ++i) {
-            const acom_plan_s* q = plans[i];
-            ACOM_CK(cudaMemcpy2DAsync(static_cast<char*>(p->Pb_r) + base * row, p->Zp * row, q->Pb_r,
-                                      q->Zp * row, q->Z * row, F, cudaMemcpyDeviceToDevice, st));
-            ACOM_CK(cudaMemcpy2DAsync(static_cast<char*>(p->Pb_i) + base * row, p->Zp * row, q->Pb_i,
-                                      q->Zp * row, q->Z * row, F, cudaMemcpyDeviceToDevice, st));
-        }
-        acom_status s = make_plan_maps(p);
+        // the merged operand from the concatenated FP32 spectra (the phases'
+        // axes no longer start on 128-axis tiles)
+        launch_plan_to_operand(p->Pr, p->Pi, p->Zp, F, Spad, p->Pb, st, kind, p->pscale);
+        ACOM_CK(cudaGetLastError());
+        acom_status s = make_bf16_map(p->map_p, p->Pb, (uint64_t)F * p->Zp * 2, (uint64_t)Spad,
+                                      kind, 256);
         if (s != ACOM_OK) {
             cudaStreamSynchronize(st);
             destroy_plan(p);
@@ -740,10 +736,10 @@ static float kappa_tc(const acom_plan_s* p) {
 }
 
 // the FP16 raster rows of a chunk into the E4M3 operand (FP8 plans)
-static void convert_fp8(acom_plan_s* p, cudaStream_t st) {
+static void convert_fp8(acom_plan_s* p, const Workspace& ws, cudaStream_t st) {
     if (p->precision != ACOM_PREC_FP8) return;
-    const int64_t n = (int64_t)p->F * p->ws.PTs * 128 * p->Spad;
-    launch_half_to_e4m3(p->ws.XB, p->ws.XB8, n, kFp8Shift, st);
+    const int64_t n = (int64_t)p->F * ws.PTs * 128 * p->Spad;
+    launch_half_to_e4m3(ws.XB, ws.XB8, n, kFp8Shift, st);
 }
 
 // Everything acom_match does up to the read of the error word: validation,
@@ -790,49 +786,48 @@ static acom_status match_enqueue(acom_plan p, const acom_peaks_csr* peaks,
     launch_check_row0(peaks->row_ptr, p->err, st);
     RasterGeom geo{p->S, p->Spad, p->N, p->F, (float)p->dq, (float)p->delta, (float)p->gamma_pow, 0};
     const int wchunk = p->ws.chunk;
+    Workspace& w = p->ws;
     for (int64_t c0 = 0; c0 < B; c0 += chunk) {
         const int nb = (int)std::min<int64_t>(chunk, B - c0);
         const bool tc = !exhaustive && tc_precision(p->precision);
-        float* xscale = tc && p->precision != ACOM_PREC_BF16 ? p->ws.xscale : nullptr;
-        PatternSource src{tc ? p->ws.XB : nullptr, p->ws.PTs, peaks->row_ptr + c0, peaks->qx,
+        float* xscale = tc && p->precision != ACOM_PREC_BF16 ? w.xscale : nullptr;
+        PatternSource src{tc ? w.XB : nullptr, w.PTs, peaks->row_ptr + c0, peaks->qx,
                           peaks->qy, peaks->I, nb, (float)p->gamma_pow, (float)p->omega,
                           xscale ? 1 : 0, xscale};
         RasterOut ro;
-        ro.re = fp32_contraction ? p->ws.Xr : nullptr;
-        ro.im = fp32_contraction ? p->ws.Xi : nullptr;
-        ro.sre = p->ws.Xsr;
-        ro.sim = p->ws.Xsi;
-        ro.sumsq = p->ws.xnorm2;
-        ro.fnorm = p->ws.xfn;
-        ro.srange = p->ws.srange;
+        ro.re = fp32_contraction ? w.Xr : nullptr;
+        ro.im = fp32_contraction ? w.Xi : nullptr;
+        ro.sre = w.Xsr;
+        ro.sim = w.Xsi;
+        ro.sumsq = w.xnorm2;
+        ro.fnorm = w.xfn;
+        ro.srange = w.srange;
         // select reads only the rows the pattern's tents reach
-        ro.rmask = exhaustive ? nullptr : p->ws.rmask;
+        ro.rmask = exhaustive ? nullptr : w.rmask;
         launch_raster_patterns(geo, src, ro, p->err, st);
         if (exhaustive) {
-            cudaMemsetAsync(p->ws.best, 0, sizeof(unsigned long long) * nb, st);
-            launch_contract_fp32(p, p->ws.Xr, p->ws.Xi, nb, p->ws.Chat, wchunk, st);
-            launch_idft_argmax_fp32(p, p->ws.Chat, nb, wchunk, p->ws.za_scores, p->ws.best, st);
-            launch_refine(p, p->ws.Chat, nb, wchunk, p->ws.za_scores, p->ws.best, p->ws.xnorm2,
-                          refine, *out, c0, st);
+            cudaMemsetAsync(w.best, 0, sizeof(unsigned long long) * nb, st);
+            launch_contract_fp32(p, w.Xr, w.Xi, nb, w.Chat, wchunk, st);
+            launch_idft_argmax_fp32(p, w.Chat, nb, wchunk, w.za_scores, w.best, st);
+            launch_refine(p, w.Chat, nb, wchunk, w.za_scores, w.best, w.xnorm2, refine, *out, c0,
+                          st);
             if (out->za_scores)
-                cudaMemcpyAsync(out->za_scores + c0 * (int64_t)p->Z, p->ws.za_scores,
+                cudaMemcpyAsync(out->za_scores + c0 * (int64_t)p->Z, w.za_scores,
                                 sizeof(float) * (size_t)nb * p->Z, cudaMemcpyDeviceToDevice, st);
             if (out->phase || out->phase_score)
-                launch_phase_outputs(p, p->ws.za_scores, nb, *out, c0, st);
+                launch_phase_outputs(p, w.za_scores, nb, *out, c0, st);
         } else {
             if (tc) {
-                convert_fp8(p, st);
-                launch_contract_bound_tc(p, p->ws.map_x, p->ws.PTs, nb, p->ws.U, st, xscale,
-                                         tile_order);
+                convert_fp8(p, w, st);
+                launch_contract_bound_tc(p, w.map_x, w.PTs, nb, w.U, st, xscale, tile_order);
             } else {
-                launch_contract_bound_fp32(p, p->ws.Xr, p->ws.Xi, nb, p->ws.U, st);
+                launch_contract_bound_fp32(p, w.Xr, w.Xi, nb, w.U, st);
             }
-            launch_select_exact(p, p->ws.Xsr, p->ws.Xsi, p->ws.U, p->ws.xfn, p->ws.srange,
-                                p->ws.rmask, p->pfmax, p->ws.xnorm2, nb,
-                                tc ? kappa_tc(p) : kappa_fp32(p), refine, *out, c0,
-                                p->ws.n_eval, st, xscale, rescore_top, p->ws.oin);
+            launch_select_exact(p, w.Xsr, w.Xsi, w.U, w.xfn, w.srange, w.rmask, p->pfmax,
+                                w.xnorm2, nb, tc ? kappa_tc(p) : kappa_fp32(p), refine, *out,
+                                c0, w.n_eval, st, xscale, rescore_top, w.oin);
             if (out->phi3 || out->orient)
-                launch_orient_compose(p, p->ws.oin, nb, refine, *out, c0, st);
+                launch_orient_compose(p, w.oin, nb, refine, *out, c0, st);
         }
     }
     cudaError_t e = cudaGetLastError();
@@ -921,7 +916,7 @@ acom_status acom_bounds(acom_plan p, const acom_peaks_csr* peaks, float* dst, vo
         launch_raster_patterns(geo, src, ro, p->err, st);
         float* U = dst + c0 * (int64_t)p->Z;
         if (tc) {
-            convert_fp8(p, st);
+            convert_fp8(p, p->ws, st);
             launch_contract_bound_tc(p, p->ws.map_x, p->ws.PTs, nb, U, st, xscale);
         } else {
             launch_contract_bound_fp32(p, p->ws.Xr, p->ws.Xi, nb, U, st);

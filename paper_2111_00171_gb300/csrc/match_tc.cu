@@ -28,16 +28,17 @@
 // committed by the owner of each use; the producer issues the next use only
 // after that commit, so those phases are ordered too.
 //
-// CTA: one TMA producer warp, two MMA-issuing warps, sixteen epilogue warps;
-// persistent over (64-pattern x 128-axis) tiles; operands stream through a
-// 4-stage shared-memory ring (K tiles of 64 16-bit operands = 128-byte rows,
-// 128-byte swizzle); accumulators are double-buffered over f in 512 TMEM
-// columns.  The TMA engine's rate (about one cycle per box row plus about
-// 100 bytes per cycle per SM, measured) bounds this kernel, so box rows that
-// carry no work are avoided: a last K tile of 32 shells (160 = 64 + 64 + 32)
-// loads 64-byte rows with 64-byte swizzle instead of half-zero 128-byte rows,
-// and a last axis tile holding at most 16 axes (903 = 7 x 128 + 7) loads
-// 16-row boxes of the plan and runs N = 32 MMAs instead of N = 256.
+// CTA: two TMA producer warps (warp 0 loads the pattern operand X, warp 3 the
+// plan operand: one box of 256 rows, the axis tile's real rows followed by its
+// imaginary rows), two MMA-issuing warps, sixteen epilogue warps; persistent
+// over (64-pattern x 128-axis) tiles; operands stream through a 4-stage
+// shared-memory ring (K tiles of 64 BF16 = 128-byte rows, 128-byte swizzle;
+// the last tile of 160 shells is half zero fill); accumulators are
+// double-buffered over f in 512 TMEM columns.  Issuing a TMA copy costs the
+// issuing thread a few hundred cycles whatever the box (measured: one thread
+// issuing three boxes per stage was busy 80 % of the time, and halving the
+// boxes' rows or bytes changed nothing), so the copies of a stage are
+// issued by two threads and the plan operand is one box.
 // Every mbarrier wait is bounded: a timeout sets the device error word, stops
 // all roles, drains copies and MMAs in flight, frees TMEM and returns.
 #include <cuda.h>
@@ -61,7 +62,9 @@ constexpr int kTileBytes = 128 * kKT * 2;      // 16 KB
 constexpr int kStageBytes = 3 * kTileBytes;    // X, then Pr and Pi as one 256-row operand
 constexpr int kEpiWarps = 16;
 constexpr int kIssuers = 2;                    // MMA-issuing warps, one per TMEM buffer
-constexpr int kThreads = (1 + kIssuers + kEpiWarps) * 32;
+constexpr int kProdP = 1 + kIssuers;           // warp of the plan-operand producer
+constexpr int kEpi0 = kProdP + 1;               // first epilogue warp
+constexpr int kThreads = (kEpi0 + kEpiWarps) * 32;
 constexpr uint32_t kTmemCols = 512;
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
 
@@ -137,16 +140,6 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     return d;
 }
 
-// the same for 64-byte rows with 64-byte swizzle (8-row groups 512 B apart)
-__device__ __forceinline__ uint64_t sdesc64(uint32_t saddr) {
-    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;
-    d |= (uint64_t)(512 >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)4 << 61;               // 64-byte swizzle
-    return d;
-}
-
 __device__ __forceinline__ void mma_f16kind(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
                                             uint32_t idesc, uint32_t accumulate) {
     asm volatile(
@@ -196,21 +189,6 @@ __device__ __forceinline__ void fence_after() {
                    "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), \
                    "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])                        \
                  : "r"(taddr))
-
-// 16 TMEM lanes x 16 columns: r[4n .. 4n+3] as for the x4 load, n = 0, 1
-#define ACOM_TMEM_LD16x256_X2(taddr, r)                                                     \
-    asm volatile("tcgen05.ld.sync.aligned.16x256b.x2.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];" \
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),  \
-                   "=r"(r[6]), "=r"(r[7])                                                   \
-                 : "r"(taddr))
-
-#define ACOM_TMEM_WAIT16(p, q)                                                              \
-    asm volatile("tcgen05.wait::ld.sync.aligned;"                                           \
-                 : "+r"(p[0]), "+r"(p[1]), "+r"(p[2]), "+r"(p[3]), "+r"(p[4]), "+r"(p[5]),  \
-                   "+r"(p[6]), "+r"(p[7]), "+r"(q[0]), "+r"(q[1]), "+r"(q[2]), "+r"(q[3]),  \
-                   "+r"(q[4]), "+r"(q[5]), "+r"(q[6]), "+r"(q[7])                          \
-                 :                                                                          \
-                 : "memory")
 
 // wait for this thread's TMEM loads; the registers are tied to the wait so no
 // use can be scheduled before it
@@ -272,7 +250,7 @@ struct TcArgs {
     int F, N, Z, nb, ZT, PT, KT;   // frequencies, bins, axes, patterns, axis tiles, pattern tiles, K tiles
     int PTs;                       // pattern tiles per frequency in the pattern map (row stride)
     int Spad;                      // shells (K) in the operand rows
-    int Zrows;                     // rows per frequency in the plan map (ZT * 128)
+    int Zrows;                     // rows per frequency in the plan map (ZT * 256)
     float* U;                      // [nb][Z]
     int* err;
     uint32_t idesc;                // MMA instruction descriptor (operand format)
@@ -283,9 +261,6 @@ struct TcArgs {
                                    // tile, 1 they share an axis tile
     long long wait_cycles;         // budget of each pipeline wait (the drain waits
                                    // that precede the exit always take kWaitCycles)
-    int tail_w;                    // axes of a narrow last axis tile (16), or 0
-    int ktail64;                   // 1: the last K tile (32 shells) has 64-byte rows
-    uint32_t idesc_tail;           // the narrow tile's MMA descriptor (N = 2 tail_w)
 };
 
 // F8: E4M3 operands (kind::f8f6f4, 128 elements per K tile), else 16-bit
@@ -293,16 +268,8 @@ struct TcArgs {
 // loop carries no branch on it
 template <bool F8>
 __global__ void __launch_bounds__(kThreads, 1)
-k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
-                    const __grid_constant__ CUtensorMap map_pi,
-                    const __grid_constant__ CUtensorMap map_x,
-                    const __grid_constant__ CUtensorMap map_pr64,
-                    const __grid_constant__ CUtensorMap map_pi64,
-                    const __grid_constant__ CUtensorMap map_x64,
-                    const __grid_constant__ CUtensorMap map_prt,
-                    const __grid_constant__ CUtensorMap map_pit,
-                    const __grid_constant__ CUtensorMap map_prt64,
-                    const __grid_constant__ CUtensorMap map_pit64, TcArgs a) {
+k_contract_bound_tc(const __grid_constant__ CUtensorMap map_p,
+                    const __grid_constant__ CUtensorMap map_x, TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte alignment of the operand ring
     unsigned char* base = reinterpret_cast<unsigned char*>(
@@ -319,7 +286,8 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kIssuers * kStages; ++s) mbar_init(smem_u32(full + s), 1);
+        // a full barrier completes on both producers' arrivals and their bytes
+        for (int s = 0; s < kIssuers * kStages; ++s) mbar_init(smem_u32(full + s), 2);
         for (int s = 0; s < kStages; ++s) mbar_init(smem_u32(empty + s), 1);
         for (int b = 0; b < kIssuers; ++b) {
             mbar_init(smem_u32(tfull + b), 1);
@@ -328,18 +296,8 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_pr)));
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_pi)));
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_p)));
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_x)));
-        if (a.ktail64) {
-            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_pr64)));
-            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_pi64)));
-            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_x64)));
-        }
-        if (a.tail_w) {
-            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_prt)));
-            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_pit)));
-        }
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -354,8 +312,10 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
     const uint32_t tmem = *tmem_slot;
     const int n_tiles = a.ZT * a.PT;
 
-    if (warp == 0) {
-        // ------------------------------------------------ TMA producer
+    if (warp == 0 || warp == kProdP) {
+        // ------------------------------------------------ TMA producers: warp 0
+        // the pattern operand, warp kProdP the plan operand of every stage
+        const bool xprod = warp == 0;
         if (lane == 0) {
             int stage = 0;
             uint32_t phase = 0;
@@ -368,11 +328,8 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
             for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
                 const int zt = a.zmajor ? t / a.PT : t % a.ZT;
                 const int pt = a.zmajor ? t % a.PT : t / a.ZT;
-                // the narrow last axis tile: tail_w plan rows of re and im
-                const bool tailt = a.tail_w > 0 && zt == a.ZT - 1;
-                const int prows = tailt ? a.tail_w : kM;
                 for (int f = 0; f < a.F && ok; ++f, ++fcount) {
-                    const int prow = f * a.Zrows + zt * kM;
+                    const int prow = f * a.Zrows + zt * 256;
                     const int xrow = (f * a.PTs + pt) * 128;
                     const int own = fcount & 1;
                     for (int kt = 0; kt < a.KT; ++kt) {
@@ -381,23 +338,16 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
                             break;
                         }
                         const uint32_t fb = smem_u32(full + own * kStages + stage);
-                        // a last K tile of 32 shells: 64-byte rows
-                        const bool k64 = a.ktail64 && kt == a.KT - 1;
-                        const int rb = k64 ? 64 : 128;
-                        mbar_expect_tx(fb, (uint32_t)((128 + 2 * prows) * rb));
                         unsigned char* sbuf = ring + stage * kStageBytes;
                         constexpr int ktel = F8 ? kKT8 : kKT;
-                        const CUtensorMap* mx = k64 ? &map_x64 : &map_x;
-                        const CUtensorMap* mr = tailt ? (k64 ? &map_prt64 : &map_prt)
-                                                      : (k64 ? &map_pr64 : &map_pr);
-                        const CUtensorMap* mi = tailt ? (k64 ? &map_pit64 : &map_pit)
-                                                      : (k64 ? &map_pi64 : &map_pi);
-                        // X rows at 0, then the B operand at kTileBytes: re rows,
-                        // then im rows right after them
-                        tma_load_2d(smem_u32(sbuf), mx, kt * ktel, xrow, fb);
-                        tma_load_2d(smem_u32(sbuf + kTileBytes), mr, kt * ktel, prow, fb);
-                        tma_load_2d(smem_u32(sbuf + kTileBytes + prows * rb), mi, kt * ktel, prow,
-                                    fb);
+                        if (xprod) {
+                            mbar_expect_tx(fb, kTileBytes);
+                            tma_load_2d(smem_u32(sbuf), &map_x, kt * ktel, xrow, fb);
+                        } else {
+                            // B operand: 256 rows, the tile's re rows then its im rows
+                            mbar_expect_tx(fb, 2 * kTileBytes);
+                            tma_load_2d(smem_u32(sbuf + kTileBytes), &map_p, kt * ktel, prow, fb);
+                        }
                         issued_mask |= 1u << stage;
                         const uint32_t par = (fpar[own] >> stage) & 1u;
                         last_par = (last_par & ~(1u << stage)) | (par << stage);
@@ -438,9 +388,6 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
             bool ok = true;
             uint64_t* myfull = full + mi * kStages;
             for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-                const int zt = a.zmajor ? t / a.PT : t % a.ZT;
-                const bool tailt = a.tail_w > 0 && zt == a.ZT - 1;
-                const uint32_t idesc = tailt ? a.idesc_tail : a.idesc;
                 for (int f = 0; f < a.F && ok; ++f, ++fcount) {
                     if ((fcount & 1) != mi) {
                         stage = (stage + a.KT) % kStages;
@@ -468,17 +415,15 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
                         // 32 bytes (2 units of 16)
                         constexpr int ktel = F8 ? kKT8 : kKT;
                         const int nk = (min(ktel, a.Spad - kt * ktel) * (F8 ? 1 : 2)) >> 5;
-                        const bool k64 = a.ktail64 && kt == a.KT - 1;
-                        const uint64_t xa = k64 ? sdesc64(sb) : sdesc(sb);
-                        const uint64_t pb = k64 ? sdesc64(sb + kTileBytes) : sdesc(sb + kTileBytes);
+                        const uint64_t xa = sdesc(sb), pb = sdesc(sb + kTileBytes);
 #pragma unroll
                         for (int k4 = 0; k4 < 4; ++k4)
                             if (k4 < nk) {
                                 if constexpr (F8)
-                                    mma_f8kind(dacc, xa + 2 * k4, pb + 2 * k4, idesc,
+                                    mma_f8kind(dacc, xa + 2 * k4, pb + 2 * k4, a.idesc,
                                                (kt | k4) ? 1u : 0u);
                                 else
-                                    mma_f16kind(dacc, xa + 2 * k4, pb + 2 * k4, idesc,
+                                    mma_f16kind(dacc, xa + 2 * k4, pb + 2 * k4, a.idesc,
                                                 (kt | k4) ? 1u : 0u);
                             }
                         mma_commit(smem_u32(empty + stage));       // frees the stage
@@ -497,7 +442,7 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
     } else {
         // ------------------------------------------------ epilogue
         const int q = warp & 3;                  // TMEM lane quarter: patterns 16q .. 16q + 15
-        const int zq = (warp - 1 - kIssuers) >> 2;   // axis columns 32 zq .. 32 zq + 31
+        const int zq = (warp - kEpi0) >> 2;      // axis columns 32 zq .. 32 zq + 31
         const float invN = 1.0f / (float)a.N;
         float ud[16];
 #pragma unroll
@@ -508,7 +453,6 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
         for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
             const int zt = a.zmajor ? t / a.PT : t % a.ZT;
             const int pt = a.zmajor ? t % a.PT : t / a.ZT;
-            const bool tailt = a.tail_w > 0 && zt == a.ZT - 1;
             for (int f = 0; f < a.F; ++f, ++fcount) {
                 const int buf = fcount & 1;
                 if (!mbar_wait(smem_u32(tfull + buf), tph[buf], abort_flag, a.err, a.wait_cycles)) {
@@ -519,32 +463,6 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_pr,
                 fence_after();
                 const float w = (f == 0 || 2 * f == a.N) ? 1.f : 2.f;
                 const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + buf * 256 + zq * 32;
-                if (tailt) {
-                    // N = 32: columns 0..15 the 16 axes' re products, 16..31 their im
-                    // products; the warps of the first 32 columns take them
-                    if (zq == 0) {
-                        uint32_t R0[8], I0[8], R1[8], I1[8];
-                        ACOM_TMEM_LD16x256_X2(tb, R0);
-                        ACOM_TMEM_LD16x256_X2(tb + 16, I0);
-                        ACOM_TMEM_LD16x256_X2(tb + (16u << 16), R1);
-                        ACOM_TMEM_LD16x256_X2(tb + (16u << 16) + 16, I1);
-                        ACOM_TMEM_WAIT16(R0, I0);
-                        ACOM_TMEM_WAIT16(R1, I1);
-#pragma unroll
-                        for (int n = 0; n < 2; ++n) {
-                            accumulate_pair2(R0[4 * n], R0[4 * n + 1], R0[4 * n + 2], R0[4 * n + 3],
-                                             I0[4 * n], I0[4 * n + 1], I0[4 * n + 2], I0[4 * n + 3],
-                                             w, ud[2 * n], ud[2 * n + 1]);
-                            accumulate_pair2(R1[4 * n], R1[4 * n + 1], R1[4 * n + 2], R1[4 * n + 3],
-                                             I1[4 * n], I1[4 * n + 1], I1[4 * n + 2], I1[4 * n + 3],
-                                             w, ud[8 + 2 * n], ud[8 + 2 * n + 1]);
-                        }
-                    }
-                    fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(smem_u32(tempty + buf));
-                    continue;
-                }
                 // two halves of 8 patterns (16 lanes each); the second half's
                 // loads are in flight while the first is reduced
                 uint32_t R0[16], I0[16], R1[16], I1[16];
@@ -622,66 +540,32 @@ static bool get_encoder() {
     return true;
 }
 
-// 2-D operand map: rows x cols (cols contiguous), boxes of row_bytes (128 or
-// 64) bytes x box_rows rows with the swizzle of that width; boxes reaching
+// 2-D operand map: rows x cols (cols contiguous), boxes of 128 bytes x box_rows
+// rows (64 16-bit or 128 8-bit columns), 128-byte swizzle; boxes reaching
 // past the last column are zero-filled.  kind: 0 BF16, 1 FP16, 2 E4M3 (as
 // bytes).
 acom_status make_bf16_map(void* map_storage, const void* base, uint64_t rows, uint64_t cols,
-                          int kind, int box_rows, int row_bytes) {
+                          int kind, int box_rows) {
     if (!get_encoder()) return set_error(ACOM_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
     const uint64_t eb = kind == 2 ? 1 : 2;
     if ((cols * eb) % 16 != 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0)
         return set_error(ACOM_ERR_INVALID_ARG, "tensor map: stride or base not 16-byte aligned");
-    if ((row_bytes != 128 && row_bytes != 64) || box_rows < 8 || box_rows > 256)
-        return set_error(ACOM_ERR_INVALID_ARG, "tensor map: unsupported box");
     CUtensorMap* m = reinterpret_cast<CUtensorMap*>(map_storage);
     const cuuint64_t dims[2] = {cols, rows};
     const cuuint64_t strides[1] = {cols * eb};
-    const cuuint32_t box[2] = {(cuuint32_t)(row_bytes / eb), (cuuint32_t)box_rows};
+    if (box_rows < 8 || box_rows > 256 || box_rows % 8 != 0)
+        return set_error(ACOM_ERR_INVALID_ARG, "tensor map: unsupported box");
+    const cuuint32_t box[2] = {(cuuint32_t)(kind == 2 ? tc::kKT8 : tc::kKT), (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     const CUtensorMapDataType dt = kind == 2   ? CU_TENSOR_MAP_DATA_TYPE_UINT8
                                    : kind == 1 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    CUresult r = g_encode(m, dt, 2, const_cast<void*>(base), dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
-                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = g_encode(m, dt, 2, const_cast<void*>(base), dims,
+                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(ACOM_ERR_CUDA, "cuTensorMapEncodeTiled failed");
     return ACOM_OK;
-}
-
-// 16-bit operands whose shells end in a 32-wide K tile load it as 64-byte rows
-static bool use_ktail64(int precision, int Spad) {
-    return precision != ACOM_PREC_FP8 && Spad % tc::kKT == 32;
-}
-
-acom_status make_plan_maps(acom_plan_s* p) {
-    const int kind = tc_kind(p->precision);
-    const uint64_t rows = (uint64_t)p->F * p->Zp, cols = (uint64_t)p->Spad;
-    // a last axis tile with at most 16 axes becomes a narrow tile (16-bit operands)
-    const int tail = p->Z - (p->Zp / tc::kM - 1) * tc::kM;
-    p->tail_w = (p->precision != ACOM_PREC_FP8 && tail > 0 && tail <= 16) ? 16 : 0;
-    p->ktail64 = use_ktail64(p->precision, p->Spad) ? 1 : 0;
-    const void* base[2] = {p->Pb_r, p->Pb_i};
-    for (int c = 0; c < 2; ++c) {
-        acom_status s = make_bf16_map(p->tmaps[0][c], base[c], rows, cols, kind, tc::kM, 128);
-        if (s == ACOM_OK && p->ktail64)
-            s = make_bf16_map(p->tmaps[1][c], base[c], rows, cols, kind, tc::kM, 64);
-        if (s == ACOM_OK && p->tail_w)
-            s = make_bf16_map(p->tmaps[2][c], base[c], rows, cols, kind, p->tail_w, 128);
-        if (s == ACOM_OK && p->tail_w && p->ktail64)
-            s = make_bf16_map(p->tmaps[3][c], base[c], rows, cols, kind, p->tail_w, 64);
-        if (s != ACOM_OK) return s;
-    }
-    return ACOM_OK;
-}
-
-acom_status make_pattern_maps(void* maps2, const void* XB, uint64_t rows, int Spad, int kind) {
-    unsigned char* m = reinterpret_cast<unsigned char*>(maps2);
-    acom_status s = make_bf16_map(m, XB, rows, (uint64_t)Spad, kind, 128, 128);
-    if (s == ACOM_OK && kind != 2 && Spad % tc::kKT == 32)
-        s = make_bf16_map(m + 128, XB, rows, (uint64_t)Spad, kind, 128, 64);
-    return s;
 }
 
 size_t tensor_map_bytes() { return sizeof(CUtensorMap); }
@@ -691,7 +575,7 @@ size_t tensor_map_bytes() { return sizeof(CUtensorMap); }
 static long long g_wait_cycles = 0;
 void set_wait_cycles(long long cycles) { g_wait_cycles = cycles > 0 ? cycles : 0; }
 
-void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x2, int pt_stride, int nb,
+void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_stride, int nb,
                               float* U, cudaStream_t st, const float* xscale, int tile_order) {
     tc::TcArgs a;
     a.zmajor = tile_order == 1 ? 1 : 0;
@@ -706,7 +590,7 @@ void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x2, int pt_s
     const int ktel = f8 ? tc::kKT8 : tc::kKT;
     a.KT = (p->Spad + ktel - 1) / ktel;
     a.Spad = p->Spad;
-    a.Zrows = p->Zp;
+    a.Zrows = 2 * p->Zp;
     a.U = U;
     a.err = p->err;
     // E4M3 is format 0 for A and B, the same bits as F16
@@ -715,10 +599,6 @@ void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x2, int pt_s
     a.xs_mul = f8 ? kFp8Shift : 1.0f;
     a.inv_pscale = 1.0f / p->pscale;
     a.wait_cycles = g_wait_cycles > 0 ? g_wait_cycles : tc::kWaitCycles;
-    a.tail_w = p->tail_w;
-    a.ktail64 = p->ktail64;
-    // the narrow tile's descriptor: N = 2 tail_w instead of 256
-    a.idesc_tail = (a.idesc & ~(0x3Fu << 17)) | ((uint32_t)(2 * p->tail_w) >> 3) << 17;
     const size_t smem = tc::tc_smem_bytes();
     auto kern = f8 ? tc::k_contract_bound_tc<true> : tc::k_contract_bound_tc<false>;
     set_max_dynamic_smem((const void*)kern, smem);
@@ -728,23 +608,16 @@ void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x2, int pt_s
     const int n_tiles = a.ZT * a.PT;
     const int grid = n_tiles < nsm ? n_tiles : nsm;
     if (grid <= 0) return;
-    // maps a kernel does not use (no 64-byte K tile, no narrow tile) are
-    // passed as copies of the ones it uses and never read
-    const CUtensorMap* mx = reinterpret_cast<const CUtensorMap*>(map_x2);
-    const CUtensorMap* pm[4][2];
-    for (int k = 0; k < 4; ++k)
-        for (int c = 0; c < 2; ++c) pm[k][c] = reinterpret_cast<const CUtensorMap*>(p->tmaps[k][c]);
-    const CUtensorMap& x64 = p->ktail64 ? mx[1] : mx[0];
-    const int k64 = p->ktail64 ? 1 : 0, kt = p->tail_w ? 2 : 0, kt64 = p->tail_w ? 2 + k64 : 0;
     prof_begin(kKContractBf16, st);
-    kern<<<grid, tc::kThreads, smem, st>>>(*pm[0][0], *pm[0][1], mx[0], *pm[k64][0], *pm[k64][1],
-                                           x64, *pm[kt][0], *pm[kt][1], *pm[kt64][0],
-                                           *pm[kt64][1], a);
+    kern<<<grid, tc::kThreads, smem, st>>>(*reinterpret_cast<const CUtensorMap*>(p->map_p),
+                                           *reinterpret_cast<const CUtensorMap*>(map_x), a);
     prof_end(kKContractBf16, st);
 }
 
-// FP32 [Zp][F][Spad] planar -> BF16 or FP16 of scale x [F][Zp][Spad]
-// (frequency-major tiles); scale is a power of two, exact in FP32.
+// FP32 spectra [Zp][F][Spad] (real and imaginary arrays) -> the merged
+// tensor-core operand [F][Zp / 128][256][Spad]: per frequency and 128-axis
+// tile, the 128 real rows then the 128 imaginary rows, BF16 / FP16 / E4M3 of
+// scale x (a power of two, exact in FP32).
 template <class T>
 __device__ __forceinline__ T to_half_type(float x);
 template <>
@@ -761,33 +634,37 @@ __device__ __forceinline__ __nv_fp8_e4m3 to_half_type<__nv_fp8_e4m3>(float x) {
 }
 
 template <class T>
-__global__ void k_plan_to_bf16(const float* __restrict__ src, int Zp, int F, int Spad,
-                               T* __restrict__ dst, float scale) {
-    const int64_t total = (int64_t)Zp * F * Spad;
+__global__ void k_plan_to_operand(const float* __restrict__ Pr, const float* __restrict__ Pi,
+                                  int Zp, int F, int Spad, T* __restrict__ dst, float scale) {
+    const int64_t total = (int64_t)2 * Zp * F * Spad;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int s = (int)(i % Spad);
-        const int64_t t = i / Spad;
-        const int z = (int)(t % Zp);
-        const int f = (int)(t / Zp);
+        const int64_t t = i / Spad;            // (f, zt, row) of the operand
+        const int row = (int)(t % 256);
+        const int64_t t2 = t / 256;
+        const int zt = (int)(t2 % (Zp / 128));
+        const int f = (int)(t2 / (Zp / 128));
+        const int z = zt * 128 + (row & 127);
+        const float* src = row < 128 ? Pr : Pi;
         dst[i] = to_half_type<T>(scale * src[((int64_t)z * F + f) * Spad + s]);
     }
 }
 
-void launch_plan_to_bf16(const float* src, int Zp, int F, int Spad, void* dst, cudaStream_t st,
-                         int kind, float scale) {
-    const int64_t total = (int64_t)Zp * F * Spad;
+void launch_plan_to_operand(const float* Pr, const float* Pi, int Zp, int F, int Spad, void* dst,
+                            cudaStream_t st, int kind, float scale) {
+    const int64_t total = (int64_t)2 * Zp * F * Spad;
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
     prof_begin(kKMisc, st);
     if (kind == 2)
-        k_plan_to_bf16<__nv_fp8_e4m3><<<blocks, 256, 0, st>>>(
-            src, Zp, F, Spad, reinterpret_cast<__nv_fp8_e4m3*>(dst), scale);
+        k_plan_to_operand<__nv_fp8_e4m3><<<blocks, 256, 0, st>>>(
+            Pr, Pi, Zp, F, Spad, reinterpret_cast<__nv_fp8_e4m3*>(dst), scale);
     else if (kind == 1)
-        k_plan_to_bf16<__half><<<blocks, 256, 0, st>>>(src, Zp, F, Spad,
-                                                        reinterpret_cast<__half*>(dst), scale);
+        k_plan_to_operand<__half><<<blocks, 256, 0, st>>>(Pr, Pi, Zp, F, Spad,
+                                                           reinterpret_cast<__half*>(dst), scale);
     else
-        k_plan_to_bf16<__nv_bfloat16><<<blocks, 256, 0, st>>>(
-            src, Zp, F, Spad, reinterpret_cast<__nv_bfloat16*>(dst), 1.0f);
+        k_plan_to_operand<__nv_bfloat16><<<blocks, 256, 0, st>>>(
+            Pr, Pi, Zp, F, Spad, reinterpret_cast<__nv_bfloat16*>(dst), 1.0f);
     prof_end(kKMisc, st);
 }
 

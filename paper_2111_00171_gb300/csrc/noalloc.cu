@@ -90,9 +90,9 @@ extern "C" acom_status acom_bounds_static(acom_plan p, const acom_peaks_csr* pea
         cur += spec * 2 * sizeof(float);
     }
     float* xnorm2 = reinterpret_cast<float*>(cur);
-    alignas(64) unsigned char map_x[2][128];
+    alignas(64) unsigned char map_x[128];
     if (tc) {
-        s = make_pattern_maps(map_x, XB, (uint64_t)p->F * PTs * 128, p->Spad, 0);
+        s = make_bf16_map(map_x, XB, (uint64_t)p->F * PTs * 128, (uint64_t)p->Spad);
         if (s != ACOM_OK) return s;
     }
     prof_suppress(true);
