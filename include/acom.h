@@ -262,6 +262,9 @@ typedef struct {
     int32_t tile_order;       /* tensor-core contraction schedule: 0 consecutive
                                  tiles share a pattern tile (default), 1 they
                                  share a zone-axis tile                       */
+    int32_t single_cta;       /* tensor-core contraction: 0 (default) pairs of
+                                 CTAs compute each MMA together (cta_group::2,
+                                 M = 256 patterns rows), 1 one CTA per MMA    */
 } acom_match_opts;
 
 /*

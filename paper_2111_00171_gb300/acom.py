@@ -83,7 +83,7 @@ class Result(C.Structure):
 
 class MatchOpts(C.Structure):
     _fields_ = [("refine", C.c_int32), ("chunk", C.c_int32), ("exhaustive", C.c_int32),
-                ("rescore_top", C.c_int32), ("tile_order", C.c_int32)]
+                ("rescore_top", C.c_int32), ("tile_order", C.c_int32), ("single_cta", C.c_int32)]
 
 
 class TuneResult(C.Structure):
@@ -365,17 +365,19 @@ class Plan:
 
     def match(self, row_ptr, qx, qy, I, refine=True, chunk=0, za_scores=False, out=None,
               exhaustive=False, phase_scores=False, runner=False, rescore_top=0, tile_order=0,
-              stream=None):
+              single_cta=0, stream=None):
         """acom_match on device CSR tensors; returns a dict of device tensors
         (with phase_scores: the phase of each winner and every phase's best;
-        with runner: the runner-up axis, score and grid orientation)."""
+        with runner: the runner-up axis, score and grid orientation;
+        single_cta=1: the tensor-core contraction with one CTA per MMA instead
+        of CTA pairs)."""
         pk = self._csr(row_ptr, qx, qy, I)
         r = out if out is not None else self.alloc_result(pk.n_patterns, za_scores=za_scores,
                                                           phase_scores=phase_scores,
                                                           runner=runner)
         res = Result(*(_ptr(r.get(k)) for k, _ in Result._fields_))
         opts = MatchOpts(1 if refine else 0, int(chunk), 1 if exhaustive else 0, int(rescore_top),
-                         int(tile_order))
+                         int(tile_order), int(single_cta))
         _check(self._lib.acom_match(self.handle, C.byref(pk), C.byref(opts), C.byref(res),
                                     _stream_ptr(stream)))
         return r

@@ -427,6 +427,9 @@ acom_status acom_plan_create(const acom_crystal* crystal, const acom_za_grid* gr
         ACOM_CK(cudaGetLastError());
         s = make_bf16_map(p->map_p, p->Pb, (uint64_t)p->F * p->Zp * 2, (uint64_t)p->Spad, kind,
                           256);
+        if (s == ACOM_OK)
+            s = make_bf16_map(p->map_p128, p->Pb, (uint64_t)p->F * p->Zp * 2, (uint64_t)p->Spad,
+                              kind, 128);
         if (s != ACOM_OK) {
             destroy_plan(p);
             return s;
@@ -580,6 +583,9 @@ acom_status acom_plan_concat(const acom_plan* plans, int32_t n_plans, void* cuda
         ACOM_CK(cudaGetLastError());
         acom_status s = make_bf16_map(p->map_p, p->Pb, (uint64_t)F * p->Zp * 2, (uint64_t)Spad,
                                       kind, 256);
+        if (s == ACOM_OK)
+            s = make_bf16_map(p->map_p128, p->Pb, (uint64_t)F * p->Zp * 2, (uint64_t)Spad, kind,
+                              128);
         if (s != ACOM_OK) {
             cudaStreamSynchronize(st);
             destroy_plan(p);
@@ -766,6 +772,9 @@ static acom_status match_enqueue(acom_plan p, const acom_peaks_csr* peaks,
     const int tile_order = opts ? opts->tile_order : 0;
     if (tile_order < 0 || tile_order > 1)
         return set_error(ACOM_ERR_INVALID_ARG, "tile_order must be 0 or 1");
+    const int single_cta = opts ? opts->single_cta : 0;
+    if (single_cta < 0 || single_cta > 1)
+        return set_error(ACOM_ERR_INVALID_ARG, "single_cta must be 0 or 1");
     if (exhaustive && (out->runner_za || out->runner_score || out->runner_orient))
         return set_error(ACOM_ERR_UNSUPPORTED, "runner-up outputs need certified pruning");
     if (!exhaustive && p->Z > 16384)
@@ -819,7 +828,8 @@ static acom_status match_enqueue(acom_plan p, const acom_peaks_csr* peaks,
         } else {
             if (tc) {
                 convert_fp8(p, w, st);
-                launch_contract_bound_tc(p, w.map_x, w.PTs, nb, w.U, st, xscale, tile_order);
+                launch_contract_bound_tc(p, w.map_x, w.PTs, nb, w.U, st, xscale, tile_order,
+                                         single_cta);
             } else {
                 launch_contract_bound_fp32(p, w.Xr, w.Xi, nb, w.U, st);
             }
@@ -1103,7 +1113,7 @@ acom_status acom_autotune(acom_plan p, const acom_peaks_csr* peaks, const acom_m
     r.phi3_bin = kb;
     r.mirror = mi;
     r.score = sc;
-    acom_match_opts o = base ? *base : acom_match_opts{1, 0, 0, 0, 0};
+    acom_match_opts o = base ? *base : acom_match_opts{1, 0, 0, 0, 0, 0};
     const int chunks[3] = {4096, 8192, 16384};
     cudaEvent_t t0, t1;
     cudaEventCreate(&t0);

@@ -57,9 +57,7 @@ constexpr int kM = 128;               // zone axes per tile (MMA N = 256 rows: r
 constexpr int kNP = 64;               // patterns per tile (MMA M = 128 rows: re, im)
 constexpr int kKT = 64;               // 16-bit operands per K tile row (128 bytes)
 constexpr int kKT8 = 128;             // 8-bit operands per K tile row (128 bytes)
-constexpr int kStages = 4;
 constexpr int kTileBytes = 128 * kKT * 2;      // 16 KB
-constexpr int kStageBytes = 3 * kTileBytes;    // X, then Pr and Pi as one 256-row operand
 constexpr int kEpiWarps = 16;
 constexpr int kIssuers = 2;                    // MMA-issuing warps, one per TMEM buffer
 constexpr int kProdP = 1 + kIssuers;           // warp of the plan-operand producer
@@ -179,6 +177,73 @@ __device__ __forceinline__ void fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
+// ---- CTA pairs (cta_group::2): a cluster of two CTAs shares each MMA ----
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// the shared::cluster address of the same shared-memory offset in CTA `rank`
+__device__ __forceinline__ uint32_t mapa_rank(uint32_t saddr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t caddr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr)
+                 : "memory");
+}
+__device__ __forceinline__ void st_cluster_u32(uint32_t caddr, uint32_t v) {
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(caddr), "r"(v) : "memory");
+}
+// a TMA copy into this CTA's shared memory that completes on a barrier of
+// either CTA of the pair (`bar` a shared::cluster address)
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                                 uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cta.global.tile.mbarrier::complete_tx::bytes.cta_group::2"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void mma_f16kind_pair(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                                 uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n"
+        "}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_f8kind_pair(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                                uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n"
+        "}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// arrive on the barrier at this offset in both CTAs once this thread's MMAs complete
+__device__ __forceinline__ void mma_commit_pair_both(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        " [%0], %1;" ::"r"(bar), "h"((uint16_t)3)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit_pair(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+
 // 16 TMEM lanes x 32 columns: thread t receives, for n = 0..3, lane t/4 at
 // columns 8n + 2(t%4) + {0, 1} in r[4n], r[4n+1] and lane t/4 + 8 at the same
 // columns in r[4n+2], r[4n+3]
@@ -266,32 +331,60 @@ struct TcArgs {
 // F8: E4M3 operands (kind::f8f6f4, 128 elements per K tile), else 16-bit
 // (kind::f16, 64 elements per K tile); a template parameter, so the MMA issue
 // loop carries no branch on it
-template <bool F8>
+// Ring geometry: a single CTA stages X (16 KB) and the whole B operand (32 KB)
+// per K tile; a CTA of a pair stages X and its half of B (16 KB each), so a
+// pair's ring is deeper.
+template <bool PAIR>
+struct Ring {
+    static constexpr int kStageBytes = (PAIR ? 2 : 3) * kTileBytes;
+    static constexpr int kStages = PAIR ? 6 : 4;
+};
+
+// F8: E4M3 operands (kind::f8f6f4, 128 elements per K tile), else 16-bit
+// (kind::f16, 64 elements per K tile); a template parameter, so the MMA issue
+// loop carries no branch on it.
+// PAIR: a cluster of two CTAs computes each MMA together (cta_group::2,
+// M = 256): CTA rank r of the pair holds pattern tile 2 p + r of the pair's
+// pattern tiles (its A rows) and half of the axis tile's B operand (rank 0 the
+// real rows, rank 1 the imaginary rows); rank 0's two threads issue every MMA,
+// whose accumulators land in both CTAs' tensor memory, lanes = the CTA's own
+// patterns, columns = all 256 B rows, exactly as for a single CTA.  Both CTAs'
+// copies complete on rank 0's full barriers; commits arrive on both CTAs'
+// barriers; both epilogues release rank 0's accumulator barrier.
+template <bool F8, bool PAIR>
 __global__ void __launch_bounds__(kThreads, 1)
 k_contract_bound_tc(const __grid_constant__ CUtensorMap map_p,
                     const __grid_constant__ CUtensorMap map_x, TcArgs a) {
+    constexpr int kSt = Ring<PAIR>::kStages;
+    constexpr int kSB = Ring<PAIR>::kStageBytes;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte alignment of the operand ring
     unsigned char* base = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char* ring = base;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(ring + kStages * kStageBytes);
-    uint64_t* full = bars;                      // [kIssuers][kStages]
-    uint64_t* empty = bars + kIssuers * kStages;   // [kStages]
-    uint64_t* tfull = empty + kStages;          // [kIssuers]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(ring + kSt * kSB);
+    uint64_t* full = bars;                      // [kIssuers][kSt]
+    uint64_t* empty = bars + kIssuers * kSt;    // [kSt]
+    uint64_t* tfull = empty + kSt;              // [kIssuers]
     uint64_t* tempty = tfull + kIssuers;        // [kIssuers]
     uint64_t* drain = tempty + kIssuers;        // [kIssuers]
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + kIssuers);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = PAIR ? cluster_rank() : 0u;
+    const bool leader = rank == 0;
+    // the pair's abort flag of the other CTA: a timeout stops both CTAs
+    const uint32_t peer_abort =
+        PAIR ? mapa_rank(smem_u32(const_cast<int*>(abort_flag)), rank ^ 1u) : 0u;
     if (threadIdx.x == 0) {
-        // a full barrier completes on both producers' arrivals and their bytes
-        for (int s = 0; s < kIssuers * kStages; ++s) mbar_init(smem_u32(full + s), 2);
-        for (int s = 0; s < kStages; ++s) mbar_init(smem_u32(empty + s), 1);
+        // a full barrier completes on the arrivals of the (leading CTA's) two
+        // producers and the bytes of every copy of the stage
+        for (int s = 0; s < kIssuers * kSt; ++s) mbar_init(smem_u32(full + s), 2);
+        for (int s = 0; s < kSt; ++s) mbar_init(smem_u32(empty + s), 1);
         for (int b = 0; b < kIssuers; ++b) {
             mbar_init(smem_u32(tfull + b), 1);
-            mbar_init(smem_u32(tempty + b), kEpiWarps);
+            mbar_init(smem_u32(tempty + b), (PAIR ? 2 : 1) * kEpiWarps);
             mbar_init(smem_u32(drain + b), 1);
         }
         *abort_flag = 0;
@@ -300,17 +393,37 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_p,
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_x)));
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_u32(tmem_slot)),
-                     "r"(kTmemCols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        if constexpr (PAIR) {
+            asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(tmem_slot)),
+                         "r"(kTmemCols)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+        } else {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(tmem_slot)),
+                         "r"(kTmemCols)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
     }
     fence_before();
-    __syncthreads();
+    if constexpr (PAIR)
+        cluster_sync_all();      // both CTAs' barriers exist before any copy or arrival
+    else
+        __syncthreads();
     fence_after();
     const uint32_t tmem = *tmem_slot;
-    const int n_tiles = a.ZT * a.PT;
+    // tiles: single CTA (axis tile, pattern tile); pair (axis tile, pair of
+    // pattern tiles), the pair's CTAs taking the two pattern tiles
+    const int PTu = PAIR ? (a.PT + 1) / 2 : a.PT;
+    const int n_tiles = a.ZT * PTu;
+    const int t0 = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+    const int tstep = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+    auto set_abort = [&]() {
+        if constexpr (PAIR) st_cluster_u32(peer_abort, 1u);
+    };
+    bool aborted = false;
 
     if (warp == 0 || warp == kProdP) {
         // ------------------------------------------------ TMA producers: warp 0
@@ -325,22 +438,35 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_p,
             uint32_t issued_mask = 0, last_par = 0, last_own = 0;
             int fcount = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-                const int zt = a.zmajor ? t / a.PT : t % a.ZT;
-                const int pt = a.zmajor ? t % a.PT : t / a.ZT;
+            for (int t = t0; t < n_tiles && ok; t += tstep) {
+                const int zt = a.zmajor ? t / PTu : t % a.ZT;
+                const int pu = a.zmajor ? t % PTu : t / a.ZT;
+                const int pt = PAIR ? 2 * pu + (int)rank : pu;
                 for (int f = 0; f < a.F && ok; ++f, ++fcount) {
-                    const int prow = f * a.Zrows + zt * 256;
+                    // a pair's CTA loads the real (rank 0) or imaginary rows of the tile
+                    const int prow = f * a.Zrows + zt * 256 + (PAIR ? 128 * (int)rank : 0);
                     const int xrow = (f * a.PTs + pt) * 128;
                     const int own = fcount & 1;
                     for (int kt = 0; kt < a.KT; ++kt) {
-                        if (!mbar_wait(smem_u32(empty + stage), phase ^ 1u, abort_flag, a.err, a.wait_cycles)) {
+                        if (!mbar_wait(smem_u32(empty + stage), phase ^ 1u, abort_flag, a.err,
+                                       a.wait_cycles)) {
                             ok = false;
                             break;
                         }
-                        const uint32_t fb = smem_u32(full + own * kStages + stage);
-                        unsigned char* sbuf = ring + stage * kStageBytes;
+                        const uint32_t fb = smem_u32(full + own * kSt + stage);
+                        unsigned char* sbuf = ring + stage * kSB;
                         constexpr int ktel = F8 ? kKT8 : kKT;
-                        if (xprod) {
+                        if constexpr (PAIR) {
+                            // every copy completes on the leading CTA's barrier, which
+                            // expects both CTAs' bytes of its operand
+                            const uint32_t fbl = mapa_rank(fb, 0);
+                            if (leader) mbar_expect_tx(fb, 2 * kTileBytes);
+                            if (xprod)
+                                tma_load_2d_pair(smem_u32(sbuf), &map_x, kt * ktel, xrow, fbl);
+                            else
+                                tma_load_2d_pair(smem_u32(sbuf + kTileBytes), &map_p, kt * ktel,
+                                                 prow, fbl);
+                        } else if (xprod) {
                             mbar_expect_tx(fb, kTileBytes);
                             tma_load_2d(smem_u32(sbuf), &map_x, kt * ktel, xrow, fb);
                         } else {
@@ -353,7 +479,7 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_p,
                         last_par = (last_par & ~(1u << stage)) | (par << stage);
                         last_own = (last_own & ~(1u << stage)) | ((uint32_t)own << stage);
                         fpar[own] ^= 1u << stage;
-                        if (++stage == kStages) {
+                        if (++stage == kSt) {
                             stage = 0;
                             phase ^= 1u;
                         }
@@ -361,16 +487,26 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_p,
                 }
             }
             if (!ok) {
-                // let copies in flight land before the CTA's shared memory goes away
-                for (int s = 0; s < kStages; ++s)
-                    if (issued_mask & (1u << s)) {
-                        const uint32_t par = (last_par >> s) & 1u;
-                        const int own = (last_own >> s) & 1u;
-                        const long long t0 = clock64();
-                        while (!mbar_try(smem_u32(full + own * kStages + s), par) &&
-                               clock64() - t0 < kWaitCycles) {
+                aborted = true;
+                set_abort();
+                if (!PAIR || leader) {
+                    // let copies in flight land before the CTA's shared memory goes away
+                    for (int s = 0; s < kSt; ++s)
+                        if (issued_mask & (1u << s)) {
+                            const uint32_t par = (last_par >> s) & 1u;
+                            const int own = (last_own >> s) & 1u;
+                            const long long w0 = clock64();
+                            while (!mbar_try(smem_u32(full + own * kSt + s), par) &&
+                                   clock64() - w0 < kWaitCycles) {
+                            }
                         }
+                } else {
+                    // this CTA's copies complete on the other CTA's barriers: give
+                    // them time to land (a copy takes microseconds)
+                    const long long w0 = clock64();
+                    while (clock64() - w0 < (1LL << 22)) {
                     }
+                }
             }
         }
         __syncwarp();
@@ -378,22 +514,23 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_p,
         // ------------------------------------------------ MMA issuers
         // issuer mi takes the frequencies with fcount % 2 == mi into TMEM
         // buffer mi; it walks the ring in the producer's order and waits only
-        // on its own full barriers
+        // on its own full barriers (a pair: the leading CTA's issuers only)
         const int mi = warp - 1;
-        if (lane == 0) {
+        if (lane == 0 && (!PAIR || leader)) {
             int stage = 0;
             uint32_t fpar = 0;           // bit s: parity of this issuer's next phase of slot s
             uint32_t tph = 0;
             int fcount = 0;
             bool ok = true;
-            uint64_t* myfull = full + mi * kStages;
-            for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+            uint64_t* myfull = full + mi * kSt;
+            for (int t = t0; t < n_tiles && ok; t += tstep) {
                 for (int f = 0; f < a.F && ok; ++f, ++fcount) {
                     if ((fcount & 1) != mi) {
-                        stage = (stage + a.KT) % kStages;
+                        stage = (stage + a.KT) % kSt;
                         continue;
                     }
-                    if (!mbar_wait(smem_u32(tempty + mi), tph ^ 1u, abort_flag, a.err, a.wait_cycles)) {
+                    if (!mbar_wait(smem_u32(tempty + mi), tph ^ 1u, abort_flag, a.err,
+                                   a.wait_cycles)) {
                         ok = false;
                         break;
                     }
@@ -408,7 +545,7 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_p,
                         }
                         fpar ^= 1u << stage;
                         fence_after();
-                        const uint32_t sb = smem_u32(ring + stage * kStageBytes);
+                        const uint32_t sb = smem_u32(ring + stage * kSB);
                         // K steps of 32 bytes inside the shells (16 16-bit or 32
                         // 8-bit elements; the tail of the last tile is TMA zero
                         // fill); a step moves the descriptors' start address by
@@ -419,23 +556,45 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_p,
 #pragma unroll
                         for (int k4 = 0; k4 < 4; ++k4)
                             if (k4 < nk) {
-                                if constexpr (F8)
-                                    mma_f8kind(dacc, xa + 2 * k4, pb + 2 * k4, a.idesc,
-                                               (kt | k4) ? 1u : 0u);
-                                else
-                                    mma_f16kind(dacc, xa + 2 * k4, pb + 2 * k4, a.idesc,
-                                                (kt | k4) ? 1u : 0u);
+                                const uint32_t acc = (kt | k4) ? 1u : 0u;
+                                if constexpr (PAIR) {
+                                    if constexpr (F8)
+                                        mma_f8kind_pair(dacc, xa + 2 * k4, pb + 2 * k4, a.idesc, acc);
+                                    else
+                                        mma_f16kind_pair(dacc, xa + 2 * k4, pb + 2 * k4, a.idesc, acc);
+                                } else {
+                                    if constexpr (F8)
+                                        mma_f8kind(dacc, xa + 2 * k4, pb + 2 * k4, a.idesc, acc);
+                                    else
+                                        mma_f16kind(dacc, xa + 2 * k4, pb + 2 * k4, a.idesc, acc);
+                                }
                             }
-                        mma_commit(smem_u32(empty + stage));       // frees the stage
-                        if (++stage == kStages) stage = 0;
+                        // frees the stage (in both CTAs of a pair)
+                        if constexpr (PAIR)
+                            mma_commit_pair_both(smem_u32(empty + stage));
+                        else
+                            mma_commit(smem_u32(empty + stage));
+                        if (++stage == kSt) stage = 0;
                     }
-                    if (ok) mma_commit(smem_u32(tfull + mi));     // accumulators ready
+                    if (ok) {                                    // accumulators ready
+                        if constexpr (PAIR)
+                            mma_commit_pair_both(smem_u32(tfull + mi));
+                        else
+                            mma_commit(smem_u32(tfull + mi));
+                    }
                 }
             }
+            if (!ok) {
+                aborted = true;
+                set_abort();
+            }
             // all MMAs issued by this thread complete before TMEM is released
-            mma_commit(smem_u32(drain + mi));
-            const long long t0 = clock64();
-            while (!mbar_try(smem_u32(drain + mi), 0) && clock64() - t0 < kWaitCycles) {
+            if constexpr (PAIR)
+                mma_commit_pair(smem_u32(drain + mi));
+            else
+                mma_commit(smem_u32(drain + mi));
+            const long long w0 = clock64();
+            while (!mbar_try(smem_u32(drain + mi), 0) && clock64() - w0 < kWaitCycles) {
             }
         }
         __syncwarp();
@@ -450,9 +609,14 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_p,
         uint32_t tph[2] = {0, 0};
         int fcount = 0;
         bool ok = true;
-        for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-            const int zt = a.zmajor ? t / a.PT : t % a.ZT;
-            const int pt = a.zmajor ? t % a.PT : t / a.ZT;
+        // the accumulator barriers live in the leading CTA
+        const uint32_t tempty_l[2] = {PAIR ? mapa_rank(smem_u32(tempty), 0) : smem_u32(tempty),
+                                      PAIR ? mapa_rank(smem_u32(tempty + 1), 0)
+                                           : smem_u32(tempty + 1)};
+        for (int t = t0; t < n_tiles && ok; t += tstep) {
+            const int zt = a.zmajor ? t / PTu : t % a.ZT;
+            const int pu = a.zmajor ? t % PTu : t / a.ZT;
+            const int pt = PAIR ? 2 * pu + (int)rank : pu;
             for (int f = 0; f < a.F; ++f, ++fcount) {
                 const int buf = fcount & 1;
                 if (!mbar_wait(smem_u32(tfull + buf), tph[buf], abort_flag, a.err, a.wait_cycles)) {
@@ -479,7 +643,12 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_p,
                 ACOM_TMEM_WAIT32(R1, I1);
                 fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(tempty + buf));
+                if (lane == 0) {
+                    if constexpr (PAIR)
+                        mbar_arrive_cluster(tempty_l[buf]);
+                    else
+                        mbar_arrive(tempty_l[buf]);
+                }
 #pragma unroll
                 for (int n = 0; n < 4; ++n)
                     accumulate_pair2(R1[4 * n], R1[4 * n + 1], R1[4 * n + 2], R1[4 * n + 3],
@@ -504,20 +673,31 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_p,
                     }
             }
         }
+        if (!ok && lane == 0) set_abort();
     }
+    (void)aborted;
     fence_before();
-    __syncthreads();
+    if constexpr (PAIR)
+        cluster_sync_all();      // the leading CTA's MMAs and every copy are done in both CTAs
+    else
+        __syncthreads();
     if (warp == 1) {
         fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(kTmemCols)
-                     : "memory");
+        if constexpr (PAIR)
+            asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                         "r"(kTmemCols)
+                         : "memory");
+        else
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                         "r"(kTmemCols)
+                         : "memory");
     }
 }
 
+template <bool PAIR>
 size_t tc_smem_bytes() {
-    return 1024 + (size_t)kStages * kStageBytes + 8 * ((kIssuers + 1) * kStages + 3 * kIssuers) +
-           16;
+    return 1024 + (size_t)Ring<PAIR>::kStages * Ring<PAIR>::kStageBytes +
+           8 * ((kIssuers + 1) * Ring<PAIR>::kStages + 3 * kIssuers) + 16;
 }
 
 }  // namespace tc
@@ -576,7 +756,8 @@ static long long g_wait_cycles = 0;
 void set_wait_cycles(long long cycles) { g_wait_cycles = cycles > 0 ? cycles : 0; }
 
 void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_stride, int nb,
-                              float* U, cudaStream_t st, const float* xscale, int tile_order) {
+                              float* U, cudaStream_t st, const float* xscale, int tile_order,
+                              int single_cta) {
     tc::TcArgs a;
     a.zmajor = tile_order == 1 ? 1 : 0;
     a.F = p->F;
@@ -599,18 +780,45 @@ void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_st
     a.xs_mul = f8 ? kFp8Shift : 1.0f;
     a.inv_pscale = 1.0f / p->pscale;
     a.wait_cycles = g_wait_cycles > 0 ? g_wait_cycles : tc::kWaitCycles;
-    const size_t smem = tc::tc_smem_bytes();
-    auto kern = f8 ? tc::k_contract_bound_tc<true> : tc::k_contract_bound_tc<false>;
-    set_max_dynamic_smem((const void*)kern, smem);
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const CUtensorMap& mx = *reinterpret_cast<const CUtensorMap*>(map_x);
+    if (!single_cta && nsm >= 2) {
+        // CTA pairs: M = 256 (the pair's two pattern tiles), each CTA loading
+        // half of the 256 B rows (128-row boxes)
+        a.idesc = (a.idesc & ~(0x1Fu << 24)) | ((256u >> 4) << 24);
+        const size_t smem = tc::tc_smem_bytes<true>();
+        auto kern = f8 ? tc::k_contract_bound_tc<true, true> : tc::k_contract_bound_tc<false, true>;
+        set_max_dynamic_smem((const void*)kern, smem);
+        const int n_tiles = a.ZT * ((a.PT + 1) / 2);
+        const int clusters = n_tiles < nsm / 2 ? n_tiles : nsm / 2;
+        if (clusters <= 0) return;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(2 * clusters, 1, 1);
+        cfg.blockDim = dim3(tc::kThreads, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        prof_begin(kKContractBf16, st);
+        cudaLaunchKernelEx(&cfg, kern, *reinterpret_cast<const CUtensorMap*>(p->map_p128), mx, a);
+        prof_end(kKContractBf16, st);
+        return;
+    }
+    const size_t smem = tc::tc_smem_bytes<false>();
+    auto kern = f8 ? tc::k_contract_bound_tc<true, false> : tc::k_contract_bound_tc<false, false>;
+    set_max_dynamic_smem((const void*)kern, smem);
     const int n_tiles = a.ZT * a.PT;
     const int grid = n_tiles < nsm ? n_tiles : nsm;
     if (grid <= 0) return;
     prof_begin(kKContractBf16, st);
-    kern<<<grid, tc::kThreads, smem, st>>>(*reinterpret_cast<const CUtensorMap*>(p->map_p),
-                                           *reinterpret_cast<const CUtensorMap*>(map_x), a);
+    kern<<<grid, tc::kThreads, smem, st>>>(*reinterpret_cast<const CUtensorMap*>(p->map_p), mx, a);
     prof_end(kKContractBf16, st);
 }
 

@@ -530,3 +530,22 @@ def test_many_peaks_and_radius_ties(c1):
         mt = O.match_pattern(oplan, *scan.pattern(b))
         assert math.isclose(sc[b], mt.score, rel_tol=1e-4), b
         assert check_argmax(mt, za[b], kk[b], mi[b], 1e-5), b
+
+
+@pytest.mark.parametrize("precision", [1, 2, 3], ids=["bf16", "fp16", "fp8"])
+def test_cta_pairs_equal_single_cta(precision):
+    """The tensor-core contraction on CTA pairs (cta_group::2, the default)
+    computes the same dot products in the same order as one CTA per MMA:
+    bounds, winners and scores are bitwise equal, on a chunk with an odd
+    number of 64-pattern tiles (the last pair's second CTA has no patterns)."""
+    import torch
+    plan = gpu_plan("au_2deg_75x180", precision=precision)
+    scan = synth.random_patterns(1601, n_patterns=300)
+    inp = to_dev(scan)
+    for chunk in (0, 192):
+        a = plan.match(*inp, za_scores=True, chunk=chunk, single_cta=0)
+        b = plan.match(*inp, za_scores=True, chunk=chunk, single_cta=1)
+        torch.cuda.synchronize()
+        for k in ("za_idx", "phi3_bin", "mirror", "score", "za_scores", "orient"):
+            assert torch.equal(a[k], b[k]), (chunk, k)
+    plan.close()
