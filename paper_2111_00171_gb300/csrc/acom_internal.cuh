@@ -187,6 +187,10 @@ struct acom_plan_s {
     void* Pb = nullptr;
     alignas(64) unsigned char map_p[128];   // TMA map of Pb (boxes of 256 rows)
     alignas(64) unsigned char map_p128[128];  // the same with boxes of 128 rows (CTA pairs)
+    // first shell of the tensor-core contraction's K range: the lowest shell
+    // (rounded down to a multiple of 16) where some axis' plan row is not
+    // zero; the products below it are zero for every axis and pattern
+    int k0 = 0;
     float4* refl_tab = nullptr;       // [G] FP32 (g, |g|^gamma |F_g|^omega) for refinement
     unsigned long long* refine_pairs = nullptr;  // (reflection, peak) pairs of the last refine
     int64_t last_refine_pairs = 0;

@@ -258,6 +258,31 @@ static void destroy_plan(acom_plan_s* p) {
 
 static bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
+// p->k0 from the plan's shell masks (synchronous copy): the lowest shell with a
+// non-zero plan row on any axis, rounded down to a multiple of 16 (one MMA's K);
+// 0 when the plan has no non-zero row at all.
+static cudaError_t plan_k0(acom_plan_s* p, cudaStream_t st) {
+    const int MW = p->Spad / 32;
+    std::vector<uint32_t> m((size_t)p->Zp * MW);
+    cudaError_t e = cudaMemcpyAsync(m.data(), p->smask, sizeof(uint32_t) * m.size(),
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    int lo = p->Spad;
+    for (int z = 0; z < p->Z; ++z)
+        for (int w = 0; w < MW; ++w) {
+            const uint32_t v = m[(size_t)z * MW + w];
+            if (v) {
+                int b = 0;
+                while (!((v >> b) & 1u)) ++b;
+                lo = std::min(lo, 32 * w + b);
+                break;
+            }
+        }
+    p->k0 = lo < p->Spad ? lo / 16 * 16 : 0;
+    return cudaSuccess;
+}
+
 // The first row pointer of a CSR batch must be 0 (the other row checks run in
 // the raster, per pattern); one thread, no allocation.
 __global__ void k_check_row0(const int64_t* row_ptr, int* err) {
@@ -436,6 +461,7 @@ acom_status acom_plan_create(const acom_crystal* crystal, const acom_za_grid* gr
         }
     }
     ACOM_CK(cudaStreamSynchronize(st));
+    ACOM_CK(plan_k0(p, st));
     prof_resolve();
     *out = p;
     return ACOM_OK;
@@ -593,6 +619,7 @@ acom_status acom_plan_concat(const acom_plan* plans, int32_t n_plans, void* cuda
         }
     }
     ACOM_CK(cudaStreamSynchronize(st));
+    ACOM_CK(plan_k0(p, st));
     *out = p;
     return ACOM_OK;
 cuda_fail:

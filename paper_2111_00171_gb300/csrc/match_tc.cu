@@ -315,6 +315,8 @@ struct TcArgs {
     int F, N, Z, nb, ZT, PT, KT;   // frequencies, bins, axes, patterns, axis tiles, pattern tiles, K tiles
     int PTs;                       // pattern tiles per frequency in the pattern map (row stride)
     int Spad;                      // shells (K) in the operand rows
+    int k0;                        // first shell of the contraction's K range (the
+                                   // plan's rows below it are zero for every axis)
     int Zrows;                     // rows per frequency in the plan map (ZT * 256)
     float* U;                      // [nb][Z]
     int* err;
@@ -462,17 +464,20 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_p,
                             const uint32_t fbl = mapa_rank(fb, 0);
                             if (leader) mbar_expect_tx(fb, 2 * kTileBytes);
                             if (xprod)
-                                tma_load_2d_pair(smem_u32(sbuf), &map_x, kt * ktel, xrow, fbl);
+                                tma_load_2d_pair(smem_u32(sbuf), &map_x, a.k0 + kt * ktel, xrow,
+                                                 fbl);
                             else
-                                tma_load_2d_pair(smem_u32(sbuf + kTileBytes), &map_p, kt * ktel,
+                                tma_load_2d_pair(smem_u32(sbuf + kTileBytes), &map_p,
+                                                 a.k0 + kt * ktel,
                                                  prow, fbl);
                         } else if (xprod) {
                             mbar_expect_tx(fb, kTileBytes);
-                            tma_load_2d(smem_u32(sbuf), &map_x, kt * ktel, xrow, fb);
+                            tma_load_2d(smem_u32(sbuf), &map_x, a.k0 + kt * ktel, xrow, fb);
                         } else {
                             // B operand: 256 rows, the tile's re rows then its im rows
                             mbar_expect_tx(fb, 2 * kTileBytes);
-                            tma_load_2d(smem_u32(sbuf + kTileBytes), &map_p, kt * ktel, prow, fb);
+                            tma_load_2d(smem_u32(sbuf + kTileBytes), &map_p, a.k0 + kt * ktel,
+                                        prow, fb);
                         }
                         issued_mask |= 1u << stage;
                         const uint32_t par = (fpar[own] >> stage) & 1u;
@@ -551,7 +556,8 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_p,
                         // fill); a step moves the descriptors' start address by
                         // 32 bytes (2 units of 16)
                         constexpr int ktel = F8 ? kKT8 : kKT;
-                        const int nk = (min(ktel, a.Spad - kt * ktel) * (F8 ? 1 : 2)) >> 5;
+                        const int nk =
+                            (min(ktel, a.Spad - a.k0 - kt * ktel) * (F8 ? 1 : 2)) >> 5;
                         const uint64_t xa = sdesc(sb), pb = sdesc(sb + kTileBytes);
 #pragma unroll
                         for (int k4 = 0; k4 < 4; ++k4)
@@ -769,7 +775,9 @@ void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_st
     a.PTs = pt_stride;
     const bool f8 = p->precision == ACOM_PREC_FP8;
     const int ktel = f8 ? tc::kKT8 : tc::kKT;
-    a.KT = (p->Spad + ktel - 1) / ktel;
+    // the K range starts at the plan's first non-zero shell (a multiple of 16)
+    a.k0 = p->k0;
+    a.KT = (p->Spad - p->k0 + ktel - 1) / ktel;
     a.Spad = p->Spad;
     a.Zrows = 2 * p->Zp;
     a.U = U;
