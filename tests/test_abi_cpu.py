@@ -119,15 +119,22 @@ def test_refine_defaults_and_argument_checks_on_host(lib):
                                       None) == 1
 
 
+def _header_struct_fields(name):
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    body = re.search(r"typedef struct \{([^}]*)\}\s*" + name + ";", text).group(1)
+    return re.findall(r"\b([a-z_][a-z_0-9]*)\s*;", body)
+
+
 def test_autotune_and_tile_order_argument_checks_on_host(lib):
     """acom_autotune rejects a null plan or result before any device work; the
-    ctypes mirror of acom_match_opts carries all five fields of the header's
-    struct, tile_order last."""
+    ctypes mirrors of acom_match_opts and acom_tune_result carry the header's
+    fields in the header's order (every field 32 bits wide)."""
     from paper_2111_00171_gb300 import acom
     pk = acom.PeaksCSR(0, None, None, None, None)
     best = acom.TuneResult()
     assert lib.acom_autotune(None, C.byref(pk), None, C.byref(best), None, None) == 1
     assert lib.acom_last_error()
-    assert [f for f, _ in acom.MatchOpts._fields_] == ["refine", "chunk", "exhaustive",
-                                                        "rescore_top", "tile_order"]
-    assert C.sizeof(acom.MatchOpts) == 20 and C.sizeof(acom.TuneResult) == 12
+    for mirror, name in ((acom.MatchOpts, "acom_match_opts"), (acom.TuneResult, "acom_tune_result")):
+        fields = _header_struct_fields(name)
+        assert [f for f, _ in mirror._fields_] == fields, name
+        assert C.sizeof(mirror) == 4 * len(fields), name
