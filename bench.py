@@ -534,8 +534,10 @@ def main():
 
     def step(inputs, out):
         p = make_plan()
+        stats["k0"] = p.info["k0"]
         p.match(*inputs, chunk=args.chunk, out=out, exhaustive=args.exhaustive,
-                phase_scores=mixed, tile_order=tuned["tile_order"] if tuned else 0)
+                phase_scores=mixed, tile_order=tuned["tile_order"] if tuned else 0,
+                cta_pairs=tuned["cta_pairs"] if tuned else 0)
         stats["evaluated"] = p.get_info()["last_evaluated"]
         if W.get("refine"):
             p.refine(*inputs, out["orient"], orient_alt=out["runner_orient"])
@@ -630,7 +632,7 @@ def main():
     K = args.steps
     value = world * B * K / (dev_ms / 1e3)
     roof = roofline(prof, peaks, src, B, K, args.precision, int(scan.row_ptr[-1]),
-                    stats.get("refine_pairs", 0), pattern_shell_rows(scan))
+                    stats.get("refine_pairs", 0), pattern_shell_rows(scan), stats.get("k0", 0))
     line = {"metric": METRIC, "value": value, "unit": "patterns/s", "n_gpus": world,
             "steps": K, "warmup": args.warmup, "ms_per_step": dev_ms / K,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -639,8 +641,10 @@ def main():
             "config": {**workload_config(scan), "precision": args.precision,
                        "chunk": args.chunk or (1024 if args.exhaustive else 8192),
                        "autotuned": ({"chunk": tuned["chunk"], "tile_order": tuned["tile_order"],
-                                      "trials_ms": {f"{t['chunk']}/{t['tile_order']}": round(t["ms"], 2)
-                                                    for t in trials}} if tuned else None),
+                                      "cta_pairs": tuned["cta_pairs"],
+                                      "trials_ms": {f"{t['chunk']}/{t['tile_order']}/{t['cta_pairs']}":
+                                                    round(t["ms"], 2) for t in trials}}
+                                     if tuned else None),
                        "mode": "exhaustive" if args.exhaustive else "certified pruning",
                        "axes_evaluated_per_pattern": stats.get("evaluated", 0) / B,
                        "l2": "flushed between steps (256 MiB write outside the timed events)",
@@ -855,7 +859,7 @@ def kernel_traffic(name, pats, precision):
 
 
 def kernel_roofline(name, cnt, ms, peaks, src, B, K, nnz, precision, refine_pairs=0,
-                    rows_nz=None):
+                    rows_nz=None, k0=0):
     """Achieved rate of one kernel class: algorithmic work per launch over its
     event-timed average launch duration."""
     Z, S, N = W["Z"], W["S"], W["N"]
@@ -870,6 +874,9 @@ def kernel_roofline(name, cnt, ms, peaks, src, B, K, nnz, precision, refine_pair
             peaks["bf16_tflops"]
         note = (f"8 Z S F flops per pattern; bf16 burst peak, which FP16 operands "
                 f"share ({src})")
+        if k0:
+            note += (f"; the kernel skips shells 0..{k0 - 1}, where every plan row is zero "
+                     f"(it executes {W['S'] - k0} of the {W['S']} shells counted)")
     elif name == "contract_fp32":
         work, unit, bound, peak = 8.0 * Z * S * F * pats, "TFLOP/s", "alu", fp32_peak
         note = "8 Z S F flops per pattern; FP32 FMA peak 152 SMs x 128 lanes x 2 x max clock"
@@ -906,7 +913,7 @@ def kernel_roofline(name, cnt, ms, peaks, src, B, K, nnz, precision, refine_pair
             "launches": cnt, "peak_source": note}
 
 
-def roofline(prof, peaks, src, B, K, precision, nnz, refine_pairs=0, rows_nz=None):
+def roofline(prof, peaks, src, B, K, precision, nnz, refine_pairs=0, rows_nz=None, k0=0):
     """The dominant kernel's roofline (the largest event-timed total among
     the kernels with a stated roofline), plus every other kernel's share."""
     rows = []
@@ -914,7 +921,7 @@ def roofline(prof, peaks, src, B, K, precision, nnz, refine_pairs=0, rows_nz=Non
         if cnt == 0:
             continue
         r = kernel_roofline(name, cnt, ms, peaks, src, B, K, nnz, precision, refine_pairs,
-                            rows_nz)
+                            rows_nz, k0)
         if r is not None:
             r["total_ms"] = ms
             rows.append(r)

@@ -142,6 +142,9 @@ typedef struct {
     int32_t n_phases;         /* crystal structures (1 unless concatenated)     */
     int64_t last_refine_pairs; /* (reflection, peak) pairs the last acom_refine
                                   summed over all its score evaluations        */
+    int32_t k0;               /* first shell of the tensor-core contraction: the
+                                 plan's rows below it are zero for every axis,
+                                 so those products are skipped (0: none)      */
 } acom_plan_info;
 
 acom_status acom_plan_get_info(acom_plan plan, acom_plan_info* info);
@@ -262,22 +265,24 @@ typedef struct {
     int32_t tile_order;       /* tensor-core contraction schedule: 0 consecutive
                                  tiles share a pattern tile (default), 1 they
                                  share a zone-axis tile                       */
-    int32_t single_cta;       /* tensor-core contraction: 0 (default) pairs of
-                                 CTAs compute each MMA together (cta_group::2,
-                                 M = 256 patterns rows), 1 one CTA per MMA    */
+    int32_t cta_pairs;        /* tensor-core contraction: 0 (default) one CTA
+                                 per MMA; 1 pairs of CTAs compute each MMA
+                                 together (cta_group::2, M = 256 pattern rows) */
 } acom_match_opts;
 
 /*
  * acom_autotune - the contraction's schedule picked by measurement: the
  * match of ``peaks`` (a representative sample, DEVICE) is timed (CUDA events,
- * after a warm-up match) for chunk sizes 4096, 8192 and 16384 and both tile
- * orders, with the other options from ``base`` (may be NULL).  ``best``
- * receives the fastest (chunk, tile_order, ms), ``trials`` (optional, 6
- * entries) every one.  Pass best's chunk and tile_order in acom_match_opts.
+ * after a warm-up match) for chunk sizes 4096, 8192 and 16384, both tile
+ * orders and both CTA arrangements (one CTA or a CTA pair per MMA), with the
+ * other options from ``base`` (may be NULL).  ``best`` receives the fastest
+ * (chunk, tile_order, cta_pairs, ms), ``trials`` (optional, 12 entries) every
+ * one.  Pass best's chunk, tile_order and cta_pairs in acom_match_opts.
  */
 typedef struct {
     int32_t chunk;
     int32_t tile_order;
+    int32_t cta_pairs;
     float ms;
 } acom_tune_result;
 

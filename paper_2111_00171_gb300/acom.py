@@ -65,7 +65,7 @@ class PlanInfo(C.Structure):
     _fields_ = [("n_za", C.c_int32), ("n_shells", C.c_int32), ("n_phi", C.c_int32),
                 ("n_freq", C.c_int32), ("n_reflections", C.c_int32), ("precision", C.c_int32),
                 ("device_bytes", C.c_int64), ("last_evaluated", C.c_int64),
-                ("n_phases", C.c_int32), ("last_refine_pairs", C.c_int64)]
+                ("n_phases", C.c_int32), ("last_refine_pairs", C.c_int64), ("k0", C.c_int32)]
 
 
 class PeaksCSR(C.Structure):
@@ -83,11 +83,12 @@ class Result(C.Structure):
 
 class MatchOpts(C.Structure):
     _fields_ = [("refine", C.c_int32), ("chunk", C.c_int32), ("exhaustive", C.c_int32),
-                ("rescore_top", C.c_int32), ("tile_order", C.c_int32), ("single_cta", C.c_int32)]
+                ("rescore_top", C.c_int32), ("tile_order", C.c_int32), ("cta_pairs", C.c_int32)]
 
 
 class TuneResult(C.Structure):
-    _fields_ = [("chunk", C.c_int32), ("tile_order", C.c_int32), ("ms", C.c_float)]
+    _fields_ = [("chunk", C.c_int32), ("tile_order", C.c_int32), ("cta_pairs", C.c_int32),
+                ("ms", C.c_float)]
 
 
 class RefineOpts(C.Structure):
@@ -365,19 +366,19 @@ class Plan:
 
     def match(self, row_ptr, qx, qy, I, refine=True, chunk=0, za_scores=False, out=None,
               exhaustive=False, phase_scores=False, runner=False, rescore_top=0, tile_order=0,
-              single_cta=0, stream=None):
+              cta_pairs=0, stream=None):
         """acom_match on device CSR tensors; returns a dict of device tensors
         (with phase_scores: the phase of each winner and every phase's best;
         with runner: the runner-up axis, score and grid orientation;
-        single_cta=1: the tensor-core contraction with one CTA per MMA instead
-        of CTA pairs)."""
+        cta_pairs=1: the tensor-core contraction on CTA pairs instead of one
+        CTA per MMA)."""
         pk = self._csr(row_ptr, qx, qy, I)
         r = out if out is not None else self.alloc_result(pk.n_patterns, za_scores=za_scores,
                                                           phase_scores=phase_scores,
                                                           runner=runner)
         res = Result(*(_ptr(r.get(k)) for k, _ in Result._fields_))
         opts = MatchOpts(1 if refine else 0, int(chunk), 1 if exhaustive else 0, int(rescore_top),
-                         int(tile_order), int(single_cta))
+                         int(tile_order), int(cta_pairs))
         _check(self._lib.acom_match(self.handle, C.byref(pk), C.byref(opts), C.byref(res),
                                     _stream_ptr(stream)))
         return r
@@ -398,13 +399,14 @@ class Plan:
 
     def autotune(self, row_ptr, qx, qy, I, stream=None):
         """acom_autotune on a sample of peaks: (best, trials), each a dict of
-        chunk, tile_order and ms."""
+        chunk, tile_order, cta_pairs and ms."""
         pk = self._csr(row_ptr, qx, qy, I)
         best = TuneResult()
-        trials = (TuneResult * 6)()
+        trials = (TuneResult * 12)()
         _check(self._lib.acom_autotune(self.handle, C.byref(pk), None, C.byref(best), trials,
                                        _stream_ptr(stream)))
-        as_dict = lambda t: {"chunk": t.chunk, "tile_order": t.tile_order, "ms": t.ms}
+        as_dict = lambda t: {"chunk": t.chunk, "tile_order": t.tile_order,
+                             "cta_pairs": t.cta_pairs, "ms": t.ms}
         return as_dict(best), [as_dict(t) for t in trials]
 
     def sync(self, stream=None):

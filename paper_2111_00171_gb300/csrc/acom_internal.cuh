@@ -279,10 +279,10 @@ void launch_half_to_e4m3(const void* src, void* dst, int64_t n, float mul, cudaS
 // budget in clock cycles of the tensor-core contraction's pipeline waits (0: default)
 void set_wait_cycles(long long cycles);
 // xscale: per-pattern 2^e of FP16 pattern spectra (nullptr: BF16, no scale)
-// single_cta: 1 one CTA per MMA (cta_group::1), 0 CTA pairs (cta_group::2)
+// cta_pairs: 0 one CTA per MMA (cta_group::1), 1 CTA pairs (cta_group::2)
 void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_stride, int nb,
                               float* U, cudaStream_t st, const float* xscale = nullptr,
-                              int tile_order = 0, int single_cta = 0);
+                              int tile_order = 0, int cta_pairs = 0);
 // the plan's FP32 spectra Pr, Pi [Zp][F][Spad] -> the merged operand p->Pb:
 // BF16 of P^ (kind 0), FP16 (1) or E4M3 (2) of scale * P^
 void launch_plan_to_operand(const float* Pr, const float* Pi, int Zp, int F, int Spad, void* dst,

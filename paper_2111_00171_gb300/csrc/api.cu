@@ -653,6 +653,7 @@ acom_status acom_plan_get_info(acom_plan p, acom_plan_info* info) {
     info->last_evaluated = p->last_evaluated;
     info->n_phases = p->n_phases;
     info->last_refine_pairs = p->last_refine_pairs;
+    info->k0 = p->k0;
     return ACOM_OK;
 }
 
@@ -799,9 +800,9 @@ static acom_status match_enqueue(acom_plan p, const acom_peaks_csr* peaks,
     const int tile_order = opts ? opts->tile_order : 0;
     if (tile_order < 0 || tile_order > 1)
         return set_error(ACOM_ERR_INVALID_ARG, "tile_order must be 0 or 1");
-    const int single_cta = opts ? opts->single_cta : 0;
-    if (single_cta < 0 || single_cta > 1)
-        return set_error(ACOM_ERR_INVALID_ARG, "single_cta must be 0 or 1");
+    const int cta_pairs = opts ? opts->cta_pairs : 0;
+    if (cta_pairs < 0 || cta_pairs > 1)
+        return set_error(ACOM_ERR_INVALID_ARG, "cta_pairs must be 0 or 1");
     if (exhaustive && (out->runner_za || out->runner_score || out->runner_orient))
         return set_error(ACOM_ERR_UNSUPPORTED, "runner-up outputs need certified pruning");
     if (!exhaustive && p->Z > 16384)
@@ -856,7 +857,7 @@ static acom_status match_enqueue(acom_plan p, const acom_peaks_csr* peaks,
             if (tc) {
                 convert_fp8(p, w, st);
                 launch_contract_bound_tc(p, w.map_x, w.PTs, nb, w.U, st, xscale, tile_order,
-                                         single_cta);
+                                         cta_pairs);
             } else {
                 launch_contract_bound_fp32(p, w.Xr, w.Xi, nb, w.U, st);
             }
@@ -1142,6 +1143,7 @@ acom_status acom_autotune(acom_plan p, const acom_peaks_csr* peaks, const acom_m
     r.score = sc;
     acom_match_opts o = base ? *base : acom_match_opts{1, 0, 0, 0, 0, 0};
     const int chunks[3] = {4096, 8192, 16384};
+    const bool tc = tc_precision(p->precision) && !o.exhaustive;
     cudaEvent_t t0, t1;
     cudaEventCreate(&t0);
     cudaEventCreate(&t1);
@@ -1149,9 +1151,11 @@ acom_status acom_autotune(acom_plan p, const acom_peaks_csr* peaks, const acom_m
     best->ms = -1.0f;
     int n = 0;
     for (int ci = 0; ci < 3 && s == ACOM_OK; ++ci)
-        for (int order = 0; order < 2 && s == ACOM_OK; ++order) {
+        for (int order = 0; order < 2 && s == ACOM_OK; ++order)
+            for (int pairs = 0; pairs < 2 && s == ACOM_OK; ++pairs) {
             o.chunk = chunks[ci];
             o.tile_order = order;
+            o.cta_pairs = tc ? pairs : 0;
             s = acom_match(p, peaks, &o, &r, cuda_stream);           // warm-up, sizes the workspace
             if (s != ACOM_OK) break;
             cudaEventRecord(t0, st);
@@ -1160,7 +1164,7 @@ acom_status acom_autotune(acom_plan p, const acom_peaks_csr* peaks, const acom_m
             cudaEventSynchronize(t1);
             float ms = 0.f;
             cudaEventElapsedTime(&ms, t0, t1);
-            const acom_tune_result tr{o.chunk, order, ms};
+            const acom_tune_result tr{o.chunk, order, o.cta_pairs, ms};
             if (trials) trials[n] = tr;
             ++n;
             if (best->ms < 0.f || ms < best->ms) *best = tr;

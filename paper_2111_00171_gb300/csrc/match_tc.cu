@@ -763,7 +763,7 @@ void set_wait_cycles(long long cycles) { g_wait_cycles = cycles > 0 ? cycles : 0
 
 void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_stride, int nb,
                               float* U, cudaStream_t st, const float* xscale, int tile_order,
-                              int single_cta) {
+                              int cta_pairs) {
     tc::TcArgs a;
     a.zmajor = tile_order == 1 ? 1 : 0;
     a.F = p->F;
@@ -792,7 +792,7 @@ void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_st
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const CUtensorMap& mx = *reinterpret_cast<const CUtensorMap*>(map_x);
-    if (!single_cta && nsm >= 2) {
+    if (cta_pairs && nsm >= 2) {
         // CTA pairs: M = 256 (the pair's two pattern tiles), each CTA loading
         // half of the 256 B rows (128-row boxes)
         a.idesc = (a.idesc & ~(0x1Fu << 24)) | ((256u >> 4) << 24);

@@ -480,7 +480,8 @@ def test_autotune_trials_and_tile_orders():
     scan = synth.random_patterns(1401, n_patterns=200)
     inp = to_dev(scan)
     best, trials = plan.autotune(*inp)
-    assert len(trials) == 6 and all(t["ms"] > 0 for t in trials)
+    assert len(trials) == 12 and all(t["ms"] > 0 for t in trials)
+    assert sorted({t["cta_pairs"] for t in trials}) == [0, 1]
     assert best["ms"] == min(t["ms"] for t in trials)
     a = plan.match(*inp, tile_order=0)
     b = plan.match(*inp, tile_order=1, chunk=best["chunk"])
@@ -534,8 +535,8 @@ def test_many_peaks_and_radius_ties(c1):
 
 @pytest.mark.parametrize("precision", [1, 2, 3], ids=["bf16", "fp16", "fp8"])
 def test_cta_pairs_equal_single_cta(precision):
-    """The tensor-core contraction on CTA pairs (cta_group::2, the default)
-    computes the same dot products in the same order as one CTA per MMA:
+    """The tensor-core contraction on CTA pairs (cta_group::2) computes the
+    same dot products in the same order as one CTA per MMA (the default):
     bounds, winners and scores are bitwise equal, on a chunk with an odd
     number of 64-pattern tiles (the last pair's second CTA has no patterns)."""
     import torch
@@ -543,8 +544,8 @@ def test_cta_pairs_equal_single_cta(precision):
     scan = synth.random_patterns(1601, n_patterns=300)
     inp = to_dev(scan)
     for chunk in (0, 192):
-        a = plan.match(*inp, za_scores=True, chunk=chunk, single_cta=0)
-        b = plan.match(*inp, za_scores=True, chunk=chunk, single_cta=1)
+        a = plan.match(*inp, za_scores=True, chunk=chunk, cta_pairs=1)
+        b = plan.match(*inp, za_scores=True, chunk=chunk, cta_pairs=0)
         torch.cuda.synchronize()
         for k in ("za_idx", "phi3_bin", "mirror", "score", "za_scores", "orient"):
             assert torch.equal(a[k], b[k]), (chunk, k)
