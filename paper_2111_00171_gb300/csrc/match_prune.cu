@@ -820,7 +820,7 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_select_exact(SelectArgs a) {
         const float Emax = sm.st->Emax;
         const int2 sr = a.srange[b];
         int evals = 0;
-        // batches in decreasing bound: the first takes the 4 largest bounds, later
+        // batches in decreasing bound: the first takes the 2 largest bounds, later
         // ones every axis whose bound can still reach the best exact score
         for (int batch = 0;; ++batch) {
             // rescore_top: the top axes by bound only, taken kBatch at a time
@@ -828,7 +828,7 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_select_exact(SelectArgs a) {
             if (a.rescore_top > 0 && left <= 0) break;
             const float thr = (batch == 0 || a.rescore_top > 0) ? -CUDART_INF_F : sm.st->T;
             const int K = a.rescore_top > 0 ? (left < kBatch ? left : kBatch)
-                                            : (batch == 0 ? 4 : kBatch);
+                                            : (batch == 0 ? 2 : kBatch);
             block_topk(sm, Z, K, thr, rel, Emax, per_phase && batch > 0 && a.rescore_top == 0,
                        nph);
             const int nc = sm.st->nc;
