@@ -632,7 +632,8 @@ def main():
     K = args.steps
     value = world * B * K / (dev_ms / 1e3)
     roof = roofline(prof, peaks, src, B, K, args.precision, int(scan.row_ptr[-1]),
-                    stats.get("refine_pairs", 0), pattern_shell_rows(scan), stats.get("k0", 0))
+                    stats.get("refine_pairs", 0),
+                    None if args.exhaustive else pattern_shell_rows(scan), stats.get("k0", 0))
     line = {"metric": METRIC, "value": value, "unit": "patterns/s", "n_gpus": world,
             "steps": K, "warmup": args.warmup, "ms_per_step": dev_ms / K,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -828,12 +829,12 @@ def read_profile(lib, acom):
 # the patterns of a launch (then another chunk size is scaled); the
 # contraction's does not (the plan is re-read once per tile wave).
 TRAFFIC_PER_LAUNCH = {
-    "select_exact": (2.54e9 + 61.46e6, 16384, ("match_prune.cu",), "6b63e7655bbedf67", "fp16",
+    "select_exact": (2.492e9 + 60.15e6, 16384, ("match_prune.cu",), "611903d9cf9ef8a2", "fp16",
                      "au_scan_256x256_1deg", True),
-    "raster_patterns": (10.39e6 + 5.72e9, 16384, ("raster.cu",), "56e2c3cbab7aa848", "fp16",
+    "raster_patterns": (11.08e6 + 4.389e9, 16384, ("raster.cu",), "85c3e7fca3930f41", "fp16",
                         "au_scan_256x256_1deg", True),
-    "contract_tc": (3.56e9 + 57.59e6, 16384, ("match_tc.cu",), "a6890ff94d6b0f7f", "fp16",
-                      "au_scan_256x256_1deg", False),
+    "contract_tc": (3.686e9 + 58.17e6, 16384, ("match_tc.cu",), "70019920168cc5bf", "fp16",
+                    "au_scan_256x256_1deg", False),
 }
 
 
@@ -899,11 +900,16 @@ def kernel_roofline(name, cnt, ms, peaks, src, B, K, nnz, precision, refine_pair
                 "FP32 FMA peak 152 SMs x 128 lanes x 2 x max clock")
     elif name == "raster_patterns":
         # algorithmic bytes: CSR in (8 B row pointer + 12 B per peak) and the
-        # spectra out (FP32 re/im, S x F; BF16 copy when the tensor path runs)
-        out_b = S * F * 2 * (4 + 2)
+        # spectra out: the contraction's operand (re/im, S x F; 16-bit, or
+        # FP32 frequency-major for the FP32 contraction) and the FP32
+        # shell-major rows select reads, those of the shells the pattern's
+        # peaks reach (rows_nz of S; the raster writes no other row)
+        rows = S if rows_nz is None else rows_nz
+        out_b = S * F * 2 * (4 if precision == "fp32" else 2) + rows * F * 8
         work = (nnz / B * 12 + 8 + out_b) * pats / 1e9
         unit, bound, peak = "GB/s", "hbm", peaks["hbm_gbs"]
-        note = f"CSR in + FP32 and 16-bit spectra out per pattern; HBM peak ({src})"
+        note = (f"CSR in + contraction operand out + FP32 shell-major spectra on the "
+                f"{rows:.1f} of {S} shells the peaks reach per pattern; HBM peak ({src})")
     else:
         return None
     ach = work / avg_s / (1e12 if unit == "TFLOP/s" else 1.0)
