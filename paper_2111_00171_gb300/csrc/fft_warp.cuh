@@ -178,6 +178,114 @@ __device__ __forceinline__ float2* warp_fft_fixed(float2* src, float2* dst, int 
     }
 }
 
+// ---------------------------------------------------------------------------
+// N = 360 as a prime-factor (Good-Thomas) transform over 8 x 9 x 5, factors
+// pairwise coprime, so no twiddle factors between the stages.  The row holds
+// the input permuted: bin j at
+//   pfa360_in(j) = 45 n1 + 5 n2 + n3,  n1 = 5j mod 8, n2 = 7j mod 9, n3 = 3j mod 5,
+// the unique (n1, n2, n3) with j = (45 n1 + 40 n2 + 72 n3) mod 360.  With
+// w_M = exp(-2 pi i / M),
+//   X[f] = sum_{n1,n2,n3} x[n1, n2, n3] w_8^(n1 f) w_9^(n2 f) w_5^(n3 f)
+// because w_360^(45 n1 f) = w_8^(n1 f) and so on, and w_8^(n1 f) depends on f
+// mod 8 only: the transform is a DFT of length 8 along n1, 9 along n2 and 5
+// along n3, computed in place (each small DFT writes the positions it read),
+// and X[f] ends at pfa360_out(f) = 45 (f mod 8) + 5 (f mod 9) + (f mod 5).
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int pfa360_in(int j) {
+    return 45 * ((5 * j) % 8) + 5 * ((7 * j) % 9) + (3 * j) % 5;
+}
+__host__ __device__ inline int pfa360_out(int f) { return 45 * (f % 8) + 5 * (f % 9) + f % 5; }
+
+__device__ __forceinline__ void dft8(float2* v) {
+    // split into even and odd outputs: b_k = v_k + v_(k+4) gives X_(2m) = DFT4(b)_m,
+    // c_k = (v_k - v_(k+4)) w_8^k gives X_(2m+1) = DFT4(c)_m
+    const float r2 = 0.7071067811865476f;     // sqrt(1/2)
+    float2 b[4], c[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        b[k] = make_float2(v[k].x + v[k + 4].x, v[k].y + v[k + 4].y);
+        c[k] = make_float2(v[k].x - v[k + 4].x, v[k].y - v[k + 4].y);
+    }
+    c[1] = make_float2(r2 * (c[1].x + c[1].y), r2 * (c[1].y - c[1].x));     // (1 - i) / sqrt 2
+    c[2] = make_float2(c[2].y, -c[2].x);                                  // -i
+    c[3] = make_float2(-r2 * (c[3].x - c[3].y), -r2 * (c[3].x + c[3].y)); // -(1 + i) / sqrt 2
+    dft_small<4>(b);
+    dft_small<4>(c);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        v[2 * m] = b[m];
+        v[2 * m + 1] = c[m];
+    }
+}
+
+__device__ __forceinline__ void dft9(float2* v) {
+    // 9 = 3 x 3 (Cooley-Tukey): input 3 n1 + n2, output k1 + 3 k2, twiddles w_9^(n2 k1)
+    const float2 w1 = make_float2(0.766044443118978f, 0.6427876096865393f);     // (cos, sin)(2 pi / 9)
+    const float2 w2 = make_float2(0.17364817766693041f, 0.984807753012208f);    // 4 pi / 9
+    const float2 w4 = make_float2(-0.9396926207859083f, 0.3420201433256689f);   // 8 pi / 9
+    float2 y[3][3];
+#pragma unroll
+    for (int n2 = 0; n2 < 3; ++n2) {
+        y[n2][0] = v[n2];
+        y[n2][1] = v[3 + n2];
+        y[n2][2] = v[6 + n2];
+        dft_small<3>(y[n2]);
+    }
+    y[1][1] = cmul_conj(y[1][1], w1);
+    y[1][2] = cmul_conj(y[1][2], w2);
+    y[2][1] = cmul_conj(y[2][1], w2);
+    y[2][2] = cmul_conj(y[2][2], w4);
+#pragma unroll
+    for (int k1 = 0; k1 < 3; ++k1) {
+        float2 t[3] = {y[0][k1], y[1][k1], y[2][k1]};
+        dft_small<3>(t);
+        v[k1] = t[0];
+        v[k1 + 3] = t[1];
+        v[k1 + 6] = t[2];
+    }
+}
+
+// In-place forward transform of the permuted row z (360 complex values, z +
+// zz when zz is given: the two rows are summed as the first stage loads them).
+// One warp; z must not be read by other warps meanwhile.
+__device__ __forceinline__ void warp_pfa360(float2* z, const float2* zz, int lane) {
+    for (int d = lane; d < 45; d += 32) {           // length 8 along n1: stride 45
+        float2 v[8];
+#pragma unroll
+        for (int n1 = 0; n1 < 8; ++n1) {
+            v[n1] = z[45 * n1 + d];
+            if (zz) {
+                const float2 u = zz[45 * n1 + d];
+                v[n1].x += u.x;
+                v[n1].y += u.y;
+            }
+        }
+        dft8(v);
+#pragma unroll
+        for (int k1 = 0; k1 < 8; ++k1) z[45 * k1 + d] = v[k1];
+    }
+    __syncwarp();
+    for (int d = lane; d < 40; d += 32) {           // length 9 along n2: stride 5
+        const int base = 45 * (d / 5) + d % 5;
+        float2 v[9];
+#pragma unroll
+        for (int n2 = 0; n2 < 9; ++n2) v[n2] = z[base + 5 * n2];
+        dft9(v);
+#pragma unroll
+        for (int k2 = 0; k2 < 9; ++k2) z[base + 5 * k2] = v[k2];
+    }
+    __syncwarp();
+    for (int d = lane; d < 72; d += 32) {           // length 5 along n3: stride 1
+        float2 v[5];
+#pragma unroll
+        for (int n3 = 0; n3 < 5; ++n3) v[n3] = z[5 * d + n3];
+        dft_small<5>(v);
+#pragma unroll
+        for (int k3 = 0; k3 < 5; ++k3) z[5 * d + k3] = v[k3];
+    }
+    __syncwarp();
+}
+
 // radices of N in the order 4, 2, 3, 5; n = 0 when N has another factor
 inline FftRadix fft_radices(int N) {
     FftRadix r{};

@@ -465,6 +465,7 @@ size_t raster_fft_smem_bytes(int N, int F, size_t peak_bytes) {
     b += sizeof(float2) * 2 * W * N;                     // per-warp row and transform buffer
     b += sizeof(uint32_t) * 2 * F * kFftStageWords;      // BF16 staging of a shell tile
     b += sizeof(int) * 64;                               // scratch
+    if (N == 360) b += sizeof(uint16_t) * 2 * 360;       // prime-factor input, output positions
     return b;
 }
 
@@ -483,6 +484,12 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
     float2* zt = zb + W * N;
     uint32_t* stage = reinterpret_cast<uint32_t*>(zt + W * N);   // [2F][kFftStageWords]
     int* s_int = reinterpret_cast<int*>(stage + 2 * F * kFftStageWords);
+    // N = 360: the rows hold the bins in the prime-factor transform's input
+    // order (bin j at s_perm[j]), the transform runs in place and leaves
+    // frequency f at s_pout[f]
+    const bool pfa = N == 360;
+    uint16_t* s_perm = reinterpret_cast<uint16_t*>(s_int + 64);
+    uint16_t* s_pout = s_perm + 360;
     float* scratch = reinterpret_cast<float*>(zb);     // after the last transform of an item
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -491,6 +498,11 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
         sincospi(2.0 * (double)i / (double)N, &sn, &c);
         tw[i] = make_float2((float)c, (float)sn);
     }
+    if (pfa)
+        for (int i = threadIdx.x; i < 360; i += blockDim.x) {
+            s_perm[i] = (uint16_t)pfa360_in(i);
+            s_pout[i] = (uint16_t)pfa360_out(i);
+        }
     __syncthreads();
     const float delta = geo.delta, d2 = delta * delta, inv_delta = 1.0f / delta;
     const float two_pi = 2.0f * CUDART_PI_F;
@@ -629,10 +641,11 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
                                 const float ta = inA ? 1.0f - sa * inv_delta : 0.f;
                                 const float tb = inB ? 1.0f - sb * inv_delta : 0.f;
                                 if (ta > 0.f || tb > 0.f) {
-                                    float2 v = acc[j];
+                                    const int jj = pfa ? (int)s_perm[j] : j;
+                                    float2 v = acc[jj];
                                     if (ta > 0.f) v.x = fmaf(wA, ta, v.x);
                                     if (tb > 0.f) v.y = fmaf(wB, tb, v.y);
-                                    acc[j] = v;
+                                    acc[jj] = v;
                                 }
                             }
                         } else {
@@ -648,10 +661,11 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
                                 const float ta = inA ? 1.0f - sa * inv_delta : 0.f;
                                 const float tb = inB ? 1.0f - sb * inv_delta : 0.f;
                                 if (ta > 0.f || tb > 0.f) {
-                                    float2 v = acc[j];
+                                    const int jj = pfa ? (int)s_perm[j] : j;
+                                    float2 v = acc[jj];
                                     if (ta > 0.f) v.x = fmaf(wA, ta, v.x);
                                     if (tb > 0.f) v.y = fmaf(wB, tb, v.y);
-                                    acc[j] = v;
+                                    acc[jj] = v;
                                 }
                             }
                         }
@@ -672,7 +686,10 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
                 if (lane == 0 && any && out.rmask)
                     atomicOr(reinterpret_cast<unsigned*>(s_int + 16 + (sA >> 5)),
                              (anyA ? 1u << (sA & 31) : 0u) | (anyB ? 1u << ((sA + 1) & 31) : 0u));
-                if (any) {
+                if (any && pfa) {
+                    __syncwarp();
+                    warp_pfa360(z, zz, lane);     // sums the two rows as it loads them
+                } else if (any) {
                     __syncwarp();
                     if ((N & 1) == 0) {
                         float4* z4 = reinterpret_cast<float4*>(z);
@@ -697,7 +714,8 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
                     }
                     __syncwarp();
                 }
-                const float2* Z = any ? warp_fft_fixed(z, zz, N, rad, tw, lane) : nullptr;
+                const float2* Z =
+                    !any ? nullptr : (pfa ? z : warp_fft_fixed(z, zz, N, rad, tw, lane));
                 // real rows a (shell sA), b (shell sA + 1) from Z = FFT(a + i b):
                 //   A_f = (Z_f + conj Z_{N-f}) / 2,  B_f = -i (Z_f - conj Z_{N-f}) / 2
                 const int64_t srow = (item * (int64_t)Spad + sA) * Fs;
@@ -708,8 +726,9 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
                     if (f >= Fs) break;
                     float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
                     if (any && f < F) {
-                        const float2 zf = Z[f];
-                        const float2 zc = Z[f == 0 ? 0 : N - f];
+                        const int fc = f == 0 ? 0 : N - f;
+                        const float2 zf = Z[pfa ? (int)s_pout[f] : f];
+                        const float2 zc = Z[pfa ? (int)s_pout[fc] : fc];
                         ar = 0.5f * (zf.x + zc.x);
                         ai = 0.5f * (zf.y - zc.y);
                         br = 0.5f * (zf.y + zc.y);
