@@ -829,11 +829,11 @@ def read_profile(lib, acom):
 # the patterns of a launch (then another chunk size is scaled); the
 # contraction's does not (the plan is re-read once per tile wave).
 TRAFFIC_PER_LAUNCH = {
-    "select_exact": (2.492e9 + 60.15e6, 16384, ("match_prune.cu",), "611903d9cf9ef8a2", "fp16",
+    "select_exact": (2.848e9 + 86.87e6, 16384, ("match_prune.cu",), "21a79e4528eed2cb", "fp16",
                      "au_scan_256x256_1deg", True),
-    "raster_patterns": (11.08e6 + 4.389e9, 16384, ("raster.cu",), "85c3e7fca3930f41", "fp16",
+    "raster_patterns": (10.24e6 + 4.388e9, 16384, ("raster.cu",), "2989349b66433168", "fp16",
                         "au_scan_256x256_1deg", True),
-    "contract_tc": (3.686e9 + 58.17e6, 16384, ("match_tc.cu",), "70019920168cc5bf", "fp16",
+    "contract_tc": (3.683e9 + 58.25e6, 16384, ("match_tc.cu",), "2957c40ed77763e1", "fp16",
                     "au_scan_256x256_1deg", False),
 }
 

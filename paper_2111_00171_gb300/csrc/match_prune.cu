@@ -192,7 +192,7 @@ void launch_plan_fnorm_max(const acom_plan_s* p, float* out, cudaStream_t st) {
 //    carries both) and the argmax over (phi3, mirror);
 //  * selection: a block-wide top-K of the pending bounds, two barriers.
 // ---------------------------------------------------------------------------
-constexpr int kSelThreads = 384;
+constexpr int kSelThreads = 256;
 constexpr int kSelWarps = kSelThreads / 32;
 constexpr int kBatch = 8;
 
@@ -231,6 +231,10 @@ struct SelSmem {
     uint16_t* slist; // [kBatch][Spad] shells of each candidate: pattern and plan rows both
                      // not zero
     int* slen;       // [kBatch]
+    // N = 360: the spectra rows hold frequency f at perm[f] (the prime-factor
+    // transform's input order), and the transform leaves bin k at pout[k]
+    uint16_t* perm;
+    uint16_t* pout;
     SelState* st;
 };
 
@@ -462,8 +466,9 @@ __device__ void batch_spectra(const SelectArgs& a, int64_t b, int nc, int s_lo, 
         const float mre = (A - B) * invN, mim = -(C + D) * invN;
         // stored conjugated: the inverse transform runs as a forward one
         float2* y = sm.y + c * N;
-        y[f] = make_float2(dre - mim, -(dim + mre));
-        if (f > 0 && 2 * f < N) y[N - f] = make_float2(dre + mim, dim - mre);
+        const bool pfa = sm.perm != nullptr;
+        y[pfa ? (int)sm.perm[f] : f] = make_float2(dre - mim, -(dim + mre));
+        if (f > 0 && 2 * f < N) y[pfa ? (int)sm.perm[N - f] : N - f] = make_float2(dre + mim, dim - mre);
     }
     __syncthreads();
 }
@@ -478,7 +483,11 @@ __device__ void batch_transforms(const SelectArgs& a, int nc, SelSmem& sm) {
         float2* row = sm.y + c * N;
         float2* alt = sm.yt + c * N;
         const float2* out;
-        if (a.rad.n > 0) {
+        const uint16_t* pout = sm.pout;     // non-null: bin k at out[pout[k]]
+        if (pout) {
+            warp_pfa360(row, nullptr, lane);
+            out = row;
+        } else if (a.rad.n > 0) {
             out = warp_fft_fixed(row, alt, N, a.rad, sm.tw, lane);
         } else {
             for (int k = lane; k < N; k += 32) {
@@ -499,7 +508,7 @@ __device__ void batch_transforms(const SelectArgs& a, int nc, SelSmem& sm) {
         float bv = -CUDART_INF_F;
         unsigned bi = 0xffffffffu;
         for (int k = lane; k < N; k += 32) {
-            const float2 v = out[k];
+            const float2 v = out[pout ? (int)pout[k] : k];
             if (better(v.x, (unsigned)k, bv, bi)) {
                 bv = v.x;
                 bi = (unsigned)k;
@@ -512,7 +521,9 @@ __device__ void batch_transforms(const SelectArgs& a, int nc, SelSmem& sm) {
         warp_argmax(bv, bi);
         if (lane == 0) {
             const int m = (int)(bi / (unsigned)N), k = (int)bi - m * N;
-            const float2 ym = out[(k + N - 1) % N], y0 = out[k], yp = out[(k + 1) % N];
+            const int km = (k + N - 1) % N, kp = (k + 1) % N;
+            const float2 ym = out[pout ? (int)pout[km] : km], y0 = out[pout ? (int)pout[k] : k],
+                         yp = out[pout ? (int)pout[kp] : kp];
             float* r = sm.res + 5 * c;
             r[0] = bv;
             r[1] = __uint_as_float(bi);
@@ -721,7 +732,7 @@ __host__ __device__ inline size_t sel_items(int F) {
     return (size_t)(kSelThreads > kBatch * Fq ? kSelThreads : kBatch * Fq);
 }
 
-__global__ void __launch_bounds__(kSelThreads, 2) k_select_exact(SelectArgs a) {
+__global__ void __launch_bounds__(kSelThreads, 3) k_select_exact(SelectArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Z = a.Z, F = a.F, N = a.N;
     SelSmem sm;
@@ -749,6 +760,11 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_select_exact(SelectArgs a) {
     sm.pmask = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (a.Spad >> 5)));
     sm.slist = reinterpret_cast<uint16_t*>(take(sizeof(uint16_t) * kBatch * a.Spad));
     sm.slen = reinterpret_cast<int*>(take(sizeof(int) * kBatch));
+    sm.perm = sm.pout = nullptr;
+    if (N == 360) {
+        sm.perm = reinterpret_cast<uint16_t*>(take(sizeof(uint16_t) * 360));
+        sm.pout = reinterpret_cast<uint16_t*>(take(sizeof(uint16_t) * 360));
+    }
     sm.st = reinterpret_cast<SelState*>(take(sizeof(SelState)));
     sm.ev = take(Z);
     sm.kb = reinterpret_cast<uint16_t*>(take(sizeof(uint16_t) * Z));
@@ -761,6 +777,10 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_select_exact(SelectArgs a) {
         double s, c;
         sincospi(2.0 * (double)i / (double)N, &s, &c);
         sm.tw[i] = make_float2((float)c, (float)s);
+        if (sm.perm) {
+            sm.perm[i] = (uint16_t)pfa360_in(i);
+            sm.pout[i] = (uint16_t)pfa360_out(i);
+        }
     }
     const float rel = 1.0f + 1e-5f;     // FP32 accumulation of U and of the scores
     const bool want_ref = (a.out.phi3 != nullptr) || (a.out.orient != nullptr);
@@ -953,6 +973,7 @@ size_t select_smem_bytes(int Z, int N, int F, int Spad) {
            r16(sizeof(float) * 2 * kSelWarps) + r16(sizeof(int) * (kMaxPhases + 1)) +
            r16(sizeof(uint32_t) * (Spad >> 5)) + r16(sizeof(uint16_t) * kBatch * Spad) +
            r16(sizeof(int) * kBatch) +
+           (N == 360 ? 2 * r16(sizeof(uint16_t) * 360) : 0) +
            r16(sizeof(SelState)) + r16(Z) + r16(sizeof(uint16_t) * Z);
 }
 
