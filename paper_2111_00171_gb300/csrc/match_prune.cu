@@ -126,26 +126,22 @@ void launch_contract_bound_fp32(const acom_plan_s* p, const float* Xr, const flo
 }
 
 // ---------------------------------------------------------------------------
-// max over zone axes of ||P^_zf||_2 (over shells), per frequency
-// ---------------------------------------------------------------------------
+// max over zone axes of ||P^_zf||_2 (over shells), per frequency, times
+// 1.0001 for the rounding of the norm itself: one warp per (axis, frequency)
+// row, lanes over the shells; the maximum of non-negative floats by an
+// integer atomicMax on their bit patterns (out cleared to +0 first)
 __global__ void k_plan_fnorm_max(const float* __restrict__ Pr, const float* __restrict__ Pi,
                                  int Z, int F, int Spad, float* __restrict__ out) {
-    const int f = blockIdx.x;
-    __shared__ float red[256];
-    float mx = 0.f;
-    for (int z = threadIdx.x; z < Z; z += blockDim.x) {
-        const int64_t o = ((int64_t)z * F + f) * Spad;
-        float a = 0.f;
-        for (int s = 0; s < Spad; ++s) a = fmaf(Pr[o + s], Pr[o + s], fmaf(Pi[o + s], Pi[o + s], a));
-        mx = fmaxf(mx, sqrtf(a));
-    }
-    red[threadIdx.x] = mx;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + o]);
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) out[f] = red[0] * 1.0001f;   // rounding of the norm itself
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= (int64_t)Z * F) return;
+    const int f = (int)(row % F);
+    const float* pr = Pr + row * Spad;
+    const float* pi = Pi + row * Spad;
+    float a = 0.f;
+    for (int s = lane; s < Spad; s += 32) a = fmaf(pr[s], pr[s], fmaf(pi[s], pi[s], a));
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) atomicMax(reinterpret_cast<int*>(out) + f, __float_as_int(sqrtf(a) * 1.0001f));
 }
 
 // bit s of word [z][s / 32]: shell row s of axis z (re or im) has a non-zero
@@ -174,8 +170,11 @@ void launch_plan_shell_mask(const acom_plan_s* p, cudaStream_t st) {
 }
 
 void launch_plan_fnorm_max(const acom_plan_s* p, float* out, cudaStream_t st) {
+    const int64_t rows = (int64_t)p->Z * p->F;
+    cudaMemsetAsync(out, 0, sizeof(float) * (size_t)p->F, st);
     prof_begin(kKMisc, st);
-    k_plan_fnorm_max<<<p->F, 256, 0, st>>>(p->Pr, p->Pi, p->Z, p->F, p->Spad, out);
+    k_plan_fnorm_max<<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(p->Pr, p->Pi, p->Z, p->F, p->Spad,
+                                                                   out);
     prof_end(kKMisc, st);
 }
 

@@ -852,25 +852,33 @@ __device__ __forceinline__ __nv_fp8_e4m3 to_half_type<__nv_fp8_e4m3>(float x) {
 template <class T>
 __global__ void k_plan_to_operand(const float* __restrict__ Pr, const float* __restrict__ Pi,
                                   int Zp, int F, int Spad, T* __restrict__ dst, float scale) {
-    const int64_t total = (int64_t)2 * Zp * F * Spad;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int s = (int)(i % Spad);
-        const int64_t t = i / Spad;            // (f, zt, row) of the operand
-        const int row = (int)(t % 256);
-        const int64_t t2 = t / 256;
-        const int zt = (int)(t2 % (Zp / 128));
-        const int f = (int)(t2 / (Zp / 128));
-        const int z = zt * 128 + (row & 127);
-        const float* src = row < 128 ? Pr : Pi;
-        dst[i] = to_half_type<T>(scale * src[((int64_t)z * F + f) * Spad + s]);
+    // one warp per operand row (f, zt, row): row < 128 takes the real part of
+    // axis zt 128 + row, row >= 128 the imaginary part of axis zt 128 + row - 128;
+    // lanes over the shells, four at a time (Spad is a multiple of 32)
+    const int lane = threadIdx.x & 31;
+    const int64_t orow = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int ZT = Zp / 128;
+    if (orow >= (int64_t)F * ZT * 256) return;
+    const int row = (int)(orow % 256);
+    const int64_t t = orow / 256;
+    const int zt = (int)(t % ZT), f = (int)(t / ZT);
+    const int z = zt * 128 + (row & 127);
+    const float4* src = reinterpret_cast<const float4*>((row < 128 ? Pr : Pi) +
+                                                        ((int64_t)z * F + f) * Spad);
+    T* d = dst + orow * Spad;
+    for (int q = lane; q < Spad / 4; q += 32) {
+        const float4 v = src[q];
+        d[4 * q] = to_half_type<T>(scale * v.x);
+        d[4 * q + 1] = to_half_type<T>(scale * v.y);
+        d[4 * q + 2] = to_half_type<T>(scale * v.z);
+        d[4 * q + 3] = to_half_type<T>(scale * v.w);
     }
 }
 
 void launch_plan_to_operand(const float* Pr, const float* Pi, int Zp, int F, int Spad, void* dst,
                             cudaStream_t st, int kind, float scale) {
-    const int64_t total = (int64_t)2 * Zp * F * Spad;
-    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
+    const int64_t rows = (int64_t)F * (Zp / 128) * 256;        // one warp per row
+    const unsigned blocks = (unsigned)((rows + 7) / 8);
     prof_begin(kKMisc, st);
     if (kind == 2)
         k_plan_to_operand<__nv_fp8_e4m3><<<blocks, 256, 0, st>>>(

@@ -874,28 +874,30 @@ void launch_raster_patterns(const RasterGeom& geo, const PatternSource& src,
 
 // P = A P0 with A = 1/||P0||_2 (0 for an empty slice): the transform is
 // linear, so the spectrum rows are scaled after the fact.
-__global__ void k_scale_rows(float* re, float* im, const float* sumsq, int items,
-                             int64_t row_elems) {
-    int64_t total = (int64_t)items * row_elems;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        int item = (int)(i / row_elems);
-        float ss = sumsq[item];
-        float a = ss > 0.f ? rsqrtf(ss) : 0.f;
-        re[i] *= a;
-        im[i] *= a;
+// rows of item y scaled by 1 / sqrt(sumsq[y]) (0 for an all-zero item);
+// row_elems is a multiple of 4 (16-byte accesses), blockIdx.y is the item
+__global__ void k_scale_rows(float* re, float* im, const float* sumsq, int row_elems) {
+    const int item = blockIdx.y;
+    const float ss = sumsq[item];
+    const float a = ss > 0.f ? rsqrtf(ss) : 0.f;
+    float4* r4 = reinterpret_cast<float4*>(re + (int64_t)item * row_elems);
+    float4* i4 = reinterpret_cast<float4*>(im + (int64_t)item * row_elems);
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < row_elems / 4; q += gridDim.x * blockDim.x) {
+        float4 u = r4[q], v = i4[q];
+        u.x *= a; u.y *= a; u.z *= a; u.w *= a;
+        v.x *= a; v.y *= a; v.z *= a; v.w *= a;
+        r4[q] = u;
+        i4[q] = v;
     }
 }
 
 void launch_scale_rows(float* re, float* im, const float* sumsq, int items, int row_elems,
                        cudaStream_t st) {
-    int64_t total = (int64_t)items * row_elems;
-    int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
-    if (blocks > 0) {
-        prof_begin(kKScale, st);
-        k_scale_rows<<<blocks, 256, 0, st>>>(re, im, sumsq, items, row_elems);
-        prof_end(kKScale, st);
-    }
+    if (items <= 0) return;
+    const dim3 grid((unsigned)((row_elems / 4 + 255) / 256), (unsigned)items);
+    prof_begin(kKScale, st);
+    k_scale_rows<<<grid, 256, 0, st>>>(re, im, sumsq, row_elems);
+    prof_end(kKScale, st);
 }
 
 // [items][F][Spad] planar -> [items][S][F][2] interleaved
