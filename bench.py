@@ -820,20 +820,20 @@ def read_profile(lib, acom):
     return {e.name.decode(): (e.launches, e.total_ms) for e in arr}
 
 
-# DRAM bytes (read + write) of one launch of 16,384 patterns, from a
-# single-pass ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# full-size run, with a hash of the kernel's
+# DRAM bytes (read + write) of one launch of the captured size (the second
+# field, in patterns), from a single-pass ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) of the full-size run, with a hash of the kernel's
 # sources at capture time, the precision and the workload of the captured
 # run: a changed kernel, or another precision or workload, reports no
 # traffic.  The last field says whether the traffic grows in proportion to
 # the patterns of a launch (then another chunk size is scaled); the
 # contraction's does not (the plan is re-read once per tile wave).
 TRAFFIC_PER_LAUNCH = {
-    "select_exact": (2.848e9 + 86.87e6, 16384, ("match_prune.cu",), "21a79e4528eed2cb", "fp16",
+    "select_exact": (5.682e9 + 155.1e6, 32768, ("match_prune.cu",), "b7df4e41a41b9963", "fp16",
                      "au_scan_256x256_1deg", True),
-    "raster_patterns": (10.24e6 + 4.388e9, 16384, ("raster.cu",), "2989349b66433168", "fp16",
+    "raster_patterns": (22.63e6 + 8.793e9, 32768, ("raster.cu",), "7ae3fe52d61f27f4", "fp16",
                         "au_scan_256x256_1deg", True),
-    "contract_tc": (3.683e9 + 58.25e6, 16384, ("match_tc.cu",), "2957c40ed77763e1", "fp16",
+    "contract_tc": (10.385e9 + 116.9e6, 32768, ("match_tc.cu",), "2374f172a1709922", "fp16",
                     "au_scan_256x256_1deg", False),
 }
 

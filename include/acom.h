@@ -273,7 +273,7 @@ typedef struct {
 /*
  * acom_autotune - the contraction's schedule picked by measurement: the
  * match of ``peaks`` (a representative sample, DEVICE) is timed (CUDA events,
- * after a warm-up match) for chunk sizes 4096, 8192 and 16384, both tile
+ * after a warm-up match) for chunk sizes 8192, 16384 and 32768, both tile
  * orders and both CTA arrangements (one CTA or a CTA pair per MMA), with the
  * other options from ``base`` (may be NULL).  ``best`` receives the fastest
  * (chunk, tile_order, cta_pairs, ms), ``trials`` (optional, 12 entries) every

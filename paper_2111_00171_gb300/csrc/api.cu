@@ -1142,7 +1142,7 @@ acom_status acom_autotune(acom_plan p, const acom_peaks_csr* peaks, const acom_m
     r.mirror = mi;
     r.score = sc;
     acom_match_opts o = base ? *base : acom_match_opts{1, 0, 0, 0, 0, 0};
-    const int chunks[3] = {4096, 8192, 16384};
+    const int chunks[3] = {8192, 16384, 32768};
     const bool tc = tc_precision(p->precision) && !o.exhaustive;
     cudaEvent_t t0, t1;
     cudaEventCreate(&t0);

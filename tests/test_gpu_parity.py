@@ -473,7 +473,8 @@ def test_match_async_captured_in_cuda_graph():
 
 
 def test_autotune_trials_and_tile_orders():
-    """acom_autotune times six schedules and returns the fastest; both tile
+    """acom_autotune times twelve schedules (three chunk sizes, two tile
+    orders, one CTA or a CTA pair per MMA) and returns the fastest; both tile
     orders of the contraction give bit-identical results."""
     import torch
     plan = gpu_plan("au_2deg_75x180", precision=2)
