@@ -333,13 +333,17 @@ struct TcArgs {
 // F8: E4M3 operands (kind::f8f6f4, 128 elements per K tile), else 16-bit
 // (kind::f16, 64 elements per K tile); a template parameter, so the MMA issue
 // loop carries no branch on it
-// Ring geometry: a single CTA stages X (16 KB) and the whole B operand (32 KB)
-// per K tile; a CTA of a pair stages X and its half of B (16 KB each), so a
-// pair's ring is deeper.
-template <bool PAIR>
+// Ring geometry.  A stage holds kSub K tiles of X (16 KB each) and of the B
+// operand: for a single CTA with 16-bit operands two K tiles (128 shells: the
+// whole K range of a frequency on the 1-degree plan, so one barrier round trip
+// per frequency instead of two), X 32 KB + B 64 KB, two stages; with E4M3
+// operands (128 shells per K tile already) one K tile, four stages; a CTA of a
+// pair stages X and its half of B (16 KB each), so a pair's ring is deeper.
+template <bool F8, bool PAIR>
 struct Ring {
-    static constexpr int kStageBytes = (PAIR ? 2 : 3) * kTileBytes;
-    static constexpr int kStages = PAIR ? 6 : 4;
+    static constexpr int kSub = (PAIR || F8) ? 1 : 2;
+    static constexpr int kStageBytes = kSub * (PAIR ? 2 : 3) * kTileBytes;
+    static constexpr int kStages = PAIR ? 6 : (kSub == 2 ? 2 : 4);
 };
 
 // F8: E4M3 operands (kind::f8f6f4, 128 elements per K tile), else 16-bit
@@ -357,8 +361,9 @@ template <bool F8, bool PAIR>
 __global__ void __launch_bounds__(kThreads, 1)
 k_contract_bound_tc(const __grid_constant__ CUtensorMap map_p,
                     const __grid_constant__ CUtensorMap map_x, TcArgs a) {
-    constexpr int kSt = Ring<PAIR>::kStages;
-    constexpr int kSB = Ring<PAIR>::kStageBytes;
+    constexpr int kSt = Ring<F8, PAIR>::kStages;
+    constexpr int kSB = Ring<F8, PAIR>::kStageBytes;
+    constexpr int kSub = Ring<F8, PAIR>::kSub;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte alignment of the operand ring
     unsigned char* base = reinterpret_cast<unsigned char*>(
@@ -458,26 +463,31 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_p,
                         const uint32_t fb = smem_u32(full + own * kSt + stage);
                         unsigned char* sbuf = ring + stage * kSB;
                         constexpr int ktel = F8 ? kKT8 : kKT;
+                        // the stage's first shell; K tiles past the padded shells are
+                        // not loaded (nor expected, nor multiplied)
+                        const int kbase = a.k0 + kt * ktel * kSub;
+                        const int nsub = (kSub == 1 || a.Spad - kbase > ktel) ? kSub : 1;
                         if constexpr (PAIR) {
                             // every copy completes on the leading CTA's barrier, which
                             // expects both CTAs' bytes of its operand
                             const uint32_t fbl = mapa_rank(fb, 0);
                             if (leader) mbar_expect_tx(fb, 2 * kTileBytes);
                             if (xprod)
-                                tma_load_2d_pair(smem_u32(sbuf), &map_x, a.k0 + kt * ktel, xrow,
-                                                 fbl);
+                                tma_load_2d_pair(smem_u32(sbuf), &map_x, kbase, xrow, fbl);
                             else
-                                tma_load_2d_pair(smem_u32(sbuf + kTileBytes), &map_p,
-                                                 a.k0 + kt * ktel,
+                                tma_load_2d_pair(smem_u32(sbuf + kTileBytes), &map_p, kbase,
                                                  prow, fbl);
                         } else if (xprod) {
-                            mbar_expect_tx(fb, kTileBytes);
-                            tma_load_2d(smem_u32(sbuf), &map_x, a.k0 + kt * ktel, xrow, fb);
+                            mbar_expect_tx(fb, nsub * kTileBytes);
+                            for (int u = 0; u < nsub; ++u)
+                                tma_load_2d(smem_u32(sbuf + u * kTileBytes), &map_x,
+                                            kbase + u * ktel, xrow, fb);
                         } else {
                             // B operand: 256 rows, the tile's re rows then its im rows
-                            mbar_expect_tx(fb, 2 * kTileBytes);
-                            tma_load_2d(smem_u32(sbuf + kTileBytes), &map_p, a.k0 + kt * ktel,
-                                        prow, fb);
+                            mbar_expect_tx(fb, nsub * 2 * kTileBytes);
+                            for (int u = 0; u < nsub; ++u)
+                                tma_load_2d(smem_u32(sbuf + (kSub + 2 * u) * kTileBytes), &map_p,
+                                            kbase + u * ktel, prow, fb);
                         }
                         issued_mask |= 1u << stage;
                         const uint32_t par = (fpar[own] >> stage) & 1u;
@@ -556,13 +566,16 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_p,
                         // fill); a step moves the descriptors' start address by
                         // 32 bytes (2 units of 16)
                         constexpr int ktel = F8 ? kKT8 : kKT;
-                        const int nk =
-                            (min(ktel, a.Spad - a.k0 - kt * ktel) * (F8 ? 1 : 2)) >> 5;
-                        const uint64_t xa = sdesc(sb), pb = sdesc(sb + kTileBytes);
+                        const int kbase = a.k0 + kt * ktel * kSub;
+                        const int nk = (min(ktel * kSub, a.Spad - kbase) * (F8 ? 1 : 2)) >> 5;
 #pragma unroll
-                        for (int k4 = 0; k4 < 4; ++k4)
-                            if (k4 < nk) {
-                                const uint32_t acc = (kt | k4) ? 1u : 0u;
+                        for (int j = 0; j < 4 * kSub; ++j)
+                            if (j < nk) {
+                                // K tile j / 4 of the stage, step j % 4 inside it
+                                const int k4 = j & 3, u = j >> 2;
+                                const uint64_t xa = sdesc(sb + u * kTileBytes);
+                                const uint64_t pb = sdesc(sb + (kSub + 2 * u) * kTileBytes);
+                                const uint32_t acc = (kt | j) ? 1u : 0u;
                                 if constexpr (PAIR) {
                                     if constexpr (F8)
                                         mma_f8kind_pair(dacc, xa + 2 * k4, pb + 2 * k4, a.idesc, acc);
@@ -700,10 +713,10 @@ k_contract_bound_tc(const __grid_constant__ CUtensorMap map_p,
     }
 }
 
-template <bool PAIR>
+template <bool F8, bool PAIR>
 size_t tc_smem_bytes() {
-    return 1024 + (size_t)Ring<PAIR>::kStages * Ring<PAIR>::kStageBytes +
-           8 * ((kIssuers + 1) * Ring<PAIR>::kStages + 3 * kIssuers) + 16;
+    return 1024 + (size_t)Ring<F8, PAIR>::kStages * Ring<F8, PAIR>::kStageBytes +
+           8 * ((kIssuers + 1) * Ring<F8, PAIR>::kStages + 3 * kIssuers) + 16;
 }
 
 }  // namespace tc
@@ -775,9 +788,10 @@ void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_st
     a.PTs = pt_stride;
     const bool f8 = p->precision == ACOM_PREC_FP8;
     const int ktel = f8 ? tc::kKT8 : tc::kKT;
-    // the K range starts at the plan's first non-zero shell (a multiple of 16)
+    // the K range starts at the plan's first non-zero shell (a multiple of 16);
+    // KT stages of kSub K tiles each per frequency
     a.k0 = p->k0;
-    a.KT = (p->Spad - p->k0 + ktel - 1) / ktel;
+    auto stages = [&](int sub) { return (p->Spad - p->k0 + ktel * sub - 1) / (ktel * sub); };
     a.Spad = p->Spad;
     a.Zrows = 2 * p->Zp;
     a.U = U;
@@ -796,7 +810,8 @@ void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_st
         // CTA pairs: M = 256 (the pair's two pattern tiles), each CTA loading
         // half of the 256 B rows (128-row boxes)
         a.idesc = (a.idesc & ~(0x1Fu << 24)) | ((256u >> 4) << 24);
-        const size_t smem = tc::tc_smem_bytes<true>();
+        a.KT = stages(1);
+        const size_t smem = f8 ? tc::tc_smem_bytes<true, true>() : tc::tc_smem_bytes<false, true>();
         auto kern = f8 ? tc::k_contract_bound_tc<true, true> : tc::k_contract_bound_tc<false, true>;
         set_max_dynamic_smem((const void*)kern, smem);
         const int n_tiles = a.ZT * ((a.PT + 1) / 2);
@@ -819,7 +834,8 @@ void launch_contract_bound_tc(const acom_plan_s* p, const void* map_x, int pt_st
         prof_end(kKContractBf16, st);
         return;
     }
-    const size_t smem = tc::tc_smem_bytes<false>();
+    a.KT = f8 ? stages(tc::Ring<true, false>::kSub) : stages(tc::Ring<false, false>::kSub);
+    const size_t smem = f8 ? tc::tc_smem_bytes<true, false>() : tc::tc_smem_bytes<false, false>();
     auto kern = f8 ? tc::k_contract_bound_tc<true, false> : tc::k_contract_bound_tc<false, false>;
     set_max_dynamic_smem((const void*)kern, smem);
     const int n_tiles = a.ZT * a.PT;
