@@ -79,6 +79,8 @@ struct PatternSource {         // one chunk of CSR patterns
     float gamma_pow, omega;
     int xb_fp16 = 0;           // xb holds FP16 of 2^e_b X^ instead of BF16 of X^
     float* xscale = nullptr;   // [n_items] 2^e_b of each pattern (with xb_fp16)
+    int xb_k0 = 0;             // the contraction reads xb from this shell on: 16-shell
+                               // tiles wholly below it are not written
 };
 
 // FP16 operands of the tensor-core contraction: each pattern's spectrum is

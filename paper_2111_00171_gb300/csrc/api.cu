@@ -830,7 +830,7 @@ static acom_status match_enqueue(acom_plan p, const acom_peaks_csr* peaks,
         float* xscale = tc && p->precision != ACOM_PREC_BF16 ? w.xscale : nullptr;
         PatternSource src{tc ? w.XB : nullptr, w.PTs, peaks->row_ptr + c0, peaks->qx,
                           peaks->qy, peaks->I, nb, (float)p->gamma_pow, (float)p->omega,
-                          xscale ? 1 : 0, xscale};
+                          xscale ? 1 : 0, xscale, p->k0};
         RasterOut ro;
         ro.re = fp32_contraction ? w.Xr : nullptr;
         ro.im = fp32_contraction ? w.Xi : nullptr;
@@ -946,7 +946,7 @@ acom_status acom_bounds(acom_plan p, const acom_peaks_csr* peaks, float* dst, vo
         float* xscale = tc && p->precision != ACOM_PREC_BF16 ? p->ws.xscale : nullptr;
         PatternSource src{tc ? p->ws.XB : nullptr, p->ws.PTs, peaks->row_ptr + c0, peaks->qx,
                           peaks->qy, peaks->I, nb, (float)p->gamma_pow, (float)p->omega,
-                          xscale ? 1 : 0, xscale};
+                          xscale ? 1 : 0, xscale, p->k0};
         RasterOut ro;
         ro.re = tc ? nullptr : p->ws.Xr;
         ro.im = tc ? nullptr : p->ws.Xi;

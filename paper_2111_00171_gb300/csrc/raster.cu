@@ -73,6 +73,7 @@ struct PatternLoader {
     __device__ int xb_tiles() const { return src.PTs; }
     __device__ bool xb_half() const { return src.xb_fp16 != 0; }
     __device__ float* xscale_out() const { return src.xscale; }
+    __device__ int xb_k0() const { return src.xb_k0; }
     __device__ int load(int64_t item, PeakXY* sp, int* s_warp, int* err) const {
         const int64_t b0 = src.row_ptr[item];
         const int64_t b1 = src.row_ptr[item + 1];
@@ -113,6 +114,7 @@ struct PlanLoader {
     __device__ int xb_tiles() const { return 0; }
     __device__ bool xb_half() const { return false; }
     __device__ float* xscale_out() const { return nullptr; }
+    __device__ int xb_k0() const { return 0; }
     __device__ int load(int64_t item, Peak* sp, int* s_warp, int* err) const {
         const double* R = src.frames + 9 * item;
         double R00 = R[0], R01 = R[1], R02 = R[2], R10 = R[3], R11 = R[4], R12 = R[5],
@@ -561,6 +563,8 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
         int w_lo = Spad, w_hi = 0;      // this warp's non-zero shells
 
         for (int t0 = 0; t0 < Spad; t0 += kFftTile) {
+            // the 16-bit copy of a tile the contraction never reads is skipped
+            const bool stg = xb && t0 + kFftTile > ld.xb_k0();
             // pairs warp and warp + W of the tile
             for (int pp = warp; pp < kFftTile / 2; pp += W) {
                 const int sA = t0 + 2 * pp;
@@ -617,8 +621,14 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
                         if (!inA && !inB) continue;
                         inA_any |= inA;
                         inB_any |= inB;
-                        const float hwA = inA ? sqrtf(d2 - a2A) * iqA : 0.f;
-                        const float hwB = inB ? sqrtf(d2 - a2B) * iqB : 0.f;
+                        // window half-widths (the window keeps a bin of margin on each
+                        // side, and each bin's tent is tested, so an approximate root
+                        // cannot drop a bin)
+                        float hwA = 0.f, hwB = 0.f;
+                        if (inA) asm("sqrt.approx.f32 %0, %1;" : "=f"(hwA) : "f"(d2 - a2A));
+                        if (inB) asm("sqrt.approx.f32 %0, %1;" : "=f"(hwB) : "f"(d2 - a2B));
+                        hwA *= iqA;
+                        hwB *= iqB;
                         const float hw = fmaxf(hwA, hwB);
                         const float wA = inA ? pk.w * rsA : 0.f, wB = inB ? pk.w * rsB : 0.f;
                         if (hw < hw_nowrap) {
@@ -749,12 +759,12 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
                             out.im[o] = ai;
                             out.im[o + 1] = bi;
                         }
-                        if (half) {
+                        if (stg && half) {
                             const __half2 vr = __floats2half2_rn(ar * xsc, br * xsc);
                             const __half2 vi = __floats2half2_rn(ai * xsc, bi * xsc);
                             stage[f * kFftStageWords + pw] = *reinterpret_cast<const uint32_t*>(&vr);
                             stage[(F + f) * kFftStageWords + pw] = *reinterpret_cast<const uint32_t*>(&vi);
-                        } else if (xb) {
+                        } else if (stg) {
                             const __nv_bfloat162 vr = __floats2bfloat162_rn(ar, br);
                             const __nv_bfloat162 vi = __floats2bfloat162_rn(ai, bi);
                             stage[f * kFftStageWords + pw] = *reinterpret_cast<const uint32_t*>(&vr);
@@ -764,7 +774,7 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
                 }
                 __syncwarp();
             }
-            if (xb) {
+            if (stg) {
                 // the tile's BF16 copy in the tensor-core layout (64-pattern tiles whose
                 // 16-row groups hold 8 patterns' real rows, then their imaginary rows):
                 // 32 bytes (16 shells) per row
