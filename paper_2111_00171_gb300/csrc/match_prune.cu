@@ -362,6 +362,7 @@ struct SelectArgs {
     int rescore_top;                  // > 0: evaluate only the top axes by bound (no certificate)
     const uint32_t* smask;            // [Zp][Spad / 32] non-zero plan shells
     OrientIn* oin;                    // [nb] the winners, for k_orient_compose
+    float eta_rs = 0.f;               // eta sqrt(Spad), from the host (FP64 there)
 };
 
 // Spectra c_dir + i c_mir of the batch's candidate axes, scaled by 1/N, into
@@ -803,7 +804,7 @@ __global__ void __launch_bounds__(kSelThreads, 3) k_select_exact(SelectArgs a) {
         //   eta sqrt(Spad) (||X^_bf|| 2^-k + ||P^_zf|| 2^-e + sqrt(Spad) eta 2^-(e+k)),
         // charged four times for the four real products of c_f
         const float inv_sc = a.xscale ? 1.0f / (a.xscale[b] * a.xs_mul) : 0.f;
-        const float tiny = (float)((double)a.eta * sqrt((double)a.Spad)) * inv_sc * a.inv_pscale;
+        const float tiny = a.eta_rs * inv_sc * a.inv_pscale;
         float e = 0.f, ea = 0.f;
         for (int f = threadIdx.x; f < F; f += kSelThreads) {
             const float w = (f == 0 || 2 * f == N) ? 1.f : 2.f;
@@ -827,7 +828,7 @@ __global__ void __launch_bounds__(kSelThreads, 3) k_select_exact(SelectArgs a) {
             }
             SelState& st = *sm.st;
             const float abs_term =
-                a.xscale ? (float)(4.0 * (double)a.eta * sqrt((double)a.Spad)) * ta : 0.f;
+                a.xscale ? 4.0f * a.eta_rs * ta : 0.f;
             st.Emax = (a.kappa * t + abs_term) / (float)N * 1.01f;
             st.T = -CUDART_INF_F;
             st.Tidx = 0xffffffffu;
@@ -988,6 +989,7 @@ void launch_select_exact(const acom_plan_s* p, const float* Xsr, const float* Xs
                  p->precision == ACOM_PREC_FP8 ? kFp8Shift : 1.0f,
                  (float)(p->precision == ACOM_PREC_FP8 ? kFp8Eta : kFp16Eta), rescore_top,
                  p->smask, oin};
+    a.eta_rs = (float)((double)a.eta * std::sqrt((double)p->Spad));
     const size_t smem = select_smem_bytes(p->Z, p->N, p->F, p->Spad);
     set_max_dynamic_smem((const void*)k_select_exact, smem);
     int dev = 0, nsm = 0, per_sm = 0;
