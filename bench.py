@@ -829,11 +829,11 @@ def read_profile(lib, acom):
 # the patterns of a launch (then another chunk size is scaled); the
 # contraction's does not (the plan is re-read once per tile wave).
 TRAFFIC_PER_LAUNCH = {
-    "select_exact": (5.682e9 + 155.1e6, 32768, ("match_prune.cu",), "b7df4e41a41b9963", "fp16",
+    "select_exact": (5.738e9 + 156.4e6, 32768, ("match_prune.cu",), "678367a81e8343f2", "fp16",
                      "au_scan_256x256_1deg", True),
-    "raster_patterns": (22.63e6 + 8.793e9, 32768, ("raster.cu",), "7ae3fe52d61f27f4", "fp16",
+    "raster_patterns": (21.40e6 + 8.037e9, 32768, ("raster.cu",), "0949631987c44546", "fp16",
                         "au_scan_256x256_1deg", True),
-    "contract_tc": (10.385e9 + 116.9e6, 32768, ("match_tc.cu",), "2374f172a1709922", "fp16",
+    "contract_tc": (7.005e9 + 115.0e6, 32768, ("match_tc.cu",), "b95d9dc1d59bc5f0", "fp16",
                     "au_scan_256x256_1deg", False),
 }
 
@@ -900,16 +900,20 @@ def kernel_roofline(name, cnt, ms, peaks, src, B, K, nnz, precision, refine_pair
                 "FP32 FMA peak 152 SMs x 128 lanes x 2 x max clock")
     elif name == "raster_patterns":
         # algorithmic bytes: CSR in (8 B row pointer + 12 B per peak) and the
-        # spectra out: the contraction's operand (re/im, S x F; 16-bit, or
-        # FP32 frequency-major for the FP32 contraction) and the FP32
-        # shell-major rows select reads, those of the shells the pattern's
-        # peaks reach (rows_nz of S; the raster writes no other row)
+        # spectra out: the contraction's operand (re/im, F frequencies: 16-bit
+        # on the shells from the plan's first non-zero shell k0 on, which are
+        # all the tensor-core contraction reads; FP32 frequency-major on all S
+        # shells for the FP32 contraction) and the FP32 shell-major rows
+        # select reads, those of the shells the pattern's peaks reach (rows_nz
+        # of S; the raster writes no other row)
         rows = S if rows_nz is None else rows_nz
-        out_b = S * F * 2 * (4 if precision == "fp32" else 2) + rows * F * 8
+        op_shells = S if precision == "fp32" else S - k0
+        out_b = op_shells * F * 2 * (4 if precision == "fp32" else 2) + rows * F * 8
         work = (nnz / B * 12 + 8 + out_b) * pats / 1e9
         unit, bound, peak = "GB/s", "hbm", peaks["hbm_gbs"]
-        note = (f"CSR in + contraction operand out + FP32 shell-major spectra on the "
-                f"{rows:.1f} of {S} shells the peaks reach per pattern; HBM peak ({src})")
+        note = (f"CSR in + contraction operand on {op_shells} shells out + FP32 shell-major "
+                f"spectra on the {rows:.1f} of {S} shells the peaks reach per pattern; "
+                f"HBM peak ({src})")
     else:
         return None
     ach = work / avg_s / (1e12 if unit == "TFLOP/s" else 1.0)
