@@ -222,11 +222,12 @@ typedef struct {
  *             bound could reach it) and is otherwise an upper bound of the
  *             axis' maximum (the bound of acom_bounds plus a rounding margin).
  *   runner_za, runner_score, runner_orient  optional (certified pruning
- *             only; ACOM_ERR_UNSUPPORTED with exhaustive): the best evaluated
- *             zone axis outside the winner's grid neighbourhood (-1 if none),
- *             its exact score, and its grid orientation [n_patterns][9] (no
- *             sub-grid refinement; the winner's when there is none): a second
- *             start for acom_refine
+ *             only; ACOM_ERR_UNSUPPORTED with exhaustive): the best zone axis
+ *             outside the winner's grid neighbourhood, certified like the
+ *             winner (every axis there whose bound could beat it is evaluated;
+ *             -1 if the neighbourhood is the whole plan), its exact score, and
+ *             its grid orientation [n_patterns][9] (no sub-grid refinement;
+ *             the winner's when there is none): a second start for acom_refine
  *   phase     optional: the phase of za_idx (0 for a single-phase plan)
  *   phase_score optional: [n_patterns][n_phases] the best score of each
  *             phase (its maximum over its axes, phi3 and mirror).  With

@@ -888,45 +888,62 @@ __global__ void __launch_bounds__(kSelThreads, 3) k_select_exact(SelectArgs a) {
                 evals += nc;
             }
         }
-        if (a.out.za_scores)
-            for (int z = threadIdx.x; z < Z; z += kSelThreads)
-                a.out.za_scores[(a.off + b) * Z + z] = sm.ev[z] ? sm.U[z] : sm.U[z] * rel + Emax;
         if (a.out.runner_za || a.out.runner_score || a.out.runner_orient) {
-            // runner-up: the best evaluated axis other than the winner and its
-            // grid neighbours (bit 4 of ev marks them while this runs)
+            // runner-up: the best axis other than the winner and its grid
+            // neighbours (bit 4 of ev marks them while this runs), certified
+            // like the winner: the best evaluated one so far, then the pending
+            // axes outside the neighbourhood whose bound can still beat it, in
+            // decreasing bound, until none can
             const int bz = sm.st->bz;
             const int q0 = a.nbr_ptr[bz], q1 = a.nbr_ptr[bz + 1];
             for (int q = q0 + threadIdx.x; q < q1; q += kSelThreads) sm.ev[a.nbr_idx[q]] |= 4;
             if (threadIdx.x == 0) sm.ev[bz] |= 4;
             __syncthreads();
-            float v = -CUDART_INF_F;
-            unsigned zi = 0xffffffffu;
-            for (int z = threadIdx.x; z < Z; z += kSelThreads)
-                if (sm.ev[z] == 1 && better(sm.U[z], (unsigned)z, v, zi)) {
-                    v = sm.U[z];
-                    zi = (unsigned)z;
-                }
-            warp_argmax(v, zi);
-            if (lane == 0) {
-                sm.wv[warp * kBatch] = v;
-                sm.wi[warp * kBatch] = (int)zi;
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                float bv = -CUDART_INF_F;
-                unsigned bi = 0xffffffffu;
-                for (int w = 0; w < kSelWarps; ++w)
-                    if (better(sm.wv[w * kBatch], (unsigned)sm.wi[w * kBatch], bv, bi)) {
-                        bv = sm.wv[w * kBatch];
-                        bi = (unsigned)sm.wi[w * kBatch];
+            for (;;) {
+                float v = -CUDART_INF_F;
+                unsigned zi = 0xffffffffu;
+                for (int z = threadIdx.x; z < Z; z += kSelThreads)
+                    if (sm.ev[z] == 1 && better(sm.U[z], (unsigned)z, v, zi)) {
+                        v = sm.U[z];
+                        zi = (unsigned)z;
                     }
-                sm.st->ru_z = bi == 0xffffffffu ? -1 : (int)bi;
-                sm.st->ru_v = bv;
+                warp_argmax(v, zi);
+                if (lane == 0) {
+                    sm.wv[warp * kBatch] = v;
+                    sm.wi[warp * kBatch] = (int)zi;
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    float bv = -CUDART_INF_F;
+                    unsigned bi = 0xffffffffu;
+                    for (int w = 0; w < kSelWarps; ++w)
+                        if (better(sm.wv[w * kBatch], (unsigned)sm.wi[w * kBatch], bv, bi)) {
+                            bv = sm.wv[w * kBatch];
+                            bi = (unsigned)sm.wi[w * kBatch];
+                        }
+                    sm.st->ru_z = bi == 0xffffffffu ? -1 : (int)bi;
+                    sm.st->ru_v = bv;
+                }
+                __syncthreads();
+                // an all-zero image: every axis ties at 0, nothing to certify
+                if (sm.st->T == 0.f && sm.st->Tidx == 0u && sm.st->ru_z >= 0) break;
+                const bool have = sm.st->ru_z >= 0;
+                block_topk(sm, Z, have ? kBatch : 2, have ? sm.st->ru_v : -CUDART_INF_F, rel, Emax,
+                           false, nph);
+                const int nc = sm.st->nc;
+                if (nc == 0) break;
+                batch_spectra(a, b, nc, sr.x, sr.y, sm);
+                batch_transforms(a, nc, sm);
+                fold_batch(nc, N, false, nph, sm);
+                evals += nc;
             }
             for (int q = q0 + threadIdx.x; q < q1; q += kSelThreads) sm.ev[a.nbr_idx[q]] &= 3;
             if (threadIdx.x == 0) sm.ev[bz] &= 3;
             __syncthreads();
         }
+        if (a.out.za_scores)
+            for (int z = threadIdx.x; z < Z; z += kSelThreads)
+                a.out.za_scores[(a.off + b) * Z + z] = sm.ev[z] ? sm.U[z] : sm.U[z] * rel + Emax;
         if (warp == 0) {
             if (lane == 0 && a.n_eval) atomicAdd(a.n_eval, evals);
             write_outputs(a, b, sm, want_ref, lane);

@@ -156,10 +156,11 @@ def test_coarse_match_then_refine_grain_scan():
 
 
 def test_runner_up_is_outside_the_winners_neighbourhood():
-    """The runner-up is the best evaluated axis that is neither the winner
-    nor one of its grid neighbours, its score is the oracle's exact maximum
-    for that axis, and its orientation is that axis' grid orientation (up to
-    the crystal's symmetry: a symmetric axis has tied maxima)."""
+    """The runner-up is the best axis that is neither the winner nor one of
+    its grid neighbours (the oracle's maximum over those axes, up to ties
+    within 1e-5), its score is the oracle's exact maximum for that axis, and
+    its orientation is that axis' grid orientation (up to the crystal's
+    symmetry: a symmetric axis has tied maxima)."""
     import torch
     plan = gpu_plan("au_2deg_75x180")
     from gpu_common import oracle_plan
@@ -178,10 +179,17 @@ def test_runner_up_is_outside_the_winners_neighbourhood():
             continue
         mt = O.match_pattern(op, *scan.pattern(b))
         assert rs[b] == pytest.approx(mt.za_scores[ru[b]], rel=1e-4), b
+        outside = np.setdiff1d(np.arange(len(op.za)), np.append(nb[za[b]], za[b]))
+        best_out = mt.za_scores[outside].max()
+        assert mt.za_scores[ru[b]] >= best_out * (1 - 1e-5), (b, ru[b], best_out)
         C = np.stack([mt.C[ru[b]], mt.Cm[ru[b]]])
-        mir, k = np.unravel_index(np.argmax(C), C.shape)
-        m = O.orientation_matrix(op.za[ru[b]], -2 * math.pi * k / N, int(mir))
-        # elementwise under the best symmetry operation (the angle from the
-        # trace is ill-conditioned for FP32-stored matrices near identity)
-        assert min(np.abs(S @ ro[b] - m).max() for S in ops) < 2e-6, b
+        # the grid orientation of the axis' maximum, or of a bin tied with it
+        # within 1e-5 (FP32 scores cannot order those); elementwise under the
+        # best symmetry operation (the angle from the trace is ill-conditioned
+        # for FP32-stored matrices near identity)
+        tied = np.argwhere(C >= C.max() - 1e-5 * abs(C.max()))
+        err = min(np.abs(S @ ro[b] - O.orientation_matrix(op.za[ru[b]], -2 * math.pi * k / N,
+                                                             int(mir))).max()
+                  for mir, k in tied for S in ops)
+        assert err < 2e-6, (b, err, len(tied))
     plan.close()
