@@ -250,6 +250,32 @@ __device__ void exp_so3(const double w[3], double E[9]) {
         }
 }
 
+// The same rotation in FP32 for the per-step update: sin(t)/t and
+// (1 - cos t)/t^2 = 2 sin^2(t/2) / t^2 (no cancellation), by their Taylor
+// series to t^4 below 0.05 rad.  The step's rotation is composed onto the
+// FP64 orientation, so its FP32 rounding (~1e-7 per step) does not accumulate
+// into the FP64 result beyond the steps' count.
+__device__ void exp_so3f(const float w[3], float E[9]) {
+    const float t2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    const float t = sqrtf(t2);
+    float A, B;
+    if (t < 0.05f) {
+        A = 1.0f - t2 * (1.0f / 6.0f - t2 * (1.0f / 120.0f));
+        B = 0.5f - t2 * (1.0f / 24.0f - t2 * (1.0f / 720.0f));
+    } else {
+        const float sh = sinf(0.5f * t);
+        A = sinf(t) / t;
+        B = 2.0f * sh * sh / t2;
+    }
+    const float K[9] = {0, -w[2], w[1], w[2], 0, -w[0], -w[1], w[0], 0};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            float k2 = 0;
+            for (int l = 0; l < 3; ++l) k2 += K[3 * i + l] * K[3 * l + j];
+            E[3 * i + j] = (i == j ? 1.0f : 0.0f) + A * K[3 * i + j] + B * k2;
+        }
+}
+
 // w = (H + damping diag(H) + 1e-12 tr(H) I)^-1 g, at most max_step in norm.
 __device__ void lm_step(const float H[6], const float g[3], float damping, float max_step,
                         float w[3]) {
@@ -278,15 +304,18 @@ __device__ void lm_step(const float H[6], const float g[3], float damping, float
     }
 }
 
-__device__ __forceinline__ void load9(const double* Rd, float R[9]) {
+__device__ __forceinline__ void load9(const float* Rf, float R[9]) {
     __syncwarp();
-    for (int i = 0; i < 9; ++i) R[i] = (float)Rd[i];
+    for (int i = 0; i < 9; ++i) R[i] = Rf[i];
 }
 
-// One refinement run from Rd (FP64 in the warp's shared memory, written by
-// lane 0).
-__device__ float refine_run(const RefArgs& a, double* Rd, int64_t p0, int M, const float* px,
-                            const float* py, const float* pa, int* act) {
+// One refinement run from Rd (FP64 in the warp's shared memory, with its FP32
+// copy Rf).  Every lane holds the same score, gradient and matrix, so every
+// lane takes the same step; lanes 0..8 compose one element of Exp(w) Rd each
+// in FP64 (FP64 instructions are scarce on this GPU: nine lanes issue three
+// multiply-adds where one lane issued a hundred).
+__device__ float refine_run(const RefArgs& a, double* Rd, float* Rf, int64_t p0, int M,
+                            const float* px, const float* py, const float* pa, int* act) {
     const int lane = threadIdx.x & 31;
     float R[9], S, g[3], H[6];
     for (int t = 0; t < a.steps; ++t) {
@@ -294,23 +323,24 @@ __device__ float refine_run(const RefArgs& a, double* Rd, int64_t p0, int M, con
                               ? a.rho_start * powf(a.rho_end / a.rho_start,
                                                    (float)t / (float)(a.steps - 1))
                               : a.rho_end;
-        load9(Rd, R);
+        load9(Rf, R);
         score_at(a, R, rho, p0, M, px, py, pa, act, S, g, H);
+        float w[3], E[9];
+        lm_step(H, g, a.damping, a.max_step, w);
+        exp_so3f(w, E);
+        double v = 0.0;
+        if (lane < 9) {
+            const int i = lane / 3, j = lane - 3 * (lane / 3);
+            v = (double)E[3 * i] * Rd[j] + (double)E[3 * i + 1] * Rd[3 + j] +
+                (double)E[3 * i + 2] * Rd[6 + j];
+        }
         __syncwarp();
-        if (lane == 0) {
-            float w[3];
-            lm_step(H, g, a.damping, a.max_step, w);
-            const double wd[3] = {w[0], w[1], w[2]};
-            double E[9], Rn[9];
-            exp_so3(wd, E);
-            for (int i = 0; i < 3; ++i)
-                for (int j = 0; j < 3; ++j)
-                    Rn[3 * i + j] = E[3 * i] * Rd[j] + E[3 * i + 1] * Rd[3 + j] +
-                                    E[3 * i + 2] * Rd[6 + j];
-            for (int i = 0; i < 9; ++i) Rd[i] = Rn[i];
+        if (lane < 9) {
+            Rd[lane] = v;
+            Rf[lane] = (float)v;
         }
     }
-    load9(Rd, R);
+    load9(Rf, R);
     score_at(a, R, a.rho_end, p0, M, px, py, pa, act, S, g, H);
     return S;
 }
@@ -351,6 +381,7 @@ __global__ void __launch_bounds__(kRefWarps * 32, 3) k_refine(RefArgs a) {
         s_pa[kRefWarps][kRefPeakSmem];
     __shared__ int s_act[kRefWarps][kRefActCap];
     __shared__ double s_R[kRefWarps][2][9];
+    __shared__ float s_Rf[kRefWarps][9];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float* px = s_px[warp];
     float* py = s_py[warp];
@@ -374,14 +405,14 @@ __global__ void __launch_bounds__(kRefWarps * 32, 3) k_refine(RefArgs a) {
             const float* src = (st & 2) ? src1 : src0;
             if (!src || ((st & 1) && !a.twin)) continue;
             __syncwarp();
-            if (lane == 0) {
-                for (int i = 0; i < 3; ++i)
-                    for (int j = 0; j < 3; ++j) {
-                        const double v = (double)src[3 * j + i];          // R = m^T
-                        Rc[3 * i + j] = ((st & 1) && i < 2) ? -v : v;     // (m Rz(pi))^T
-                    }
+            if (lane < 9) {
+                const int i = lane / 3, j = lane - 3 * (lane / 3);
+                const float v = src[3 * j + i];                    // R = m^T
+                const float r = ((st & 1) && i < 2) ? -v : v;      // (m Rz(pi))^T
+                Rc[lane] = (double)r;
+                s_Rf[warp][lane] = r;
             }
-            const float S = refine_run(a, Rc, p0, M, px, py, pa, act);
+            const float S = refine_run(a, Rc, s_Rf[warp], p0, M, px, py, pa, act);
             __syncwarp();
             if (S > best || st == 0) {
                 best = S;
@@ -433,7 +464,8 @@ __global__ void __launch_bounds__(kRefWarps * 32) k_kin_score(RefArgs a) {
                                     E[3 * i + 2] * M0[6 + j];
         }
         float R[9], S, g[3], H[6];
-        load9(Rd, R);
+        __syncwarp();
+        for (int i = 0; i < 9; ++i) R[i] = (float)Rd[i];
         score_at(a, R, a.rho, p0, M, px, py, pa, act, S, g, H);
         if (lane == 0) {
             if (a.score) a.score[b] = S;
