@@ -206,6 +206,7 @@ struct SelState {
     int q;               // next neighbour to consider (refinement batches)
     float best3[3];      // winning correlation at bins k - 1, k, k + 1
     float Emax;          // rounding margin of the bounds
+    float next_u;        // bound of the best pending axis after a batch's picks
     float Tp[kMaxPhases];  // best exact score so far of each phase
     int ru_z;            // runner-up: best evaluated axis outside the winner's
     float ru_v;          // grid neighbourhood (-1: none), and its score
@@ -265,11 +266,14 @@ __device__ inline void warp_argmax(float& v, unsigned& i) {
 // ev = 2.  Each warp takes its K best by repeated argmax over entries strictly
 // below its previous pick; warp 0 merges the warps' lists the same way.
 __device__ void block_topk(SelSmem& sm, int Z, int K, float thr, float rel, float Emax,
-                           bool per_phase, int nph) {
+                           bool per_phase, int nph, bool want_next = false) {
+    // with want_next, one more round finds the best pending axis after the K
+    // picks (K < kBatch): its bound goes to st->next_u (-inf: none), unpicked
+    const int Kr = K + (want_next ? 1 : 0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float lv = CUDART_INF_F;
     unsigned li = 0u;                       // previous pick (nothing is above it)
-    for (int r = 0; r < K; ++r) {
+    for (int r = 0; r < Kr; ++r) {
         float v = -CUDART_INF_F;
         unsigned zi = 0xffffffffu;
         for (int z = warp * 32 + lane; z < Z; z += kSelThreads) {
@@ -288,7 +292,7 @@ __device__ void block_topk(SelSmem& sm, int Z, int K, float thr, float rel, floa
             sm.wi[warp * kBatch + r] = (int)zi;
         }
         if (zi == 0xffffffffu) {
-            for (int r2 = r + 1 + lane; r2 < K; r2 += 32) sm.wi[warp * kBatch + r2] = -1;
+            for (int r2 = r + 1 + lane; r2 < Kr; r2 += 32) sm.wi[warp * kBatch + r2] = -1;
             break;
         }
         lv = v;
@@ -296,15 +300,16 @@ __device__ void block_topk(SelSmem& sm, int Z, int K, float thr, float rel, floa
     }
     __syncthreads();
     if (warp == 0) {
-        const int ne = kSelWarps * K;
+        const int ne = kSelWarps * Kr;
         lv = CUDART_INF_F;
         li = 0u;
         int n = 0;
-        for (int r = 0; r < K; ++r) {
+        float next = -CUDART_INF_F;
+        for (int r = 0; r < Kr; ++r) {
             float v = -CUDART_INF_F;
             unsigned zi = 0xffffffffu;
             for (int e = lane; e < ne; e += 32) {
-                const int w = e / K, j = e - w * K;
+                const int w = e / Kr, j = e - w * Kr;
                 const int z = sm.wi[w * kBatch + j];
                 if (z < 0) continue;
                 const float u = sm.wv[w * kBatch + j];
@@ -315,6 +320,10 @@ __device__ void block_topk(SelSmem& sm, int Z, int K, float thr, float rel, floa
             }
             warp_argmax(v, zi);
             if (zi == 0xffffffffu) break;
+            if (r == K) {                    // the best axis after the picks
+                next = v;
+                break;
+            }
             if (lane == 0) {
                 sm.cand[n] = (int)zi;
                 sm.ev[zi] = 2;
@@ -323,7 +332,10 @@ __device__ void block_topk(SelSmem& sm, int Z, int K, float thr, float rel, floa
             lv = v;
             li = zi;
         }
-        if (lane == 0) sm.st->nc = n;
+        if (lane == 0) {
+            sm.st->nc = n;
+            sm.st->next_u = next;
+        }
     }
     __syncthreads();
 }
@@ -840,66 +852,56 @@ __global__ void __launch_bounds__(kSelThreads, 3) k_select_exact(SelectArgs a) {
         const float Emax = sm.st->Emax;
         const int2 sr = a.srange[b];
         int evals = 0;
-        // batches in decreasing bound: the first takes the 2 largest bounds, later
-        // ones every axis whose bound can still reach the best exact score
-        for (int batch = 0;; ++batch) {
-            // rescore_top: the top axes by bound only, taken kBatch at a time
-            const int left = a.rescore_top - evals;
-            if (a.rescore_top > 0 && left <= 0) break;
-            const float thr = (batch == 0 || a.rescore_top > 0) ? -CUDART_INF_F : sm.st->T;
-            const int K = a.rescore_top > 0 ? (left < kBatch ? left : kBatch)
-                                            : (batch == 0 ? 2 : kBatch);
-            block_topk(sm, Z, K, thr, rel, Emax, per_phase && batch > 0 && a.rescore_top == 0,
-                       nph);
-            const int nc = sm.st->nc;
-            if (nc == 0) break;
-            batch_spectra(a, b, nc, sr.x, sr.y, sm);
-            batch_transforms(a, nc, sm);
-            fold_batch(nc, N, true, nph, sm);
-            evals += nc;
-            // an all-zero image: every axis ties at 0 and the lowest index has won
-            if (sm.st->T == 0.f && sm.st->Tidx == 0u) break;
-        }
-        // zone-axis neighbours that may reach 0.9 of the best need their exact score
-        const float T = sm.st->T;
-        if (want_ref && a.refine && T > 0.f) {
-            const int bz = sm.st->bz;
-            const int qe = a.nbr_ptr[bz + 1];
-            if (threadIdx.x == 0) sm.st->q = a.nbr_ptr[bz];
-            for (;;) {
-                // thread 0 gathers the next batch; every thread then runs it
+        // Three stages share one evaluation site (one copy of the batch code):
+        //  0 search: batches in decreasing bound, the first the 2 largest
+        //    bounds, later ones every axis whose bound can still reach the best
+        //    exact score (rescore_top: the top axes by bound only);
+        //  1 the winner's grid neighbours that may reach 0.9 of the best (their
+        //    exact scores weight the orientation refinement);
+        //  2 the runner-up: the best axis outside the winner and its grid
+        //    neighbours (bit 4 of ev marks them meanwhile), certified like the
+        //    winner.
+        const bool single = !per_phase && a.rescore_top == 0;
+        const bool want_ru = a.out.runner_za || a.out.runner_score || a.out.runner_orient;
+        int stage = 0, batch = 0;
+        for (;;) {
+            int nc = 0;
+            bool update = false;
+            if (stage == 0) {
+                const int left = a.rescore_top - evals;
+                if (a.rescore_top == 0 || left > 0) {
+                    const float thr =
+                        (batch == 0 || a.rescore_top > 0) ? -CUDART_INF_F : sm.st->T;
+                    const int K = a.rescore_top > 0 ? (left < kBatch ? left : kBatch)
+                                                    : (batch == 0 ? 2 : kBatch);
+                    // the first batch also finds the best bound after its picks:
+                    // when that cannot reach the batch's best score, no later batch
+                    // would find a candidate and the search ends without a scan
+                    block_topk(sm, Z, K, thr, rel, Emax,
+                               per_phase && batch > 0 && a.rescore_top == 0, nph,
+                               single && batch == 0);
+                    nc = sm.st->nc;
+                }
+                update = true;
+            } else if (stage == 1) {
+                // thread 0 gathers the next batch of neighbours; all threads run it
+                const float T = sm.st->T;
                 if (threadIdx.x == 0) {
-                    int q = sm.st->q, nc = 0;
-                    for (; q < qe && nc < kBatch; ++q) {
+                    const int qe = a.nbr_ptr[sm.st->bz + 1];
+                    int q = sm.st->q, n = 0;
+                    for (; q < qe && n < kBatch; ++q) {
                         const int z2 = a.nbr_idx[q];
                         if (sm.ev[z2] || sm.U[z2] * rel + Emax < 0.9f * T) continue;
-                        sm.cand[nc++] = z2;
+                        sm.cand[n++] = z2;
                         sm.ev[z2] = 2;
                     }
                     sm.st->q = q;
-                    sm.st->nref = nc;
+                    sm.st->nref = n;
                 }
                 __syncthreads();
-                const int nc = sm.st->nref;
-                if (nc == 0) break;
-                batch_spectra(a, b, nc, sr.x, sr.y, sm);
-                batch_transforms(a, nc, sm);
-                fold_batch(nc, N, false, nph, sm);
-                evals += nc;
-            }
-        }
-        if (a.out.runner_za || a.out.runner_score || a.out.runner_orient) {
-            // runner-up: the best axis other than the winner and its grid
-            // neighbours (bit 4 of ev marks them while this runs), certified
-            // like the winner: the best evaluated one so far, then the pending
-            // axes outside the neighbourhood whose bound can still beat it, in
-            // decreasing bound, until none can
-            const int bz = sm.st->bz;
-            const int q0 = a.nbr_ptr[bz], q1 = a.nbr_ptr[bz + 1];
-            for (int q = q0 + threadIdx.x; q < q1; q += kSelThreads) sm.ev[a.nbr_idx[q]] |= 4;
-            if (threadIdx.x == 0) sm.ev[bz] |= 4;
-            __syncthreads();
-            for (;;) {
+                nc = sm.st->nref;
+            } else if (stage == 2) {
+                // the best evaluated axis outside the neighbourhood so far
                 float v = -CUDART_INF_F;
                 unsigned zi = 0xffffffffu;
                 for (int z = threadIdx.x; z < Z; z += kSelThreads)
@@ -925,21 +927,55 @@ __global__ void __launch_bounds__(kSelThreads, 3) k_select_exact(SelectArgs a) {
                     sm.st->ru_v = bv;
                 }
                 __syncthreads();
-                // an all-zero image: every axis ties at 0, nothing to certify
-                if (sm.st->T == 0.f && sm.st->Tidx == 0u && sm.st->ru_z >= 0) break;
                 const bool have = sm.st->ru_z >= 0;
-                block_topk(sm, Z, have ? kBatch : 2, have ? sm.st->ru_v : -CUDART_INF_F, rel, Emax,
-                           false, nph);
-                const int nc = sm.st->nc;
-                if (nc == 0) break;
+                // an all-zero image: every axis ties at 0, nothing to certify
+                if (!(have && sm.st->T == 0.f && sm.st->Tidx == 0u)) {
+                    block_topk(sm, Z, have ? kBatch : 2, have ? sm.st->ru_v : -CUDART_INF_F,
+                               rel, Emax, false, nph);
+                    nc = sm.st->nc;
+                }
+            } else {
+                break;
+            }
+            if (nc > 0) {
                 batch_spectra(a, b, nc, sr.x, sr.y, sm);
                 batch_transforms(a, nc, sm);
-                fold_batch(nc, N, false, nph, sm);
+                fold_batch(nc, N, update, nph, sm);
                 evals += nc;
             }
-            for (int q = q0 + threadIdx.x; q < q1; q += kSelThreads) sm.ev[a.nbr_idx[q]] &= 3;
-            if (threadIdx.x == 0) sm.ev[bz] &= 3;
-            __syncthreads();
+            bool next = nc == 0;
+            if (stage == 0 && nc > 0) {
+                ++batch;
+                // an all-zero image: every axis ties at 0 and the lowest index has won
+                if (sm.st->T == 0.f && sm.st->Tidx == 0u) next = true;
+                if (single && batch == 1 && sm.st->next_u * rel + Emax < sm.st->T) next = true;
+            }
+            if (!next) continue;
+            // the next stage that applies
+            const int bz = sm.st->bz;
+            if (stage == 2) {
+                for (int q = a.nbr_ptr[bz] + threadIdx.x; q < a.nbr_ptr[bz + 1]; q += kSelThreads)
+                    sm.ev[a.nbr_idx[q]] &= 3;
+                if (threadIdx.x == 0) sm.ev[bz] &= 3;
+                __syncthreads();
+                stage = 3;
+                continue;
+            }
+            if (stage == 0 && want_ref && a.refine && sm.st->T > 0.f) {
+                __syncthreads();                 // every thread has read nc
+                if (threadIdx.x == 0) sm.st->q = a.nbr_ptr[bz];
+                stage = 1;
+                continue;
+            }
+            if (want_ru) {
+                for (int q = a.nbr_ptr[bz] + threadIdx.x; q < a.nbr_ptr[bz + 1]; q += kSelThreads)
+                    sm.ev[a.nbr_idx[q]] |= 4;
+                if (threadIdx.x == 0) sm.ev[bz] |= 4;
+                __syncthreads();
+                stage = 2;
+                continue;
+            }
+            stage = 3;
         }
         if (a.out.za_scores)
             for (int z = threadIdx.x; z < Z; z += kSelThreads)
