@@ -380,6 +380,7 @@ struct SelectArgs {
 // Spectra c_dir + i c_mir of the batch's candidate axes, scaled by 1/N, into
 // the rows y[c] (both halves of the conjugate-symmetric spectrum), stored as
 // their complex conjugates.
+template <bool PFA>
 __device__ void batch_spectra(const SelectArgs& a, int64_t b, int nc, int s_lo, int s_hi,
                               SelSmem& sm) {
     const int F = a.F, N = a.N, Fq = shell_row_stride(F) >> 2;
@@ -478,9 +479,8 @@ __device__ void batch_spectra(const SelectArgs& a, int64_t b, int nc, int s_lo, 
         const float mre = (A - B) * invN, mim = -(C + D) * invN;
         // stored conjugated: the inverse transform runs as a forward one
         float2* y = sm.y + c * N;
-        const bool pfa = sm.perm != nullptr;
-        y[pfa ? (int)sm.perm[f] : f] = make_float2(dre - mim, -(dim + mre));
-        if (f > 0 && 2 * f < N) y[pfa ? (int)sm.perm[N - f] : N - f] = make_float2(dre + mim, dim - mre);
+        y[PFA ? (int)sm.perm[f] : f] = make_float2(dre - mim, -(dim + mre));
+        if (f > 0 && 2 * f < N) y[PFA ? (int)sm.perm[N - f] : N - f] = make_float2(dre + mim, dim - mre);
     }
     __syncthreads();
 }
@@ -489,14 +489,15 @@ __device__ void batch_spectra(const SelectArgs& a, int64_t b, int nc, int s_lo, 
 // taken as the conjugate of the forward transform of conj(y) (the rows hold
 // conj(y)); the argmax over
 // (k, mirror) with the correlation at k - 1, k, k + 1 goes to res[c].
+template <bool PFA>
 __device__ void batch_transforms(const SelectArgs& a, int nc, SelSmem& sm) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, N = a.N;
     for (int c = warp; c < nc; c += kSelWarps) {
         float2* row = sm.y + c * N;
         float2* alt = sm.yt + c * N;
         const float2* out;
-        const uint16_t* pout = sm.pout;     // non-null: bin k at out[pout[k]]
-        if (pout) {
+        const uint16_t* pout = sm.pout;     // PFA: bin k at out[pout[k]]
+        if constexpr (PFA) {
             warp_pfa360(row, nullptr, lane);
             out = row;
         } else if (a.rad.n > 0) {
@@ -520,7 +521,7 @@ __device__ void batch_transforms(const SelectArgs& a, int nc, SelSmem& sm) {
         float bv = -CUDART_INF_F;
         unsigned bi = 0xffffffffu;
         for (int k = lane; k < N; k += 32) {
-            const float2 v = out[pout ? (int)pout[k] : k];
+            const float2 v = out[PFA ? (int)pout[k] : k];
             if (better(v.x, (unsigned)k, bv, bi)) {
                 bv = v.x;
                 bi = (unsigned)k;
@@ -534,8 +535,8 @@ __device__ void batch_transforms(const SelectArgs& a, int nc, SelSmem& sm) {
         if (lane == 0) {
             const int m = (int)(bi / (unsigned)N), k = (int)bi - m * N;
             const int km = (k + N - 1) % N, kp = (k + 1) % N;
-            const float2 ym = out[pout ? (int)pout[km] : km], y0 = out[pout ? (int)pout[k] : k],
-                         yp = out[pout ? (int)pout[kp] : kp];
+            const float2 ym = out[PFA ? (int)pout[km] : km], y0 = out[PFA ? (int)pout[k] : k],
+                         yp = out[PFA ? (int)pout[kp] : kp];
             float* r = sm.res + 5 * c;
             r[0] = bv;
             r[1] = __uint_as_float(bi);
@@ -744,6 +745,9 @@ __host__ __device__ inline size_t sel_items(int F) {
     return (size_t)(kSelThreads > kBatch * Fq ? kSelThreads : kBatch * Fq);
 }
 
+// PFA: N = 360 with the prime-factor inverse transform, compiled alone (the
+// radix transforms' code stays out of this kernel).
+template <bool PFA>
 __global__ void __launch_bounds__(kSelThreads, 3) k_select_exact(SelectArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Z = a.Z, F = a.F, N = a.N;
@@ -773,7 +777,7 @@ __global__ void __launch_bounds__(kSelThreads, 3) k_select_exact(SelectArgs a) {
     sm.slist = reinterpret_cast<uint16_t*>(take(sizeof(uint16_t) * kBatch * a.Spad));
     sm.slen = reinterpret_cast<int*>(take(sizeof(int) * kBatch));
     sm.perm = sm.pout = nullptr;
-    if (N == 360) {
+    if (PFA) {
         sm.perm = reinterpret_cast<uint16_t*>(take(sizeof(uint16_t) * 360));
         sm.pout = reinterpret_cast<uint16_t*>(take(sizeof(uint16_t) * 360));
     }
@@ -786,12 +790,13 @@ __global__ void __launch_bounds__(kSelThreads, 3) k_select_exact(SelectArgs a) {
     const bool per_phase = a.out.phase_score != nullptr && nph > 1;
 
     for (int i = threadIdx.x; i < N; i += kSelThreads) {
-        double s, c;
-        sincospi(2.0 * (double)i / (double)N, &s, &c);
-        sm.tw[i] = make_float2((float)c, (float)s);
-        if (sm.perm) {
+        if constexpr (PFA) {
             sm.perm[i] = (uint16_t)pfa360_in(i);
             sm.pout[i] = (uint16_t)pfa360_out(i);
+        } else {
+            double s, c;
+            sincospi(2.0 * (double)i / (double)N, &s, &c);
+            sm.tw[i] = make_float2((float)c, (float)s);
         }
     }
     const float rel = 1.0f + 1e-5f;     // FP32 accumulation of U and of the scores
@@ -938,8 +943,8 @@ __global__ void __launch_bounds__(kSelThreads, 3) k_select_exact(SelectArgs a) {
                 break;
             }
             if (nc > 0) {
-                batch_spectra(a, b, nc, sr.x, sr.y, sm);
-                batch_transforms(a, nc, sm);
+                batch_spectra<PFA>(a, b, nc, sr.x, sr.y, sm);
+                batch_transforms<PFA>(a, nc, sm);
                 fold_batch(nc, N, update, nph, sm);
                 evals += nc;
             }
@@ -1044,16 +1049,21 @@ void launch_select_exact(const acom_plan_s* p, const float* Xsr, const float* Xs
                  p->smask, oin};
     a.eta_rs = (float)((double)a.eta * std::sqrt((double)p->Spad));
     const size_t smem = select_smem_bytes(p->Z, p->N, p->F, p->Spad);
-    set_max_dynamic_smem((const void*)k_select_exact, smem);
+    const bool pfa = p->N == 360;
+    const void* kern = pfa ? (const void*)k_select_exact<true> : (const void*)k_select_exact<false>;
+    set_max_dynamic_smem(kern, smem);
     int dev = 0, nsm = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_select_exact, kSelThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSelThreads, smem);
     int64_t grid = (int64_t)nsm * (per_sm > 0 ? per_sm : 1);
     if (grid > nb) grid = nb;
     if (grid <= 0) return;
     prof_begin(kKSelect, st);
-    k_select_exact<<<(int)grid, kSelThreads, smem, st>>>(a);
+    if (pfa)
+        k_select_exact<true><<<(int)grid, kSelThreads, smem, st>>>(a);
+    else
+        k_select_exact<false><<<(int)grid, kSelThreads, smem, st>>>(a);
     prof_end(kKSelect, st);
 }
 

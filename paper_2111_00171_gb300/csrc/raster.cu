@@ -471,10 +471,13 @@ size_t raster_fft_smem_bytes(int N, int F, size_t peak_bytes) {
     return b;
 }
 
-template <class Loader>
+// PFA: N = 360 and its prime-factor transform, compiled alone (the radix
+// transforms' code stays out of this kernel), six frequencies per lane.
+template <class Loader, bool PFA>
 __global__ void __launch_bounds__(kRasterThreads, Loader::kMinBlocks)
 k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix rad,
              int* err) {
+    constexpr int kFL = PFA ? 6 : kMaxFPerLane;     // frequencies per lane (F <= 32 kFL)
     extern __shared__ __align__(16) unsigned char smem[];
     const int N = geo.N, F = geo.F, S = geo.S, Spad = geo.Spad;
     const int Fs = shell_row_stride(F);
@@ -489,7 +492,7 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
     // N = 360: the rows hold the bins in the prime-factor transform's input
     // order (bin j at s_perm[j]), the transform runs in place and leaves
     // frequency f at s_pout[f]
-    const bool pfa = N == 360;
+    constexpr bool pfa = PFA;
     uint16_t* s_perm = reinterpret_cast<uint16_t*>(s_int + 64);
     uint16_t* s_pout = s_perm + 360;
     float* scratch = reinterpret_cast<float*>(zb);     // after the last transform of an item
@@ -557,9 +560,9 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
             xsc = fp16_pattern_scale(sp, np, geo, dphi, s_int + 56);
             if (threadIdx.x == 0) ld.xscale_out()[item] = xsc;
         }
-        float fa[kMaxFPerLane];         // sum over this warp's shells of |X^_sf|^2, f = lane + 32 k
+        float fa[kFL];                  // sum over this warp's shells of |X^_sf|^2, f = lane + 32 k
 #pragma unroll
-        for (int k = 0; k < kMaxFPerLane; ++k) fa[k] = 0.f;
+        for (int k = 0; k < kFL; ++k) fa[k] = 0.f;
         int w_lo = Spad, w_hi = 0;      // this warp's non-zero shells
 
         for (int t0 = 0; t0 < Spad; t0 += kFftTile) {
@@ -731,7 +734,7 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
                 const int64_t srow = (item * (int64_t)Spad + sA) * Fs;
                 const int pw = pp;                               // word of the pair in a staged row
 #pragma unroll
-                for (int k = 0; k < kMaxFPerLane; ++k) {
+                for (int k = 0; k < kFL; ++k) {
                     const int f = lane + 32 * k;
                     if (f >= Fs) break;
                     float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
@@ -798,7 +801,7 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
         }
         __syncthreads();                 // every transform of the item is done
 #pragma unroll
-        for (int k = 0; k < kMaxFPerLane; ++k) {
+        for (int k = 0; k < kFL; ++k) {
             const int f = lane + 32 * k;
             if (f < F) scratch[warp * F + f] = fa[k];
         }
@@ -837,18 +840,24 @@ static bool launch_raster_fft(const RasterGeom& geo, const Loader& ld, int64_t n
     if (rad.n == 0 || geo.Spad % kFftTile != 0 || geo.F > 32 * kMaxFPerLane) return false;
     const size_t smem = raster_fft_smem_bytes(geo.N, geo.F, sizeof(typename Loader::PeakT));
     if (smem > 227 * 1024) return false;
-    set_max_dynamic_smem((const void*)k_raster_fft<Loader>, smem);
+    const bool pfa = geo.N == 360;
+    const void* kern = pfa ? (const void*)k_raster_fft<Loader, true>
+                           : (const void*)k_raster_fft<Loader, false>;
+    set_max_dynamic_smem(kern, smem);
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_fft<Loader>, kRasterThreads,
-                                                  smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRasterThreads, smem);
     int64_t grid = (int64_t)nsm * (per_sm > 0 ? per_sm : 1);
     if (grid > n_items) grid = n_items;
     prof_begin(cls, st);
-    k_raster_fft<Loader><<<(unsigned)grid, kRasterThreads, smem, st>>>(geo, ld, n_items, out, rad,
-                                                                        err);
+    if (pfa)
+        k_raster_fft<Loader, true><<<(unsigned)grid, kRasterThreads, smem, st>>>(
+            geo, ld, n_items, out, rad, err);
+    else
+        k_raster_fft<Loader, false><<<(unsigned)grid, kRasterThreads, smem, st>>>(
+            geo, ld, n_items, out, rad, err);
     prof_end(cls, st);
     return true;
 }
