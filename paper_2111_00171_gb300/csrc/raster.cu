@@ -24,6 +24,8 @@
 #include <cuda_fp16.h>
 #include <math_constants.h>
 
+#include <type_traits>
+
 #include "acom_internal.cuh"
 #include "fft_warp.cuh"
 
@@ -69,9 +71,9 @@ struct PatternLoader {
     using PeakT = PeakXY;
     static constexpr int kMinBlocks = 3;   // FFT raster CTAs per SM (74.5 KB of shared memory)
     PatternSource src;
-    __device__ void* xb_out() const { return src.xb; }
+    __host__ __device__ void* xb_out() const { return src.xb; }
     __device__ int xb_tiles() const { return src.PTs; }
-    __device__ bool xb_half() const { return src.xb_fp16 != 0; }
+    __host__ __device__ bool xb_half() const { return src.xb_fp16 != 0; }
     __device__ float* xscale_out() const { return src.xscale; }
     __device__ int xb_k0() const { return src.xb_k0; }
     __device__ int load(int64_t item, PeakXY* sp, int* s_warp, int* err) const {
@@ -110,9 +112,9 @@ struct PlanLoader {
     static constexpr int kMinBlocks = 2;
     PlanSource src;
     float delta;
-    __device__ void* xb_out() const { return nullptr; }
+    __host__ __device__ void* xb_out() const { return nullptr; }
     __device__ int xb_tiles() const { return 0; }
-    __device__ bool xb_half() const { return false; }
+    __host__ __device__ bool xb_half() const { return false; }
     __device__ float* xscale_out() const { return nullptr; }
     __device__ int xb_k0() const { return 0; }
     __device__ int load(int64_t item, Peak* sp, int* s_warp, int* err) const {
@@ -473,7 +475,9 @@ size_t raster_fft_smem_bytes(int N, int F, size_t peak_bytes) {
 
 // PFA: N = 360 and its prime-factor transform, compiled alone (the radix
 // transforms' code stays out of this kernel), six frequencies per lane.
-template <class Loader, bool PFA>
+// XB: the tensor-core copy written, 0 none (FP32 contraction or plan), 1 BF16,
+// 2 FP16 of 2^e X^ (each instance carries only its own output code).
+template <class Loader, bool PFA, int XB>
 __global__ void __launch_bounds__(kRasterThreads, Loader::kMinBlocks)
 k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix rad,
              int* err) {
@@ -519,7 +523,7 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
     const float invN = 1.0f / (float)N;
     float2* z = zb + warp * N;
     float2* zz = zt + warp * N;
-    __nv_bfloat16* xb = reinterpret_cast<__nv_bfloat16*>(ld.xb_out());
+    __nv_bfloat16* xb = XB ? reinterpret_cast<__nv_bfloat16*>(ld.xb_out()) : nullptr;
 
     for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int np = ld.load(item, sp, s_int, err);
@@ -554,7 +558,7 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
         }
         if (threadIdx.x < 16) s_int[16 + threadIdx.x] = 0;    // shells the tents reach
         __syncthreads();
-        const bool half = xb && ld.xb_half();
+        constexpr bool half = XB == 2;
         float xsc = 1.0f;
         if (half) {
             xsc = fp16_pattern_scale(sp, np, geo, dphi, s_int + 56);
@@ -567,7 +571,7 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
 
         for (int t0 = 0; t0 < Spad; t0 += kFftTile) {
             // the 16-bit copy of a tile the contraction never reads is skipped
-            const bool stg = xb && t0 + kFftTile > ld.xb_k0();
+            const bool stg = XB != 0 && t0 + kFftTile > ld.xb_k0();
             // pairs warp and warp + W of the tile
             for (int pp = warp; pp < kFftTile / 2; pp += W) {
                 const int sA = t0 + 2 * pp;
@@ -755,19 +759,19 @@ k_raster_fft(RasterGeom geo, Loader ld, int64_t n_items, RasterOut out, FftRadix
                     }
                     if (f < F) {
                         fa[k] = fmaf(ar, ar, fmaf(ai, ai, fmaf(br, br, fmaf(bi, bi, fa[k]))));
-                        if (out.re) {
+                        if (XB == 0 && out.re) {
                             const int64_t o = (item * (int64_t)F + f) * Spad + sA;
                             out.re[o] = ar;
                             out.re[o + 1] = br;
                             out.im[o] = ai;
                             out.im[o + 1] = bi;
                         }
-                        if (stg && half) {
+                        if (XB == 2 && stg) {
                             const __half2 vr = __floats2half2_rn(ar * xsc, br * xsc);
                             const __half2 vi = __floats2half2_rn(ai * xsc, bi * xsc);
                             stage[f * kFftStageWords + pw] = *reinterpret_cast<const uint32_t*>(&vr);
                             stage[(F + f) * kFftStageWords + pw] = *reinterpret_cast<const uint32_t*>(&vi);
-                        } else if (stg) {
+                        } else if (XB == 1 && stg) {
                             const __nv_bfloat162 vr = __floats2bfloat162_rn(ar, br);
                             const __nv_bfloat162 vi = __floats2bfloat162_rn(ai, bi);
                             stage[f * kFftStageWords + pw] = *reinterpret_cast<const uint32_t*>(&vr);
@@ -841,8 +845,14 @@ static bool launch_raster_fft(const RasterGeom& geo, const Loader& ld, int64_t n
     const size_t smem = raster_fft_smem_bytes(geo.N, geo.F, sizeof(typename Loader::PeakT));
     if (smem > 227 * 1024) return false;
     const bool pfa = geo.N == 360;
-    const void* kern = pfa ? (const void*)k_raster_fft<Loader, true>
-                           : (const void*)k_raster_fft<Loader, false>;
+    const int xk = ld.xb_out() ? (ld.xb_half() ? 2 : 1) : 0;
+    auto pick = [&](auto pfa_c) -> const void* {
+        constexpr bool P = decltype(pfa_c)::value;
+        return xk == 2 ? (const void*)k_raster_fft<Loader, P, 2>
+                       : (xk == 1 ? (const void*)k_raster_fft<Loader, P, 1>
+                                  : (const void*)k_raster_fft<Loader, P, 0>);
+    };
+    const void* kern = pfa ? pick(std::true_type{}) : pick(std::false_type{});
     set_max_dynamic_smem(kern, smem);
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
@@ -852,12 +862,8 @@ static bool launch_raster_fft(const RasterGeom& geo, const Loader& ld, int64_t n
     int64_t grid = (int64_t)nsm * (per_sm > 0 ? per_sm : 1);
     if (grid > n_items) grid = n_items;
     prof_begin(cls, st);
-    if (pfa)
-        k_raster_fft<Loader, true><<<(unsigned)grid, kRasterThreads, smem, st>>>(
-            geo, ld, n_items, out, rad, err);
-    else
-        k_raster_fft<Loader, false><<<(unsigned)grid, kRasterThreads, smem, st>>>(
-            geo, ld, n_items, out, rad, err);
+    void* args[] = {(void*)&geo, (void*)&ld, (void*)&n_items, (void*)&out, (void*)&rad, (void*)&err};
+    cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(kRasterThreads), args, smem, st);
     prof_end(cls, st);
     return true;
 }
