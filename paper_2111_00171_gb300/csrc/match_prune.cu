@@ -746,8 +746,11 @@ __host__ __device__ inline size_t sel_items(int F) {
 }
 
 // PFA: N = 360 with the prime-factor inverse transform, compiled alone (the
-// radix transforms' code stays out of this kernel).
-template <bool PFA>
+// radix transforms' code stays out of this kernel).  FULL: per-phase
+// certificates, top-K rescoring or the runner-up may be asked for; without
+// them the kernel carries only the one-certificate search and the winner's
+// neighbours (a smaller kernel runs faster).
+template <bool PFA, bool FULL>
 __global__ void __launch_bounds__(kSelThreads, 3) k_select_exact(SelectArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Z = a.Z, F = a.F, N = a.N;
@@ -787,7 +790,8 @@ __global__ void __launch_bounds__(kSelThreads, 3) k_select_exact(SelectArgs a) {
     const int nph = a.n_phases;
     for (int i = threadIdx.x; i <= nph; i += kSelThreads) sm.poff[i] = a.phase_off[i];
     // with per-phase scores requested, every phase's best is certified
-    const bool per_phase = a.out.phase_score != nullptr && nph > 1;
+    const bool per_phase = FULL && a.out.phase_score != nullptr && nph > 1;
+    const int rescore_top = FULL ? a.rescore_top : 0;
 
     for (int i = threadIdx.x; i < N; i += kSelThreads) {
         if constexpr (PFA) {
@@ -866,24 +870,24 @@ __global__ void __launch_bounds__(kSelThreads, 3) k_select_exact(SelectArgs a) {
         //  2 the runner-up: the best axis outside the winner and its grid
         //    neighbours (bit 4 of ev marks them meanwhile), certified like the
         //    winner.
-        const bool single = !per_phase && a.rescore_top == 0;
-        const bool want_ru = a.out.runner_za || a.out.runner_score || a.out.runner_orient;
+        const bool single = !per_phase && rescore_top == 0;
+        const bool want_ru = FULL && (a.out.runner_za || a.out.runner_score || a.out.runner_orient);
         int stage = 0, batch = 0;
         for (;;) {
             int nc = 0;
             bool update = false;
             if (stage == 0) {
-                const int left = a.rescore_top - evals;
-                if (a.rescore_top == 0 || left > 0) {
+                const int left = rescore_top - evals;
+                if (rescore_top == 0 || left > 0) {
                     const float thr =
-                        (batch == 0 || a.rescore_top > 0) ? -CUDART_INF_F : sm.st->T;
-                    const int K = a.rescore_top > 0 ? (left < kBatch ? left : kBatch)
-                                                    : (batch == 0 ? 2 : kBatch);
+                        (batch == 0 || rescore_top > 0) ? -CUDART_INF_F : sm.st->T;
+                    const int K = rescore_top > 0 ? (left < kBatch ? left : kBatch)
+                                                  : (batch == 0 ? 2 : kBatch);
                     // the first batch also finds the best bound after its picks:
                     // when that cannot reach the batch's best score, no later batch
                     // would find a candidate and the search ends without a scan
                     block_topk(sm, Z, K, thr, rel, Emax,
-                               per_phase && batch > 0 && a.rescore_top == 0, nph,
+                               per_phase && batch > 0 && rescore_top == 0, nph,
                                single && batch == 0);
                     nc = sm.st->nc;
                 }
@@ -905,7 +909,7 @@ __global__ void __launch_bounds__(kSelThreads, 3) k_select_exact(SelectArgs a) {
                 }
                 __syncthreads();
                 nc = sm.st->nref;
-            } else if (stage == 2) {
+            } else if (FULL && stage == 2) {
                 // the best evaluated axis outside the neighbourhood so far
                 float v = -CUDART_INF_F;
                 unsigned zi = 0xffffffffu;
@@ -1050,7 +1054,12 @@ void launch_select_exact(const acom_plan_s* p, const float* Xsr, const float* Xs
     a.eta_rs = (float)((double)a.eta * std::sqrt((double)p->Spad));
     const size_t smem = select_smem_bytes(p->Z, p->N, p->F, p->Spad);
     const bool pfa = p->N == 360;
-    const void* kern = pfa ? (const void*)k_select_exact<true> : (const void*)k_select_exact<false>;
+    const bool full = (out.phase_score != nullptr && p->n_phases > 1) || rescore_top > 0 ||
+                      out.runner_za || out.runner_score || out.runner_orient;
+    const void* kern = pfa ? (full ? (const void*)k_select_exact<true, true>
+                                   : (const void*)k_select_exact<true, false>)
+                           : (full ? (const void*)k_select_exact<false, true>
+                                   : (const void*)k_select_exact<false, false>);
     set_max_dynamic_smem(kern, smem);
     int dev = 0, nsm = 0, per_sm = 0;
     cudaGetDevice(&dev);
@@ -1060,10 +1069,8 @@ void launch_select_exact(const acom_plan_s* p, const float* Xsr, const float* Xs
     if (grid > nb) grid = nb;
     if (grid <= 0) return;
     prof_begin(kKSelect, st);
-    if (pfa)
-        k_select_exact<true><<<(int)grid, kSelThreads, smem, st>>>(a);
-    else
-        k_select_exact<false><<<(int)grid, kSelThreads, smem, st>>>(a);
+    void* args[] = {(void*)&a};
+    cudaLaunchKernel(kern, dim3((unsigned)grid), dim3(kSelThreads), args, smem, st);
     prof_end(kKSelect, st);
 }
 
