@@ -829,9 +829,9 @@ def read_profile(lib, acom):
 # the patterns of a launch (then another chunk size is scaled); the
 # contraction's does not (the plan is re-read once per tile wave).
 TRAFFIC_PER_LAUNCH = {
-    "select_exact": (5.738e9 + 156.4e6, 32768, ("match_prune.cu",), "678367a81e8343f2", "fp16",
+    "select_exact": (5.336e9 + 20.93e6, 32768, ("match_prune.cu",), "fa610bc3a2c270c8", "fp16",
                      "au_scan_256x256_1deg", True),
-    "raster_patterns": (21.40e6 + 8.037e9, 32768, ("raster.cu",), "0949631987c44546", "fp16",
+    "raster_patterns": (21.54e6 + 8.031e9, 32768, ("raster.cu",), "d3a55181529a4cae", "fp16",
                         "au_scan_256x256_1deg", True),
     "contract_tc": (7.005e9 + 115.0e6, 32768, ("match_tc.cu",), "b95d9dc1d59bc5f0", "fp16",
                     "au_scan_256x256_1deg", False),
