@@ -473,6 +473,24 @@ acom_status acom_kinematical_score(acom_plan plan, const acom_peaks_csr* peaks, 
                                    float* gn, void* cuda_stream);
 
 /*
+ * acom_kinematical_score_strain - the same with the reciprocal lattice of
+ * each pattern deformed by a small symmetric strain e: every reflection g of
+ * the plan moves to R (I + e) g, R = Exp(r) m^T (reading: strain moves the
+ * spots and changes their excitation errors; the amplitudes |g|^gamma
+ * |F_g|^omega keep their unstrained values).  ``strain`` [n][6] DEVICE
+ * (xx, xy, xz, yy, yz, zz; NULL means e = 0); ``strain_grad`` [n][6] DEVICE
+ * receives dS/de in the same component order, an off-diagonal component
+ * counting both symmetric entries (dS/de_kl = sum_g u_k g_l + u_l g_k with
+ * u = R^T dS/d(R (I + e) g)).  Other arguments, outputs and errors as for
+ * acom_kinematical_score, which is this call with both strain pointers NULL.
+ */
+acom_status acom_kinematical_score_strain(acom_plan plan, const acom_peaks_csr* peaks,
+                                          const float* orient, const float* r,
+                                          const float* strain, float rho, float* score,
+                                          float* grad, float* gn, float* strain_grad,
+                                          void* cuda_stream);
+
+/*
  * acom_bounds - the shell contraction alone: for every pattern and zone axis
  * the spectral bound U = (1/N) sum_f w_f max(|c_f^dir|, |c_f^mir|) of the
  * direct and mirror correlation spectra, which is >= max over phi3 of both C

@@ -44,6 +44,9 @@ kinematical_score         continuous correlation of the peaks with the
                           kinematical pattern of an orientation (Eqs. 6, 8;
                           the paper refines on the grid only: reading), its
                           gradient and Gauss-Newton matrix
+kinematical_score_strain  the same score with the reciprocal lattice deformed by a
+                          small symmetric strain e (g -> (I + e) g, reading),
+                          and dS/de beside dS/dw
 refine_continuous         gradient ascent of that score from a grid match
 refine_with_twin          the same from the match and from its in-plane
                           Friedel twin m Rz(pi), keeping the higher score
@@ -65,7 +68,9 @@ angle) and by noiseless off-grid patterns refined closer to the truth than
 the grid on average.  The forward model's excitation cut (``forward_spots``)
 is pinned by the zero-order-Laue-zone closed form at [001]; the paper's
 unique-radius shells (``unique_shell_radii``, ``plan_slice_unique``) by the
-fcc radius set, the [001] slice and self-indexing.
+fcc radius set, the [001] slice and self-indexing.  The strain gradient of
+``kinematical_score_strain`` is pinned by central finite differences of the
+score itself and by its reduction to ``kinematical_score`` at zero strain.
 """
 
 from __future__ import annotations
@@ -745,6 +750,60 @@ def kinematical_score(R, qx, qy, I, refl: Reflections, lam, sigma, rho, gamma_po
     H = ((np.einsum('g,gi,gj->ij', W, jx, jx) + np.einsum('g,gi,gj->ij', W, jy, jy)) / (rho * rho)
          + (np.einsum('g,gi,gj->ij', W, js, js) / se2 if omega > 0 else 0.0)) / nb
     return Score(S, grad, H)
+
+
+def kinematical_score_strain(R, e6, qx, qy, I, refl: Reflections, lam, sigma, rho,
+                             gamma_pow=1.0, omega=1.0):
+    """kinematical_score with the reciprocal lattice deformed by a small
+    symmetric strain e, components e6 = (xx, xy, xz, yy, yz, zz) in the
+    crystal frame: each reflection moves to R (I + e) g.  reading: lattice
+    strain, which the paper does not treat, moves the spots and changes their
+    excitation errors; the amplitudes |g|^gamma |F_g|^omega keep their
+    unstrained values (their change with |g| is second order for small e).
+    Returns (Score at that strain, dS/de6): with u_g = R^T dS/d(R (I+e) g),
+    dS/de_kl = sum_g u_k g_l + u_l g_k for k != l and sum_g u_k g_k on the
+    diagonal, g the unstrained vector."""
+    e6 = np.asarray(e6, dtype=np.float64)
+    E = np.array([[e6[0], e6[1], e6[2]], [e6[1], e6[3], e6[4]], [e6[2], e6[4], e6[5]]])
+    R = np.asarray(R, dtype=np.float64)
+    g0 = refl.g
+    v = g0 @ (np.eye(3) + E) @ R.T                              # rows R (I + e) g
+    k = beam_vector(lam)
+    kv = k + v
+    nkv = np.linalg.norm(kv, axis=1)
+    s = excitation_error(v, k)
+    ds_dv = -kv * ((nkv + s) / (nkv * nkv))[:, None]
+    gn = np.linalg.norm(g0, axis=1)
+    se2 = 2 * sigma * sigma / omega if omega > 0 else math.inf
+    b = gn ** gamma_pow * np.abs(refl.F) ** omega * np.exp(-(s * s) / (2 * se2))
+    nb = float(np.sqrt(np.sum(b * b)))
+    if nb == 0.0:
+        return Score(0.0, np.zeros(3), np.zeros((3, 3))), np.zeros(6)
+    db_dv = (-s / se2 * b)[:, None] * ds_dv
+    a = peak_weights(qx, qy, I, gamma_pow, omega)
+    p = np.stack([np.asarray(qx, np.float64), np.asarray(qy, np.float64)], axis=1)
+    d = p[None, :, :] - v[:, None, :2]
+    aE = a[None, :] * np.exp(-np.sum(d * d, axis=2) / (2 * rho * rho))
+    sE = aE.sum(axis=1)
+    W = b * sE
+    C = float(W.sum())
+    S = C / nb
+    dC_dv = np.zeros_like(v)
+    dC_dv[:, :2] = b[:, None] * np.einsum('gm,gmc->gc', aE, d) / (rho * rho)
+    dC_dv += sE[:, None] * db_dv
+    dS_dv = dC_dv / nb - (C / nb ** 3) * b[:, None] * db_dv
+    grad = np.cross(v, dS_dv).sum(axis=0)
+    zero = np.zeros(len(v))
+    jx = np.stack([zero, v[:, 2], -v[:, 1]], axis=1)
+    jy = np.stack([-v[:, 2], zero, v[:, 0]], axis=1)
+    js = np.cross(v, ds_dv)
+    H = ((np.einsum('g,gi,gj->ij', W, jx, jx) + np.einsum('g,gi,gj->ij', W, jy, jy)) / (rho * rho)
+         + (np.einsum('g,gi,gj->ij', W, js, js) / se2 if omega > 0 else 0.0)) / nb
+    u = dS_dv @ R                                               # rows R^T dS/dv
+    M = u.T @ g0                                                # sum_g u g^T
+    de = np.array([M[0, 0], M[0, 1] + M[1, 0], M[0, 2] + M[2, 0], M[1, 1], M[1, 2] + M[2, 1],
+                   M[2, 2]])
+    return Score(S, grad, H), de
 
 
 def so3_left_jacobian(r):

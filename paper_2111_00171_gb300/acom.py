@@ -30,7 +30,8 @@ EXPORTED = ("acom_plan_create", "acom_plan_destroy", "acom_plan_get_info",
             "acom_last_error",
             "acom_version", "acom_profile_enable", "acom_profile_reset", "acom_profile_read",
             "acom_kernel_launches", "acom_plan_concat", "acom_plan_get_phases", "acom_refine",
-            "acom_refine_defaults", "acom_kinematical_score", "acom_match_multi",
+            "acom_refine_defaults", "acom_kinematical_score", "acom_kinematical_score_strain",
+            "acom_match_multi",
             "acom_match_async", "acom_sync", "acom_autotune", "acom_device_allocations",
             "acom_set_device_wait_limit")
 
@@ -124,6 +125,8 @@ def load_library():
     lib.acom_refine.argtypes = [P, C.POINTER(PeaksCSR), C.POINTER(RefineOpts), P, P, P, P, P]
     lib.acom_refine_defaults.restype = RefineOpts
     lib.acom_kinematical_score.argtypes = [P, C.POINTER(PeaksCSR), P, P, C.c_float, P, P, P, P]
+    lib.acom_kinematical_score_strain.argtypes = [P, C.POINTER(PeaksCSR), P, P, P, C.c_float, P,
+                                                  P, P, P, P]
     lib.acom_match_multi.argtypes = [P, C.POINTER(PeaksCSR), C.POINTER(MatchOpts), C.c_int32,
                                      C.c_float, C.POINTER(Result), P]
     lib.acom_match_async.argtypes = [P, C.POINTER(PeaksCSR), C.POINTER(MatchOpts),
@@ -150,7 +153,8 @@ def load_library():
     lib.acom_version.restype = C.c_int32
     for name in ("acom_plan_create", "acom_plan_destroy", "acom_plan_get_info",
                  "acom_plan_concat", "acom_plan_get_phases", "acom_refine",
-                 "acom_kinematical_score", "acom_match_multi", "acom_match_async", "acom_sync",
+                 "acom_kinematical_score", "acom_kinematical_score_strain", "acom_match_multi",
+                 "acom_match_async", "acom_sync",
                  "acom_autotune",
                  "acom_plan_get_zone_axes", "acom_plan_get_spectra", "acom_match",
                  "acom_polar_spectra", "acom_bounds", "acom_bounds_static"):
@@ -449,9 +453,12 @@ class Plan:
                                      _ptr(alt), _ptr(score), _ptr(tw), _stream_ptr(stream)))
         return orient, score, tw
 
-    def kinematical_score(self, row_ptr, qx, qy, I, orient, r=None, rho=0.03, stream=None):
+    def kinematical_score(self, row_ptr, qx, qy, I, orient, r=None, rho=0.03, strain=None,
+                          stream=None):
         """acom_kinematical_score at Exp(r) m^T: (score [B], dS/dr [B][3],
-        Gauss-Newton matrix [B][6])."""
+        Gauss-Newton matrix [B][6]); with ``strain`` ([B][6] reciprocal-lattice
+        strain xx xy xz yy yz zz, acom_kinematical_score_strain) also dS/de
+        [B][6] as a fourth element."""
         import torch
         pk = self._csr(row_ptr, qx, qy, I)
         n = pk.n_patterns
@@ -459,11 +466,22 @@ class Plan:
         grad = torch.empty((n, 3), dtype=torch.float32, device="cuda")
         gn = torch.empty((n, 6), dtype=torch.float32, device="cuda")
         rr = None if r is None else r.detach().to(torch.float32).contiguous()
-        _check(self._lib.acom_kinematical_score(self.handle, C.byref(pk),
-                                                _ptr(orient.contiguous()), _ptr(rr), float(rho),
-                                                _ptr(score), _ptr(grad), _ptr(gn),
-                                                _stream_ptr(stream)))
-        return score, grad, gn
+        if strain is None:
+            _check(self._lib.acom_kinematical_score(self.handle, C.byref(pk),
+                                                    _ptr(orient.contiguous()), _ptr(rr),
+                                                    float(rho), _ptr(score), _ptr(grad),
+                                                    _ptr(gn), _stream_ptr(stream)))
+            return score, grad, gn
+        ee = strain.detach().to(torch.float32).contiguous()
+        if tuple(ee.shape) != (n, 6) or not ee.is_cuda:
+            raise ValueError("strain must be a CUDA tensor [B][6]")
+        de = torch.empty((n, 6), dtype=torch.float32, device="cuda")
+        _check(self._lib.acom_kinematical_score_strain(self.handle, C.byref(pk),
+                                                       _ptr(orient.contiguous()), _ptr(rr),
+                                                       _ptr(ee), float(rho), _ptr(score),
+                                                       _ptr(grad), _ptr(gn), _ptr(de),
+                                                       _stream_ptr(stream)))
+        return score, grad, gn, de
 
 
 def _autograd_function():
@@ -484,7 +502,22 @@ def _autograd_function():
             (g,) = ctx.saved_tensors
             return gs[:, None] * g, None, None, None, None
 
-    return KinematicalScore
+    class KinematicalScoreStrain(torch.autograd.Function):
+        """S(r, e) with the reciprocal lattice strained by e ([B][6]), with
+        dS/dr and dS/de from the same kernel launch."""
+
+        @staticmethod
+        def forward(ctx, r, e, plan, peaks, orient, rho):
+            s, g, _, de = plan.kinematical_score(*peaks, orient, r=r, rho=rho, strain=e)
+            ctx.save_for_backward(g, de)
+            return s
+
+        @staticmethod
+        def backward(ctx, gs):
+            g, de = ctx.saved_tensors
+            return gs[:, None] * g, gs[:, None] * de, None, None, None, None
+
+    return KinematicalScore, KinematicalScoreStrain
 
 
 def kinematical_score(r, plan, peaks, orient, rho=0.03):
@@ -494,7 +527,16 @@ def kinematical_score(r, plan, peaks, orient, rho=0.03):
     global _KIN
     if _KIN is None:
         _KIN = _autograd_function()
-    return _KIN.apply(r, plan, peaks, orient, rho)
+    return _KIN[0].apply(r, plan, peaks, orient, rho)
+
+
+def kinematical_score_strain(r, e, plan, peaks, orient, rho=0.03):
+    """Differentiable S(r, e): as kinematical_score, with ``e`` [B][6] the
+    reciprocal-lattice strain (xx, xy, xz, yy, yz, zz) of each pattern."""
+    global _KIN
+    if _KIN is None:
+        _KIN = _autograd_function()
+    return _KIN[1].apply(r, e, plan, peaks, orient, rho)
 
 
 _KIN = None

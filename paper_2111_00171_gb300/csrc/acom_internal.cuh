@@ -303,8 +303,8 @@ void launch_refine_orient(const acom_plan_s* p, const acom_peaks_csr* pk, int st
                           float* orient, const float* orient_alt, float* score, uint8_t* start_out,
                           cudaStream_t st);
 void launch_kin_score(const acom_plan_s* p, const acom_peaks_csr* pk, const float* orient,
-                      const float* r, float rho, float* score, float* grad, float* gn,
-                      cudaStream_t st);
+                      const float* r, const float* strain, float rho, float* score, float* grad,
+                      float* gn, float* strain_grad, cudaStream_t st);
 // multimatch.cu: peak deletion after a match, full-pattern score at a match
 void launch_delete_peaks(const acom_plan_s* p, const acom_peaks_csr* work, const acom_result& r,
                          float r_del, float d_min, cudaStream_t st);

@@ -997,9 +997,11 @@ acom_status acom_refine(acom_plan p, const acom_peaks_csr* peaks, const acom_ref
     return s;
 }
 
-acom_status acom_kinematical_score(acom_plan p, const acom_peaks_csr* peaks, const float* orient,
-                                   const float* r, float rho, float* score, float* grad,
-                                   float* gn, void* cuda_stream) {
+acom_status acom_kinematical_score_strain(acom_plan p, const acom_peaks_csr* peaks,
+                                          const float* orient, const float* r,
+                                          const float* strain, float rho, float* score,
+                                          float* grad, float* gn, float* strain_grad,
+                                          void* cuda_stream) {
     g_last_error.clear();
     if (!p || !orient) return set_error(ACOM_ERR_INVALID_ARG, "null argument");
     acom_status s = check_peaks(peaks);
@@ -1011,10 +1013,17 @@ acom_status acom_kinematical_score(acom_plan p, const acom_peaks_csr* peaks, con
     if (s != ACOM_OK) return s;
     cudaMemsetAsync(p->err, 0, sizeof(int), st);
     launch_check_row0(peaks->row_ptr, p->err, st);
-    launch_kin_score(p, peaks, orient, r, rho, score, grad, gn, st);
+    launch_kin_score(p, peaks, orient, r, strain, rho, score, grad, gn, strain_grad, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "score launch");
     return read_error_word(p, st);
+}
+
+acom_status acom_kinematical_score(acom_plan p, const acom_peaks_csr* peaks, const float* orient,
+                                   const float* r, float rho, float* score, float* grad,
+                                   float* gn, void* cuda_stream) {
+    return acom_kinematical_score_strain(p, peaks, orient, r, nullptr, rho, score, grad, gn,
+                                         nullptr, cuda_stream);
 }
 
 acom_refine_opts acom_refine_defaults(void) {

@@ -55,6 +55,8 @@ struct RefArgs {
     int twin;
     // score mode
     const float* r;            // [nb][3] axis-angle about orient, or nullptr
+    const float* strain;       // [nb][6] reciprocal-lattice strain (xx xy xz yy yz zz), or nullptr
+    float* strain_grad;        // [nb][6] dS/de, or nullptr
     float rho;
     // in / out
     float* orient;             // [nb][9] m (sample to crystal), row major
@@ -87,16 +89,31 @@ struct Acc {
     float C, nb2;
     float g1[3], g2[3];
     float h[6];          // xx, xy, xz, yy, yz, zz
+    float e1[6], e2[6];  // strain: sym(R^T dC/dv g^T), sym(b R^T db/dv g^T) (xx xy xz yy yz zz)
 };
 
-// Adds reflection g's terms to acc: this lane sums over all M peaks.
-__device__ __forceinline__ void add_reflection(const RefArgs& a, const float R[9], float4 g,
-                                               float inv_r2, float l2_half_inv_r2, bool exc,
-                                               float inv_se2, int64_t p0, int M, const float* px,
-                                               const float* py, const float* pa, Acc& acc) {
-    const float vx = R[0] * g.x + R[1] * g.y + R[2] * g.z;
-    const float vy = R[3] * g.x + R[4] * g.y + R[5] * g.z;
-    const float vz = R[6] * g.x + R[7] * g.y + R[8] * g.z;
+// g + e g for the symmetric strain e (xx xy xz yy yz zz)
+__device__ __forceinline__ void strained(const float e[6], float& x, float& y, float& z) {
+    const float x0 = x, y0 = y, z0 = z;
+    x = x0 + e[0] * x0 + e[1] * y0 + e[2] * z0;
+    y = y0 + e[1] * x0 + e[3] * y0 + e[4] * z0;
+    z = z0 + e[2] * x0 + e[4] * y0 + e[5] * z0;
+}
+
+// Adds reflection g's terms to acc: this lane sums over all M peaks.  STRAIN:
+// the reflection sits at R (I + e) g (reading: lattice strain moves the spots,
+// the amplitudes keep their unstrained values), and dS/de is accumulated.
+template <bool STRAIN>
+__device__ __forceinline__ void add_reflection(const RefArgs& a, const float R[9], const float e[6],
+                                               float4 g, float inv_r2, float l2_half_inv_r2,
+                                               bool exc, float inv_se2, int64_t p0, int M,
+                                               const float* px, const float* py, const float* pa,
+                                               Acc& acc) {
+    float gx = g.x, gy = g.y, gz = g.z;
+    if (STRAIN) strained(e, gx, gy, gz);
+    const float vx = R[0] * gx + R[1] * gy + R[2] * gz;
+    const float vy = R[3] * gx + R[4] * gy + R[5] * gz;
+    const float vz = R[6] * gx + R[7] * gy + R[8] * gz;
     const float v2 = vx * vx + vy * vy + vz * vz;
     const float kz = vz - a.inv_lam;
     const float nkv2 = vx * vx + vy * vy + kz * kz;
@@ -133,6 +150,29 @@ __device__ __forceinline__ void add_reflection(const RefArgs& a, const float R[9
     const float dcx = b * sEx * inv_r2 + sE * dbx;
     const float dcy = b * sEy * inv_r2 + sE * dby;
     const float dcz = sE * dbz;
+    if (STRAIN) {
+        // dv/de_kl = R (basis_kl) g with the unstrained g: with u = R^T dC/dv,
+        // dC/de_kl = u_k g_l + u_l g_k (k != l), u_k g_k (k = l); the same for
+        // the b db/dv part of the quotient rule
+        const float u1x = R[0] * dcx + R[3] * dcy + R[6] * dcz;
+        const float u1y = R[1] * dcx + R[4] * dcy + R[7] * dcz;
+        const float u1z = R[2] * dcx + R[5] * dcy + R[8] * dcz;
+        const float u2x = b * (R[0] * dbx + R[3] * dby + R[6] * dbz);
+        const float u2y = b * (R[1] * dbx + R[4] * dby + R[7] * dbz);
+        const float u2z = b * (R[2] * dbx + R[5] * dby + R[8] * dbz);
+        acc.e1[0] += u1x * g.x;
+        acc.e1[1] += u1x * g.y + u1y * g.x;
+        acc.e1[2] += u1x * g.z + u1z * g.x;
+        acc.e1[3] += u1y * g.y;
+        acc.e1[4] += u1y * g.z + u1z * g.y;
+        acc.e1[5] += u1z * g.z;
+        acc.e2[0] += u2x * g.x;
+        acc.e2[1] += u2x * g.y + u2y * g.x;
+        acc.e2[2] += u2x * g.z + u2z * g.x;
+        acc.e2[3] += u2y * g.y;
+        acc.e2[4] += u2y * g.z + u2z * g.y;
+        acc.e2[5] += u2z * g.z;
+    }
     acc.g1[0] += vy * dcz - vz * dcy;
     acc.g1[1] += vz * dcx - vx * dcz;
     acc.g1[2] += vx * dcy - vy * dcx;
@@ -165,9 +205,10 @@ __device__ __forceinline__ void add_reflection(const RefArgs& a, const float R[9
 // ... of each list and sums over all peaks; the per-lane sums are then added
 // by a butterfly.  Peaks: the first kRefPeakSmem in (px, py, pa), the rest
 // read from global memory.
-__device__ void score_at(const RefArgs& a, const float R[9], float rho, int64_t p0, int M,
-                         const float* px, const float* py, const float* pa, int* act, float& S,
-                         float grad[3], float H[6]) {
+template <bool STRAIN>
+__device__ void score_at(const RefArgs& a, const float R[9], const float e[6], float rho,
+                         int64_t p0, int M, const float* px, const float* py, const float* pa,
+                         int* act, float& S, float grad[3], float H[6], float de[6]) {
     const int lane = threadIdx.x & 31;
     const float inv_r2 = 1.0f / (rho * rho);
     // exp(-x / (2 rho^2)) = 2^(-x log2(e) / (2 rho^2)): the spot Gaussian as one
@@ -185,9 +226,11 @@ __device__ void score_at(const RefArgs& a, const float R[9], float rho, int64_t 
             bool active = false;
             if (gi < c1) {
                 const float4 g = __ldg(a.refl + gi);
-                const float vx = R[0] * g.x + R[1] * g.y + R[2] * g.z;
-                const float vy = R[3] * g.x + R[4] * g.y + R[5] * g.z;
-                const float vz = R[6] * g.x + R[7] * g.y + R[8] * g.z;
+                float gx = g.x, gy = g.y, gz = g.z;
+                if (STRAIN) strained(e, gx, gy, gz);
+                const float vx = R[0] * gx + R[1] * gy + R[2] * gz;
+                const float vy = R[3] * gx + R[4] * gy + R[5] * gz;
+                const float vz = R[6] * gx + R[7] * gy + R[8] * gz;
                 const float v2 = vx * vx + vy * vy + vz * vz;
                 const float kz = vz - a.inv_lam;
                 const float nkv = sqrtf(vx * vx + vy * vy + kz * kz);
@@ -201,8 +244,8 @@ __device__ void score_at(const RefArgs& a, const float R[9], float rho, int64_t 
         __syncwarp();
         if (a.pairs && lane == 0) atomicAdd(a.pairs, (unsigned long long)n * (unsigned long long)M);
         for (int j = lane; j < n; j += 32)
-            add_reflection(a, R, __ldg(a.refl + act[j]), inv_r2, l2_half_inv_r2, exc, inv_se2, p0, M,
-                           px, py, pa, acc);
+            add_reflection<STRAIN>(a, R, e, __ldg(a.refl + act[j]), inv_r2, l2_half_inv_r2, exc,
+                                   inv_se2, p0, M, px, py, pa, acc);
         __syncwarp();
     }
     acc.C = warp_sum(acc.C);
@@ -212,10 +255,17 @@ __device__ void score_at(const RefArgs& a, const float R[9], float rho, int64_t 
         acc.g2[i] = warp_sum(acc.g2[i]);
     }
     for (int i = 0; i < 6; ++i) acc.h[i] = warp_sum(acc.h[i]);
+    if (STRAIN)
+        for (int i = 0; i < 6; ++i) {
+            acc.e1[i] = warp_sum(acc.e1[i]);
+            acc.e2[i] = warp_sum(acc.e2[i]);
+        }
     if (!(acc.nb2 > 0.0f)) {
         S = 0.0f;
         grad[0] = grad[1] = grad[2] = 0.0f;
         for (int i = 0; i < 6; ++i) H[i] = 0.0f;
+        if (STRAIN)
+            for (int i = 0; i < 6; ++i) de[i] = 0.0f;
         return;
     }
     const float nb = sqrtf(acc.nb2);
@@ -224,6 +274,8 @@ __device__ void score_at(const RefArgs& a, const float R[9], float rho, int64_t 
     const float q = acc.C * inv_nb * inv_nb * inv_nb;
     for (int i = 0; i < 3; ++i) grad[i] = acc.g1[i] * inv_nb - q * acc.g2[i];
     for (int i = 0; i < 6; ++i) H[i] = acc.h[i] * inv_nb;
+    if (STRAIN)
+        for (int i = 0; i < 6; ++i) de[i] = acc.e1[i] * inv_nb - q * acc.e2[i];
 }
 
 // Rotation by |w| about w (Rodrigues), FP64, row major.  Below 0.05 rad the
@@ -324,7 +376,7 @@ __device__ float refine_run(const RefArgs& a, double* Rd, float* Rf, int64_t p0,
                                                    (float)t / (float)(a.steps - 1))
                               : a.rho_end;
         load9(Rf, R);
-        score_at(a, R, rho, p0, M, px, py, pa, act, S, g, H);
+        score_at<false>(a, R, nullptr, rho, p0, M, px, py, pa, act, S, g, H, nullptr);
         float w[3], E[9];
         lm_step(H, g, a.damping, a.max_step, w);
         exp_so3f(w, E);
@@ -341,7 +393,7 @@ __device__ float refine_run(const RefArgs& a, double* Rd, float* Rf, int64_t p0,
         }
     }
     load9(Rf, R);
-    score_at(a, R, a.rho_end, p0, M, px, py, pa, act, S, g, H);
+    score_at<false>(a, R, nullptr, a.rho_end, p0, M, px, py, pa, act, S, g, H, nullptr);
     return S;
 }
 
@@ -463,10 +515,11 @@ __global__ void __launch_bounds__(kRefWarps * 32) k_kin_score(RefArgs a) {
                     Rd[3 * i + j] = E[3 * i] * M0[j] + E[3 * i + 1] * M0[3 + j] +
                                     E[3 * i + 2] * M0[6 + j];
         }
-        float R[9], S, g[3], H[6];
+        float R[9], S, g[3], H[6], e[6], de[6];
         __syncwarp();
         for (int i = 0; i < 9; ++i) R[i] = (float)Rd[i];
-        score_at(a, R, a.rho, p0, M, px, py, pa, act, S, g, H);
+        for (int i = 0; i < 6; ++i) e[i] = a.strain ? a.strain[6 * b + i] : 0.0f;
+        score_at<true>(a, R, e, a.rho, p0, M, px, py, pa, act, S, g, H, de);
         if (lane == 0) {
             if (a.score) a.score[b] = S;
             if (a.grad) {
@@ -494,6 +547,8 @@ __global__ void __launch_bounds__(kRefWarps * 32) k_kin_score(RefArgs a) {
             }
             if (a.gn)
                 for (int i = 0; i < 6; ++i) a.gn[6 * b + i] = H[i];
+            if (a.strain_grad)
+                for (int i = 0; i < 6; ++i) a.strain_grad[6 * b + i] = de[i];
         }
     }
 }
@@ -578,11 +633,13 @@ void launch_refine_orient(const acom_plan_s* p, const acom_peaks_csr* pk, int st
 }
 
 void launch_kin_score(const acom_plan_s* p, const acom_peaks_csr* pk, const float* orient,
-                      const float* r, float rho, float* score, float* grad, float* gn,
-                      cudaStream_t st) {
+                      const float* r, const float* strain, float rho, float* score, float* grad,
+                      float* gn, float* strain_grad, cudaStream_t st) {
     RefArgs a = ref_args(p, pk);
     a.orient = const_cast<float*>(orient);
     a.r = r;
+    a.strain = strain;
+    a.strain_grad = strain_grad;
     a.rho = rho;
     a.score = score;
     a.grad = grad;

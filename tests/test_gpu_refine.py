@@ -102,6 +102,71 @@ def test_autograd_gradient_matches_finite_differences(plan):
         np.testing.assert_allclose(a[i], b[i], rtol=0, atol=2e-2 * np.abs(b[i]).max(), err_msg=str(i))
 
 
+def test_strained_score_and_gradients_match_oracle(plan):
+    """acom_kinematical_score_strain at strains of a few 1e-3 against the
+    oracle's kinematical_score_strain: the score within 1e-4 relative, dS/dr
+    and dS/de within 1e-3 of their largest entry.  At zero strain the strained
+    entry gives the plain entry's score and gradient."""
+    import torch
+    scan = synth.random_patterns(1104, n_patterns=48)
+    m0 = _starts(scan, 0.5, 5)
+    rng = np.random.default_rng(6)
+    r = (rng.normal(size=(scan.n_patterns, 3)) * 0.01).astype(np.float32)
+    e = (rng.normal(size=(scan.n_patterns, 6)) * 3e-3).astype(np.float32)
+    peaks = to_dev(scan)
+    om = torch.from_numpy(m0).cuda()
+    rd = torch.from_numpy(r).cuda()
+    s, g, _, de = plan.kinematical_score(*peaks, om, r=rd, rho=0.05,
+                                         strain=torch.from_numpy(e).cuda())
+    s, g, de = s.cpu().numpy(), g.cpu().numpy(), de.cpu().numpy()
+    refl = au_refl()
+    for b in range(scan.n_patterns):
+        qx, qy, I = scan.pattern(b)
+        rb = r[b].astype(np.float64)
+        R = O.so3_exp(rb) @ m0[b].astype(np.float64).T
+        sc, deo = O.kinematical_score_strain(R, e[b].astype(np.float64), qx, qy, I, refl,
+                                             LAM, 0.02, 0.05)
+        go = O.so3_left_jacobian(rb).T @ sc.grad
+        assert s[b] == pytest.approx(sc.S, rel=1e-4), b
+        np.testing.assert_allclose(g[b], go, rtol=0, atol=1e-3 * np.abs(go).max(), err_msg=str(b))
+        np.testing.assert_allclose(de[b], deo, rtol=0, atol=1e-3 * np.abs(deo).max(),
+                                   err_msg=str(b))
+    s0, g0, gn0 = plan.kinematical_score(*peaks, om, r=rd, rho=0.05)
+    s1, g1, gn1, _ = plan.kinematical_score(*peaks, om, r=rd, rho=0.05,
+                                            strain=torch.zeros((scan.n_patterns, 6),
+                                                               device="cuda"))
+    assert torch.equal(s0, s1) and torch.equal(g0, g1) and torch.equal(gn0, gn1)
+
+
+def test_strain_autograd_matches_finite_differences(plan):
+    """torch.autograd through acom.kinematical_score_strain: dS/de against
+    central differences of the FP32 score (step 1e-3 in each component)."""
+    import torch
+
+    from paper_2111_00171_gb300 import acom
+    scan = synth.random_patterns(1105, n_patterns=16)
+    peaks = to_dev(scan)
+    orient = torch.from_numpy(_starts(scan, 0.3, 7)).cuda()
+    rng = np.random.default_rng(8)
+    r = torch.from_numpy((rng.normal(size=(16, 3)) * 0.005).astype(np.float32)).cuda()
+    e0 = torch.from_numpy((rng.normal(size=(16, 6)) * 2e-3).astype(np.float32)).cuda()
+    e = e0.clone().requires_grad_(True)
+    S = acom.kinematical_score_strain(r, e, plan, peaks, orient, rho=0.05)
+    S.sum().backward()
+    h = 1e-3
+    fd = torch.zeros_like(e0)
+    for j in range(6):
+        d = torch.zeros_like(e0)
+        d[:, j] = h
+        sp = plan.kinematical_score(*peaks, orient, r=r, rho=0.05, strain=e0 + d)[0]
+        sm = plan.kinematical_score(*peaks, orient, r=r, rho=0.05, strain=e0 - d)[0]
+        fd[:, j] = (sp - sm) / (2 * h)
+    a, b = e.grad.cpu().numpy(), fd.cpu().numpy()
+    for i in range(16):
+        np.testing.assert_allclose(a[i], b[i], rtol=0, atol=3e-2 * np.abs(b[i]).max(),
+                                   err_msg=str(i))
+
+
 def test_refine_matches_oracle(plan):
     """acom_refine from starts 1.5 degrees off (every third a Friedel twin)
     against the oracle's refine_with_twin from the same FP32 starts."""

@@ -557,6 +557,54 @@ def test_score_axis_angle_gradient_matches_finite_differences():
     np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-7 * np.abs(fd).max())
 
 
+def test_strain_score_reduces_to_the_score_at_zero_strain():
+    """At e = 0 the strained score, its rotation gradient and Gauss-Newton
+    matrix are those of the unstrained score."""
+    refl, m, qx, qy, I = _score_case(23)
+    R = O.so3_exp([0.01, 0.02, -0.01]) @ m.T
+    a = O.kinematical_score(R, qx, qy, I, refl, LAM, 0.02, 0.05)
+    b, _ = O.kinematical_score_strain(R, np.zeros(6), qx, qy, I, refl, LAM, 0.02, 0.05)
+    assert b.S == pytest.approx(a.S, rel=1e-14)
+    np.testing.assert_allclose(b.grad, a.grad, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(b.H, a.H, rtol=1e-12, atol=1e-14)
+
+
+def test_strain_gradient_matches_finite_differences():
+    """dS/de for the six strain components against central differences of
+    the score, at zero and at a non-zero strain; the rotation gradient at
+    non-zero strain against differences too."""
+    refl, m, qx, qy, I = _score_case(24)
+    R = O.so3_exp([-0.01, 0.015, 0.01]) @ m.T
+    h = 1e-7
+    for e0 in (np.zeros(6), np.array([2e-3, -1e-3, 5e-4, -1.5e-3, 1e-3, 3e-3])):
+        sc, de = O.kinematical_score_strain(R, e0, qx, qy, I, refl, LAM, 0.02, 0.05)
+        fd = np.array([(O.kinematical_score_strain(R, e0 + h * d, qx, qy, I, refl, LAM, 0.02,
+                                                   0.05)[0].S
+                        - O.kinematical_score_strain(R, e0 - h * d, qx, qy, I, refl, LAM, 0.02,
+                                                     0.05)[0].S) / (2 * h) for d in np.eye(6)])
+        np.testing.assert_allclose(de, fd, rtol=1e-5, atol=1e-6 * np.abs(fd).max())
+        fw = np.array([(O.kinematical_score_strain(O.so3_exp(1e-6 * w) @ R, e0, qx, qy, I, refl,
+                                                   LAM, 0.02, 0.05)[0].S
+                        - O.kinematical_score_strain(O.so3_exp(-1e-6 * w) @ R, e0, qx, qy, I,
+                                                     refl, LAM, 0.02, 0.05)[0].S) / 2e-6
+                       for w in np.eye(3)])
+        np.testing.assert_allclose(sc.grad, fw, rtol=1e-6, atol=1e-7 * np.abs(fw).max())
+
+
+def test_strain_of_an_isotropic_scaling_moves_every_spot_radially():
+    """e = t I scales every reflection by (1 + t): the strained score at R
+    equals the unstrained score of the scaled reflection set."""
+    refl, m, qx, qy, I = _score_case(25)
+    R = m.T
+    t = 4e-3
+    sc, _ = O.kinematical_score_strain(R, np.array([t, 0, 0, t, 0, t]), qx, qy, I, refl, LAM, 0.02,
+                                       0.05)
+    # the scaled set keeps the unstrained amplitudes: scale g, then restore |g|^gamma
+    scaled = O.Reflections(g=refl.g * (1 + t), hkl=refl.hkl, F=refl.F / (1 + t))
+    ref = O.kinematical_score(R, qx, qy, I, scaled, LAM, 0.02, 0.05)
+    assert sc.S == pytest.approx(ref.S, rel=1e-12)
+
+
 def test_score_single_peak_single_reflection_closed_form():
     """One reflection and one peak: b / ||b|| = 1, so S = a exp(-|d|^2/2rho^2)."""
     g = np.array([[0.5, 0.2, 0.01]])
