@@ -79,3 +79,30 @@ def _tiny_plans():
     v0, v1, v2, om = O.cubic_triangle()
     za = O.zone_axis_grid(v0, v1, v2, 6.0, om)
     return [O.orientation_plan(refl, za, O.PlanParams(40, 0.0375, 72, 0.08, lam=0.01969))]
+
+
+def test_sweep_oracle_subset_agreement(monkeypatch):
+    """The sweep's oracle agreement: the patterns are matched by oracle worker
+    processes against the plan of the given step, and each run's choices are
+    compared with the oracle's argmax (its own argmax agrees on every
+    pattern; a choice moved off the argmax to a lower value does not).  A
+    small plan (6-degree grid, 40 shells, 72 bins) keeps this fast."""
+    tiny = dict(bench.W, S=40, dq=0.0375, N=72, delta=0.08, q_max=1.5)
+    monkeypatch.setattr(bench, "W", tiny)
+    scan = synth.grain_scan(1002, H=3, W=3, peaks="uniform10-60")
+    refl = O.reflections(np.eye(3) * 4.08, [[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0]],
+                         [79.0] * 4, [0.25] * 4, 1.5)
+    v0, v1, v2, om = O.cubic_triangle()
+    za = O.zone_axis_grid(v0, v1, v2, 6.0, om)
+    plan = O.orientation_plan(refl, za, O.PlanParams(40, 0.0375, 72, 0.08, lam=tiny["lam"]))
+    idx = np.array([0, 4, 8])
+    own, off = [], []
+    for b in idx:
+        mt = O.match_pattern(plan, *scan.pattern(int(b)))
+        own.append((mt.za, mt.k, mt.mirror))
+        C = mt.Cm if mt.mirror else mt.C
+        k2 = int(np.argmin(C[mt.za]))             # the axis' lowest bin
+        off.append((mt.za, k2, mt.mirror))
+    got = bench.oracle_subset_agreement(scan, idx, 6.0, len(za), [own, off], cores=2)
+    assert got[0] == "3/3"
+    assert got[1] == "0/3"
