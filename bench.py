@@ -830,11 +830,11 @@ def read_profile(lib, acom):
 # the patterns of a launch (then another chunk size is scaled); the
 # contraction's does not (the plan is re-read once per tile wave).
 TRAFFIC_PER_LAUNCH = {
-    "select_exact": (5.336e9 + 20.93e6, 32768, ("match_prune.cu",), "fa610bc3a2c270c8", "fp16",
+    "select_exact": (5.341e9 + 20.85e6, 32768, ("match_prune.cu",), "5542e2567c0d4a2d", "fp16",
                      "au_scan_256x256_1deg", True),
-    "raster_patterns": (21.54e6 + 8.031e9, 32768, ("raster.cu",), "d3a55181529a4cae", "fp16",
+    "raster_patterns": (21.56e6 + 8.031e9, 32768, ("raster.cu",), "65f790beeba11713", "fp16",
                         "au_scan_256x256_1deg", True),
-    "contract_tc": (7.005e9 + 115.0e6, 32768, ("match_tc.cu",), "b95d9dc1d59bc5f0", "fp16",
+    "contract_tc": (7.005e9 + 115.2e6, 32768, ("match_tc.cu",), "98bbb62117c87ae7", "fp16",
                     "au_scan_256x256_1deg", False),
 }
 
