@@ -19,6 +19,7 @@ CONFIGS = {
     "au_1deg_150x360": (1.0, 150, 0.01, 360),    # 256x256 Voronoi scan, 903 zone axes
     "au_6deg_40x72": (6.0, 40, 0.0375, 72),      # tiny case for quick checks
     "au_halfdeg_150x360": (0.5, 150, 0.01, 360),  # 512x512 sweep scan, 3486 zone axes
+    "au_6deg_200x72": (6.0, 200, 0.0075, 72),     # contraction K range over two ring stages
 }
 
 

@@ -362,6 +362,21 @@ def test_match_tc_matches_oracle(c1_tc, chunk):
 
 
 @pytest.mark.parametrize("precision", TC_PRECISIONS, ids=TC_IDS)
+def test_match_tc_two_stage_k_range(precision):
+    """A plan whose contraction K range spans two ring stages, the second only
+    partly filled (200 shells of 0.0075 1/A: K runs over 176 shells, a stage
+    of two K tiles, then one of a single K tile whose second full barrier is
+    only arrived on): the oracle's winners (up to ties) and FP32-level scores."""
+    plan = gpu_plan("au_6deg_200x72", precision=precision)
+    spad = (200 + 15) // 16 * 16
+    k_range = spad - plan.get_info()["k0"]
+    assert k_range > 128 and k_range % 128 <= 64, k_range
+    scan = synth.random_patterns(1007, n_patterns=60)
+    _match_and_compare(plan, oracle_plan("au_6deg_200x72"), scan, exhaustive=False)
+    plan.close()
+
+
+@pytest.mark.parametrize("precision", TC_PRECISIONS, ids=TC_IDS)
 def test_full_size_tc_equals_fp32(full_scan, precision):
     """The 256x256 scan, 1-degree plan: BF16 or FP16 certified pruning returns
     the FP32 winners (differences only at FP32 ties, checked against the oracle)."""
