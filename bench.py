@@ -231,9 +231,11 @@ def hexagonal_ops():
     return np.array(ops)
 
 
-def misorientation(m_est, m_true, ops=None):
+def misorientation(m_est, m_true, ops=None, spread=None):
     """Mean symmetry-reduced misorientation (deg), also reduced over the
-    in-plane Friedel twin m Rz(pi), and the zone-axis tilt error."""
+    in-plane Friedel twin m Rz(pi), and the zone-axis tilt error.  With a
+    dict ``spread``, also the median misorientation and the fraction of
+    patterns within 0.1 and 1 degree go into it."""
     ops = cubic_ops() if ops is None else ops
     me = m_est.astype(np.float64)
     # re-orthonormalise the FP32-stored matrices before taking angles
@@ -255,6 +257,10 @@ def misorientation(m_est, m_true, ops=None):
     we = np.einsum("sij,bj->sbi", ops, me[:, :, 2])
     c = np.abs(np.einsum("sbi,bi->sb", we, m_true[:, :, 2])).max(axis=0)
     tilt = np.degrees(np.arccos(np.clip(c, -1, 1)))
+    if spread is not None:
+        spread.update({"median_misorientation_deg": float(np.median(ang)),
+                       "frac_within_0.1_deg": float(np.mean(ang <= 0.1)),
+                       "frac_within_1_deg": float(np.mean(ang <= 1.0))})
     return float(ang.mean()), float(ang2.mean()), float(tilt.mean())
 
 
@@ -629,9 +635,10 @@ def main():
             accuracy[name] = {"mean_misorientation_deg": m, "mean_misorientation_friedel_deg": mt,
                               "mean_za_tilt_deg": t, "patterns": int(sel.sum())}
     else:
-        mis, mis_twin, tilt = misorientation(res["orient"], scan.truth)
+        spread = {}
+        mis, mis_twin, tilt = misorientation(res["orient"], scan.truth, spread=spread)
         accuracy = {"mean_misorientation_deg": mis, "mean_misorientation_friedel_deg": mis_twin,
-                    "mean_za_tilt_deg": tilt}
+                    "mean_za_tilt_deg": tilt, **spread}
     peaks, src = peaks_file()
     K = args.steps
     value = world * B * K / (dev_ms / 1e3)
