@@ -21,11 +21,12 @@
 //
 // One warp per pattern.  The lanes compute the excitation factor of their
 // reflections and ballot the ones that contribute into a list; each lane then
-// takes its share of the list and sums over all peaks (every lane reads the
-// same peak from shared memory); one butterfly reduction per evaluation gives
-// every lane the same totals.  Lane 0 solves the 3x3 step and composes the
-// rotation in FP64 (kept in shared memory); the FP32 copy used by the score
-// is broadcast.  A reflection whose excitation factor is below e^-18 of
+// takes its share of the list (the last, partial round split by peaks) and
+// sums over the peaks (the lanes of a round read the same peak from shared
+// memory); one butterfly reduction per evaluation gives every lane the same
+// totals.  Every lane takes the same 3x3 step in FP32 and nine lanes compose
+// the rotation in FP64, one element each (kept in shared memory with its FP32
+// copy, which the score reads).  A reflection whose excitation factor is below e^-18 of
 // its weight is skipped (its share of S is below FP32 resolution).
 #include <math_constants.h>
 
@@ -38,7 +39,7 @@ namespace {
 constexpr int kRefWarps = 8;                    // patterns per block
 constexpr int kRefPeakSmem = 128;               // peaks per pattern kept in shared memory
 constexpr float kExcCut = 18.0f;                // skip when s^2 / (2 sigma_e^2) > kExcCut
-constexpr int kRefActCap = 256;                 // contributing reflections listed at a time
+constexpr int kRefActCap = 512;                 // contributing reflections listed at a time
 
 struct RefArgs {
     const float4* refl;        // [G] (g_x, g_y, g_z, |g|^gamma |F_g|^omega)
@@ -100,15 +101,18 @@ __device__ __forceinline__ void strained(const float e[6], float& x, float& y, f
     z = z0 + e[2] * x0 + e[4] * y0 + e[5] * z0;
 }
 
-// Adds reflection g's terms to acc: this lane sums over all M peaks.  STRAIN:
+// Adds reflection g's terms over peaks m0 .. m1 - 1 to acc.  Every term is
+// linear in the three peak sums except ||b||^2 and the b db/dv parts, which
+// do not depend on the peaks: with `once` they are added too (a reflection
+// whose peaks are split between lanes adds them in one lane only).  STRAIN:
 // the reflection sits at R (I + e) g (reading: lattice strain moves the spots,
 // the amplitudes keep their unstrained values), and dS/de is accumulated.
 template <bool STRAIN>
 __device__ __forceinline__ void add_reflection(const RefArgs& a, const float R[9], const float e[6],
                                                float4 g, float inv_r2, float l2_half_inv_r2,
-                                               bool exc, float inv_se2, int64_t p0, int M,
-                                               const float* px, const float* py, const float* pa,
-                                               Acc& acc) {
+                                               bool exc, float inv_se2, int64_t p0, int m0,
+                                               int m1, bool once, const float* px,
+                                               const float* py, const float* pa, Acc& acc) {
     float gx = g.x, gy = g.y, gz = g.z;
     if (STRAIN) strained(e, gx, gy, gz);
     const float vx = R[0] * gx + R[1] * gy + R[2] * gz;
@@ -124,16 +128,16 @@ __device__ __forceinline__ void add_reflection(const RefArgs& a, const float R[9
     const float f = -(nkv + s) / nkv2;
     const float dsx = f * vx, dsy = f * vy, dsz = f * kz;
     float sE = 0.f, sEx = 0.f, sEy = 0.f;
-    const int Ms = M < kRefPeakSmem ? M : kRefPeakSmem;
+    const int Ms = m1 < kRefPeakSmem ? m1 : kRefPeakSmem;
 #pragma unroll 4
-    for (int m = 0; m < Ms; ++m) {               // every lane reads the same peak
+    for (int m = m0; m < Ms; ++m) {              // the lanes of a round read the same peak
         const float dx = px[m] - vx, dy = py[m] - vy;
         const float e = pa[m] * exp2f(-(dx * dx + dy * dy) * l2_half_inv_r2);
         sE += e;
         sEx = fmaf(e, dx, sEx);
         sEy = fmaf(e, dy, sEy);
     }
-    for (int m = kRefPeakSmem; m < M; ++m) {
+    for (int m = m0 > kRefPeakSmem ? m0 : kRefPeakSmem; m < m1; ++m) {
         const float x = a.qx[p0 + m], y = a.qy[p0 + m];
         const float w = peak_weight(x, y, a.I[p0 + m], a.gamma_pow, a.omega);
         const float dx = x - vx, dy = y - vy;
@@ -144,7 +148,7 @@ __device__ __forceinline__ void add_reflection(const RefArgs& a, const float R[9
     }
     const float W = b * sE;
     acc.C += W;
-    acc.nb2 = fmaf(b, b, acc.nb2);
+    if (once) acc.nb2 = fmaf(b, b, acc.nb2);
     const float c = exc ? -s * inv_se2 * b : 0.0f;             // db/ds
     const float dbx = c * dsx, dby = c * dsy, dbz = c * dsz;    // db/dv
     const float dcx = b * sEx * inv_r2 + sE * dbx;
@@ -157,9 +161,10 @@ __device__ __forceinline__ void add_reflection(const RefArgs& a, const float R[9
         const float u1x = R[0] * dcx + R[3] * dcy + R[6] * dcz;
         const float u1y = R[1] * dcx + R[4] * dcy + R[7] * dcz;
         const float u1z = R[2] * dcx + R[5] * dcy + R[8] * dcz;
-        const float u2x = b * (R[0] * dbx + R[3] * dby + R[6] * dbz);
-        const float u2y = b * (R[1] * dbx + R[4] * dby + R[7] * dbz);
-        const float u2z = b * (R[2] * dbx + R[5] * dby + R[8] * dbz);
+        const float bo = once ? b : 0.0f;
+        const float u2x = bo * (R[0] * dbx + R[3] * dby + R[6] * dbz);
+        const float u2y = bo * (R[1] * dbx + R[4] * dby + R[7] * dbz);
+        const float u2z = bo * (R[2] * dbx + R[5] * dby + R[8] * dbz);
         acc.e1[0] += u1x * g.x;
         acc.e1[1] += u1x * g.y + u1y * g.x;
         acc.e1[2] += u1x * g.z + u1z * g.x;
@@ -176,9 +181,11 @@ __device__ __forceinline__ void add_reflection(const RefArgs& a, const float R[9
     acc.g1[0] += vy * dcz - vz * dcy;
     acc.g1[1] += vz * dcx - vx * dcz;
     acc.g1[2] += vx * dcy - vy * dcx;
-    acc.g2[0] += b * (vy * dbz - vz * dby);
-    acc.g2[1] += b * (vz * dbx - vx * dbz);
-    acc.g2[2] += b * (vx * dby - vy * dbx);
+    if (once) {
+        acc.g2[0] += b * (vy * dbz - vz * dby);
+        acc.g2[1] += b * (vz * dbx - vx * dbz);
+        acc.g2[2] += b * (vx * dby - vy * dbx);
+    }
     // position part: jx = (0, vz, -vy), jy = (-vz, 0, vx)
     const float wp = W * inv_r2;
     acc.h[0] += wp * (vz * vz);
@@ -201,10 +208,12 @@ __device__ __forceinline__ void add_reflection(const RefArgs& a, const float R[9
 
 // S, dS/dw and the Gauss-Newton matrix of the warp's pattern at rotation R
 // (identical in every lane).  The reflections that contribute are listed in
-// the warp's act[] buffer kRefActCap at a time; lane l takes entries l, l + 32,
-// ... of each list and sums over all peaks; the per-lane sums are then added
-// by a butterfly.  Peaks: the first kRefPeakSmem in (px, py, pa), the rest
-// read from global memory.
+// the warp's act[] buffer kRefActCap at a time; the whole rounds of the list
+// give lane l entries l, l + 32, ... with all their peaks, and the rem < 32
+// entries left over are split into 32 / rem chunks of peaks each, one chunk
+// per lane, so that the last round does not leave most lanes idle; the
+// per-lane sums are then added by a butterfly.  Peaks: the first kRefPeakSmem
+// in (px, py, pa), the rest read from global memory.
 template <bool STRAIN>
 __device__ void score_at(const RefArgs& a, const float R[9], const float e[6], float rho,
                          int64_t p0, int M, const float* px, const float* py, const float* pa,
@@ -243,9 +252,20 @@ __device__ void score_at(const RefArgs& a, const float R[9], const float e[6], f
         }
         __syncwarp();
         if (a.pairs && lane == 0) atomicAdd(a.pairs, (unsigned long long)n * (unsigned long long)M);
-        for (int j = lane; j < n; j += 32)
+        const int whole = n & ~31;
+        for (int j = lane; j < whole; j += 32)
             add_reflection<STRAIN>(a, R, e, __ldg(a.refl + act[j]), inv_r2, l2_half_inv_r2, exc,
-                                   inv_se2, p0, M, px, py, pa, acc);
+                                   inv_se2, p0, 0, M, true, px, py, pa, acc);
+        const int rem = n - whole;
+        if (rem > 0) {
+            const int cps = 32 / rem;                // chunks per left-over reflection
+            if (lane < rem * cps) {
+                const int j = whole + lane / cps, c = lane - (lane / cps) * cps;
+                add_reflection<STRAIN>(a, R, e, __ldg(a.refl + act[j]), inv_r2, l2_half_inv_r2,
+                                       exc, inv_se2, p0, (M * c) / cps, (M * (c + 1)) / cps,
+                                       c == 0, px, py, pa, acc);
+            }
+        }
         __syncwarp();
     }
     acc.C = warp_sum(acc.C);
