@@ -22,12 +22,13 @@
 // One warp per pattern.  The lanes compute the excitation factor of their
 // reflections and ballot the ones that contribute into a list; each lane then
 // takes its share of the list (the last, partial round split by peaks) and
-// sums over the peaks (the lanes of a round read the same peak from shared
-// memory); one butterfly reduction per evaluation gives every lane the same
-// totals.  Every lane takes the same 3x3 step in FP32 and nine lanes compose
-// the rotation in FP64, one element each (kept in shared memory with its FP32
-// copy, which the score reads).  A reflection whose excitation factor is below e^-18 of
-// its weight is skipped (its share of S is below FP32 resolution).
+// sums over the peaks (in a whole round every lane reads the same peak from
+// shared memory); one butterfly reduction per evaluation gives every lane the
+// same totals.  Every lane takes the same 3x3 step in FP32 and nine lanes
+// compose the rotation in FP64, one element each (kept in shared memory with
+// its FP32 copy, which the score reads).  A reflection whose excitation
+// factor is below e^-18 of its weight is skipped (its share of S is below
+// FP32 resolution).
 #include <math_constants.h>
 
 #include "acom_internal.cuh"
@@ -130,7 +131,7 @@ __device__ __forceinline__ void add_reflection(const RefArgs& a, const float R[9
     float sE = 0.f, sEx = 0.f, sEy = 0.f;
     const int Ms = m1 < kRefPeakSmem ? m1 : kRefPeakSmem;
 #pragma unroll 4
-    for (int m = m0; m < Ms; ++m) {              // the lanes of a round read the same peak
+    for (int m = m0; m < Ms; ++m) {              // a whole round: every lane reads the same peak
         const float dx = px[m] - vx, dy = py[m] - vy;
         const float e = pa[m] * exp2f(-(dx * dx + dy * dy) * l2_half_inv_r2);
         sE += e;
